@@ -1,0 +1,151 @@
+"""Pins of the oracle's assembled operator (eqs. "cutfem_nitsche",
+"cutfem-ghost", "weak-equation") against closed forms and invariants."""
+
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spl
+from numpy.polynomial import Polynomial
+
+from oracle.basis import Basis1D
+from oracle.fem import (Level, assemble_level, assemble_rhs, cut_cell_matrix,
+                        l2_error, uncut_stiffness)
+from oracle.levelset import Plane, Sphere
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _q2_1d():
+    g = json.load(open(os.path.join(GOLD, "q2_reference_1d.json")))
+    return np.array(g["mass_times_30"]) / 30.0, np.array(g["stiffness_times_3"]) / 3.0
+
+
+def _kron_stiffness(K1, M1, d, h):
+    out = 0
+    for k in range(d):
+        mats = [K1 if j == k else M1 for j in range(d)]
+        t = mats[d - 1]
+        for j in range(d - 2, -1, -1):
+            t = np.kron(t, mats[j])
+        out = out + t
+    return out * h ** (d - 2)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_uncut_stiffness_is_kronecker_of_closed_form_1d(d):
+    M1, K1 = _q2_1d()
+    lev = Level(Sphere([0.0] * d, 0.5), d, 4, 2)
+    K = uncut_stiffness(lev)
+    assert np.allclose(K, _kron_stiffness(K1, M1, d, lev.h), rtol=0, atol=1e-13)
+
+
+def test_cut_cell_matrix_half_cell_plane_closed_form():
+    """A plane x = x0 + h/2 cuts a 2D cell in half: volume part is the
+    stiffness over the half cell, Nitsche part is the line integral at
+    xi = 1/2 with normal e_x, both written from exact 1D integrals."""
+    p = 2
+    b = Basis1D(p)
+    N = 4
+    ls = Plane([1.0, 0.0], -0.75)  # cells [-1, -0.5] x . are cut in half
+    lev = Level(ls, 2, N, p)
+    h = lev.h
+    c = int(np.nonzero(lev.cut)[0][0])
+    gD = 80.0
+    K = cut_cell_matrix(lev, c, gD, 4)
+    # exact 1D integrals on [0, 1/2] and [0, 1]
+    def integ(P, a, bnd):
+        Q = P.integ()
+        return Q(bnd) - Q(a)
+    L = b.polys
+    Mh = np.array([[integ(L[i] * L[j], 0, 0.5) for j in range(3)] for i in range(3)])
+    Kh = np.array([[integ(L[i].deriv() * L[j].deriv(), 0, 0.5) for j in range(3)] for i in range(3)])
+    M1 = np.array([[integ(L[i] * L[j], 0, 1) for j in range(3)] for i in range(3)])
+    K1 = np.array([[integ(L[i].deriv() * L[j].deriv(), 0, 1) for j in range(3)] for i in range(3)])
+    # local index = a_x + 3 a_y -> kron(Y, X)
+    vol = np.kron(M1, Kh) + np.kron(K1, Mh)
+    v = np.array([P(0.5) for P in L])
+    dv = np.array([P.deriv()(0.5) for P in L]) / h
+    Sx = -(np.outer(v, dv) + np.outer(dv, v)) + gD / h * np.outer(v, v)
+    nit = np.kron(M1 * h, Sx)
+    assert np.allclose(K, vol + nit, rtol=0, atol=1e-12)
+
+
+@pytest.fixture(scope="module")
+def disk():
+    ls = Sphere([0.031, 0.017], 0.7)
+    lev = Level(ls, 2, 16, 2)
+    A, info = assemble_level(lev, 80.0, [0.1, 0.1], 4)
+    return lev, A, info
+
+
+def test_symmetric(disk):
+    lev, A, _ = disk
+    assert abs(A - A.T).max() <= 1e-14 * abs(A).max()
+
+
+def test_constant_energy_is_nitsche_penalty_times_perimeter(disk):
+    """Gradients and ghost jumps of a constant vanish, so 1^T A 1 =
+    gamma_D/h * sum of surface weights = gamma_D/h |Gamma_h|."""
+    lev, A, _ = disk
+    from oracle.quadrature import cut_cell_rule
+    S = 0.0
+    for c in np.nonzero(lev.cut)[0]:
+        lo = lev.cell_lo[c]
+        S += cut_cell_rule(lev.ls, lo, lo + lev.h, 4)[3].sum()
+    one = np.ones(lev.ndof)
+    assert one @ (A @ one) == pytest.approx(80.0 / lev.h * S, rel=1e-12)
+    assert S == pytest.approx(2 * math.pi * 0.7, rel=1e-8)
+
+
+def test_ghost_penalty_vanishes_on_global_polynomials(disk):
+    lev, A, info = disk
+    rows, cols, vals = [], [], []
+    for (k, c1, c2) in info["ghost_faces"]:
+        D = np.concatenate([lev.cell_dofs(c1), lev.cell_dofs(c2)])
+        rows.append(np.repeat(D, D.size))
+        cols.append(np.tile(D, D.size))
+        vals.append(info["Gref"][k].ravel())
+    G = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=A.shape)
+    X = lev.node_coords(lev.dof_nodes)
+    for u in (X[:, 0] * X[:, 1] ** 2, 1 + X[:, 0] ** 2 - 3 * X[:, 1], X[:, 0] ** 2 * X[:, 1] ** 2):
+        assert np.abs(G @ u).max() < 1e-12 * np.abs(G).max() * np.abs(u).max() * 10
+    # ... and does not vanish on a kink
+    assert np.abs(G @ np.abs(X[:, 0] - 0.013)).max() > 1e-6
+
+
+def test_patch_test_reproduces_q2_polynomial():
+    """u in Q_2 (globally) with f = -Laplace u and g = u: the discrete
+    solution is the interpolant of u (consistency of the Nitsche terms and
+    the right-hand side)."""
+    ls = Sphere([0.031, 0.017], 0.7)
+    lev = Level(ls, 2, 16, 2)
+    # the default q = p + 2 leaves an O(h^(2q)) quadrature residual of ~1e-5
+    # here; q = 10 takes it below the solve tolerance
+    A, _ = assemble_level(lev, 80.0, [0.1, 0.1], 10)
+    u = lambda X: 1 + X[:, 0] - 2 * X[:, 1] + 0.5 * X[:, 0] * X[:, 1] + 0.3 * X[:, 0] ** 2 * X[:, 1] - 0.2 * X[:, 1] ** 2
+    f = lambda X: -(0.6 * X[:, 1] - 0.4)
+    b = assemble_rhs(lev, 80.0, 10, u=u, f=f)
+    x = spl.spsolve(A.tocsc(), b)
+    X = lev.node_coords(lev.dof_nodes)
+    assert np.abs(x - u(X)).max() < 1e-9
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_l2_convergence_rate_p_plus_one(p):
+    ls = Sphere([0.031, 0.017], 0.7)
+    errs = []
+    Ns = (8, 16, 32)
+    for N in Ns:
+        lev = Level(ls, 2, N, p)
+        gD = 20.0 * p * p
+        A, _ = assemble_level(lev, gD, [0.1] * p, p + 2)
+        b = assemble_rhs(lev, gD, p + 2)
+        x = spl.spsolve(A.tocsc(), b)
+        errs.append(l2_error(lev, x, p + 2))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+    assert rates[-1] == pytest.approx(p + 1, abs=0.3)
