@@ -3,12 +3,17 @@ matrix: the plain definition of A_l.
 
   a_l(u, v) = (grad u, grad v)_Omega - (d_n u, v)_Gamma - (u, d_n v)_Gamma
               + (gamma_D / h) (u, v)_Gamma                       eq. "cutfem_nitsche"
-  g_l(u, v) = sum_{F in F_G} sum_{k=1..p} gamma_k h^(2k+1)/(k!)^2
+  g_l(u, v) = sum_{F in F_G} sum_{k=1..p} gamma_k h^(2k-1)/(k!)^2
               ([d_n^k u], [d_n^k v])_F                           eq. "cutfem-ghost"
 
 Readings (the paper leaves them open):
 * active cell: min_T phi < 0; cut cell: min_T phi < 0 < max_T phi;
 * the k = 0 ghost term vanishes for continuous V_l and is dropped;
+* the face weight is h_F^(2k-1)/(k!)^2, the scaling of the face ghost penalty
+  the paper cites (Burman-Hansbo 2012, and the deal.II step-85 construction it
+  says it follows); the printed h_F^(2k+1) weakens the penalty by h^2 against
+  the stiffness, and with it A_l is indefinite on a 64^3 ball (a sliver cut at
+  the top cap gives a negative eigenvalue of a patch matrix);
 * h_F = h; gamma_D is one constant per level, used as gamma_D / h;
 * right-hand side b_i = (f, phi_i)_Omega + (g, gamma_D/h phi_i - d_n phi_i)_Gamma
   (the consistent Nitsche data term for u = g on Gamma);
@@ -161,7 +166,7 @@ def ghost_face_matrix(lev, k, gammas):
                 for jj, j in enumerate(tdims):
                     val = val * lev.basis.eval(tpts[:, jj])[a[j]]
                 J[side * nb + i] = val if side == 0 else -val
-        coef = gammas[m - 1] * h ** (2 * m + 1) / math.factorial(m) ** 2
+        coef = gammas[m - 1] * h ** (2 * m - 1) / math.factorial(m) ** 2
         Gm += coef * (J * tw) @ J.T * h ** (d - 1)
     return Gm
 

@@ -139,7 +139,7 @@ def test_patch_test_reproduces_q2_polynomial():
 def test_l2_convergence_rate_p_plus_one(p):
     ls = Sphere([0.031, 0.017], 0.7)
     errs = []
-    Ns = (8, 16, 32)
+    Ns = (16, 32, 64)
     for N in Ns:
         lev = Level(ls, 2, N, p)
         gD = 20.0 * p * p
