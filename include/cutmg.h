@@ -1,0 +1,185 @@
+/*
+ * cutmg: GB300 (sm_103a) CutFEM multigrid — C ABI.
+ *
+ * Solves the Nitsche-Dirichlet Poisson problem on a level-set domain cut out
+ * of a Cartesian background mesh, with face-based ghost penalties, by CG
+ * preconditioned with a V-cycle whose smoother is the multiplicative
+ * vertex-patch smoother (Cui & Kanschat, arXiv 2508.11608):
+ *   operator       eqs. "cutfem_nitsche" and "cutfem-ghost" (Sec. 2.1)
+ *   transfer       embedding prolongation, restriction = transpose (Sec. 2.2)
+ *   smoother       eqs. "local-solver", "smoother", "smoother-split" (Sec. 2.3, Sec. 3)
+ *
+ * Conventions shared by every call:
+ *  - Vectors are caller-owned DEVICE arrays of doubles of length
+ *    cf_level_n_dofs(problem, level) (cf_n_dofs for the finest level).  DoFs
+ *    are the lattice nodes of active cells, numbered by increasing lattice
+ *    flat index i_0 + n i_1 + n^2 i_2 (n = p N + 1 nodes per direction), i.e.
+ *    first coordinate fastest; cf_dof_lattice returns that index per DoF.
+ *  - Every call that takes a stream is stream-ordered and does not
+ *    synchronise unless stated.  `stream` is a cudaStream_t (0 = legacy
+ *    default stream).
+ *  - Every call returns a cf_status; on failure cf_last_error() holds a
+ *    message (thread-local).  A problem handle stays valid after CF_ENOCONV.
+ *  - The problem handle owns every hierarchy buffer on the device it was
+ *    created on (the current device at cf_setup).
+ *  - Supported: dim 2 with degree 1..3, dim 3 with degree 1..2.
+ */
+#ifndef CUTMG_H
+#define CUTMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CF_OK = 0,
+  CF_EINVAL = 1,
+  CF_ENOMEM = 2,
+  CF_ECUDA = 3,
+  CF_ENOCONV = 4,
+  CF_ETIMEOUT = 5,
+  CF_EUNSUPPORTED = 6
+} cf_status;
+
+/* Level-set kinds (Omega = {phi < 0}; Sec. 4 uses an analytic level set). */
+typedef enum {
+  CF_LS_SPHERE = 0, /* phi = |x - center| - radius (disk in 2D)               */
+  CF_LS_PLANE = 1   /* phi = normal . x - offset (half space; used in tests)   */
+} cf_levelset_kind;
+
+typedef enum { CF_FP64 = 0, CF_MIXED = 1 } cf_precision;
+
+/* Background mesh [lo, hi]^dim with n_cells cells per direction on the finest
+ * level and n_levels levels; level l has n_cells / 2^(n_levels-1-l) cells per
+ * direction (Sec. 2.1 nested hierarchy).  n_cells must be divisible by
+ * 2^(n_levels-1). */
+typedef struct {
+  int dim;
+  int n_cells;
+  double lo, hi;
+  int n_levels;
+} cf_mesh;
+
+typedef struct {
+  int kind;          /* cf_levelset_kind */
+  double center[3];  /* sphere centre */
+  double radius;     /* sphere radius */
+  double normal[3];  /* plane normal */
+  double offset;     /* plane offset */
+} cf_levelset;
+
+/* Method parameters.  Zero / negative entries select the defaults given. */
+typedef struct {
+  double gamma_D;        /* Nitsche penalty, used as gamma_D / h (eq. "cutfem_nitsche"); default 20 p^2 */
+  double gamma_ghost[4]; /* ghost penalty gamma_k, k = 1..p (eq. "cutfem-ghost"); default 0.1 each */
+  int n_c;               /* repetitions of the cut-patch sweep (eq. "smoother-split"); default 2 */
+  int quad_q;            /* Gauss points per sub-interval of the cut-cell rules; default p + 2 */
+  int precision;         /* cf_precision of cf_vcycle / cf_solve; default CF_FP64 */
+} cf_params;
+
+typedef struct {
+  int iterations;          /* CG iterations taken */
+  double rel_residual;     /* final recursive ||r|| / ||b|| */
+  double true_rel_residual;/* ||b - A x|| / ||b|| recomputed at exit */
+  double solve_ms;         /* wall time of the solve on the stream (device events) */
+} cf_info;
+
+typedef struct cf_problem cf_problem;
+
+/* Build the hierarchy: classification, cut-cell quadrature, cell and patch
+ * matrices (host, FP64), upload to the current device.  Blocking.
+ * Errors: CF_EINVAL (bad sizes, degree, kind), CF_EUNSUPPORTED (dim 3 with
+ * degree 3), CF_ENOMEM, CF_ECUDA. */
+cf_status cf_setup(const cf_mesh* mesh, const cf_levelset* ls, int degree,
+                   const cf_params* params, cf_problem** out);
+void cf_destroy(cf_problem* pb);
+const char* cf_last_error(void);
+
+int cf_n_levels(const cf_problem* pb);
+int64_t cf_n_dofs(const cf_problem* pb);
+int64_t cf_level_n_dofs(const cf_problem* pb, int level);
+/* Host array of cf_level_n_dofs int64 lattice flat indices. */
+cf_status cf_dof_lattice(const cf_problem* pb, int level, int64_t* h_idx);
+/* Host array of dim * n doubles, node coordinates (x_0, x_1, ..) per DoF. */
+cf_status cf_dof_coords(const cf_problem* pb, int level, double* h_xyz);
+/* Host counters of the finest level: [active cells, cut cells, ghost faces,
+ * patches, cut patches, cut-patch matrix entries]. */
+cf_status cf_stats(const cf_problem* pb, int level, int64_t* h_out6);
+
+/* Select the precision of cf_vcycle and cf_solve (CF_FP64 or CF_MIXED). */
+cf_status cf_set_precision(cf_problem* pb, int precision);
+
+/* b = right-hand side of the manufactured solution u = prod_k sin(pi x_k),
+ * f = d pi^2 u, Dirichlet data g = u (Nitsche data terms), finest level. */
+cf_status cf_rhs(cf_problem* pb, double* d_b, void* stream);
+
+/* y = A_L x on the finest level, FP64 (matrix-free). */
+cf_status cf_apply(cf_problem* pb, const double* d_x, double* d_y, void* stream);
+
+/* z = B r: one V-cycle with zero initial guess (precision as selected). */
+cf_status cf_vcycle(cf_problem* pb, const double* d_r, double* d_z, void* stream);
+
+/* CG preconditioned by one V-cycle per iteration, x_0 = 0, until
+ * ||r||_2 <= rtol ||b||_2 (recursive residual) or maxit.  Synchronises the
+ * stream once per iteration to read ||r||.  Returns CF_ENOCONV if maxit was
+ * reached (x holds the last iterate). */
+cf_status cf_solve(cf_problem* pb, const double* d_b, double* d_x, double rtol,
+                   int maxit, cf_info* info, void* stream);
+
+/* ---- single steps of the hot path on one level (parity testing) ---------
+ * All vectors are FP64 device arrays in the level's DoF order; `precision`
+ * selects the FP64 kernels or the FP32 kernels of the mixed form (inputs are
+ * rounded to FP32, outputs widened back). */
+
+/* y = A_l x (Sec. 2.1 operator, matrix-free). */
+cf_status cf_level_apply(cf_problem* pb, int level, int precision,
+                         const double* d_x, double* d_y, void* stream);
+/* One colour step of the smoother: for every patch of the given colour and
+ * kind (cut != 0: cut patches, else interior patches) x[I_j] += A_j^{-1}
+ * (b - A x)[I_j], all from one residual (Sec. 2.3 inconsistent treatment). */
+cf_status cf_level_colour_step(cf_problem* pb, int level, int precision, int cut,
+                               int colour, double* d_x, const double* d_b, void* stream);
+/* One full smoothing step (eq. "smoother-split"), post != 0: reversed order. */
+cf_status cf_level_smooth(cf_problem* pb, int level, int precision, int post,
+                          double* d_x, const double* d_b, void* stream);
+/* b_{l-1} = P_l^T r_l (level >= 1). */
+cf_status cf_level_restrict(cf_problem* pb, int level, int precision,
+                            const double* d_r_fine, double* d_b_coarse, void* stream);
+/* x_l += P_l x_{l-1} (level >= 1). */
+cf_status cf_level_prolongate(cf_problem* pb, int level, int precision,
+                              const double* d_x_coarse, double* d_x_fine, void* stream);
+/* x_0 = A_0^{-1} b_0 (exact coarsest solve). */
+cf_status cf_coarse_solve(cf_problem* pb, int precision, const double* d_b0,
+                          double* d_x0, void* stream);
+
+/* ---- host-only handles (no device work; used to check the setup) ---------
+ * cf_setup_host builds the same hierarchy as cf_setup on the host only.  The
+ * handle answers the size / map / stats queries above and the calls below;
+ * every device call on it returns CF_EINVAL. */
+cf_status cf_setup_host(const cf_mesh* mesh, const cf_levelset* ls, int degree,
+                        const cf_params* params, cf_problem** out);
+/* Finest-level right-hand side (host array of cf_n_dofs doubles). */
+cf_status cf_host_rhs(const cf_problem* pb, double* h_b);
+/* Element matrix of cell `cell` (flat index c_0 + N c_1 + N^2 c_2) of a level:
+ * volume + Nitsche terms for a cut cell, the uncut stiffness for an uncut
+ * active cell; (p+1)^d x (p+1)^d row-major, local nodes first coordinate
+ * fastest.  CF_EINVAL for an inactive cell. */
+cf_status cf_host_cell_matrix(const cf_problem* pb, int level, int64_t cell, double* h_out);
+/* Number of interior (fast-diagonalisation) and cut (dense inverse) patches. */
+cf_status cf_host_patch_counts(const cf_problem* pb, int level, int64_t* n_interior, int64_t* n_cut);
+/* Interior patch j: its vertex (lattice vertex index v_0 + (N+1) v_1 + ..). */
+cf_status cf_host_interior_patch(const cf_problem* pb, int level, int64_t j, int64_t* vertex);
+/* Cut patch j: vertex, DoF count m, lattice indices of its m DoFs (h_nodes,
+ * room for (2p+1)^d) and, if h_inv is not NULL, the m x m explicit inverse
+ * of A[I_j, I_j] (row-major, in the order of h_nodes). */
+cf_status cf_host_cut_patch(const cf_problem* pb, int level, int64_t j, int64_t* vertex, int* m,
+                            int64_t* h_nodes, double* h_inv);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CUTMG_H */

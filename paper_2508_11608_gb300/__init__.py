@@ -1,0 +1,181 @@
+"""GB300-native CutFEM multigrid (arXiv 2508.11608): Python handle over the
+C ABI of libcutmg.so.
+
+Device vectors are torch CUDA tensors of dtype float64 in the library's DoF
+order; torch is used for device memory and streams only.
+"""
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import CF_FP64, CF_MIXED, CutmgError, check  # noqa: F401
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Problem:
+    """A resident multigrid hierarchy (cf_setup .. cf_destroy)."""
+
+    def __init__(self, dim, n_cells, n_levels, degree, center=None, radius=None, plane=None,
+                 lo=-1.0, hi=1.0, gamma_D=0.0, gamma_ghost=(0.0,) * 4, n_c=0, quad_q=0,
+                 precision=CF_FP64, host_only=False):
+        lib = _lib.load()
+        self._lib = lib
+        mesh = _lib.cf_mesh(dim, n_cells, lo, hi, n_levels)
+        ls = _lib.cf_levelset()
+        if plane is not None:
+            ls.kind = _lib.CF_LS_PLANE
+            normal, offset = plane
+            for k, v in enumerate(normal):
+                ls.normal[k] = v
+            ls.offset = offset
+        else:
+            ls.kind = _lib.CF_LS_SPHERE
+            for k, v in enumerate(center):
+                ls.center[k] = v
+            ls.radius = radius
+        prm = _lib.cf_params()
+        prm.gamma_D = gamma_D
+        for k, v in enumerate(gamma_ghost):
+            prm.gamma_ghost[k] = v
+        prm.n_c = n_c
+        prm.quad_q = quad_q
+        prm.precision = precision
+        h = ctypes.c_void_p()
+        setup = lib.cf_setup_host if host_only else lib.cf_setup
+        check(setup(ctypes.byref(mesh), ctypes.byref(ls), degree, ctypes.byref(prm), ctypes.byref(h)))
+        self._h = h
+        self.dim = dim
+        self.degree = degree
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.cf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- sizes and maps ---------------------------------------------------------
+    @property
+    def n_levels(self):
+        return self._lib.cf_n_levels(self._h)
+
+    def n_dofs(self, level=None):
+        if level is None:
+            return self._lib.cf_n_dofs(self._h)
+        return self._lib.cf_level_n_dofs(self._h, level)
+
+    def dof_lattice(self, level=None):
+        level = self.n_levels - 1 if level is None else level
+        out = np.empty(self.n_dofs(level), dtype=np.int64)
+        check(self._lib.cf_dof_lattice(self._h, level, out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def dof_coords(self, level=None):
+        level = self.n_levels - 1 if level is None else level
+        out = np.empty((self.n_dofs(level), self.dim), dtype=np.float64)
+        check(self._lib.cf_dof_coords(self._h, level, out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def stats(self, level=None):
+        level = self.n_levels - 1 if level is None else level
+        out = np.empty(6, dtype=np.int64)
+        check(self._lib.cf_stats(self._h, level, out.ctypes.data_as(ctypes.c_void_p)))
+        keys = ["active_cells", "cut_cells", "ghost_faces", "patches", "cut_patches", "inverse_entries"]
+        return dict(zip(keys, out.tolist()))
+
+    def set_precision(self, precision):
+        check(self._lib.cf_set_precision(self._h, precision))
+
+    # ---- finest-level calls ----------------------------------------------------------
+    def rhs(self, b, stream=None):
+        check(self._lib.cf_rhs(self._h, _ptr(b), _stream(stream)))
+
+    def apply(self, x, y, stream=None):
+        check(self._lib.cf_apply(self._h, _ptr(x), _ptr(y), _stream(stream)))
+
+    def vcycle(self, r, z, stream=None):
+        check(self._lib.cf_vcycle(self._h, _ptr(r), _ptr(z), _stream(stream)))
+
+    def solve(self, b, x, rtol=1e-8, maxit=500, stream=None, allow_noconv=False):
+        info = _lib.cf_info()
+        st = self._lib.cf_solve(self._h, _ptr(b), _ptr(x), rtol, maxit, ctypes.byref(info),
+                                _stream(stream))
+        if not (allow_noconv and st == _lib.CF_ENOCONV):
+            check(st)
+        return {"iterations": info.iterations, "rel_residual": info.rel_residual,
+                "true_rel_residual": info.true_rel_residual, "solve_ms": info.solve_ms}
+
+    # ---- single steps on one level ---------------------------------------------------
+    def level_apply(self, level, x, y, precision=CF_FP64, stream=None):
+        check(self._lib.cf_level_apply(self._h, level, precision, _ptr(x), _ptr(y), _stream(stream)))
+
+    def colour_step(self, level, cut, colour, x, b, precision=CF_FP64, stream=None):
+        check(self._lib.cf_level_colour_step(self._h, level, precision, int(cut), colour, _ptr(x),
+                                             _ptr(b), _stream(stream)))
+
+    def smooth(self, level, x, b, post=False, precision=CF_FP64, stream=None):
+        check(self._lib.cf_level_smooth(self._h, level, precision, int(post), _ptr(x), _ptr(b),
+                                        _stream(stream)))
+
+    def restrict(self, level, r_fine, b_coarse, precision=CF_FP64, stream=None):
+        check(self._lib.cf_level_restrict(self._h, level, precision, _ptr(r_fine), _ptr(b_coarse),
+                                          _stream(stream)))
+
+    def prolongate(self, level, x_coarse, x_fine, precision=CF_FP64, stream=None):
+        check(self._lib.cf_level_prolongate(self._h, level, precision, _ptr(x_coarse), _ptr(x_fine),
+                                            _stream(stream)))
+
+    def coarse_solve(self, b0, x0, precision=CF_FP64, stream=None):
+        check(self._lib.cf_coarse_solve(self._h, precision, _ptr(b0), _ptr(x0), _stream(stream)))
+
+    # ---- host-side views of the setup (work on host-only handles too) -------------
+    def host_rhs(self):
+        out = np.empty(self.n_dofs(), dtype=np.float64)
+        check(self._lib.cf_host_rhs(self._h, out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def host_cell_matrix(self, level, cell):
+        nb = (self.degree + 1) ** self.dim
+        out = np.empty((nb, nb), dtype=np.float64)
+        check(self._lib.cf_host_cell_matrix(self._h, level, cell, out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def host_patches(self, level, with_inverse=True):
+        """(interior vertices, [(vertex, lattice nodes, inverse or None)] of cut patches)."""
+        ni = ctypes.c_int64()
+        nc = ctypes.c_int64()
+        check(self._lib.cf_host_patch_counts(self._h, level, ctypes.byref(ni), ctypes.byref(nc)))
+        inter = []
+        v = ctypes.c_int64()
+        for j in range(ni.value):
+            check(self._lib.cf_host_interior_patch(self._h, level, j, ctypes.byref(v)))
+            inter.append(v.value)
+        cmax = (2 * self.degree + 1) ** self.dim
+        nodes = np.empty(cmax, dtype=np.int64)
+        m = ctypes.c_int()
+        cut = []
+        for j in range(nc.value):
+            inv = np.empty(cmax * cmax, dtype=np.float64) if with_inverse else None
+            check(self._lib.cf_host_cut_patch(
+                self._h, level, j, ctypes.byref(v), ctypes.byref(m),
+                nodes.ctypes.data_as(ctypes.c_void_p),
+                inv.ctypes.data_as(ctypes.c_void_p) if with_inverse else None))
+            k = m.value
+            cut.append((v.value, nodes[:k].copy(),
+                        inv[:k * k].reshape(k, k).copy() if with_inverse else None))
+        return inter, cut

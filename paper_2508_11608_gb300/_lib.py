@@ -1,0 +1,102 @@
+"""ctypes binding of libcutmg.so (include/cutmg.h): argument marshalling only.
+
+Every numerical step runs in the library's CUDA kernels; there is no Python
+or CPU fallback.  Loading fails loudly when the library has not been built.
+"""
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcutmg.so")
+
+CF_OK, CF_EINVAL, CF_ENOMEM, CF_ECUDA, CF_ENOCONV, CF_ETIMEOUT, CF_EUNSUPPORTED = range(7)
+CF_LS_SPHERE, CF_LS_PLANE = 0, 1
+CF_FP64, CF_MIXED = 0, 1
+
+EXPORTED = [
+    "cf_setup", "cf_destroy", "cf_last_error", "cf_n_levels", "cf_n_dofs", "cf_level_n_dofs",
+    "cf_dof_lattice", "cf_dof_coords", "cf_stats", "cf_set_precision", "cf_rhs", "cf_apply",
+    "cf_vcycle", "cf_solve", "cf_level_apply", "cf_level_colour_step", "cf_level_smooth",
+    "cf_level_restrict", "cf_level_prolongate", "cf_coarse_solve", "cf_setup_host", "cf_host_rhs",
+    "cf_host_cell_matrix", "cf_host_patch_counts", "cf_host_interior_patch", "cf_host_cut_patch",
+]
+
+
+class cf_mesh(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n_cells", ctypes.c_int), ("lo", ctypes.c_double),
+                ("hi", ctypes.c_double), ("n_levels", ctypes.c_int)]
+
+
+class cf_levelset(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("center", ctypes.c_double * 3), ("radius", ctypes.c_double),
+                ("normal", ctypes.c_double * 3), ("offset", ctypes.c_double)]
+
+
+class cf_params(ctypes.Structure):
+    _fields_ = [("gamma_D", ctypes.c_double), ("gamma_ghost", ctypes.c_double * 4), ("n_c", ctypes.c_int),
+                ("quad_q", ctypes.c_int), ("precision", ctypes.c_int)]
+
+
+class cf_info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("rel_residual", ctypes.c_double),
+                ("true_rel_residual", ctypes.c_double), ("solve_ms", ctypes.c_double)]
+
+
+class CutmgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"cutmg status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load():
+    """Load the shared library (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_2508_11608_gb300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, D, V = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+    lib.cf_setup.argtypes = [ctypes.POINTER(cf_mesh), ctypes.POINTER(cf_levelset), I,
+                             ctypes.POINTER(cf_params), ctypes.POINTER(P)]
+    lib.cf_destroy.argtypes = [P]
+    lib.cf_destroy.restype = None
+    lib.cf_last_error.restype = ctypes.c_char_p
+    lib.cf_n_levels.argtypes = [P]
+    lib.cf_n_dofs.argtypes = [P]
+    lib.cf_n_dofs.restype = ctypes.c_int64
+    lib.cf_level_n_dofs.argtypes = [P, I]
+    lib.cf_level_n_dofs.restype = ctypes.c_int64
+    lib.cf_dof_lattice.argtypes = [P, I, P]
+    lib.cf_dof_coords.argtypes = [P, I, P]
+    lib.cf_stats.argtypes = [P, I, P]
+    lib.cf_set_precision.argtypes = [P, I]
+    lib.cf_rhs.argtypes = [P, P, V]
+    lib.cf_apply.argtypes = [P, P, P, V]
+    lib.cf_vcycle.argtypes = [P, P, P, V]
+    lib.cf_solve.argtypes = [P, P, P, D, I, ctypes.POINTER(cf_info), V]
+    lib.cf_level_apply.argtypes = [P, I, I, P, P, V]
+    lib.cf_level_colour_step.argtypes = [P, I, I, I, I, P, P, V]
+    lib.cf_level_smooth.argtypes = [P, I, I, I, P, P, V]
+    lib.cf_level_restrict.argtypes = [P, I, I, P, P, V]
+    lib.cf_level_prolongate.argtypes = [P, I, I, P, P, V]
+    lib.cf_coarse_solve.argtypes = [P, I, P, P, V]
+    lib.cf_setup_host.argtypes = lib.cf_setup.argtypes
+    lib.cf_host_rhs.argtypes = [P, P]
+    lib.cf_host_cell_matrix.argtypes = [P, I, ctypes.c_int64, P]
+    lib.cf_host_patch_counts.argtypes = [P, I, P, P]
+    lib.cf_host_interior_patch.argtypes = [P, I, ctypes.c_int64, P]
+    lib.cf_host_cut_patch.argtypes = [P, I, ctypes.c_int64, P, P, P, P]
+    for name in EXPORTED:
+        getattr(lib, name)  # raises AttributeError if the library lacks a symbol
+    _lib = lib
+    return lib
+
+
+def check(status):
+    if status != CF_OK:
+        raise CutmgError(status, load().cf_last_error().decode())

@@ -1,0 +1,317 @@
+// C ABI of the library (include/cutmg.h): argument checking, error
+// translation, dispatch to the (dim, degree)-specialised engines.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+
+#include "../../include/cutmg.h"
+#include "engine_api.hpp"
+#include "setup.hpp"
+
+using namespace cutmg;
+
+struct cf_problem {
+  Hierarchy H;
+  std::unique_ptr<EngineBase> eng;
+  int precision = CF_FP64;
+  int device = 0;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+cf_status fail(cf_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+template <typename F>
+cf_status guarded(F&& f) {
+  try {
+    f();
+    return CF_OK;
+  } catch (const std::invalid_argument& e) {
+    return fail(CF_EINVAL, e.what());
+  } catch (const OomError& e) {
+    return fail(CF_ENOMEM, e.what());
+  } catch (const std::bad_alloc&) {
+    return fail(CF_ENOMEM, "host allocation failed");
+  } catch (const CudaError& e) {
+    return fail(CF_ECUDA, e.what());
+  } catch (const std::exception& e) {
+    return fail(CF_EINVAL, e.what());
+  }
+}
+
+bool bad_level(const cf_problem* pb, int level) {
+  return !pb || level < 0 || level >= (int)pb->H.levels.size();
+}
+
+bool no_device(const cf_problem* pb) { return !pb || !pb->eng; }
+
+bool bad_prec(int p) { return p != CF_FP64 && p != CF_MIXED; }
+
+cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+}  // namespace
+
+extern "C" {
+
+const char* cf_last_error(void) { return g_err.c_str(); }
+
+static cf_status setup_impl(const cf_mesh* mesh, const cf_levelset* ls, int degree, const cf_params* params,
+                            cf_problem** out, bool device) {
+  if (!mesh || !ls || !out) return fail(CF_EINVAL, "null argument");
+  *out = nullptr;
+  if (mesh->dim != 2 && mesh->dim != 3) return fail(CF_EINVAL, "dim must be 2 or 3");
+  if (degree < 1 || degree > 3) return fail(CF_EINVAL, "degree must be 1, 2 or 3");
+  if (mesh->dim == 3 && degree > 2) return fail(CF_EUNSUPPORTED, "dim 3 supports degree 1 and 2");
+  if (mesh->n_cells < 1 || mesh->n_levels < 1) return fail(CF_EINVAL, "n_cells and n_levels must be positive");
+  if (ls->kind != CF_LS_SPHERE && ls->kind != CF_LS_PLANE) return fail(CF_EINVAL, "unknown level-set kind");
+  if (ls->kind == CF_LS_SPHERE && !(ls->radius > 0.0)) return fail(CF_EINVAL, "radius must be positive");
+  SetupParams prm;
+  prm.dim = mesh->dim;
+  prm.degree = degree;
+  prm.n_cells = mesh->n_cells;
+  prm.n_levels = mesh->n_levels;
+  prm.lo = mesh->lo;
+  prm.hi = mesh->hi;
+  prm.gamma_D = 20.0 * degree * degree;
+  prm.n_c = 2;
+  prm.quad_q = degree + 2;
+  int precision = CF_FP64;
+  if (params) {
+    if (params->gamma_D > 0) prm.gamma_D = params->gamma_D;
+    for (int k = 0; k < 4; ++k)
+      if (params->gamma_ghost[k] > 0) prm.gamma_ghost[k] = params->gamma_ghost[k];
+    if (params->n_c > 0) prm.n_c = params->n_c;
+    if (params->quad_q > 0) prm.quad_q = params->quad_q;
+    if (bad_prec(params->precision)) return fail(CF_EINVAL, "bad precision");
+    precision = params->precision;
+  }
+  prm.ls.kind = ls->kind;
+  prm.ls.d = mesh->dim;
+  for (int k = 0; k < 3; ++k) {
+    prm.ls.c[k] = ls->center[k];
+    prm.ls.nrm[k] = ls->normal[k];
+  }
+  prm.ls.r = ls->radius;
+  prm.ls.off = ls->offset;
+  std::unique_ptr<cf_problem> pb;
+  cf_status st = guarded([&] {
+    pb.reset(new cf_problem());
+    build_hierarchy(prm, pb->H);
+    if (device) {
+      if (cudaGetDevice(&pb->device) != cudaSuccess) throw CudaError("no CUDA device");
+      pb->eng = mesh->dim == 2 ? make_engine_d2(degree, pb->H) : make_engine_d3(degree, pb->H);
+    }
+    pb->precision = precision;
+  });
+  if (st != CF_OK) return st;
+  *out = pb.release();
+  return CF_OK;
+}
+
+cf_status cf_setup(const cf_mesh* mesh, const cf_levelset* ls, int degree, const cf_params* params,
+                   cf_problem** out) {
+  return setup_impl(mesh, ls, degree, params, out, true);
+}
+
+cf_status cf_setup_host(const cf_mesh* mesh, const cf_levelset* ls, int degree, const cf_params* params,
+                        cf_problem** out) {
+  return setup_impl(mesh, ls, degree, params, out, false);
+}
+
+void cf_destroy(cf_problem* pb) { delete pb; }
+
+int cf_n_levels(const cf_problem* pb) { return pb ? (int)pb->H.levels.size() : 0; }
+
+int64_t cf_n_dofs(const cf_problem* pb) { return pb ? (int64_t)pb->H.levels.back().dofs.size() : 0; }
+
+int64_t cf_level_n_dofs(const cf_problem* pb, int level) {
+  return bad_level(pb, level) ? 0 : (int64_t)pb->H.levels[level].dofs.size();
+}
+
+cf_status cf_dof_lattice(const cf_problem* pb, int level, int64_t* h_idx) {
+  if (bad_level(pb, level) || !h_idx) return fail(CF_EINVAL, "bad level or null output");
+  const auto& d = pb->H.levels[level].dofs;
+  std::memcpy(h_idx, d.data(), d.size() * sizeof(int64_t));
+  return CF_OK;
+}
+
+cf_status cf_dof_coords(const cf_problem* pb, int level, double* h_xyz) {
+  if (bad_level(pb, level) || !h_xyz) return fail(CF_EINVAL, "bad level or null output");
+  const HostLevel& L = pb->H.levels[level];
+  Poly1D b(L.p);
+  for (size_t i = 0; i < L.dofs.size(); ++i) {
+    int64_t t = L.dofs[i];
+    for (int k = 0; k < L.d; ++k) {
+      int ik = (int)(t % L.n);
+      t /= L.n;
+      int c = std::min(ik / L.p, L.N - 1);
+      h_xyz[i * L.d + k] = L.lo + L.h * (c + b.nodes[ik - L.p * c]);
+    }
+  }
+  return CF_OK;
+}
+
+cf_status cf_stats(const cf_problem* pb, int level, int64_t* h_out6) {
+  if (bad_level(pb, level) || !h_out6) return fail(CF_EINVAL, "bad level or null output");
+  const HostLevel& L = pb->H.levels[level];
+  h_out6[0] = L.n_active;
+  h_out6[1] = L.n_cut;
+  h_out6[2] = L.n_ghost;
+  h_out6[3] = (int64_t)(L.cart_vert.size() + L.cut_vert.size());
+  h_out6[4] = (int64_t)L.cut_vert.size();
+  h_out6[5] = (int64_t)L.inv.size();
+  return CF_OK;
+}
+
+cf_status cf_set_precision(cf_problem* pb, int precision) {
+  if (!pb || bad_prec(precision)) return fail(CF_EINVAL, "bad precision");
+  pb->precision = precision;
+  return CF_OK;
+}
+
+cf_status cf_rhs(cf_problem* pb, double* d_b, void* stream) {
+  if (no_device(pb) || !d_b) return fail(CF_EINVAL, "null argument");
+  return guarded([&] { pb->eng->rhs(d_b, S(stream)); });
+}
+
+cf_status cf_apply(cf_problem* pb, const double* d_x, double* d_y, void* stream) {
+  if (no_device(pb) || !d_x || !d_y) return fail(CF_EINVAL, "null argument");
+  return guarded([&] { pb->eng->apply_fine(d_x, d_y, S(stream)); });
+}
+
+cf_status cf_vcycle(cf_problem* pb, const double* d_r, double* d_z, void* stream) {
+  if (no_device(pb) || !d_r || !d_z) return fail(CF_EINVAL, "null argument");
+  return guarded([&] { pb->eng->vcycle(pb->precision, d_r, d_z, S(stream)); });
+}
+
+cf_status cf_solve(cf_problem* pb, const double* d_b, double* d_x, double rtol, int maxit,
+                   cf_info* info, void* stream) {
+  if (no_device(pb) || !d_b || !d_x) return fail(CF_EINVAL, "null argument");
+  if (!(rtol > 0.0) || maxit < 1) return fail(CF_EINVAL, "rtol must be positive and maxit >= 1");
+  int it = 0;
+  double rel = 0, trel = 0;
+  float ms = 0;
+  cf_status st = guarded([&] {
+    it = pb->eng->solve(pb->precision, d_b, d_x, rtol, maxit, &rel, &trel, &ms, S(stream));
+  });
+  if (st != CF_OK) return st;
+  if (info) {
+    info->iterations = it;
+    info->rel_residual = rel;
+    info->true_rel_residual = trel;
+    info->solve_ms = ms;
+  }
+  if (rel > rtol) return fail(CF_ENOCONV, "CG reached maxit before the tolerance");
+  return CF_OK;
+}
+
+cf_status cf_level_apply(cf_problem* pb, int level, int precision, const double* d_x, double* d_y,
+                         void* stream) {
+  if (bad_level(pb, level) || no_device(pb) || bad_prec(precision) || !d_x || !d_y) return fail(CF_EINVAL, "bad argument");
+  return guarded([&] { pb->eng->level_apply(level, precision, d_x, d_y, S(stream)); });
+}
+
+cf_status cf_level_colour_step(cf_problem* pb, int level, int precision, int cut, int colour,
+                               double* d_x, const double* d_b, void* stream) {
+  if (bad_level(pb, level) || no_device(pb) || bad_prec(precision) || !d_x || !d_b) return fail(CF_EINVAL, "bad argument");
+  if (colour < 0 || colour >= (1 << pb->H.prm.dim)) return fail(CF_EINVAL, "bad colour");
+  return guarded([&] { pb->eng->level_colour(level, precision, cut, colour, d_x, d_b, S(stream)); });
+}
+
+cf_status cf_level_smooth(cf_problem* pb, int level, int precision, int post, double* d_x,
+                          const double* d_b, void* stream) {
+  if (bad_level(pb, level) || no_device(pb) || bad_prec(precision) || !d_x || !d_b) return fail(CF_EINVAL, "bad argument");
+  return guarded([&] { pb->eng->level_smooth(level, precision, post, d_x, d_b, S(stream)); });
+}
+
+cf_status cf_level_restrict(cf_problem* pb, int level, int precision, const double* d_r_fine,
+                            double* d_b_coarse, void* stream) {
+  if (bad_level(pb, level) || no_device(pb) || level < 1 || bad_prec(precision) || !d_r_fine || !d_b_coarse)
+    return fail(CF_EINVAL, "bad argument");
+  return guarded([&] { pb->eng->level_restrict(level, precision, d_r_fine, d_b_coarse, S(stream)); });
+}
+
+cf_status cf_level_prolongate(cf_problem* pb, int level, int precision, const double* d_x_coarse,
+                              double* d_x_fine, void* stream) {
+  if (bad_level(pb, level) || no_device(pb) || level < 1 || bad_prec(precision) || !d_x_coarse || !d_x_fine)
+    return fail(CF_EINVAL, "bad argument");
+  return guarded([&] { pb->eng->level_prolongate(level, precision, d_x_coarse, d_x_fine, S(stream)); });
+}
+
+cf_status cf_coarse_solve(cf_problem* pb, int precision, const double* d_b0, double* d_x0, void* stream) {
+  if (no_device(pb) || bad_prec(precision) || !d_b0 || !d_x0) return fail(CF_EINVAL, "bad argument");
+  return guarded([&] { pb->eng->coarse_solve(precision, d_b0, d_x0, S(stream)); });
+}
+
+
+cf_status cf_host_rhs(const cf_problem* pb, double* h_b) {
+  if (!pb || !h_b) return fail(CF_EINVAL, "null argument");
+  std::memcpy(h_b, pb->H.rhs.data(), pb->H.rhs.size() * sizeof(double));
+  return CF_OK;
+}
+
+cf_status cf_host_cell_matrix(const cf_problem* pb, int level, int64_t cell, double* h_out) {
+  if (bad_level(pb, level) || !h_out) return fail(CF_EINVAL, "bad level or null output");
+  const HostLevel& L = pb->H.levels[level];
+  if (cell < 0 || cell >= (int64_t)L.cflag.size() || !(L.cflag[cell] & kFlagActive))
+    return fail(CF_EINVAL, "cell out of range or inactive");
+  const size_t nb2 = L.Kref.size();
+  const double* src = (L.cflag[cell] & kFlagCut) ? &L.cutmat[(size_t)L.cut_id[cell] * nb2] : L.Kref.data();
+  std::memcpy(h_out, src, nb2 * sizeof(double));
+  return CF_OK;
+}
+
+cf_status cf_host_patch_counts(const cf_problem* pb, int level, int64_t* n_interior, int64_t* n_cut) {
+  if (bad_level(pb, level) || !n_interior || !n_cut) return fail(CF_EINVAL, "bad argument");
+  *n_interior = (int64_t)pb->H.levels[level].cart_vert.size();
+  *n_cut = (int64_t)pb->H.levels[level].cut_vert.size();
+  return CF_OK;
+}
+
+cf_status cf_host_interior_patch(const cf_problem* pb, int level, int64_t j, int64_t* vertex) {
+  if (bad_level(pb, level) || !vertex) return fail(CF_EINVAL, "bad argument");
+  const HostLevel& L = pb->H.levels[level];
+  if (j < 0 || j >= (int64_t)L.cart_vert.size()) return fail(CF_EINVAL, "patch index out of range");
+  *vertex = L.cart_vert[j];
+  return CF_OK;
+}
+
+cf_status cf_host_cut_patch(const cf_problem* pb, int level, int64_t j, int64_t* vertex, int* m,
+                            int64_t* h_nodes, double* h_inv) {
+  if (bad_level(pb, level) || !vertex || !m || !h_nodes) return fail(CF_EINVAL, "bad argument");
+  const HostLevel& L = pb->H.levels[level];
+  if (j < 0 || j >= (int64_t)L.cut_vert.size()) return fail(CF_EINVAL, "patch index out of range");
+  const int np = L.N + 1, C = 2 * L.p + 1;
+  *vertex = L.cut_vert[j];
+  *m = L.cut_n[j];
+  int v[3] = {0, 0, 0};
+  int64_t t = L.cut_vert[j];
+  for (int k = 0; k < L.d; ++k) {
+    v[k] = (int)(t % np);
+    t /= np;
+  }
+  for (int e = 0; e < L.cut_n[j]; ++e) {
+    int o = L.members[L.cut_moff[j] + e];
+    int64_t node = 0, st = 1;
+    for (int k = 0; k < L.d; ++k) {
+      node += (int64_t)(L.p * (v[k] - 1) + o % C) * st;
+      o /= C;
+      st *= L.n;
+    }
+    h_nodes[e] = node;
+  }
+  if (h_inv)
+    std::memcpy(h_inv, &L.inv[L.cut_ioff[j]], sizeof(double) * L.cut_n[j] * L.cut_n[j]);
+  return CF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,594 @@
+// Device-resident hierarchy and the orchestration of the hot path: V-cycle
+// (Sec. 2.2) with the partitioned multiplicative vertex-patch smoother
+// (eq. "smoother-split") inside FP64 CG.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "engine_api.hpp"
+#include "kernels.cuh"
+#include "setup.hpp"
+
+namespace cutmg {
+
+#define CUTMG_CUDA(expr)                                                                   \
+  do {                                                                                     \
+    cudaError_t e__ = (expr);                                                              \
+    if (e__ != cudaSuccess)                                                                \
+      throw CudaError(std::string(#expr) + ": " + cudaGetErrorString(e__));               \
+  } while (0)
+
+inline void launch_check(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) throw CudaError(std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// owns every device allocation of a problem
+class DevPool {
+ public:
+  ~DevPool() {
+    for (void* p : ptrs_) cudaFree(p);
+  }
+  template <typename T>
+  T* alloc(size_t count, bool zero = true) {
+    if (count == 0) count = 1;
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+    if (e != cudaSuccess) throw OomError("cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed");
+    ptrs_.push_back(p);
+    bytes_ += count * sizeof(T);
+    if (zero) CUTMG_CUDA(cudaMemset(p, 0, count * sizeof(T)));
+    return static_cast<T*>(p);
+  }
+  template <typename T, typename S>
+  T* upload(const std::vector<S>& v) {
+    std::vector<T> tmp(v.begin(), v.end());
+    T* p = alloc<T>(tmp.size(), false);
+    if (!tmp.empty()) CUTMG_CUDA(cudaMemcpy(p, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return p;
+  }
+  size_t bytes() const { return bytes_; }
+
+ private:
+  std::vector<void*> ptrs_;
+  size_t bytes_ = 0;
+};
+
+inline int blocks_for(int64_t n, int bs) { return (int)((n + bs - 1) / bs); }
+
+template <int DIM, int P>
+class Engine final : public EngineBase {
+  static constexpr int NB = Shape<DIM, P>::NB;
+  static constexpr int C = 2 * P + 1, M = 2 * P - 1;
+  static constexpr int WARPS = 4;
+
+  struct Common {  // precision-independent level data
+    int N, n;
+    int64_t nbox, ndof;
+    uint8_t* cflag;
+    int* cut_id;
+    uint8_t* nact;
+    int64_t* dofs;
+    int* bulk;
+    int nbulk;
+    int* bnd;
+    int nbnd;
+    int* cart;
+    std::vector<int> cart_start;
+    int* cutv;
+    int* cutn;
+    int* cutmo;
+    int64_t* cutio;
+    uint16_t* members;
+    std::vector<int> cut_start;
+    int64_t nmembers;
+    int* pro_col;
+    int* res_col;
+    int* coarse_nodes;
+    Region region;  // bbox of the active nodes
+    int bb_lo[3], bb_hi[3];
+  };
+  template <typename T>
+  struct Typed {  // per-precision level data and work vectors
+    OpArgs<T> op;
+    FdArgs<T, P> fd;
+    T* inv;
+    T* pro_w;
+    T* res_w;
+    T* coarse_inv;
+    T *x, *b, *r;          // box vectors
+    T *t1, *t2, *t3, *t4;  // transfer intermediates (restriction: t1,t2; prolongation: t3,t4)
+    T* rbuf;               // cut-patch residual rows
+  };
+
+ public:
+  explicit Engine(const Hierarchy& H) : H_(H) {
+    const int L = (int)H.levels.size();
+    com_.resize(L);
+    d64_.resize(L);
+    d32_.resize(L);
+    for (int l = 0; l < L; ++l) upload_level(l);
+    const auto& F = com_.back();
+    xF_ = pool_.alloc<double>(F.nbox);
+    rF_ = pool_.alloc<double>(F.nbox);
+    pF_ = pool_.alloc<double>(F.nbox);
+    qF_ = pool_.alloc<double>(F.nbox);
+    zF_ = pool_.alloc<double>(F.nbox);
+    bF_ = pool_.alloc<double>(F.nbox);
+    tF_ = pool_.alloc<double>(F.nbox);
+    aux_ = pool_.alloc<double>(F.nbox);
+    aux2_ = pool_.alloc<double>(F.nbox);
+    part_ = pool_.alloc<double>(kDotBlocks);
+    sc_ = pool_.alloc<double>(16);
+    CUTMG_CUDA(cudaMallocHost(&host_sc_, 16 * sizeof(double)));
+  }
+  ~Engine() override {
+    if (host_sc_) cudaFreeHost(host_sc_);
+  }
+
+  int n_levels() const override { return (int)com_.size(); }
+  int64_t n_dofs(int l) const override { return com_[l].ndof; }
+  size_t device_bytes() const override { return pool_.bytes(); }
+
+  // ---- single steps on compact FP64 vectors --------------------------------
+  void level_apply(int l, int prec, const double* x, double* y, cudaStream_t s) override {
+    if (prec == 1) {
+      auto& D = d32_[l];
+      to_box(l, x, D.x, s);
+      apply<float>(l, D, D.x, nullptr, D.r, s);
+      from_box(l, D.r, y, s);
+    } else {
+      auto& D = d64_[l];
+      to_box(l, x, D.x, s);
+      apply<double>(l, D, D.x, nullptr, D.r, s);
+      from_box(l, D.r, y, s);
+    }
+  }
+  void level_colour(int l, int prec, int cut, int colour, double* x, const double* b,
+                    cudaStream_t s) override {
+    check_smooth_level(l);
+    if (prec == 1) {
+      auto& D = d32_[l];
+      to_box(l, x, D.x, s);
+      to_box(l, b, D.b, s);
+      colour_step<float>(l, D, cut, colour, D.x, D.b, s);
+      from_box(l, D.x, x, s);
+    } else {
+      auto& D = d64_[l];
+      to_box(l, x, D.x, s);
+      to_box(l, b, D.b, s);
+      colour_step<double>(l, D, cut, colour, D.x, D.b, s);
+      from_box(l, D.x, x, s);
+    }
+  }
+  void level_smooth(int l, int prec, int post, double* x, const double* b, cudaStream_t s) override {
+    check_smooth_level(l);
+    if (prec == 1) {
+      auto& D = d32_[l];
+      to_box(l, x, D.x, s);
+      to_box(l, b, D.b, s);
+      smooth<float>(l, D, post != 0, D.x, D.b, s);
+      from_box(l, D.x, x, s);
+    } else {
+      auto& D = d64_[l];
+      to_box(l, x, D.x, s);
+      to_box(l, b, D.b, s);
+      smooth<double>(l, D, post != 0, D.x, D.b, s);
+      from_box(l, D.x, x, s);
+    }
+  }
+  void level_restrict(int l, int prec, const double* rf, double* bc, cudaStream_t s) override {
+    check_smooth_level(l);
+    if (prec == 1) {
+      to_box(l, rf, d32_[l].r, s);
+      restrict_<float>(l, d32_, d32_[l].r, d32_[l - 1].b, s);
+      from_box(l - 1, d32_[l - 1].b, bc, s);
+    } else {
+      to_box(l, rf, d64_[l].r, s);
+      restrict_<double>(l, d64_, d64_[l].r, d64_[l - 1].b, s);
+      from_box(l - 1, d64_[l - 1].b, bc, s);
+    }
+  }
+  void level_prolongate(int l, int prec, const double* xc, double* xf, cudaStream_t s) override {
+    check_smooth_level(l);
+    if (prec == 1) {
+      to_box(l - 1, xc, d32_[l - 1].x, s);
+      to_box(l, xf, d32_[l].x, s);
+      prolong<float>(l, d32_, d32_[l - 1].x, d32_[l].x, s);
+      from_box(l, d32_[l].x, xf, s);
+    } else {
+      to_box(l - 1, xc, d64_[l - 1].x, s);
+      to_box(l, xf, d64_[l].x, s);
+      prolong<double>(l, d64_, d64_[l - 1].x, d64_[l].x, s);
+      from_box(l, d64_[l].x, xf, s);
+    }
+  }
+  void coarse_solve(int prec, const double* b0, double* x0, cudaStream_t s) override {
+    if (prec == 1) {
+      to_box(0, b0, d32_[0].b, s);
+      coarse<float>(d32_[0], d32_[0].b, d32_[0].x, s);
+      from_box(0, d32_[0].x, x0, s);
+    } else {
+      to_box(0, b0, d64_[0].b, s);
+      coarse<double>(d64_[0], d64_[0].b, d64_[0].x, s);
+      from_box(0, d64_[0].x, x0, s);
+    }
+  }
+
+  // ---- finest-level operations ------------------------------------------------
+  void apply_fine(const double* x, double* y, cudaStream_t s) override {
+    level_apply(n_levels() - 1, 0, x, y, s);
+  }
+  void rhs(double* b, cudaStream_t s) override {
+    CUTMG_CUDA(cudaMemcpyAsync(b, rhs_d_, sizeof(double) * com_.back().ndof,
+                               cudaMemcpyDeviceToDevice, s));
+  }
+  void vcycle(int prec, const double* r, double* z, cudaStream_t s) override {
+    const int L = n_levels() - 1;
+    to_box(L, r, aux_, s);
+    precondition(prec, aux_, aux2_, s);
+    from_box(L, aux2_, z, s);
+  }
+
+  int solve(int prec, const double* b, double* x, double rtol, int maxit, double* rel,
+            double* true_rel, float* ms, cudaStream_t s) override {
+    const int L = n_levels() - 1;
+    const auto& F = com_[L];
+    cudaEvent_t e0, e1;
+    CUTMG_CUDA(cudaEventCreate(&e0));
+    CUTMG_CUDA(cudaEventCreate(&e1));
+    CUTMG_CUDA(cudaEventRecord(e0, s));
+    to_box(L, b, bF_, s);
+    const size_t bytes = sizeof(double) * F.nbox;
+    CUTMG_CUDA(cudaMemsetAsync(xF_, 0, bytes, s));
+    CUTMG_CUDA(cudaMemcpyAsync(rF_, bF_, bytes, cudaMemcpyDeviceToDevice, s));
+    dot(F.region, bF_, bF_, sc_ + 4, s);
+    double bn2 = read_scalar(4, s);
+    const double bn = std::sqrt(bn2);
+    int it = 0;
+    double rn = bn;
+    if (bn > 0.0) {
+      precondition(prec, rF_, zF_, s);
+      dot(F.region, rF_, zF_, sc_ + 0, s);  // rz
+      CUTMG_CUDA(cudaMemcpyAsync(pF_, zF_, bytes, cudaMemcpyDeviceToDevice, s));
+      while (it < maxit) {
+        apply<double>(L, d64_[L], pF_, nullptr, qF_, s);
+        dot(F.region, pF_, qF_, sc_ + 1, s);  // pq
+        k_cg_update_xr<<<kVecBlocks, 256, 0, s>>>(F.region, sc_, xF_, rF_, pF_, qF_);
+        launch_check("cg update x r");
+        dot(F.region, rF_, rF_, sc_ + 3, s);  // rr
+        ++it;
+        rn = std::sqrt(read_scalar(3, s));
+        if (!(rn > rtol * bn)) break;
+        precondition(prec, rF_, zF_, s);
+        dot(F.region, rF_, zF_, sc_ + 2, s);  // rz_new
+        k_cg_update_p<<<kVecBlocks, 256, 0, s>>>(F.region, sc_, pF_, zF_);
+        launch_check("cg update p");
+        k_copy_scalar<<<1, 1, 0, s>>>(sc_, 0, 2);
+        launch_check("cg scalar");
+      }
+    }
+    CUTMG_CUDA(cudaEventRecord(e1, s));
+    CUTMG_CUDA(cudaEventSynchronize(e1));
+    CUTMG_CUDA(cudaEventElapsedTime(ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // true residual
+    apply<double>(L, d64_[L], xF_, bF_, tF_, s);
+    dot(F.region, tF_, tF_, sc_ + 5, s);
+    double tr = std::sqrt(read_scalar(5, s));
+    from_box(L, xF_, x, s);
+    *rel = bn > 0 ? rn / bn : 0.0;
+    *true_rel = bn > 0 ? tr / bn : 0.0;
+    return it;
+  }
+
+ private:
+  static constexpr int kDotBlocks = 512;
+  static constexpr int kVecBlocks = 1024;
+
+  const Hierarchy& H_;
+  DevPool pool_;
+  std::vector<Common> com_;
+  std::vector<Typed<double>> d64_;
+  std::vector<Typed<float>> d32_;
+  double *xF_, *rF_, *pF_, *qF_, *zF_, *bF_, *tF_, *aux_, *aux2_, *part_, *sc_;
+  double* host_sc_ = nullptr;
+  double* rhs_d_ = nullptr;
+  float *bL32_ = nullptr, *xL32_ = nullptr;
+
+  void check_smooth_level(int l) const {
+    if (l < 1 || l >= n_levels()) throw std::invalid_argument("level must be in [1, n_levels)");
+  }
+
+  template <typename T>
+  void fill_typed(const HostLevel& h, Typed<T>& D, const Common& c, int l) {
+    D.op.N = h.N;
+    D.op.n = h.n;
+    D.op.cflag = c.cflag;
+    D.op.cut_id = c.cut_id;
+    D.op.cutmat = pool_.upload<T>(h.cutmat);
+    D.op.Kref = pool_.upload<T>(h.Kref);
+    for (int m = 0; m < 3; ++m) {
+      for (int i = 0; i < 7; ++i) D.op.dvec[m][i] = (T)h.dvec[m][i];
+      D.op.coef[m] = (T)h.coef[m];
+    }
+    for (int a = 0; a < 4; ++a)
+      for (int b2 = 0; b2 < 4; ++b2) D.op.Mhat[a][b2] = (T)h.Mhat[a][b2];
+    for (int i = 0; i < M; ++i) {
+      for (int j = 0; j < C; ++j) {
+        D.fd.Mr[i][j] = (T)h.Mr[i * C + j];
+        D.fd.Kr[i][j] = (T)h.Kr[i * C + j];
+      }
+      for (int j = 0; j < M; ++j) D.fd.S[i][j] = (T)h.S[i * M + j];
+      D.fd.lam[i] = (T)h.lam[i];
+    }
+    D.inv = pool_.upload<T>(h.inv);
+    D.pro_w = l > 0 ? pool_.upload<T>(h.pro_w) : nullptr;
+    D.res_w = l > 0 ? pool_.upload<T>(h.res_w) : nullptr;
+    D.coarse_inv = l == 0 ? pool_.upload<T>(h.coarse_inv) : nullptr;
+    D.x = pool_.alloc<T>(c.nbox);
+    D.b = pool_.alloc<T>(c.nbox);
+    D.r = pool_.alloc<T>(c.nbox);
+    D.rbuf = pool_.alloc<T>(c.nmembers);
+    D.t1 = D.t2 = D.t3 = D.t4 = nullptr;
+    if (l > 0) {
+      const int64_t nf = h.n, nc = H_.levels[l - 1].n;
+      if (DIM == 3) {
+        D.t1 = pool_.alloc<T>(nc * nf * nf);
+        D.t2 = pool_.alloc<T>(nc * nc * nf);
+        D.t3 = pool_.alloc<T>(nf * nc * nc);
+        D.t4 = pool_.alloc<T>(nf * nf * nc);
+      } else {
+        D.t1 = pool_.alloc<T>(nc * nf);
+        D.t3 = pool_.alloc<T>(nf * nc);
+      }
+    }
+  }
+
+  void upload_level(int l) {
+    const HostLevel& h = H_.levels[l];
+    Common& c = com_[l];
+    c.N = h.N;
+    c.n = h.n;
+    c.nbox = (int64_t)h.nact.size();
+    c.ndof = (int64_t)h.dofs.size();
+    c.cflag = pool_.upload<uint8_t>(h.cflag);
+    c.cut_id = pool_.upload<int>(h.cut_id);
+    c.nact = pool_.upload<uint8_t>(h.nact);
+    c.dofs = pool_.upload<int64_t>(h.dofs);
+    c.bulk = pool_.upload<int>(h.bulk_pos);
+    c.nbulk = (int)h.bulk_pos.size();
+    c.bnd = pool_.upload<int>(h.bnd_node);
+    c.nbnd = (int)h.bnd_node.size();
+    c.cart = pool_.upload<int>(h.cart_vert);
+    c.cart_start = h.cart_start;
+    c.cutv = pool_.upload<int>(h.cut_vert);
+    c.cutn = pool_.upload<int>(h.cut_n);
+    c.cutmo = pool_.upload<int>(h.cut_moff);
+    c.cutio = pool_.upload<int64_t>(h.cut_ioff);
+    c.members = pool_.upload<uint16_t>(h.members);
+    c.cut_start = h.cut_start;
+    c.nmembers = (int64_t)h.members.size();
+    c.pro_col = l > 0 ? pool_.upload<int>(h.pro_col) : nullptr;
+    c.res_col = l > 0 ? pool_.upload<int>(h.res_col) : nullptr;
+    if (l == 0) {
+      std::vector<int> nodes(h.dofs.begin(), h.dofs.end());
+      c.coarse_nodes = pool_.upload<int>(nodes);
+    } else {
+      c.coarse_nodes = nullptr;
+    }
+    for (int k = 0; k < 3; ++k) {
+      c.bb_lo[k] = h.bb_lo[k];
+      c.bb_hi[k] = h.bb_hi[k];
+    }
+    c.region.n0 = h.n;
+    c.region.n1 = DIM >= 2 ? h.n : 1;
+    c.region.lo0 = h.bb_lo[0];
+    c.region.lo1 = h.bb_lo[1];
+    c.region.lo2 = DIM == 3 ? h.bb_lo[2] : 0;
+    c.region.e0 = h.bb_hi[0] - h.bb_lo[0] + 1;
+    c.region.e1 = h.bb_hi[1] - h.bb_lo[1] + 1;
+    c.region.e2 = DIM == 3 ? h.bb_hi[2] - h.bb_lo[2] + 1 : 1;
+    fill_typed<double>(h, d64_[l], c, l);
+    fill_typed<float>(h, d32_[l], c, l);
+    if (l == (int)H_.levels.size() - 1) rhs_d_ = pool_.upload<double>(H_.rhs);
+  }
+
+  // compact (FP64) <-> box (T): the box is zeroed first so that inactive
+  // nodes are zero whatever the buffer held before
+  template <typename T>
+  void to_box(int l, const double* in, T* box, cudaStream_t s) {
+    const Common& c = com_[l];
+    CUTMG_CUDA(cudaMemsetAsync(box, 0, sizeof(T) * c.nbox, s));
+    k_scatter<T, double><<<std::min(blocks_for(c.ndof, 256), 4096), 256, 0, s>>>(c.dofs, c.ndof, in, box);
+    launch_check("scatter");
+  }
+  template <typename T>
+  void from_box(int l, const T* box, double* out, cudaStream_t s) {
+    const Common& c = com_[l];
+    k_gather<double, T><<<std::min(blocks_for(c.ndof, 256), 4096), 256, 0, s>>>(c.dofs, c.ndof, box, out);
+    launch_check("gather");
+  }
+
+  double read_scalar(int i, cudaStream_t s) {
+    CUTMG_CUDA(cudaMemcpyAsync(host_sc_ + i, sc_ + i, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUTMG_CUDA(cudaStreamSynchronize(s));
+    return host_sc_[i];
+  }
+
+  void dot(const Region& R, const double* a, const double* b, double* out, cudaStream_t s) {
+    k_dot_partial<<<kDotBlocks, 256, 0, s>>>(R, a, b, part_);
+    launch_check("dot partial");
+    k_dot_final<<<1, 256, 0, s>>>(part_, kDotBlocks, out);
+    launch_check("dot final");
+  }
+
+  // y = A x or y = b - A x on level l (box layout, precision T)
+  template <typename T>
+  void apply(int l, Typed<T>& D, const T* x, const T* b, T* y, cudaStream_t s) {
+    const Common& c = com_[l];
+    if (c.nbulk > 0) {
+      k_apply_bulk<DIM, P, T><<<blocks_for(c.nbulk, 128), 128, 0, s>>>(D.op, x, b, y, c.bulk, c.nbulk);
+      launch_check("apply bulk");
+    }
+    if (c.nbnd > 0) {
+      k_apply_bnd<DIM, P, T><<<blocks_for(c.nbnd, 128), 128, 0, s>>>(D.op, x, b, y, c.bnd, c.nbnd);
+      launch_check("apply boundary");
+    }
+  }
+
+  template <typename T>
+  void colour_step(int l, Typed<T>& D, int cut, int colour, T* x, const T* b, cudaStream_t s) {
+    const Common& c = com_[l];
+    if (!cut) {
+      const int a0 = c.cart_start[colour], cnt = c.cart_start[colour + 1] - a0;
+      if (cnt <= 0) return;
+      k_smooth_cart<DIM, P, T, WARPS><<<blocks_for(cnt, WARPS), 32 * WARPS, 0, s>>>(
+          D.fd, c.N, c.n, x, b, c.cart + a0, cnt);
+      launch_check("smooth interior patches");
+    } else {
+      const int a0 = c.cut_start[colour], cnt = c.cut_start[colour + 1] - a0;
+      if (cnt <= 0) return;
+      k_cut_resid<DIM, P, T, WARPS><<<blocks_for(cnt, WARPS), 32 * WARPS, 0, s>>>(
+          D.op, x, b, c.cutv + a0, c.cutn + a0, c.cutmo + a0, c.members, D.rbuf, cnt);
+      launch_check("cut patch residual");
+      k_cut_update<DIM, P, T, WARPS><<<blocks_for(cnt, WARPS), 32 * WARPS, 0, s>>>(
+          c.N, c.n, x, c.cutv + a0, c.cutn + a0, c.cutmo + a0, c.cutio + a0, c.members, D.inv,
+          D.rbuf, cnt);
+      launch_check("cut patch update");
+    }
+  }
+
+  // eq. "smoother-split": interior colours, then n_c sweeps of the cut
+  // colours; the post-smoother runs the same steps in reverse order
+  template <typename T>
+  void smooth(int l, Typed<T>& D, bool post, T* x, const T* b, cudaStream_t s) {
+    const int ncol = 1 << DIM, nc = H_.prm.n_c;
+    std::vector<std::pair<int, int>> seq;
+    for (int c = 0; c < ncol; ++c) seq.push_back({0, c});
+    for (int r = 0; r < nc; ++r)
+      for (int c = 0; c < ncol; ++c) seq.push_back({1, c});
+    if (post)
+      for (int i = (int)seq.size() - 1; i >= 0; --i) colour_step<T>(l, D, seq[i].first, seq[i].second, x, b, s);
+    else
+      for (auto& st : seq) colour_step<T>(l, D, st.first, st.second, x, b, s);
+  }
+
+  template <typename T, int MODE>
+  void pass(const T* in, T* out, int in0, int in1, int out0, int out1, int axis, const int* lo,
+            const int* ext, const int* col, const T* wt, int W, const uint8_t* mask, cudaStream_t s) {
+    const int64_t tot = (int64_t)ext[0] * ext[1] * ext[2];
+    if (tot <= 0) return;
+    k_pass<T, MODE><<<blocks_for(tot, 256), 256, 0, s>>>(in, out, in0, in1, out0, out1, axis, lo[0], lo[1],
+                                                          lo[2], ext[0], ext[1], ext[2], col, wt, W, mask);
+    launch_check("transfer pass");
+  }
+
+  // b_{l-1} = P^T r_l, separably (x, y, z passes) over the active boxes
+  template <typename T>
+  void restrict_(int l, std::vector<Typed<T>>& DD, const T* rf, T* bc, cudaStream_t s) {
+    const Common& F = com_[l];
+    const Common& Cc = com_[l - 1];
+    Typed<T>& D = DD[l];
+    const int nf = F.n, nc = Cc.n, W = 4 * P + 1;
+    if (DIM == 3) {
+      int lo1[3] = {Cc.bb_lo[0], F.bb_lo[1], F.bb_lo[2]};
+      int ex1[3] = {Cc.bb_hi[0] - Cc.bb_lo[0] + 1, F.bb_hi[1] - F.bb_lo[1] + 1, F.bb_hi[2] - F.bb_lo[2] + 1};
+      pass<T, 0>(rf, D.t1, nf, nf, nc, nf, 0, lo1, ex1, F.res_col, D.res_w, W, nullptr, s);
+      int lo2[3] = {Cc.bb_lo[0], Cc.bb_lo[1], F.bb_lo[2]};
+      int ex2[3] = {ex1[0], Cc.bb_hi[1] - Cc.bb_lo[1] + 1, ex1[2]};
+      pass<T, 0>(D.t1, D.t2, nc, nf, nc, nc, 1, lo2, ex2, F.res_col, D.res_w, W, nullptr, s);
+      int lo3[3] = {Cc.bb_lo[0], Cc.bb_lo[1], Cc.bb_lo[2]};
+      int ex3[3] = {ex1[0], ex2[1], Cc.bb_hi[2] - Cc.bb_lo[2] + 1};
+      CUTMG_CUDA(cudaMemsetAsync(bc, 0, sizeof(T) * Cc.nbox, s));
+      pass<T, 1>(D.t2, bc, nc, nc, nc, nc, 2, lo3, ex3, F.res_col, D.res_w, W, Cc.nact, s);
+    } else {
+      int lo1[3] = {Cc.bb_lo[0], F.bb_lo[1], 0};
+      int ex1[3] = {Cc.bb_hi[0] - Cc.bb_lo[0] + 1, F.bb_hi[1] - F.bb_lo[1] + 1, 1};
+      pass<T, 0>(rf, D.t1, nf, nf, nc, nf, 0, lo1, ex1, F.res_col, D.res_w, W, nullptr, s);
+      int lo2[3] = {Cc.bb_lo[0], Cc.bb_lo[1], 0};
+      int ex2[3] = {ex1[0], Cc.bb_hi[1] - Cc.bb_lo[1] + 1, 1};
+      CUTMG_CUDA(cudaMemsetAsync(bc, 0, sizeof(T) * Cc.nbox, s));
+      pass<T, 1>(D.t1, bc, nc, nf, nc, nc, 1, lo2, ex2, F.res_col, D.res_w, W, Cc.nact, s);
+    }
+  }
+
+  // x_l += P x_{l-1}
+  template <typename T>
+  void prolong(int l, std::vector<Typed<T>>& DD, const T* xc, T* xf, cudaStream_t s) {
+    const Common& F = com_[l];
+    const Common& Cc = com_[l - 1];
+    Typed<T>& D = DD[l];
+    const int nf = F.n, nc = Cc.n, W = P + 1;
+    if (DIM == 3) {
+      int lo1[3] = {F.bb_lo[0], Cc.bb_lo[1], Cc.bb_lo[2]};
+      int ex1[3] = {F.bb_hi[0] - F.bb_lo[0] + 1, Cc.bb_hi[1] - Cc.bb_lo[1] + 1, Cc.bb_hi[2] - Cc.bb_lo[2] + 1};
+      pass<T, 0>(xc, D.t3, nc, nc, nf, nc, 0, lo1, ex1, F.pro_col, D.pro_w, W, nullptr, s);
+      int lo2[3] = {F.bb_lo[0], F.bb_lo[1], Cc.bb_lo[2]};
+      int ex2[3] = {ex1[0], F.bb_hi[1] - F.bb_lo[1] + 1, ex1[2]};
+      pass<T, 0>(D.t3, D.t4, nf, nc, nf, nf, 1, lo2, ex2, F.pro_col, D.pro_w, W, nullptr, s);
+      int lo3[3] = {F.bb_lo[0], F.bb_lo[1], F.bb_lo[2]};
+      int ex3[3] = {ex1[0], ex2[1], F.bb_hi[2] - F.bb_lo[2] + 1};
+      pass<T, 2>(D.t4, xf, nf, nf, nf, nf, 2, lo3, ex3, F.pro_col, D.pro_w, W, F.nact, s);
+    } else {
+      int lo1[3] = {F.bb_lo[0], Cc.bb_lo[1], 0};
+      int ex1[3] = {F.bb_hi[0] - F.bb_lo[0] + 1, Cc.bb_hi[1] - Cc.bb_lo[1] + 1, 1};
+      pass<T, 0>(xc, D.t3, nc, nc, nf, nc, 0, lo1, ex1, F.pro_col, D.pro_w, W, nullptr, s);
+      int lo2[3] = {F.bb_lo[0], F.bb_lo[1], 0};
+      int ex2[3] = {ex1[0], F.bb_hi[1] - F.bb_lo[1] + 1, 1};
+      pass<T, 2>(D.t3, xf, nf, nc, nf, nf, 1, lo2, ex2, F.pro_col, D.pro_w, W, F.nact, s);
+    }
+  }
+
+  template <typename T>
+  void coarse(Typed<T>& D, const T* b, T* x, cudaStream_t s) {
+    const Common& c = com_[0];
+    const int n0 = (int)c.ndof;
+    k_coarse<T><<<blocks_for(n0, 8), 256, 0, s>>>(D.coarse_inv, c.coarse_nodes, n0, b, x);
+    launch_check("coarse solve");
+  }
+
+  // V-cycle with zero initial guess on level l: x = B_l b (Sec. 2.2)
+  template <typename T>
+  void vcycle_level(int l, std::vector<Typed<T>>& DD, const T* b, T* x, cudaStream_t s) {
+    if (l == 0) {
+      coarse<T>(DD[0], b, x, s);
+      return;
+    }
+    Typed<T>& D = DD[l];
+    CUTMG_CUDA(cudaMemsetAsync(x, 0, sizeof(T) * com_[l].nbox, s));
+    smooth<T>(l, D, false, x, b, s);
+    apply<T>(l, D, x, b, D.r, s);
+    restrict_<T>(l, DD, D.r, DD[l - 1].b, s);
+    vcycle_level<T>(l - 1, DD, DD[l - 1].b, DD[l - 1].x, s);
+    prolong<T>(l, DD, DD[l - 1].x, x, s);
+    smooth<T>(l, D, true, x, b, s);
+  }
+
+  // z = B r on the finest level (box layout, FP64 in and out)
+  void precondition(int prec, const double* r, double* z, cudaStream_t s) {
+    const int L = n_levels() - 1;
+    const auto& F = com_[L];
+    if (prec == 1) {
+      Typed<float>& D = d32_[L];
+      k_convert<float, double><<<kVecBlocks, 256, 0, s>>>(F.region, r, D.b);
+      launch_check("convert r");
+      vcycle_level<float>(L, d32_, D.b, D.x, s);
+      CUTMG_CUDA(cudaMemsetAsync(z, 0, sizeof(double) * F.nbox, s));
+      k_convert<double, float><<<kVecBlocks, 256, 0, s>>>(F.region, D.x, z);
+      launch_check("convert z");
+    } else {
+      vcycle_level<double>(L, d64_, r, z, s);
+    }
+  }
+};
+
+}  // namespace cutmg

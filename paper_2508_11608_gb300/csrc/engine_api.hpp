@@ -1,0 +1,46 @@
+// Type-erased interface between the C ABI and the (dim, degree)-specialised
+// device engines.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <memory>
+#include <stdexcept>
+#include <string>
+
+namespace cutmg {
+
+struct Hierarchy;
+
+struct CudaError : std::runtime_error {
+  using std::runtime_error::runtime_error;
+};
+struct OomError : std::runtime_error {
+  using std::runtime_error::runtime_error;
+};
+
+class EngineBase {
+ public:
+  virtual ~EngineBase() = default;
+  virtual int n_levels() const = 0;
+  virtual int64_t n_dofs(int level) const = 0;
+  virtual size_t device_bytes() const = 0;
+  virtual void level_apply(int l, int prec, const double* x, double* y, cudaStream_t s) = 0;
+  virtual void level_colour(int l, int prec, int cut, int colour, double* x, const double* b,
+                            cudaStream_t s) = 0;
+  virtual void level_smooth(int l, int prec, int post, double* x, const double* b, cudaStream_t s) = 0;
+  virtual void level_restrict(int l, int prec, const double* rf, double* bc, cudaStream_t s) = 0;
+  virtual void level_prolongate(int l, int prec, const double* xc, double* xf, cudaStream_t s) = 0;
+  virtual void coarse_solve(int prec, const double* b0, double* x0, cudaStream_t s) = 0;
+  virtual void apply_fine(const double* x, double* y, cudaStream_t s) = 0;
+  virtual void rhs(double* b, cudaStream_t s) = 0;
+  virtual void vcycle(int prec, const double* r, double* z, cudaStream_t s) = 0;
+  virtual int solve(int prec, const double* b, double* x, double rtol, int maxit, double* rel,
+                    double* true_rel, float* ms, cudaStream_t s) = 0;
+};
+
+std::unique_ptr<EngineBase> make_engine_d2(int degree, const Hierarchy& H);
+std::unique_ptr<EngineBase> make_engine_d3(int degree, const Hierarchy& H);
+
+}  // namespace cutmg

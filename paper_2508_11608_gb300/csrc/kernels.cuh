@@ -1,0 +1,712 @@
+// Device kernels of the CutFEM multigrid hot path (sm_103a), templated on the
+// dimension, the polynomial degree and the arithmetic type (double for the
+// plain form, float for the mixed form's V-cycle).
+//
+// Layout: every level vector lives on the full (pN+1)^DIM lattice ("box"),
+// first coordinate fastest; inactive nodes hold zero and are never written.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace cutmg {
+
+constexpr uint8_t kActive = 1;
+constexpr uint8_t kCutCell = 2;
+
+template <int DIM, int P>
+struct Shape {
+  static constexpr int NB = (DIM == 2) ? (P + 1) * (P + 1) : (P + 1) * (P + 1) * (P + 1);
+  static constexpr int C = 2 * P + 1;  // closure nodes per direction of a patch
+  static constexpr int M = 2 * P - 1;  // interior nodes per direction of a patch
+  static constexpr int NO = (DIM == 2) ? P * P : P * P * P;  // nodes owned by a position
+};
+
+// Everything the matrix-free operator needs on one level.
+template <typename T>
+struct OpArgs {
+  int N, n;               // cells and nodes per direction
+  const uint8_t* cflag;   // N^DIM cell flags
+  const int* cut_id;      // N^DIM index of the cut-cell matrix, -1 if none
+  const T* cutmat;        // [n_cut][NB][NB] volume + Nitsche terms of cut cells
+  const T* Kref;          // [NB][NB] stiffness of an uncut cell
+  T dvec[3][7];           // jump weights of the m-th normal derivative across a face
+  T coef[3];              // gamma_m h^(2m-1)/(m!)^2 h^(DIM-1)
+  T Mhat[4][4];           // 1D reference mass matrix
+};
+
+// ---------------------------------------------------------------------------
+// (A x)_i for one lattice node i (idx = its lattice coordinates): every
+// active cell containing i plus every ghost face whose two cells contain i.
+template <int DIM, int P, typename T>
+__device__ __forceinline__ T row_apply(const OpArgs<T>& A, const T* __restrict__ x,
+                                       const int* idx, const T* __restrict__ sK) {
+  constexpr int NB = Shape<DIM, P>::NB;
+  const int N = A.N, n = A.n;
+  T acc = T(0);
+  int cc[DIM][2], lc[DIM][2], nopt[DIM];
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) {
+    int i = idx[k], a = i / P, r = i - a * P, m = 0;
+    if (r == 0) {
+      if (a - 1 >= 0) { cc[k][m] = a - 1; lc[k][m] = P; ++m; }
+      if (a < N) { cc[k][m] = a; lc[k][m] = 0; ++m; }
+    } else {
+      cc[k][m] = a; lc[k][m] = r; ++m;
+    }
+    nopt[k] = m;
+  }
+  const int tot = (DIM == 2) ? nopt[0] * nopt[1] : nopt[0] * nopt[1] * nopt[2];
+  for (int s = 0; s < tot; ++s) {
+    int t = s, cell = 0, row = 0, base = 0, cst = 1, rst = 1, nst = 1;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+      int o = t % nopt[k];
+      t /= nopt[k];
+      cell += cc[k][o] * cst;
+      cst *= N;
+      row += lc[k][o] * rst;
+      rst *= (P + 1);
+      base += P * cc[k][o] * nst;
+      nst *= n;
+    }
+    const uint8_t f = A.cflag[cell];
+    if (!(f & kActive)) continue;
+    const T* Mrow = (f & kCutCell) ? (A.cutmat + (size_t)A.cut_id[cell] * NB * NB + row * NB)
+                                   : (sK + row * NB);
+    if (DIM == 2) {
+#pragma unroll
+      for (int j1 = 0; j1 <= P; ++j1)
+#pragma unroll
+        for (int j0 = 0; j0 <= P; ++j0)
+          acc += Mrow[j0 + (P + 1) * j1] * x[base + j0 + n * j1];
+    } else {
+#pragma unroll
+      for (int j2 = 0; j2 <= P; ++j2)
+#pragma unroll
+        for (int j1 = 0; j1 <= P; ++j1)
+#pragma unroll
+          for (int j0 = 0; j0 <= P; ++j0)
+            acc += Mrow[j0 + (P + 1) * (j1 + (P + 1) * j2)] * x[base + j0 + n * (j1 + n * j2)];
+    }
+  }
+  // ghost faces with normal k: lower cell L, upper L + e_k
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) {
+    const int i = idx[k], a = i / P, r = i - a * P;
+    int Llo = (r == 0) ? a - 2 : a - 1, Lhi = a;
+    if (Llo < 0) Llo = 0;
+    if (Lhi > N - 2) Lhi = N - 2;
+    // tangential options: the cells containing i in the other directions
+    int tc[2][2], to[2], tdim[2], q = 0;
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) {
+      if (j == k) continue;
+      tdim[q] = j;
+      to[q] = nopt[j];
+      tc[q][0] = cc[j][0];
+      tc[q][1] = cc[j][nopt[j] > 1 ? 1 : 0];
+      ++q;
+    }
+    const int ntan = (DIM == 2) ? to[0] : to[0] * to[1];
+    for (int Lk = Llo; Lk <= Lhi; ++Lk) {
+      for (int s = 0; s < ntan; ++s) {
+        int c1[3] = {0, 0, 0};
+        c1[k] = Lk;
+        int u = s;
+#pragma unroll
+        for (int qq = 0; qq < DIM - 1; ++qq) {
+          c1[tdim[qq]] = tc[qq][u % to[qq]];
+          u /= to[qq];
+        }
+        int cell1 = c1[0] + N * (c1[1] + (DIM == 3 ? N * c1[2] : 0));
+        int stride_k = (k == 0) ? 1 : (k == 1 ? N : N * N);
+        const uint8_t f1 = A.cflag[cell1], f2 = A.cflag[cell1 + stride_k];
+        if (!((f1 & kActive) && (f2 & kActive) && ((f1 | f2) & kCutCell))) continue;
+        // local coordinates of i in the face block
+        const int il = i - P * Lk;
+        int tl[2] = {0, 0};
+#pragma unroll
+        for (int qq = 0; qq < DIM - 1; ++qq) tl[qq] = idx[tdim[qq]] - P * c1[tdim[qq]];
+        // S_m = sum_{i'} dvec[m][i'] sum_{t'} prod Mhat[t][t'] x(i', t')
+        T Sm[P];
+#pragma unroll
+        for (int m = 0; m < P; ++m) Sm[m] = T(0);
+        int sk = 1, s0 = 1, s1 = 1;
+        {
+          int st = 1;
+#pragma unroll
+          for (int j = 0; j < DIM; ++j) {
+            if (j == k) sk = st;
+            st *= n;
+          }
+          s0 = (tdim[0] == 0) ? 1 : (tdim[0] == 1 ? n : n * n);
+          if (DIM == 3) s1 = (tdim[1] == 0) ? 1 : (tdim[1] == 1 ? n : n * n);
+        }
+        int base = P * (c1[0] + n * (c1[1] + (DIM == 3 ? n * c1[2] : 0)));
+#pragma unroll
+        for (int ip = 0; ip <= 2 * P; ++ip) {
+          T w = T(0);
+          if (DIM == 2) {
+#pragma unroll
+            for (int t0 = 0; t0 <= P; ++t0) w += A.Mhat[tl[0]][t0] * x[base + ip * sk + t0 * s0];
+          } else {
+#pragma unroll
+            for (int t1 = 0; t1 <= P; ++t1) {
+              T w1 = T(0);
+#pragma unroll
+              for (int t0 = 0; t0 <= P; ++t0) w1 += A.Mhat[tl[0]][t0] * x[base + ip * sk + t0 * s0 + t1 * s1];
+              w += A.Mhat[tl[1]][t1] * w1;
+            }
+          }
+#pragma unroll
+          for (int m = 0; m < P; ++m) Sm[m] += A.dvec[m][ip] * w;
+        }
+#pragma unroll
+        for (int m = 0; m < P; ++m) acc += A.coef[m] * A.dvec[m][il] * Sm[m];
+      }
+    }
+  }
+  return acc;
+}
+
+template <int NB, typename T>
+__device__ __forceinline__ void stage_kref(const T* __restrict__ g, T* s) {
+  for (int i = threadIdx.x; i < NB * NB; i += blockDim.x) s[i] = g[i];
+  __syncthreads();
+}
+
+// y = A x (b == nullptr) or y = b - A x, at the active nodes of positions whose
+// 2^DIM surrounding cells are all plain interior cells: each thread owns the
+// P^DIM nodes P a + alpha, alpha in [0, P)^DIM, and sums their rows over the
+// 2^DIM cells with the uncut element matrix.
+template <int DIM, int P, typename T>
+__global__ void __launch_bounds__(128) k_apply_bulk(OpArgs<T> A, const T* __restrict__ x,
+                                                    const T* __restrict__ b, T* __restrict__ y,
+                                                    const int* __restrict__ pos, int npos) {
+  constexpr int NB = Shape<DIM, P>::NB;
+  constexpr int NO = Shape<DIM, P>::NO;
+  __shared__ T sK[NB * NB];
+  stage_kref<NB>(A.Kref, sK);
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= npos) return;
+  const int np = A.N + 1, n = A.n;
+  int q = pos[t];
+  int a[3] = {0, 0, 0};
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) {
+    a[k] = q % np;
+    q /= np;
+  }
+  T out[NO];
+#pragma unroll
+  for (int o = 0; o < NO; ++o) out[o] = T(0);
+#pragma unroll
+  for (int s = 0; s < (1 << DIM); ++s) {
+    int base = 0, st = 1;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+      base += P * (a[k] - ((s >> k) & 1)) * st;
+      st *= n;
+    }
+    T xv[NB];
+    if (DIM == 2) {
+#pragma unroll
+      for (int j1 = 0; j1 <= P; ++j1)
+#pragma unroll
+        for (int j0 = 0; j0 <= P; ++j0) xv[j0 + (P + 1) * j1] = x[base + j0 + n * j1];
+    } else {
+#pragma unroll
+      for (int j2 = 0; j2 <= P; ++j2)
+#pragma unroll
+        for (int j1 = 0; j1 <= P; ++j1)
+#pragma unroll
+          for (int j0 = 0; j0 <= P; ++j0)
+            xv[j0 + (P + 1) * (j1 + (P + 1) * j2)] = x[base + j0 + n * (j1 + n * j2)];
+    }
+#pragma unroll
+    for (int o = 0; o < NO; ++o) {
+      int al[3] = {0, 0, 0}, u = o;
+      bool in = true;
+      int row = 0, rst = 1;
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) {
+        al[k] = u % P;
+        u /= P;
+        const int sk = (s >> k) & 1;
+        if (sk && al[k] != 0) in = false;
+        row += (sk ? P : al[k]) * rst;
+        rst *= (P + 1);
+      }
+      if (!in) continue;
+      T acc = T(0);
+#pragma unroll
+      for (int j = 0; j < NB; ++j) acc += sK[row * NB + j] * xv[j];
+      out[o] += acc;
+    }
+  }
+#pragma unroll
+  for (int o = 0; o < NO; ++o) {
+    int u = o, node = 0, st = 1;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+      node += (P * a[k] + u % P) * st;
+      u /= P;
+      st *= n;
+    }
+    y[node] = b ? b[node] - out[o] : out[o];
+  }
+}
+
+// Same output for the remaining active nodes, one thread per node, general rows.
+template <int DIM, int P, typename T>
+__global__ void __launch_bounds__(128) k_apply_bnd(OpArgs<T> A, const T* __restrict__ x,
+                                                   const T* __restrict__ b, T* __restrict__ y,
+                                                   const int* __restrict__ nodes, int nn) {
+  constexpr int NB = Shape<DIM, P>::NB;
+  __shared__ T sK[NB * NB];
+  stage_kref<NB>(A.Kref, sK);
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nn) return;
+  const int node = nodes[t];
+  int idx[3] = {0, 0, 0}, u = node;
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) {
+    idx[k] = u % A.n;
+    u /= A.n;
+  }
+  const T v = row_apply<DIM, P, T>(A, x, idx, sK);
+  y[node] = b ? b[node] - v : v;
+}
+
+// ---------------------------------------------------------------------------
+// Interior-patch colour step (Sec. 3, fast diagonalisation): one warp per
+// patch.  r_I = b_I - (sum_k (x)_k Kbar/Mbar)[I, closure] x_closure by sum
+// factorisation over the 2p+1 closure lattice; delta = (S x..x S)
+// diag(1/sum lam) (S^T x..x S^T) r_I; x_I += delta.  Patches of one colour
+// have disjoint closures' interiors and no ghost coupling, so every warp
+// reads only values no other warp of the launch writes.
+template <typename T, int P>
+struct FdArgs {
+  static constexpr int C = 2 * P + 1, M = 2 * P - 1;
+  T Mr[M][C], Kr[M][C];  // interior rows of the two-cell 1D mass / stiffness
+  T S[M][M];             // K_I S = M_I S diag(lam), S^T M_I S = I
+  T lam[M];
+};
+
+template <int DIM, int P, typename T, int WARPS>
+__global__ void __launch_bounds__(32 * WARPS) k_smooth_cart(FdArgs<T, P> F, int N, int n,
+                                                            T* __restrict__ x, const T* __restrict__ b,
+                                                            const int* __restrict__ verts, int nv) {
+  constexpr int C = 2 * P + 1, M = 2 * P - 1;
+  constexpr int NC = (DIM == 2) ? C * C : C * C * C;
+  constexpr int NI = (DIM == 2) ? M * M : M * M * M;
+  constexpr int NU = (DIM == 2) ? M * C : M * C * C;  // after the first contraction
+  constexpr int NV = (DIM == 2) ? 1 : M * M * C;       // after the second (3D)
+  __shared__ T sx[WARPS][NC];
+  __shared__ T su[WARPS][2][NU];
+  __shared__ T sv[WARPS][3][NV];
+  __shared__ T sr[WARPS][NI];
+  __shared__ T st[WARPS][NI];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int pidx = blockIdx.x * WARPS + w;
+  if (pidx >= nv) return;
+  const int np = N + 1;
+  int q = verts[pidx], v[3] = {0, 0, 0};
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) {
+    v[k] = q % np;
+    q /= np;
+  }
+  int base = 0;
+  {
+    int s = 1;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+      base += P * (v[k] - 1) * s;
+      s *= n;
+    }
+  }
+  T* X = sx[w];
+  for (int e = lane; e < NC; e += 32) {
+    int o0 = e % C, r = e / C;
+    int off = (DIM == 2) ? o0 + n * r : o0 + n * (r % C + n * (r / C));
+    X[e] = x[base + off];
+  }
+  __syncwarp();
+  T* U1 = su[w][0];
+  T* U2 = su[w][1];
+  T* R = sr[w];
+  if (DIM == 2) {
+    // u1[yi][x] = sum_y Mr[yi][y] X[y][x]; u2 with Kr
+    for (int e = lane; e < M * C; e += 32) {
+      int xx = e % C, yi = e / C;
+      T a1 = T(0), a2 = T(0);
+#pragma unroll
+      for (int y = 0; y < C; ++y) {
+        T xv = X[y * C + xx];
+        a1 += F.Mr[yi][y] * xv;
+        a2 += F.Kr[yi][y] * xv;
+      }
+      U1[e] = a1;
+      U2[e] = a2;
+    }
+    __syncwarp();
+    // r = b - (Kx u1 + Mx u2)
+    for (int e = lane; e < NI; e += 32) {
+      int xi = e % M, yi = e / M;
+      T acc = T(0);
+#pragma unroll
+      for (int xx = 0; xx < C; ++xx) acc += F.Kr[xi][xx] * U1[yi * C + xx] + F.Mr[xi][xx] * U2[yi * C + xx];
+      int node = base + (xi + 1) + n * (yi + 1);
+      R[e] = b[node] - acc;
+    }
+  } else {
+    T* V1 = sv[w][0];
+    T* V2 = sv[w][1];
+    T* V3 = sv[w][2];
+    // along z: u1 = Mz X, u2 = Kz X   (zi, y, x)
+    for (int e = lane; e < M * C * C; e += 32) {
+      int yx = e % (C * C), zi = e / (C * C);
+      T a1 = T(0), a2 = T(0);
+#pragma unroll
+      for (int z = 0; z < C; ++z) {
+        T xv = X[z * C * C + yx];
+        a1 += F.Mr[zi][z] * xv;
+        a2 += F.Kr[zi][z] * xv;
+      }
+      U1[e] = a1;
+      U2[e] = a2;
+    }
+    __syncwarp();
+    // along y: v1 = My u1, v2 = Ky u1, v3 = My u2   (zi, yi, x)
+    for (int e = lane; e < M * M * C; e += 32) {
+      int xx = e % C, r = e / C, yi = r % M, zi = r / M;
+      T a1 = T(0), a2 = T(0), a3 = T(0);
+#pragma unroll
+      for (int y = 0; y < C; ++y) {
+        T u1 = U1[(zi * C + y) * C + xx], u2 = U2[(zi * C + y) * C + xx];
+        a1 += F.Mr[yi][y] * u1;
+        a2 += F.Kr[yi][y] * u1;
+        a3 += F.Mr[yi][y] * u2;
+      }
+      V1[e] = a1;
+      V2[e] = a2;
+      V3[e] = a3;
+    }
+    __syncwarp();
+    // along x: r = b - (Kx v1 + Mx (v2 + v3))
+    for (int e = lane; e < NI; e += 32) {
+      int xi = e % M, r = e / M, yi = r % M, zi = r / M;
+      T acc = T(0);
+#pragma unroll
+      for (int xx = 0; xx < C; ++xx) {
+        int o = (zi * M + yi) * C + xx;
+        acc += F.Kr[xi][xx] * V1[o] + F.Mr[xi][xx] * (V2[o] + V3[o]);
+      }
+      int node = base + (xi + 1) + n * ((yi + 1) + n * (zi + 1));
+      R[e] = b[node] - acc;
+    }
+  }
+  __syncwarp();
+  // fast diagonalisation: t = (S^T)^{(x) DIM} r, scale, delta = S^{(x) DIM} t
+  T* Tt = st[w];
+  // S^T along x
+  for (int e = lane; e < NI; e += 32) {
+    int a = e % M, rest = e / M;
+    T acc = T(0);
+#pragma unroll
+    for (int i = 0; i < M; ++i) acc += F.S[i][a] * R[rest * M + i];
+    Tt[e] = acc;
+  }
+  __syncwarp();
+  // S^T along y
+  for (int e = lane; e < NI; e += 32) {
+    int xx = e % M, r = e / M, bb = r % M, zi = r / M;
+    T acc = T(0);
+#pragma unroll
+    for (int i = 0; i < M; ++i) acc += F.S[i][bb] * Tt[(zi * M + i) * M + xx];
+    R[e] = acc;
+  }
+  __syncwarp();
+  if (DIM == 3) {
+    // S^T along z, then scale
+    for (int e = lane; e < NI; e += 32) {
+      int yx = e % (M * M), cz = e / (M * M);
+      T acc = T(0);
+#pragma unroll
+      for (int i = 0; i < M; ++i) acc += F.S[i][cz] * R[i * M * M + yx];
+      int a = e % M, bb = (e / M) % M;
+      Tt[e] = acc / (F.lam[a] + F.lam[bb] + F.lam[cz]);
+    }
+    __syncwarp();
+    // S along z
+    for (int e = lane; e < NI; e += 32) {
+      int yx = e % (M * M), zi = e / (M * M);
+      T acc = T(0);
+#pragma unroll
+      for (int c = 0; c < M; ++c) acc += F.S[zi][c] * Tt[c * M * M + yx];
+      R[e] = acc;
+    }
+  } else {
+    for (int e = lane; e < NI; e += 32) {
+      int a = e % M, bb = e / M;
+      R[e] = R[e] / (F.lam[a] + F.lam[bb]);
+    }
+  }
+  __syncwarp();
+  // S along y
+  for (int e = lane; e < NI; e += 32) {
+    int xx = e % M, r = e / M, yi = r % M, zi = r / M;
+    T acc = T(0);
+#pragma unroll
+    for (int c = 0; c < M; ++c) acc += F.S[yi][c] * R[(zi * M + c) * M + xx];
+    Tt[e] = acc;
+  }
+  __syncwarp();
+  // S along x, update x
+  for (int e = lane; e < NI; e += 32) {
+    int xi = e % M, rest = e / M;
+    T acc = T(0);
+#pragma unroll
+    for (int c = 0; c < M; ++c) acc += F.S[xi][c] * Tt[rest * M + c];
+    int yi = rest % M, zi = rest / M;
+    int node = (DIM == 2) ? base + (xi + 1) + n * (yi + 1)
+                          : base + (xi + 1) + n * ((yi + 1) + n * (zi + 1));
+    x[node] += acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Cut-patch colour step, phase 1: residual rows of every patch DoF of the
+// colour into rbuf (all patches of the colour read the same x: additive within
+// a colour, Sec. 2.3 inconsistent ghost-penalty treatment).  One warp per patch.
+template <int DIM, int P, typename T, int WARPS>
+__global__ void __launch_bounds__(32 * WARPS) k_cut_resid(OpArgs<T> A, const T* __restrict__ x,
+                                                          const T* __restrict__ b,
+                                                          const int* __restrict__ verts,
+                                                          const int* __restrict__ cnt,
+                                                          const int* __restrict__ moff,
+                                                          const uint16_t* __restrict__ members,
+                                                          T* __restrict__ rbuf, int npatch) {
+  constexpr int NB = Shape<DIM, P>::NB;
+  constexpr int C = 2 * P + 1;
+  __shared__ T sK[NB * NB];
+  stage_kref<NB>(A.Kref, sK);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int pidx = blockIdx.x * WARPS + w;
+  if (pidx >= npatch) return;
+  const int np = A.N + 1;
+  int q = verts[pidx], v[3] = {0, 0, 0};
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) {
+    v[k] = q % np;
+    q /= np;
+  }
+  const int m = cnt[pidx], mo = moff[pidx];
+  for (int e = lane; e < m; e += 32) {
+    int o = members[mo + e], idx[3] = {0, 0, 0}, node = 0, st = 1;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+      idx[k] = P * (v[k] - 1) + o % C;
+      o /= C;
+      node += idx[k] * st;
+      st *= A.n;
+    }
+    rbuf[mo + e] = b[node] - row_apply<DIM, P, T>(A, x, idx, sK);
+  }
+}
+
+// Phase 2: delta = A_j^{-1} r_j (explicit inverse, symmetric, read by
+// columns so that lanes load consecutive entries), x[I_j] += delta.
+template <int DIM, int P, typename T, int WARPS>
+__global__ void __launch_bounds__(32 * WARPS) k_cut_update(int N, int n, T* __restrict__ x,
+                                                           const int* __restrict__ verts,
+                                                           const int* __restrict__ cnt,
+                                                           const int* __restrict__ moff,
+                                                           const int64_t* __restrict__ ioff,
+                                                           const uint16_t* __restrict__ members,
+                                                           const T* __restrict__ inv,
+                                                           const T* __restrict__ rbuf, int npatch) {
+  constexpr int C = 2 * P + 1;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int pidx = blockIdx.x * WARPS + w;
+  if (pidx >= npatch) return;
+  const int np = N + 1;
+  int q = verts[pidx], v[3] = {0, 0, 0};
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) {
+    v[k] = q % np;
+    q /= np;
+  }
+  const int m = cnt[pidx], mo = moff[pidx];
+  const T* Ai = inv + ioff[pidx];
+  const T* r = rbuf + mo;
+  for (int e = lane; e < m; e += 32) {
+    T acc = T(0);
+    for (int j = 0; j < m; ++j) acc += Ai[(size_t)j * m + e] * r[j];
+    int o = members[mo + e], node = 0, st = 1;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+      node += (P * (v[k] - 1) + o % C) * st;
+      o /= C;
+      st *= n;
+    }
+    x[node] += acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Transfer: one direction of a tensor-product sparse 1D matrix with W entries
+// per output index, over a box region of the output.  MODE 0: out = sum;
+// MODE 1: out = mask ? sum : 0; MODE 2: out += mask ? sum : 0.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) k_pass(const T* __restrict__ in, T* __restrict__ out,
+                                              int in0, int in1, int out0, int out1, int axis,
+                                              int lo0, int lo1, int lo2, int ext0, int ext1,
+                                              int ext2, const int* __restrict__ col,
+                                              const T* __restrict__ wt, int W,
+                                              const uint8_t* __restrict__ mask) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t total = (int64_t)ext0 * ext1 * ext2;
+  if (t >= total) return;
+  const int i0 = lo0 + (int)(t % ext0);
+  const int i1 = lo1 + (int)((t / ext0) % ext1);
+  const int i2 = lo2 + (int)(t / ((int64_t)ext0 * ext1));
+  const int io = (axis == 0) ? i0 : (axis == 1 ? i1 : i2);
+  T acc = T(0);
+  for (int e = 0; e < W; ++e) {
+    const int c = col[io * W + e];
+    const T wv = wt[io * W + e];
+    const int j0 = axis == 0 ? c : i0, j1 = axis == 1 ? c : i1, j2 = axis == 2 ? c : i2;
+    acc += wv * in[(int64_t)j0 + (int64_t)in0 * (j1 + (int64_t)in1 * j2)];
+  }
+  const int64_t o = (int64_t)i0 + (int64_t)out0 * (i1 + (int64_t)out1 * i2);
+  if (MODE == 0) out[o] = acc;
+  else if (MODE == 1) out[o] = mask[o] ? acc : T(0);
+  else if (mask[o]) out[o] += acc;
+}
+
+// Coarsest level: x0[node_i] = sum_j Ainv[i][j] b0[node_j], one warp per row.
+template <typename T>
+__global__ void __launch_bounds__(256) k_coarse(const T* __restrict__ Ainv, const int* __restrict__ nodes,
+                                                int n0, const T* __restrict__ b, T* __restrict__ x) {
+  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= n0) return;
+  T acc = T(0);
+  for (int j = lane; j < n0; j += 32) acc += Ainv[(size_t)row * n0 + j] * b[nodes[j]];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) x[nodes[row]] = acc;
+}
+
+// ---------------------------------------------------------------------------
+// Vector kernels over a box region (bbox of the active nodes).
+struct Region {
+  int n0, n1;             // lattice strides (nodes per direction)
+  int lo0, lo1, lo2;      // region origin
+  int e0, e1, e2;         // region extents
+  __device__ __forceinline__ int64_t at(int64_t t) const {
+    const int i0 = lo0 + (int)(t % e0);
+    const int i1 = lo1 + (int)((t / e0) % e1);
+    const int i2 = lo2 + (int)(t / ((int64_t)e0 * e1));
+    return (int64_t)i0 + (int64_t)n0 * (i1 + (int64_t)n1 * i2);
+  }
+  __host__ __device__ int64_t size() const { return (int64_t)e0 * e1 * e2; }
+};
+
+// partial sums of a.b, one per block, fixed assignment (deterministic)
+static __global__ void __launch_bounds__(256) k_dot_partial(Region R, const double* __restrict__ a,
+                                                     const double* __restrict__ b,
+                                                     double* __restrict__ part) {
+  __shared__ double s[256];
+  double acc = 0.0;
+  const int64_t tot = R.size();
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = R.at(t);
+    acc += a[o] * b[o];
+  }
+  s[threadIdx.x] = acc;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h) s[threadIdx.x] += s[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = s[0];
+}
+
+static __global__ void __launch_bounds__(256) k_dot_final(const double* __restrict__ part, int np,
+                                                   double* __restrict__ out) {
+  __shared__ double s[256];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < np; i += 256) acc += part[i];
+  s[threadIdx.x] = acc;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h) s[threadIdx.x] += s[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = s[0];
+}
+
+// CG scalars: sc[0] = rz, sc[1] = pq, sc[2] = rz_new
+// x += alpha p, r -= alpha q with alpha = rz / pq
+static __global__ void __launch_bounds__(256) k_cg_update_xr(Region R, const double* __restrict__ sc,
+                                                      double* __restrict__ x, double* __restrict__ r,
+                                                      const double* __restrict__ p,
+                                                      const double* __restrict__ q) {
+  const double alpha = sc[0] / sc[1];
+  const int64_t tot = R.size();
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = R.at(t);
+    x[o] += alpha * p[o];
+    r[o] -= alpha * q[o];
+  }
+}
+
+// p = z + beta p, beta = rz_new / rz; then rz = rz_new (single writer after the grid)
+static __global__ void __launch_bounds__(256) k_cg_update_p(Region R, const double* __restrict__ sc,
+                                                     double* __restrict__ p, const double* __restrict__ z) {
+  const double beta = sc[2] / sc[0];
+  const int64_t tot = R.size();
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = R.at(t);
+    p[o] = z[o] + beta * p[o];
+  }
+}
+
+static __global__ void k_copy_scalar(double* __restrict__ sc, int dst, int src) { sc[dst] = sc[src]; }
+
+template <typename TO, typename TI>
+__global__ void __launch_bounds__(256) k_convert(Region R, const TI* __restrict__ in, TO* __restrict__ out) {
+  const int64_t tot = R.size();
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = R.at(t);
+    out[o] = (TO)in[o];
+  }
+}
+
+// compact (DoF order) <-> box
+template <typename TO, typename TI>
+__global__ void __launch_bounds__(256) k_scatter(const int64_t* __restrict__ dofs, int64_t nd,
+                                                 const TI* __restrict__ in, TO* __restrict__ box) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nd;
+       i += (int64_t)gridDim.x * blockDim.x)
+    box[dofs[i]] = (TO)in[i];
+}
+
+template <typename TO, typename TI>
+__global__ void __launch_bounds__(256) k_gather(const int64_t* __restrict__ dofs, int64_t nd,
+                                                const TI* __restrict__ box, TO* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nd;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (TO)box[dofs[i]];
+}
+
+}  // namespace cutmg

@@ -1,0 +1,875 @@
+// Host construction of the CutFEM multigrid hierarchy (FP64, OpenMP over
+// cells and patches).  See setup.hpp for the data layout.
+//
+// Operator (Sec. 2.1, eqs. "cutfem_nitsche", "cutfem-ghost"):
+//   uncut cells       standard Q_p stiffness, Kronecker form of 1D matrices
+//   cut cells         volume + Nitsche terms by the cut-cell rules
+//   ghost faces       sum_m gamma_m h^(2m-1)/(m!)^2 ([d_n^m u], [d_n^m v])_F
+//                     (the face scaling of the ghost penalty the paper cites; the
+//                     printed h^(2m+1) loses coercivity under refinement)
+// Patches (Sec. 2.3, Sec. 3): one per vertex of an active cell (the patches
+// cover Omega_l); DoFs whose support lies in the patch; interior patches
+// (2^d uncut cells, no ghost face on any patch cell) use fast
+// diagonalisation, all others an explicit FP64 inverse of A[I_j, I_j].
+#include "setup.hpp"
+
+#include <cmath>
+#include <cstring>
+#include <stdexcept>
+
+namespace cutmg {
+namespace {
+
+int ipow(int b, int e) {
+  int r = 1;
+  for (int i = 0; i < e; ++i) r *= b;
+  return r;
+}
+
+// SPD matrix (row-major, n x n) -> its inverse, through L L^T.
+void spd_inverse(int n, double* A) {
+  std::vector<double> L((size_t)n * n, 0.0), Li((size_t)n * n, 0.0);
+  for (int j = 0; j < n; ++j) {
+    double s = A[(size_t)j * n + j];
+    for (int k = 0; k < j; ++k) s -= L[(size_t)j * n + k] * L[(size_t)j * n + k];
+    if (!(s > 0.0))
+      throw std::runtime_error("matrix is not positive definite (pivot " + std::to_string(j) + " of " +
+                               std::to_string(n) + ": " + std::to_string(s) + ")");
+    double ljj = std::sqrt(s);
+    L[(size_t)j * n + j] = ljj;
+    for (int i = j + 1; i < n; ++i) {
+      double t = A[(size_t)i * n + j];
+      for (int k = 0; k < j; ++k) t -= L[(size_t)i * n + k] * L[(size_t)j * n + k];
+      L[(size_t)i * n + j] = t / ljj;
+    }
+  }
+  // Li = L^{-1} (lower triangular), column by column
+  for (int c = 0; c < n; ++c) {
+    for (int i = c; i < n; ++i) {
+      double t = (i == c) ? 1.0 : 0.0;
+      for (int k = c; k < i; ++k) t -= L[(size_t)i * n + k] * Li[(size_t)k * n + c];
+      Li[(size_t)i * n + c] = t / L[(size_t)i * n + i];
+    }
+  }
+  // A^{-1} = Li^T Li
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j <= i; ++j) {
+      double t = 0.0;
+      for (int k = i; k < n; ++k) t += Li[(size_t)k * n + i] * Li[(size_t)k * n + j];
+      A[(size_t)i * n + j] = t;
+      A[(size_t)j * n + i] = t;
+    }
+}
+
+// Symmetric eigen-decomposition by cyclic Jacobi rotations: A = Q diag(lam) Q^T.
+void jacobi_eigen(int n, std::vector<double> A, std::vector<double>& Q, std::vector<double>& lam) {
+  Q.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) Q[(size_t)i * n + i] = 1.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0;
+    for (int i = 0; i < n; ++i)
+      for (int j = i + 1; j < n; ++j) off += A[(size_t)i * n + j] * A[(size_t)i * n + j];
+    if (off < 1e-60) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        double apq = A[(size_t)p * n + q];
+        if (apq == 0.0) continue;
+        double theta = (A[(size_t)q * n + q] - A[(size_t)p * n + p]) / (2.0 * apq);
+        double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < n; ++k) {
+          double akp = A[(size_t)k * n + p], akq = A[(size_t)k * n + q];
+          A[(size_t)k * n + p] = c * akp - s * akq;
+          A[(size_t)k * n + q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) {
+          double apk = A[(size_t)p * n + k], aqk = A[(size_t)q * n + k];
+          A[(size_t)p * n + k] = c * apk - s * aqk;
+          A[(size_t)q * n + k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < n; ++k) {
+          double qkp = Q[(size_t)k * n + p], qkq = Q[(size_t)k * n + q];
+          Q[(size_t)k * n + p] = c * qkp - s * qkq;
+          Q[(size_t)k * n + q] = s * qkp + c * qkq;
+        }
+      }
+  }
+  lam.resize(n);
+  for (int i = 0; i < n; ++i) lam[i] = A[(size_t)i * n + i];
+}
+
+struct RefTables {
+  int p, d, NB;
+  Poly1D b;
+  std::vector<double> M1, K1;  // (p+1)^2 reference mass / stiffness on [0, 1]
+  explicit RefTables(int p_, int d_) : p(p_), d(d_), NB(ipow(p_ + 1, d_)), b(p_) {
+    GaussRule g = gauss_legendre01(p + 1);
+    M1.assign((p + 1) * (p + 1), 0.0);
+    K1.assign((p + 1) * (p + 1), 0.0);
+    for (int a = 0; a <= p; ++a)
+      for (int c = 0; c <= p; ++c)
+        for (int i = 0; i <= p; ++i) {
+          double xi = g.x[i];
+          M1[a * (p + 1) + c] += g.w[i] * b.eval(a, xi) * b.eval(c, xi);
+          K1[a * (p + 1) + c] += g.w[i] * b.eval(a, xi, 1) * b.eval(c, xi, 1);
+        }
+  }
+  // local index j -> multi-index, first coordinate fastest
+  void split(int j, int* a) const {
+    for (int k = 0; k < d; ++k) {
+      a[k] = j % (p + 1);
+      j /= p + 1;
+    }
+  }
+  // tensor basis values and physical gradients at reference point xi
+  void eval(const double* xi, double h, double* v, double* g /* NB x d */) const {
+    double l[3][4], dl[3][4];
+    for (int k = 0; k < d; ++k)
+      for (int a = 0; a <= p; ++a) {
+        l[k][a] = b.eval(a, xi[k]);
+        dl[k][a] = b.eval(a, xi[k], 1) / h;
+      }
+    for (int j = 0; j < NB; ++j) {
+      int a[3];
+      split(j, a);
+      double val = 1.0;
+      for (int k = 0; k < d; ++k) val *= l[k][a[k]];
+      v[j] = val;
+      for (int k = 0; k < d; ++k) {
+        double t = 1.0;
+        for (int kk = 0; kk < d; ++kk) t *= (kk == k) ? dl[kk][a[kk]] : l[kk][a[kk]];
+        g[j * d + k] = t;
+      }
+    }
+  }
+};
+
+// a_T(phi_j, phi_i) of a cut cell: volume + Nitsche terms
+void cut_cell_matrix(const RefTables& R, const CutRule& rule, const double* lo, double h,
+                     double gamma_D, double* K) {
+  const int NB = R.NB, d = R.d;
+  std::vector<double> v(NB), g(NB * d);
+  std::fill(K, K + NB * NB, 0.0);
+  double xi[3];
+  for (const auto& nd : rule.vol) {
+    for (int k = 0; k < d; ++k) xi[k] = (nd.x[k] - lo[k]) / h;
+    R.eval(xi, h, v.data(), g.data());
+    for (int i = 0; i < NB; ++i)
+      for (int j = 0; j < NB; ++j) {
+        double s = 0.0;
+        for (int k = 0; k < d; ++k) s += g[i * d + k] * g[j * d + k];
+        K[i * NB + j] += nd.w * s;
+      }
+  }
+  std::vector<double> dn(NB);
+  for (size_t q = 0; q < rule.surf.size(); ++q) {
+    const auto& nd = rule.surf[q];
+    for (int k = 0; k < d; ++k) xi[k] = (nd.x[k] - lo[k]) / h;
+    R.eval(xi, h, v.data(), g.data());
+    for (int i = 0; i < NB; ++i) {
+      double s = 0.0;
+      for (int k = 0; k < d; ++k) s += rule.normal[q][k] * g[i * d + k];
+      dn[i] = s;
+    }
+    for (int i = 0; i < NB; ++i)
+      for (int j = 0; j < NB; ++j)
+        K[i * NB + j] += nd.w * (-(dn[i] * v[j] + v[i] * dn[j]) + gamma_D / h * v[i] * v[j]);
+  }
+}
+
+// cells containing lattice coordinate i along one direction
+int cells_of(int i, int p, int N, int* c, int* loc) {
+  int a = i / p, r = i - a * p, m = 0;
+  if (r == 0) {
+    if (a - 1 >= 0) { c[m] = a - 1; loc[m] = p; ++m; }
+    if (a < N) { c[m] = a; loc[m] = 0; ++m; }
+  } else {
+    c[m] = a; loc[m] = r; ++m;
+  }
+  return m;
+}
+
+void build_level(const SetupParams& prm, const RefTables& R, int N, HostLevel& L) {
+  const int d = prm.dim, p = prm.degree, NB = R.NB;
+  L.d = d;
+  L.p = p;
+  L.N = N;
+  L.n = p * N + 1;
+  L.lo = prm.lo;
+  L.h = (prm.hi - prm.lo) / N;
+  const double h = L.h;
+  const int n = L.n;
+  const int64_t ncell = (int64_t)ipow(N, d), nnode = (int64_t)ipow(n, d);
+  L.cflag.assign(ncell, 0);
+  L.cut_id.assign(ncell, -1);
+  // classification (Sec. 2.1: active = meets Omega, cut = meets Gamma)
+#pragma omp parallel for schedule(static)
+  for (int64_t c = 0; c < ncell; ++c) {
+    double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    int64_t t = c;
+    for (int k = 0; k < d; ++k) {
+      int ck = (int)(t % N);
+      t /= N;
+      lo[k] = prm.lo + h * ck;
+      hi[k] = prm.lo + h * (ck + 1);
+    }
+    double mn, mx;
+    prm.ls.box_minmax(lo, hi, mn, mx);
+    uint8_t f = 0;
+    if (mn < 0.0) f |= kFlagActive;
+    if (mn < 0.0 && mx > 0.0) f |= kFlagCut;
+    L.cflag[c] = f;
+  }
+  std::vector<int64_t> cut_cells;
+  for (int64_t c = 0; c < ncell; ++c) {
+    if (L.cflag[c] & kFlagActive) L.n_active++;
+    if (L.cflag[c] & kFlagCut) {
+      L.cut_id[c] = (int)cut_cells.size();
+      cut_cells.push_back(c);
+    }
+  }
+  L.n_cut = (int64_t)cut_cells.size();
+  L.cutmat.assign((size_t)L.n_cut * NB * NB, 0.0);
+  CutQuadrature Q(prm.ls, prm.quad_q);
+#pragma omp parallel for schedule(dynamic, 8)
+  for (int64_t i = 0; i < L.n_cut; ++i) {
+    int64_t c = cut_cells[i], t = c;
+    double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    for (int k = 0; k < d; ++k) {
+      lo[k] = prm.lo + h * (int)(t % N);
+      t /= N;
+    }
+    for (int k = 0; k < d; ++k) hi[k] = lo[k] + h;
+    CutRule rule = Q.cell(lo, hi);
+    cut_cell_matrix(R, rule, lo, h, prm.gamma_D, &L.cutmat[(size_t)i * NB * NB]);
+  }
+  // uncut stiffness, Kronecker form of 1D reference matrices
+  L.Kref.assign(NB * NB, 0.0);
+  for (int i = 0; i < NB; ++i)
+    for (int j = 0; j < NB; ++j) {
+      int a[3], b[3];
+      R.split(i, a);
+      R.split(j, b);
+      double s = 0.0;
+      for (int k = 0; k < d; ++k) {
+        double t = 1.0;
+        for (int kk = 0; kk < d; ++kk)
+          t *= (kk == k ? R.K1 : R.M1)[a[kk] * (p + 1) + b[kk]];
+        s += t;
+      }
+      L.Kref[i * NB + j] = s * std::pow(h, d - 2);
+    }
+  // ghost-face tables
+  for (int m = 1; m <= p; ++m) {
+    double hm = std::pow(h, m), fact = 1.0;
+    for (int j = 2; j <= m; ++j) fact *= j;
+    for (int i = 0; i <= 2 * p; ++i) {
+      double v = 0.0;
+      if (i <= p) v += R.b.eval(i, 1.0, m) / hm;
+      if (i >= p) v -= R.b.eval(i - p, 0.0, m) / hm;
+      L.dvec[m - 1][i] = v;
+    }
+    L.coef[m - 1] = prm.gamma_ghost[m - 1] * std::pow(h, 2 * m - 1) / (fact * fact) * std::pow(h, d - 1);
+  }
+  for (int a = 0; a <= p; ++a)
+    for (int b = 0; b <= p; ++b) L.Mhat[a][b] = R.M1[a * (p + 1) + b];
+  // nodes
+  L.nact.assign(nnode, 0);
+  for (int64_t c = 0; c < ncell; ++c) {
+    if (!(L.cflag[c] & kFlagActive)) continue;
+    int ci[3] = {0, 0, 0};
+    int64_t t = c;
+    for (int k = 0; k < d; ++k) {
+      ci[k] = (int)(t % N);
+      t /= N;
+    }
+    for (int j = 0; j < NB; ++j) {
+      int a[3] = {0, 0, 0};
+      R.split(j, a);
+      int64_t node = 0, st = 1;
+      for (int k = 0; k < d; ++k) {
+        node += (int64_t)(p * ci[k] + a[k]) * st;
+        st *= n;
+      }
+      L.nact[node] = 1;
+    }
+  }
+  for (int k = 0; k < 3; ++k) {
+    L.bb_lo[k] = (k < d) ? n : 0;
+    L.bb_hi[k] = (k < d) ? -1 : 0;
+  }
+  for (int64_t i = 0; i < nnode; ++i) {
+    if (!L.nact[i]) continue;
+    L.dofs.push_back(i);
+    int64_t t = i;
+    for (int k = 0; k < d; ++k) {
+      int ik = (int)(t % n);
+      t /= n;
+      L.bb_lo[k] = std::min(L.bb_lo[k], ik);
+      L.bb_hi[k] = std::max(L.bb_hi[k], ik);
+    }
+  }
+  auto cflag_at = [&](const int* c) -> uint8_t {
+    int64_t f = 0, st = 1;
+    for (int k = 0; k < d; ++k) {
+      if (c[k] < 0 || c[k] >= N) return 0;
+      f += (int64_t)c[k] * st;
+      st *= N;
+    }
+    return L.cflag[f];
+  };
+  // ghost faces count
+  for (int64_t c = 0; c < ncell; ++c) {
+    int ci[3] = {0, 0, 0};
+    int64_t t = c;
+    for (int k = 0; k < d; ++k) {
+      ci[k] = (int)(t % N);
+      t /= N;
+    }
+    for (int k = 0; k < d; ++k) {
+      int cj[3] = {ci[0], ci[1], ci[2]};
+      cj[k] += 1;
+      uint8_t f1 = L.cflag[c], f2 = cflag_at(cj);
+      if ((f1 & kFlagActive) && (f2 & kFlagActive) && ((f1 | f2) & kFlagCut)) L.n_ghost++;
+    }
+  }
+  // "plain" cell: active, uncut, no cut face-neighbour (no ghost face)
+  auto plain = [&](const int* c) -> bool {
+    uint8_t f = cflag_at(c);
+    if (!(f & kFlagActive) || (f & kFlagCut)) return false;
+    for (int k = 0; k < d; ++k)
+      for (int s = -1; s <= 1; s += 2) {
+        int cj[3] = {c[0], c[1], c[2]};
+        cj[k] += s;
+        if (cflag_at(cj) & kFlagCut) return false;
+      }
+    return true;
+  };
+  // apply: bulk positions and boundary nodes
+  {
+    const int np = N + 1;
+    const int64_t npos = (int64_t)ipow(np, d);
+    std::vector<uint8_t> bulk(npos, 0);
+    for (int64_t q = 0; q < npos; ++q) {
+      int a[3] = {0, 0, 0};
+      int64_t t = q;
+      bool ok = true;
+      for (int k = 0; k < d; ++k) {
+        a[k] = (int)(t % np);
+        t /= np;
+        if (a[k] < 1 || a[k] > N - 1) ok = false;
+      }
+      if (!ok) continue;
+      for (int s = 0; s < (1 << d) && ok; ++s) {
+        int c[3] = {0, 0, 0};
+        for (int k = 0; k < d; ++k) c[k] = a[k] - ((s >> k) & 1);
+        if (!plain(c)) ok = false;
+      }
+      if (ok) {
+        bulk[q] = 1;
+        L.bulk_pos.push_back((int)q);
+      }
+    }
+    for (int64_t i : L.dofs) {
+      int64_t t = i, q = 0, st = 1;
+      for (int k = 0; k < d; ++k) {
+        int ik = (int)(t % n);
+        t /= n;
+        q += (int64_t)(ik / p) * st;
+        st *= np;
+      }
+      if (!bulk[q]) L.bnd_node.push_back((int)i);
+    }
+  }
+  // one-dimensional two-cell patch matrices and fast diagonalisation
+  {
+    const int C = 2 * p + 1, M = 2 * p - 1;
+    std::vector<double> Mb(C * C, 0.0), Kb(C * C, 0.0);
+    for (int s = 0; s < 2; ++s)
+      for (int a = 0; a <= p; ++a)
+        for (int b = 0; b <= p; ++b) {
+          Mb[(s * p + a) * C + s * p + b] += R.M1[a * (p + 1) + b] * h;
+          Kb[(s * p + a) * C + s * p + b] += R.K1[a * (p + 1) + b] / h;
+        }
+    L.Mr.assign(M * C, 0.0);
+    L.Kr.assign(M * C, 0.0);
+    for (int i = 0; i < M; ++i)
+      for (int j = 0; j < C; ++j) {
+        L.Mr[i * C + j] = Mb[(i + 1) * C + j];
+        L.Kr[i * C + j] = Kb[(i + 1) * C + j];
+      }
+    // K_I s = lam M_I s with S^T M_I S = I: M_I = G G^T, Jacobi on G^-1 K_I G^-T
+    std::vector<double> MI(M * M), KI(M * M), G(M * M, 0.0), Gi(M * M, 0.0);
+    for (int i = 0; i < M; ++i)
+      for (int j = 0; j < M; ++j) {
+        MI[i * M + j] = L.Mr[i * C + j + 1];
+        KI[i * M + j] = L.Kr[i * C + j + 1];
+      }
+    for (int j = 0; j < M; ++j) {
+      double s = MI[j * M + j];
+      for (int k = 0; k < j; ++k) s -= G[j * M + k] * G[j * M + k];
+      G[j * M + j] = std::sqrt(s);
+      for (int i = j + 1; i < M; ++i) {
+        double t = MI[i * M + j];
+        for (int k = 0; k < j; ++k) t -= G[i * M + k] * G[j * M + k];
+        G[i * M + j] = t / G[j * M + j];
+      }
+    }
+    for (int c = 0; c < M; ++c)
+      for (int i = c; i < M; ++i) {
+        double t = (i == c) ? 1.0 : 0.0;
+        for (int k = c; k < i; ++k) t -= G[i * M + k] * Gi[k * M + c];
+        Gi[i * M + c] = t / G[i * M + i];
+      }
+    std::vector<double> Cm(M * M, 0.0), Qv, lam;
+    for (int i = 0; i < M; ++i)
+      for (int j = 0; j < M; ++j) {
+        double t = 0.0;
+        for (int a = 0; a < M; ++a)
+          for (int b = 0; b < M; ++b) t += Gi[i * M + a] * KI[a * M + b] * Gi[j * M + b];
+        Cm[i * M + j] = t;
+      }
+    jacobi_eigen(M, Cm, Qv, lam);
+    L.S.assign(M * M, 0.0);
+    for (int i = 0; i < M; ++i)
+      for (int j = 0; j < M; ++j) {
+        double t = 0.0;
+        for (int a = 0; a < M; ++a) t += Gi[a * M + i] * Qv[a * M + j];  // G^-T Q
+        L.S[i * M + j] = t;
+      }
+    L.lam = lam;
+  }
+  // patches
+  {
+    const int np = N + 1, C = 2 * p + 1, ncol = 1 << d;
+    const int NCL = ipow(C, d);
+    const int64_t nvert = (int64_t)ipow(np, d);
+    std::vector<std::vector<int>> cart(ncol), cutv(ncol);
+    for (int64_t q = 0; q < nvert; ++q) {
+      int v[3] = {0, 0, 0};
+      int64_t t = q;
+      for (int k = 0; k < d; ++k) {
+        v[k] = (int)(t % np);
+        t /= np;
+      }
+      bool any = false, cartesian = true;
+      for (int s = 0; s < (1 << d); ++s) {
+        int c[3] = {0, 0, 0};
+        for (int k = 0; k < d; ++k) c[k] = v[k] - 1 + ((s >> k) & 1);
+        if (cflag_at(c) & kFlagActive) any = true;
+        if (!plain(c)) cartesian = false;
+      }
+      if (!any) continue;
+      int col = 0;
+      for (int k = 0; k < d; ++k) col |= (v[k] & 1) << k;
+      (cartesian ? cart : cutv)[col].push_back((int)q);
+    }
+    L.cart_start.assign(ncol + 1, 0);
+    L.cut_start.assign(ncol + 1, 0);
+    for (int c = 0; c < ncol; ++c) {
+      L.cart_vert.insert(L.cart_vert.end(), cart[c].begin(), cart[c].end());
+      L.cut_vert.insert(L.cut_vert.end(), cutv[c].begin(), cutv[c].end());
+      L.cart_start[c + 1] = (int)L.cart_vert.size();
+      L.cut_start[c + 1] = (int)L.cut_vert.size();
+    }
+    const int64_t ncp = (int64_t)L.cut_vert.size();
+    // members: closure nodes all of whose active cells are patch cells
+    std::vector<std::vector<uint16_t>> mem(ncp);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t j = 0; j < ncp; ++j) {
+      int v[3] = {0, 0, 0};
+      int64_t t = L.cut_vert[j];
+      for (int k = 0; k < d; ++k) {
+        v[k] = (int)(t % np);
+        t /= np;
+      }
+      for (int o = 0; o < NCL; ++o) {
+        int oc[3] = {0, 0, 0}, li[3] = {0, 0, 0}, u = o;
+        bool valid = true;
+        for (int k = 0; k < d; ++k) {
+          oc[k] = u % C;
+          u /= C;
+          li[k] = p * (v[k] - 1) + oc[k];
+          if (li[k] < 0 || li[k] >= n) valid = false;
+        }
+        if (!valid) continue;
+        int cc[3][2], lc[3][2], nc[3] = {1, 1, 1};
+        for (int k = 0; k < d; ++k) nc[k] = cells_of(li[k], p, N, cc[k], lc[k]);
+        bool inside = false, outside = false;
+        int tot = nc[0] * nc[1] * nc[2];
+        for (int s = 0; s < tot; ++s) {
+          int c[3] = {0, 0, 0}, r = s;
+          bool in_patch = true;
+          for (int k = 0; k < d; ++k) {
+            c[k] = cc[k][r % nc[k]];
+            r /= nc[k];
+            if (c[k] != v[k] - 1 && c[k] != v[k]) in_patch = false;
+          }
+          if (cflag_at(c) & kFlagActive) (in_patch ? inside : outside) = true;
+        }
+        if (inside && !outside) mem[j].push_back((uint16_t)o);
+      }
+    }
+    L.cut_n.resize(ncp);
+    L.cut_moff.resize(ncp);
+    L.cut_ioff.resize(ncp);
+    int64_t moff = 0, ioff = 0;
+    for (int64_t j = 0; j < ncp; ++j) {
+      int m = (int)mem[j].size();
+      L.cut_n[j] = m;
+      L.cut_moff[j] = (int)moff;
+      L.cut_ioff[j] = ioff;
+      moff += m;
+      ioff += (int64_t)m * m;
+      L.members.insert(L.members.end(), mem[j].begin(), mem[j].end());
+    }
+    L.inv.assign(ioff, 0.0);
+    // A_j = A[I_j, I_j] from cell and ghost-face pieces, then inverted
+    std::vector<int> err(ncp, 0);
+    std::string first_err;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t j = 0; j < ncp; ++j) {
+      int v[3] = {0, 0, 0};
+      int64_t t = L.cut_vert[j];
+      for (int k = 0; k < d; ++k) {
+        v[k] = (int)(t % np);
+        t /= np;
+      }
+      const int m = L.cut_n[j];
+      std::vector<int> pos(NCL, -1);
+      for (int a = 0; a < m; ++a) pos[mem[j][a]] = a;
+      double* A = &L.inv[L.cut_ioff[j]];
+      auto closure_of = [&](const int* lat) -> int {  // lattice coords -> member or -1
+        int o = 0, st = 1;
+        for (int k = 0; k < d; ++k) {
+          int ok = lat[k] - p * (v[k] - 1);
+          if (ok < 0 || ok >= C) return -1;
+          o += ok * st;
+          st *= C;
+        }
+        return pos[o];
+      };
+      // cells of the patch
+      for (int s = 0; s < (1 << d); ++s) {
+        int c[3] = {0, 0, 0};
+        for (int k = 0; k < d; ++k) c[k] = v[k] - 1 + ((s >> k) & 1);
+        uint8_t f = cflag_at(c);
+        if (!(f & kFlagActive)) continue;
+        int64_t cf = 0, st = 1;
+        for (int k = 0; k < d; ++k) {
+          cf += (int64_t)c[k] * st;
+          st *= N;
+        }
+        const double* K = (f & kFlagCut) ? &L.cutmat[(size_t)L.cut_id[cf] * NB * NB] : L.Kref.data();
+        int mi[64];
+        for (int jl = 0; jl < NB; ++jl) {
+          int a[3] = {0, 0, 0}, lat[3] = {0, 0, 0};
+          R.split(jl, a);
+          for (int k = 0; k < d; ++k) lat[k] = p * c[k] + a[k];
+          mi[jl] = closure_of(lat);
+        }
+        for (int a = 0; a < NB; ++a) {
+          if (mi[a] < 0) continue;
+          for (int b = 0; b < NB; ++b)
+            if (mi[b] >= 0) A[(size_t)mi[a] * m + mi[b]] += K[a * NB + b];
+        }
+      }
+      // ghost faces touching a patch cell: lower cell Lc, upper Lc + e_k
+      for (int k = 0; k < d; ++k) {
+        int rng_lo[3], rng_hi[3];
+        for (int kk = 0; kk < d; ++kk) {
+          rng_lo[kk] = v[kk] - 1;
+          rng_hi[kk] = v[kk];
+        }
+        rng_lo[k] = v[k] - 2;
+        for (int c2 = (d > 2 ? rng_lo[2] : 0); c2 <= (d > 2 ? rng_hi[2] : 0); ++c2)
+          for (int c1 = rng_lo[1]; c1 <= rng_hi[1]; ++c1)
+            for (int c0 = rng_lo[0]; c0 <= rng_hi[0]; ++c0) {
+              int lc[3] = {c0, c1, c2}, uc[3] = {c0, c1, c2};
+              uc[k] += 1;
+              uint8_t f1 = cflag_at(lc), f2 = cflag_at(uc);
+              if (!((f1 & kFlagActive) && (f2 & kFlagActive) && ((f1 | f2) & kFlagCut))) continue;
+              // block nodes: i in [0, 2p] along k, t in [0, p] tangential
+              const int tn = ipow(p + 1, d - 1);
+              const int nbk = (2 * p + 1) * tn;
+              std::vector<int> mi(nbk);
+              std::vector<int> ii(nbk), tt(nbk * 2);
+              for (int e = 0; e < nbk; ++e) {
+                int i = e % (2 * p + 1), u = e / (2 * p + 1);
+                int lat[3] = {0, 0, 0}, q = 0;
+                for (int kk = 0; kk < d; ++kk) {
+                  if (kk == k) {
+                    lat[kk] = p * lc[kk] + i;
+                  } else {
+                    int tv = u % (p + 1);
+                    u /= p + 1;
+                    lat[kk] = p * lc[kk] + tv;
+                    tt[e * 2 + q++] = tv;
+                  }
+                }
+                ii[e] = i;
+                mi[e] = closure_of(lat);
+              }
+              for (int e1 = 0; e1 < nbk; ++e1) {
+                if (mi[e1] < 0) continue;
+                for (int e2 = 0; e2 < nbk; ++e2) {
+                  if (mi[e2] < 0) continue;
+                  double tm = 1.0;
+                  for (int q = 0; q < d - 1; ++q) tm *= L.Mhat[tt[e1 * 2 + q]][tt[e2 * 2 + q]];
+                  double s = 0.0;
+                  for (int mm = 0; mm < p; ++mm) s += L.coef[mm] * L.dvec[mm][ii[e1]] * L.dvec[mm][ii[e2]];
+                  A[(size_t)mi[e1] * m + mi[e2]] += s * tm;
+                }
+              }
+            }
+      }
+      try {
+        spd_inverse(m, A);
+      } catch (const std::exception& e) {
+        err[j] = 1;
+#pragma omp critical
+        if (first_err.empty())
+          first_err = "cut patch at vertex (" + std::to_string(v[0]) + "," + std::to_string(v[1]) + "," +
+                      std::to_string(v[2]) + ") with " + std::to_string(m) + " DoFs on level N=" +
+                      std::to_string(N) + ": " + e.what();
+      }
+    }
+    for (int64_t j = 0; j < ncp; ++j)
+      if (err[j]) throw std::runtime_error(first_err);
+  }
+}
+
+// 1D transfer tables between a coarse level (Nc cells) and its refinement
+void build_transfer(const RefTables& R, int Nc, HostLevel& F) {
+  const int p = R.p, Nf = 2 * Nc, nf = p * Nf + 1, nc = p * Nc + 1;
+  F.pro_col.assign((size_t)nf * (p + 1), 0);
+  F.pro_w.assign((size_t)nf * (p + 1), 0.0);
+  std::vector<std::vector<std::pair<int, double>>> cols(nc);
+  for (int I = 0; I < nf; ++I) {
+    int cf = std::min(I / p, Nf - 1), af = I - p * cf, cc = cf / 2;
+    double xi = ((cf % 2) + R.b.nodes[af]) * 0.5;
+    for (int a = 0; a <= p; ++a) {
+      double w = R.b.eval(a, xi);
+      F.pro_col[(size_t)I * (p + 1) + a] = p * cc + a;
+      F.pro_w[(size_t)I * (p + 1) + a] = w;
+      if (w != 0.0) cols[p * cc + a].push_back({I, w});
+    }
+  }
+  const int W = 4 * p + 1;
+  F.res_col.assign((size_t)nc * W, 0);
+  F.res_w.assign((size_t)nc * W, 0.0);
+  for (int J = 0; J < nc; ++J) {
+    if ((int)cols[J].size() > W) throw std::runtime_error("transfer stencil wider than expected");
+    for (size_t e = 0; e < cols[J].size(); ++e) {
+      F.res_col[(size_t)J * W + e] = cols[J][e].first;
+      F.res_w[(size_t)J * W + e] = cols[J][e].second;
+    }
+    for (size_t e = cols[J].size(); e < (size_t)W; ++e) F.res_col[(size_t)J * W + e] = cols[J].empty() ? 0 : cols[J][0].first;
+  }
+}
+
+// dense A_0 over the coarsest DoFs, explicit inverse
+void build_coarse(const RefTables& R, HostLevel& L) {
+  const int d = L.d, p = L.p, N = L.N, n = L.n, NB = R.NB;
+  const int64_t nd = (int64_t)L.dofs.size();
+  std::vector<int64_t> map((size_t)ipow(n, d), -1);
+  for (int64_t i = 0; i < nd; ++i) map[L.dofs[i]] = i;
+  std::vector<double>& A = L.coarse_inv;
+  A.assign((size_t)nd * nd, 0.0);
+  auto node_of = [&](const int* lat) -> int64_t {
+    int64_t f = 0, st = 1;
+    for (int k = 0; k < d; ++k) {
+      f += (int64_t)lat[k] * st;
+      st *= n;
+    }
+    return map[f];
+  };
+  auto cflag_at = [&](const int* c) -> uint8_t {
+    int64_t f = 0, st = 1;
+    for (int k = 0; k < d; ++k) {
+      if (c[k] < 0 || c[k] >= N) return 0;
+      f += (int64_t)c[k] * st;
+      st *= N;
+    }
+    return L.cflag[f];
+  };
+  const int64_t ncell = ipow(N, d);
+  for (int64_t c = 0; c < ncell; ++c) {
+    uint8_t f = L.cflag[c];
+    if (!(f & kFlagActive)) continue;
+    int ci[3] = {0, 0, 0};
+    int64_t t = c;
+    for (int k = 0; k < d; ++k) {
+      ci[k] = (int)(t % N);
+      t /= N;
+    }
+    const double* K = (f & kFlagCut) ? &L.cutmat[(size_t)L.cut_id[c] * NB * NB] : L.Kref.data();
+    std::vector<int64_t> g(NB);
+    for (int j = 0; j < NB; ++j) {
+      int a[3] = {0, 0, 0}, lat[3] = {0, 0, 0};
+      R.split(j, a);
+      for (int k = 0; k < d; ++k) lat[k] = p * ci[k] + a[k];
+      g[j] = node_of(lat);
+    }
+    for (int a = 0; a < NB; ++a)
+      for (int b = 0; b < NB; ++b) A[(size_t)g[a] * nd + g[b]] += K[a * NB + b];
+    for (int k = 0; k < d; ++k) {
+      int uc[3] = {ci[0], ci[1], ci[2]};
+      uc[k] += 1;
+      uint8_t f2 = cflag_at(uc);
+      if (!((f2 & kFlagActive) && ((f | f2) & kFlagCut))) continue;
+      const int tn = ipow(p + 1, d - 1), nbk = (2 * p + 1) * tn;
+      std::vector<int64_t> gi(nbk);
+      std::vector<int> ii(nbk), tt(nbk * 2);
+      for (int e = 0; e < nbk; ++e) {
+        int i = e % (2 * p + 1), u = e / (2 * p + 1), q = 0;
+        int lat[3] = {0, 0, 0};
+        for (int kk = 0; kk < d; ++kk) {
+          if (kk == k) {
+            lat[kk] = p * ci[kk] + i;
+          } else {
+            int tv = u % (p + 1);
+            u /= p + 1;
+            lat[kk] = p * ci[kk] + tv;
+            tt[e * 2 + q++] = tv;
+          }
+        }
+        ii[e] = i;
+        gi[e] = node_of(lat);
+      }
+      for (int e1 = 0; e1 < nbk; ++e1)
+        for (int e2 = 0; e2 < nbk; ++e2) {
+          double tm = 1.0;
+          for (int q = 0; q < d - 1; ++q) tm *= L.Mhat[tt[e1 * 2 + q]][tt[e2 * 2 + q]];
+          double s = 0.0;
+          for (int mm = 0; mm < p; ++mm) s += L.coef[mm] * L.dvec[mm][ii[e1]] * L.dvec[mm][ii[e2]];
+          A[(size_t)gi[e1] * nd + gi[e2]] += s * tm;
+        }
+    }
+  }
+  spd_inverse((int)nd, A.data());
+}
+
+// b_i = (f, phi_i)_Omega + (g, gamma_D/h phi_i - d_n phi_i)_Gamma for
+// u = prod sin(pi x_k), f = d pi^2 u, g = u
+void build_rhs(const SetupParams& prm, const RefTables& R, const HostLevel& L,
+               std::vector<double>& b) {
+  const int d = L.d, p = L.p, N = L.N, n = L.n, NB = R.NB, q = prm.quad_q;
+  const double h = L.h;
+  std::vector<int64_t> map((size_t)ipow(n, d), -1);
+  for (size_t i = 0; i < L.dofs.size(); ++i) map[L.dofs[i]] = (int64_t)i;
+  b.assign(L.dofs.size(), 0.0);
+  auto uex = [&](const double* x) {
+    double u = 1.0;
+    for (int k = 0; k < d; ++k) u *= std::sin(M_PI * x[k]);
+    return u;
+  };
+  GaussRule g = gauss_legendre01(q);
+  const int nq = ipow(q, d);
+  CutQuadrature Q(prm.ls, q);
+  const int64_t ncell = ipow(N, d);
+  std::vector<double> v(NB), gr(NB * d);
+  for (int64_t c = 0; c < ncell; ++c) {
+    uint8_t f = L.cflag[c];
+    if (!(f & kFlagActive)) continue;
+    int ci[3] = {0, 0, 0};
+    double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    int64_t t = c;
+    for (int k = 0; k < d; ++k) {
+      ci[k] = (int)(t % N);
+      t /= N;
+      lo[k] = prm.lo + h * ci[k];
+      hi[k] = lo[k] + h;
+    }
+    std::vector<double> loc(NB, 0.0);
+    if (!(f & kFlagCut)) {
+      for (int iq = 0; iq < nq; ++iq) {
+        double xi[3] = {0, 0, 0}, x[3] = {0, 0, 0}, w = 1.0;
+        int u = iq;
+        for (int k = 0; k < d; ++k) {
+          int a = u % q;
+          u /= q;
+          xi[k] = g.x[a];
+          w *= g.w[a];
+          x[k] = lo[k] + h * xi[k];
+        }
+        R.eval(xi, h, v.data(), gr.data());
+        double fx = d * M_PI * M_PI * uex(x) * w * std::pow(h, d);
+        for (int j = 0; j < NB; ++j) loc[j] += v[j] * fx;
+      }
+    } else {
+      CutRule rule = Q.cell(lo, hi);
+      for (const auto& nd : rule.vol) {
+        double xi[3] = {0, 0, 0};
+        for (int k = 0; k < d; ++k) xi[k] = (nd.x[k] - lo[k]) / h;
+        R.eval(xi, h, v.data(), gr.data());
+        double fx = d * M_PI * M_PI * uex(nd.x) * nd.w;
+        for (int j = 0; j < NB; ++j) loc[j] += v[j] * fx;
+      }
+      for (size_t s = 0; s < rule.surf.size(); ++s) {
+        const auto& nd = rule.surf[s];
+        double xi[3] = {0, 0, 0};
+        for (int k = 0; k < d; ++k) xi[k] = (nd.x[k] - lo[k]) / h;
+        R.eval(xi, h, v.data(), gr.data());
+        double gx = uex(nd.x) * nd.w;
+        for (int j = 0; j < NB; ++j) {
+          double dn = 0.0;
+          for (int k = 0; k < d; ++k) dn += rule.normal[s][k] * gr[j * d + k];
+          loc[j] += gx * (prm.gamma_D / h * v[j] - dn);
+        }
+      }
+    }
+    for (int j = 0; j < NB; ++j) {
+      int a[3] = {0, 0, 0};
+      R.split(j, a);
+      int64_t node = 0, st = 1;
+      for (int k = 0; k < d; ++k) {
+        node += (int64_t)(p * ci[k] + a[k]) * st;
+        st *= n;
+      }
+      b[map[node]] += loc[j];
+    }
+  }
+}
+
+}  // namespace
+
+void build_hierarchy(const SetupParams& prm, Hierarchy& H) {
+  if (prm.dim != 2 && prm.dim != 3) throw std::invalid_argument("dim must be 2 or 3");
+  if (prm.degree < 1 || prm.degree > 3) throw std::invalid_argument("degree must be 1, 2 or 3");
+  if (prm.n_levels < 1 || prm.n_levels > 12) throw std::invalid_argument("n_levels out of range");
+  if (prm.n_cells % (1 << (prm.n_levels - 1)) != 0)
+    throw std::invalid_argument("n_cells must be divisible by 2^(n_levels-1)");
+  if (prm.n_cells >> (prm.n_levels - 1) < 1) throw std::invalid_argument("coarsest level empty");
+  if (!(prm.hi > prm.lo)) throw std::invalid_argument("empty box");
+  H.prm = prm;
+  H.levels.assign(prm.n_levels, HostLevel());
+  RefTables R(prm.degree, prm.dim);
+  for (int l = 0; l < prm.n_levels; ++l) {
+    int Nl = prm.n_cells >> (prm.n_levels - 1 - l);
+    build_level(prm, R, Nl, H.levels[l]);
+    if (H.levels[l].dofs.empty()) throw std::invalid_argument("level without active cells");
+    if (l > 0) {
+      build_transfer(R, H.levels[l - 1].N, H.levels[l]);
+      // nesting Omega_l within Omega_{l-1} (Sec. 2.2): every active fine cell has an active parent
+      const HostLevel& F = H.levels[l];
+      const HostLevel& Cc = H.levels[l - 1];
+      const int64_t ncell = ipow(F.N, F.d);
+      for (int64_t c = 0; c < ncell; ++c) {
+        if (!(F.cflag[c] & kFlagActive)) continue;
+        int64_t t = c, pc = 0, st = 1;
+        for (int k = 0; k < F.d; ++k) {
+          pc += (t % F.N) / 2 * st;
+          t /= F.N;
+          st *= Cc.N;
+        }
+        if (!(Cc.cflag[pc] & kFlagActive))
+          throw std::invalid_argument("active domains are not nested across levels");
+      }
+    }
+  }
+  build_coarse(R, H.levels[0]);
+  build_rhs(prm, R, H.levels.back(), H.rhs);
+}
+
+}  // namespace cutmg

@@ -1,0 +1,77 @@
+// Host-side construction of the multigrid hierarchy (setup phase, FP64).
+// Everything the device kernels read is produced here once and uploaded.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "geometry.hpp"
+
+namespace cutmg {
+
+constexpr uint8_t kFlagActive = 1;
+constexpr uint8_t kFlagCut = 2;
+
+struct SetupParams {
+  int dim = 3, degree = 2, n_cells = 16, n_levels = 2;
+  double lo = -1.0, hi = 1.0;
+  double gamma_D = 80.0;
+  double gamma_ghost[4] = {0.1, 0.1, 0.1, 0.1};
+  int n_c = 2;
+  int quad_q = 4;
+  LevelSet ls;
+};
+
+// One level of the hierarchy in lattice ("box") layout: every vector lives on
+// the full (pN+1)^d node lattice; inactive nodes stay zero.
+struct HostLevel {
+  int d = 3, p = 2, N = 0, n = 0;  // cells and nodes per direction
+  double h = 0.0, lo = -1.0;
+  // cells
+  std::vector<uint8_t> cflag;   // N^d: kFlagActive | kFlagCut
+  std::vector<int> cut_id;      // N^d: row block in cutmat or -1
+  std::vector<double> cutmat;   // [n_cut][NB][NB] volume + Nitsche terms
+  int64_t n_cut = 0, n_active = 0, n_ghost = 0;
+  // nodes
+  std::vector<uint8_t> nact;    // n^d: node belongs to an active cell
+  std::vector<int64_t> dofs;    // lattice index of each DoF (ascending)
+  int bb_lo[3] = {0, 0, 0}, bb_hi[3] = {0, 0, 0};  // inclusive node bbox of the DoFs
+  // matrix-free apply: owner positions whose 2^d cells are plain interior
+  // cells, and the remaining active nodes
+  std::vector<int> bulk_pos;    // packed a_0 + (N+1)(a_1 + (N+1) a_2)
+  std::vector<int> bnd_node;    // lattice index
+  // patches (sorted by colour; start offsets per colour, 2^d + 1 entries)
+  std::vector<int> cart_vert;   // packed vertex v_0 + (N+1)(v_1 + (N+1) v_2)
+  std::vector<int> cart_start;
+  std::vector<int> cut_vert, cut_n, cut_moff;
+  std::vector<int64_t> cut_ioff;
+  std::vector<int> cut_start;
+  std::vector<uint16_t> members;  // closure-local node index per cut-patch DoF
+  std::vector<double> inv;        // explicit FP64 inverses A_j^{-1}, row-major
+  // reference tables
+  std::vector<double> Kref;       // NB x NB stiffness of an uncut cell
+  std::vector<double> Mr, Kr;     // M x C rows of the two-cell 1D mass / stiffness
+  std::vector<double> S, lam;     // fast-diagonalisation eigenvectors / values (M)
+  double dvec[3][7] = {};         // ghost normal-derivative jump weights
+  double coef[3] = {};            // gamma_m h^(2m-1)/(m!)^2 * h^(d-1)
+  double Mhat[4][4] = {};         // reference 1D mass on [0, 1]
+  // transfer from the next coarser level (l >= 1)
+  std::vector<int> pro_col;       // n x (p+1): coarse 1D column per fine 1D index
+  std::vector<double> pro_w;
+  std::vector<int> res_col;       // n_coarse x (4p+1): fine columns per coarse index
+  std::vector<double> res_w;
+  // coarsest level
+  std::vector<double> coarse_inv; // ndof x ndof explicit inverse (row-major)
+};
+
+struct Hierarchy {
+  SetupParams prm;
+  std::vector<HostLevel> levels;
+  std::vector<double> rhs;  // finest-level manufactured right-hand side (per DoF)
+};
+
+// Builds the hierarchy.  Throws std::runtime_error with a message on error.
+void build_hierarchy(const SetupParams& prm, Hierarchy& H);
+
+}  // namespace cutmg

@@ -1,0 +1,91 @@
+"""The library's host setup (classification, DoF numbering, cut-cell and
+uncut element matrices, right-hand side, patch sets, cut-patch inverses)
+against the oracle, on CPU through cf_setup_host.  No device is touched."""
+
+import numpy as np
+import pytest
+
+from oracle import Hierarchy, Sphere
+
+cm = pytest.importorskip("paper_2508_11608_gb300")
+
+CASES = {
+    "disk_q2": dict(dim=2, N=32, L=3, p=2, c=[0.031, 0.017], r=0.7),
+    "disk_q3": dict(dim=2, N=16, L=2, p=3, c=[0.031, 0.017], r=0.7),
+    "ball_q2": dict(dim=3, N=8, L=2, p=2, c=[0.05, 0.03, 0.02], r=0.7),
+    "ball_q1": dict(dim=3, N=16, L=3, p=1, c=[0.05, 0.03, 0.02], r=0.7),
+}
+
+
+@pytest.fixture(scope="module", params=list(CASES))
+def pair(request):
+    k = CASES[request.param]
+    try:
+        pb = cm.Problem(k["dim"], k["N"], k["L"], k["p"], center=k["c"], radius=k["r"], host_only=True)
+    except ImportError as e:
+        pytest.skip(str(e))
+    H = Hierarchy(Sphere(k["c"], k["r"]), k["dim"], k["N"], k["p"], k["L"])
+    return pb, H, k
+
+
+def test_dof_numbering_matches(pair):
+    pb, H, k = pair
+    for l in range(k["L"]):
+        assert np.array_equal(pb.dof_lattice(l), H.levels[l].lev.dof_nodes)
+        X = pb.dof_coords(l)
+        Xo = H.levels[l].lev.node_coords(H.levels[l].lev.dof_nodes)
+        assert np.abs(X - Xo).max() < 1e-14
+
+
+def test_cell_matrices_match(pair):
+    pb, H, k = pair
+    for l in range(k["L"]):
+        parts = H.levels[l].parts
+        lev = H.levels[l].lev
+        for c, K in parts["cut"].items():
+            Kp = pb.host_cell_matrix(l, c)
+            assert np.abs(Kp - K).max() <= 1e-12 * np.abs(K).max()
+        unc = np.nonzero(lev.active & ~lev.cut)[0]
+        if unc.size:
+            Kp = pb.host_cell_matrix(l, int(unc[0]))
+            assert np.abs(Kp - parts["Kref"]).max() <= 1e-13 * np.abs(parts["Kref"]).max()
+
+
+def test_rhs_matches(pair):
+    pb, H, k = pair
+    b, bo = pb.host_rhs(), H.rhs()
+    assert np.abs(b - bo).max() <= 1e-13 * np.abs(bo).max()
+
+
+def test_patches_and_inverses_match(pair):
+    pb, H, k = pair
+    d = k["dim"]
+    for l in range(1, k["L"]):
+        P = H.levels[l].patches
+        lev = H.levels[l].lev
+        N = lev.N
+        pack = lambda v: int(sum(int(v[i]) * (N + 1) ** i for i in range(d)))
+        inter, cut = pb.host_patches(l)
+        o_inter = sorted(pack(v) for v, c in zip(P.verts, P.cut) if not c)
+        assert sorted(inter) == o_inter
+        o_cut = {pack(v): j for j, (v, c) in enumerate(zip(P.verts, P.cut)) if c}
+        assert sorted(v for v, _, _ in cut) == sorted(o_cut)
+        for v, nodes, inv in cut:
+            j = o_cut[v]
+            onodes = lev.dof_nodes[P.I[j]]
+            assert sorted(nodes.tolist()) == sorted(onodes.tolist())
+            order = np.argsort(onodes)
+            Aj = P.Aj[j][np.ix_(order, order)]
+            po = np.argsort(nodes)
+            invs = inv[np.ix_(po, po)]
+            I = invs @ Aj
+            assert np.abs(I - np.eye(len(nodes))).max() < 1e-9
+
+
+def test_invalid_arguments_are_rejected():
+    with pytest.raises(cm.CutmgError):
+        cm.Problem(3, 16, 3, 3, center=[0, 0, 0], radius=0.5, host_only=True)  # 3D Q3 unsupported
+    with pytest.raises(cm.CutmgError):
+        cm.Problem(2, 12, 4, 2, center=[0, 0], radius=0.5, host_only=True)  # 12 not divisible by 8
+    with pytest.raises(cm.CutmgError):
+        cm.Problem(2, 16, 2, 2, center=[0, 0], radius=-1.0, host_only=True)
