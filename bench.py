@@ -1,0 +1,361 @@
+"""Benchmark: DoF/s of the CutFEM multigrid solve to a 1e-8 relative residual.
+
+One step = one CG solve (V-cycle preconditioner, x_0 = 0, rtol 1e-8) of the
+3D Q2 ball problem on a 64^3 background mesh (435,603 active DoFs, 5
+levels), FP64 plain form, inputs resident in HBM.  The mixed form (FP32
+V-cycle inside FP64 CG) is timed on the same problem and reported under
+"mixed".  Each rank solves its own copy of the problem (weak scaling, no
+collective on the data path).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (test infrastructure, plain numpy /
+scipy) on a bounded sample of the same workload: the same ball on a 32^3
+mesh (4 levels), PCG only (its setup is untimed).
+"""
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "DoF/s solved to 1e-8 rel. residual, mixed vs FP64 form; p50/p99 latency"
+WORKLOAD = "ball3d_q2_n64"
+SAMPLE = "ball3d_q2_n32"
+RTOL = 1e-8
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def _workload_desc(name):
+    from paper_2508_11608_gb300.workloads import CONFIGS
+    c = CONFIGS[name]
+    return (f"{name}: 3D Poisson -Laplace u = f, u = prod sin(pi x_k), on the ball r={c['radius']} "
+            f"at {tuple(c['center'])} cut from [-1,1]^3, {c['n_cells']}^3 cells, Q{c['degree']}, "
+            f"{c['n_levels']} levels, Nitsche 20p^2/h, ghost penalty 0.1, n_c=2, CG + V-cycle "
+            f"(1 pre/1 post MVS step), rtol {RTOL:g}")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+# FP64 FMA throughput of this GB300 pool, measured by
+# paper_2508_11608_gb300/csrc/alu_peak_probe.cu (2 flops per FMA), and the
+# FP32 figure from the same probe.
+FP64_PEAK_TFLOPS = 1.20
+FP32_PEAK_TFLOPS = 74.7
+
+
+def cpu_baseline(steps=1):
+    """Oracle PCG on the bounded sample, single-threaded BLAS, in a subprocess."""
+    code = r"""
+import json, os, sys, time
+sys.path.insert(0, %r)
+from oracle import Hierarchy, Sphere
+from paper_2508_11608_gb300.workloads import CONFIGS
+c = CONFIGS[%r]
+H = Hierarchy(Sphere(c["center"], c["radius"]), c["dim"], c["n_cells"], c["degree"], c["n_levels"])
+b = H.rhs()
+n = b.size
+out = []
+for s in range(%d):
+    t = time.perf_counter()
+    x, it, hist = H.pcg(b, rtol=%r)
+    out.append((time.perf_counter() - t, it))
+print(json.dumps({"n": int(n), "runs": out}))
+""" % (ROOT, SAMPLE, steps, RTOL)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    p = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if p.returncode != 0:
+        return {"error": p.stderr.strip().splitlines()[-1] if p.stderr.strip() else "failed"}
+    r = json.loads(p.stdout.strip().splitlines()[-1])
+    secs = [t for t, _ in r["runs"]]
+    return {"n": r["n"], "secs": secs, "iterations": r["runs"][-1][1]}
+
+
+def run_reference(args):
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return 0
+    res = cpu_baseline(steps=args.warmup + args.steps)
+    if "error" in res:
+        print(json.dumps({"impl": "reference", "unavailable": res["error"]}))
+        return 0
+    secs = res["secs"][args.warmup:]
+    tot = sum(secs)
+    value = res["n"] * len(secs) / tot
+    sample = (f"oracle PCG (numpy/scipy, 1 thread) on {SAMPLE} ({res['n']} active DoFs), same ball "
+              f"and method at 32^3 cells instead of 64^3, {res['iterations']} CG iterations; setup untimed")
+    line = {
+        "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(secs), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": _workload_desc(WORKLOAD), "sample": SAMPLE},
+        "impl": "reference",
+        "cpu_baseline": {"value": value, "unit": "DoF/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2508_11608_gb300 as cm
+    from paper_2508_11608_gb300.workloads import problem_kwargs
+
+    rank, world, local = _env_rank()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    pb = cm.Problem(**problem_kwargs(WORKLOAD))
+    n = pb.n_dofs()
+    b = torch.zeros(n, dtype=torch.float64, device=dev)
+    x = torch.zeros_like(b)
+    pb.rhs(b)
+    # L2 is 129 MB: a 512 MB write between timed solves evicts it
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float64, device=dev)
+
+    def timed_solves(prec, steps, warmup, profile_kernel=None):
+        pb.set_precision(prec)
+        for _ in range(warmup):
+            pb.solve(b, x, rtol=RTOL)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        if profile_kernel:
+            pb.profile_start(profile_kernel)
+        l0 = pb.launch_count()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        infos = []
+        t0 = time.perf_counter()
+        for k in range(steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            infos.append(pb.solve(b, x, rtol=RTOL))
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        if dist:
+            dist.barrier()
+        launches = pb.launch_count() - l0
+        prof = pb.profile_read() if profile_kernel else None
+        ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+        return ms, infos, launches, prof, wall
+
+    # FP64 plain form: the headline; the cut-patch solve kernels (the largest
+    # share of the step) are event-timed inside this timed region
+    sampler = ClockSampler(local)
+    sampler.start()
+    ms64, inf64, launches, pr_head, _ = timed_solves(cm.CF_FP64, args.steps, args.warmup,
+                                                     profile_kernel=cm._lib.CF_K_CUT_SOLVE)
+    clocks = sampler.stop()
+    # mixed form
+    ms32, inf32, _, _, _ = timed_solves(cm.CF_MIXED, args.steps, 1)
+
+    # shares of the other kernel families, from short separate passes
+    prof = {cm._lib.CF_K_CUT_SOLVE: pr_head}
+    for kern in (cm._lib.CF_K_INTERIOR, cm._lib.CF_K_APPLY_BULK, cm._lib.CF_K_APPLY_BND):
+        msk, _, _, pr, _ = timed_solves(cm.CF_FP64, 2, 1, profile_kernel=kern)
+        pr["share"] = pr["ms"] / sum(msk)
+        prof[kern] = pr
+    prof[cm._lib.CF_K_CUT_SOLVE]["share"] = pr_head["ms"] / sum(ms64)
+
+    # e2e through the C ABI with host buffers: H2D of b, solve, D2H of x
+    pb.set_precision(cm.CF_FP64)
+    hb = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    hb.copy_(b.cpu())
+    hx = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    db = torch.empty_like(b)
+    e2e_ms = []
+    for k in range(args.steps + 1):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        db.copy_(hb, non_blocking=True)
+        pb.solve(db, x, rtol=RTOL)
+        hx.copy_(x, non_blocking=True)
+        torch.cuda.synchronize()
+        if k > 0:
+            e2e_ms.append(1e3 * (time.perf_counter() - t))
+
+    def agg_max(v):
+        if not dist:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return t.item()
+
+    tot64 = agg_max(sum(ms64))
+    tot32 = agg_max(sum(ms32))
+    tote2e = agg_max(sum(e2e_ms))
+    value = world * n * args.steps / (tot64 * 1e-3)
+    mixed_value = world * n * args.steps / (tot32 * 1e-3)
+    e2e_value = world * n * len(e2e_ms) / (tote2e * 1e-3)
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    peaks = _peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    top = max(prof, key=lambda k: prof[k]["share"])
+    pr = prof[top]
+    names = {1: "k_cut_solve (cut-patch residual + dense local solve)",
+             2: "k_smooth_cart (interior-patch residual + fast diagonalisation)",
+             3: "k_apply_bulk (operator, interior positions)",
+             4: "k_apply_bnd (operator, boundary positions)"}
+    per_launch_ms = pr["ms"] / max(pr["launches"], 1)
+    fl_rate = pr["flops"] / (pr["ms"] * 1e-3) / 1e12 if pr["ms"] > 0 else 0.0
+    by_rate = pr["bytes"] / (pr["ms"] * 1e-3) / 1e9 if pr["ms"] > 0 else 0.0
+    # FP64: the arithmetic bound is 1.2 TFLOP/s; compare time-at-peak of flops and bytes
+    t_alu = pr["flops"] / (FP64_PEAK_TFLOPS * 1e12)
+    t_hbm = pr["bytes"] / (hbm * 1e9)
+    if t_alu >= t_hbm:
+        roof = {"bound": "alu", "achieved": fl_rate, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": fl_rate / FP64_PEAK_TFLOPS}
+    else:
+        roof = {"bound": "hbm", "achieved": by_rate, "peak": hbm, "unit": "GB/s", "frac": by_rate / hbm}
+    roof.update({"kernel": names[top], "traffic": None, "per_launch_ms": per_launch_ms,
+                 "launches_timed": pr["launches"],
+                 "share_of_step": pr["share"],
+                 "shares": {names[k].split(" ")[0]: round(prof[k]["share"], 4) for k in prof},
+                 "flops_per_launch": pr["flops"] / max(pr["launches"], 1),
+                 "bytes_per_launch": pr["bytes"] / max(pr["launches"], 1),
+                 "peak_source": "FP64 FMA probe (paper_2508_11608_gb300/csrc/alu_peak_probe.cu)"
+                 if roof["bound"] == "alu" else "MEASURED_PEAKS.json hbm_gbs"})
+
+    cpu = cpu_baseline(steps=2) if world == 1 else {"error": "rank 0 at N=1 only"}
+    if "error" not in cpu:
+        cpu_line = {"value": cpu["n"] / min(cpu["secs"]), "unit": "DoF/s", "cores": 1, "kind": "oracle",
+                    "sample": f"oracle PCG on {SAMPLE} ({cpu['n']} DoFs, {cpu['iterations']} iterations), "
+                              f"1 thread, best of {len(cpu['secs'])}; setup untimed"}
+    else:
+        cpu_line = None
+
+    lat = sorted(ms64)
+    p50 = float(np.percentile(lat, 50))
+    p99 = float(np.percentile(lat, 99))
+    line = {
+        "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot64 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": _workload_desc(WORKLOAD), "active_dofs": n,
+                   "form": "FP64 plain (CG, V-cycle, smoother, transfer all FP64)",
+                   "l2": "512 MB buffer written between timed solves (flush)",
+                   "iterations": inf64[-1]["iterations"],
+                   "true_rel_residual": inf64[-1]["true_rel_residual"]},
+        "latency_ms": {"p50": p50, "p99": p99},
+        "mixed": {"value": mixed_value, "unit": "DoF/s", "ms_per_step": tot32 / args.steps,
+                  "iterations": inf32[-1]["iterations"],
+                  "true_rel_residual": inf32[-1]["true_rel_residual"],
+                  "latency_ms": {"p50": float(np.percentile(ms32, 50)), "p99": float(np.percentile(ms32, 99))},
+                  "form": "FP32 V-cycle (smoother, transfer, cut-patch inverses) inside FP64 CG"},
+        "e2e": {"value": e2e_value, "unit": "DoF/s", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "cpu_baseline": cpu_line,
+        "clocks": clocks,
+    }
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -155,6 +155,24 @@ cf_status cf_level_prolongate(cf_problem* pb, int level, int precision,
 cf_status cf_coarse_solve(cf_problem* pb, int precision, const double* d_b0,
                           double* d_x0, void* stream);
 
+/* ---- instrumentation ----------------------------------------------------- */
+/* Number of kernel launches this handle has issued (all calls). */
+int64_t cf_launch_count(const cf_problem* pb);
+/* Kernel families for cf_profile_start. */
+typedef enum {
+  CF_K_CUT_SOLVE = 1, /* cut-patch residual + dense local solve */
+  CF_K_INTERIOR = 2,  /* interior-patch residual + fast diagonalisation */
+  CF_K_APPLY_BULK = 3,/* operator, interior positions */
+  CF_K_APPLY_BND = 4  /* operator, positions near the boundary */
+} cf_kernel;
+/* From now on record a CUDA event pair (on the launching stream) around every
+ * launch of one kernel family; cf_profile_read synchronises those events and
+ * returns their summed duration, the launch count and the algorithmic flops
+ * and bytes of those launches (a model computed at setup: see the design
+ * notes), then stops recording.  Adds two event records per launch. */
+cf_status cf_profile_start(cf_problem* pb, int kernel);
+cf_status cf_profile_read(cf_problem* pb, double* ms, int64_t* launches, double* flops, double* bytes);
+
 /* ---- host-only handles (no device work; used to check the setup) ---------
  * cf_setup_host builds the same hierarchy as cf_setup on the host only.  The
  * handle answers the size / map / stats queries above and the calls below;

@@ -143,6 +143,22 @@ class Problem:
     def coarse_solve(self, b0, x0, precision=CF_FP64, stream=None):
         check(self._lib.cf_coarse_solve(self._h, precision, _ptr(b0), _ptr(x0), _stream(stream)))
 
+    # ---- instrumentation --------------------------------------------------------------
+    def launch_count(self):
+        return self._lib.cf_launch_count(self._h)
+
+    def profile_start(self, kernel):
+        check(self._lib.cf_profile_start(self._h, kernel))
+
+    def profile_read(self):
+        ms = ctypes.c_double()
+        n = ctypes.c_int64()
+        fl = ctypes.c_double()
+        by = ctypes.c_double()
+        check(self._lib.cf_profile_read(self._h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(fl),
+                                        ctypes.byref(by)))
+        return {"ms": ms.value, "launches": n.value, "flops": fl.value, "bytes": by.value}
+
     # ---- host-side views of the setup (work on host-only handles too) -------------
     def host_rhs(self):
         out = np.empty(self.n_dofs(), dtype=np.float64)

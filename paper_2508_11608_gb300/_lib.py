@@ -13,6 +13,7 @@ LIB_PATH = os.path.join(_HERE, "libcutmg.so")
 CF_OK, CF_EINVAL, CF_ENOMEM, CF_ECUDA, CF_ENOCONV, CF_ETIMEOUT, CF_EUNSUPPORTED = range(7)
 CF_LS_SPHERE, CF_LS_PLANE = 0, 1
 CF_FP64, CF_MIXED = 0, 1
+CF_K_CUT_SOLVE, CF_K_INTERIOR, CF_K_APPLY_BULK, CF_K_APPLY_BND = 1, 2, 3, 4
 
 EXPORTED = [
     "cf_setup", "cf_destroy", "cf_last_error", "cf_n_levels", "cf_n_dofs", "cf_level_n_dofs",
@@ -20,6 +21,7 @@ EXPORTED = [
     "cf_vcycle", "cf_solve", "cf_level_apply", "cf_level_colour_step", "cf_level_smooth",
     "cf_level_restrict", "cf_level_prolongate", "cf_coarse_solve", "cf_setup_host", "cf_host_rhs",
     "cf_host_cell_matrix", "cf_host_patch_counts", "cf_host_interior_patch", "cf_host_cut_patch",
+    "cf_launch_count", "cf_profile_start", "cf_profile_read",
 ]
 
 
@@ -91,6 +93,10 @@ def load():
     lib.cf_host_patch_counts.argtypes = [P, I, P, P]
     lib.cf_host_interior_patch.argtypes = [P, I, ctypes.c_int64, P]
     lib.cf_host_cut_patch.argtypes = [P, I, ctypes.c_int64, P, P, P, P]
+    lib.cf_launch_count.argtypes = [P]
+    lib.cf_launch_count.restype = ctypes.c_int64
+    lib.cf_profile_start.argtypes = [P, I]
+    lib.cf_profile_read.argtypes = [P, P, P, P, P]
     for name in EXPORTED:
         getattr(lib, name)  # raises AttributeError if the library lacks a symbol
     _lib = lib

@@ -253,6 +253,18 @@ cf_status cf_coarse_solve(cf_problem* pb, int precision, const double* d_b0, dou
 }
 
 
+int64_t cf_launch_count(const cf_problem* pb) { return no_device(pb) ? 0 : pb->eng->launches(); }
+
+cf_status cf_profile_start(cf_problem* pb, int kernel) {
+  if (no_device(pb) || kernel < 1 || kernel > 4) return fail(CF_EINVAL, "bad argument");
+  return guarded([&] { pb->eng->profile_start(kernel); });
+}
+
+cf_status cf_profile_read(cf_problem* pb, double* ms, int64_t* launches, double* flops, double* bytes) {
+  if (no_device(pb) || !ms || !launches || !flops || !bytes) return fail(CF_EINVAL, "bad argument");
+  return guarded([&] { pb->eng->profile_read(ms, launches, flops, bytes); });
+}
+
 cf_status cf_host_rhs(const cf_problem* pb, double* h_b) {
   if (!pb || !h_b) return fail(CF_EINVAL, "null argument");
   std::memcpy(h_b, pb->H.rhs.data(), pb->H.rhs.size() * sizeof(double));

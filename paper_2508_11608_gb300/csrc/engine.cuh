@@ -80,6 +80,10 @@ class Engine final : public EngineBase {
     int nbulk;
     int* bnd;
     int nbnd;
+    int* mnode;
+    int* faces;
+    int nfaces;
+    int* face_id;
     int* cart;
     std::vector<int> cart_start;
     int* cutv;
@@ -88,6 +92,7 @@ class Engine final : public EngineBase {
     int64_t* cutio;
     uint16_t* members;
     std::vector<int> cut_start;
+    std::vector<int> cut_moff_h;
     int64_t nmembers;
     int* pro_col;
     int* res_col;
@@ -105,7 +110,7 @@ class Engine final : public EngineBase {
     T* coarse_inv;
     T *x, *b, *r;          // box vectors
     T *t1, *t2, *t3, *t4;  // transfer intermediates (restriction: t1,t2; prolongation: t3,t4)
-    T* rbuf;               // cut-patch residual rows
+    T* dbuf;               // cut-patch corrections A_j^{-1} r_j
   };
 
  public:
@@ -131,6 +136,30 @@ class Engine final : public EngineBase {
   }
   ~Engine() override {
     if (host_sc_) cudaFreeHost(host_sc_);
+    for (auto& e : prof_.ev) cudaEventDestroy(e);
+  }
+
+  int64_t launches() const override { return launches_; }
+  void profile_start(int kind) override {
+    prof_.kind = kind;
+    prof_.used = 0;
+    prof_.flops = prof_.bytes = 0.0;
+    prof_.n = 0;
+  }
+  void profile_read(double* ms, int64_t* n, double* flops, double* bytes) override {
+    double tot = 0.0;
+    for (int i = 0; i + 1 < prof_.used; i += 2) {
+      CUTMG_CUDA(cudaEventSynchronize(prof_.ev[i + 1]));
+      float t = 0.f;
+      CUTMG_CUDA(cudaEventElapsedTime(&t, prof_.ev[i], prof_.ev[i + 1]));
+      tot += t;
+    }
+    *ms = tot;
+    *n = prof_.n;
+    *flops = prof_.flops;
+    *bytes = prof_.bytes;
+    prof_.kind = 0;
+    prof_.used = 0;
   }
 
   int n_levels() const override { return (int)com_.size(); }
@@ -262,7 +291,7 @@ class Engine final : public EngineBase {
         apply<double>(L, d64_[L], pF_, nullptr, qF_, s);
         dot(F.region, pF_, qF_, sc_ + 1, s);  // pq
         k_cg_update_xr<<<kVecBlocks, 256, 0, s>>>(F.region, sc_, xF_, rF_, pF_, qF_);
-        launch_check("cg update x r");
+        count_launch("cg update x r");
         dot(F.region, rF_, rF_, sc_ + 3, s);  // rr
         ++it;
         rn = std::sqrt(read_scalar(3, s));
@@ -270,9 +299,9 @@ class Engine final : public EngineBase {
         precondition(prec, rF_, zF_, s);
         dot(F.region, rF_, zF_, sc_ + 2, s);  // rz_new
         k_cg_update_p<<<kVecBlocks, 256, 0, s>>>(F.region, sc_, pF_, zF_);
-        launch_check("cg update p");
+        count_launch("cg update p");
         k_copy_scalar<<<1, 1, 0, s>>>(sc_, 0, 2);
-        launch_check("cg scalar");
+        count_launch("cg scalar");
       }
     }
     CUTMG_CUDA(cudaEventRecord(e1, s));
@@ -296,6 +325,35 @@ class Engine final : public EngineBase {
 
   const Hierarchy& H_;
   DevPool pool_;
+  int64_t launches_ = 0;
+  struct Prof {
+    int kind = 0;  // 1 cut-patch solve, 2 interior-patch step, 3 apply (bulk), 4 apply (boundary)
+    std::vector<cudaEvent_t> ev;
+    int used = 0;
+    int64_t n = 0;
+    double flops = 0.0, bytes = 0.0;
+  } prof_;
+
+  void count_launch(const char* what) {
+    launch_check(what);
+    ++launches_;
+  }
+  // event pair around a launch of the profiled family (on the launching stream)
+  void prof_mark(int kind, cudaStream_t s) {
+    if (prof_.kind != kind) return;
+    if (prof_.used == (int)prof_.ev.size()) {
+      cudaEvent_t e;
+      CUTMG_CUDA(cudaEventCreate(&e));
+      prof_.ev.push_back(e);
+    }
+    CUTMG_CUDA(cudaEventRecord(prof_.ev[prof_.used++], s));
+  }
+  void prof_work(int kind, double flops, double bytes) {
+    if (prof_.kind != kind) return;
+    prof_.n += 1;
+    prof_.flops += flops;
+    prof_.bytes += bytes;
+  }
   std::vector<Common> com_;
   std::vector<Typed<double>> d64_;
   std::vector<Typed<float>> d32_;
@@ -315,6 +373,8 @@ class Engine final : public EngineBase {
     D.op.cflag = c.cflag;
     D.op.cut_id = c.cut_id;
     D.op.cutmat = pool_.upload<T>(h.cutmat);
+    D.op.face_id = c.face_id;
+    D.op.G = pool_.alloc<T>((size_t)std::max<int64_t>(1, (int64_t)h.ghost_faces.size()) * P * (DIM == 2 ? P + 1 : (P + 1) * (P + 1)));
     D.op.Kref = pool_.upload<T>(h.Kref);
     for (int m = 0; m < 3; ++m) {
       for (int i = 0; i < 7; ++i) D.op.dvec[m][i] = (T)h.dvec[m][i];
@@ -337,7 +397,7 @@ class Engine final : public EngineBase {
     D.x = pool_.alloc<T>(c.nbox);
     D.b = pool_.alloc<T>(c.nbox);
     D.r = pool_.alloc<T>(c.nbox);
-    D.rbuf = pool_.alloc<T>(c.nmembers);
+    D.dbuf = pool_.alloc<T>(c.nmembers);
     D.t1 = D.t2 = D.t3 = D.t4 = nullptr;
     if (l > 0) {
       const int64_t nf = h.n, nc = H_.levels[l - 1].n;
@@ -368,6 +428,10 @@ class Engine final : public EngineBase {
     c.nbulk = (int)h.bulk_pos.size();
     c.bnd = pool_.upload<int>(h.bnd_node);
     c.nbnd = (int)h.bnd_node.size();
+    c.faces = pool_.upload<int>(h.ghost_faces);
+    c.nfaces = (int)h.ghost_faces.size();
+    c.face_id = pool_.upload<int>(h.face_id);
+    c.mnode = pool_.upload<int>(h.member_node);
     c.cart = pool_.upload<int>(h.cart_vert);
     c.cart_start = h.cart_start;
     c.cutv = pool_.upload<int>(h.cut_vert);
@@ -376,6 +440,7 @@ class Engine final : public EngineBase {
     c.cutio = pool_.upload<int64_t>(h.cut_ioff);
     c.members = pool_.upload<uint16_t>(h.members);
     c.cut_start = h.cut_start;
+    c.cut_moff_h = h.cut_moff;
     c.nmembers = (int64_t)h.members.size();
     c.pro_col = l > 0 ? pool_.upload<int>(h.pro_col) : nullptr;
     c.res_col = l > 0 ? pool_.upload<int>(h.res_col) : nullptr;
@@ -409,13 +474,13 @@ class Engine final : public EngineBase {
     const Common& c = com_[l];
     CUTMG_CUDA(cudaMemsetAsync(box, 0, sizeof(T) * c.nbox, s));
     k_scatter<T, double><<<std::min(blocks_for(c.ndof, 256), 4096), 256, 0, s>>>(c.dofs, c.ndof, in, box);
-    launch_check("scatter");
+    count_launch("scatter");
   }
   template <typename T>
   void from_box(int l, const T* box, double* out, cudaStream_t s) {
     const Common& c = com_[l];
     k_gather<double, T><<<std::min(blocks_for(c.ndof, 256), 4096), 256, 0, s>>>(c.dofs, c.ndof, box, out);
-    launch_check("gather");
+    count_launch("gather");
   }
 
   double read_scalar(int i, cudaStream_t s) {
@@ -426,9 +491,9 @@ class Engine final : public EngineBase {
 
   void dot(const Region& R, const double* a, const double* b, double* out, cudaStream_t s) {
     k_dot_partial<<<kDotBlocks, 256, 0, s>>>(R, a, b, part_);
-    launch_check("dot partial");
+    count_launch("dot partial");
     k_dot_final<<<1, 256, 0, s>>>(part_, kDotBlocks, out);
-    launch_check("dot final");
+    count_launch("dot final");
   }
 
   // y = A x or y = b - A x on level l (box layout, precision T)
@@ -436,13 +501,31 @@ class Engine final : public EngineBase {
   void apply(int l, Typed<T>& D, const T* x, const T* b, T* y, cudaStream_t s) {
     const Common& c = com_[l];
     if (c.nbulk > 0) {
+      prof_mark(3, s);
       k_apply_bulk<DIM, P, T><<<blocks_for(c.nbulk, 128), 128, 0, s>>>(D.op, x, b, y, c.bulk, c.nbulk);
-      launch_check("apply bulk");
+      count_launch("apply bulk");
+      prof_mark(3, s);
+      // per position: 2 NB^2 flops; x read and y written once per owned node (+ b)
+      constexpr int NO = Shape<DIM, P>::NO;
+      prof_work(3, 2.0 * NB * NB * c.nbulk, (double)c.nbulk * (NO * (b ? 3 : 2) * sizeof(T) + 4));
     }
     if (c.nbnd > 0) {
+      prof_mark(4, s);
+      face_moments<T>(l, D, x, s);
       k_apply_bnd<DIM, P, T><<<blocks_for(c.nbnd, 128), 128, 0, s>>>(D.op, x, b, y, c.bnd, c.nbnd);
-      launch_check("apply boundary");
+      count_launch("apply boundary");
+      prof_mark(4, s);
+      prof_work(4, 0.0, 0.0);
     }
+  }
+
+  // jump moments of every ghost face of level l for the vector x
+  template <typename T>
+  void face_moments(int l, Typed<T>& D, const T* x, cudaStream_t s) {
+    const Common& c = com_[l];
+    if (c.nfaces == 0) return;
+    k_face_moments<DIM, P, T><<<blocks_for(c.nfaces, 128), 128, 0, s>>>(D.op, x, c.faces, c.nfaces);
+    count_launch("ghost face moments");
   }
 
   template <typename T>
@@ -451,19 +534,29 @@ class Engine final : public EngineBase {
     if (!cut) {
       const int a0 = c.cart_start[colour], cnt = c.cart_start[colour + 1] - a0;
       if (cnt <= 0) return;
+      prof_mark(2, s);
       k_smooth_cart<DIM, P, T, WARPS><<<blocks_for(cnt, WARPS), 32 * WARPS, 0, s>>>(
           D.fd, c.N, c.n, x, b, c.cart + a0, cnt);
-      launch_check("smooth interior patches");
+      count_launch("smooth interior patches");
+      prof_mark(2, s);
+      const auto& w = H_.levels[l].work_cart[colour];
+      prof_work(2, w[0], w[1] * sizeof(T) + w[2]);
     } else {
       const int a0 = c.cut_start[colour], cnt = c.cut_start[colour + 1] - a0;
       if (cnt <= 0) return;
-      k_cut_resid<DIM, P, T, WARPS><<<blocks_for(cnt, WARPS), 32 * WARPS, 0, s>>>(
-          D.op, x, b, c.cutv + a0, c.cutn + a0, c.cutmo + a0, c.members, D.rbuf, cnt);
-      launch_check("cut patch residual");
-      k_cut_update<DIM, P, T, WARPS><<<blocks_for(cnt, WARPS), 32 * WARPS, 0, s>>>(
-          c.N, c.n, x, c.cutv + a0, c.cutn + a0, c.cutmo + a0, c.cutio + a0, c.members, D.inv,
-          D.rbuf, cnt);
-      launch_check("cut patch update");
+      prof_mark(1, s);
+      face_moments<T>(l, D, x, s);
+      k_cut_solve<DIM, P, T, WARPS><<<blocks_for(cnt, WARPS), 32 * WARPS, 0, s>>>(
+          D.op, x, b, c.cutv + a0, c.cutn + a0, c.cutmo + a0, c.cutio + a0, c.members, c.mnode, D.inv,
+          D.dbuf, cnt);
+      count_launch("cut patch solve");
+      prof_mark(1, s);
+      const auto& w = H_.levels[l].work_cut[colour];
+      prof_work(1, w[0], w[1] * sizeof(T) + w[2]);
+      const int m0 = c.cut_moff_h[a0];
+      const int m1 = (a0 + cnt < (int)c.cut_moff_h.size()) ? c.cut_moff_h[a0 + cnt] : (int)c.nmembers;
+      k_cut_scatter<T><<<blocks_for(m1 - m0, 256), 256, 0, s>>>(x, c.mnode, D.dbuf, m0, m1);
+      count_launch("cut patch scatter");
     }
   }
 
@@ -489,7 +582,7 @@ class Engine final : public EngineBase {
     if (tot <= 0) return;
     k_pass<T, MODE><<<blocks_for(tot, 256), 256, 0, s>>>(in, out, in0, in1, out0, out1, axis, lo[0], lo[1],
                                                           lo[2], ext[0], ext[1], ext[2], col, wt, W, mask);
-    launch_check("transfer pass");
+    count_launch("transfer pass");
   }
 
   // b_{l-1} = P^T r_l, separably (x, y, z passes) over the active boxes
@@ -553,7 +646,7 @@ class Engine final : public EngineBase {
     const Common& c = com_[0];
     const int n0 = (int)c.ndof;
     k_coarse<T><<<blocks_for(n0, 8), 256, 0, s>>>(D.coarse_inv, c.coarse_nodes, n0, b, x);
-    launch_check("coarse solve");
+    count_launch("coarse solve");
   }
 
   // V-cycle with zero initial guess on level l: x = B_l b (Sec. 2.2)
@@ -580,11 +673,11 @@ class Engine final : public EngineBase {
     if (prec == 1) {
       Typed<float>& D = d32_[L];
       k_convert<float, double><<<kVecBlocks, 256, 0, s>>>(F.region, r, D.b);
-      launch_check("convert r");
+      count_launch("convert r");
       vcycle_level<float>(L, d32_, D.b, D.x, s);
       CUTMG_CUDA(cudaMemsetAsync(z, 0, sizeof(double) * F.nbox, s));
       k_convert<double, float><<<kVecBlocks, 256, 0, s>>>(F.region, D.x, z);
-      launch_check("convert z");
+      count_launch("convert z");
     } else {
       vcycle_level<double>(L, d64_, r, z, s);
     }

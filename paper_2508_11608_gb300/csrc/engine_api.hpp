@@ -38,6 +38,10 @@ class EngineBase {
   virtual void vcycle(int prec, const double* r, double* z, cudaStream_t s) = 0;
   virtual int solve(int prec, const double* b, double* x, double rtol, int maxit, double* rel,
                     double* true_rel, float* ms, cudaStream_t s) = 0;
+  // kernel launches issued so far, and event timing of one kernel family
+  virtual int64_t launches() const = 0;
+  virtual void profile_start(int kind) = 0;
+  virtual void profile_read(double* ms, int64_t* n, double* flops, double* bytes) = 0;
 };
 
 std::unique_ptr<EngineBase> make_engine_d2(int degree, const Hierarchy& H);

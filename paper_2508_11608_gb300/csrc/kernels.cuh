@@ -34,21 +34,139 @@ struct OpArgs {
   T dvec[3][7];           // jump weights of the m-th normal derivative across a face
   T coef[3];              // gamma_m h^(2m-1)/(m!)^2 h^(DIM-1)
   T Mhat[4][4];           // 1D reference mass matrix
+  const int* face_id;     // [N^DIM][DIM] index of the ghost face (c, c + e_k), -1 if none
+  T* G;                   // [n_ghost][P][(P+1)^(DIM-1)] face moments of the current x
 };
 
 // ---------------------------------------------------------------------------
-// (A x)_i for one lattice node i (idx = its lattice coordinates): every
-// active cell containing i plus every ghost face whose two cells contain i.
+// Ghost faces.  For the face F between cells L and L + e_k the penalty
+// couples the (2P+1) x (P+1)^(DIM-1) nodes of the two cells:
+//   (G_F x)(i, t) = sum_m dvec_m[i] G_m[t],
+//   G_m[t] = coef_m sum_t' prod_j Mhat[t_j][t'_j] sum_i' dvec_m[i'] x(i', t').
+// k_face_moments evaluates G_m[t] once per ghost face for the current x; the
+// rows then only look them up.
+template <int DIM, int P>
+struct FaceGeo {
+  static constexpr int NT = (DIM == 2) ? P + 1 : (P + 1) * (P + 1);
+};
+
 template <int DIM, int P, typename T>
-__device__ __forceinline__ T row_apply(const OpArgs<T>& A, const T* __restrict__ x,
-                                       const int* idx, const T* __restrict__ sK) {
+__global__ void __launch_bounds__(128) k_face_moments(OpArgs<T> A, const T* __restrict__ x,
+                                                      const int* __restrict__ faces, int nfaces) {
+  constexpr int NT = FaceGeo<DIM, P>::NT;
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= nfaces) return;
+  const int packed = faces[f], k = packed % DIM;
+  int c = packed / DIM, lc[3] = {0, 0, 0};
+#pragma unroll
+  for (int j = 0; j < DIM; ++j) {
+    lc[j] = c % A.N;
+    c /= A.N;
+  }
+  const int n = A.n;
+  const int sk = (k == 0) ? 1 : (k == 1 ? n : n * n);
+  int tdim[2] = {0, 0}, q = 0;
+#pragma unroll
+  for (int j = 0; j < DIM; ++j)
+    if (j != k) tdim[q++] = j;
+  const int s0 = (tdim[0] == 0) ? 1 : (tdim[0] == 1 ? n : n * n);
+  const int s1 = (DIM == 3) ? ((tdim[1] == 0) ? 1 : (tdim[1] == 1 ? n : n * n)) : 0;
+  const int base = P * (lc[0] + n * (lc[1] + (DIM == 3 ? n * lc[2] : 0)));
+  T J[P][NT];
+#pragma unroll
+  for (int tp = 0; tp < NT; ++tp) {
+    const int off = base + (tp % (P + 1)) * s0 + (DIM == 3 ? (tp / (P + 1)) * s1 : 0);
+    T acc[P];
+#pragma unroll
+    for (int m = 0; m < P; ++m) acc[m] = T(0);
+#pragma unroll
+    for (int ip = 0; ip <= 2 * P; ++ip) {
+      const T xv = x[off + ip * sk];
+#pragma unroll
+      for (int m = 0; m < P; ++m) acc[m] += A.dvec[m][ip] * xv;
+    }
+#pragma unroll
+    for (int m = 0; m < P; ++m) J[m][tp] = acc[m];
+  }
+  T* g = A.G + (size_t)f * P * NT;
+#pragma unroll
+  for (int m = 0; m < P; ++m)
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      T acc = T(0);
+#pragma unroll
+      for (int tq = 0; tq < NT; ++tq) {
+        T w = A.Mhat[t % (P + 1)][tq % (P + 1)];
+        if (DIM == 3) w *= A.Mhat[t / (P + 1)][tq / (P + 1)];
+        acc += w * J[m][tq];
+      }
+      g[m * NT + t] = A.coef[m] * acc;
+    }
+}
+
+// sum over the ghost faces whose two cells contain node idx of (G_F x)(node)
+template <int DIM, int P, typename T>
+__device__ __forceinline__ T node_faces(const OpArgs<T>& A, const int* idx) {
+  constexpr int NT = FaceGeo<DIM, P>::NT;
+  const int N = A.N;
+  int cc[DIM][2], nopt[DIM];
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) {
+    const int i = idx[k], a = i / P, r = i - a * P;
+    int m = 0;
+    if (r == 0) {
+      if (a - 1 >= 0) cc[k][m++] = a - 1;
+      if (a < N) cc[k][m++] = a;
+    } else {
+      cc[k][m++] = a;
+    }
+    nopt[k] = m;
+  }
+  T acc = T(0);
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) {
+    const int i = idx[k], a = i / P, r = i - a * P;
+    int Llo = (r == 0) ? a - 2 : a - 1, Lhi = a;
+    if (Llo < 0) Llo = 0;
+    if (Lhi > N - 2) Lhi = N - 2;
+    int tdim[2] = {0, 0}, q = 0;
+#pragma unroll
+    for (int j = 0; j < DIM; ++j)
+      if (j != k) tdim[q++] = j;
+    const int n0 = nopt[tdim[0]], n1 = (DIM == 3) ? nopt[tdim[1]] : 1;
+    for (int Lk = Llo; Lk <= Lhi; ++Lk)
+      for (int u0 = 0; u0 < n0; ++u0)
+        for (int u1 = 0; u1 < n1; ++u1) {
+          int c[3] = {0, 0, 0};
+          c[k] = Lk;
+          c[tdim[0]] = cc[tdim[0]][u0];
+          if (DIM == 3) c[tdim[1]] = cc[tdim[1]][u1];
+          const int cell = (DIM == 2) ? c[0] + N * c[1] : c[0] + N * (c[1] + N * c[2]);
+          const int id = A.face_id[cell * DIM + k];
+          if (id < 0) continue;
+          const int il = i - P * Lk;
+          int t = idx[tdim[0]] - P * c[tdim[0]];
+          if (DIM == 3) t += (P + 1) * (idx[tdim[1]] - P * c[tdim[1]]);
+          const T* g = A.G + (size_t)id * P * NT;
+#pragma unroll
+          for (int m = 0; m < P; ++m) acc += A.dvec[m][il] * g[m * NT + t];
+        }
+  }
+  return acc;
+}
+
+// (A x)_i for one lattice node: its active cells (cut-cell or uncut element
+// matrix rows) plus its ghost faces (moments looked up).
+template <int DIM, int P, typename T>
+__device__ __forceinline__ T node_row(const OpArgs<T>& A, const T* __restrict__ x, const int* idx,
+                                      const T* __restrict__ sK) {
   constexpr int NB = Shape<DIM, P>::NB;
   const int N = A.N, n = A.n;
-  T acc = T(0);
   int cc[DIM][2], lc[DIM][2], nopt[DIM];
 #pragma unroll
   for (int k = 0; k < DIM; ++k) {
-    int i = idx[k], a = i / P, r = i - a * P, m = 0;
+    const int i = idx[k], a = i / P, r = i - a * P;
+    int m = 0;
     if (r == 0) {
       if (a - 1 >= 0) { cc[k][m] = a - 1; lc[k][m] = P; ++m; }
       if (a < N) { cc[k][m] = a; lc[k][m] = 0; ++m; }
@@ -57,12 +175,13 @@ __device__ __forceinline__ T row_apply(const OpArgs<T>& A, const T* __restrict__
     }
     nopt[k] = m;
   }
+  T acc = T(0);
   const int tot = (DIM == 2) ? nopt[0] * nopt[1] : nopt[0] * nopt[1] * nopt[2];
   for (int s = 0; s < tot; ++s) {
     int t = s, cell = 0, row = 0, base = 0, cst = 1, rst = 1, nst = 1;
 #pragma unroll
     for (int k = 0; k < DIM; ++k) {
-      int o = t % nopt[k];
+      const int o = t % nopt[k];
       t /= nopt[k];
       cell += cc[k][o] * cst;
       cst *= N;
@@ -79,8 +198,7 @@ __device__ __forceinline__ T row_apply(const OpArgs<T>& A, const T* __restrict__
 #pragma unroll
       for (int j1 = 0; j1 <= P; ++j1)
 #pragma unroll
-        for (int j0 = 0; j0 <= P; ++j0)
-          acc += Mrow[j0 + (P + 1) * j1] * x[base + j0 + n * j1];
+        for (int j0 = 0; j0 <= P; ++j0) acc += Mrow[j0 + (P + 1) * j1] * x[base + j0 + n * j1];
     } else {
 #pragma unroll
       for (int j2 = 0; j2 <= P; ++j2)
@@ -91,84 +209,127 @@ __device__ __forceinline__ T row_apply(const OpArgs<T>& A, const T* __restrict__
             acc += Mrow[j0 + (P + 1) * (j1 + (P + 1) * j2)] * x[base + j0 + n * (j1 + n * j2)];
     }
   }
-  // ghost faces with normal k: lower cell L, upper L + e_k
+  return acc + node_faces<DIM, P, T>(A, idx);
+}
+
+// ---------------------------------------------------------------------------
+// Rows (A x)_i of the DoFs of a cut patch (vertex v, 2^DIM cells v-1+s) by
+// one warp: the (2P+1)^DIM closure of x is staged in shared memory, every
+// (patch cell, local node) pair whose node is a DoF of the patch gets its
+// cell row times x once, then each DoF sums its cells in a fixed order and
+// adds its ghost faces.  Every active cell containing a patch DoF is a patch
+// cell (the support rule that defines the DoFs).
+template <int DIM, int P>
+struct PatchGeo {
+  static constexpr int C = 2 * P + 1;
+  static constexpr int NCL = (DIM == 2) ? C * C : C * C * C;
+  static constexpr int NB = Shape<DIM, P>::NB;
+  static constexpr int NCELL = 1 << DIM;
+};
+
+template <int DIM, int P, typename T>
+struct PatchScratch {
+  using G = PatchGeo<DIM, P>;
+  T x[G::NCL];
+  T part[G::NCELL][G::NB];
+  T r[G::NCL];
+  short mem[G::NCL];
+};
+
+template <int DIM>
+__device__ __forceinline__ int lat_index(const int* c, int n) {
+  return (DIM == 2) ? c[0] + n * c[1] : c[0] + n * (c[1] + n * c[2]);
+}
+
+template <int DIM, int P, typename T>
+__device__ __forceinline__ void patch_rows(const OpArgs<T>& A, const T* __restrict__ x, const int* v,
+                                           const uint16_t* __restrict__ tgt, int m,
+                                           PatchScratch<DIM, P, T>& S, const T* __restrict__ sK,
+                                           int lane) {
+  using G = PatchGeo<DIM, P>;
+  constexpr int C = G::C, NB = G::NB;
+  const int N = A.N, n = A.n;
+  for (int e = lane; e < G::NCL; e += 32) {
+    int u = e, c[3] = {0, 0, 0};
+    bool in = true;
 #pragma unroll
-  for (int k = 0; k < DIM; ++k) {
-    const int i = idx[k], a = i / P, r = i - a * P;
-    int Llo = (r == 0) ? a - 2 : a - 1, Lhi = a;
-    if (Llo < 0) Llo = 0;
-    if (Lhi > N - 2) Lhi = N - 2;
-    // tangential options: the cells containing i in the other directions
-    int tc[2][2], to[2], tdim[2], q = 0;
-#pragma unroll
-    for (int j = 0; j < DIM; ++j) {
-      if (j == k) continue;
-      tdim[q] = j;
-      to[q] = nopt[j];
-      tc[q][0] = cc[j][0];
-      tc[q][1] = cc[j][nopt[j] > 1 ? 1 : 0];
-      ++q;
+    for (int k = 0; k < DIM; ++k) {
+      c[k] = P * (v[k] - 1) + u % C;
+      u /= C;
+      if (c[k] < 0 || c[k] >= n) in = false;
     }
-    const int ntan = (DIM == 2) ? to[0] : to[0] * to[1];
-    for (int Lk = Llo; Lk <= Lhi; ++Lk) {
-      for (int s = 0; s < ntan; ++s) {
-        int c1[3] = {0, 0, 0};
-        c1[k] = Lk;
-        int u = s;
-#pragma unroll
-        for (int qq = 0; qq < DIM - 1; ++qq) {
-          c1[tdim[qq]] = tc[qq][u % to[qq]];
-          u /= to[qq];
-        }
-        int cell1 = c1[0] + N * (c1[1] + (DIM == 3 ? N * c1[2] : 0));
-        int stride_k = (k == 0) ? 1 : (k == 1 ? N : N * N);
-        const uint8_t f1 = A.cflag[cell1], f2 = A.cflag[cell1 + stride_k];
-        if (!((f1 & kActive) && (f2 & kActive) && ((f1 | f2) & kCutCell))) continue;
-        // local coordinates of i in the face block
-        const int il = i - P * Lk;
-        int tl[2] = {0, 0};
-#pragma unroll
-        for (int qq = 0; qq < DIM - 1; ++qq) tl[qq] = idx[tdim[qq]] - P * c1[tdim[qq]];
-        // S_m = sum_{i'} dvec[m][i'] sum_{t'} prod Mhat[t][t'] x(i', t')
-        T Sm[P];
-#pragma unroll
-        for (int m = 0; m < P; ++m) Sm[m] = T(0);
-        int sk = 1, s0 = 1, s1 = 1;
-        {
-          int st = 1;
-#pragma unroll
-          for (int j = 0; j < DIM; ++j) {
-            if (j == k) sk = st;
-            st *= n;
-          }
-          s0 = (tdim[0] == 0) ? 1 : (tdim[0] == 1 ? n : n * n);
-          if (DIM == 3) s1 = (tdim[1] == 0) ? 1 : (tdim[1] == 1 ? n : n * n);
-        }
-        int base = P * (c1[0] + n * (c1[1] + (DIM == 3 ? n * c1[2] : 0)));
-#pragma unroll
-        for (int ip = 0; ip <= 2 * P; ++ip) {
-          T w = T(0);
-          if (DIM == 2) {
-#pragma unroll
-            for (int t0 = 0; t0 <= P; ++t0) w += A.Mhat[tl[0]][t0] * x[base + ip * sk + t0 * s0];
-          } else {
-#pragma unroll
-            for (int t1 = 0; t1 <= P; ++t1) {
-              T w1 = T(0);
-#pragma unroll
-              for (int t0 = 0; t0 <= P; ++t0) w1 += A.Mhat[tl[0]][t0] * x[base + ip * sk + t0 * s0 + t1 * s1];
-              w += A.Mhat[tl[1]][t1] * w1;
-            }
-          }
-#pragma unroll
-          for (int m = 0; m < P; ++m) Sm[m] += A.dvec[m][ip] * w;
-        }
-#pragma unroll
-        for (int m = 0; m < P; ++m) acc += A.coef[m] * A.dvec[m][il] * Sm[m];
-      }
-    }
+    S.x[e] = in ? x[lat_index<DIM>(c, n)] : T(0);
+    S.mem[e] = -1;
   }
-  return acc;
+  __syncwarp();
+  for (int e = lane; e < m; e += 32) S.mem[tgt[e]] = (short)e;
+  __syncwarp();
+  for (int it = lane; it < G::NCELL * NB; it += 32) {
+    const int s = it / NB, j = it - s * NB;
+    int c[3] = {0, 0, 0}, o = 0, ost = 1, u = j, base = 0;
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+      const int sk = (s >> k) & 1, a = u % (P + 1);
+      u /= (P + 1);
+      c[k] = v[k] - 1 + sk;
+      if (c[k] < 0 || c[k] >= N) ok = false;
+      o += (P * sk + a) * ost;
+      base += P * sk * ost;
+      ost *= C;
+    }
+    if (!ok || S.mem[o] < 0) continue;
+    const int cell = (DIM == 2) ? c[0] + N * c[1] : c[0] + N * (c[1] + N * c[2]);
+    const uint8_t fl = A.cflag[cell];
+    if (!(fl & kActive)) continue;
+    const T* row = (fl & kCutCell) ? A.cutmat + (size_t)A.cut_id[cell] * NB * NB + j * NB : sK + j * NB;
+    T acc = T(0);
+    if (DIM == 2) {
+#pragma unroll
+      for (int q1 = 0; q1 <= P; ++q1)
+#pragma unroll
+        for (int q0 = 0; q0 <= P; ++q0) acc += row[q0 + (P + 1) * q1] * S.x[base + q0 + C * q1];
+    } else {
+#pragma unroll
+      for (int q2 = 0; q2 <= P; ++q2)
+#pragma unroll
+        for (int q1 = 0; q1 <= P; ++q1)
+#pragma unroll
+          for (int q0 = 0; q0 <= P; ++q0)
+            acc += row[q0 + (P + 1) * (q1 + (P + 1) * q2)] * S.x[base + q0 + C * (q1 + C * q2)];
+    }
+    S.part[s][j] = acc;
+  }
+  __syncwarp();
+  for (int e = lane; e < m; e += 32) {
+    int o[3] = {0, 0, 0}, idx[3] = {0, 0, 0}, u = tgt[e];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+      o[k] = u % C;
+      u /= C;
+      idx[k] = P * (v[k] - 1) + o[k];
+    }
+    T acc = T(0);
+    for (int s = 0; s < G::NCELL; ++s) {
+      int j = 0, jst = 1, c[3] = {0, 0, 0};
+      bool in = true;
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) {
+        const int sk = (s >> k) & 1, a = o[k] - P * sk;
+        if (a < 0 || a > P) in = false;
+        j += a * jst;
+        jst *= (P + 1);
+        c[k] = v[k] - 1 + sk;
+        if (c[k] < 0 || c[k] >= N) in = false;
+      }
+      if (!in) continue;
+      const int cell = (DIM == 2) ? c[0] + N * c[1] : c[0] + N * (c[1] + N * c[2]);
+      if (!(A.cflag[cell] & kActive)) continue;
+      acc += S.part[s][j];
+    }
+    S.r[e] = acc + node_faces<DIM, P, T>(A, idx);
+  }
+  __syncwarp();
 }
 
 template <int NB, typename T>
@@ -259,7 +420,8 @@ __global__ void __launch_bounds__(128) k_apply_bulk(OpArgs<T> A, const T* __rest
   }
 }
 
-// Same output for the remaining active nodes, one thread per node, general rows.
+// Same output for the remaining active nodes (near the boundary), one thread
+// per node: its cells' rows and its ghost faces (moments precomputed).
 template <int DIM, int P, typename T>
 __global__ void __launch_bounds__(128) k_apply_bnd(OpArgs<T> A, const T* __restrict__ x,
                                                    const T* __restrict__ b, T* __restrict__ y,
@@ -276,7 +438,7 @@ __global__ void __launch_bounds__(128) k_apply_bnd(OpArgs<T> A, const T* __restr
     idx[k] = u % A.n;
     u /= A.n;
   }
-  const T v = row_apply<DIM, P, T>(A, x, idx, sK);
+  const T v = node_row<DIM, P, T>(A, x, idx, sK);
   y[node] = b ? b[node] - v : v;
 }
 
@@ -479,20 +641,26 @@ __global__ void __launch_bounds__(32 * WARPS) k_smooth_cart(FdArgs<T, P> F, int 
 }
 
 // ---------------------------------------------------------------------------
-// Cut-patch colour step, phase 1: residual rows of every patch DoF of the
-// colour into rbuf (all patches of the colour read the same x: additive within
-// a colour, Sec. 2.3 inconsistent ghost-penalty treatment).  One warp per patch.
+// Cut-patch colour step (Sec. 3: dense local solver on cut patches), phase 1:
+// one warp per patch; r_I = b_I - (A x)_I by patch_rows, delta = A_j^{-1} r_I
+// with the explicit inverse (symmetric, read by columns so that lanes load
+// consecutive entries), delta to dbuf.  x is not written here, so every patch
+// of the colour sees the same x: additive within a colour, which is the
+// paper's inconsistent treatment of ghost coupling between patches (Sec. 2.3).
 template <int DIM, int P, typename T, int WARPS>
-__global__ void __launch_bounds__(32 * WARPS) k_cut_resid(OpArgs<T> A, const T* __restrict__ x,
+__global__ void __launch_bounds__(32 * WARPS) k_cut_solve(OpArgs<T> A, const T* __restrict__ x,
                                                           const T* __restrict__ b,
                                                           const int* __restrict__ verts,
                                                           const int* __restrict__ cnt,
                                                           const int* __restrict__ moff,
+                                                          const int64_t* __restrict__ ioff,
                                                           const uint16_t* __restrict__ members,
-                                                          T* __restrict__ rbuf, int npatch) {
+                                                          const int* __restrict__ mnode,
+                                                          const T* __restrict__ inv,
+                                                          T* __restrict__ dbuf, int npatch) {
   constexpr int NB = Shape<DIM, P>::NB;
-  constexpr int C = 2 * P + 1;
   __shared__ T sK[NB * NB];
+  __shared__ PatchScratch<DIM, P, T> sS[WARPS];
   stage_kref<NB>(A.Kref, sK);
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int pidx = blockIdx.x * WARPS + w;
@@ -505,56 +673,29 @@ __global__ void __launch_bounds__(32 * WARPS) k_cut_resid(OpArgs<T> A, const T* 
     q /= np;
   }
   const int m = cnt[pidx], mo = moff[pidx];
+  PatchScratch<DIM, P, T>& S = sS[w];
+  patch_rows<DIM, P, T>(A, x, v, members + mo, m, S, sK, lane);
+  for (int e = lane; e < m; e += 32) S.r[e] = b[mnode[mo + e]] - S.r[e];
+  __syncwarp();
+  const T* Ai = inv + ioff[pidx];
   for (int e = lane; e < m; e += 32) {
-    int o = members[mo + e], idx[3] = {0, 0, 0}, node = 0, st = 1;
-#pragma unroll
-    for (int k = 0; k < DIM; ++k) {
-      idx[k] = P * (v[k] - 1) + o % C;
-      o /= C;
-      node += idx[k] * st;
-      st *= A.n;
+    T a0 = T(0), a1 = T(0);
+    int j = 0;
+    for (; j + 1 < m; j += 2) {
+      a0 += Ai[(size_t)j * m + e] * S.r[j];
+      a1 += Ai[(size_t)(j + 1) * m + e] * S.r[j + 1];
     }
-    rbuf[mo + e] = b[node] - row_apply<DIM, P, T>(A, x, idx, sK);
+    if (j < m) a0 += Ai[(size_t)j * m + e] * S.r[j];
+    dbuf[mo + e] = a0 + a1;
   }
 }
 
-// Phase 2: delta = A_j^{-1} r_j (explicit inverse, symmetric, read by
-// columns so that lanes load consecutive entries), x[I_j] += delta.
-template <int DIM, int P, typename T, int WARPS>
-__global__ void __launch_bounds__(32 * WARPS) k_cut_update(int N, int n, T* __restrict__ x,
-                                                           const int* __restrict__ verts,
-                                                           const int* __restrict__ cnt,
-                                                           const int* __restrict__ moff,
-                                                           const int64_t* __restrict__ ioff,
-                                                           const uint16_t* __restrict__ members,
-                                                           const T* __restrict__ inv,
-                                                           const T* __restrict__ rbuf, int npatch) {
-  constexpr int C = 2 * P + 1;
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int pidx = blockIdx.x * WARPS + w;
-  if (pidx >= npatch) return;
-  const int np = N + 1;
-  int q = verts[pidx], v[3] = {0, 0, 0};
-#pragma unroll
-  for (int k = 0; k < DIM; ++k) {
-    v[k] = q % np;
-    q /= np;
-  }
-  const int m = cnt[pidx], mo = moff[pidx];
-  const T* Ai = inv + ioff[pidx];
-  const T* r = rbuf + mo;
-  for (int e = lane; e < m; e += 32) {
-    T acc = T(0);
-    for (int j = 0; j < m; ++j) acc += Ai[(size_t)j * m + e] * r[j];
-    int o = members[mo + e], node = 0, st = 1;
-#pragma unroll
-    for (int k = 0; k < DIM; ++k) {
-      node += (P * (v[k] - 1) + o % C) * st;
-      o /= C;
-      st *= n;
-    }
-    x[node] += acc;
-  }
+// Phase 2: x[I_j] += delta for every DoF of the colour's patches.
+template <typename T>
+__global__ void __launch_bounds__(256) k_cut_scatter(T* __restrict__ x, const int* __restrict__ mnode,
+                                                     const T* __restrict__ dbuf, int m0, int m1) {
+  const int i = m0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m1) x[mnode[i]] += dbuf[i];
 }
 
 // ---------------------------------------------------------------------------

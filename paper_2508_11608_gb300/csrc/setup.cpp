@@ -318,7 +318,8 @@ void build_level(const SetupParams& prm, const RefTables& R, int N, HostLevel& L
     }
     return L.cflag[f];
   };
-  // ghost faces count
+  // ghost faces: list and per-cell ids
+  L.face_id.assign((size_t)ncell * d, -1);
   for (int64_t c = 0; c < ncell; ++c) {
     int ci[3] = {0, 0, 0};
     int64_t t = c;
@@ -330,7 +331,11 @@ void build_level(const SetupParams& prm, const RefTables& R, int N, HostLevel& L
       int cj[3] = {ci[0], ci[1], ci[2]};
       cj[k] += 1;
       uint8_t f1 = L.cflag[c], f2 = cflag_at(cj);
-      if ((f1 & kFlagActive) && (f2 & kFlagActive) && ((f1 | f2) & kFlagCut)) L.n_ghost++;
+      if ((f1 & kFlagActive) && (f2 & kFlagActive) && ((f1 | f2) & kFlagCut)) {
+        L.face_id[(size_t)c * d + k] = (int)L.ghost_faces.size();
+        L.ghost_faces.push_back((int)(c * d + k));
+        L.n_ghost++;
+      }
     }
   }
   // "plain" cell: active, uncut, no cut face-neighbour (no ghost face)
@@ -369,6 +374,17 @@ void build_level(const SetupParams& prm, const RefTables& R, int N, HostLevel& L
         bulk[q] = 1;
         L.bulk_pos.push_back((int)q);
       }
+    }
+    std::vector<uint8_t> owns(npos, 0);
+    for (int64_t i : L.dofs) {
+      int64_t t = i, q = 0, st = 1;
+      for (int k = 0; k < d; ++k) {
+        int ik = (int)(t % n);
+        t /= n;
+        q += (int64_t)(ik / p) * st;
+        st *= np;
+      }
+      owns[q] = 1;
     }
     for (int64_t i : L.dofs) {
       int64_t t = i, q = 0, st = 1;
@@ -522,8 +538,108 @@ void build_level(const SetupParams& prm, const RefTables& R, int N, HostLevel& L
       moff += m;
       ioff += (int64_t)m * m;
       L.members.insert(L.members.end(), mem[j].begin(), mem[j].end());
+      int v[3] = {0, 0, 0};
+      int64_t t = L.cut_vert[j];
+      for (int k = 0; k < d; ++k) {
+        v[k] = (int)(t % np);
+        t /= np;
+      }
+      for (int e = 0; e < m; ++e) {
+        int o = mem[j][e];
+        int64_t node = 0, st = 1;
+        for (int k = 0; k < d; ++k) {
+          node += (int64_t)(p * (v[k] - 1) + o % C) * st;
+          o /= C;
+          st *= n;
+        }
+        L.member_node.push_back((int)node);
+      }
     }
     L.inv.assign(ioff, 0.0);
+    // work model of the cut-patch solve (what the kernel computes per patch):
+    // cell rows 2 NB per (active patch cell, target in it); ghost-face moments
+    // 2 (2p+1) p NT + 2 p NT^2 per ghost face; 2 p per (target, ghost face);
+    // inverse 2 m^2.  Moved scalars: inverse, the rows of cut-cell matrices
+    // used, the closure of x, b and delta of the targets.
+    {
+      const int NT = ipow(p + 1, d - 1);
+      L.work_cut.assign(ncol, {0.0, 0.0, 0.0});
+      for (int col = 0; col < ncol; ++col)
+        for (int j = L.cut_start[col]; j < L.cut_start[col + 1]; ++j) {
+          int v[3] = {0, 0, 0};
+          int64_t t = L.cut_vert[j];
+          for (int k = 0; k < d; ++k) {
+            v[k] = (int)(t % np);
+            t /= np;
+          }
+          const int m = L.cut_n[j];
+          double fl = 2.0 * m * m, sc = (double)m * m + NCL + 2.0 * m;
+          for (int s2 = 0; s2 < (1 << d); ++s2) {
+            int c[3] = {0, 0, 0};
+            for (int k = 0; k < d; ++k) c[k] = v[k] - 1 + ((s2 >> k) & 1);
+            uint8_t f = cflag_at(c);
+            if (!(f & kFlagActive)) continue;
+            int rows = 0;
+            for (int e = 0; e < m; ++e) {
+              int o = mem[j][e];
+              bool in = true;
+              for (int k = 0; k < d; ++k) {
+                int a = o % C - p * ((s2 >> k) & 1);
+                o /= C;
+                if (a < 0 || a > p) in = false;
+              }
+              rows += in;
+            }
+            fl += 2.0 * NB * rows;
+            if (f & kFlagCut) sc += (double)rows * NB;
+          }
+          for (int k = 0; k < d; ++k)
+            for (int ok = -2; ok <= 0; ++ok)
+              for (int tb = 0; tb < (1 << (d - 1)); ++tb) {
+                int lc[3] = {0, 0, 0}, q = 0, off[3] = {0, 0, 0};
+                for (int kk = 0; kk < d; ++kk) {
+                  if (kk == k) { off[kk] = ok; continue; }
+                  off[kk] = ((tb >> q) & 1) - 1;
+                  ++q;
+                }
+                for (int kk = 0; kk < d; ++kk) lc[kk] = v[kk] + off[kk];
+                int uc[3] = {lc[0], lc[1], lc[2]};
+                uc[k] += 1;
+                uint8_t f1 = cflag_at(lc), f2 = cflag_at(uc);
+                if (!((f1 & kFlagActive) && (f2 & kFlagActive) && ((f1 | f2) & kFlagCut))) continue;
+                fl += 2.0 * (2 * p + 1) * p * NT + 2.0 * p * NT * NT;
+                for (int e = 0; e < m; ++e) {
+                  int o = mem[j][e];
+                  bool in = true;
+                  for (int kk = 0; kk < d; ++kk) {
+                    int ov = o % C;
+                    o /= C;
+                    int loc = ov - p * (off[kk] + 1);
+                    if (loc < 0 || loc > (kk == k ? 2 * p : p)) in = false;
+                  }
+                  if (in) fl += 2.0 * p;
+                }
+              }
+          L.work_cut[col][0] += fl;
+          L.work_cut[col][1] += sc;
+          L.work_cut[col][2] += 6.0 * m + 24.0;
+        }
+      // interior patches: sum factorisation and fast diagonalisation
+      const int M = 2 * p - 1;
+      double flc, scc;
+      if (d == 3) {
+        flc = 2.0 * (2.0 * M * C * C * C + 3.0 * M * M * C * C + 2.0 * M * M * M * C + 6.0 * M * M * M * M + M * M * M);
+        scc = (double)C * C * C + 2.0 * M * M * M;
+      } else {
+        flc = 2.0 * (2.0 * M * C * C + 2.0 * M * M * C + 4.0 * M * M * M + M * M);
+        scc = (double)C * C + 2.0 * M * M;
+      }
+      L.work_cart.assign(ncol, {0.0, 0.0, 0.0});
+      for (int col = 0; col < ncol; ++col) {
+        double np_ = L.cart_start[col + 1] - L.cart_start[col];
+        L.work_cart[col] = {np_ * flc, np_ * scc, np_ * 4.0};
+      }
+    }
     // A_j = A[I_j, I_j] from cell and ghost-face pieces, then inverted
     std::vector<int> err(ncp, 0);
     std::string first_err;

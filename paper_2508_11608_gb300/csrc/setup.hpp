@@ -4,6 +4,7 @@
 
 #include <cstdint>
 #include <string>
+#include <array>
 #include <vector>
 
 #include "geometry.hpp"
@@ -37,10 +38,13 @@ struct HostLevel {
   std::vector<uint8_t> nact;    // n^d: node belongs to an active cell
   std::vector<int64_t> dofs;    // lattice index of each DoF (ascending)
   int bb_lo[3] = {0, 0, 0}, bb_hi[3] = {0, 0, 0};  // inclusive node bbox of the DoFs
-  // matrix-free apply: owner positions whose 2^d cells are plain interior
-  // cells, and the remaining active nodes
+  // matrix-free apply: positions a own the nodes p a + alpha, alpha in
+  // [0, p)^d; bulk positions have 2^d plain interior cells around them
   std::vector<int> bulk_pos;    // packed a_0 + (N+1)(a_1 + (N+1) a_2)
-  std::vector<int> bnd_node;    // lattice index
+  std::vector<int> bnd_node;    // active nodes not owned by a bulk position
+  // ghost faces (c, c + e_k): packed c * d + k, and the id of each face per cell
+  std::vector<int> ghost_faces;
+  std::vector<int> face_id;     // N^d * d, -1 where (c, c + e_k) is not a ghost face
   // patches (sorted by colour; start offsets per colour, 2^d + 1 entries)
   std::vector<int> cart_vert;   // packed vertex v_0 + (N+1)(v_1 + (N+1) v_2)
   std::vector<int> cart_start;
@@ -48,7 +52,12 @@ struct HostLevel {
   std::vector<int64_t> cut_ioff;
   std::vector<int> cut_start;
   std::vector<uint16_t> members;  // closure-local node index per cut-patch DoF
+  std::vector<int> member_node;   // lattice index per cut-patch DoF
   std::vector<double> inv;        // explicit FP64 inverses A_j^{-1}, row-major
+  // algorithmic work per launch, used to report achieved FLOP/s and bytes:
+  // per colour of the cut-patch solve and of the interior-patch step
+  // {flops, scalars moved, index bytes moved}
+  std::vector<std::array<double, 3>> work_cut, work_cart;
   // reference tables
   std::vector<double> Kref;       // NB x NB stiffness of an uncut cell
   std::vector<double> Mr, Kr;     // M x C rows of the two-cell 1D mass / stiffness
