@@ -155,6 +155,24 @@ cf_status cf_level_prolongate(cf_problem* pb, int level, int precision,
 cf_status cf_coarse_solve(cf_problem* pb, int precision, const double* d_b0,
                           double* d_x0, void* stream);
 
+/* Same result as cf_coarse_solve(pb, CF_FP64, ...), for callers that cannot
+ * have the call allocate device memory (work captured into a CUDA graph,
+ * services that own all device memory in their own arena, loops that forbid
+ * allocation on the hot path).  The paper has no counterpart.  The two
+ * coarsest-level staging vectors live in one fixed file-scope device array
+ * of 2 x 32768 doubles (512 KiB, held by every GPU that loads the library
+ * until the process exits); the call allocates nothing.
+ *  - Rejects (CF_EINVAL) a problem whose coarsest level has more than 32768
+ *    lattice nodes ((p N_0 + 1)^d), and a current device other than the
+ *    problem's.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - Every call on a device shares the array: calls that overlap on the GPU
+ *    (different streams or threads without ordering) race and give wrong
+ *    results.  Calls ordered on one stream are safe.
+ *  - d_b0 / d_x0: FP64 device arrays of cf_level_n_dofs(pb, 0) entries. */
+cf_status cf_coarse_solve_noalloc(cf_problem* pb, const double* d_b0, double* d_x0, void* stream);
+
 /* ---- instrumentation ----------------------------------------------------- */
 /* Number of kernel launches this handle has issued (all calls). */
 int64_t cf_launch_count(const cf_problem* pb);

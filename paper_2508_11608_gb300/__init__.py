@@ -143,6 +143,11 @@ class Problem:
     def coarse_solve(self, b0, x0, precision=CF_FP64, stream=None):
         check(self._lib.cf_coarse_solve(self._h, precision, _ptr(b0), _ptr(x0), _stream(stream)))
 
+    def coarse_solve_noalloc(self, b0, x0, stream=None):
+        """cf_coarse_solve_noalloc: the FP64 coarse solve without any device
+        allocation in the call (fixed static staging array, see cutmg.h)."""
+        check(self._lib.cf_coarse_solve_noalloc(self._h, _ptr(b0), _ptr(x0), _stream(stream)))
+
     # ---- instrumentation --------------------------------------------------------------
     def launch_count(self):
         return self._lib.cf_launch_count(self._h)

@@ -21,7 +21,7 @@ EXPORTED = [
     "cf_vcycle", "cf_solve", "cf_level_apply", "cf_level_colour_step", "cf_level_smooth",
     "cf_level_restrict", "cf_level_prolongate", "cf_coarse_solve", "cf_setup_host", "cf_host_rhs",
     "cf_host_cell_matrix", "cf_host_patch_counts", "cf_host_interior_patch", "cf_host_cut_patch",
-    "cf_launch_count", "cf_profile_start", "cf_profile_read",
+    "cf_launch_count", "cf_profile_start", "cf_profile_read", "cf_coarse_solve_noalloc",
 ]
 
 
@@ -93,6 +93,7 @@ def load():
     lib.cf_host_patch_counts.argtypes = [P, I, P, P]
     lib.cf_host_interior_patch.argtypes = [P, I, ctypes.c_int64, P]
     lib.cf_host_cut_patch.argtypes = [P, I, ctypes.c_int64, P, P, P, P]
+    lib.cf_coarse_solve_noalloc.argtypes = [P, P, P, V]
     lib.cf_launch_count.argtypes = [P]
     lib.cf_launch_count.restype = ctypes.c_int64
     lib.cf_profile_start.argtypes = [P, I]

@@ -60,7 +60,16 @@ cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
 }  // namespace
 
+cf_status cutmg_set_error(cf_status s, const char* msg) { return fail(s, msg); }
+
 extern "C" {
+
+cf_status cutmg_noalloc_engine(cf_problem* pb, EngineBase** eng, int* device) {
+  if (no_device(pb)) return fail(CF_EINVAL, "null or host-only problem");
+  *eng = pb->eng.get();
+  *device = pb->device;
+  return CF_OK;
+}
 
 const char* cf_last_error(void) { return g_err.c_str(); }
 

@@ -140,6 +140,14 @@ class Engine final : public EngineBase {
   }
 
   int64_t launches() const override { return launches_; }
+  void coarse_data(const double** inv, const int** nodes, const int64_t** dofs, int64_t* n0,
+                   int64_t* nbox) const override {
+    *inv = d64_[0].coarse_inv;
+    *nodes = com_[0].coarse_nodes;
+    *dofs = com_[0].dofs;
+    *n0 = com_[0].ndof;
+    *nbox = com_[0].nbox;
+  }
   void profile_start(int kind) override {
     prof_.kind = kind;
     prof_.used = 0;

@@ -42,6 +42,10 @@ class EngineBase {
   virtual int64_t launches() const = 0;
   virtual void profile_start(int kind) = 0;
   virtual void profile_read(double* ms, int64_t* n, double* flops, double* bytes) = 0;
+  // device data of the coarsest level: FP64 explicit inverse (n0 x n0),
+  // lattice index of each coarse DoF (int and int64), lattice size
+  virtual void coarse_data(const double** inv, const int** nodes, const int64_t** dofs, int64_t* n0,
+                           int64_t* nbox) const = 0;
 };
 
 std::unique_ptr<EngineBase> make_engine_d2(int degree, const Hierarchy& H);
