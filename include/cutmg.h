@@ -44,10 +44,14 @@ typedef enum {
   CF_EUNSUPPORTED = 6
 } cf_status;
 
-/* Level-set kinds (Omega = {phi < 0}; Sec. 4 uses an analytic level set). */
+/* Level-set kinds (Omega = {phi < 0}; Sec. 4 uses an analytic level set).
+ * y = rot (x - center) are body coordinates (rot row-major, rows = axes). */
 typedef enum {
-  CF_LS_SPHERE = 0, /* phi = |x - center| - radius (disk in 2D)               */
-  CF_LS_PLANE = 1   /* phi = normal . x - offset (half space; used in tests)   */
+  CF_LS_SPHERE = 0,    /* phi = |x - center| - radius (disk in 2D)                        */
+  CF_LS_PLANE = 1,     /* phi = normal . x - offset (half space; used in tests)            */
+  CF_LS_ELLIPSOID = 2, /* phi = sqrt(sum (y_i / axes_i)^2) - 1 (3D)                         */
+  CF_LS_TORUS = 3,     /* phi = sqrt((sqrt(y_0^2 + y_1^2) - major)^2 + y_2^2) - radius (3D) */
+  CF_LS_FLOWER = 4     /* phi = |x - c| - (radius + amplitude cos(lobes (theta - phase))) (2D) */
 } cf_levelset_kind;
 
 typedef enum { CF_FP64 = 0, CF_MIXED = 1 } cf_precision;
@@ -65,10 +69,16 @@ typedef struct {
 
 typedef struct {
   int kind;          /* cf_levelset_kind */
-  double center[3];  /* sphere centre */
-  double radius;     /* sphere radius */
+  double center[3];  /* centre (sphere, ellipsoid, torus, flower) */
+  double radius;     /* sphere radius; torus minor radius; flower base radius */
   double normal[3];  /* plane normal */
   double offset;     /* plane offset */
+  double axes[3];    /* ellipsoid semi-axes */
+  double rot[9];     /* ellipsoid / torus rotation, row-major, rows = body axes */
+  double major;      /* torus major radius */
+  int lobes;         /* flower: number of lobes */
+  double amplitude;  /* flower: radius amplitude */
+  double phase;      /* flower: rotation angle theta_0 */
 } cf_levelset;
 
 /* Method parameters.  Zero / negative entries select the defaults given. */

@@ -4,16 +4,117 @@ Sec. 4 setup).  Omega = {phi < 0}, Gamma = {phi = 0}.
 Each level set provides
   phi(X)                 values at points X (..., d)
   grad(X)                gradient at points
-  box_minmax(lo, hi)     exact min and max of phi over a closed box (degenerate
-                         sides allowed), used for classification and to drop
-                         functions without a zero in a box
+  box_minmax(lo, hi)     bounds of phi over a closed box (degenerate sides
+                         allowed): exact for the sphere and the plane; for the
+                         other shapes an interval enclosure, refined by
+                         halving the box (all directions) while the sign is
+                         undecided, at most BOX_DEPTH times
   grad_sign_const(k, lo, hi)
-                         True when d phi / d x_k has one strict sign on the box
-                         (monotonicity test of the dimension-reduction rule)
+                         True when d phi / d x_k provably keeps one strict sign
+                         on the box (monotonicity test of the cut quadrature)
+
+Interval enclosures use plain floating point (no outward rounding); the
+library's setup evaluates the same expressions in the same order.
 """
+
+import math
 
 import numpy as np
 
+BOX_DEPTH = 2
+
+
+# ---------------------------------------------------------------------------
+# closed intervals as (lo, hi) tuples
+
+def iadd(a, b):
+    return (a[0] + b[0], a[1] + b[1])
+
+
+def isub(a, b):
+    return (a[0] - b[1], a[1] - b[0])
+
+
+def iscale(s, a):
+    u, v = s * a[0], s * a[1]
+    return (min(u, v), max(u, v))
+
+
+def imul(a, b):
+    p = (a[0] * b[0], a[0] * b[1], a[1] * b[0], a[1] * b[1])
+    return (min(p), max(p))
+
+
+def isqr(a):
+    u, v = a[0] * a[0], a[1] * a[1]
+    if a[0] <= 0.0 <= a[1]:
+        return (0.0, max(u, v))
+    return (min(u, v), max(u, v))
+
+
+def isqrt(a):
+    return (math.sqrt(max(a[0], 0.0)), math.sqrt(max(a[1], 0.0)))
+
+
+def idiv(a, b):
+    """a / b for an interval b not containing 0 (caller checks)."""
+    return imul(a, (1.0 / b[1], 1.0 / b[0]))
+
+
+def icos(a):
+    lo, hi = a
+    if hi - lo >= 2.0 * math.pi:
+        return (-1.0, 1.0)
+    c0, c1 = math.cos(lo), math.cos(hi)
+    mn, mx = min(c0, c1), max(c0, c1)
+    # a multiple of 2 pi inside -> max 1; an odd multiple of pi inside -> min -1
+    k = math.ceil(lo / (2.0 * math.pi))
+    if 2.0 * math.pi * k <= hi:
+        mx = 1.0
+    k = math.ceil((lo - math.pi) / (2.0 * math.pi))
+    if math.pi + 2.0 * math.pi * k <= hi:
+        mn = -1.0
+    return (mn, mx)
+
+
+def isin(a):
+    return icos((a[0] - 0.5 * math.pi, a[1] - 0.5 * math.pi))
+
+
+def _box_dist(lo, hi, c, d):
+    """Exact min and max of |x - c| over a box."""
+    smin = 0.0
+    smax = 0.0
+    for k in range(d):
+        a = lo[k] - c[k]
+        b = hi[k] - c[k]
+        near = a if a > 0 else (-b if b < 0 else 0.0)
+        far = max(abs(a), abs(b))
+        smin = smin + near * near
+        smax = smax + far * far
+    return math.sqrt(smin), math.sqrt(smax)
+
+
+def _refined(fn, lo, hi, d, depth=0):
+    mn, mx = fn(lo, hi)
+    if mn < 0.0 < mx and depth < BOX_DEPTH:
+        free = [k for k in range(d) if hi[k] > lo[k]]
+        mn, mx = math.inf, -math.inf
+        for bits in range(1 << len(free)):
+            clo = list(lo)
+            chi = list(hi)
+            for i, k in enumerate(free):
+                mid = 0.5 * (lo[k] + hi[k])
+                if (bits >> i) & 1:
+                    clo[k] = mid
+                else:
+                    chi[k] = mid
+            a, b = _refined(fn, clo, chi, d, depth + 1)
+            mn, mx = min(mn, a), max(mx, b)
+    return mn, mx
+
+
+# ---------------------------------------------------------------------------
 
 class Sphere:
     """phi(x) = |x - c| - r: a disk (d = 2) or ball (d = 3)."""
@@ -42,16 +143,8 @@ class Sphere:
         return (X - self.c) / nrm[..., None]
 
     def box_minmax(self, lo, hi):
-        smin = 0.0
-        smax = 0.0
-        for k in range(self.d):
-            a = lo[k] - self.c[k]
-            b = hi[k] - self.c[k]
-            near = a if a > 0 else (-b if b < 0 else 0.0)
-            far = max(abs(a), abs(b))
-            smin = smin + near * near
-            smax = smax + far * far
-        return np.sqrt(smin) - self.r, np.sqrt(smax) - self.r
+        dmin, dmax = _box_dist(lo, hi, self.c, self.d)
+        return dmin - self.r, dmax - self.r
 
     def grad_sign_const(self, k, lo, hi):
         return bool(self.c[k] < lo[k] or self.c[k] > hi[k])
@@ -94,12 +187,229 @@ class Plane:
         return bool(self.n[k] != 0.0)
 
 
+class Ellipsoid:
+    """phi(x) = sqrt(sum_i (y_i / a_i)^2) - 1 with y = R (x - c): the
+    ellipsoid with semi-axes a_i along the rows of the rotation R (d = 3)."""
+
+    kind = "ellipsoid"
+
+    def __init__(self, center, axes, rot):
+        self.c = np.asarray(center, dtype=np.float64)
+        self.a = np.asarray(axes, dtype=np.float64)
+        self.R = np.asarray(rot, dtype=np.float64).reshape(3, 3)
+        self.d = 3
+
+    def _y(self, X):
+        X = np.asarray(X, dtype=np.float64)
+        D = [X[..., j] - self.c[j] for j in range(3)]
+        return [self.R[i, 0] * D[0] + self.R[i, 1] * D[1] + self.R[i, 2] * D[2] for i in range(3)]
+
+    def phi(self, X):
+        y = self._y(X)
+        s = None
+        for i in range(3):
+            t = y[i] / self.a[i]
+            s = t * t if s is None else s + t * t
+        return np.sqrt(s) - 1.0
+
+    def grad(self, X):
+        y = self._y(X)
+        s = None
+        for i in range(3):
+            t = y[i] / self.a[i]
+            s = t * t if s is None else s + t * t
+        q = np.sqrt(s)
+        g = [y[i] / (self.a[i] * self.a[i]) / q for i in range(3)]
+        return np.stack([self.R[0, j] * g[0] + self.R[1, j] * g[1] + self.R[2, j] * g[2]
+                         for j in range(3)], axis=-1)
+
+    def _iy(self, lo, hi):
+        D = [(lo[j] - self.c[j], hi[j] - self.c[j]) for j in range(3)]
+        out = []
+        for i in range(3):
+            t = iscale(self.R[i, 0], D[0])
+            t = iadd(t, iscale(self.R[i, 1], D[1]))
+            t = iadd(t, iscale(self.R[i, 2], D[2]))
+            out.append(t)
+        return out
+
+    def _natural(self, lo, hi):
+        y = self._iy(lo, hi)
+        s = isqr(iscale(1.0 / self.a[0], y[0]))
+        s = iadd(s, isqr(iscale(1.0 / self.a[1], y[1])))
+        s = iadd(s, isqr(iscale(1.0 / self.a[2], y[2])))
+        q = isqrt(s)
+        return q[0] - 1.0, q[1] - 1.0
+
+    def box_minmax(self, lo, hi):
+        return _refined(self._natural, lo, hi, 3)
+
+    def grad_sign_const(self, k, lo, hi):
+        # sign of sum_i R_ik y_i / a_i^2 (the positive factor 1/|.| dropped)
+        y = self._iy(lo, hi)
+        t = iscale(self.R[0, k] / (self.a[0] * self.a[0]), y[0])
+        t = iadd(t, iscale(self.R[1, k] / (self.a[1] * self.a[1]), y[1]))
+        t = iadd(t, iscale(self.R[2, k] / (self.a[2] * self.a[2]), y[2]))
+        return bool(t[0] > 0.0 or t[1] < 0.0)
+
+
+class Torus:
+    """phi(x) = sqrt((sqrt(y_0^2 + y_1^2) - R0)^2 + y_2^2) - r0 with
+    y = Q (x - c): the torus around the axis Q[2] (d = 3)."""
+
+    kind = "torus"
+
+    def __init__(self, center, rot, major, minor):
+        self.c = np.asarray(center, dtype=np.float64)
+        self.Q = np.asarray(rot, dtype=np.float64).reshape(3, 3)
+        self.R0 = float(major)
+        self.r0 = float(minor)
+        self.d = 3
+
+    def _y(self, X):
+        X = np.asarray(X, dtype=np.float64)
+        D = [X[..., j] - self.c[j] for j in range(3)]
+        return [self.Q[i, 0] * D[0] + self.Q[i, 1] * D[1] + self.Q[i, 2] * D[2] for i in range(3)]
+
+    def phi(self, X):
+        y = self._y(X)
+        rho = np.sqrt(y[0] * y[0] + y[1] * y[1])
+        t = rho - self.R0
+        return np.sqrt(t * t + y[2] * y[2]) - self.r0
+
+    def grad(self, X):
+        y = self._y(X)
+        rho = np.sqrt(y[0] * y[0] + y[1] * y[1])
+        t = rho - self.R0
+        q = np.sqrt(t * t + y[2] * y[2])
+        g = [t / q * y[0] / rho, t / q * y[1] / rho, y[2] / q]
+        return np.stack([self.Q[0, j] * g[0] + self.Q[1, j] * g[1] + self.Q[2, j] * g[2]
+                         for j in range(3)], axis=-1)
+
+    def _iy(self, lo, hi):
+        D = [(lo[j] - self.c[j], hi[j] - self.c[j]) for j in range(3)]
+        out = []
+        for i in range(3):
+            t = iscale(self.Q[i, 0], D[0])
+            t = iadd(t, iscale(self.Q[i, 1], D[1]))
+            t = iadd(t, iscale(self.Q[i, 2], D[2]))
+            out.append(t)
+        return out
+
+    def _natural(self, lo, hi):
+        y = self._iy(lo, hi)
+        rho = isqrt(iadd(isqr(y[0]), isqr(y[1])))
+        t = (rho[0] - self.R0, rho[1] - self.R0)
+        q = isqrt(iadd(isqr(t), isqr(y[2])))
+        return q[0] - self.r0, q[1] - self.r0
+
+    def box_minmax(self, lo, hi):
+        return _refined(self._natural, lo, hi, 3)
+
+    def grad_sign_const(self, k, lo, hi):
+        y = self._iy(lo, hi)
+        rho2 = iadd(isqr(y[0]), isqr(y[1]))
+        if rho2[0] <= 0.0:
+            return False
+        rho = isqrt(rho2)
+        t = (rho[0] - self.R0, rho[1] - self.R0)
+        # q * dphi/dx_k = t/rho (Q0k y0 + Q1k y1) + Q2k y2  (q > 0 dropped)
+        w = iadd(iscale(self.Q[0, k], y[0]), iscale(self.Q[1, k], y[1]))
+        a = imul(idiv(t, rho), w)
+        s = iadd(a, iscale(self.Q[2, k], y[2]))
+        return bool(s[0] > 0.0 or s[1] < 0.0)
+
+
+class Flower:
+    """phi(x) = |x - c| - (r0 + a0 cos(m (theta - theta0))), theta the polar
+    angle of x - c (d = 2): the curve r(theta) = 0.6 + 0.1 cos(m theta)
+    rotated by theta0."""
+
+    kind = "flower"
+
+    def __init__(self, center, lobes, phase, base=0.6, amplitude=0.1):
+        self.c = np.asarray(center, dtype=np.float64)
+        self.m = int(lobes)
+        self.t0 = float(phase)
+        self.r0 = float(base)
+        self.a0 = float(amplitude)
+        self.d = 2
+
+    def phi(self, X):
+        X = np.asarray(X, dtype=np.float64)
+        dx = X[..., 0] - self.c[0]
+        dy = X[..., 1] - self.c[1]
+        rho = np.sqrt(dx * dx + dy * dy)
+        th = np.arctan2(dy, dx)
+        return rho - (self.r0 + self.a0 * np.cos(self.m * (th - self.t0)))
+
+    def grad(self, X):
+        X = np.asarray(X, dtype=np.float64)
+        dx = X[..., 0] - self.c[0]
+        dy = X[..., 1] - self.c[1]
+        r2 = dx * dx + dy * dy
+        rho = np.sqrt(r2)
+        th = np.arctan2(dy, dx)
+        s = self.a0 * self.m * np.sin(self.m * (th - self.t0))
+        return np.stack([dx / rho - s * dy / r2, dy / rho + s * dx / r2], axis=-1)
+
+    def _theta(self, lo, hi):
+        """Range of the polar angle over a box not containing c, in radians,
+        possibly beyond pi when the box crosses the negative x half-axis."""
+        xs = (lo[0] - self.c[0], hi[0] - self.c[0])
+        ys = (lo[1] - self.c[1], hi[1] - self.c[1])
+        ang = [math.atan2(y, x) for x in xs for y in ys]
+        if xs[1] < 0.0 and ys[0] <= 0.0 <= ys[1]:
+            ang = [a + 2.0 * math.pi if a < 0.0 else a for a in ang]
+        return (min(ang), max(ang))
+
+    def _contains_c(self, lo, hi):
+        return lo[0] <= self.c[0] <= hi[0] and lo[1] <= self.c[1] <= hi[1]
+
+    def _wave(self, lo, hi):
+        if self._contains_c(lo, hi):
+            return (-1.0, 1.0), None
+        th = self._theta(lo, hi)
+        arg = (self.m * (th[0] - self.t0), self.m * (th[1] - self.t0))
+        return icos(arg), arg
+
+    def _natural(self, lo, hi):
+        dmin, dmax = _box_dist(lo, hi, self.c, 2)
+        cw, _ = self._wave(lo, hi)
+        return dmin - (self.r0 + self.a0 * cw[1]), dmax - (self.r0 + self.a0 * cw[0])
+
+    def box_minmax(self, lo, hi):
+        return _refined(self._natural, lo, hi, 2)
+
+    def grad_sign_const(self, k, lo, hi):
+        if self._contains_c(lo, hi):
+            return False
+        dx = (lo[0] - self.c[0], hi[0] - self.c[0])
+        dy = (lo[1] - self.c[1], hi[1] - self.c[1])
+        dmin, dmax = _box_dist(lo, hi, self.c, 2)
+        _, arg = self._wave(lo, hi)
+        sw = iscale(self.a0 * self.m, isin(arg))
+        # rho^2 dphi/dx = dx rho - s dy ; rho^2 dphi/dy = dy rho + s dx
+        rho = (dmin, dmax)
+        if k == 0:
+            v = isub(imul(dx, rho), imul(sw, dy))
+        else:
+            v = iadd(imul(dy, rho), imul(sw, dx))
+        return bool(v[0] > 0.0 or v[1] < 0.0)
+
+
 def make_levelset(spec):
-    """Build a level set from a plain dict: {"kind": "sphere", "center": [...],
-    "radius": r} or {"kind": "plane", "normal": [...], "offset": a}."""
+    """Build a level set from a plain dict (kind and its parameters)."""
     kind = spec["kind"]
     if kind == "sphere":
         return Sphere(spec["center"], spec["radius"])
     if kind == "plane":
         return Plane(spec["normal"], spec["offset"])
+    if kind == "ellipsoid":
+        return Ellipsoid(spec["center"], spec["axes"], spec["rot"])
+    if kind == "torus":
+        return Torus(spec["center"], spec["rot"], spec["major"], spec["minor"])
+    if kind == "flower":
+        return Flower(spec["center"], spec["lobes"], spec["phase"], spec.get("base", 0.6),
+                      spec.get("amplitude", 0.1))
     raise ValueError(f"unknown level set kind {kind!r}")

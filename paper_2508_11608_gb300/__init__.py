@@ -27,23 +27,18 @@ class Problem:
     """A resident multigrid hierarchy (cf_setup .. cf_destroy)."""
 
     def __init__(self, dim, n_cells, n_levels, degree, center=None, radius=None, plane=None,
-                 lo=-1.0, hi=1.0, gamma_D=0.0, gamma_ghost=(0.0,) * 4, n_c=0, quad_q=0,
-                 precision=CF_FP64, host_only=False):
+                 levelset=None, lo=-1.0, hi=1.0, gamma_D=0.0, gamma_ghost=(0.0,) * 4, n_c=0,
+                 quad_q=0, precision=CF_FP64, host_only=False):
         lib = _lib.load()
         self._lib = lib
         mesh = _lib.cf_mesh(dim, n_cells, lo, hi, n_levels)
-        ls = _lib.cf_levelset()
-        if plane is not None:
-            ls.kind = _lib.CF_LS_PLANE
-            normal, offset = plane
-            for k, v in enumerate(normal):
-                ls.normal[k] = v
-            ls.offset = offset
+        if levelset is not None:
+            spec = levelset
+        elif plane is not None:
+            spec = {"kind": "plane", "normal": plane[0], "offset": plane[1]}
         else:
-            ls.kind = _lib.CF_LS_SPHERE
-            for k, v in enumerate(center):
-                ls.center[k] = v
-            ls.radius = radius
+            spec = {"kind": "sphere", "center": center, "radius": radius}
+        ls = _lib.make_levelset(spec)
         prm = _lib.cf_params()
         prm.gamma_D = gamma_D
         for k, v in enumerate(gamma_ghost):

@@ -11,7 +11,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libcutmg.so")
 
 CF_OK, CF_EINVAL, CF_ENOMEM, CF_ECUDA, CF_ENOCONV, CF_ETIMEOUT, CF_EUNSUPPORTED = range(7)
-CF_LS_SPHERE, CF_LS_PLANE = 0, 1
+CF_LS_SPHERE, CF_LS_PLANE, CF_LS_ELLIPSOID, CF_LS_TORUS, CF_LS_FLOWER = 0, 1, 2, 3, 4
 CF_FP64, CF_MIXED = 0, 1
 CF_K_CUT_SOLVE, CF_K_INTERIOR, CF_K_APPLY_BULK, CF_K_APPLY_BND = 1, 2, 3, 4
 
@@ -32,7 +32,9 @@ class cf_mesh(ctypes.Structure):
 
 class cf_levelset(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("center", ctypes.c_double * 3), ("radius", ctypes.c_double),
-                ("normal", ctypes.c_double * 3), ("offset", ctypes.c_double)]
+                ("normal", ctypes.c_double * 3), ("offset", ctypes.c_double),
+                ("axes", ctypes.c_double * 3), ("rot", ctypes.c_double * 9), ("major", ctypes.c_double),
+                ("lobes", ctypes.c_int), ("amplitude", ctypes.c_double), ("phase", ctypes.c_double)]
 
 
 class cf_params(ctypes.Structure):
@@ -107,3 +109,39 @@ def load():
 def check(status):
     if status != CF_OK:
         raise CutmgError(status, load().cf_last_error().decode())
+
+
+def make_levelset(spec):
+    """cf_levelset from a plain dict: {"kind": "sphere", "center", "radius"},
+    {"kind": "plane", "normal", "offset"}, {"kind": "ellipsoid", "center",
+    "axes", "rot"}, {"kind": "torus", "center", "rot", "major", "minor"},
+    {"kind": "flower", "center", "lobes", "phase", "base", "amplitude"}."""
+    ls = cf_levelset()
+    kind = spec["kind"]
+    kinds = {"sphere": CF_LS_SPHERE, "plane": CF_LS_PLANE, "ellipsoid": CF_LS_ELLIPSOID,
+             "torus": CF_LS_TORUS, "flower": CF_LS_FLOWER}
+    ls.kind = kinds[kind]
+    for k, v in enumerate(spec.get("center", [])):
+        ls.center[k] = v
+    if kind == "sphere":
+        ls.radius = spec["radius"]
+    elif kind == "plane":
+        for k, v in enumerate(spec["normal"]):
+            ls.normal[k] = v
+        ls.offset = spec["offset"]
+    elif kind == "ellipsoid":
+        for k, v in enumerate(spec["axes"]):
+            ls.axes[k] = v
+        for k, v in enumerate(list(map(float, __import__("numpy").asarray(spec["rot"]).ravel()))):
+            ls.rot[k] = v
+    elif kind == "torus":
+        for k, v in enumerate(list(map(float, __import__("numpy").asarray(spec["rot"]).ravel()))):
+            ls.rot[k] = v
+        ls.major = spec["major"]
+        ls.radius = spec["minor"]
+    elif kind == "flower":
+        ls.lobes = int(spec["lobes"])
+        ls.phase = spec["phase"]
+        ls.radius = spec.get("base", 0.6)
+        ls.amplitude = spec.get("amplitude", 0.1)
+    return ls

@@ -81,8 +81,17 @@ static cf_status setup_impl(const cf_mesh* mesh, const cf_levelset* ls, int degr
   if (degree < 1 || degree > 3) return fail(CF_EINVAL, "degree must be 1, 2 or 3");
   if (mesh->dim == 3 && degree > 2) return fail(CF_EUNSUPPORTED, "dim 3 supports degree 1 and 2");
   if (mesh->n_cells < 1 || mesh->n_levels < 1) return fail(CF_EINVAL, "n_cells and n_levels must be positive");
-  if (ls->kind != CF_LS_SPHERE && ls->kind != CF_LS_PLANE) return fail(CF_EINVAL, "unknown level-set kind");
+  if (ls->kind < CF_LS_SPHERE || ls->kind > CF_LS_FLOWER) return fail(CF_EINVAL, "unknown level-set kind");
   if (ls->kind == CF_LS_SPHERE && !(ls->radius > 0.0)) return fail(CF_EINVAL, "radius must be positive");
+  if ((ls->kind == CF_LS_ELLIPSOID || ls->kind == CF_LS_TORUS) && mesh->dim != 3)
+    return fail(CF_EINVAL, "ellipsoid and torus level sets are three-dimensional");
+  if (ls->kind == CF_LS_FLOWER && mesh->dim != 2) return fail(CF_EINVAL, "the flower level set is two-dimensional");
+  if (ls->kind == CF_LS_ELLIPSOID && !(ls->axes[0] > 0 && ls->axes[1] > 0 && ls->axes[2] > 0))
+    return fail(CF_EINVAL, "ellipsoid semi-axes must be positive");
+  if (ls->kind == CF_LS_TORUS && !(ls->major > ls->radius && ls->radius > 0))
+    return fail(CF_EINVAL, "torus radii must satisfy major > minor > 0");
+  if (ls->kind == CF_LS_FLOWER && !(ls->radius > ls->amplitude && ls->amplitude >= 0 && ls->lobes >= 1))
+    return fail(CF_EINVAL, "flower needs radius > amplitude >= 0 and lobes >= 1");
   SetupParams prm;
   prm.dim = mesh->dim;
   prm.degree = degree;
@@ -111,6 +120,13 @@ static cf_status setup_impl(const cf_mesh* mesh, const cf_levelset* ls, int degr
   }
   prm.ls.r = ls->radius;
   prm.ls.off = ls->offset;
+  for (int k = 0; k < 3; ++k) prm.ls.ax[k] = ls->axes[k];
+  if (ls->kind == CF_LS_ELLIPSOID || ls->kind == CF_LS_TORUS)
+    for (int k = 0; k < 9; ++k) prm.ls.R[k] = ls->rot[k];
+  prm.ls.major = ls->major;
+  prm.ls.lobes = ls->lobes;
+  prm.ls.amp = ls->amplitude;
+  prm.ls.phase = ls->phase;
   std::unique_ptr<cf_problem> pb;
   cf_status st = guarded([&] {
     pb.reset(new cf_problem());

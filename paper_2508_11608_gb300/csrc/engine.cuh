@@ -6,8 +6,11 @@
 #include <cuda_runtime.h>
 
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
 #include <memory>
+#include <tuple>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -84,6 +87,10 @@ class Engine final : public EngineBase {
     int* faces;
     int nfaces;
     int* face_id;
+    int* fofs;
+    int* fent;
+    int* cfaces;
+    std::vector<int> cf_start;
     int* cart;
     std::vector<int> cart_start;
     int* cutv;
@@ -133,8 +140,13 @@ class Engine final : public EngineBase {
     part_ = pool_.alloc<double>(kDotBlocks);
     sc_ = pool_.alloc<double>(16);
     CUTMG_CUDA(cudaMallocHost(&host_sc_, 16 * sizeof(double)));
+    CUTMG_CUDA(cudaStreamCreateWithFlags(&cap_, cudaStreamNonBlocking));
+    const char* g = std::getenv("CUTMG_GRAPHS");
+    use_graphs_ = !(g && g[0] == '0');
   }
   ~Engine() override {
+    for (auto& kv : graphs_) cudaGraphExecDestroy(kv.second.exec);
+    if (cap_) cudaStreamDestroy(cap_);
     if (host_sc_) cudaFreeHost(host_sc_);
     for (auto& e : prof_.ev) cudaEventDestroy(e);
   }
@@ -270,7 +282,7 @@ class Engine final : public EngineBase {
   void vcycle(int prec, const double* r, double* z, cudaStream_t s) override {
     const int L = n_levels() - 1;
     to_box(L, r, aux_, s);
-    precondition(prec, aux_, aux2_, s);
+    run_graph(GraphKey{300 + prec, aux_, aux2_}, s, [&](cudaStream_t cs) { precondition(prec, aux_, aux2_, cs); });
     from_box(L, aux2_, z, s);
   }
 
@@ -292,24 +304,32 @@ class Engine final : public EngineBase {
     int it = 0;
     double rn = bn;
     if (bn > 0.0) {
-      precondition(prec, rF_, zF_, s);
+      run_graph(GraphKey{300 + prec, rF_, zF_}, s, [&](cudaStream_t cs) { precondition(prec, rF_, zF_, cs); });
       dot(F.region, rF_, zF_, sc_ + 0, s);  // rz
       CUTMG_CUDA(cudaMemcpyAsync(pF_, zF_, bytes, cudaMemcpyDeviceToDevice, s));
       while (it < maxit) {
-        apply<double>(L, d64_[L], pF_, nullptr, qF_, s);
-        dot(F.region, pF_, qF_, sc_ + 1, s);  // pq
-        k_cg_update_xr<<<kVecBlocks, 256, 0, s>>>(F.region, sc_, xF_, rF_, pF_, qF_);
-        count_launch("cg update x r");
-        dot(F.region, rF_, rF_, sc_ + 3, s);  // rr
+        // q = A p, alpha = rz / (p, q), x += alpha p, r -= alpha q, ||r||^2 to the host
+        run_graph(GraphKey{100, pF_, xF_}, s, [&](cudaStream_t cs) {
+          apply<double>(L, d64_[L], pF_, nullptr, qF_, cs);
+          dot(F.region, pF_, qF_, sc_ + 1, cs);  // pq
+          k_cg_update_xr<<<kVecBlocks, 256, 0, cs>>>(F.region, sc_, xF_, rF_, pF_, qF_);
+          count_launch("cg update x r");
+          dot(F.region, rF_, rF_, sc_ + 3, cs);  // rr
+          CUTMG_CUDA(cudaMemcpyAsync(host_sc_ + 3, sc_ + 3, sizeof(double), cudaMemcpyDeviceToHost, cs));
+        });
+        CUTMG_CUDA(cudaStreamSynchronize(s));
         ++it;
-        rn = std::sqrt(read_scalar(3, s));
+        rn = std::sqrt(host_sc_[3]);
         if (!(rn > rtol * bn)) break;
-        precondition(prec, rF_, zF_, s);
-        dot(F.region, rF_, zF_, sc_ + 2, s);  // rz_new
-        k_cg_update_p<<<kVecBlocks, 256, 0, s>>>(F.region, sc_, pF_, zF_);
-        count_launch("cg update p");
-        k_copy_scalar<<<1, 1, 0, s>>>(sc_, 0, 2);
-        count_launch("cg scalar");
+        // z = B r, beta = (r, z)_new / (r, z), p = z + beta p
+        run_graph(GraphKey{200 + prec, rF_, zF_}, s, [&](cudaStream_t cs) {
+          precondition(prec, rF_, zF_, cs);
+          dot(F.region, rF_, zF_, sc_ + 2, cs);  // rz_new
+          k_cg_update_p<<<kVecBlocks, 256, 0, cs>>>(F.region, sc_, pF_, zF_);
+          count_launch("cg update p");
+          k_copy_scalar<<<1, 1, 0, cs>>>(sc_, 0, 2);
+          count_launch("cg scalar");
+        });
       }
     }
     CUTMG_CUDA(cudaEventRecord(e1, s));
@@ -341,6 +361,50 @@ class Engine final : public EngineBase {
     int64_t n = 0;
     double flops = 0.0, bytes = 0.0;
   } prof_;
+
+  // CUDA graphs: a fixed launch sequence is captured once on the internal
+  // stream cap_ and replayed on the caller's stream (graph launches are legal
+  // on every stream, capture is not legal on the legacy default stream).
+  // Disabled while a kernel family is being event-timed.
+  struct GraphEntry {
+    cudaGraphExec_t exec;
+    int64_t launches;
+  };
+  using GraphKey = std::tuple<int, const void*, const void*>;
+  std::map<GraphKey, GraphEntry> graphs_;
+  cudaStream_t cap_ = nullptr;
+  bool use_graphs_ = true;
+
+  template <class F>
+  void run_graph(const GraphKey& key, cudaStream_t s, F&& body) {
+    if (!use_graphs_ || prof_.kind != 0) {
+      body(s);
+      return;
+    }
+    auto it = graphs_.find(key);
+    if (it == graphs_.end()) {
+      const int64_t l0 = launches_;
+      cudaGraph_t g = nullptr;
+      CUTMG_CUDA(cudaStreamBeginCapture(cap_, cudaStreamCaptureModeThreadLocal));
+      try {
+        body(cap_);
+      } catch (...) {
+        cudaStreamEndCapture(cap_, &g);
+        if (g) cudaGraphDestroy(g);
+        launches_ = l0;
+        throw;
+      }
+      CUTMG_CUDA(cudaStreamEndCapture(cap_, &g));
+      cudaGraphExec_t ex = nullptr;
+      cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) throw CudaError(std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+      it = graphs_.emplace(key, GraphEntry{ex, launches_ - l0}).first;
+      launches_ = l0;
+    }
+    CUTMG_CUDA(cudaGraphLaunch(it->second.exec, s));
+    launches_ += it->second.launches;
+  }
 
   void count_launch(const char* what) {
     launch_check(what);
@@ -439,6 +503,10 @@ class Engine final : public EngineBase {
     c.faces = pool_.upload<int>(h.ghost_faces);
     c.nfaces = (int)h.ghost_faces.size();
     c.face_id = pool_.upload<int>(h.face_id);
+    c.fofs = pool_.upload<int>(h.fofs);
+    c.fent = pool_.upload<int>(h.fent);
+    c.cfaces = pool_.upload<int>(h.cfaces);
+    c.cf_start = h.cf_start;
     c.mnode = pool_.upload<int>(h.member_node);
     c.cart = pool_.upload<int>(h.cart_vert);
     c.cart_start = h.cart_start;
@@ -528,11 +596,18 @@ class Engine final : public EngineBase {
   }
 
   // jump moments of every ghost face of level l for the vector x
+  // (colour < 0: all of them; else only the faces the colour's cut patches need)
   template <typename T>
-  void face_moments(int l, Typed<T>& D, const T* x, cudaStream_t s) {
+  void face_moments(int l, Typed<T>& D, const T* x, cudaStream_t s, int colour = -1) {
     const Common& c = com_[l];
-    if (c.nfaces == 0) return;
-    k_face_moments<DIM, P, T><<<blocks_for(c.nfaces, 128), 128, 0, s>>>(D.op, x, c.faces, c.nfaces);
+    const int* ids = nullptr;
+    int cnt = c.nfaces;
+    if (colour >= 0) {
+      ids = c.cfaces + c.cf_start[colour];
+      cnt = c.cf_start[colour + 1] - c.cf_start[colour];
+    }
+    if (cnt <= 0) return;
+    k_face_moments<DIM, P, T><<<blocks_for(cnt, 128), 128, 0, s>>>(D.op, x, c.faces, ids, cnt);
     count_launch("ghost face moments");
   }
 
@@ -553,10 +628,10 @@ class Engine final : public EngineBase {
       const int a0 = c.cut_start[colour], cnt = c.cut_start[colour + 1] - a0;
       if (cnt <= 0) return;
       prof_mark(1, s);
-      face_moments<T>(l, D, x, s);
+      face_moments<T>(l, D, x, s, colour);
       k_cut_solve<DIM, P, T, WARPS><<<blocks_for(cnt, WARPS), 32 * WARPS, 0, s>>>(
-          D.op, x, b, c.cutv + a0, c.cutn + a0, c.cutmo + a0, c.cutio + a0, c.members, c.mnode, D.inv,
-          D.dbuf, cnt);
+          D.op, x, b, c.cutv + a0, c.cutn + a0, c.cutmo + a0, c.cutio + a0, c.members, c.mnode, c.fofs,
+          c.fent, D.inv, D.dbuf, cnt);
       count_launch("cut patch solve");
       prof_mark(1, s);
       const auto& w = H_.levels[l].work_cut[colour];

@@ -123,71 +123,313 @@ struct Poly1D {
 };
 
 // ---------------------------------------------------------------------------
-// Level sets.  Omega = {phi < 0}.
+// Closed intervals for bounds of level sets over boxes (plain floating point,
+// no outward rounding).
+struct Iv {
+  double lo, hi;
+};
+inline Iv iv_add(Iv a, Iv b) { return {a.lo + b.lo, a.hi + b.hi}; }
+inline Iv iv_sub(Iv a, Iv b) { return {a.lo - b.hi, a.hi - b.lo}; }
+inline Iv iv_scale(double s, Iv a) {
+  double u = s * a.lo, v = s * a.hi;
+  return {std::min(u, v), std::max(u, v)};
+}
+inline Iv iv_mul(Iv a, Iv b) {
+  double p0 = a.lo * b.lo, p1 = a.lo * b.hi, p2 = a.hi * b.lo, p3 = a.hi * b.hi;
+  return {std::min(std::min(p0, p1), std::min(p2, p3)), std::max(std::max(p0, p1), std::max(p2, p3))};
+}
+inline Iv iv_sqr(Iv a) {
+  double u = a.lo * a.lo, v = a.hi * a.hi;
+  if (a.lo <= 0.0 && 0.0 <= a.hi) return {0.0, std::max(u, v)};
+  return {std::min(u, v), std::max(u, v)};
+}
+inline Iv iv_sqrt(Iv a) { return {std::sqrt(std::max(a.lo, 0.0)), std::sqrt(std::max(a.hi, 0.0))}; }
+inline Iv iv_div(Iv a, Iv b) { return iv_mul(a, Iv{1.0 / b.hi, 1.0 / b.lo}); }
+inline Iv iv_cos(Iv a) {
+  const double tp = 2.0 * M_PI;
+  if (a.hi - a.lo >= tp) return {-1.0, 1.0};
+  double c0 = std::cos(a.lo), c1 = std::cos(a.hi);
+  double mn = std::min(c0, c1), mx = std::max(c0, c1);
+  if (tp * std::ceil(a.lo / tp) <= a.hi) mx = 1.0;
+  if (M_PI + tp * std::ceil((a.lo - M_PI) / tp) <= a.hi) mn = -1.0;
+  return {mn, mx};
+}
+inline Iv iv_sin(Iv a) { return iv_cos(Iv{a.lo - 0.5 * M_PI, a.hi - 0.5 * M_PI}); }
+
+// ---------------------------------------------------------------------------
+// Level sets.  Omega = {phi < 0}.  Sphere and plane have exact box bounds;
+// ellipsoid, torus (3D) and the flower curve (2D) use interval enclosures,
+// refined by halving the box in every non-degenerate direction while the sign
+// is undecided, at most kBoxDepth times (dyadic, so that nested cells keep
+// nested classifications).
+constexpr int kBoxDepth = 2;
+
 struct LevelSet {
-  int kind = 0;  // 0 sphere, 1 plane
+  enum Kind { kSphere = 0, kPlane = 1, kEllipsoid = 2, kTorus = 3, kFlower = 4 };
+  int kind = kSphere;
   int d = 3;
   double c[3] = {0, 0, 0};
-  double r = 0;
-  double nrm[3] = {0, 0, 0};
-  double off = 0;
+  double r = 0;                 // sphere radius / torus minor radius / flower base radius
+  double nrm[3] = {0, 0, 0};    // plane normal
+  double off = 0;               // plane offset
+  double ax[3] = {1, 1, 1};     // ellipsoid semi-axes
+  double R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};  // rotation (rows = body axes)
+  double major = 0;             // torus major radius
+  int lobes = 0;                // flower
+  double amp = 0, phase = 0;    // flower
+
+  // body coordinates y = R (x - c)
+  void body(const double* x, double* y) const {
+    double dd[3] = {x[0] - c[0], x[1] - c[1], d > 2 ? x[2] - c[2] : 0.0};
+    for (int i = 0; i < 3; ++i) y[i] = R[3 * i + 0] * dd[0] + R[3 * i + 1] * dd[1] + R[3 * i + 2] * dd[2];
+  }
 
   double phi(const double* x) const {
-    if (kind == 0) {
-      double s = 0.0;
-      for (int k = 0; k < d; ++k) {
-        double t = x[k] - c[k];
-        s = (k == 0) ? t * t : s + t * t;
+    switch (kind) {
+      case kSphere: {
+        double s = 0.0;
+        for (int k = 0; k < d; ++k) {
+          double t = x[k] - c[k];
+          s = (k == 0) ? t * t : s + t * t;
+        }
+        return std::sqrt(s) - r;
       }
-      return std::sqrt(s) - r;
+      case kPlane: {
+        double s = 0.0;
+        for (int k = 0; k < d; ++k) s = (k == 0) ? nrm[0] * x[0] : s + nrm[k] * x[k];
+        return s - off;
+      }
+      case kEllipsoid: {
+        double y[3];
+        body(x, y);
+        double s = 0.0;
+        for (int i = 0; i < 3; ++i) {
+          double t = y[i] / ax[i];
+          s = (i == 0) ? t * t : s + t * t;
+        }
+        return std::sqrt(s) - 1.0;
+      }
+      case kTorus: {
+        double y[3];
+        body(x, y);
+        double rho = std::sqrt(y[0] * y[0] + y[1] * y[1]);
+        double t = rho - major;
+        return std::sqrt(t * t + y[2] * y[2]) - r;
+      }
+      default: {
+        double dx = x[0] - c[0], dy = x[1] - c[1];
+        double rho = std::sqrt(dx * dx + dy * dy), th = std::atan2(dy, dx);
+        return rho - (r + amp * std::cos(lobes * (th - phase)));
+      }
     }
-    double s = 0.0;
-    for (int k = 0; k < d; ++k) s = (k == 0) ? nrm[0] * x[0] : s + nrm[k] * x[k];
-    return s - off;
   }
 
   void grad(const double* x, double* g) const {
-    if (kind == 0) {
-      double s = 0.0;
-      for (int k = 0; k < d; ++k) {
-        double t = x[k] - c[k];
-        s = (k == 0) ? t * t : s + t * t;
+    switch (kind) {
+      case kSphere: {
+        double s = 0.0;
+        for (int k = 0; k < d; ++k) {
+          double t = x[k] - c[k];
+          s = (k == 0) ? t * t : s + t * t;
+        }
+        double nr = std::sqrt(s);
+        for (int k = 0; k < d; ++k) g[k] = (x[k] - c[k]) / nr;
+        return;
       }
-      double nr = std::sqrt(s);
-      for (int k = 0; k < d; ++k) g[k] = (x[k] - c[k]) / nr;
-      return;
+      case kPlane:
+        for (int k = 0; k < d; ++k) g[k] = nrm[k];
+        return;
+      case kEllipsoid: {
+        double y[3];
+        body(x, y);
+        double s = 0.0;
+        for (int i = 0; i < 3; ++i) {
+          double t = y[i] / ax[i];
+          s = (i == 0) ? t * t : s + t * t;
+        }
+        double q = std::sqrt(s), gy[3];
+        for (int i = 0; i < 3; ++i) gy[i] = y[i] / (ax[i] * ax[i]) / q;
+        for (int j = 0; j < 3; ++j) g[j] = R[j] * gy[0] + R[3 + j] * gy[1] + R[6 + j] * gy[2];
+        return;
+      }
+      case kTorus: {
+        double y[3];
+        body(x, y);
+        double rho = std::sqrt(y[0] * y[0] + y[1] * y[1]);
+        double t = rho - major;
+        double q = std::sqrt(t * t + y[2] * y[2]);
+        double gy[3] = {t / q * y[0] / rho, t / q * y[1] / rho, y[2] / q};
+        for (int j = 0; j < 3; ++j) g[j] = R[j] * gy[0] + R[3 + j] * gy[1] + R[6 + j] * gy[2];
+        return;
+      }
+      default: {
+        double dx = x[0] - c[0], dy = x[1] - c[1];
+        double r2 = dx * dx + dy * dy, rho = std::sqrt(r2), th = std::atan2(dy, dx);
+        double s = amp * lobes * std::sin(lobes * (th - phase));
+        g[0] = dx / rho - s * dy / r2;
+        g[1] = dy / rho + s * dx / r2;
+        return;
+      }
     }
-    for (int k = 0; k < d; ++k) g[k] = nrm[k];
   }
 
-  // exact min / max of phi over a closed (possibly degenerate) box
-  void box_minmax(const double* lo, const double* hi, double& mn, double& mx) const {
-    if (kind == 0) {
-      double s0 = 0.0, s1 = 0.0;
-      for (int k = 0; k < d; ++k) {
-        double a = lo[k] - c[k], b = hi[k] - c[k];
-        double nearv = a > 0 ? a : (b < 0 ? -b : 0.0);
-        double farv = std::max(std::fabs(a), std::fabs(b));
-        s0 = s0 + nearv * nearv;
-        s1 = s1 + farv * farv;
-      }
-      mn = std::sqrt(s0) - r;
-      mx = std::sqrt(s1) - r;
-      return;
-    }
-    mn = -off;
-    mx = -off;
+  // exact min / max of |x - c| over a box
+  void box_dist(const double* lo, const double* hi, double& dmin, double& dmax) const {
+    double s0 = 0.0, s1 = 0.0;
     for (int k = 0; k < d; ++k) {
-      double u = nrm[k] * lo[k], v = nrm[k] * hi[k];
-      mn += std::min(u, v);
-      mx += std::max(u, v);
+      double a = lo[k] - c[k], b = hi[k] - c[k];
+      double nearv = a > 0 ? a : (b < 0 ? -b : 0.0);
+      double farv = std::max(std::fabs(a), std::fabs(b));
+      s0 = s0 + nearv * nearv;
+      s1 = s1 + farv * farv;
+    }
+    dmin = std::sqrt(s0);
+    dmax = std::sqrt(s1);
+  }
+
+  void body_iv(const double* lo, const double* hi, Iv* y) const {
+    Iv D[3] = {{lo[0] - c[0], hi[0] - c[0]}, {lo[1] - c[1], hi[1] - c[1]}, {lo[2] - c[2], hi[2] - c[2]}};
+    for (int i = 0; i < 3; ++i) {
+      Iv t = iv_scale(R[3 * i + 0], D[0]);
+      t = iv_add(t, iv_scale(R[3 * i + 1], D[1]));
+      t = iv_add(t, iv_scale(R[3 * i + 2], D[2]));
+      y[i] = t;
     }
   }
 
-  // true when d phi / d x_k keeps one strict sign on the box
+  bool flower_contains_c(const double* lo, const double* hi) const {
+    return lo[0] <= c[0] && c[0] <= hi[0] && lo[1] <= c[1] && c[1] <= hi[1];
+  }
+  // range of the polar angle over a box not containing c
+  Iv flower_theta(const double* lo, const double* hi) const {
+    double xs[2] = {lo[0] - c[0], hi[0] - c[0]}, ys[2] = {lo[1] - c[1], hi[1] - c[1]};
+    bool wrap = xs[1] < 0.0 && ys[0] <= 0.0 && 0.0 <= ys[1];
+    double mn = 1e300, mx = -1e300;
+    for (int i = 0; i < 2; ++i)
+      for (int j = 0; j < 2; ++j) {
+        double a = std::atan2(ys[j], xs[i]);
+        if (wrap && a < 0.0) a += 2.0 * M_PI;
+        mn = std::min(mn, a);
+        mx = std::max(mx, a);
+      }
+    return {mn, mx};
+  }
+
+  void natural(const double* lo, const double* hi, double& mn, double& mx) const {
+    if (kind == kEllipsoid) {
+      Iv y[3];
+      body_iv(lo, hi, y);
+      Iv s = iv_sqr(iv_scale(1.0 / ax[0], y[0]));
+      s = iv_add(s, iv_sqr(iv_scale(1.0 / ax[1], y[1])));
+      s = iv_add(s, iv_sqr(iv_scale(1.0 / ax[2], y[2])));
+      Iv q = iv_sqrt(s);
+      mn = q.lo - 1.0;
+      mx = q.hi - 1.0;
+    } else if (kind == kTorus) {
+      Iv y[3];
+      body_iv(lo, hi, y);
+      Iv rho = iv_sqrt(iv_add(iv_sqr(y[0]), iv_sqr(y[1])));
+      Iv t{rho.lo - major, rho.hi - major};
+      Iv q = iv_sqrt(iv_add(iv_sqr(t), iv_sqr(y[2])));
+      mn = q.lo - r;
+      mx = q.hi - r;
+    } else {  // flower
+      double dmin, dmax;
+      box_dist(lo, hi, dmin, dmax);
+      Iv cw{-1.0, 1.0};
+      if (!flower_contains_c(lo, hi)) {
+        Iv th = flower_theta(lo, hi);
+        cw = iv_cos(Iv{lobes * (th.lo - phase), lobes * (th.hi - phase)});
+      }
+      mn = dmin - (r + amp * cw.hi);
+      mx = dmax - (r + amp * cw.lo);
+    }
+  }
+
+  void refined(const double* lo, const double* hi, int depth, double& mn, double& mx) const {
+    natural(lo, hi, mn, mx);
+    if (!(mn < 0.0 && 0.0 < mx) || depth >= kBoxDepth) return;
+    int freed[3], nf = 0;
+    for (int k = 0; k < d; ++k)
+      if (hi[k] > lo[k]) freed[nf++] = k;
+    mn = 1e300;
+    mx = -1e300;
+    for (int bits = 0; bits < (1 << nf); ++bits) {
+      double clo[3] = {lo[0], lo[1], lo[2]}, chi[3] = {hi[0], hi[1], hi[2]};
+      for (int i = 0; i < nf; ++i) {
+        int k = freed[i];
+        double mid = 0.5 * (lo[k] + hi[k]);
+        if ((bits >> i) & 1)
+          clo[k] = mid;
+        else
+          chi[k] = mid;
+      }
+      double a, b;
+      refined(clo, chi, depth + 1, a, b);
+      mn = std::min(mn, a);
+      mx = std::max(mx, b);
+    }
+  }
+
+  // bounds of phi over a closed (possibly degenerate) box
+  void box_minmax(const double* lo, const double* hi, double& mn, double& mx) const {
+    if (kind == kSphere) {
+      double dmin, dmax;
+      box_dist(lo, hi, dmin, dmax);
+      mn = dmin - r;
+      mx = dmax - r;
+      return;
+    }
+    if (kind == kPlane) {
+      mn = -off;
+      mx = -off;
+      for (int k = 0; k < d; ++k) {
+        double u = nrm[k] * lo[k], v = nrm[k] * hi[k];
+        mn += std::min(u, v);
+        mx += std::max(u, v);
+      }
+      return;
+    }
+    refined(lo, hi, 0, mn, mx);
+  }
+
+  // true when d phi / d x_k provably keeps one strict sign on the box
   bool monotone_in(int k, const double* lo, const double* hi) const {
-    if (kind == 0) return c[k] < lo[k] || c[k] > hi[k];
-    return nrm[k] != 0.0;
+    switch (kind) {
+      case kSphere: return c[k] < lo[k] || c[k] > hi[k];
+      case kPlane: return nrm[k] != 0.0;
+      case kEllipsoid: {
+        Iv y[3];
+        body_iv(lo, hi, y);
+        Iv t = iv_scale(R[k] / (ax[0] * ax[0]), y[0]);
+        t = iv_add(t, iv_scale(R[3 + k] / (ax[1] * ax[1]), y[1]));
+        t = iv_add(t, iv_scale(R[6 + k] / (ax[2] * ax[2]), y[2]));
+        return t.lo > 0.0 || t.hi < 0.0;
+      }
+      case kTorus: {
+        Iv y[3];
+        body_iv(lo, hi, y);
+        Iv rho2 = iv_add(iv_sqr(y[0]), iv_sqr(y[1]));
+        if (rho2.lo <= 0.0) return false;
+        Iv rho = iv_sqrt(rho2);
+        Iv t{rho.lo - major, rho.hi - major};
+        Iv w = iv_add(iv_scale(R[k], y[0]), iv_scale(R[3 + k], y[1]));
+        Iv a = iv_mul(iv_div(t, rho), w);
+        Iv sm = iv_add(a, iv_scale(R[6 + k], y[2]));
+        return sm.lo > 0.0 || sm.hi < 0.0;
+      }
+      default: {
+        if (flower_contains_c(lo, hi)) return false;
+        Iv dx{lo[0] - c[0], hi[0] - c[0]}, dy{lo[1] - c[1], hi[1] - c[1]};
+        double dmin, dmax;
+        box_dist(lo, hi, dmin, dmax);
+        Iv th = flower_theta(lo, hi);
+        Iv sw = iv_scale(amp * lobes, iv_sin(Iv{lobes * (th.lo - phase), lobes * (th.hi - phase)}));
+        Iv rho{dmin, dmax};
+        Iv v = (k == 0) ? iv_sub(iv_mul(dx, rho), iv_mul(sw, dy)) : iv_add(iv_mul(dy, rho), iv_mul(sw, dx));
+        return v.lo > 0.0 || v.hi < 0.0;
+      }
+    }
   }
 };
 

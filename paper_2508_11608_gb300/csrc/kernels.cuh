@@ -52,10 +52,12 @@ struct FaceGeo {
 
 template <int DIM, int P, typename T>
 __global__ void __launch_bounds__(128) k_face_moments(OpArgs<T> A, const T* __restrict__ x,
-                                                      const int* __restrict__ faces, int nfaces) {
+                                                      const int* __restrict__ faces,
+                                                      const int* __restrict__ ids, int nfaces) {
   constexpr int NT = FaceGeo<DIM, P>::NT;
-  const int f = blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= nfaces) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nfaces) return;
+  const int f = ids ? ids[i] : i;
   const int packed = faces[f], k = packed % DIM;
   int c = packed / DIM, lc[3] = {0, 0, 0};
 #pragma unroll
@@ -244,10 +246,11 @@ __device__ __forceinline__ int lat_index(const int* c, int n) {
 template <int DIM, int P, typename T>
 __device__ __forceinline__ void patch_rows(const OpArgs<T>& A, const T* __restrict__ x, const int* v,
                                            const uint16_t* __restrict__ tgt, int m,
+                                           const int* __restrict__ fofs, const int* __restrict__ fent,
                                            PatchScratch<DIM, P, T>& S, const T* __restrict__ sK,
                                            int lane) {
   using G = PatchGeo<DIM, P>;
-  constexpr int C = G::C, NB = G::NB;
+  constexpr int C = G::C, NB = G::NB, NTF = FaceGeo<DIM, P>::NT;
   const int N = A.N, n = A.n;
   for (int e = lane; e < G::NCL; e += 32) {
     int u = e, c[3] = {0, 0, 0};
@@ -302,12 +305,11 @@ __device__ __forceinline__ void patch_rows(const OpArgs<T>& A, const T* __restri
   }
   __syncwarp();
   for (int e = lane; e < m; e += 32) {
-    int o[3] = {0, 0, 0}, idx[3] = {0, 0, 0}, u = tgt[e];
+    int o[3] = {0, 0, 0}, u = tgt[e];
 #pragma unroll
     for (int k = 0; k < DIM; ++k) {
       o[k] = u % C;
       u /= C;
-      idx[k] = P * (v[k] - 1) + o[k];
     }
     T acc = T(0);
     for (int s = 0; s < G::NCELL; ++s) {
@@ -327,7 +329,14 @@ __device__ __forceinline__ void patch_rows(const OpArgs<T>& A, const T* __restri
       if (!(A.cflag[cell] & kActive)) continue;
       acc += S.part[s][j];
     }
-    S.r[e] = acc + node_faces<DIM, P, T>(A, idx);
+    const int f0 = fofs[e], f1 = fofs[e + 1];
+    for (int q = f0; q < f1; ++q) {
+      const int ent = fent[q], il = ent & 7;
+      const T* g = A.G + (size_t)(ent >> 3) / NTF * (P * NTF) + (ent >> 3) % NTF;
+#pragma unroll
+      for (int mm = 0; mm < P; ++mm) acc += A.dvec[mm][il] * g[mm * NTF];
+    }
+    S.r[e] = acc;
   }
   __syncwarp();
 }
@@ -656,6 +665,8 @@ __global__ void __launch_bounds__(32 * WARPS) k_cut_solve(OpArgs<T> A, const T* 
                                                           const int64_t* __restrict__ ioff,
                                                           const uint16_t* __restrict__ members,
                                                           const int* __restrict__ mnode,
+                                                          const int* __restrict__ fofs,
+                                                          const int* __restrict__ fent,
                                                           const T* __restrict__ inv,
                                                           T* __restrict__ dbuf, int npatch) {
   constexpr int NB = Shape<DIM, P>::NB;
@@ -674,7 +685,7 @@ __global__ void __launch_bounds__(32 * WARPS) k_cut_solve(OpArgs<T> A, const T* 
   }
   const int m = cnt[pidx], mo = moff[pidx];
   PatchScratch<DIM, P, T>& S = sS[w];
-  patch_rows<DIM, P, T>(A, x, v, members + mo, m, S, sK, lane);
+  patch_rows<DIM, P, T>(A, x, v, members + mo, m, fofs + mo, fent, S, sK, lane);
   for (int e = lane; e < m; e += 32) S.r[e] = b[mnode[mo + e]] - S.r[e];
   __syncwarp();
   const T* Ai = inv + ioff[pidx];

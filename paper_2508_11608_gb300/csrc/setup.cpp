@@ -556,6 +556,58 @@ void build_level(const SetupParams& prm, const RefTables& R, int N, HostLevel& L
       }
     }
     L.inv.assign(ioff, 0.0);
+    // ghost-face entries of every cut-patch DoF (the faces whose two cells
+    // contain the node), and per colour the faces these rows need
+    {
+      const int NTf = ipow(p + 1, d - 1);
+      L.fofs.assign(L.member_node.size() + 1, 0);
+      L.cf_start.assign(ncol + 1, 0);
+      std::vector<uint8_t> need(L.ghost_faces.size(), 0);
+      size_t gm = 0;
+      for (int col = 0; col < ncol; ++col) {
+        std::fill(need.begin(), need.end(), 0);
+        for (int j = L.cut_start[col]; j < L.cut_start[col + 1]; ++j)
+          for (int e = 0; e < L.cut_n[j]; ++e, ++gm) {
+            int64_t t = L.member_node[gm];
+            int idx[3] = {0, 0, 0};
+            for (int k = 0; k < d; ++k) {
+              idx[k] = (int)(t % n);
+              t /= n;
+            }
+            int cc[3][2], lcl[3][2], nopt[3] = {1, 1, 1};
+            for (int k = 0; k < d; ++k) nopt[k] = cells_of(idx[k], p, N, cc[k], lcl[k]);
+            for (int k = 0; k < d; ++k) {
+              const int a = idx[k] / p, r = idx[k] - a * p;
+              int Llo = (r == 0) ? a - 2 : a - 1, Lhi = a;
+              Llo = std::max(Llo, 0);
+              Lhi = std::min(Lhi, N - 2);
+              int td[2] = {0, 0}, q = 0;
+              for (int jj = 0; jj < d; ++jj)
+                if (jj != k) td[q++] = jj;
+              const int n0 = nopt[td[0]], n1 = (d == 3) ? nopt[td[1]] : 1;
+              for (int Lk = Llo; Lk <= Lhi; ++Lk)
+                for (int u0 = 0; u0 < n0; ++u0)
+                  for (int u1 = 0; u1 < n1; ++u1) {
+                    int c[3] = {0, 0, 0};
+                    c[k] = Lk;
+                    c[td[0]] = cc[td[0]][u0];
+                    if (d == 3) c[td[1]] = cc[td[1]][u1];
+                    int64_t cell = c[0] + (int64_t)N * (c[1] + (d == 3 ? (int64_t)N * c[2] : 0));
+                    const int id = L.face_id[(size_t)cell * d + k];
+                    if (id < 0) continue;
+                    int tt = idx[td[0]] - p * c[td[0]];
+                    if (d == 3) tt += (p + 1) * (idx[td[1]] - p * c[td[1]]);
+                    L.fent.push_back(((id * NTf) + tt) * 8 + (idx[k] - p * Lk));
+                    need[id] = 1;
+                  }
+            }
+            L.fofs[gm + 1] = (int)L.fent.size();
+          }
+        for (size_t f = 0; f < need.size(); ++f)
+          if (need[f]) L.cfaces.push_back((int)f);
+        L.cf_start[col + 1] = (int)L.cfaces.size();
+      }
+    }
     // work model of the cut-patch solve (what the kernel computes per patch):
     // cell rows 2 NB per (active patch cell, target in it); ghost-face moments
     // 2 (2p+1) p NT + 2 p NT^2 per ghost face; 2 p per (target, ghost face);

@@ -53,6 +53,11 @@ struct HostLevel {
   std::vector<int> cut_start;
   std::vector<uint16_t> members;  // closure-local node index per cut-patch DoF
   std::vector<int> member_node;   // lattice index per cut-patch DoF
+  // ghost-face terms of each cut-patch DoF's row: entries fent[fofs[i] ..
+  // fofs[i+1]) = (face id * (p+1)^(d-1) + t) * 8 + i_k, and per colour the
+  // ghost faces those rows need (colour c: cfaces[cf_start[c] .. cf_start[c+1]))
+  std::vector<int> fofs, fent;
+  std::vector<int> cfaces, cf_start;
   std::vector<double> inv;        // explicit FP64 inverses A_j^{-1}, row-major
   // algorithmic work per launch, used to report achieved FLOP/s and bytes:
   // per colour of the cut-patch solve and of the interior-patch step

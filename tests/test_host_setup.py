@@ -5,15 +5,33 @@ against the oracle, on CPU through cf_setup_host.  No device is touched."""
 import numpy as np
 import pytest
 
-from oracle import Hierarchy, Sphere
+from oracle import Hierarchy
+from oracle.levelset import make_levelset
 
 cm = pytest.importorskip("paper_2508_11608_gb300")
 
+
+def _rot(a, b):
+    import math
+    ca, sa, cb, sb = math.cos(a), math.sin(a), math.cos(b), math.sin(b)
+    Rz = np.array([[ca, -sa, 0], [sa, ca, 0], [0, 0, 1]])
+    Rx = np.array([[1, 0, 0], [0, cb, -sb], [0, sb, cb]])
+    return (Rz @ Rx).tolist()
+
+
+SPH2 = {"kind": "sphere", "center": [0.031, 0.017], "radius": 0.7}
+SPH3 = {"kind": "sphere", "center": [0.05, 0.03, 0.02], "radius": 0.7}
 CASES = {
-    "disk_q2": dict(dim=2, N=32, L=3, p=2, c=[0.031, 0.017], r=0.7),
-    "disk_q3": dict(dim=2, N=16, L=2, p=3, c=[0.031, 0.017], r=0.7),
-    "ball_q2": dict(dim=3, N=8, L=2, p=2, c=[0.05, 0.03, 0.02], r=0.7),
-    "ball_q1": dict(dim=3, N=16, L=3, p=1, c=[0.05, 0.03, 0.02], r=0.7),
+    "disk_q2": dict(dim=2, N=32, L=3, p=2, ls=SPH2),
+    "disk_q3": dict(dim=2, N=16, L=2, p=3, ls=SPH2),
+    "ball_q2": dict(dim=3, N=8, L=2, p=2, ls=SPH3),
+    "ball_q1": dict(dim=3, N=16, L=3, p=1, ls=SPH3),
+    "flower_q2": dict(dim=2, N=32, L=3, p=2, ls={"kind": "flower", "center": [0.02, -0.03], "lobes": 5,
+                                                 "phase": 0.4}),
+    "ellipsoid_q2": dict(dim=3, N=8, L=2, p=2, ls={"kind": "ellipsoid", "center": [0.03, -0.02, 0.01],
+                                                   "axes": [0.7, 0.5, 0.45], "rot": _rot(0.3, 0.5)}),
+    "torus_q2": dict(dim=3, N=16, L=2, p=2, ls={"kind": "torus", "center": [0.02, 0.01, -0.03],
+                                                "rot": _rot(0.4, 0.7), "major": 0.6, "minor": 0.2}),
 }
 
 
@@ -21,10 +39,10 @@ CASES = {
 def pair(request):
     k = CASES[request.param]
     try:
-        pb = cm.Problem(k["dim"], k["N"], k["L"], k["p"], center=k["c"], radius=k["r"], host_only=True)
+        pb = cm.Problem(k["dim"], k["N"], k["L"], k["p"], levelset=k["ls"], host_only=True)
     except ImportError as e:
         pytest.skip(str(e))
-    H = Hierarchy(Sphere(k["c"], k["r"]), k["dim"], k["N"], k["p"], k["L"])
+    H = Hierarchy(make_levelset(k["ls"]), k["dim"], k["N"], k["p"], k["L"])
     return pb, H, k
 
 
