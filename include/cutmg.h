@@ -183,6 +183,28 @@ cf_status cf_coarse_solve(cf_problem* pb, int precision, const double* d_b0,
  *  - d_b0 / d_x0: FP64 device arrays of cf_level_n_dofs(pb, 0) entries. */
 cf_status cf_coarse_solve_noalloc(cf_problem* pb, const double* d_b0, double* d_x0, void* stream);
 
+/* ---- batched form -----------------------------------------------------------
+ * Many independent problems (any geometries, mesh sizes and degrees) solved
+ * together: problems with the same (dim, degree) share every launch of the
+ * hot path, one persistent grid-stride launch per (V-cycle depth, colour,
+ * step) over a work list of (problem, patch) pairs, with tile shapes chosen
+ * by a timing autotuner at cf_batch_create.  Each problem runs its own CG
+ * (own scalars, own convergence; converged problems drop out of the work
+ * lists) and performs the same floating-point operations as cf_solve on it
+ * alone.  The batch references the problems; they must outlive it and must
+ * not be used on other streams while a batched solve runs. */
+typedef struct cf_batch cf_batch;
+/* Errors: CF_EINVAL (empty list, problems on different devices or host-only,
+ * different n_c within one (dim, degree) group). */
+cf_status cf_batch_create(cf_problem* const* problems, int count, cf_batch** out);
+/* d_b[i], d_x[i]: FP64 device vectors of problem i (host arrays of count
+ * pointers); infos: host array of count entries (solve_ms = the batch's time).
+ * Returns CF_ENOCONV if any problem reached maxit. */
+cf_status cf_batch_solve(cf_batch* bt, int precision, const double* const* d_b, double* const* d_x,
+                         double rtol, int maxit, cf_info* infos, void* stream);
+int64_t cf_batch_launch_count(const cf_batch* bt);
+void cf_batch_destroy(cf_batch* bt);
+
 /* ---- instrumentation ----------------------------------------------------- */
 /* Number of kernel launches this handle has issued (all calls). */
 int64_t cf_launch_count(const cf_problem* pb);

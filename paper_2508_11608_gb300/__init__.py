@@ -195,3 +195,41 @@ class Problem:
             cut.append((v.value, nodes[:k].copy(),
                         inv[:k * k].reshape(k, k).copy() if with_inverse else None))
         return inter, cut
+
+
+class Batch:
+    """Many problems solved together (cf_batch_*): one launch per V-cycle
+    depth, colour and step for all problems of the same (dim, degree)."""
+
+    def __init__(self, problems):
+        self._lib = _lib.load()
+        self.problems = list(problems)
+        arr = (ctypes.c_void_p * len(self.problems))(*[p._h.value for p in self.problems])
+        h = ctypes.c_void_p()
+        check(self._lib.cf_batch_create(arr, len(self.problems), ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.cf_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def launch_count(self):
+        return self._lib.cf_batch_launch_count(self._h)
+
+    def solve(self, bs, xs, rtol=1e-8, maxit=500, precision=CF_FP64, stream=None, allow_noconv=False):
+        k = len(self.problems)
+        pb = (ctypes.c_void_p * k)(*[b.data_ptr() for b in bs])
+        px = (ctypes.c_void_p * k)(*[x.data_ptr() for x in xs])
+        infos = (_lib.cf_info * k)()
+        st = self._lib.cf_batch_solve(self._h, precision, pb, px, rtol, maxit, infos, _stream(stream))
+        if not (allow_noconv and st == _lib.CF_ENOCONV):
+            check(st)
+        return [{"iterations": i.iterations, "rel_residual": i.rel_residual,
+                 "true_rel_residual": i.true_rel_residual, "solve_ms": i.solve_ms} for i in infos]

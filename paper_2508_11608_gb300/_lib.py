@@ -22,6 +22,7 @@ EXPORTED = [
     "cf_level_restrict", "cf_level_prolongate", "cf_coarse_solve", "cf_setup_host", "cf_host_rhs",
     "cf_host_cell_matrix", "cf_host_patch_counts", "cf_host_interior_patch", "cf_host_cut_patch",
     "cf_launch_count", "cf_profile_start", "cf_profile_read", "cf_coarse_solve_noalloc",
+    "cf_batch_create", "cf_batch_solve", "cf_batch_launch_count", "cf_batch_destroy",
 ]
 
 
@@ -96,6 +97,12 @@ def load():
     lib.cf_host_interior_patch.argtypes = [P, I, ctypes.c_int64, P]
     lib.cf_host_cut_patch.argtypes = [P, I, ctypes.c_int64, P, P, P, P]
     lib.cf_coarse_solve_noalloc.argtypes = [P, P, P, V]
+    lib.cf_batch_create.argtypes = [P, I, ctypes.POINTER(P)]
+    lib.cf_batch_solve.argtypes = [P, I, P, P, D, I, P, V]
+    lib.cf_batch_launch_count.argtypes = [P]
+    lib.cf_batch_launch_count.restype = ctypes.c_int64
+    lib.cf_batch_destroy.argtypes = [P]
+    lib.cf_batch_destroy.restype = None
     lib.cf_launch_count.argtypes = [P]
     lib.cf_launch_count.restype = ctypes.c_int64
     lib.cf_profile_start.argtypes = [P, I]

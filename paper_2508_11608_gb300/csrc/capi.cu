@@ -9,6 +9,7 @@
 #include <string>
 
 #include "../../include/cutmg.h"
+#include "batch_api.hpp"
 #include "engine_api.hpp"
 #include "setup.hpp"
 
@@ -19,6 +20,12 @@ struct cf_problem {
   std::unique_ptr<EngineBase> eng;
   int precision = CF_FP64;
   int device = 0;
+};
+
+struct cf_batch {
+  std::vector<std::unique_ptr<BatchGroupBase>> groups;
+  std::vector<std::vector<int>> members;  // input index of each group member
+  int count = 0;
 };
 
 namespace {
@@ -61,6 +68,12 @@ cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 }  // namespace
 
 cf_status cutmg_set_error(cf_status s, const char* msg) { return fail(s, msg); }
+
+#define CUTMG_CHECK(expr)                                                                   \
+  do {                                                                                     \
+    cudaError_t e__ = (expr);                                                              \
+    if (e__ != cudaSuccess) throw CudaError(std::string(#expr) + ": " + cudaGetErrorString(e__)); \
+  } while (0)
 
 extern "C" {
 
@@ -289,6 +302,129 @@ cf_status cf_profile_read(cf_problem* pb, double* ms, int64_t* launches, double*
   if (no_device(pb) || !ms || !launches || !flops || !bytes) return fail(CF_EINVAL, "bad argument");
   return guarded([&] { pb->eng->profile_read(ms, launches, flops, bytes); });
 }
+
+cf_status cf_batch_create(cf_problem* const* problems, int count, cf_batch** out) {
+  if (!problems || count < 1 || !out) return fail(CF_EINVAL, "empty batch");
+  *out = nullptr;
+  int dev = -1;
+  for (int i = 0; i < count; ++i) {
+    if (no_device(problems[i])) return fail(CF_EINVAL, "null or host-only problem in batch");
+    if (i == 0) dev = problems[i]->device;
+    if (problems[i]->device != dev) return fail(CF_EINVAL, "problems on different devices");
+  }
+  std::unique_ptr<cf_batch> bt(new cf_batch());
+  bt->count = count;
+  cf_status st = guarded([&] {
+    for (int dim = 2; dim <= 3; ++dim)
+      for (int deg = 1; deg <= 3; ++deg) {
+        std::vector<EngineBase*> inst;
+        std::vector<int> idx;
+        int n_c = -1;
+        for (int i = 0; i < count; ++i) {
+          const auto& prm = problems[i]->H.prm;
+          if (prm.dim != dim || prm.degree != deg) continue;
+          if (n_c >= 0 && prm.n_c != n_c) throw std::invalid_argument("n_c differs within a batch group");
+          n_c = prm.n_c;
+          inst.push_back(problems[i]->eng.get());
+          idx.push_back(i);
+        }
+        if (inst.empty()) continue;
+        bt->groups.push_back(dim == 2 ? make_batch_group_d2(deg, inst, n_c) : make_batch_group_d3(deg, inst, n_c));
+        bt->members.push_back(idx);
+      }
+    cudaStream_t s;
+    CUTMG_CHECK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    for (auto& g : bt->groups) g->autotune(s);
+    CUTMG_CHECK(cudaStreamSynchronize(s));
+    cudaStreamDestroy(s);
+  });
+  if (st != CF_OK) return st;
+  *out = bt.release();
+  return CF_OK;
+}
+
+cf_status cf_batch_solve(cf_batch* bt, int precision, const double* const* d_b, double* const* d_x, double rtol,
+                         int maxit, cf_info* infos, void* stream) {
+  if (!bt || !d_b || !d_x || bad_prec(precision)) return fail(CF_EINVAL, "bad argument");
+  if (!(rtol > 0.0) || maxit < 1) return fail(CF_EINVAL, "rtol must be positive and maxit >= 1");
+  bool noconv = false;
+  cf_status st = guarded([&] {
+    cudaStream_t s = S(stream);
+    cudaEvent_t e0, e1;
+    CUTMG_CHECK(cudaEventCreate(&e0));
+    CUTMG_CHECK(cudaEventCreate(&e1));
+    CUTMG_CHECK(cudaEventRecord(e0, s));
+    const size_t G = bt->groups.size();
+    std::vector<std::vector<double>> bn(G), rr(G);
+    for (size_t g = 0; g < G; ++g) {
+      std::vector<const double*> b;
+      for (int i : bt->members[g]) b.push_back(d_b[i]);
+      bt->groups[g]->start(precision, b.data(), s);
+      bn[g].assign(bt->members[g].size(), 0.0);
+      rr[g].assign(bt->members[g].size(), 0.0);
+      bt->groups[g]->bnorms(bn[g].data());
+    }
+    int it = 0;
+    while (it < maxit) {
+      bool any = false;
+      for (size_t g = 0; g < G; ++g)
+        if (bt->groups[g]->active() > 0) {
+          bt->groups[g]->half_a(s);
+          any = true;
+        }
+      if (!any) break;
+      ++it;
+      bool left = false;
+      for (size_t g = 0; g < G; ++g) {
+        if (bt->groups[g]->active() == 0) continue;
+        bt->groups[g]->read_rr(rr[g].data(), s);
+        std::vector<int> done;
+        for (size_t i = 0; i < rr[g].size(); ++i)
+          if (!(std::sqrt(rr[g][i]) > rtol * bn[g][i])) done.push_back((int)i);
+        bt->groups[g]->deactivate(done);
+        if (bt->groups[g]->active() > 0) left = true;
+      }
+      if (!left) break;
+      for (size_t g = 0; g < G; ++g)
+        if (bt->groups[g]->active() > 0) bt->groups[g]->half_b(precision, s);
+    }
+    CUTMG_CHECK(cudaEventRecord(e1, s));
+    CUTMG_CHECK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CUTMG_CHECK(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (size_t g = 0; g < G; ++g) {
+      const size_t n = bt->members[g].size();
+      std::vector<double*> x;
+      for (int i : bt->members[g]) x.push_back(d_x[i]);
+      std::vector<BatchInfo> inf(n);
+      bt->groups[g]->finish(x.data(), inf.data(), s);
+      for (size_t k = 0; k < n; ++k) {
+        const int i = bt->members[g][k];
+        if (inf[k].rel > rtol) noconv = true;
+        if (infos) {
+          infos[i].iterations = inf[k].iterations;
+          infos[i].rel_residual = inf[k].rel;
+          infos[i].true_rel_residual = inf[k].true_rel;
+          infos[i].solve_ms = ms;
+        }
+      }
+    }
+  });
+  if (st != CF_OK) return st;
+  if (noconv) return fail(CF_ENOCONV, "a problem of the batch reached maxit before the tolerance");
+  return CF_OK;
+}
+
+int64_t cf_batch_launch_count(const cf_batch* bt) {
+  if (!bt) return 0;
+  int64_t n = 0;
+  for (auto& g : bt->groups) n += g->launches();
+  return n;
+}
+
+void cf_batch_destroy(cf_batch* bt) { delete bt; }
 
 cf_status cf_host_rhs(const cf_problem* pb, double* h_b) {
   if (!pb || !h_b) return fail(CF_EINVAL, "null argument");

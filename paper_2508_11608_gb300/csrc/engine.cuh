@@ -11,6 +11,7 @@
 #include <map>
 #include <memory>
 #include <tuple>
+#include <type_traits>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -67,7 +68,11 @@ class DevPool {
 inline int blocks_for(int64_t n, int bs) { return (int)((n + bs - 1) / bs); }
 
 template <int DIM, int P>
+class BatchGroup;
+
+template <int DIM, int P>
 class Engine final : public EngineBase {
+  friend class BatchGroup<DIM, P>;
   static constexpr int NB = Shape<DIM, P>::NB;
   static constexpr int C = 2 * P + 1, M = 2 * P - 1;
   static constexpr int WARPS = 4;
@@ -345,6 +350,71 @@ class Engine final : public EngineBase {
     *rel = bn > 0 ? rn / bn : 0.0;
     *true_rel = bn > 0 ? tr / bn : 0.0;
     return it;
+  }
+
+  template <typename T>
+  std::vector<Typed<T>>& typed();
+
+  // descriptors of the separable transfer passes of level l (restriction
+  // l -> l-1 and prolongation l-1 -> l), as run by restrict_ and prolong
+  template <typename T, typename PD>
+  void pass_descs(int l, std::vector<PD>* rp, std::vector<PD>* pp, int i) {
+    auto& DD = typed<T>();
+    const Common& F = com_[l];
+    const Common& Cc = com_[l - 1];
+    Typed<T>& D = DD[l];
+    const int nf = F.n, nc = Cc.n, Wr = 4 * P + 1, Wp = P + 1;
+    auto set = [](PD& q, const void* in, void* out, int in0, int in1, int out0, int out1, int axis,
+                  const int* lo, const int* ext, const int* col, const void* wt, int W, const uint8_t* mask) {
+      q.in = in;
+      q.out = out;
+      q.in0 = in0;
+      q.in1 = in1;
+      q.out0 = out0;
+      q.out1 = out1;
+      q.axis = axis;
+      q.W = W;
+      for (int k = 0; k < 3; ++k) {
+        q.lo[k] = lo[k];
+        q.ext[k] = ext[k];
+      }
+      q.col = col;
+      q.wt = wt;
+      q.mask = mask;
+    };
+    if (DIM == 3) {
+      int lo1[3] = {Cc.bb_lo[0], F.bb_lo[1], F.bb_lo[2]};
+      int ex1[3] = {Cc.bb_hi[0] - Cc.bb_lo[0] + 1, F.bb_hi[1] - F.bb_lo[1] + 1, F.bb_hi[2] - F.bb_lo[2] + 1};
+      set(rp[0][i], D.r, D.t1, nf, nf, nc, nf, 0, lo1, ex1, F.res_col, D.res_w, Wr, nullptr);
+      int lo2[3] = {Cc.bb_lo[0], Cc.bb_lo[1], F.bb_lo[2]};
+      int ex2[3] = {ex1[0], Cc.bb_hi[1] - Cc.bb_lo[1] + 1, ex1[2]};
+      set(rp[1][i], D.t1, D.t2, nc, nf, nc, nc, 1, lo2, ex2, F.res_col, D.res_w, Wr, nullptr);
+      int lo3[3] = {Cc.bb_lo[0], Cc.bb_lo[1], Cc.bb_lo[2]};
+      int ex3[3] = {ex1[0], ex2[1], Cc.bb_hi[2] - Cc.bb_lo[2] + 1};
+      set(rp[2][i], D.t2, DD[l - 1].b, nc, nc, nc, nc, 2, lo3, ex3, F.res_col, D.res_w, Wr, Cc.nact);
+      int plo1[3] = {F.bb_lo[0], Cc.bb_lo[1], Cc.bb_lo[2]};
+      int pex1[3] = {F.bb_hi[0] - F.bb_lo[0] + 1, Cc.bb_hi[1] - Cc.bb_lo[1] + 1, Cc.bb_hi[2] - Cc.bb_lo[2] + 1};
+      set(pp[0][i], DD[l - 1].x, D.t3, nc, nc, nf, nc, 0, plo1, pex1, F.pro_col, D.pro_w, Wp, nullptr);
+      int plo2[3] = {F.bb_lo[0], F.bb_lo[1], Cc.bb_lo[2]};
+      int pex2[3] = {pex1[0], F.bb_hi[1] - F.bb_lo[1] + 1, pex1[2]};
+      set(pp[1][i], D.t3, D.t4, nf, nc, nf, nf, 1, plo2, pex2, F.pro_col, D.pro_w, Wp, nullptr);
+      int plo3[3] = {F.bb_lo[0], F.bb_lo[1], F.bb_lo[2]};
+      int pex3[3] = {pex1[0], pex2[1], F.bb_hi[2] - F.bb_lo[2] + 1};
+      set(pp[2][i], D.t4, D.x, nf, nf, nf, nf, 2, plo3, pex3, F.pro_col, D.pro_w, Wp, F.nact);
+    } else {
+      int lo1[3] = {Cc.bb_lo[0], F.bb_lo[1], 0};
+      int ex1[3] = {Cc.bb_hi[0] - Cc.bb_lo[0] + 1, F.bb_hi[1] - F.bb_lo[1] + 1, 1};
+      set(rp[0][i], D.r, D.t1, nf, nf, nc, nf, 0, lo1, ex1, F.res_col, D.res_w, Wr, nullptr);
+      int lo2[3] = {Cc.bb_lo[0], Cc.bb_lo[1], 0};
+      int ex2[3] = {ex1[0], Cc.bb_hi[1] - Cc.bb_lo[1] + 1, 1};
+      set(rp[1][i], D.t1, DD[l - 1].b, nc, nf, nc, nc, 1, lo2, ex2, F.res_col, D.res_w, Wr, Cc.nact);
+      int plo1[3] = {F.bb_lo[0], Cc.bb_lo[1], 0};
+      int pex1[3] = {F.bb_hi[0] - F.bb_lo[0] + 1, Cc.bb_hi[1] - Cc.bb_lo[1] + 1, 1};
+      set(pp[0][i], DD[l - 1].x, D.t3, nc, nc, nf, nc, 0, plo1, pex1, F.pro_col, D.pro_w, Wp, nullptr);
+      int plo2[3] = {F.bb_lo[0], F.bb_lo[1], 0};
+      int pex2[3] = {pex1[0], F.bb_hi[1] - F.bb_lo[1] + 1, 1};
+      set(pp[1][i], D.t3, D.x, nf, nc, nf, nf, 1, plo2, pex2, F.pro_col, D.pro_w, Wp, F.nact);
+    }
   }
 
  private:
@@ -766,5 +836,12 @@ class Engine final : public EngineBase {
     }
   }
 };
+
+template <int DIM, int P>
+template <typename T>
+std::vector<typename Engine<DIM, P>::template Typed<T>>& Engine<DIM, P>::typed() {
+  if constexpr (std::is_same<T, double>::value) return d64_;
+  else return d32_;
+}
 
 }  // namespace cutmg

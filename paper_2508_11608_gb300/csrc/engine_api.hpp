@@ -8,6 +8,7 @@
 #include <memory>
 #include <stdexcept>
 #include <string>
+#include <vector>
 
 namespace cutmg {
 
@@ -50,5 +51,9 @@ class EngineBase {
 
 std::unique_ptr<EngineBase> make_engine_d2(int degree, const Hierarchy& H);
 std::unique_ptr<EngineBase> make_engine_d3(int degree, const Hierarchy& H);
+
+class BatchGroupBase;
+std::unique_ptr<BatchGroupBase> make_batch_group_d2(int degree, const std::vector<EngineBase*>& inst, int n_c);
+std::unique_ptr<BatchGroupBase> make_batch_group_d3(int degree, const std::vector<EngineBase*>& inst, int n_c);
 
 }  // namespace cutmg

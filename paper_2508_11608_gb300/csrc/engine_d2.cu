@@ -1,5 +1,5 @@
 // Engines for two-dimensional problems, degrees 1..3.
-#include "engine.cuh"
+#include "batch.cuh"
 
 namespace cutmg {
 
@@ -8,6 +8,28 @@ std::unique_ptr<EngineBase> make_engine_d2(int degree, const Hierarchy& H) {
     case 1: return std::make_unique<Engine<2, 1>>(H);
     case 2: return std::make_unique<Engine<2, 2>>(H);
     case 3: return std::make_unique<Engine<2, 3>>(H);
+    default: throw std::invalid_argument("unsupported degree");
+  }
+}
+
+std::unique_ptr<BatchGroupBase> make_batch_group_d2(int degree, const std::vector<EngineBase*>& inst,
+                                                      int n_c) {
+  switch (degree) {
+    case 1: {
+      std::vector<Engine<2, 1>*> v;
+      for (EngineBase* e : inst) v.push_back(static_cast<Engine<2, 1>*>(e));
+      return std::make_unique<BatchGroup<2, 1>>(v, n_c);
+    }
+    case 2: {
+      std::vector<Engine<2, 2>*> v;
+      for (EngineBase* e : inst) v.push_back(static_cast<Engine<2, 2>*>(e));
+      return std::make_unique<BatchGroup<2, 2>>(v, n_c);
+    }
+    case 3: {
+      std::vector<Engine<2, 3>*> v;
+      for (EngineBase* e : inst) v.push_back(static_cast<Engine<2, 3>*>(e));
+      return std::make_unique<BatchGroup<2, 3>>(v, n_c);
+    }
     default: throw std::invalid_argument("unsupported degree");
   }
 }

@@ -1,5 +1,5 @@
 // Engines for three-dimensional problems, degrees 1..2.
-#include "engine.cuh"
+#include "batch.cuh"
 
 namespace cutmg {
 
@@ -7,6 +7,23 @@ std::unique_ptr<EngineBase> make_engine_d3(int degree, const Hierarchy& H) {
   switch (degree) {
     case 1: return std::make_unique<Engine<3, 1>>(H);
     case 2: return std::make_unique<Engine<3, 2>>(H);
+    default: throw std::invalid_argument("unsupported degree");
+  }
+}
+
+std::unique_ptr<BatchGroupBase> make_batch_group_d3(int degree, const std::vector<EngineBase*>& inst,
+                                                      int n_c) {
+  switch (degree) {
+    case 1: {
+      std::vector<Engine<3, 1>*> v;
+      for (EngineBase* e : inst) v.push_back(static_cast<Engine<3, 1>*>(e));
+      return std::make_unique<BatchGroup<3, 1>>(v, n_c);
+    }
+    case 2: {
+      std::vector<Engine<3, 2>*> v;
+      for (EngineBase* e : inst) v.push_back(static_cast<Engine<3, 2>*>(e));
+      return std::make_unique<BatchGroup<3, 2>>(v, n_c);
+    }
     default: throw std::invalid_argument("unsupported degree");
   }
 }

@@ -51,13 +51,9 @@ struct FaceGeo {
 };
 
 template <int DIM, int P, typename T>
-__global__ void __launch_bounds__(128) k_face_moments(OpArgs<T> A, const T* __restrict__ x,
-                                                      const int* __restrict__ faces,
-                                                      const int* __restrict__ ids, int nfaces) {
+__device__ __forceinline__ void face_moment_body(const OpArgs<T>& A, const T* __restrict__ x,
+                                                 const int* __restrict__ faces, int f) {
   constexpr int NT = FaceGeo<DIM, P>::NT;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nfaces) return;
-  const int f = ids ? ids[i] : i;
   const int packed = faces[f], k = packed % DIM;
   int c = packed / DIM, lc[3] = {0, 0, 0};
 #pragma unroll
@@ -104,6 +100,15 @@ __global__ void __launch_bounds__(128) k_face_moments(OpArgs<T> A, const T* __re
       }
       g[m * NT + t] = A.coef[m] * acc;
     }
+}
+
+template <int DIM, int P, typename T>
+__global__ void __launch_bounds__(128) k_face_moments(OpArgs<T> A, const T* __restrict__ x,
+                                                      const int* __restrict__ faces,
+                                                      const int* __restrict__ ids, int nfaces) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nfaces) return;
+  face_moment_body<DIM, P, T>(A, x, faces, ids ? ids[i] : i);
 }
 
 // sum over the ghost faces whose two cells contain node idx of (G_F x)(node)
@@ -252,17 +257,22 @@ __device__ __forceinline__ void patch_rows(const OpArgs<T>& A, const T* __restri
   using G = PatchGeo<DIM, P>;
   constexpr int C = G::C, NB = G::NB, NTF = FaceGeo<DIM, P>::NT;
   const int N = A.N, n = A.n;
-  for (int e = lane; e < G::NCL; e += 32) {
-    int u = e, c[3] = {0, 0, 0};
-    bool in = true;
+  constexpr int NROUND = (G::NCL + 31) / 32;
 #pragma unroll
-    for (int k = 0; k < DIM; ++k) {
-      c[k] = P * (v[k] - 1) + u % C;
-      u /= C;
-      if (c[k] < 0 || c[k] >= n) in = false;
+  for (int rr = 0; rr < NROUND; ++rr) {
+    const int e = lane + 32 * rr;
+    if (e < G::NCL) {
+      int u = e, c[3] = {0, 0, 0};
+      bool in = true;
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) {
+        c[k] = P * (v[k] - 1) + u % C;
+        u /= C;
+        if (c[k] < 0 || c[k] >= n) in = false;
+      }
+      S.x[e] = in ? x[lat_index<DIM>(c, n)] : T(0);
+      S.mem[e] = -1;
     }
-    S.x[e] = in ? x[lat_index<DIM>(c, n)] : T(0);
-    S.mem[e] = -1;
   }
   __syncwarp();
   for (int e = lane; e < m; e += 32) S.mem[tgt[e]] = (short)e;
@@ -330,11 +340,25 @@ __device__ __forceinline__ void patch_rows(const OpArgs<T>& A, const T* __restri
       acc += S.part[s][j];
     }
     const int f0 = fofs[e], f1 = fofs[e + 1];
-    for (int q = f0; q < f1; ++q) {
-      const int ent = fent[q], il = ent & 7;
-      const T* g = A.G + (size_t)(ent >> 3) / NTF * (P * NTF) + (ent >> 3) % NTF;
+    for (int q0 = f0; q0 < f1; q0 += 8) {
+      int ent[8];
 #pragma unroll
-      for (int mm = 0; mm < P; ++mm) acc += A.dvec[mm][il] * g[mm * NTF];
+      for (int u = 0; u < 8; ++u) ent[u] = (q0 + u < f1) ? fent[q0 + u] : -1;
+      T gv[8][P];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (ent[u] < 0) continue;
+        const T* g = A.G + (size_t)(ent[u] >> 3) / NTF * (P * NTF) + (ent[u] >> 3) % NTF;
+#pragma unroll
+        for (int mm = 0; mm < P; ++mm) gv[u][mm] = g[mm * NTF];
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (ent[u] < 0) continue;
+        const int il = ent[u] & 7;
+#pragma unroll
+        for (int mm = 0; mm < P; ++mm) acc += A.dvec[mm][il] * gv[u][mm];
+      }
     }
     S.r[e] = acc;
   }
@@ -352,17 +376,12 @@ __device__ __forceinline__ void stage_kref(const T* __restrict__ g, T* s) {
 // P^DIM nodes P a + alpha, alpha in [0, P)^DIM, and sums their rows over the
 // 2^DIM cells with the uncut element matrix.
 template <int DIM, int P, typename T>
-__global__ void __launch_bounds__(128) k_apply_bulk(OpArgs<T> A, const T* __restrict__ x,
-                                                    const T* __restrict__ b, T* __restrict__ y,
-                                                    const int* __restrict__ pos, int npos) {
+__device__ __forceinline__ void bulk_body(const OpArgs<T>& A, const T* __restrict__ x,
+                                          const T* __restrict__ b, T* __restrict__ y, int q,
+                                          const T* __restrict__ sK) {
   constexpr int NB = Shape<DIM, P>::NB;
   constexpr int NO = Shape<DIM, P>::NO;
-  __shared__ T sK[NB * NB];
-  stage_kref<NB>(A.Kref, sK);
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= npos) return;
   const int np = A.N + 1, n = A.n;
-  int q = pos[t];
   int a[3] = {0, 0, 0};
 #pragma unroll
   for (int k = 0; k < DIM; ++k) {
@@ -429,8 +448,34 @@ __global__ void __launch_bounds__(128) k_apply_bulk(OpArgs<T> A, const T* __rest
   }
 }
 
+template <int DIM, int P, typename T>
+__global__ void __launch_bounds__(128) k_apply_bulk(OpArgs<T> A, const T* __restrict__ x,
+                                                    const T* __restrict__ b, T* __restrict__ y,
+                                                    const int* __restrict__ pos, int npos) {
+  constexpr int NB = Shape<DIM, P>::NB;
+  __shared__ T sK[NB * NB];
+  stage_kref<NB>(A.Kref, sK);
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= npos) return;
+  bulk_body<DIM, P, T>(A, x, b, y, pos[t], sK);
+}
+
 // Same output for the remaining active nodes (near the boundary), one thread
 // per node: its cells' rows and its ghost faces (moments precomputed).
+template <int DIM, int P, typename T>
+__device__ __forceinline__ void bnd_body(const OpArgs<T>& A, const T* __restrict__ x,
+                                         const T* __restrict__ b, T* __restrict__ y, int node,
+                                         const T* __restrict__ sK) {
+  int idx[3] = {0, 0, 0}, u = node;
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) {
+    idx[k] = u % A.n;
+    u /= A.n;
+  }
+  const T v = node_row<DIM, P, T>(A, x, idx, sK);
+  y[node] = b ? b[node] - v : v;
+}
+
 template <int DIM, int P, typename T>
 __global__ void __launch_bounds__(128) k_apply_bnd(OpArgs<T> A, const T* __restrict__ x,
                                                    const T* __restrict__ b, T* __restrict__ y,
@@ -440,15 +485,7 @@ __global__ void __launch_bounds__(128) k_apply_bnd(OpArgs<T> A, const T* __restr
   stage_kref<NB>(A.Kref, sK);
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nn) return;
-  const int node = nodes[t];
-  int idx[3] = {0, 0, 0}, u = node;
-#pragma unroll
-  for (int k = 0; k < DIM; ++k) {
-    idx[k] = u % A.n;
-    u /= A.n;
-  }
-  const T v = node_row<DIM, P, T>(A, x, idx, sK);
-  y[node] = b ? b[node] - v : v;
+  bnd_body<DIM, P, T>(A, x, b, y, nodes[t], sK);
 }
 
 // ---------------------------------------------------------------------------
@@ -466,25 +503,34 @@ struct FdArgs {
   T lam[M];
 };
 
-template <int DIM, int P, typename T, int WARPS>
-__global__ void __launch_bounds__(32 * WARPS) k_smooth_cart(FdArgs<T, P> F, int N, int n,
-                                                            T* __restrict__ x, const T* __restrict__ b,
-                                                            const int* __restrict__ verts, int nv) {
+template <int DIM, int P>
+struct CartGeo {
+  static constexpr int C = 2 * P + 1, M = 2 * P - 1;
+  static constexpr int NC = (DIM == 2) ? C * C : C * C * C;
+  static constexpr int NI = (DIM == 2) ? M * M : M * M * M;
+  static constexpr int NU = (DIM == 2) ? M * C : M * C * C;  // after the first contraction
+  static constexpr int NV = (DIM == 2) ? 1 : M * M * C;       // after the second (3D)
+};
+
+template <int DIM, int P, typename T>
+struct CartScratch {
+  using G = CartGeo<DIM, P>;
+  T x[G::NC];
+  T u[2][G::NU];
+  T v[3][G::NV];
+  T r[G::NI];
+  T t[G::NI];
+};
+
+template <int DIM, int P, typename T>
+__device__ __forceinline__ void cart_body(const FdArgs<T, P>& F, int N, int n, T* __restrict__ x,
+                                          const T* __restrict__ b, int vert, int lane,
+                                          CartScratch<DIM, P, T>& CS) {
   constexpr int C = 2 * P + 1, M = 2 * P - 1;
-  constexpr int NC = (DIM == 2) ? C * C : C * C * C;
-  constexpr int NI = (DIM == 2) ? M * M : M * M * M;
-  constexpr int NU = (DIM == 2) ? M * C : M * C * C;  // after the first contraction
-  constexpr int NV = (DIM == 2) ? 1 : M * M * C;       // after the second (3D)
-  __shared__ T sx[WARPS][NC];
-  __shared__ T su[WARPS][2][NU];
-  __shared__ T sv[WARPS][3][NV];
-  __shared__ T sr[WARPS][NI];
-  __shared__ T st[WARPS][NI];
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int pidx = blockIdx.x * WARPS + w;
-  if (pidx >= nv) return;
+  constexpr int NC = CartGeo<DIM, P>::NC;
+  constexpr int NI = CartGeo<DIM, P>::NI;
   const int np = N + 1;
-  int q = verts[pidx], v[3] = {0, 0, 0};
+  int q = vert, v[3] = {0, 0, 0};
 #pragma unroll
   for (int k = 0; k < DIM; ++k) {
     v[k] = q % np;
@@ -499,16 +545,16 @@ __global__ void __launch_bounds__(32 * WARPS) k_smooth_cart(FdArgs<T, P> F, int 
       s *= n;
     }
   }
-  T* X = sx[w];
+  T* X = CS.x;
   for (int e = lane; e < NC; e += 32) {
     int o0 = e % C, r = e / C;
     int off = (DIM == 2) ? o0 + n * r : o0 + n * (r % C + n * (r / C));
     X[e] = x[base + off];
   }
   __syncwarp();
-  T* U1 = su[w][0];
-  T* U2 = su[w][1];
-  T* R = sr[w];
+  T* U1 = CS.u[0];
+  T* U2 = CS.u[1];
+  T* R = CS.r;
   if (DIM == 2) {
     // u1[yi][x] = sum_y Mr[yi][y] X[y][x]; u2 with Kr
     for (int e = lane; e < M * C; e += 32) {
@@ -534,9 +580,9 @@ __global__ void __launch_bounds__(32 * WARPS) k_smooth_cart(FdArgs<T, P> F, int 
       R[e] = b[node] - acc;
     }
   } else {
-    T* V1 = sv[w][0];
-    T* V2 = sv[w][1];
-    T* V3 = sv[w][2];
+    T* V1 = CS.v[0];
+    T* V2 = CS.v[1];
+    T* V3 = CS.v[2];
     // along z: u1 = Mz X, u2 = Kz X   (zi, y, x)
     for (int e = lane; e < M * C * C; e += 32) {
       int yx = e % (C * C), zi = e / (C * C);
@@ -582,7 +628,7 @@ __global__ void __launch_bounds__(32 * WARPS) k_smooth_cart(FdArgs<T, P> F, int 
   }
   __syncwarp();
   // fast diagonalisation: t = (S^T)^{(x) DIM} r, scale, delta = S^{(x) DIM} t
-  T* Tt = st[w];
+  T* Tt = CS.t;
   // S^T along x
   for (int e = lane; e < NI; e += 32) {
     int a = e % M, rest = e / M;
@@ -649,6 +695,17 @@ __global__ void __launch_bounds__(32 * WARPS) k_smooth_cart(FdArgs<T, P> F, int 
   }
 }
 
+template <int DIM, int P, typename T, int WARPS>
+__global__ void __launch_bounds__(32 * WARPS) k_smooth_cart(FdArgs<T, P> F, int N, int n,
+                                                            T* __restrict__ x, const T* __restrict__ b,
+                                                            const int* __restrict__ verts, int nv) {
+  __shared__ CartScratch<DIM, P, T> sCS[WARPS];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int pidx = blockIdx.x * WARPS + w;
+  if (pidx >= nv) return;
+  cart_body<DIM, P, T>(F, N, n, x, b, verts[pidx], lane, sCS[w]);
+}
+
 // ---------------------------------------------------------------------------
 // Cut-patch colour step (Sec. 3: dense local solver on cut patches), phase 1:
 // one warp per patch; r_I = b_I - (A x)_I by patch_rows, delta = A_j^{-1} r_I
@@ -656,6 +713,43 @@ __global__ void __launch_bounds__(32 * WARPS) k_smooth_cart(FdArgs<T, P> F, int 
 // consecutive entries), delta to dbuf.  x is not written here, so every patch
 // of the colour sees the same x: additive within a colour, which is the
 // paper's inconsistent treatment of ghost coupling between patches (Sec. 2.3).
+template <int DIM, int P, typename T>
+__device__ __forceinline__ void cut_body(const OpArgs<T>& A, const T* __restrict__ x,
+                                         const T* __restrict__ b, int vert, int m, int mo, int64_t io,
+                                         const uint16_t* __restrict__ members,
+                                         const int* __restrict__ mnode, const int* __restrict__ fofs,
+                                         const int* __restrict__ fent, const T* __restrict__ inv,
+                                         T* __restrict__ dbuf, PatchScratch<DIM, P, T>& S,
+                                         const T* __restrict__ sK, int lane) {
+  const int np = A.N + 1;
+  int q = vert, v[3] = {0, 0, 0};
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) {
+    v[k] = q % np;
+    q /= np;
+  }
+  patch_rows<DIM, P, T>(A, x, v, members + mo, m, fofs + mo, fent, S, sK, lane);
+  for (int e = lane; e < m; e += 32) S.r[e] = b[mnode[mo + e]] - S.r[e];
+  __syncwarp();
+  // delta = A_j^{-1} r with eight independent loads in flight per lane
+  const T* Ai = inv + io;
+  for (int e = lane; e < m; e += 32) {
+    T acc[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc[u] = T(0);
+    int j = 0;
+    for (; j + 8 <= m; j += 8) {
+      T a[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) a[u] = __ldg(Ai + (size_t)(j + u) * m + e);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) acc[u] += a[u] * S.r[j + u];
+    }
+    for (; j < m; ++j) acc[0] += __ldg(Ai + (size_t)j * m + e) * S.r[j];
+    dbuf[mo + e] = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+  }
+}
+
 template <int DIM, int P, typename T, int WARPS>
 __global__ void __launch_bounds__(32 * WARPS) k_cut_solve(OpArgs<T> A, const T* __restrict__ x,
                                                           const T* __restrict__ b,
@@ -676,29 +770,8 @@ __global__ void __launch_bounds__(32 * WARPS) k_cut_solve(OpArgs<T> A, const T* 
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int pidx = blockIdx.x * WARPS + w;
   if (pidx >= npatch) return;
-  const int np = A.N + 1;
-  int q = verts[pidx], v[3] = {0, 0, 0};
-#pragma unroll
-  for (int k = 0; k < DIM; ++k) {
-    v[k] = q % np;
-    q /= np;
-  }
-  const int m = cnt[pidx], mo = moff[pidx];
-  PatchScratch<DIM, P, T>& S = sS[w];
-  patch_rows<DIM, P, T>(A, x, v, members + mo, m, fofs + mo, fent, S, sK, lane);
-  for (int e = lane; e < m; e += 32) S.r[e] = b[mnode[mo + e]] - S.r[e];
-  __syncwarp();
-  const T* Ai = inv + ioff[pidx];
-  for (int e = lane; e < m; e += 32) {
-    T a0 = T(0), a1 = T(0);
-    int j = 0;
-    for (; j + 1 < m; j += 2) {
-      a0 += Ai[(size_t)j * m + e] * S.r[j];
-      a1 += Ai[(size_t)(j + 1) * m + e] * S.r[j + 1];
-    }
-    if (j < m) a0 += Ai[(size_t)j * m + e] * S.r[j];
-    dbuf[mo + e] = a0 + a1;
-  }
+  cut_body<DIM, P, T>(A, x, b, verts[pidx], cnt[pidx], moff[pidx], ioff[pidx], members, mnode, fofs, fent,
+                      inv, dbuf, sS[w], sK, lane);
 }
 
 // Phase 2: x[I_j] += delta for every DoF of the colour's patches.
