@@ -205,6 +205,34 @@ cf_status cf_batch_solve(cf_batch* bt, int precision, const double* const* d_b, 
 int64_t cf_batch_launch_count(const cf_batch* bt);
 void cf_batch_destroy(cf_batch* bt);
 
+/* ---- served form -------------------------------------------------------------
+ * A stream of solve requests with arrival times, solved with continuous
+ * batching: a host thread builds each hierarchy after its arrival; a prepared
+ * request is admitted (FIFO) when its estimated device footprint fits the HBM
+ * budget next to the resident problems and an active slot is free; every tick
+ * runs one CG iteration of all active problems with the batched kernels;
+ * finished problems retire at once and free their memory.  Each request
+ * performs the same floating-point operations as cf_solve on it alone.
+ * Precision applies to every request (CF_FP64 or CF_MIXED). */
+typedef struct cf_server cf_server;
+cf_status cf_server_create(size_t hbm_budget_bytes, int max_active, int precision, int keep_solutions,
+                           cf_server** out);
+/* Queue a request (arrival_s: seconds after cf_server_run starts; requests in
+ * non-decreasing arrival order).  id receives its index. */
+cf_status cf_server_submit(cf_server* s, const cf_mesh* mesh, const cf_levelset* ls, int degree,
+                           const cf_params* params, double rtol, int maxit, double arrival_s, int64_t* id);
+/* Serve every queued request (blocking, on `stream`, on the current device). */
+cf_status cf_server_run(cf_server* s, void* stream);
+/* Result of request id: info (solve_ms = admission to completion), times3 =
+ * {arrival, admission, completion} in seconds, ndof, and the solution (host
+ * array of ndof doubles, only with keep_solutions).  CF_EINVAL if the request
+ * failed (message in cf_last_error) or has not finished. */
+cf_status cf_server_result(const cf_server* s, int64_t id, cf_info* info, double* times3, int64_t* ndof,
+                           double* h_x);
+/* {peak device bytes of resident problems, peak active problems, ticks, run seconds} */
+cf_status cf_server_stats(const cf_server* s, double* out4);
+void cf_server_destroy(cf_server* s);
+
 /* ---- instrumentation ----------------------------------------------------- */
 /* Number of kernel launches this handle has issued (all calls). */
 int64_t cf_launch_count(const cf_problem* pb);

@@ -233,3 +233,60 @@ class Batch:
             check(st)
         return [{"iterations": i.iterations, "rel_residual": i.rel_residual,
                  "true_rel_residual": i.true_rel_residual, "solve_ms": i.solve_ms} for i in infos]
+
+
+class Server:
+    """Continuous-batching solve server (cf_server_*)."""
+
+    def __init__(self, hbm_budget_bytes, max_active=64, precision=CF_FP64, keep_solutions=False):
+        self._lib = _lib.load()
+        h = ctypes.c_void_p()
+        check(self._lib.cf_server_create(int(hbm_budget_bytes), max_active, precision, int(keep_solutions),
+                                         ctypes.byref(h)))
+        self._h = h
+        self.keep = keep_solutions
+        self.ndofs = []
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.cf_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, dim, n_cells, n_levels, degree, levelset, arrival_s, rtol=1e-8, maxit=500,
+               lo=-1.0, hi=1.0):
+        mesh = _lib.cf_mesh(dim, n_cells, lo, hi, n_levels)
+        ls = _lib.make_levelset(levelset)
+        prm = _lib.cf_params()
+        rid = ctypes.c_int64()
+        check(self._lib.cf_server_submit(self._h, ctypes.byref(mesh), ctypes.byref(ls), degree,
+                                         ctypes.byref(prm), rtol, maxit, float(arrival_s), ctypes.byref(rid)))
+        return rid.value
+
+    def run(self, stream=None):
+        check(self._lib.cf_server_run(self._h, _stream(stream)))
+
+    def result(self, rid):
+        info = _lib.cf_info()
+        times = np.zeros(3)
+        nd = ctypes.c_int64()
+        check(self._lib.cf_server_result(self._h, rid, ctypes.byref(info), times.ctypes.data_as(ctypes.c_void_p),
+                                         ctypes.byref(nd), None))
+        out = {"iterations": info.iterations, "rel_residual": info.rel_residual,
+               "true_rel_residual": info.true_rel_residual, "arrival": times[0], "admitted": times[1],
+               "done": times[2], "latency_s": times[2] - times[0], "ndof": nd.value}
+        if self.keep:
+            x = np.empty(nd.value)
+            check(self._lib.cf_server_result(self._h, rid, None, None, None, x.ctypes.data_as(ctypes.c_void_p)))
+            out["x"] = x
+        return out
+
+    def stats(self):
+        out = np.zeros(4)
+        check(self._lib.cf_server_stats(self._h, out.ctypes.data_as(ctypes.c_void_p)))
+        return {"peak_device_bytes": out[0], "peak_active": int(out[1]), "ticks": int(out[2]), "run_s": out[3]}

@@ -23,6 +23,8 @@ EXPORTED = [
     "cf_host_cell_matrix", "cf_host_patch_counts", "cf_host_interior_patch", "cf_host_cut_patch",
     "cf_launch_count", "cf_profile_start", "cf_profile_read", "cf_coarse_solve_noalloc",
     "cf_batch_create", "cf_batch_solve", "cf_batch_launch_count", "cf_batch_destroy",
+    "cf_server_create", "cf_server_submit", "cf_server_run", "cf_server_result", "cf_server_stats",
+    "cf_server_destroy",
 ]
 
 
@@ -103,6 +105,14 @@ def load():
     lib.cf_batch_launch_count.restype = ctypes.c_int64
     lib.cf_batch_destroy.argtypes = [P]
     lib.cf_batch_destroy.restype = None
+    lib.cf_server_create.argtypes = [ctypes.c_size_t, I, I, I, ctypes.POINTER(P)]
+    lib.cf_server_submit.argtypes = [P, ctypes.POINTER(cf_mesh), ctypes.POINTER(cf_levelset), I,
+                                     ctypes.POINTER(cf_params), D, I, D, ctypes.POINTER(ctypes.c_int64)]
+    lib.cf_server_run.argtypes = [P, V]
+    lib.cf_server_result.argtypes = [P, ctypes.c_int64, ctypes.POINTER(cf_info), P, P, P]
+    lib.cf_server_stats.argtypes = [P, P]
+    lib.cf_server_destroy.argtypes = [P]
+    lib.cf_server_destroy.restype = None
     lib.cf_launch_count.argtypes = [P]
     lib.cf_launch_count.restype = ctypes.c_int64
     lib.cf_profile_start.argtypes = [P, I]

@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcutmg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["capi.cu", "engine_d2.cu", "engine_d3.cu", "noalloc.cu"]
+CU_SOURCES = ["capi.cu", "engine_d2.cu", "engine_d3.cu", "noalloc.cu", "server.cu"]
 CPP_SOURCES = ["setup.cpp"]
 
 

@@ -254,7 +254,7 @@ static __global__ void __launch_bounds__(256) kb_dot_partial(const VecDesc* __re
 }
 
 static __global__ void __launch_bounds__(256) kb_dot_final(const double* __restrict__ part, const int* __restrict__ list,
-                                                    double* __restrict__ sc, int slot) {
+                                                    double* const* __restrict__ sc, int slot) {
   __shared__ double s[256];
   const int i = list[blockIdx.x];
   double acc = 0.0;
@@ -265,37 +265,43 @@ static __global__ void __launch_bounds__(256) kb_dot_final(const double* __restr
     if (threadIdx.x < h) s[threadIdx.x] += s[threadIdx.x + h];
     __syncthreads();
   }
-  if (threadIdx.x == 0) sc[i * 16 + slot] = s[0];
+  if (threadIdx.x == 0) sc[i][slot] = s[0];
 }
 
 // CG updates of the listed instances: a = x, b = r, c = p, d = q (or z)
-static __global__ void __launch_bounds__(256) kb_cg_xr(const VecDesc* __restrict__ V, const double* __restrict__ sc,
+static __global__ void __launch_bounds__(256) kb_cg_xr(const VecDesc* __restrict__ V, double* const* __restrict__ sc,
                                                 const int* __restrict__ off, int K, int total) {
   for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < total; it += gridDim.x * blockDim.x) {
     const int i = find_inst(off, K, it);
     const VecDesc& Q = V[i];
-    const double alpha = sc[i * 16 + 0] / sc[i * 16 + 1];
+    const double alpha = sc[i][0] / sc[i][1];
     const int64_t o = Q.R.at(it - off[i]);
     static_cast<double*>(Q.a)[o] += alpha * static_cast<const double*>(Q.c)[o];
     static_cast<double*>(Q.b)[o] -= alpha * static_cast<const double*>(Q.d)[o];
   }
 }
 
-static __global__ void __launch_bounds__(256) kb_cg_p(const VecDesc* __restrict__ V, const double* __restrict__ sc,
+static __global__ void __launch_bounds__(256) kb_cg_p(const VecDesc* __restrict__ V, double* const* __restrict__ sc,
                                                const int* __restrict__ off, int K, int total) {
   for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < total; it += gridDim.x * blockDim.x) {
     const int i = find_inst(off, K, it);
     const VecDesc& Q = V[i];
-    const double beta = sc[i * 16 + 2] / sc[i * 16 + 0];
+    const double beta = sc[i][2] / sc[i][0];
     const int64_t o = Q.R.at(it - off[i]);
     double* p = static_cast<double*>(Q.c);
     p[o] = static_cast<const double*>(Q.d)[o] + beta * p[o];
   }
 }
 
-static __global__ void kb_copy_scalar(double* __restrict__ sc, const int* __restrict__ list, int n, int dst, int src) {
+static __global__ void kb_gather_scalars(double* const* __restrict__ sc, int K, double* __restrict__ out) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n) sc[list[t] * 16 + dst] = sc[list[t] * 16 + src];
+  if (t < K * 16) out[t] = sc[t / 16][t % 16];
+}
+
+static __global__ void kb_copy_scalar(double* const* __restrict__ sc, const int* __restrict__ list, int n, int dst,
+                                      int src) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) sc[list[t]][dst] = sc[list[t]][src];
 }
 
 // ---------------------------------------------------------------------------
@@ -316,8 +322,13 @@ class BatchGroup final : public BatchGroupBase {
     CUTMG_CUDA(cudaDeviceGetAttribute(&sms_, cudaDevAttrMultiProcessorCount, dev_));
     build_desc<double>(d64_);
     build_desc<float>(d32_);
-    sc_ = pool_.alloc<double>((size_t)K_ * 16);
+    {
+      std::vector<double*> sct(K_);
+      for (int i = 0; i < K_; ++i) sct[i] = inst_[i]->sc_;
+      sc_ = upload(sct);
+    }
     part_ = pool_.alloc<double>((size_t)K_ * kBatchDotBlocks);
+    scg_ = pool_.alloc<double>((size_t)K_ * 16);
     CUTMG_CUDA(cudaMallocHost(&host_sc_, sizeof(double) * K_ * 16));
     rebuild_lists();
   }
@@ -332,6 +343,14 @@ class BatchGroup final : public BatchGroupBase {
     return a;
   }
   int64_t launches() const override { return launches_; }
+  void get_tile(int* w, int* b) const override {
+    *w = tile_w_;
+    *b = tile_b_;
+  }
+  void set_tile(int w, int b) override {
+    tile_w_ = (w == 2 || w == 8) ? w : 4;
+    tile_b_ = b > 0 ? b : 4;
+  }
 
   void autotune(cudaStream_t s) override {
     // candidates for the two patch kernels: warps per block and blocks per
@@ -385,8 +404,7 @@ class BatchGroup final : public BatchGroupBase {
       CUTMG_CUDA(cudaMemcpyAsync(e->rF_, e->bF_, bytes, cudaMemcpyDeviceToDevice, s));
     }
     dot_all(1, 4, s);  // ||b||^2 -> slot 4   (vec set 1: a = b, b = b)
-    CUTMG_CUDA(cudaMemcpyAsync(host_sc_, sc_, sizeof(double) * K_ * 16, cudaMemcpyDeviceToHost, s));
-    CUTMG_CUDA(cudaStreamSynchronize(s));
+    read_scalars(s);
     std::vector<int> zero;
     for (int i = 0; i < K_; ++i) {
       bn_[i] = std::sqrt(host_sc_[i * 16 + 4]);
@@ -415,14 +433,14 @@ class BatchGroup final : public BatchGroupBase {
   }
 
   void read_rr(double* host_rr, cudaStream_t s) override {
-    CUTMG_CUDA(cudaMemcpyAsync(host_sc_, sc_, sizeof(double) * K_ * 16, cudaMemcpyDeviceToHost, s));
-    CUTMG_CUDA(cudaStreamSynchronize(s));
+    read_scalars(s);
     for (int i = 0; i < K_; ++i) host_rr[i] = host_sc_[i * 16 + 3];
-    for (int i = 0; i < K_; ++i)
-      if (act_[i]) {
-        its_[i] += 1;
-        rel_[i] = std::sqrt(host_rr[i]) / bn_[i];
-      }
+    if ((int)its_.size() == K_)
+      for (int i = 0; i < K_; ++i)
+        if (act_[i]) {
+          its_[i] += 1;
+          rel_[i] = std::sqrt(host_rr[i]) / bn_[i];
+        }
   }
 
   void deactivate(const std::vector<int>& idx) override {
@@ -451,8 +469,7 @@ class BatchGroup final : public BatchGroupBase {
     rebuild_lists();
     apply_true(s);
     dot_all(5, 5, s);
-    CUTMG_CUDA(cudaMemcpyAsync(host_sc_, sc_, sizeof(double) * K_ * 16, cudaMemcpyDeviceToHost, s));
-    CUTMG_CUDA(cudaStreamSynchronize(s));
+    read_scalars(s);
     for (int i = 0; i < K_; ++i) {
       E* e = inst_[i];
       e->from_box(e->n_levels() - 1, e->xF_, x[i], s);
@@ -471,8 +488,9 @@ class BatchGroup final : public BatchGroupBase {
   int tile_w_ = 4, tile_b_ = 4, best_w_ = 4, best_b_ = 4;
   std::vector<int> act_, its_;
   std::vector<double> bn_, rel_;
-  double* sc_ = nullptr;
+  double** sc_ = nullptr;  // each problem's own CG scalars (Engine::sc_), so CG state survives regrouping
   double* part_ = nullptr;
+  double* scg_ = nullptr;
   double* host_sc_ = nullptr;
 
   template <typename T>
@@ -515,6 +533,13 @@ class BatchGroup final : public BatchGroupBase {
   void count(const char* what) {
     launch_check(what);
     ++launches_;
+  }
+  // host copy of every problem's 16 CG scalars (gathered into one buffer)
+  void read_scalars(cudaStream_t s) {
+    kb_gather_scalars<<<(K_ * 16 + 255) / 256, 256, 0, s>>>(sc_, K_, scg_);
+    count("batched gather scalars");
+    CUTMG_CUDA(cudaMemcpyAsync(host_sc_, scg_, sizeof(double) * K_ * 16, cudaMemcpyDeviceToHost, s));
+    CUTMG_CUDA(cudaStreamSynchronize(s));
   }
   int grid(int total, int per_block) const {
     int g = (total + per_block - 1) / per_block;

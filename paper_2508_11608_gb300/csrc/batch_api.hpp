@@ -29,6 +29,8 @@ class BatchGroupBase {
   virtual void bnorms(double* host_bn) = 0;
   virtual int64_t launches() const = 0;
   virtual void autotune(cudaStream_t s) = 0;
+  virtual void get_tile(int* warps, int* blocks_per_sm) const = 0;
+  virtual void set_tile(int warps, int blocks_per_sm) = 0;
 };
 
 }  // namespace cutmg

@@ -11,16 +11,11 @@
 #include "../../include/cutmg.h"
 #include "batch_api.hpp"
 #include "engine_api.hpp"
+#include "problem.hpp"
 #include "setup.hpp"
 
 using namespace cutmg;
 
-struct cf_problem {
-  Hierarchy H;
-  std::unique_ptr<EngineBase> eng;
-  int precision = CF_FP64;
-  int device = 0;
-};
 
 struct cf_batch {
   std::vector<std::unique_ptr<BatchGroupBase>> groups;
@@ -158,6 +153,47 @@ static cf_status setup_impl(const cf_mesh* mesh, const cf_levelset* ls, int degr
 cf_status cf_setup(const cf_mesh* mesh, const cf_levelset* ls, int degree, const cf_params* params,
                    cf_problem** out) {
   return setup_impl(mesh, ls, degree, params, out, true);
+}
+
+cf_status cutmg_build_host(const cf_mesh* mesh, const cf_levelset* ls, int degree, const cf_params* params,
+                           cf_problem** out) {
+  return setup_impl(mesh, ls, degree, params, out, false);
+}
+
+cf_status cutmg_attach_device(cf_problem* pb) {
+  if (!pb) return fail(CF_EINVAL, "null problem");
+  if (pb->eng) return CF_OK;
+  return guarded([&] {
+    if (cudaGetDevice(&pb->device) != cudaSuccess) throw CudaError("no CUDA device");
+    pb->eng = pb->H.prm.dim == 2 ? make_engine_d2(pb->H.prm.degree, pb->H) : make_engine_d3(pb->H.prm.degree, pb->H);
+  });
+}
+
+size_t cutmg_estimate_device_bytes(const cf_problem* pb) {
+  // mirrors the allocations of Engine (both precisions) and its CG vectors
+  const auto& H = pb->H;
+  const int d = H.prm.dim, p = H.prm.degree;
+  size_t nb = 1;
+  for (int k = 0; k < d; ++k) nb *= (size_t)(p + 1);
+  const size_t nt = d == 2 ? (size_t)(p + 1) : (size_t)(p + 1) * (p + 1);
+  size_t tot = 0;
+  for (size_t l = 0; l < H.levels.size(); ++l) {
+    const auto& L = H.levels[l];
+    const size_t nbox = L.nact.size(), ncell = L.cflag.size();
+    tot += ncell * 5 + nbox + L.dofs.size() * 8 + (L.bulk_pos.size() + L.bnd_node.size()) * 4;
+    tot += (L.cart_vert.size() + L.cut_vert.size() * 3 + L.member_node.size() + L.fent.size() + L.fofs.size() +
+            L.ghost_faces.size() + L.cfaces.size() + L.face_id.size()) * 4 + L.cut_vert.size() * 8 + L.members.size() * 2;
+    tot += (L.pro_col.size() + L.res_col.size()) * 4;
+    size_t typed = L.cutmat.size() + L.Kref.size() + L.inv.size() + L.pro_w.size() + L.res_w.size() +
+                   L.coarse_inv.size() + 3 * nbox + L.members.size() + L.ghost_faces.size() * p * nt;
+    if (l > 0) {
+      const size_t nf = L.n, nc = H.levels[l - 1].n;
+      typed += d == 3 ? nc * nf * nf + nc * nc * nf + nf * nc * nc + nf * nf * nc : 2 * nc * nf;
+    }
+    tot += typed * 12;  // FP64 + FP32 copies
+  }
+  tot += 9 * H.levels.back().nact.size() * 8 + H.rhs.size() * 8 + 64 * 1024;
+  return tot;
 }
 
 cf_status cf_setup_host(const cf_mesh* mesh, const cf_levelset* ls, int degree, const cf_params* params,

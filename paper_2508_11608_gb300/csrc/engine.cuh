@@ -291,6 +291,32 @@ class Engine final : public EngineBase {
     from_box(L, aux2_, z, s);
   }
 
+  double cg_begin(int prec, const double* b, cudaStream_t s) override {
+    const int L = n_levels() - 1;
+    const auto& F = com_[L];
+    to_box(L, b, bF_, s);
+    const size_t bytes = sizeof(double) * F.nbox;
+    CUTMG_CUDA(cudaMemsetAsync(xF_, 0, bytes, s));
+    CUTMG_CUDA(cudaMemcpyAsync(rF_, bF_, bytes, cudaMemcpyDeviceToDevice, s));
+    dot(F.region, bF_, bF_, sc_ + 4, s);
+    const double bn = std::sqrt(read_scalar(4, s));
+    if (bn > 0.0) {
+      run_graph(GraphKey{300 + prec, rF_, zF_}, s, [&](cudaStream_t cs) { precondition(prec, rF_, zF_, cs); });
+      dot(F.region, rF_, zF_, sc_ + 0, s);
+      CUTMG_CUDA(cudaMemcpyAsync(pF_, zF_, bytes, cudaMemcpyDeviceToDevice, s));
+    }
+    return bn;
+  }
+  double cg_end(double* x, cudaStream_t s) override {
+    const int L = n_levels() - 1;
+    const auto& F = com_[L];
+    apply<double>(L, d64_[L], xF_, bF_, tF_, s);
+    dot(F.region, tF_, tF_, sc_ + 5, s);
+    const double tr = std::sqrt(read_scalar(5, s));
+    from_box(L, xF_, x, s);
+    return tr;
+  }
+
   int solve(int prec, const double* b, double* x, double rtol, int maxit, double* rel,
             double* true_rel, float* ms, cudaStream_t s) override {
     const int L = n_levels() - 1;

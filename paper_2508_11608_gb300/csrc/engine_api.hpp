@@ -39,6 +39,10 @@ class EngineBase {
   virtual void vcycle(int prec, const double* r, double* z, cudaStream_t s) = 0;
   virtual int solve(int prec, const double* b, double* x, double rtol, int maxit, double* rel,
                     double* true_rel, float* ms, cudaStream_t s) = 0;
+  // the parts of a CG solve around its iterations: x = 0, r = b, z = B r,
+  // p = z (returns ||b||); at the end the true residual norm and x gathered
+  virtual double cg_begin(int prec, const double* b, cudaStream_t s) = 0;
+  virtual double cg_end(double* x, cudaStream_t s) = 0;
   // kernel launches issued so far, and event timing of one kernel family
   virtual int64_t launches() const = 0;
   virtual void profile_start(int kind) = 0;

@@ -240,6 +240,7 @@ struct PatchScratch {
   T x[G::NCL];
   T part[G::NCELL][G::NB];
   T r[G::NCL];
+  const T* rowbase[G::NCELL];  // element matrix of each patch cell, nullptr if inactive
   short mem[G::NCL];
 };
 
@@ -274,6 +275,22 @@ __device__ __forceinline__ void patch_rows(const OpArgs<T>& A, const T* __restri
       S.mem[e] = -1;
     }
   }
+  if (lane < G::NCELL) {
+    int c[3] = {0, 0, 0};
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+      c[k] = v[k] - 1 + ((lane >> k) & 1);
+      if (c[k] < 0 || c[k] >= N) ok = false;
+    }
+    const T* rb = nullptr;
+    if (ok) {
+      const int cell = (DIM == 2) ? c[0] + N * c[1] : c[0] + N * (c[1] + N * c[2]);
+      const uint8_t fl = A.cflag[cell];
+      if (fl & kActive) rb = (fl & kCutCell) ? A.cutmat + (size_t)A.cut_id[cell] * NB * NB : sK;
+    }
+    S.rowbase[lane] = rb;
+  }
   __syncwarp();
   for (int e = lane; e < m; e += 32) S.mem[tgt[e]] = (short)e;
   __syncwarp();
@@ -291,11 +308,8 @@ __device__ __forceinline__ void patch_rows(const OpArgs<T>& A, const T* __restri
       base += P * sk * ost;
       ost *= C;
     }
-    if (!ok || S.mem[o] < 0) continue;
-    const int cell = (DIM == 2) ? c[0] + N * c[1] : c[0] + N * (c[1] + N * c[2]);
-    const uint8_t fl = A.cflag[cell];
-    if (!(fl & kActive)) continue;
-    const T* row = (fl & kCutCell) ? A.cutmat + (size_t)A.cut_id[cell] * NB * NB + j * NB : sK + j * NB;
+    if (!ok || S.mem[o] < 0 || !S.rowbase[s]) continue;
+    const T* row = S.rowbase[s] + j * NB;
     T acc = T(0);
     if (DIM == 2) {
 #pragma unroll
@@ -322,22 +336,18 @@ __device__ __forceinline__ void patch_rows(const OpArgs<T>& A, const T* __restri
       u /= C;
     }
     T acc = T(0);
+#pragma unroll
     for (int s = 0; s < G::NCELL; ++s) {
-      int j = 0, jst = 1, c[3] = {0, 0, 0};
-      bool in = true;
+      int j = 0, jst = 1;
+      bool in = S.rowbase[s] != nullptr;
 #pragma unroll
       for (int k = 0; k < DIM; ++k) {
         const int sk = (s >> k) & 1, a = o[k] - P * sk;
         if (a < 0 || a > P) in = false;
         j += a * jst;
         jst *= (P + 1);
-        c[k] = v[k] - 1 + sk;
-        if (c[k] < 0 || c[k] >= N) in = false;
       }
-      if (!in) continue;
-      const int cell = (DIM == 2) ? c[0] + N * c[1] : c[0] + N * (c[1] + N * c[2]);
-      if (!(A.cflag[cell] & kActive)) continue;
-      acc += S.part[s][j];
+      if (in) acc += S.part[s][j];
     }
     const int f0 = fofs[e], f1 = fofs[e + 1];
     for (int q0 = f0; q0 < f1; q0 += 8) {
