@@ -134,6 +134,26 @@ __global__ void __launch_bounds__(32 * WARPS) kb_cut_solve(const LvlDesc<DIM, P,
 }
 
 template <int DIM, int P, typename T>
+__global__ void __launch_bounds__(kCutThreads) kb_cut_solve_cta(const LvlDesc<DIM, P, T>* __restrict__ D,
+                                                                const int* __restrict__ off, int K, int total,
+                                                                int colour, int inv_cap, int* err) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ PatchScratch<DIM, P, T> S;
+  T* sinv = reinterpret_cast<T*>(dsm);
+  if (threadIdx.x == 0) mbar_init(&bar);
+  __syncthreads();
+  uint32_t phase = 0;
+  for (int it = blockIdx.x; it < total; it += gridDim.x) {
+    const int i = find_inst(off, K, it);
+    const LvlDesc<DIM, P, T>& L = D[i];
+    const int j = L.cut_start[colour] + it - off[i];
+    cut_body_cta<DIM, P, T>(L.op, L.x, L.b, L.cutv[j], L.cutn[j], L.cutmo[j], L.cutio[j], L.members, L.mnode,
+                            L.fofs, L.fent, L.inv, L.dbuf, S, sinv, inv_cap, &bar, phase, L.op.Kref, err);
+  }
+}
+
+template <int DIM, int P, typename T>
 __global__ void __launch_bounds__(256) kb_cut_scatter(const LvlDesc<DIM, P, T>* __restrict__ D,
                                                       const int* __restrict__ off, int K, int total,
                                                       int colour) {
@@ -329,6 +349,11 @@ class BatchGroup final : public BatchGroupBase {
     }
     part_ = pool_.alloc<double>((size_t)K_ * kBatchDotBlocks);
     scg_ = pool_.alloc<double>((size_t)K_ * 16);
+    err_ = pool_.alloc<int>(1);
+    CUTMG_CUDA(cudaFuncSetAttribute(kb_cut_solve_cta<DIM, P, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    E::kInvSlotBytes));
+    CUTMG_CUDA(cudaFuncSetAttribute(kb_cut_solve_cta<DIM, P, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    E::kInvSlotBytes));
     CUTMG_CUDA(cudaMallocHost(&host_sc_, sizeof(double) * K_ * 16));
     rebuild_lists();
   }
@@ -491,6 +516,7 @@ class BatchGroup final : public BatchGroupBase {
   double** sc_ = nullptr;  // each problem's own CG scalars (Engine::sc_), so CG state survives regrouping
   double* part_ = nullptr;
   double* scg_ = nullptr;
+  int* err_ = nullptr;
   double* host_sc_ = nullptr;
 
   template <typename T>
@@ -769,7 +795,18 @@ class BatchGroup final : public BatchGroupBase {
         kb_face_moments<DIM, P, T><<<grid(wf.total, 128), 128, 0, s>>>(D, nullptr, wf.off, K_, wf.total, colour);
         count("batched face moments");
       }
-      launch_cut<T>(D, w, colour, s);
+      {
+        int maxm2 = 0;
+        for (int i = 0; i < K_; ++i) {
+          const int l = DV[t].level[i];
+          if (l >= 1 && act_[i]) maxm2 = std::max(maxm2, inst_[i]->com_[l].cut_maxm2[colour]);
+        }
+        const int cap = E::template inv_cap_for<T>(maxm2);
+        const int gridc = std::max(1, std::min(w.total, sms_ * 16));
+        kb_cut_solve_cta<DIM, P, T><<<gridc, kCutThreads, E::template inv_slot_bytes<T>(cap), s>>>(
+            D, w.off, K_, w.total, colour, cap, err_);
+        count("batched cut patches");
+      }
       const Work& wm = w_mem_[t][colour];
       kb_cut_scatter<DIM, P, T><<<grid(wm.total, 256), 256, 0, s>>>(D, wm.off, K_, wm.total, colour);
       count("batched cut scatter");

@@ -45,6 +45,8 @@ cf_status guarded(F&& f) {
     return fail(CF_ENOMEM, "host allocation failed");
   } catch (const CudaError& e) {
     return fail(CF_ECUDA, e.what());
+  } catch (const TimeoutError& e) {
+    return fail(CF_ETIMEOUT, e.what());
   } catch (const std::exception& e) {
     return fail(CF_EINVAL, e.what());
   }

@@ -105,6 +105,7 @@ class Engine final : public EngineBase {
     uint16_t* members;
     std::vector<int> cut_start;
     std::vector<int> cut_moff_h;
+    std::vector<int> cut_maxm2;
     int64_t nmembers;
     int* pro_col;
     int* res_col;
@@ -144,6 +145,11 @@ class Engine final : public EngineBase {
     aux2_ = pool_.alloc<double>(F.nbox);
     part_ = pool_.alloc<double>(kDotBlocks);
     sc_ = pool_.alloc<double>(16);
+    err_ = pool_.alloc<int>(1);
+    CUTMG_CUDA(cudaFuncSetAttribute(k_cut_solve_cta<DIM, P, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    kInvSlotBytes));
+    CUTMG_CUDA(cudaFuncSetAttribute(k_cut_solve_cta<DIM, P, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    kInvSlotBytes));
     CUTMG_CUDA(cudaMallocHost(&host_sc_, 16 * sizeof(double)));
     CUTMG_CUDA(cudaStreamCreateWithFlags(&cap_, cudaStreamNonBlocking));
     const char* g = std::getenv("CUTMG_GRAPHS");
@@ -368,6 +374,7 @@ class Engine final : public EngineBase {
     CUTMG_CUDA(cudaEventElapsedTime(ms, e0, e1));
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    check_err(s);
     // true residual
     apply<double>(L, d64_[L], xF_, bF_, tF_, s);
     dot(F.region, tF_, tF_, sc_ + 5, s);
@@ -445,6 +452,21 @@ class Engine final : public EngineBase {
 
  private:
   static constexpr int kDotBlocks = 512;
+ public:
+  // shared-memory slot for one patch inverse in the cut-patch kernel
+  static constexpr int kInvSlotBytes = 96 * 1024;
+  // inverses with m^2 <= cap elements go through shared memory; the slot
+  // holds the 16-byte-rounded copy
+  template <typename T>
+  static int inv_cap_for(int maxm2) {
+    const int cap = (kInvSlotBytes - 16) / (int)sizeof(T);
+    return maxm2 < cap ? maxm2 : cap;
+  }
+  template <typename T>
+  static size_t inv_slot_bytes(int cap) {
+    return ((size_t)cap * sizeof(T) + 15) / 16 * 16;
+  }
+ private:
   static constexpr int kVecBlocks = 1024;
 
   const Hierarchy& H_;
@@ -526,6 +548,7 @@ class Engine final : public EngineBase {
   std::vector<Typed<double>> d64_;
   std::vector<Typed<float>> d32_;
   double *xF_, *rF_, *pF_, *qF_, *zF_, *bF_, *tF_, *aux_, *aux2_, *part_, *sc_;
+  int* err_ = nullptr;  // set by kernels whose bounded waits ran out
   double* host_sc_ = nullptr;
   double* rhs_d_ = nullptr;
   float *bL32_ = nullptr, *xL32_ = nullptr;
@@ -613,6 +636,7 @@ class Engine final : public EngineBase {
     c.members = pool_.upload<uint16_t>(h.members);
     c.cut_start = h.cut_start;
     c.cut_moff_h = h.cut_moff;
+    c.cut_maxm2 = h.cut_maxm2;
     c.nmembers = (int64_t)h.members.size();
     c.pro_col = l > 0 ? pool_.upload<int>(h.pro_col) : nullptr;
     c.res_col = l > 0 ? pool_.upload<int>(h.res_col) : nullptr;
@@ -653,6 +677,17 @@ class Engine final : public EngineBase {
     const Common& c = com_[l];
     k_gather<double, T><<<std::min(blocks_for(c.ndof, 256), 4096), 256, 0, s>>>(c.dofs, c.ndof, box, out);
     count_launch("gather");
+  }
+
+  // a bounded wait inside a kernel ran out: report and clear the flag
+  void check_err(cudaStream_t s) {
+    int h = 0;
+    CUTMG_CUDA(cudaMemcpyAsync(&h, err_, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CUTMG_CUDA(cudaStreamSynchronize(s));
+    if (h) {
+      CUTMG_CUDA(cudaMemsetAsync(err_, 0, sizeof(int), s));
+      throw TimeoutError("a bounded wait on a TMA copy ran out in the cut-patch kernel");
+    }
   }
 
   double read_scalar(int i, cudaStream_t s) {
@@ -725,9 +760,11 @@ class Engine final : public EngineBase {
       if (cnt <= 0) return;
       prof_mark(1, s);
       face_moments<T>(l, D, x, s, colour);
-      k_cut_solve<DIM, P, T, WARPS><<<blocks_for(cnt, WARPS), 32 * WARPS, 0, s>>>(
+      const int cap = inv_cap_for<T>(c.cut_maxm2[colour]);
+      const int grid = std::min(cnt, 152 * 16);
+      k_cut_solve_cta<DIM, P, T><<<grid, kCutThreads, inv_slot_bytes<T>(cap), s>>>(
           D.op, x, b, c.cutv + a0, c.cutn + a0, c.cutmo + a0, c.cutio + a0, c.members, c.mnode, c.fofs,
-          c.fent, D.inv, D.dbuf, cnt);
+          c.fent, D.inv, D.dbuf, cnt, cap, err_);
       count_launch("cut patch solve");
       prof_mark(1, s);
       const auto& w = H_.levels[l].work_cut[colour];

@@ -20,6 +20,9 @@ struct CudaError : std::runtime_error {
 struct OomError : std::runtime_error {
   using std::runtime_error::runtime_error;
 };
+struct TimeoutError : std::runtime_error {
+  using std::runtime_error::runtime_error;
+};
 
 class EngineBase {
  public:

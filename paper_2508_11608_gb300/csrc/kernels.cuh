@@ -249,7 +249,16 @@ __device__ __forceinline__ int lat_index(const int* c, int n) {
   return (DIM == 2) ? c[0] + n * c[1] : c[0] + n * (c[1] + n * c[2]);
 }
 
-template <int DIM, int P, typename T>
+// synchronisation of the threads that work on one patch
+template <int NT>
+__device__ __forceinline__ void psync() {
+  if (NT == 32)
+    __syncwarp();
+  else
+    __syncthreads();
+}
+
+template <int DIM, int P, typename T, int NT = 32>
 __device__ __forceinline__ void patch_rows(const OpArgs<T>& A, const T* __restrict__ x, const int* v,
                                            const uint16_t* __restrict__ tgt, int m,
                                            const int* __restrict__ fofs, const int* __restrict__ fent,
@@ -258,10 +267,10 @@ __device__ __forceinline__ void patch_rows(const OpArgs<T>& A, const T* __restri
   using G = PatchGeo<DIM, P>;
   constexpr int C = G::C, NB = G::NB, NTF = FaceGeo<DIM, P>::NT;
   const int N = A.N, n = A.n;
-  constexpr int NROUND = (G::NCL + 31) / 32;
+  constexpr int NROUND = (G::NCL + NT - 1) / NT;
 #pragma unroll
   for (int rr = 0; rr < NROUND; ++rr) {
-    const int e = lane + 32 * rr;
+    const int e = lane + NT * rr;
     if (e < G::NCL) {
       int u = e, c[3] = {0, 0, 0};
       bool in = true;
@@ -291,10 +300,10 @@ __device__ __forceinline__ void patch_rows(const OpArgs<T>& A, const T* __restri
     }
     S.rowbase[lane] = rb;
   }
-  __syncwarp();
-  for (int e = lane; e < m; e += 32) S.mem[tgt[e]] = (short)e;
-  __syncwarp();
-  for (int it = lane; it < G::NCELL * NB; it += 32) {
+  psync<NT>();
+  for (int e = lane; e < m; e += NT) S.mem[tgt[e]] = (short)e;
+  psync<NT>();
+  for (int it = lane; it < G::NCELL * NB; it += NT) {
     const int s = it / NB, j = it - s * NB;
     int c[3] = {0, 0, 0}, o = 0, ost = 1, u = j, base = 0;
     bool ok = true;
@@ -327,8 +336,8 @@ __device__ __forceinline__ void patch_rows(const OpArgs<T>& A, const T* __restri
     }
     S.part[s][j] = acc;
   }
-  __syncwarp();
-  for (int e = lane; e < m; e += 32) {
+  psync<NT>();
+  for (int e = lane; e < m; e += NT) {
     int o[3] = {0, 0, 0}, u = tgt[e];
 #pragma unroll
     for (int k = 0; k < DIM; ++k) {
@@ -372,7 +381,7 @@ __device__ __forceinline__ void patch_rows(const OpArgs<T>& A, const T* __restri
     }
     S.r[e] = acc;
   }
-  __syncwarp();
+  psync<NT>();
 }
 
 template <int NB, typename T>
@@ -782,6 +791,123 @@ __global__ void __launch_bounds__(32 * WARPS) k_cut_solve(OpArgs<T> A, const T* 
   if (pidx >= npatch) return;
   cut_body<DIM, P, T>(A, x, b, verts[pidx], cnt[pidx], moff[pidx], ioff[pidx], members, mnode, fofs, fent,
                       inv, dbuf, sS[w], sK, lane);
+}
+
+// ---------------------------------------------------------------------------
+// Cut-patch step with one 128-thread block per patch.  Thread 0 starts a TMA
+// bulk copy (cp.async.bulk, completion on an mbarrier) of the patch's
+// explicit inverse into shared memory as soon as the patch is known; the
+// copy runs while the block forms the residual rows, and the local solve
+// then reads the inverse from shared memory.  Inverses larger than the
+// shared-memory slot are read from global memory instead.  The wait on the
+// mbarrier is bounded: past kTmaSpin polls the block records an error in
+// *err, polls again (bounded) for its own copy and gives up the patch.
+constexpr int kCutThreads = 128;
+constexpr int kTmaSpin = 1 << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// true once phase `parity` of the barrier has completed (bounded polling)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (int it = 0; it < kTmaSpin; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+template <int DIM, int P, typename T>
+__device__ __forceinline__ void cut_body_cta(const OpArgs<T>& A, const T* __restrict__ x,
+                                             const T* __restrict__ b, int vert, int m, int mo, int64_t io,
+                                             const uint16_t* __restrict__ members,
+                                             const int* __restrict__ mnode, const int* __restrict__ fofs,
+                                             const int* __restrict__ fent, const T* __restrict__ inv,
+                                             T* __restrict__ dbuf, PatchScratch<DIM, P, T>& S, T* sinv,
+                                             int inv_cap, uint64_t* bar, uint32_t& phase,
+                                             const T* __restrict__ sK, int* err) {
+  const int tid = threadIdx.x;
+  const bool tma = m * m <= inv_cap;
+  if (tma && tid == 0) {
+    const uint32_t bytes = (uint32_t)(((size_t)m * m * sizeof(T) + 15) / 16 * 16);
+    tma_load_1d(sinv, inv + io, bytes, bar);
+  }
+  const int np = A.N + 1;
+  int q = vert, v[3] = {0, 0, 0};
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) {
+    v[k] = q % np;
+    q /= np;
+  }
+  patch_rows<DIM, P, T, kCutThreads>(A, x, v, members + mo, m, fofs + mo, fent, S, sK, tid);
+  for (int e = tid; e < m; e += kCutThreads) S.r[e] = b[mnode[mo + e]] - S.r[e];
+  bool ok = true;
+  if (tma) {
+    ok = mbar_wait(bar, phase & 1u);
+    if (!ok) {
+      atomicExch(err, 1);
+      mbar_wait(bar, phase & 1u);
+    }
+    phase += 1;
+  }
+  __syncthreads();
+  if (ok) {
+    const T* Ai = tma ? sinv : inv + io;
+    for (int e = tid; e < m; e += kCutThreads) {
+      T acc[4] = {T(0), T(0), T(0), T(0)};
+      int j = 0;
+      for (; j + 4 <= m; j += 4) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[u] += Ai[(size_t)(j + u) * m + e] * S.r[j + u];
+      }
+      for (; j < m; ++j) acc[0] += Ai[(size_t)j * m + e] * S.r[j];
+      dbuf[mo + e] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+    }
+  }
+  __syncthreads();
+}
+
+template <int DIM, int P, typename T>
+__global__ void __launch_bounds__(kCutThreads) k_cut_solve_cta(
+    OpArgs<T> A, const T* __restrict__ x, const T* __restrict__ b, const int* __restrict__ verts,
+    const int* __restrict__ cnt, const int* __restrict__ moff, const int64_t* __restrict__ ioff,
+    const uint16_t* __restrict__ members, const int* __restrict__ mnode, const int* __restrict__ fofs,
+    const int* __restrict__ fent, const T* __restrict__ inv, T* __restrict__ dbuf, int npatch, int inv_cap,
+    int* err) {
+  constexpr int NB = Shape<DIM, P>::NB;
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ T sK[NB * NB];
+  __shared__ PatchScratch<DIM, P, T> S;
+  T* sinv = reinterpret_cast<T*>(dsm);
+  if (threadIdx.x == 0) mbar_init(&bar);
+  stage_kref<NB>(A.Kref, sK);  // includes __syncthreads
+  uint32_t phase = 0;
+  for (int pidx = blockIdx.x; pidx < npatch; pidx += gridDim.x)
+    cut_body_cta<DIM, P, T>(A, x, b, verts[pidx], cnt[pidx], moff[pidx], ioff[pidx], members, mnode, fofs, fent,
+                            inv, dbuf, S, sinv, inv_cap, &bar, phase, sK, err);
 }
 
 // Phase 2: x[I_j] += delta for every DoF of the colour's patches.
