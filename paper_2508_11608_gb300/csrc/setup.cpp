@@ -26,9 +26,12 @@ int ipow(int b, int e) {
   return r;
 }
 
-// SPD matrix (row-major, n x n) -> its inverse, through L L^T.
+// SPD matrix (row-major, n x n) -> its inverse, through L L^T.  All inner
+// products run over contiguous rows; large matrices (the coarsest-level
+// operator) are split over threads, with the same summation order per entry.
 void spd_inverse(int n, double* A) {
-  std::vector<double> L((size_t)n * n, 0.0), Li((size_t)n * n, 0.0);
+  std::vector<double> L((size_t)n * n, 0.0), U((size_t)n * n, 0.0);
+  const bool par = n > 256;
   for (int j = 0; j < n; ++j) {
     double s = A[(size_t)j * n + j];
     for (int k = 0; k < j; ++k) s -= L[(size_t)j * n + k] * L[(size_t)j * n + k];
@@ -37,28 +40,38 @@ void spd_inverse(int n, double* A) {
                                std::to_string(n) + ": " + std::to_string(s) + ")");
     double ljj = std::sqrt(s);
     L[(size_t)j * n + j] = ljj;
+    const double* Lj = &L[(size_t)j * n];
+#pragma omp parallel for schedule(static) if (par)
     for (int i = j + 1; i < n; ++i) {
+      const double* Li = &L[(size_t)i * n];
       double t = A[(size_t)i * n + j];
-      for (int k = 0; k < j; ++k) t -= L[(size_t)i * n + k] * L[(size_t)j * n + k];
+      for (int k = 0; k < j; ++k) t -= Li[k] * Lj[k];
       L[(size_t)i * n + j] = t / ljj;
     }
   }
-  // Li = L^{-1} (lower triangular), column by column
+  // U = L^{-T}: row c of U is column c of L^{-1} (forward substitution)
+#pragma omp parallel for schedule(dynamic, 8) if (par)
   for (int c = 0; c < n; ++c) {
+    double* Uc = &U[(size_t)c * n];
     for (int i = c; i < n; ++i) {
+      const double* Li = &L[(size_t)i * n];
       double t = (i == c) ? 1.0 : 0.0;
-      for (int k = c; k < i; ++k) t -= L[(size_t)i * n + k] * Li[(size_t)k * n + c];
-      Li[(size_t)i * n + c] = t / L[(size_t)i * n + i];
+      for (int k = c; k < i; ++k) t -= Li[k] * Uc[k];
+      Uc[i] = t / Li[i];
     }
   }
-  // A^{-1} = Li^T Li
-  for (int i = 0; i < n; ++i)
+  // A^{-1} = L^{-T} L^{-1}: entry (i, j), j <= i, is row i of U dotted with row j
+#pragma omp parallel for schedule(dynamic, 8) if (par)
+  for (int i = 0; i < n; ++i) {
+    const double* Ui = &U[(size_t)i * n];
     for (int j = 0; j <= i; ++j) {
+      const double* Uj = &U[(size_t)j * n];
       double t = 0.0;
-      for (int k = i; k < n; ++k) t += Li[(size_t)k * n + i] * Li[(size_t)k * n + j];
+      for (int k = i; k < n; ++k) t += Ui[k] * Uj[k];
       A[(size_t)i * n + j] = t;
       A[(size_t)j * n + i] = t;
     }
+  }
 }
 
 // Symmetric eigen-decomposition by cyclic Jacobi rotations: A = Q diag(lam) Q^T.
@@ -530,13 +543,17 @@ void build_level(const SetupParams& prm, const RefTables& R, int N, HostLevel& L
     L.cut_moff.resize(ncp);
     L.cut_ioff.resize(ncp);
     int64_t moff = 0, ioff = 0;
+    L.cut_maxm2.assign(ncol, 0);
     for (int64_t j = 0; j < ncp; ++j) {
       int m = (int)mem[j].size();
       L.cut_n[j] = m;
       L.cut_moff[j] = (int)moff;
       L.cut_ioff[j] = ioff;
       moff += m;
-      ioff += (int64_t)m * m;
+      // every inverse starts on a 16-byte boundary in FP64 and FP32 (TMA bulk copies)
+      ioff += ((int64_t)m * m + 3) / 4 * 4;
+      for (int col = 0; col < ncol; ++col)
+        if (j >= L.cut_start[col] && j < L.cut_start[col + 1]) L.cut_maxm2[col] = std::max(L.cut_maxm2[col], m * m);
       L.members.insert(L.members.end(), mem[j].begin(), mem[j].end());
       int v[3] = {0, 0, 0};
       int64_t t = L.cut_vert[j];
@@ -1036,6 +1053,9 @@ void build_hierarchy(const SetupParams& prm, Hierarchy& H) {
       }
     }
   }
+  if (H.levels[0].dofs.size() > 12000)
+    throw std::invalid_argument("the coarsest level has " + std::to_string(H.levels[0].dofs.size()) +
+                                " DoFs (dense exact solve); use more levels");
   build_coarse(R, H.levels[0]);
   build_rhs(prm, R, H.levels.back(), H.rhs);
 }

@@ -49,7 +49,8 @@ struct HostLevel {
   std::vector<int> cart_vert;   // packed vertex v_0 + (N+1)(v_1 + (N+1) v_2)
   std::vector<int> cart_start;
   std::vector<int> cut_vert, cut_n, cut_moff;
-  std::vector<int64_t> cut_ioff;
+  std::vector<int64_t> cut_ioff;  // inverse offsets, multiples of 4 elements
+  std::vector<int> cut_maxm2;     // per colour: largest m^2 of its cut patches
   std::vector<int> cut_start;
   std::vector<uint16_t> members;  // closure-local node index per cut-patch DoF
   std::vector<int> member_node;   // lattice index per cut-patch DoF

@@ -26,7 +26,7 @@ REQS = [
     dict(dim=3, n_cells=16, n_levels=2, degree=2,
          levelset={"kind": "torus", "center": [0.0, 0.02, 0.01], "rot": rotation(0.5, 0.9, 0.0),
                    "major": 0.6, "minor": 0.2}),
-    dict(dim=3, n_cells=24, n_levels=2, degree=2,
+    dict(dim=3, n_cells=24, n_levels=3, degree=2,
          levelset={"kind": "sphere", "center": [-0.02, 0.03, 0.0], "radius": 0.75}),
     dict(dim=3, n_cells=8, n_levels=2, degree=2,
          levelset={"kind": "sphere", "center": [0.0, 0.0, 0.01], "radius": 0.45}),
