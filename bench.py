@@ -172,6 +172,24 @@ def run_reference(args):
     return 0
 
 
+def agg_max(v, dist=None, device=None):
+    """Max of a per-rank float over all ranks (the rank-local value without a
+    process group).  gloo reduces CPU tensors, nccl device tensors."""
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def whole_job_rate(units_per_rank, world, ms_local, dist=None, device=None):
+    """Weak scaling: every rank processes units_per_rank in its own timed
+    region; the job's rate is all units over the slowest rank's time."""
+    ms = agg_max(ms_local, dist, device)
+    return world * units_per_rank / (ms * 1e-3), ms
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -263,20 +281,13 @@ def run_ours(args):
     batched = None
     if not args.no_batch:
         batched = run_batched(cm, torch, dev, stream, args)
+    served = None
+    if not args.no_serve and world == 1:
+        served = run_serving(cm, torch, args)
 
-    def agg_max(v):
-        if not dist:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return t.item()
-
-    tot64 = agg_max(sum(ms64))
-    tot32 = agg_max(sum(ms32))
-    tote2e = agg_max(sum(e2e_ms))
-    value = world * n * args.steps / (tot64 * 1e-3)
-    mixed_value = world * n * args.steps / (tot32 * 1e-3)
-    e2e_value = world * n * len(e2e_ms) / (tote2e * 1e-3)
+    value, tot64 = whole_job_rate(n * args.steps, world, sum(ms64), dist, dev)
+    mixed_value, tot32 = whole_job_rate(n * args.steps, world, sum(ms32), dist, dev)
+    e2e_value, tote2e = whole_job_rate(n * len(e2e_ms), world, sum(e2e_ms), dist, dev)
 
     if rank != 0:
         if dist:
@@ -343,6 +354,7 @@ def run_ours(args):
         "cpu_baseline": cpu_line,
         "clocks": clocks,
         "batched": batched,
+        "served": served,
     }
     print(json.dumps(line))
     if dist:
@@ -388,6 +400,38 @@ def run_batched(cm, torch, dev, stream, args):
                         "N in {32, 64, 128, 256}, Q2/Q3, coarsest 8^2, seed 20260101"}
 
 
+def run_serving(cm, torch, args):
+    """Served form: a seeded stream of 3D Q2 requests (spheres, ellipsoids,
+    tori; 32^3..96^3) with Poisson arrivals, served by cf_server_* with
+    continuous batching in the mixed form.  Latency = arrival to result; the
+    host builds each hierarchy after its arrival, so it includes setup."""
+    import numpy as np
+    from paper_2508_11608_gb300.workloads import serving_requests
+    reqs = serving_requests(count=args.serve_count)
+    rng = np.random.default_rng(20260103)
+    gaps = rng.exponential(1.0 / args.serve_rate, len(reqs))
+    arrivals = np.cumsum(gaps) - gaps[0]
+    srv = cm.Server(hbm_budget_bytes=64 << 30, max_active=32, precision=cm.CF_MIXED)
+    ids = [srv.submit(arrival_s=float(a), **k) for k, a in zip(reqs, arrivals)]
+    srv.run()
+    res = [srv.result(i) for i in ids]
+    st = srv.stats()
+    lat = np.array([r["latency_s"] for r in res]) * 1e3
+    dev = np.array([r["done"] - r["admitted"] for r in res]) * 1e3
+    ndof = sum(r["ndof"] for r in res)
+    span = max(r["done"] for r in res) - min(r["arrival"] for r in res)
+    srv.close()
+    return {"value": ndof / span, "unit": "DoF/s", "requests": len(res), "active_dofs": ndof,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+            "device_latency_ms": {"p50": float(np.percentile(dev, 50)), "p99": float(np.percentile(dev, 99))},
+            "worst_true_rel_residual": max(r["true_rel_residual"] for r in res),
+            "peak_active": st["peak_active"], "peak_device_gb": st["peak_device_bytes"] / 1e9,
+            "arrival_rate_per_s": args.serve_rate, "precision": "mixed",
+            "workload": "3D Q2 spheres r in [0.4,0.8] / ellipsoids semi-axes in [0.4,0.8] / tori R=0.6 r=0.2, "
+                        "offset <= 0.05, N in {32,48,64,96}, seed 20260102, Poisson arrivals seed 20260103; "
+                        "latency includes the host setup after arrival, device_latency is admission to result"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -396,6 +440,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-form measurement")
     ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--no-serve", action="store_true", help="skip the served-form measurement")
+    ap.add_argument("--serve-count", type=int, default=16)
+    ap.add_argument("--serve-rate", type=float, default=0.5, help="Poisson arrivals per second")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -118,6 +118,14 @@ cf_status cf_dof_coords(const cf_problem* pb, int level, double* h_xyz);
 /* Host counters of the finest level: [active cells, cut cells, ghost faces,
  * patches, cut patches, cut-patch matrix entries]. */
 cf_status cf_stats(const cf_problem* pb, int level, int64_t* h_out6);
+/* Algorithmic work of one colour step on a level, from the host setup
+ * (Sec. 3's two patch kinds): kind 0 = interior patches (fast
+ * diagonalisation, Sec. 2.3), 1 = cut patches (residual rows and the dense
+ * local inverse).  h_out3 = [flops, scalars moved, index bytes moved]; bytes
+ * = scalars x sizeof(precision) + index bytes.  CF_EINVAL for a bad level,
+ * kind or colour (0 <= colour < 2^dim); level 0 (the coarsest, solved
+ * exactly) has no colour steps and reports zeros. */
+cf_status cf_work_model(const cf_problem* pb, int level, int kind, int colour, double* h_out3);
 
 /* Select the precision of cf_vcycle and cf_solve (CF_FP64 or CF_MIXED). */
 cf_status cf_set_precision(cf_problem* pb, int precision);

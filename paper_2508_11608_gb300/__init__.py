@@ -93,6 +93,13 @@ class Problem:
         keys = ["active_cells", "cut_cells", "ghost_faces", "patches", "cut_patches", "inverse_entries"]
         return dict(zip(keys, out.tolist()))
 
+    def work_model(self, level, kind, colour):
+        """Algorithmic work of one colour step: kind 0 interior, 1 cut patches.
+        Returns (flops, scalars moved, index bytes moved)."""
+        out = np.empty(3, dtype=np.float64)
+        check(self._lib.cf_work_model(self._h, level, kind, colour, out.ctypes.data_as(ctypes.c_void_p)))
+        return tuple(out.tolist())
+
     def set_precision(self, precision):
         check(self._lib.cf_set_precision(self._h, precision))
 

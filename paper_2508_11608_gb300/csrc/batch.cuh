@@ -38,6 +38,7 @@ struct LvlDesc {
   const int* cutn;
   const int* cutmo;
   const int64_t* cutio;
+  CutPatchArgs cp;
   const uint16_t* members;
   const int* mnode;
   const int* fofs;
@@ -108,12 +109,19 @@ __global__ void __launch_bounds__(128) kb_face_moments(const LvlDesc<DIM, P, T>*
                                                        const T* const* __restrict__ X,
                                                        const int* __restrict__ off, int K, int total,
                                                        int colour) {
-  for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < total; it += gridDim.x * blockDim.x) {
-    const int i = find_inst(off, K, it);
+  constexpr int NT = FaceGeo<DIM, P>::NT, PW = FaceGeo<DIM, P>::PER_WARP;
+  const int lane = threadIdx.x & 31;
+  const int warps = gridDim.x * (blockDim.x >> 5);
+  // warp-uniform loop over groups of PW faces; lanes of one warp may serve
+  // faces of different instances
+  for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w * PW < total; w += warps) {
+    const int it = w * PW + lane / NT;
+    const bool ok = lane / NT < PW && it < total;
+    const int i = find_inst(off, K, ok ? it : w * PW);
     const LvlDesc<DIM, P, T>& L = D[i];
-    const int local = it - off[i];
+    const int local = (ok ? it : w * PW) - off[i];
     const int f = colour >= 0 ? L.cfaces[L.cf_start[colour] + local] : local;
-    face_moment_body<DIM, P, T>(L.op, X ? X[i] : L.x, L.faces, f);
+    face_moment_lanes<DIM, P, T>(L.op, X ? X[i] : L.x, ok ? L.faces[f] : -1, f, lane);
   }
 }
 
@@ -139,8 +147,9 @@ __global__ void __launch_bounds__(kCutThreads) kb_cut_solve_cta(const LvlDesc<DI
                                                                 int colour, int inv_cap, int* err) {
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ __align__(8) uint64_t bar;
-  __shared__ PatchScratch<DIM, P, T> S;
+  __shared__ CutScratch<DIM, P, T> S;
   T* sinv = reinterpret_cast<T*>(dsm);
+  if ((int)blockIdx.x >= total) return;
   if (threadIdx.x == 0) mbar_init(&bar);
   __syncthreads();
   uint32_t phase = 0;
@@ -148,8 +157,11 @@ __global__ void __launch_bounds__(kCutThreads) kb_cut_solve_cta(const LvlDesc<DI
     const int i = find_inst(off, K, it);
     const LvlDesc<DIM, P, T>& L = D[i];
     const int j = L.cut_start[colour] + it - off[i];
-    cut_body_cta<DIM, P, T>(L.op, L.x, L.b, L.cutv[j], L.cutn[j], L.cutmo[j], L.cutio[j], L.members, L.mnode,
-                            L.fofs, L.fent, L.inv, L.dbuf, S, sinv, inv_cap, &bar, phase, L.op.Kref, err);
+    const CutMeta M = cut_meta(L.cp, j);
+    // uncut cells read the level's element matrix from global memory
+    // (instances differ in h)
+    cut_body_cta<DIM, P, T>(L.op, L.x, L.b, M, j, L.cp, L.members, L.mnode, L.fofs, L.fent, L.inv, L.dbuf, S,
+                            sinv, inv_cap, &bar, phase, L.op.Kref, err);
   }
 }
 
@@ -608,6 +620,7 @@ class BatchGroup final : public BatchGroupBase {
         L.cutn = C.cutn;
         L.cutmo = C.cutmo;
         L.cutio = C.cutio;
+        L.cp = E::cut_args(C);
         L.members = C.members;
         L.mnode = C.mnode;
         L.fofs = C.fofs;
@@ -792,7 +805,8 @@ class BatchGroup final : public BatchGroupBase {
       if (w.total == 0) return;
       const Work& wf = w_cf_[t][colour];
       if (wf.total > 0) {
-        kb_face_moments<DIM, P, T><<<grid(wf.total, 128), 128, 0, s>>>(D, nullptr, wf.off, K_, wf.total, colour);
+        kb_face_moments<DIM, P, T><<<grid(wf.total, 4 * FaceGeo<DIM, P>::PER_WARP), 128, 0, s>>>(D, nullptr, wf.off, K_,
+                                                                                             wf.total, colour);
         count("batched face moments");
       }
       {
@@ -801,11 +815,15 @@ class BatchGroup final : public BatchGroupBase {
           const int l = DV[t].level[i];
           if (l >= 1 && act_[i]) maxm2 = std::max(maxm2, inst_[i]->com_[l].cut_maxm2[colour]);
         }
-        const int cap = E::template inv_cap_for<T>(maxm2);
-        const int gridc = std::max(1, std::min(w.total, sms_ * 16));
-        kb_cut_solve_cta<DIM, P, T><<<gridc, kCutThreads, E::template inv_slot_bytes<T>(cap), s>>>(
-            D, w.off, K_, w.total, colour, cap, err_);
-        count("batched cut patches");
+        if (E::kWarpCut) {
+          launch_cut<T>(D, w, colour, s);
+        } else {
+          const int cap = E::template inv_cap_for<T>(maxm2);
+          const int gridc = std::max(1, std::min(w.total, sms_ * 16));
+          kb_cut_solve_cta<DIM, P, T><<<gridc, kCutThreads, E::template inv_slot_bytes<T>(cap), s>>>(
+              D, w.off, K_, w.total, colour, cap, err_);
+          count("batched cut patches");
+        }
       }
       const Work& wm = w_mem_[t][colour];
       kb_cut_scatter<DIM, P, T><<<grid(wm.total, 256), 256, 0, s>>>(D, wm.off, K_, wm.total, colour);
@@ -848,7 +866,8 @@ class BatchGroup final : public BatchGroupBase {
     auto* D = DV[t].desc;
     const Work& wf = w_faces_[t];
     if (wf.total > 0) {
-      kb_face_moments<DIM, P, T><<<grid(wf.total, 128), 128, 0, s>>>(D, nullptr, wf.off, K_, wf.total, -1);
+      kb_face_moments<DIM, P, T><<<grid(wf.total, 4 * FaceGeo<DIM, P>::PER_WARP), 128, 0, s>>>(D, nullptr, wf.off, K_,
+                                                                                             wf.total, -1);
       count("batched face moments");
     }
     // X = x, B = b, Y = r from the descriptors: pointer tables built here once
@@ -968,7 +987,8 @@ class BatchGroup final : public BatchGroupBase {
     auto* D = d64_[0].desc;
     const Work& wf = w_faces_[0];
     if (wf.total > 0) {
-      kb_face_moments<DIM, P, double><<<grid(wf.total, 128), 128, 0, s>>>(D, X, wf.off, K_, wf.total, -1);
+      kb_face_moments<DIM, P, double><<<grid(wf.total, 4 * FaceGeo<DIM, P>::PER_WARP), 128, 0, s>>>(D, X, wf.off, K_,
+                                                                                                  wf.total, -1);
       count("batched face moments");
     }
     if (w_bulk_[0].total > 0) {

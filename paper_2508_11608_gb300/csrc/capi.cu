@@ -184,7 +184,8 @@ size_t cutmg_estimate_device_bytes(const cf_problem* pb) {
     const size_t nbox = L.nact.size(), ncell = L.cflag.size();
     tot += ncell * 5 + nbox + L.dofs.size() * 8 + (L.bulk_pos.size() + L.bnd_node.size()) * 4;
     tot += (L.cart_vert.size() + L.cut_vert.size() * 3 + L.member_node.size() + L.fent.size() + L.fofs.size() +
-            L.ghost_faces.size() + L.cfaces.size() + L.face_id.size()) * 4 + L.cut_vert.size() * 8 + L.members.size() * 2;
+            L.ghost_faces.size() + L.cfaces.size() + L.face_id.size() + L.cut_fo.size() + L.cut_cell.size() +
+            L.cut_item_off.size()) * 4 + L.cut_vert.size() * 8 + L.members.size() * 2 + L.cut_items.size();
     tot += (L.pro_col.size() + L.res_col.size()) * 4;
     size_t typed = L.cutmat.size() + L.Kref.size() + L.inv.size() + L.pro_w.size() + L.res_w.size() +
                    L.coarse_inv.size() + 3 * nbox + L.members.size() + L.ghost_faces.size() * p * nt;
@@ -245,6 +246,15 @@ cf_status cf_stats(const cf_problem* pb, int level, int64_t* h_out6) {
   h_out6[3] = (int64_t)(L.cart_vert.size() + L.cut_vert.size());
   h_out6[4] = (int64_t)L.cut_vert.size();
   h_out6[5] = (int64_t)L.inv.size();
+  return CF_OK;
+}
+
+cf_status cf_work_model(const cf_problem* pb, int level, int kind, int colour, double* h_out3) {
+  if (bad_level(pb, level) || !h_out3 || (kind != 0 && kind != 1)) return fail(CF_EINVAL, "bad argument");
+  const HostLevel& L = pb->H.levels[level];
+  if (colour < 0 || colour >= (1 << L.d)) return fail(CF_EINVAL, "bad colour");
+  const auto& w = kind == 0 ? L.work_cart : L.work_cut;
+  for (int i = 0; i < 3; ++i) h_out3[i] = (colour < (int)w.size()) ? w[colour][i] : 0.0;
   return CF_OK;
 }
 

@@ -102,6 +102,10 @@ class Engine final : public EngineBase {
     int* cutn;
     int* cutmo;
     int64_t* cutio;
+    int* cutfo;
+    int* cutcell;
+    int* citoff;
+    uint8_t* citems;
     uint16_t* members;
     std::vector<int> cut_start;
     std::vector<int> cut_moff_h;
@@ -455,8 +459,16 @@ class Engine final : public EngineBase {
  public:
   // shared-memory slot for one patch inverse in the cut-patch kernel
   static constexpr int kInvSlotBytes = 96 * 1024;
+  // when no patch can exceed 64 DoFs, (2p+1)^d <= 64 (2D Q1-Q3, 3D Q1), one
+  // warp solves a patch, one or two rows per lane; otherwise (3D Q2) each
+  // patch takes a block.  The choice depends on (d, p) only, so a problem
+  // solved alone and inside a batch runs the same arithmetic.
+  static constexpr bool kWarpCut = (DIM == 2 ? (2 * P + 1) * (2 * P + 1) : (2 * P + 1) * (2 * P + 1) * (2 * P + 1)) <= 64;
   // inverses with m^2 <= cap elements go through shared memory; the slot
   // holds the 16-byte-rounded copy
+  static CutPatchArgs cut_args(const Common& c) {
+    return CutPatchArgs{c.cutv, c.cutn, c.cutmo, c.cutio, c.cutfo, c.cutcell, c.citoff, c.citems};
+  }
   template <typename T>
   static int inv_cap_for(int maxm2) {
     const int cap = (kInvSlotBytes - 16) / (int)sizeof(T);
@@ -633,6 +645,10 @@ class Engine final : public EngineBase {
     c.cutn = pool_.upload<int>(h.cut_n);
     c.cutmo = pool_.upload<int>(h.cut_moff);
     c.cutio = pool_.upload<int64_t>(h.cut_ioff);
+    c.cutfo = pool_.upload<int>(h.cut_fo);
+    c.cutcell = pool_.upload<int>(h.cut_cell);
+    c.citoff = pool_.upload<int>(h.cut_item_off);
+    c.citems = pool_.upload<uint8_t>(h.cut_items);
     c.members = pool_.upload<uint16_t>(h.members);
     c.cut_start = h.cut_start;
     c.cut_moff_h = h.cut_moff;
@@ -738,7 +754,8 @@ class Engine final : public EngineBase {
       cnt = c.cf_start[colour + 1] - c.cf_start[colour];
     }
     if (cnt <= 0) return;
-    k_face_moments<DIM, P, T><<<blocks_for(cnt, 128), 128, 0, s>>>(D.op, x, c.faces, ids, cnt);
+    constexpr int PW = FaceGeo<DIM, P>::PER_WARP;
+    k_face_moments<DIM, P, T><<<blocks_for(blocks_for(cnt, PW), 4), 128, 0, s>>>(D.op, x, c.faces, ids, cnt);
     count_launch("ghost face moments");
   }
 
@@ -760,11 +777,16 @@ class Engine final : public EngineBase {
       if (cnt <= 0) return;
       prof_mark(1, s);
       face_moments<T>(l, D, x, s, colour);
-      const int cap = inv_cap_for<T>(c.cut_maxm2[colour]);
-      const int grid = std::min(cnt, 152 * 16);
-      k_cut_solve_cta<DIM, P, T><<<grid, kCutThreads, inv_slot_bytes<T>(cap), s>>>(
-          D.op, x, b, c.cutv + a0, c.cutn + a0, c.cutmo + a0, c.cutio + a0, c.members, c.mnode, c.fofs,
-          c.fent, D.inv, D.dbuf, cnt, cap, err_);
+      if (kWarpCut) {
+        k_cut_solve<DIM, P, T, WARPS><<<blocks_for(cnt, WARPS), 32 * WARPS, 0, s>>>(
+            D.op, x, b, c.cutv + a0, c.cutn + a0, c.cutmo + a0, c.cutio + a0, c.members, c.mnode, c.fofs,
+            c.fent, D.inv, D.dbuf, cnt);
+      } else {
+        const int cap = inv_cap_for<T>(c.cut_maxm2[colour]);
+        const int grid = std::min(cnt, 152 * 16);
+        k_cut_solve_cta<DIM, P, T><<<grid, kCutThreads, inv_slot_bytes<T>(cap), s>>>(
+            D.op, x, b, cut_args(c), c.members, c.mnode, c.fofs, c.fent, D.inv, D.dbuf, a0, cnt, cap, err_);
+      }
       count_launch("cut patch solve");
       prof_mark(1, s);
       const auto& w = H_.levels[l].work_cut[colour];

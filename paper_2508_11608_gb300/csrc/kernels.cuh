@@ -48,67 +48,91 @@ struct OpArgs {
 template <int DIM, int P>
 struct FaceGeo {
   static constexpr int NT = (DIM == 2) ? P + 1 : (P + 1) * (P + 1);
+  static constexpr int PER_WARP = 32 / NT;  // faces one warp evaluates together
 };
 
+// One face on NT lanes of a warp: lane t = (t0, t1) forms the jumps J_m[t]
+// of its node column; the face mass Mhat x Mhat is applied in two 1D passes
+// across the group by shuffles, and lane t writes G_m[t].  All 32 lanes must
+// call this (packed < 0: padding lane).
 template <int DIM, int P, typename T>
-__device__ __forceinline__ void face_moment_body(const OpArgs<T>& A, const T* __restrict__ x,
-                                                 const int* __restrict__ faces, int f) {
+__device__ __forceinline__ void face_moment_lanes(const OpArgs<T>& A, const T* __restrict__ x, int packed, int f,
+                                                  int lane) {
   constexpr int NT = FaceGeo<DIM, P>::NT;
-  const int packed = faces[f], k = packed % DIM;
-  int c = packed / DIM, lc[3] = {0, 0, 0};
+  const int grp = lane / NT, t = lane - grp * NT;
+  T J[P];
 #pragma unroll
-  for (int j = 0; j < DIM; ++j) {
-    lc[j] = c % A.N;
-    c /= A.N;
+  for (int m = 0; m < P; ++m) J[m] = T(0);
+  if (packed >= 0) {
+    const int k = packed % DIM;
+    int c = packed / DIM, lc[3] = {0, 0, 0};
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) {
+      lc[j] = c % A.N;
+      c /= A.N;
+    }
+    const int n = A.n;
+    const int sk = (k == 0) ? 1 : (k == 1 ? n : n * n);
+    int tdim[2] = {0, 0}, q = 0;
+#pragma unroll
+    for (int j = 0; j < DIM; ++j)
+      if (j != k) tdim[q++] = j;
+    const int s0 = (tdim[0] == 0) ? 1 : (tdim[0] == 1 ? n : n * n);
+    const int s1 = (DIM == 3) ? ((tdim[1] == 0) ? 1 : (tdim[1] == 1 ? n : n * n)) : 0;
+    const int base = P * (lc[0] + n * (lc[1] + (DIM == 3 ? n * lc[2] : 0)));
+    const int off = base + (t % (P + 1)) * s0 + (DIM == 3 ? (t / (P + 1)) * s1 : 0);
+    T xv[2 * P + 1];
+#pragma unroll
+    for (int ip = 0; ip <= 2 * P; ++ip) xv[ip] = x[off + ip * sk];
+#pragma unroll
+    for (int ip = 0; ip <= 2 * P; ++ip)
+#pragma unroll
+      for (int m = 0; m < P; ++m) J[m] += A.dvec[m][ip] * xv[ip];
   }
-  const int n = A.n;
-  const int sk = (k == 0) ? 1 : (k == 1 ? n : n * n);
-  int tdim[2] = {0, 0}, q = 0;
+  const int src = (grp * NT < 32 - NT) ? grp * NT : 32 - NT;
+  const int t0 = t % (P + 1), t1 = t / (P + 1);
+  // face mass by sum factorisation: one 1D pass per face direction
+  T acc[P];
 #pragma unroll
-  for (int j = 0; j < DIM; ++j)
-    if (j != k) tdim[q++] = j;
-  const int s0 = (tdim[0] == 0) ? 1 : (tdim[0] == 1 ? n : n * n);
-  const int s1 = (DIM == 3) ? ((tdim[1] == 0) ? 1 : (tdim[1] == 1 ? n : n * n)) : 0;
-  const int base = P * (lc[0] + n * (lc[1] + (DIM == 3 ? n * lc[2] : 0)));
-  T J[P][NT];
+  for (int m = 0; m < P; ++m) acc[m] = T(0);
 #pragma unroll
-  for (int tp = 0; tp < NT; ++tp) {
-    const int off = base + (tp % (P + 1)) * s0 + (DIM == 3 ? (tp / (P + 1)) * s1 : 0);
-    T acc[P];
+  for (int q = 0; q <= P; ++q) {
+    const T w = A.Mhat[t0][q];
 #pragma unroll
-    for (int m = 0; m < P; ++m) acc[m] = T(0);
+    for (int m = 0; m < P; ++m) acc[m] += w * __shfl_sync(0xffffffffu, J[m], src + q + (P + 1) * t1);
+  }
+  if (DIM == 3) {
+    T h[P];
 #pragma unroll
-    for (int ip = 0; ip <= 2 * P; ++ip) {
-      const T xv = x[off + ip * sk];
-#pragma unroll
-      for (int m = 0; m < P; ++m) acc[m] += A.dvec[m][ip] * xv;
+    for (int m = 0; m < P; ++m) {
+      h[m] = acc[m];
+      acc[m] = T(0);
     }
 #pragma unroll
-    for (int m = 0; m < P; ++m) J[m][tp] = acc[m];
-  }
-  T* g = A.G + (size_t)f * P * NT;
+    for (int q = 0; q <= P; ++q) {
+      const T w = A.Mhat[t1][q];
 #pragma unroll
-  for (int m = 0; m < P; ++m)
-#pragma unroll
-    for (int t = 0; t < NT; ++t) {
-      T acc = T(0);
-#pragma unroll
-      for (int tq = 0; tq < NT; ++tq) {
-        T w = A.Mhat[t % (P + 1)][tq % (P + 1)];
-        if (DIM == 3) w *= A.Mhat[t / (P + 1)][tq / (P + 1)];
-        acc += w * J[m][tq];
-      }
-      g[m * NT + t] = A.coef[m] * acc;
+      for (int m = 0; m < P; ++m) acc[m] += w * __shfl_sync(0xffffffffu, h[m], src + t0 + (P + 1) * q);
     }
+  }
+  if (packed >= 0) {
+    T* g = A.G + (size_t)f * P * NT;
+#pragma unroll
+    for (int m = 0; m < P; ++m) g[m * NT + t] = A.coef[m] * acc[m];
+  }
 }
 
 template <int DIM, int P, typename T>
 __global__ void __launch_bounds__(128) k_face_moments(OpArgs<T> A, const T* __restrict__ x,
                                                       const int* __restrict__ faces,
                                                       const int* __restrict__ ids, int nfaces) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nfaces) return;
-  face_moment_body<DIM, P, T>(A, x, faces, ids ? ids[i] : i);
+  constexpr int NT = FaceGeo<DIM, P>::NT, PW = FaceGeo<DIM, P>::PER_WARP;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp * PW >= nfaces) return;  // whole warp
+  const int i = warp * PW + lane / NT;
+  const bool ok = lane / NT < PW && i < nfaces;
+  const int f = ok ? (ids ? ids[i] : i) : 0;
+  face_moment_lanes<DIM, P, T>(A, x, ok ? faces[f] : -1, f, lane);
 }
 
 // sum over the ghost faces whose two cells contain node idx of (G_F x)(node)
@@ -839,30 +863,190 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   return false;
 }
 
+// Per-patch arrays of the block kernel (absolute patch index j).
+struct CutPatchArgs {
+  const int* vert;       // packed patch vertex
+  const int* cnt;        // m, DoFs of the patch
+  const int* moff;       // first member of the patch
+  const int64_t* ioff;   // offset of the patch inverse
+  const int* fo;         // [npatch + 1] ghost-face entries fent[fo[j] .. fo[j+1])
+  const int* cell;       // [npatch][2^DIM] cut-cell matrix id, -1 uncut, -2 inactive
+  const int* item_off;   // [npatch + 1]
+  const uint8_t* items;  // s * NB + i: rows (patch cell s, local node i) to form
+};
+
+struct CutMeta {
+  int vert, m, mo, f0, f1, i0, i1;
+  int64_t io;
+};
+
+__device__ __forceinline__ CutMeta cut_meta(const CutPatchArgs& C, int j) {
+  CutMeta t;
+  t.vert = C.vert[j];
+  t.m = C.cnt[j];
+  t.mo = C.moff[j];
+  t.io = C.ioff[j];
+  t.f0 = C.fo[j];
+  t.f1 = C.fo[j + 1];
+  t.i0 = C.item_off[j];
+  t.i1 = C.item_off[j + 1];
+  return t;
+}
+
+constexpr int kFeCap = 512;  // ghost-face entries of one patch staged in shared memory (more: read from global)
+
+template <int DIM, int P, typename T>
+struct CutScratch {
+  using G = PatchGeo<DIM, P>;
+  T x[G::NCL];
+  T part[G::NCELL][G::NB];
+  T r[G::NCL];
+  const T* rowbase[G::NCELL];
+  int fe[kFeCap];
+  uint8_t item[G::NCELL * G::NB];
+};
+
+// One cut patch on one block.  Every load that depends only on the patch
+// metadata is issued in one round (closure of x, DoF lists, cell matrices,
+// ghost-face entries, row items, the TMA copy of the inverse); the residual
+// rows then read only shared memory, the cut-cell matrix rows and the
+// ghost-face moments; the solve splits each of the m rows over 128/m' lanes.
 template <int DIM, int P, typename T>
 __device__ __forceinline__ void cut_body_cta(const OpArgs<T>& A, const T* __restrict__ x,
-                                             const T* __restrict__ b, int vert, int m, int mo, int64_t io,
-                                             const uint16_t* __restrict__ members,
+                                             const T* __restrict__ b, const CutMeta& M, int j,
+                                             const CutPatchArgs& C, const uint16_t* __restrict__ members,
                                              const int* __restrict__ mnode, const int* __restrict__ fofs,
                                              const int* __restrict__ fent, const T* __restrict__ inv,
-                                             T* __restrict__ dbuf, PatchScratch<DIM, P, T>& S, T* sinv,
+                                             T* __restrict__ dbuf, CutScratch<DIM, P, T>& S, T* sinv,
                                              int inv_cap, uint64_t* bar, uint32_t& phase,
                                              const T* __restrict__ sK, int* err) {
-  const int tid = threadIdx.x;
+  using G = PatchGeo<DIM, P>;
+  constexpr int CC = G::C, NB = G::NB, NCL = G::NCL, NCELL = G::NCELL, NTF = FaceGeo<DIM, P>::NT;
+  static_assert(NCL <= kCutThreads, "one patch DoF per thread");
+  const int tid = threadIdx.x, m = M.m, n = A.n;
   const bool tma = m * m <= inv_cap;
   if (tma && tid == 0) {
     const uint32_t bytes = (uint32_t)(((size_t)m * m * sizeof(T) + 15) / 16 * 16);
-    tma_load_1d(sinv, inv + io, bytes, bar);
+    tma_load_1d(sinv, inv + M.io, bytes, bar);
   }
   const int np = A.N + 1;
-  int q = vert, v[3] = {0, 0, 0};
+  int v[3] = {0, 0, 0};
+  {
+    int q = M.vert;
 #pragma unroll
-  for (int k = 0; k < DIM; ++k) {
-    v[k] = q % np;
-    q /= np;
+    for (int k = 0; k < DIM; ++k) {
+      v[k] = q % np;
+      q /= np;
+    }
   }
-  patch_rows<DIM, P, T, kCutThreads>(A, x, v, members + mo, m, fofs + mo, fent, S, sK, tid);
-  for (int e = tid; e < m; e += kCutThreads) S.r[e] = b[mnode[mo + e]] - S.r[e];
+  // round 1: everything that depends on the metadata only
+  if (tid < NCL) {
+    int u = tid, c[3] = {0, 0, 0};
+    bool in = true;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+      c[k] = P * (v[k] - 1) + u % CC;
+      u /= CC;
+      if (c[k] < 0 || c[k] >= n) in = false;
+    }
+    S.x[tid] = in ? x[lat_index<DIM>(c, n)] : T(0);
+  }
+  if (tid < NCELL) {
+    const int id = C.cell[(size_t)j * NCELL + tid];
+    S.rowbase[tid] = id == -2 ? nullptr : (id == -1 ? sK : A.cutmat + (size_t)id * NB * NB);
+  }
+  const int nfe = M.f1 - M.f0, nit = M.i1 - M.i0;
+  const bool fe_smem = nfe <= kFeCap;
+  if (fe_smem)
+    for (int q = tid; q < nfe; q += kCutThreads) S.fe[q] = fent[M.f0 + q];
+  for (int q = tid; q < nit; q += kCutThreads) S.item[q] = C.items[M.i0 + q];
+  int tg = 0, fa = 0, fb = 0;
+  T bval = T(0);
+  if (tid < m) {
+    tg = members[M.mo + tid];
+    fa = fofs[M.mo + tid] - M.f0;
+    fb = fofs[M.mo + tid + 1] - M.f0;
+    bval = b[mnode[M.mo + tid]];
+  }
+  __syncthreads();
+  // round 2: ghost-face terms of the own row
+  T facc = T(0);
+  if (tid < m) {
+    const int* fe = fe_smem ? S.fe : fent + M.f0;
+    for (int q0 = fa; q0 < fb; q0 += 8) {
+      int ent[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) ent[u] = (q0 + u < fb) ? fe[q0 + u] : -1;
+      T gv[8][P];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (ent[u] < 0) continue;
+        const T* g = A.G + (size_t)(ent[u] >> 3) / NTF * (P * NTF) + (ent[u] >> 3) % NTF;
+#pragma unroll
+        for (int mm = 0; mm < P; ++mm) gv[u][mm] = g[mm * NTF];
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (ent[u] < 0) continue;
+        const int il = ent[u] & 7;
+#pragma unroll
+        for (int mm = 0; mm < P; ++mm) facc += A.dvec[mm][il] * gv[u][mm];
+      }
+    }
+  }
+  // rows (patch cell s, local node i) of the patch DoFs: row_i of the cell
+  // matrix against the cell's closure values
+  for (int q = tid; q < nit; q += kCutThreads) {
+    const int it = S.item[q], sc = it / NB, jj = it - sc * NB;
+    int base = 0, ost = 1;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+      base += P * ((sc >> k) & 1) * ost;
+      ost *= CC;
+    }
+    const T* row = S.rowbase[sc] + jj * NB;
+    T acc = T(0);
+    if (DIM == 2) {
+#pragma unroll
+      for (int q1 = 0; q1 <= P; ++q1)
+#pragma unroll
+        for (int q0 = 0; q0 <= P; ++q0) acc += row[q0 + (P + 1) * q1] * S.x[base + q0 + CC * q1];
+    } else {
+#pragma unroll
+      for (int q2 = 0; q2 <= P; ++q2)
+#pragma unroll
+        for (int q1 = 0; q1 <= P; ++q1)
+#pragma unroll
+          for (int q0 = 0; q0 <= P; ++q0)
+            acc += row[q0 + (P + 1) * (q1 + (P + 1) * q2)] * S.x[base + q0 + CC * (q1 + CC * q2)];
+    }
+    S.part[sc][jj] = acc;
+  }
+  __syncthreads();
+  // residual of the own row: cell parts in cell order, then the face terms
+  if (tid < m) {
+    int o[3] = {0, 0, 0}, u = tg;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+      o[k] = u % CC;
+      u /= CC;
+    }
+    T acc = T(0);
+#pragma unroll
+    for (int sc = 0; sc < NCELL; ++sc) {
+      int jj = 0, jst = 1;
+      bool in = S.rowbase[sc] != nullptr;
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) {
+        const int a = o[k] - P * ((sc >> k) & 1);
+        if (a < 0 || a > P) in = false;
+        jj += a * jst;
+        jst *= (P + 1);
+      }
+      if (in) acc += S.part[sc][jj];
+    }
+    S.r[tid] = bval - (acc + facc);
+  }
   bool ok = true;
   if (tma) {
     ok = mbar_wait(bar, phase & 1u);
@@ -872,42 +1056,62 @@ __device__ __forceinline__ void cut_body_cta(const OpArgs<T>& A, const T* __rest
     }
     phase += 1;
   }
-  __syncthreads();
+  // block-uniform outcome (the solve below shuffles across full warps)
+  ok = __syncthreads_and(ok) != 0;
   if (ok) {
-    const T* Ai = tma ? sinv : inv + io;
-    for (int e = tid; e < m; e += kCutThreads) {
-      T acc[4] = {T(0), T(0), T(0), T(0)};
-      int j = 0;
-      for (; j + 4 <= m; j += 4) {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) acc[u] += Ai[(size_t)(j + u) * m + e] * S.r[j + u];
+    // delta = A_j^{-1} r: row e split over K lanes (columns k, k + K, ..),
+    // the K partial sums combined by shuffles in a fixed order
+    const T* Ai = tma ? sinv : inv + M.io;
+    const int K = m <= 32 ? 4 : (m <= 64 ? 2 : 1);
+    for (int e0 = 0; e0 < m; e0 += kCutThreads / K) {
+      const int e = e0 + tid / K, k = tid - (tid / K) * K;
+      T a0 = T(0), a1 = T(0);
+      if (e < m) {
+        const T* Ar = Ai + (size_t)e * m;
+        int c = k;
+        for (; c + K < m; c += 2 * K) {
+          a0 += Ar[c] * S.r[c];
+          a1 += Ar[c + K] * S.r[c + K];
+        }
+        if (c < m) a0 += Ar[c] * S.r[c];
       }
-      for (; j < m; ++j) acc[0] += Ai[(size_t)j * m + e] * S.r[j];
-      dbuf[mo + e] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+      T a = a0 + a1;
+      if (K >= 4) a += __shfl_xor_sync(0xffffffffu, a, 2);
+      if (K >= 2) a += __shfl_xor_sync(0xffffffffu, a, 1);
+      if (e < m && k == 0) dbuf[M.mo + e] = a;
     }
   }
   __syncthreads();
 }
 
 template <int DIM, int P, typename T>
-__global__ void __launch_bounds__(kCutThreads) k_cut_solve_cta(
-    OpArgs<T> A, const T* __restrict__ x, const T* __restrict__ b, const int* __restrict__ verts,
-    const int* __restrict__ cnt, const int* __restrict__ moff, const int64_t* __restrict__ ioff,
-    const uint16_t* __restrict__ members, const int* __restrict__ mnode, const int* __restrict__ fofs,
-    const int* __restrict__ fent, const T* __restrict__ inv, T* __restrict__ dbuf, int npatch, int inv_cap,
-    int* err) {
+__global__ void __launch_bounds__(kCutThreads) k_cut_solve_cta(OpArgs<T> A, const T* __restrict__ x,
+                                                               const T* __restrict__ b, CutPatchArgs C,
+                                                               const uint16_t* __restrict__ members,
+                                                               const int* __restrict__ mnode,
+                                                               const int* __restrict__ fofs,
+                                                               const int* __restrict__ fent,
+                                                               const T* __restrict__ inv, T* __restrict__ dbuf,
+                                                               int j0, int npatch, int inv_cap, int* err) {
   constexpr int NB = Shape<DIM, P>::NB;
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ __align__(8) uint64_t bar;
   __shared__ T sK[NB * NB];
-  __shared__ PatchScratch<DIM, P, T> S;
+  __shared__ CutScratch<DIM, P, T> S;
   T* sinv = reinterpret_cast<T*>(dsm);
+  int j = blockIdx.x;
+  if (j >= npatch) return;
+  CutMeta cur = cut_meta(C, j0 + j);
   if (threadIdx.x == 0) mbar_init(&bar);
   stage_kref<NB>(A.Kref, sK);  // includes __syncthreads
   uint32_t phase = 0;
-  for (int pidx = blockIdx.x; pidx < npatch; pidx += gridDim.x)
-    cut_body_cta<DIM, P, T>(A, x, b, verts[pidx], cnt[pidx], moff[pidx], ioff[pidx], members, mnode, fofs, fent,
-                            inv, dbuf, S, sinv, inv_cap, &bar, phase, sK, err);
+  for (; j < npatch; j += gridDim.x) {
+    CutMeta nxt = cur;
+    if (j + (int)gridDim.x < npatch) nxt = cut_meta(C, j0 + j + gridDim.x);
+    cut_body_cta<DIM, P, T>(A, x, b, cur, j0 + j, C, members, mnode, fofs, fent, inv, dbuf, S, sinv, inv_cap,
+                            &bar, phase, sK, err);
+    cur = nxt;
+  }
 }
 
 // Phase 2: x[I_j] += delta for every DoF of the colour's patches.

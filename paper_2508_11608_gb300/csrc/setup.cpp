@@ -625,6 +625,47 @@ void build_level(const SetupParams& prm, const RefTables& R, int N, HostLevel& L
         L.cf_start[col + 1] = (int)L.cfaces.size();
       }
     }
+    // per cut patch, what its block loads up front: the range of its
+    // ghost-face entries, the element matrix of each patch cell and the
+    // (cell, local node) pairs whose rows it forms (node a patch DoF)
+    {
+      const int NCELL = 1 << d;
+      L.cut_fo.resize(ncp + 1);
+      L.cut_cell.assign((size_t)ncp * NCELL, -2);
+      L.cut_item_off.assign(ncp + 1, 0);
+      L.cut_items.clear();
+      std::vector<char> is_mem(NCL);
+      for (int64_t j = 0; j < ncp; ++j) {
+        L.cut_fo[j] = L.fofs[L.cut_moff[j]];
+        int v[3] = {0, 0, 0};
+        int64_t t = L.cut_vert[j];
+        for (int k = 0; k < d; ++k) {
+          v[k] = (int)(t % np);
+          t /= np;
+        }
+        std::fill(is_mem.begin(), is_mem.end(), 0);
+        for (int e = 0; e < L.cut_n[j]; ++e) is_mem[L.members[L.cut_moff[j] + e]] = 1;
+        for (int sc = 0; sc < NCELL; ++sc) {
+          int c[3] = {0, 0, 0};
+          for (int k = 0; k < d; ++k) c[k] = v[k] - 1 + ((sc >> k) & 1);
+          const uint8_t f = cflag_at(c);
+          if (!(f & kFlagActive)) continue;
+          const int64_t cell = c[0] + (int64_t)N * (c[1] + (d == 3 ? (int64_t)N * c[2] : 0));
+          L.cut_cell[(size_t)j * NCELL + sc] = (f & kFlagCut) ? L.cut_id[cell] : -1;
+          for (int jj = 0; jj < NB; ++jj) {
+            int o = 0, ost = 1, u = jj;
+            for (int k = 0; k < d; ++k) {
+              o += (p * ((sc >> k) & 1) + u % (p + 1)) * ost;
+              u /= (p + 1);
+              ost *= C;
+            }
+            if (is_mem[o]) L.cut_items.push_back((uint8_t)(sc * NB + jj));
+          }
+        }
+        L.cut_item_off[j + 1] = (int)L.cut_items.size();
+      }
+      L.cut_fo[ncp] = L.fofs[L.member_node.size()];
+    }
     // work model of the cut-patch solve (what the kernel computes per patch):
     // cell rows 2 NB per (active patch cell, target in it); ghost-face moments
     // 2 (2p+1) p NT + 2 p NT^2 per ghost face; 2 p per (target, ghost face);

@@ -59,6 +59,12 @@ struct HostLevel {
   // ghost faces those rows need (colour c: cfaces[cf_start[c] .. cf_start[c+1]))
   std::vector<int> fofs, fent;
   std::vector<int> cfaces, cf_start;
+  // per cut patch j: its ghost-face entries are fent[cut_fo[j] .. cut_fo[j+1]);
+  // cut_cell[j * 2^d + s] = cut-cell matrix of patch cell s (-1 uncut, -2
+  // inactive); cut_items[cut_item_off[j] ..] = s * NB + i for the rows
+  // (patch cell s, local node i) that belong to a patch DoF
+  std::vector<int> cut_fo, cut_cell, cut_item_off;
+  std::vector<uint8_t> cut_items;
   std::vector<double> inv;        // explicit FP64 inverses A_j^{-1}, row-major
   // algorithmic work per launch, used to report achieved FLOP/s and bytes:
   // per colour of the cut-patch solve and of the interior-patch step
