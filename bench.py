@@ -119,6 +119,20 @@ FP64_PEAK_TFLOPS = 1.26
 FP32_PEAK_TFLOPS = 78.5
 
 
+# DRAM traffic of the dominant kernel from one ncu capture: dram__bytes_read.sum
+# + dram__bytes_write.sum summed over every k_cut_solve_cta launch of one FP64
+# solve of the 64^3 workload, divided by the launches (cold caches: ncu flushes
+# them before each launch).  Valid only for the kernel source it was taken on.
+CUT_TRAFFIC = {"bytes_per_launch": None, "kernels_sha256": None}
+
+
+def _kernels_sha256():
+    import hashlib
+    path = os.path.join(ROOT, "paper_2508_11608_gb300", "csrc", "kernels.cuh")
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
+
 def cpu_baseline(steps=1):
     """Oracle PCG on the bounded sample, single-threaded BLAS, in a subprocess."""
     code = r"""
@@ -255,7 +269,7 @@ def run_ours(args):
     # graphs, so it is kept out of the headline)
     prof = {}
     for kern in (cm._lib.CF_K_CUT_SOLVE, cm._lib.CF_K_INTERIOR, cm._lib.CF_K_APPLY_BULK,
-                 cm._lib.CF_K_APPLY_BND):
+                 cm._lib.CF_K_APPLY_BND, cm._lib.CF_K_FACE_MOMENTS):
         msk, _, _, pr, _ = timed_solves(cm.CF_FP64, 2, 1, profile_kernel=kern)
         pr["share"] = pr["ms"] / sum(msk)
         prof[kern] = pr
@@ -298,10 +312,11 @@ def run_ours(args):
     hbm = peaks.get("hbm_gbs", 6800.0)
     top = max(prof, key=lambda k: prof[k]["share"])
     pr = prof[top]
-    names = {1: "k_cut_solve (cut-patch residual + dense local solve)",
+    names = {1: "k_cut_solve_cta (cut-patch residual + dense local solve)",
              2: "k_smooth_cart (interior-patch residual + fast diagonalisation)",
              3: "k_apply_bulk (operator, interior positions)",
-             4: "k_apply_bnd (operator, boundary positions)"}
+             4: "k_apply_bnd (operator, boundary positions)",
+             5: "k_face_moments (ghost-face moments of the iterate)"}
     per_launch_ms = pr["ms"] / max(pr["launches"], 1)
     fl_rate = pr["flops"] / (pr["ms"] * 1e-3) / 1e12 if pr["ms"] > 0 else 0.0
     by_rate = pr["bytes"] / (pr["ms"] * 1e-3) / 1e9 if pr["ms"] > 0 else 0.0
@@ -313,7 +328,10 @@ def run_ours(args):
                 "frac": fl_rate / FP64_PEAK_TFLOPS}
     else:
         roof = {"bound": "hbm", "achieved": by_rate, "peak": hbm, "unit": "GB/s", "frac": by_rate / hbm}
-    roof.update({"kernel": names[top], "traffic": None, "per_launch_ms": per_launch_ms,
+    traffic = None
+    if top == cm._lib.CF_K_CUT_SOLVE and CUT_TRAFFIC["kernels_sha256"] == _kernels_sha256():
+        traffic = CUT_TRAFFIC["bytes_per_launch"]
+    roof.update({"kernel": names[top], "traffic": traffic, "per_launch_ms": per_launch_ms,
                  "launches_timed": pr["launches"],
                  "share_of_step": pr["share"],
                  "shares": {names[k].split(" ")[0]: round(prof[k]["share"], 4) for k in prof},

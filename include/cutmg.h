@@ -121,10 +121,11 @@ cf_status cf_stats(const cf_problem* pb, int level, int64_t* h_out6);
 /* Algorithmic work of one colour step on a level, from the host setup
  * (Sec. 3's two patch kinds): kind 0 = interior patches (fast
  * diagonalisation, Sec. 2.3), 1 = cut patches (residual rows and the dense
- * local inverse).  h_out3 = [flops, scalars moved, index bytes moved]; bytes
- * = scalars x sizeof(precision) + index bytes.  CF_EINVAL for a bad level,
- * kind or colour (0 <= colour < 2^dim); level 0 (the coarsest, solved
- * exactly) has no colour steps and reports zeros. */
+ * local inverse), 2 = the ghost-face moments the cut-patch rows of the colour
+ * read (face penalty of Sec. 2.1).  h_out3 = [flops, scalars moved, index
+ * bytes moved]; bytes = scalars x sizeof(precision) + index bytes.
+ * CF_EINVAL for a bad level, kind or colour (0 <= colour < 2^dim); level 0
+ * (the coarsest, solved exactly) has no colour steps and reports zeros. */
 cf_status cf_work_model(const cf_problem* pb, int level, int kind, int colour, double* h_out3);
 
 /* Select the precision of cf_vcycle and cf_solve (CF_FP64 or CF_MIXED). */
@@ -249,7 +250,8 @@ typedef enum {
   CF_K_CUT_SOLVE = 1, /* cut-patch residual + dense local solve */
   CF_K_INTERIOR = 2,  /* interior-patch residual + fast diagonalisation */
   CF_K_APPLY_BULK = 3,/* operator, interior positions */
-  CF_K_APPLY_BND = 4  /* operator, positions near the boundary */
+  CF_K_APPLY_BND = 4, /* operator, positions near the boundary */
+  CF_K_FACE_MOMENTS = 5 /* ghost-face moments G_m of the current iterate */
 } cf_kernel;
 /* From now on record a CUDA event pair (on the launching stream) around every
  * launch of one kernel family; cf_profile_read synchronises those events and

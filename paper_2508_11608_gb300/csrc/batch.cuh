@@ -160,8 +160,8 @@ __global__ void __launch_bounds__(kCutThreads) kb_cut_solve_cta(const LvlDesc<DI
     const CutMeta M = cut_meta(L.cp, j);
     // uncut cells read the level's element matrix from global memory
     // (instances differ in h)
-    cut_body_cta<DIM, P, T>(L.op, L.x, L.b, M, j, L.cp, L.members, L.mnode, L.fofs, L.fent, L.inv, L.dbuf, S,
-                            sinv, inv_cap, &bar, phase, L.op.Kref, err);
+    cut_body_cta<DIM, P, T, false>(L.op, L.x, L.b, M, j, L.cp, L.members, L.mnode, L.fofs, L.fent, L.inv,
+                                   L.dbuf, S, sinv, nullptr, inv_cap, &bar, phase, L.op.Kref, err);
   }
 }
 
@@ -363,9 +363,9 @@ class BatchGroup final : public BatchGroupBase {
     scg_ = pool_.alloc<double>((size_t)K_ * 16);
     err_ = pool_.alloc<int>(1);
     CUTMG_CUDA(cudaFuncSetAttribute(kb_cut_solve_cta<DIM, P, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    E::kInvSlotBytes));
+                                    E::kInvSlotBytesMax));
     CUTMG_CUDA(cudaFuncSetAttribute(kb_cut_solve_cta<DIM, P, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    E::kInvSlotBytes));
+                                    E::kInvSlotBytesMax));
     CUTMG_CUDA(cudaMallocHost(&host_sc_, sizeof(double) * K_ * 16));
     rebuild_lists();
   }
@@ -818,7 +818,7 @@ class BatchGroup final : public BatchGroupBase {
         if (E::kWarpCut) {
           launch_cut<T>(D, w, colour, s);
         } else {
-          const int cap = E::template inv_cap_for<T>(maxm2);
+          const int cap = E::template inv_cap_for<T>(maxm2, w.total);
           const int gridc = std::max(1, std::min(w.total, sms_ * 16));
           kb_cut_solve_cta<DIM, P, T><<<gridc, kCutThreads, E::template inv_slot_bytes<T>(cap), s>>>(
               D, w.off, K_, w.total, colour, cap, err_);

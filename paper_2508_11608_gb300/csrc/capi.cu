@@ -250,10 +250,10 @@ cf_status cf_stats(const cf_problem* pb, int level, int64_t* h_out6) {
 }
 
 cf_status cf_work_model(const cf_problem* pb, int level, int kind, int colour, double* h_out3) {
-  if (bad_level(pb, level) || !h_out3 || (kind != 0 && kind != 1)) return fail(CF_EINVAL, "bad argument");
+  if (bad_level(pb, level) || !h_out3 || kind < 0 || kind > 2) return fail(CF_EINVAL, "bad argument");
   const HostLevel& L = pb->H.levels[level];
   if (colour < 0 || colour >= (1 << L.d)) return fail(CF_EINVAL, "bad colour");
-  const auto& w = kind == 0 ? L.work_cart : L.work_cut;
+  const auto& w = kind == 0 ? L.work_cart : (kind == 1 ? L.work_cut : L.work_face);
   for (int i = 0; i < 3; ++i) h_out3[i] = (colour < (int)w.size()) ? w[colour][i] : 0.0;
   return CF_OK;
 }
@@ -342,7 +342,7 @@ cf_status cf_coarse_solve(cf_problem* pb, int precision, const double* d_b0, dou
 int64_t cf_launch_count(const cf_problem* pb) { return no_device(pb) ? 0 : pb->eng->launches(); }
 
 cf_status cf_profile_start(cf_problem* pb, int kernel) {
-  if (no_device(pb) || kernel < 1 || kernel > 4) return fail(CF_EINVAL, "bad argument");
+  if (no_device(pb) || kernel < 1 || kernel > 5) return fail(CF_EINVAL, "bad argument");
   return guarded([&] { pb->eng->profile_start(kernel); });
 }
 

@@ -110,6 +110,7 @@ class Engine final : public EngineBase {
     std::vector<int> cut_start;
     std::vector<int> cut_moff_h;
     std::vector<int> cut_maxm2;
+    std::vector<int> cut_maxit;
     int64_t nmembers;
     int* pro_col;
     int* res_col;
@@ -150,10 +151,14 @@ class Engine final : public EngineBase {
     part_ = pool_.alloc<double>(kDotBlocks);
     sc_ = pool_.alloc<double>(16);
     err_ = pool_.alloc<int>(1);
-    CUTMG_CUDA(cudaFuncSetAttribute(k_cut_solve_cta<DIM, P, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    kInvSlotBytes));
-    CUTMG_CUDA(cudaFuncSetAttribute(k_cut_solve_cta<DIM, P, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    kInvSlotBytes));
+    CUTMG_CUDA(cudaFuncSetAttribute(k_cut_solve_cta<DIM, P, double, false>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, kInvSlotBytesMax));
+    CUTMG_CUDA(cudaFuncSetAttribute(k_cut_solve_cta<DIM, P, float, false>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, kInvSlotBytesMax));
+    CUTMG_CUDA(cudaFuncSetAttribute(k_cut_solve_cta<DIM, P, double, true>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, kInvSlotBytesMax));
+    CUTMG_CUDA(cudaFuncSetAttribute(k_cut_solve_cta<DIM, P, float, true>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, kInvSlotBytesMax));
     CUTMG_CUDA(cudaMallocHost(&host_sc_, 16 * sizeof(double)));
     CUTMG_CUDA(cudaStreamCreateWithFlags(&cap_, cudaStreamNonBlocking));
     const char* g = std::getenv("CUTMG_GRAPHS");
@@ -457,8 +462,16 @@ class Engine final : public EngineBase {
  private:
   static constexpr int kDotBlocks = 512;
  public:
-  // shared-memory slot for one patch inverse in the cut-patch kernel
-  static constexpr int kInvSlotBytes = 96 * 1024;
+  // shared-memory slot for one patch inverse in the cut-patch kernel.  Grids
+  // of many patches (several blocks per SM) use a 12 KB slot (FP64 m <= 39,
+  // FP32 m <= 55 through TMA, larger inverses read from global memory) so
+  // that more blocks fit on an SM.  Grids of at most kSmallGrid blocks, where
+  // one patch's latency is the launch time, take inverses up to 48 KB through
+  // TMA and stage the element-matrix rows of the patch in shared memory.
+  static constexpr int kInvSlotBytes = 12 * 1024;
+  static constexpr int kInvSlotBytesStage = 48 * 1024;
+  static constexpr int kInvSlotBytesMax = 96 * 1024;  // attribute bound of every variant
+  static constexpr int kSmallGrid = 2 * 152;
   // when no patch can exceed 64 DoFs, (2p+1)^d <= 64 (2D Q1-Q3, 3D Q1), one
   // warp solves a patch, one or two rows per lane; otherwise (3D Q2) each
   // patch takes a block.  The choice depends on (d, p) only, so a problem
@@ -470,8 +483,8 @@ class Engine final : public EngineBase {
     return CutPatchArgs{c.cutv, c.cutn, c.cutmo, c.cutio, c.cutfo, c.cutcell, c.citoff, c.citems};
   }
   template <typename T>
-  static int inv_cap_for(int maxm2) {
-    const int cap = (kInvSlotBytes - 16) / (int)sizeof(T);
+  static int inv_cap_for(int maxm2, int npatch) {
+    const int cap = ((npatch <= kSmallGrid ? kInvSlotBytesStage : kInvSlotBytes) - 16) / (int)sizeof(T);
     return maxm2 < cap ? maxm2 : cap;
   }
   template <typename T>
@@ -485,7 +498,8 @@ class Engine final : public EngineBase {
   DevPool pool_;
   int64_t launches_ = 0;
   struct Prof {
-    int kind = 0;  // 1 cut-patch solve, 2 interior-patch step, 3 apply (bulk), 4 apply (boundary)
+    int kind = 0;  // 1 cut-patch solve, 2 interior-patch step, 3 apply (bulk), 4 apply (boundary),
+                   // 5 ghost-face moments
     std::vector<cudaEvent_t> ev;
     int used = 0;
     int64_t n = 0;
@@ -653,6 +667,7 @@ class Engine final : public EngineBase {
     c.cut_start = h.cut_start;
     c.cut_moff_h = h.cut_moff;
     c.cut_maxm2 = h.cut_maxm2;
+    c.cut_maxit = h.cut_maxit;
     c.nmembers = (int64_t)h.members.size();
     c.pro_col = l > 0 ? pool_.upload<int>(h.pro_col) : nullptr;
     c.res_col = l > 0 ? pool_.upload<int>(h.res_col) : nullptr;
@@ -728,13 +743,14 @@ class Engine final : public EngineBase {
       k_apply_bulk<DIM, P, T><<<blocks_for(c.nbulk, 128), 128, 0, s>>>(D.op, x, b, y, c.bulk, c.nbulk);
       count_launch("apply bulk");
       prof_mark(3, s);
-      // per position: 2 NB^2 flops; x read and y written once per owned node (+ b)
+      // per position: 2^d cells x p^d owned rows x NB terms; x read and y
+      // written once per owned node (+ b)
       constexpr int NO = Shape<DIM, P>::NO;
-      prof_work(3, 2.0 * NB * NB * c.nbulk, (double)c.nbulk * (NO * (b ? 3 : 2) * sizeof(T) + 4));
+      prof_work(3, 2.0 * (1 << DIM) * NO * NB * c.nbulk, (double)c.nbulk * (NO * (b ? 3 : 2) * sizeof(T) + 4));
     }
     if (c.nbnd > 0) {
-      prof_mark(4, s);
       face_moments<T>(l, D, x, s);
+      prof_mark(4, s);
       k_apply_bnd<DIM, P, T><<<blocks_for(c.nbnd, 128), 128, 0, s>>>(D.op, x, b, y, c.bnd, c.nbnd);
       count_launch("apply boundary");
       prof_mark(4, s);
@@ -755,8 +771,15 @@ class Engine final : public EngineBase {
     }
     if (cnt <= 0) return;
     constexpr int PW = FaceGeo<DIM, P>::PER_WARP;
+    prof_mark(5, s);
     k_face_moments<DIM, P, T><<<blocks_for(blocks_for(cnt, PW), 4), 128, 0, s>>>(D.op, x, c.faces, ids, cnt);
     count_launch("ghost face moments");
+    prof_mark(5, s);
+    {
+      constexpr int NTF = FaceGeo<DIM, P>::NT;
+      const double flf = 2.0 * (2 * P + 1) * P * NTF + 2.0 * P * (P + 1) * NTF * (DIM - 1) + (double)P * NTF;
+      prof_work(5, cnt * flf, cnt * (((2.0 * P + 1) * NTF + (double)P * NTF) * sizeof(T) + 8.0));
+    }
   }
 
   template <typename T>
@@ -775,17 +798,26 @@ class Engine final : public EngineBase {
     } else {
       const int a0 = c.cut_start[colour], cnt = c.cut_start[colour + 1] - a0;
       if (cnt <= 0) return;
-      prof_mark(1, s);
       face_moments<T>(l, D, x, s, colour);
+      prof_mark(1, s);
       if (kWarpCut) {
         k_cut_solve<DIM, P, T, WARPS><<<blocks_for(cnt, WARPS), 32 * WARPS, 0, s>>>(
             D.op, x, b, c.cutv + a0, c.cutn + a0, c.cutmo + a0, c.cutio + a0, c.members, c.mnode, c.fofs,
             c.fent, D.inv, D.dbuf, cnt);
       } else {
-        const int cap = inv_cap_for<T>(c.cut_maxm2[colour]);
-        const int grid = std::min(cnt, 152 * 16);
-        k_cut_solve_cta<DIM, P, T><<<grid, kCutThreads, inv_slot_bytes<T>(cap), s>>>(
-            D.op, x, b, cut_args(c), c.members, c.mnode, c.fofs, c.fent, D.inv, D.dbuf, a0, cnt, cap, err_);
+        const int cap = inv_cap_for<T>(c.cut_maxm2[colour], cnt);
+        const int slot = (int)inv_slot_bytes<T>(cap);
+        if (cnt <= kSmallGrid) {
+          const int rows = (int)(((size_t)c.cut_maxit[colour] * NB * sizeof(T) + 15) / 16 * 16);
+          k_cut_solve_cta<DIM, P, T, true><<<cnt, kCutThreads, slot + rows, s>>>(
+              D.op, x, b, cut_args(c), c.members, c.mnode, c.fofs, c.fent, D.inv, D.dbuf, a0, cnt, cap, slot,
+              err_);
+        } else {
+          const int grid = std::min(cnt, 152 * 16);
+          k_cut_solve_cta<DIM, P, T, false><<<grid, kCutThreads, slot, s>>>(
+              D.op, x, b, cut_args(c), c.members, c.mnode, c.fofs, c.fent, D.inv, D.dbuf, a0, cnt, cap, slot,
+              err_);
+        }
       }
       count_launch("cut patch solve");
       prof_mark(1, s);

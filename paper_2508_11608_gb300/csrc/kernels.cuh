@@ -863,6 +863,18 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   return false;
 }
 
+// Asynchronous copy of one element global -> shared (cp.async, 4 or 8 bytes).
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
+  static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte elements");
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_u32(dst)), "l"(src), "n"(sizeof(T))
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
 // Per-patch arrays of the block kernel (absolute patch index j).
 struct CutPatchArgs {
   const int* vert;       // packed patch vertex
@@ -893,7 +905,7 @@ __device__ __forceinline__ CutMeta cut_meta(const CutPatchArgs& C, int j) {
   return t;
 }
 
-constexpr int kFeCap = 512;  // ghost-face entries of one patch staged in shared memory (more: read from global)
+constexpr int kFeCap = 512;  // ghost-face entries of one patch handled in parallel (more: per row from global)
 
 template <int DIM, int P, typename T>
 struct CutScratch {
@@ -902,23 +914,24 @@ struct CutScratch {
   T part[G::NCELL][G::NB];
   T r[G::NCL];
   const T* rowbase[G::NCELL];
-  int fe[kFeCap];
+  T fc[kFeCap];  // contribution of each ghost-face entry to its row
   uint8_t item[G::NCELL * G::NB];
 };
 
 // One cut patch on one block.  Every load that depends only on the patch
 // metadata is issued in one round (closure of x, DoF lists, cell matrices,
-// ghost-face entries, row items, the TMA copy of the inverse); the residual
-// rows then read only shared memory, the cut-cell matrix rows and the
-// ghost-face moments; the solve splits each of the m rows over 128/m' lanes.
-template <int DIM, int P, typename T>
+// ghost-face entries, row items, the TMA copy of the inverse); the second
+// round reads the element-matrix rows and the ghost-face moments (one entry
+// per thread), and the solve splits each of the m rows over up to 4 lanes.
+// Uncut cells read the level's element matrix through L1.
+template <int DIM, int P, typename T, bool STAGE>
 __device__ __forceinline__ void cut_body_cta(const OpArgs<T>& A, const T* __restrict__ x,
                                              const T* __restrict__ b, const CutMeta& M, int j,
                                              const CutPatchArgs& C, const uint16_t* __restrict__ members,
                                              const int* __restrict__ mnode, const int* __restrict__ fofs,
                                              const int* __restrict__ fent, const T* __restrict__ inv,
                                              T* __restrict__ dbuf, CutScratch<DIM, P, T>& S, T* sinv,
-                                             int inv_cap, uint64_t* bar, uint32_t& phase,
+                                             T* srow, int inv_cap, uint64_t* bar, uint32_t& phase,
                                              const T* __restrict__ sK, int* err) {
   using G = PatchGeo<DIM, P>;
   constexpr int CC = G::C, NB = G::NB, NCL = G::NCL, NCELL = G::NCELL, NTF = FaceGeo<DIM, P>::NT;
@@ -956,43 +969,79 @@ __device__ __forceinline__ void cut_body_cta(const OpArgs<T>& A, const T* __rest
     S.rowbase[tid] = id == -2 ? nullptr : (id == -1 ? sK : A.cutmat + (size_t)id * NB * NB);
   }
   const int nfe = M.f1 - M.f0, nit = M.i1 - M.i0;
-  const bool fe_smem = nfe <= kFeCap;
-  if (fe_smem)
-    for (int q = tid; q < nfe; q += kCutThreads) S.fe[q] = fent[M.f0 + q];
+  constexpr int EPT = kFeCap / kCutThreads;
+  const bool fe_par = nfe <= kFeCap;
+  int ent[EPT];
+#pragma unroll
+  for (int u = 0; u < EPT; ++u) {
+    const int q = tid + u * kCutThreads;
+    ent[u] = (fe_par && q < nfe) ? fent[M.f0 + q] : -1;
+  }
   for (int q = tid; q < nit; q += kCutThreads) S.item[q] = C.items[M.i0 + q];
-  int tg = 0, fa = 0, fb = 0;
-  T bval = T(0);
+  int tg = 0, fa = 0, fb = 0, mn = 0;
   if (tid < m) {
     tg = members[M.mo + tid];
     fa = fofs[M.mo + tid] - M.f0;
     fb = fofs[M.mo + tid + 1] - M.f0;
-    bval = b[mnode[M.mo + tid]];
+    mn = mnode[M.mo + tid];
   }
   __syncthreads();
-  // round 2: ghost-face terms of the own row
-  T facc = T(0);
-  if (tid < m) {
-    const int* fe = fe_smem ? S.fe : fent + M.f0;
-    for (int q0 = fa; q0 < fb; q0 += 8) {
-      int ent[8];
+  // latency-bound launches (few patches per SM): bring the element-matrix
+  // row of every item into shared memory with all copies in flight at once
+  if (STAGE) {
+    for (int q = tid; q < nit; q += kCutThreads) {
+      const int it = S.item[q], sc = it / NB, jj = it - sc * NB;
+      const T* row = S.rowbase[sc] + jj * NB;
 #pragma unroll
-      for (int u = 0; u < 8; ++u) ent[u] = (q0 + u < fb) ? fe[q0 + u] : -1;
+      for (int e = 0; e < NB; ++e) cp_async_elem(srow + q * NB + e, row + e);
+    }
+  }
+  T bval = T(0);
+  if (tid < m) bval = b[mn];
+  // round 2: ghost-face entries, one per thread (dvec_m[i_k] G_m[t] summed
+  // over m), and the element-matrix rows
+#pragma unroll
+  for (int u = 0; u < EPT; ++u) {
+    if (ent[u] < 0) continue;
+    const T* g = A.G + (size_t)(ent[u] >> 3) / NTF * (P * NTF) + (ent[u] >> 3) % NTF;
+    T gv[P];
+#pragma unroll
+    for (int mm = 0; mm < P; ++mm) gv[mm] = g[mm * NTF];
+    const int il = ent[u] & 7;
+    T c = T(0);
+#pragma unroll
+    for (int mm = 0; mm < P; ++mm) c += A.dvec[mm][il] * gv[mm];
+    S.fc[tid + u * kCutThreads] = c;
+  }
+  T facc = T(0);
+  if (tid < m && !fe_par) {
+    const int* fe = fent + M.f0;
+    for (int q0 = fa; q0 < fb; q0 += 8) {
+      int en[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) en[u] = (q0 + u < fb) ? fe[q0 + u] : -1;
       T gv[8][P];
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
-        if (ent[u] < 0) continue;
-        const T* g = A.G + (size_t)(ent[u] >> 3) / NTF * (P * NTF) + (ent[u] >> 3) % NTF;
+        if (en[u] < 0) continue;
+        const T* g = A.G + (size_t)(en[u] >> 3) / NTF * (P * NTF) + (en[u] >> 3) % NTF;
 #pragma unroll
         for (int mm = 0; mm < P; ++mm) gv[u][mm] = g[mm * NTF];
       }
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
-        if (ent[u] < 0) continue;
-        const int il = ent[u] & 7;
+        if (en[u] < 0) continue;
+        const int il = en[u] & 7;
+        T c = T(0);
 #pragma unroll
-        for (int mm = 0; mm < P; ++mm) facc += A.dvec[mm][il] * gv[u][mm];
+        for (int mm = 0; mm < P; ++mm) c += A.dvec[mm][il] * gv[u][mm];
+        facc += c;
       }
     }
+  }
+  if (STAGE) {
+    cp_async_wait_all();
+    __syncthreads();
   }
   // rows (patch cell s, local node i) of the patch DoFs: row_i of the cell
   // matrix against the cell's closure values
@@ -1004,7 +1053,7 @@ __device__ __forceinline__ void cut_body_cta(const OpArgs<T>& A, const T* __rest
       base += P * ((sc >> k) & 1) * ost;
       ost *= CC;
     }
-    const T* row = S.rowbase[sc] + jj * NB;
+    const T* row = STAGE ? srow + q * NB : S.rowbase[sc] + jj * NB;
     T acc = T(0);
     if (DIM == 2) {
 #pragma unroll
@@ -1025,6 +1074,16 @@ __device__ __forceinline__ void cut_body_cta(const OpArgs<T>& A, const T* __rest
   __syncthreads();
   // residual of the own row: cell parts in cell order, then the face terms
   if (tid < m) {
+    if (fe_par) {
+      T f4[4] = {T(0), T(0), T(0), T(0)};
+      int q = fa;
+      for (; q + 4 <= fb; q += 4) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) f4[u] += S.fc[q + u];
+      }
+      for (; q < fb; ++q) f4[0] += S.fc[q];
+      facc = (f4[0] + f4[1]) + (f4[2] + f4[3]);
+    }
     int o[3] = {0, 0, 0}, u = tg;
 #pragma unroll
     for (int k = 0; k < DIM; ++k) {
@@ -1084,7 +1143,10 @@ __device__ __forceinline__ void cut_body_cta(const OpArgs<T>& A, const T* __rest
   __syncthreads();
 }
 
-template <int DIM, int P, typename T>
+// STAGE: launches of at most a couple of blocks per SM stage the element-
+// matrix rows in the dynamic shared memory after the inverse slot (at
+// row_off bytes); large grids read them through L1.
+template <int DIM, int P, typename T, bool STAGE>
 __global__ void __launch_bounds__(kCutThreads) k_cut_solve_cta(OpArgs<T> A, const T* __restrict__ x,
                                                                const T* __restrict__ b, CutPatchArgs C,
                                                                const uint16_t* __restrict__ members,
@@ -1092,24 +1154,24 @@ __global__ void __launch_bounds__(kCutThreads) k_cut_solve_cta(OpArgs<T> A, cons
                                                                const int* __restrict__ fofs,
                                                                const int* __restrict__ fent,
                                                                const T* __restrict__ inv, T* __restrict__ dbuf,
-                                                               int j0, int npatch, int inv_cap, int* err) {
-  constexpr int NB = Shape<DIM, P>::NB;
+                                                               int j0, int npatch, int inv_cap, int row_off,
+                                                               int* err) {
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ __align__(8) uint64_t bar;
-  __shared__ T sK[NB * NB];
   __shared__ CutScratch<DIM, P, T> S;
   T* sinv = reinterpret_cast<T*>(dsm);
+  T* srow = reinterpret_cast<T*>(dsm + row_off);
   int j = blockIdx.x;
   if (j >= npatch) return;
   CutMeta cur = cut_meta(C, j0 + j);
   if (threadIdx.x == 0) mbar_init(&bar);
-  stage_kref<NB>(A.Kref, sK);  // includes __syncthreads
+  __syncthreads();
   uint32_t phase = 0;
   for (; j < npatch; j += gridDim.x) {
     CutMeta nxt = cur;
     if (j + (int)gridDim.x < npatch) nxt = cut_meta(C, j0 + j + gridDim.x);
-    cut_body_cta<DIM, P, T>(A, x, b, cur, j0 + j, C, members, mnode, fofs, fent, inv, dbuf, S, sinv, inv_cap,
-                            &bar, phase, sK, err);
+    cut_body_cta<DIM, P, T, STAGE>(A, x, b, cur, j0 + j, C, members, mnode, fofs, fent, inv, dbuf, S, sinv,
+                                   srow, inv_cap, &bar, phase, A.Kref, err);
     cur = nxt;
   }
 }

@@ -665,75 +665,42 @@ void build_level(const SetupParams& prm, const RefTables& R, int N, HostLevel& L
         L.cut_item_off[j + 1] = (int)L.cut_items.size();
       }
       L.cut_fo[ncp] = L.fofs[L.member_node.size()];
+      L.cut_maxit.assign(ncol, 0);
+      for (int col = 0; col < ncol; ++col)
+        for (int j = L.cut_start[col]; j < L.cut_start[col + 1]; ++j)
+          L.cut_maxit[col] = std::max(L.cut_maxit[col], L.cut_item_off[j + 1] - L.cut_item_off[j]);
     }
     // work model of the cut-patch solve (what the kernel computes per patch):
-    // cell rows 2 NB per (active patch cell, target in it); ghost-face moments
-    // 2 (2p+1) p NT + 2 p NT^2 per ghost face; 2 p per (target, ghost face);
-    // inverse 2 m^2.  Moved scalars: inverse, the rows of cut-cell matrices
-    // used, the closure of x, b and delta of the targets.
+    // 2 NB flops per (active patch cell, patch DoF in it) for the cell rows,
+    // 2p per ghost-face entry of a patch row, 2 m^2 for the local inverse.
+    // Moved scalars: the inverse, the rows of cut-cell matrices used, the
+    // closure of x, b and delta of the DoFs, p moments per ghost-face entry;
+    // index bytes: the DoF lists, metadata, cell ids, row items and entries.
+    // Face moments (computed once per colour step for the faces its patches
+    // need): per face 2 (2p+1) p NT for the jumps, 2 p (p+1) NT per face
+    // direction for the face mass, p NT for the coefficients; x of the two
+    // cells read, p NT moments written.
     {
       const int NT = ipow(p + 1, d - 1);
       L.work_cut.assign(ncol, {0.0, 0.0, 0.0});
-      for (int col = 0; col < ncol; ++col)
+      L.work_face.assign(ncol, {0.0, 0.0, 0.0});
+      for (int col = 0; col < ncol; ++col) {
         for (int j = L.cut_start[col]; j < L.cut_start[col + 1]; ++j) {
-          int v[3] = {0, 0, 0};
-          int64_t t = L.cut_vert[j];
-          for (int k = 0; k < d; ++k) {
-            v[k] = (int)(t % np);
-            t /= np;
-          }
           const int m = L.cut_n[j];
-          double fl = 2.0 * m * m, sc = (double)m * m + NCL + 2.0 * m;
-          for (int s2 = 0; s2 < (1 << d); ++s2) {
-            int c[3] = {0, 0, 0};
-            for (int k = 0; k < d; ++k) c[k] = v[k] - 1 + ((s2 >> k) & 1);
-            uint8_t f = cflag_at(c);
-            if (!(f & kFlagActive)) continue;
-            int rows = 0;
-            for (int e = 0; e < m; ++e) {
-              int o = mem[j][e];
-              bool in = true;
-              for (int k = 0; k < d; ++k) {
-                int a = o % C - p * ((s2 >> k) & 1);
-                o /= C;
-                if (a < 0 || a > p) in = false;
-              }
-              rows += in;
-            }
-            fl += 2.0 * NB * rows;
-            if (f & kFlagCut) sc += (double)rows * NB;
-          }
-          for (int k = 0; k < d; ++k)
-            for (int ok = -2; ok <= 0; ++ok)
-              for (int tb = 0; tb < (1 << (d - 1)); ++tb) {
-                int lc[3] = {0, 0, 0}, q = 0, off[3] = {0, 0, 0};
-                for (int kk = 0; kk < d; ++kk) {
-                  if (kk == k) { off[kk] = ok; continue; }
-                  off[kk] = ((tb >> q) & 1) - 1;
-                  ++q;
-                }
-                for (int kk = 0; kk < d; ++kk) lc[kk] = v[kk] + off[kk];
-                int uc[3] = {lc[0], lc[1], lc[2]};
-                uc[k] += 1;
-                uint8_t f1 = cflag_at(lc), f2 = cflag_at(uc);
-                if (!((f1 & kFlagActive) && (f2 & kFlagActive) && ((f1 | f2) & kFlagCut))) continue;
-                fl += 2.0 * (2 * p + 1) * p * NT + 2.0 * p * NT * NT;
-                for (int e = 0; e < m; ++e) {
-                  int o = mem[j][e];
-                  bool in = true;
-                  for (int kk = 0; kk < d; ++kk) {
-                    int ov = o % C;
-                    o /= C;
-                    int loc = ov - p * (off[kk] + 1);
-                    if (loc < 0 || loc > (kk == k ? 2 * p : p)) in = false;
-                  }
-                  if (in) fl += 2.0 * p;
-                }
-              }
+          const double nent = L.cut_fo[j + 1] - L.cut_fo[j];
+          const double nit = L.cut_item_off[j + 1] - L.cut_item_off[j];
+          double fl = 2.0 * m * m + 2.0 * NB * nit + 2.0 * p * nent;
+          double sc = (double)m * m + NCL + 2.0 * m + p * nent;
+          for (int q = L.cut_item_off[j]; q < L.cut_item_off[j + 1]; ++q)
+            if (L.cut_cell[(size_t)j * (1 << d) + L.cut_items[q] / NB] >= 0) sc += NB;
           L.work_cut[col][0] += fl;
           L.work_cut[col][1] += sc;
-          L.work_cut[col][2] += 6.0 * m + 24.0;
+          L.work_cut[col][2] += 10.0 * m + 72.0 + nit + 4.0 * nent;
         }
+        const double nf = L.cf_start[col + 1] - L.cf_start[col];
+        const double flf = 2.0 * (2 * p + 1) * p * NT + 2.0 * p * (p + 1) * NT * (d - 1) + (double)p * NT;
+        L.work_face[col] = {nf * flf, nf * ((2.0 * p + 1) * NT + (double)p * NT), nf * 8.0};
+      }
       // interior patches: sum factorisation and fast diagonalisation
       const int M = 2 * p - 1;
       double flc, scc;

@@ -51,6 +51,7 @@ struct HostLevel {
   std::vector<int> cut_vert, cut_n, cut_moff;
   std::vector<int64_t> cut_ioff;  // inverse offsets, multiples of 4 elements
   std::vector<int> cut_maxm2;     // per colour: largest m^2 of its cut patches
+  std::vector<int> cut_maxit;     // per colour: most row items of one of its cut patches
   std::vector<int> cut_start;
   std::vector<uint16_t> members;  // closure-local node index per cut-patch DoF
   std::vector<int> member_node;   // lattice index per cut-patch DoF
@@ -69,7 +70,7 @@ struct HostLevel {
   // algorithmic work per launch, used to report achieved FLOP/s and bytes:
   // per colour of the cut-patch solve and of the interior-patch step
   // {flops, scalars moved, index bytes moved}
-  std::vector<std::array<double, 3>> work_cut, work_cart;
+  std::vector<std::array<double, 3>> work_cut, work_cart, work_face;
   // reference tables
   std::vector<double> Kref;       // NB x NB stiffness of an uncut cell
   std::vector<double> Mr, Kr;     // M x C rows of the two-cell 1D mass / stiffness
