@@ -48,8 +48,7 @@ struct LvlDesc {
   const int* bulk;
   const int* bnd;
   const T* inv;
-  T* dbuf;
-  int cart_start[9], cut_start[9], cf_start[9], mem_start[9];
+  int cart_start[9], cut_start[9], cf_start[9];
   int nfaces;
   const T* coarse_inv;
   const int* coarse_nodes;
@@ -136,7 +135,7 @@ __global__ void __launch_bounds__(32 * WARPS) kb_cut_solve(const LvlDesc<DIM, P,
     const LvlDesc<DIM, P, T>& L = D[i];
     const int j = L.cut_start[colour] + it - off[i];
     cut_body<DIM, P, T>(L.op, L.x, L.b, L.cutv[j], L.cutn[j], L.cutmo[j], L.cutio[j], L.members, L.mnode,
-                        L.fofs, L.fent, L.inv, L.dbuf, sS[w], L.op.Kref, lane);
+                        L.fofs, L.fent, L.inv, sS[w], L.op.Kref, lane);
     __syncwarp();
   }
 }
@@ -160,20 +159,8 @@ __global__ void __launch_bounds__(kCutThreads) kb_cut_solve_cta(const LvlDesc<DI
     const CutMeta M = cut_meta(L.cp, j);
     // uncut cells read the level's element matrix from global memory
     // (instances differ in h)
-    cut_body_cta<DIM, P, T, false>(L.op, L.x, L.b, M, j, L.cp, L.members, L.mnode, L.fofs, L.fent, L.inv,
-                                   L.dbuf, S, sinv, nullptr, inv_cap, &bar, phase, L.op.Kref, err);
-  }
-}
-
-template <int DIM, int P, typename T>
-__global__ void __launch_bounds__(256) kb_cut_scatter(const LvlDesc<DIM, P, T>* __restrict__ D,
-                                                      const int* __restrict__ off, int K, int total,
-                                                      int colour) {
-  for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < total; it += gridDim.x * blockDim.x) {
-    const int i = find_inst(off, K, it);
-    const LvlDesc<DIM, P, T>& L = D[i];
-    const int m = L.mem_start[colour] + it - off[i];
-    L.x[L.mnode[m]] += L.dbuf[m];
+    cut_body_cta<DIM, P, T, false>(L.op, L.x, L.b, M, j, L.cp, L.members, L.mnode, L.fofs, L.fent, L.inv, S,
+                                   sinv, nullptr, inv_cap, &bar, phase, L.op.Kref, err);
   }
 }
 
@@ -550,7 +537,7 @@ class BatchGroup final : public BatchGroupBase {
     int* off = nullptr;  // device, K + 1
     int total = 0;
   };
-  std::vector<std::vector<Work>> w_cart_, w_cut_, w_mem_, w_cf_;  // [depth][colour]
+  std::vector<std::vector<Work>> w_cart_, w_cut_, w_cf_;  // [depth][colour]
   std::vector<Work> w_bulk_, w_bnd_, w_faces_, w_coarse_, w_xzero_;
   std::vector<std::array<Work, 3>> w_rpass_, w_ppass_;
   Work w_vecF_;
@@ -630,13 +617,10 @@ class BatchGroup final : public BatchGroupBase {
         L.bulk = C.bulk;
         L.bnd = C.bnd;
         L.inv = Ty.inv;
-        L.dbuf = Ty.dbuf;
         for (int c = 0; c <= NCOL; ++c) {
           L.cart_start[c] = C.cart_start[c];
           L.cut_start[c] = C.cut_start[c];
           L.cf_start[c] = C.cf_start[c];
-          L.mem_start[c] = C.cut_start[c] < (int)C.cut_moff_h.size() ? C.cut_moff_h[C.cut_start[c]]
-                                                                     : (int)C.nmembers;
         }
         L.nfaces = C.nfaces;
         L.coarse_inv = Ty.coarse_inv;
@@ -675,7 +659,6 @@ class BatchGroup final : public BatchGroupBase {
     // (device memory of old lists is kept in the pool; rebuilds are rare)
     w_cart_.assign(depth_, std::vector<Work>(NCOL));
     w_cut_.assign(depth_, std::vector<Work>(NCOL));
-    w_mem_.assign(depth_, std::vector<Work>(NCOL));
     w_cf_.assign(depth_, std::vector<Work>(NCOL));
     w_bulk_.assign(depth_, Work{});
     w_bnd_.assign(depth_, Work{});
@@ -703,12 +686,6 @@ class BatchGroup final : public BatchGroupBase {
           if (l < 1) return 0;
           auto& C = inst_[i]->com_[l];
           return C.cut_start[c + 1] - C.cut_start[c];
-        });
-        w_mem_[t][c] = fill([&](int i) {
-          const int l = lv[i];
-          if (l < 1) return 0;
-          const auto& h = d64_[t].host[i];
-          return h.mem_start[c + 1] - h.mem_start[c];
         });
         w_cf_[t][c] = fill([&](int i) {
           const int l = lv[i];
@@ -825,9 +802,6 @@ class BatchGroup final : public BatchGroupBase {
           count("batched cut patches");
         }
       }
-      const Work& wm = w_mem_[t][colour];
-      kb_cut_scatter<DIM, P, T><<<grid(wm.total, 256), 256, 0, s>>>(D, wm.off, K_, wm.total, colour);
-      count("batched cut scatter");
     }
   }
 

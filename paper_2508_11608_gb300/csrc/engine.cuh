@@ -108,9 +108,9 @@ class Engine final : public EngineBase {
     uint8_t* citems;
     uint16_t* members;
     std::vector<int> cut_start;
-    std::vector<int> cut_moff_h;
     std::vector<int> cut_maxm2;
     std::vector<int> cut_maxit;
+    std::vector<CutPlan> plan64, plan32;  // launch shape of the block cut kernel per colour
     int64_t nmembers;
     int* pro_col;
     int* res_col;
@@ -128,7 +128,6 @@ class Engine final : public EngineBase {
     T* coarse_inv;
     T *x, *b, *r;          // box vectors
     T *t1, *t2, *t3, *t4;  // transfer intermediates (restriction: t1,t2; prolongation: t3,t4)
-    T* dbuf;               // cut-patch corrections A_j^{-1} r_j
   };
 
  public:
@@ -159,6 +158,16 @@ class Engine final : public EngineBase {
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, kInvSlotBytesMax));
     CUTMG_CUDA(cudaFuncSetAttribute(k_cut_solve_cta<DIM, P, float, true>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, kInvSlotBytesMax));
+    {
+      int dev = 0;
+      CUTMG_CUDA(cudaGetDevice(&dev));
+      CUTMG_CUDA(cudaDeviceGetAttribute(&sms_, cudaDevAttrMultiProcessorCount, dev));
+    }
+    for (int l = 1; l < L; ++l)
+      for (int col = 0; col < (1 << DIM); ++col) {
+        com_[l].plan64.push_back(cut_plan<double>(com_[l], col));
+        com_[l].plan32.push_back(cut_plan<float>(com_[l], col));
+      }
     CUTMG_CUDA(cudaMallocHost(&host_sc_, 16 * sizeof(double)));
     CUTMG_CUDA(cudaStreamCreateWithFlags(&cap_, cudaStreamNonBlocking));
     const char* g = std::getenv("CUTMG_GRAPHS");
@@ -479,6 +488,38 @@ class Engine final : public EngineBase {
   static constexpr bool kWarpCut = (DIM == 2 ? (2 * P + 1) * (2 * P + 1) : (2 * P + 1) * (2 * P + 1) * (2 * P + 1)) <= 64;
   // inverses with m^2 <= cap elements go through shared memory; the slot
   // holds the 16-byte-rounded copy
+  // Launch shape of one cut colour step of the block kernel.  At most two
+  // patches per SM (latency-bound): staged rows and the largest inverse slot
+  // (48, 24, 12 KB) with which every patch of the colour is resident at once.
+  // Otherwise the unstaged kernel with a 12 KB slot, eight blocks per SM
+  // hiding each other's latency, over a grid of at most 16 blocks per SM.
+  template <typename T>
+  CutPlan cut_plan(const Common& c, int colour) const {
+    CutPlan pl;
+    const int cnt = c.cut_start[colour + 1] - c.cut_start[colour];
+    if (kWarpCut || cnt <= 0) return pl;
+    const int rows = (int)(((size_t)c.cut_maxit[colour] * NB * sizeof(T) + 15) / 16 * 16);
+    if (cnt <= 2 * sms_)
+      for (int slot : {kInvSlotBytesStage, kInvSlotBytesStage / 2, kInvSlotBytes}) {
+        const int cap = std::min(c.cut_maxm2[colour], (slot - 16) / (int)sizeof(T));
+        const int dyn = (int)inv_slot_bytes<T>(cap) + rows;
+        int nb = 0;
+        CUTMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cut_solve_cta<DIM, P, T, true>,
+                                                                 kCutThreads, dyn));
+        if (nb > 0 && cnt <= nb * sms_) {
+          pl.staged = true;
+          pl.cap = cap;
+          pl.row_off = (int)inv_slot_bytes<T>(cap);
+          pl.dyn = dyn;
+          pl.grid = cnt;
+          return pl;
+        }
+      }
+    pl.cap = std::min(c.cut_maxm2[colour], (kInvSlotBytes - 16) / (int)sizeof(T));
+    pl.row_off = pl.dyn = (int)inv_slot_bytes<T>(pl.cap);
+    pl.grid = std::min(cnt, sms_ * 16);
+    return pl;
+  }
   static CutPatchArgs cut_args(const Common& c) {
     return CutPatchArgs{c.cutv, c.cutn, c.cutmo, c.cutio, c.cutfo, c.cutcell, c.citoff, c.citems};
   }
@@ -493,6 +534,7 @@ class Engine final : public EngineBase {
   }
  private:
   static constexpr int kVecBlocks = 1024;
+  int sms_ = 152;
 
   const Hierarchy& H_;
   DevPool pool_;
@@ -614,7 +656,6 @@ class Engine final : public EngineBase {
     D.x = pool_.alloc<T>(c.nbox);
     D.b = pool_.alloc<T>(c.nbox);
     D.r = pool_.alloc<T>(c.nbox);
-    D.dbuf = pool_.alloc<T>(c.nmembers);
     D.t1 = D.t2 = D.t3 = D.t4 = nullptr;
     if (l > 0) {
       const int64_t nf = h.n, nc = H_.levels[l - 1].n;
@@ -665,7 +706,6 @@ class Engine final : public EngineBase {
     c.citems = pool_.upload<uint8_t>(h.cut_items);
     c.members = pool_.upload<uint16_t>(h.members);
     c.cut_start = h.cut_start;
-    c.cut_moff_h = h.cut_moff;
     c.cut_maxm2 = h.cut_maxm2;
     c.cut_maxit = h.cut_maxit;
     c.nmembers = (int64_t)h.members.size();
@@ -789,8 +829,11 @@ class Engine final : public EngineBase {
       const int a0 = c.cart_start[colour], cnt = c.cart_start[colour + 1] - a0;
       if (cnt <= 0) return;
       prof_mark(2, s);
-      k_smooth_cart<DIM, P, T, WARPS><<<blocks_for(cnt, WARPS), 32 * WARPS, 0, s>>>(
-          D.fd, c.N, c.n, x, b, c.cart + a0, cnt);
+      if (cnt <= 4 * sms_)
+        k_smooth_cart_cta<DIM, P, T><<<cnt, 128, 0, s>>>(D.fd, c.N, c.n, x, b, c.cart + a0, cnt);
+      else
+        k_smooth_cart<DIM, P, T, WARPS><<<blocks_for(cnt, WARPS), 32 * WARPS, 0, s>>>(
+            D.fd, c.N, c.n, x, b, c.cart + a0, cnt);
       count_launch("smooth interior patches");
       prof_mark(2, s);
       const auto& w = H_.levels[l].work_cart[colour];
@@ -803,30 +846,22 @@ class Engine final : public EngineBase {
       if (kWarpCut) {
         k_cut_solve<DIM, P, T, WARPS><<<blocks_for(cnt, WARPS), 32 * WARPS, 0, s>>>(
             D.op, x, b, c.cutv + a0, c.cutn + a0, c.cutmo + a0, c.cutio + a0, c.members, c.mnode, c.fofs,
-            c.fent, D.inv, D.dbuf, cnt);
+            c.fent, D.inv, cnt);
       } else {
-        const int cap = inv_cap_for<T>(c.cut_maxm2[colour], cnt);
-        const int slot = (int)inv_slot_bytes<T>(cap);
-        if (cnt <= kSmallGrid) {
-          const int rows = (int)(((size_t)c.cut_maxit[colour] * NB * sizeof(T) + 15) / 16 * 16);
-          k_cut_solve_cta<DIM, P, T, true><<<cnt, kCutThreads, slot + rows, s>>>(
-              D.op, x, b, cut_args(c), c.members, c.mnode, c.fofs, c.fent, D.inv, D.dbuf, a0, cnt, cap, slot,
-              err_);
-        } else {
-          const int grid = std::min(cnt, 152 * 16);
-          k_cut_solve_cta<DIM, P, T, false><<<grid, kCutThreads, slot, s>>>(
-              D.op, x, b, cut_args(c), c.members, c.mnode, c.fofs, c.fent, D.inv, D.dbuf, a0, cnt, cap, slot,
-              err_);
-        }
+        const CutPlan& pl = (sizeof(T) == 8 ? c.plan64 : c.plan32)[colour];
+        if (pl.staged)
+          k_cut_solve_cta<DIM, P, T, true><<<pl.grid, kCutThreads, pl.dyn, s>>>(
+              D.op, x, b, cut_args(c), c.members, c.mnode, c.fofs, c.fent, D.inv, a0, cnt, pl.cap,
+              pl.row_off, err_);
+        else
+          k_cut_solve_cta<DIM, P, T, false><<<pl.grid, kCutThreads, pl.dyn, s>>>(
+              D.op, x, b, cut_args(c), c.members, c.mnode, c.fofs, c.fent, D.inv, a0, cnt, pl.cap,
+              pl.row_off, err_);
       }
       count_launch("cut patch solve");
       prof_mark(1, s);
       const auto& w = H_.levels[l].work_cut[colour];
       prof_work(1, w[0], w[1] * sizeof(T) + w[2]);
-      const int m0 = c.cut_moff_h[a0];
-      const int m1 = (a0 + cnt < (int)c.cut_moff_h.size()) ? c.cut_moff_h[a0 + cnt] : (int)c.nmembers;
-      k_cut_scatter<T><<<blocks_for(m1 - m0, 256), 256, 0, s>>>(x, c.mnode, D.dbuf, m0, m1);
-      count_launch("cut patch scatter");
     }
   }
 

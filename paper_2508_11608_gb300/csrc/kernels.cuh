@@ -565,7 +565,8 @@ struct CartScratch {
   T t[G::NI];
 };
 
-template <int DIM, int P, typename T>
+// NT threads (a warp, or a block for latency-bound launches) per patch
+template <int DIM, int P, typename T, int NT = 32>
 __device__ __forceinline__ void cart_body(const FdArgs<T, P>& F, int N, int n, T* __restrict__ x,
                                           const T* __restrict__ b, int vert, int lane,
                                           CartScratch<DIM, P, T>& CS) {
@@ -589,18 +590,18 @@ __device__ __forceinline__ void cart_body(const FdArgs<T, P>& F, int N, int n, T
     }
   }
   T* X = CS.x;
-  for (int e = lane; e < NC; e += 32) {
+  for (int e = lane; e < NC; e += NT) {
     int o0 = e % C, r = e / C;
     int off = (DIM == 2) ? o0 + n * r : o0 + n * (r % C + n * (r / C));
     X[e] = x[base + off];
   }
-  __syncwarp();
+  psync<NT>();
   T* U1 = CS.u[0];
   T* U2 = CS.u[1];
   T* R = CS.r;
   if (DIM == 2) {
     // u1[yi][x] = sum_y Mr[yi][y] X[y][x]; u2 with Kr
-    for (int e = lane; e < M * C; e += 32) {
+    for (int e = lane; e < M * C; e += NT) {
       int xx = e % C, yi = e / C;
       T a1 = T(0), a2 = T(0);
 #pragma unroll
@@ -612,9 +613,9 @@ __device__ __forceinline__ void cart_body(const FdArgs<T, P>& F, int N, int n, T
       U1[e] = a1;
       U2[e] = a2;
     }
-    __syncwarp();
+    psync<NT>();
     // r = b - (Kx u1 + Mx u2)
-    for (int e = lane; e < NI; e += 32) {
+    for (int e = lane; e < NI; e += NT) {
       int xi = e % M, yi = e / M;
       T acc = T(0);
 #pragma unroll
@@ -627,7 +628,7 @@ __device__ __forceinline__ void cart_body(const FdArgs<T, P>& F, int N, int n, T
     T* V2 = CS.v[1];
     T* V3 = CS.v[2];
     // along z: u1 = Mz X, u2 = Kz X   (zi, y, x)
-    for (int e = lane; e < M * C * C; e += 32) {
+    for (int e = lane; e < M * C * C; e += NT) {
       int yx = e % (C * C), zi = e / (C * C);
       T a1 = T(0), a2 = T(0);
 #pragma unroll
@@ -639,9 +640,9 @@ __device__ __forceinline__ void cart_body(const FdArgs<T, P>& F, int N, int n, T
       U1[e] = a1;
       U2[e] = a2;
     }
-    __syncwarp();
+    psync<NT>();
     // along y: v1 = My u1, v2 = Ky u1, v3 = My u2   (zi, yi, x)
-    for (int e = lane; e < M * M * C; e += 32) {
+    for (int e = lane; e < M * M * C; e += NT) {
       int xx = e % C, r = e / C, yi = r % M, zi = r / M;
       T a1 = T(0), a2 = T(0), a3 = T(0);
 #pragma unroll
@@ -655,9 +656,9 @@ __device__ __forceinline__ void cart_body(const FdArgs<T, P>& F, int N, int n, T
       V2[e] = a2;
       V3[e] = a3;
     }
-    __syncwarp();
+    psync<NT>();
     // along x: r = b - (Kx v1 + Mx (v2 + v3))
-    for (int e = lane; e < NI; e += 32) {
+    for (int e = lane; e < NI; e += NT) {
       int xi = e % M, r = e / M, yi = r % M, zi = r / M;
       T acc = T(0);
 #pragma unroll
@@ -669,30 +670,30 @@ __device__ __forceinline__ void cart_body(const FdArgs<T, P>& F, int N, int n, T
       R[e] = b[node] - acc;
     }
   }
-  __syncwarp();
+  psync<NT>();
   // fast diagonalisation: t = (S^T)^{(x) DIM} r, scale, delta = S^{(x) DIM} t
   T* Tt = CS.t;
   // S^T along x
-  for (int e = lane; e < NI; e += 32) {
+  for (int e = lane; e < NI; e += NT) {
     int a = e % M, rest = e / M;
     T acc = T(0);
 #pragma unroll
     for (int i = 0; i < M; ++i) acc += F.S[i][a] * R[rest * M + i];
     Tt[e] = acc;
   }
-  __syncwarp();
+  psync<NT>();
   // S^T along y
-  for (int e = lane; e < NI; e += 32) {
+  for (int e = lane; e < NI; e += NT) {
     int xx = e % M, r = e / M, bb = r % M, zi = r / M;
     T acc = T(0);
 #pragma unroll
     for (int i = 0; i < M; ++i) acc += F.S[i][bb] * Tt[(zi * M + i) * M + xx];
     R[e] = acc;
   }
-  __syncwarp();
+  psync<NT>();
   if (DIM == 3) {
     // S^T along z, then scale
-    for (int e = lane; e < NI; e += 32) {
+    for (int e = lane; e < NI; e += NT) {
       int yx = e % (M * M), cz = e / (M * M);
       T acc = T(0);
 #pragma unroll
@@ -700,9 +701,9 @@ __device__ __forceinline__ void cart_body(const FdArgs<T, P>& F, int N, int n, T
       int a = e % M, bb = (e / M) % M;
       Tt[e] = acc / (F.lam[a] + F.lam[bb] + F.lam[cz]);
     }
-    __syncwarp();
+    psync<NT>();
     // S along z
-    for (int e = lane; e < NI; e += 32) {
+    for (int e = lane; e < NI; e += NT) {
       int yx = e % (M * M), zi = e / (M * M);
       T acc = T(0);
 #pragma unroll
@@ -710,23 +711,23 @@ __device__ __forceinline__ void cart_body(const FdArgs<T, P>& F, int N, int n, T
       R[e] = acc;
     }
   } else {
-    for (int e = lane; e < NI; e += 32) {
+    for (int e = lane; e < NI; e += NT) {
       int a = e % M, bb = e / M;
       R[e] = R[e] / (F.lam[a] + F.lam[bb]);
     }
   }
-  __syncwarp();
+  psync<NT>();
   // S along y
-  for (int e = lane; e < NI; e += 32) {
+  for (int e = lane; e < NI; e += NT) {
     int xx = e % M, r = e / M, yi = r % M, zi = r / M;
     T acc = T(0);
 #pragma unroll
     for (int c = 0; c < M; ++c) acc += F.S[yi][c] * R[(zi * M + c) * M + xx];
     Tt[e] = acc;
   }
-  __syncwarp();
+  psync<NT>();
   // S along x, update x
-  for (int e = lane; e < NI; e += 32) {
+  for (int e = lane; e < NI; e += NT) {
     int xi = e % M, rest = e / M;
     T acc = T(0);
 #pragma unroll
@@ -749,21 +750,38 @@ __global__ void __launch_bounds__(32 * WARPS) k_smooth_cart(FdArgs<T, P> F, int 
   cart_body<DIM, P, T>(F, N, n, x, b, verts[pidx], lane, sCS[w]);
 }
 
-// ---------------------------------------------------------------------------
-// Cut-patch colour step (Sec. 3: dense local solver on cut patches), phase 1:
-// one warp per patch; r_I = b_I - (A x)_I by patch_rows, delta = A_j^{-1} r_I
-// with the explicit inverse (symmetric, read by columns so that lanes load
-// consecutive entries), delta to dbuf.  x is not written here, so every patch
-// of the colour sees the same x: additive within a colour, which is the
-// paper's inconsistent treatment of ghost coupling between patches (Sec. 2.3).
+// One 128-thread block per interior patch: for launches with few patches per
+// SM, where one warp's chain of dependent FP64 steps sets the launch time.
 template <int DIM, int P, typename T>
-__device__ __forceinline__ void cut_body(const OpArgs<T>& A, const T* __restrict__ x,
+__global__ void __launch_bounds__(128) k_smooth_cart_cta(FdArgs<T, P> F, int N, int n, T* __restrict__ x,
+                                                          const T* __restrict__ b,
+                                                          const int* __restrict__ verts, int nv) {
+  __shared__ CartScratch<DIM, P, T> CS;
+  for (int pidx = blockIdx.x; pidx < nv; pidx += gridDim.x) {
+    cart_body<DIM, P, T, 128>(F, N, n, x, b, verts[pidx], threadIdx.x, CS);
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Cut-patch colour step (Sec. 3: dense local solver on cut patches), one warp
+// per patch: r_I = b_I - (A x)_I by patch_rows, delta = A_j^{-1} r_I with the
+// explicit inverse (symmetric, read by columns so that lanes load consecutive
+// entries), x_I += delta.
+//
+// Additive within a colour (the paper's inconsistent treatment of the ghost
+// coupling between patches, Sec. 2.3) without a second pass: the DoF sets of
+// one colour's patches are disjoint, a DoF of patch A has all its active
+// cells in A, so no cell row of another patch of the colour reads it, and the
+// ghost-face terms read moments computed before the colour step.  Every patch
+// therefore sees the x from before the colour step and writes its own DoFs.
+template <int DIM, int P, typename T>
+__device__ __forceinline__ void cut_body(const OpArgs<T>& A, T* __restrict__ x,
                                          const T* __restrict__ b, int vert, int m, int mo, int64_t io,
                                          const uint16_t* __restrict__ members,
                                          const int* __restrict__ mnode, const int* __restrict__ fofs,
                                          const int* __restrict__ fent, const T* __restrict__ inv,
-                                         T* __restrict__ dbuf, PatchScratch<DIM, P, T>& S,
-                                         const T* __restrict__ sK, int lane) {
+                                         PatchScratch<DIM, P, T>& S, const T* __restrict__ sK, int lane) {
   const int np = A.N + 1;
   int q = vert, v[3] = {0, 0, 0};
 #pragma unroll
@@ -789,12 +807,12 @@ __device__ __forceinline__ void cut_body(const OpArgs<T>& A, const T* __restrict
       for (int u = 0; u < 8; ++u) acc[u] += a[u] * S.r[j + u];
     }
     for (; j < m; ++j) acc[0] += __ldg(Ai + (size_t)j * m + e) * S.r[j];
-    dbuf[mo + e] = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+    x[mnode[mo + e]] += ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
   }
 }
 
 template <int DIM, int P, typename T, int WARPS>
-__global__ void __launch_bounds__(32 * WARPS) k_cut_solve(OpArgs<T> A, const T* __restrict__ x,
+__global__ void __launch_bounds__(32 * WARPS) k_cut_solve(OpArgs<T> A, T* __restrict__ x,
                                                           const T* __restrict__ b,
                                                           const int* __restrict__ verts,
                                                           const int* __restrict__ cnt,
@@ -804,8 +822,7 @@ __global__ void __launch_bounds__(32 * WARPS) k_cut_solve(OpArgs<T> A, const T* 
                                                           const int* __restrict__ mnode,
                                                           const int* __restrict__ fofs,
                                                           const int* __restrict__ fent,
-                                                          const T* __restrict__ inv,
-                                                          T* __restrict__ dbuf, int npatch) {
+                                                          const T* __restrict__ inv, int npatch) {
   constexpr int NB = Shape<DIM, P>::NB;
   __shared__ T sK[NB * NB];
   __shared__ PatchScratch<DIM, P, T> sS[WARPS];
@@ -814,7 +831,7 @@ __global__ void __launch_bounds__(32 * WARPS) k_cut_solve(OpArgs<T> A, const T* 
   const int pidx = blockIdx.x * WARPS + w;
   if (pidx >= npatch) return;
   cut_body<DIM, P, T>(A, x, b, verts[pidx], cnt[pidx], moff[pidx], ioff[pidx], members, mnode, fofs, fent,
-                      inv, dbuf, sS[w], sK, lane);
+                      inv, sS[w], sK, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -887,6 +904,12 @@ struct CutPatchArgs {
   const uint8_t* items;  // s * NB + i: rows (patch cell s, local node i) to form
 };
 
+// Launch shape of the block cut kernel for one colour step.
+struct CutPlan {
+  bool staged = false;
+  int cap = 0, row_off = 0, dyn = 0, grid = 0;
+};
+
 struct CutMeta {
   int vert, m, mo, f0, f1, i0, i1;
   int64_t io;
@@ -915,6 +938,7 @@ struct CutScratch {
   T r[G::NCL];
   const T* rowbase[G::NCELL];
   T fc[kFeCap];  // contribution of each ghost-face entry to its row
+  int mn[G::NCL];  // lattice index of each patch DoF
   uint8_t item[G::NCELL * G::NB];
 };
 
@@ -925,14 +949,14 @@ struct CutScratch {
 // per thread), and the solve splits each of the m rows over up to 4 lanes.
 // Uncut cells read the level's element matrix through L1.
 template <int DIM, int P, typename T, bool STAGE>
-__device__ __forceinline__ void cut_body_cta(const OpArgs<T>& A, const T* __restrict__ x,
+__device__ __forceinline__ void cut_body_cta(const OpArgs<T>& A, T* __restrict__ x,
                                              const T* __restrict__ b, const CutMeta& M, int j,
                                              const CutPatchArgs& C, const uint16_t* __restrict__ members,
                                              const int* __restrict__ mnode, const int* __restrict__ fofs,
                                              const int* __restrict__ fent, const T* __restrict__ inv,
-                                             T* __restrict__ dbuf, CutScratch<DIM, P, T>& S, T* sinv,
-                                             T* srow, int inv_cap, uint64_t* bar, uint32_t& phase,
-                                             const T* __restrict__ sK, int* err) {
+                                             CutScratch<DIM, P, T>& S, T* sinv, T* srow, int inv_cap,
+                                             uint64_t* bar, uint32_t& phase, const T* __restrict__ sK,
+                                             int* err) {
   using G = PatchGeo<DIM, P>;
   constexpr int CC = G::C, NB = G::NB, NCL = G::NCL, NCELL = G::NCELL, NTF = FaceGeo<DIM, P>::NT;
   static_assert(NCL <= kCutThreads, "one patch DoF per thread");
@@ -984,6 +1008,7 @@ __device__ __forceinline__ void cut_body_cta(const OpArgs<T>& A, const T* __rest
     fa = fofs[M.mo + tid] - M.f0;
     fb = fofs[M.mo + tid + 1] - M.f0;
     mn = mnode[M.mo + tid];
+    S.mn[tid] = mn;
   }
   __syncthreads();
   // latency-bound launches (few patches per SM): bring the element-matrix
@@ -1137,7 +1162,7 @@ __device__ __forceinline__ void cut_body_cta(const OpArgs<T>& A, const T* __rest
       T a = a0 + a1;
       if (K >= 4) a += __shfl_xor_sync(0xffffffffu, a, 2);
       if (K >= 2) a += __shfl_xor_sync(0xffffffffu, a, 1);
-      if (e < m && k == 0) dbuf[M.mo + e] = a;
+      if (e < m && k == 0) x[S.mn[e]] += a;
     }
   }
   __syncthreads();
@@ -1147,15 +1172,14 @@ __device__ __forceinline__ void cut_body_cta(const OpArgs<T>& A, const T* __rest
 // matrix rows in the dynamic shared memory after the inverse slot (at
 // row_off bytes); large grids read them through L1.
 template <int DIM, int P, typename T, bool STAGE>
-__global__ void __launch_bounds__(kCutThreads) k_cut_solve_cta(OpArgs<T> A, const T* __restrict__ x,
+__global__ void __launch_bounds__(kCutThreads) k_cut_solve_cta(OpArgs<T> A, T* __restrict__ x,
                                                                const T* __restrict__ b, CutPatchArgs C,
                                                                const uint16_t* __restrict__ members,
                                                                const int* __restrict__ mnode,
                                                                const int* __restrict__ fofs,
                                                                const int* __restrict__ fent,
-                                                               const T* __restrict__ inv, T* __restrict__ dbuf,
-                                                               int j0, int npatch, int inv_cap, int row_off,
-                                                               int* err) {
+                                                               const T* __restrict__ inv, int j0, int npatch,
+                                                               int inv_cap, int row_off, int* err) {
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ __align__(8) uint64_t bar;
   __shared__ CutScratch<DIM, P, T> S;
@@ -1170,18 +1194,10 @@ __global__ void __launch_bounds__(kCutThreads) k_cut_solve_cta(OpArgs<T> A, cons
   for (; j < npatch; j += gridDim.x) {
     CutMeta nxt = cur;
     if (j + (int)gridDim.x < npatch) nxt = cut_meta(C, j0 + j + gridDim.x);
-    cut_body_cta<DIM, P, T, STAGE>(A, x, b, cur, j0 + j, C, members, mnode, fofs, fent, inv, dbuf, S, sinv,
-                                   srow, inv_cap, &bar, phase, A.Kref, err);
+    cut_body_cta<DIM, P, T, STAGE>(A, x, b, cur, j0 + j, C, members, mnode, fofs, fent, inv, S, sinv, srow,
+                                   inv_cap, &bar, phase, A.Kref, err);
     cur = nxt;
   }
-}
-
-// Phase 2: x[I_j] += delta for every DoF of the colour's patches.
-template <typename T>
-__global__ void __launch_bounds__(256) k_cut_scatter(T* __restrict__ x, const int* __restrict__ mnode,
-                                                     const T* __restrict__ dbuf, int m0, int m1) {
-  const int i = m0 + blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < m1) x[mnode[i]] += dbuf[i];
 }
 
 // ---------------------------------------------------------------------------
