@@ -267,6 +267,11 @@ cf_status cf_profile_read(cf_problem* pb, double* ms, int64_t* launches, double*
  * every device call on it returns CF_EINVAL. */
 cf_status cf_setup_host(const cf_mesh* mesh, const cf_levelset* ls, int degree,
                         const cf_params* params, cf_problem** out);
+/* Device memory a device handle of this problem holds (hierarchy in both
+ * precisions, CG vectors, graph scratch), estimated from the host setup: the
+ * figure the served form admits requests by (Sec. 5's resident
+ * hierarchies).  Works on host-only and device handles; CF_EINVAL on null. */
+cf_status cf_footprint(const cf_problem* pb, size_t* bytes);
 /* Finest-level right-hand side (host array of cf_n_dofs doubles). */
 cf_status cf_host_rhs(const cf_problem* pb, double* h_b);
 /* Element matrix of cell `cell` (flat index c_0 + N c_1 + N^2 c_2) of a level:

@@ -93,6 +93,12 @@ class Problem:
         keys = ["active_cells", "cut_cells", "ghost_faces", "patches", "cut_patches", "inverse_entries"]
         return dict(zip(keys, out.tolist()))
 
+    def footprint(self):
+        """Estimated device bytes of this problem's device handle."""
+        out = ctypes.c_size_t()
+        check(self._lib.cf_footprint(self._h, ctypes.byref(out)))
+        return out.value
+
     def work_model(self, level, kind, colour):
         """Algorithmic work of one colour step: kind 0 interior, 1 cut patches.
         Returns (flops, scalars moved, index bytes moved)."""

@@ -17,7 +17,7 @@ CF_K_CUT_SOLVE, CF_K_INTERIOR, CF_K_APPLY_BULK, CF_K_APPLY_BND, CF_K_FACE_MOMENT
 
 EXPORTED = [
     "cf_setup", "cf_destroy", "cf_last_error", "cf_n_levels", "cf_n_dofs", "cf_level_n_dofs",
-    "cf_dof_lattice", "cf_dof_coords", "cf_stats", "cf_work_model", "cf_set_precision", "cf_rhs", "cf_apply",
+    "cf_dof_lattice", "cf_dof_coords", "cf_stats", "cf_work_model", "cf_footprint", "cf_set_precision", "cf_rhs", "cf_apply",
     "cf_vcycle", "cf_solve", "cf_level_apply", "cf_level_colour_step", "cf_level_smooth",
     "cf_level_restrict", "cf_level_prolongate", "cf_coarse_solve", "cf_setup_host", "cf_host_rhs",
     "cf_host_cell_matrix", "cf_host_patch_counts", "cf_host_interior_patch", "cf_host_cut_patch",
@@ -82,6 +82,7 @@ def load():
     lib.cf_dof_coords.argtypes = [P, I, P]
     lib.cf_stats.argtypes = [P, I, P]
     lib.cf_work_model.argtypes = [P, I, I, I, P]
+    lib.cf_footprint.argtypes = [P, P]
     lib.cf_set_precision.argtypes = [P, I]
     lib.cf_rhs.argtypes = [P, P, V]
     lib.cf_apply.argtypes = [P, P, P, V]

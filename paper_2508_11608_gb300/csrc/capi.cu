@@ -206,6 +206,12 @@ cf_status cf_setup_host(const cf_mesh* mesh, const cf_levelset* ls, int degree, 
 
 void cf_destroy(cf_problem* pb) { delete pb; }
 
+cf_status cf_footprint(const cf_problem* pb, size_t* bytes) {
+  if (!pb || !bytes) return fail(CF_EINVAL, "null argument");
+  *bytes = cutmg_estimate_device_bytes(pb);
+  return CF_OK;
+}
+
 int cf_n_levels(const cf_problem* pb) { return pb ? (int)pb->H.levels.size() : 0; }
 
 int64_t cf_n_dofs(const cf_problem* pb) { return pb ? (int64_t)pb->H.levels.back().dofs.size() : 0; }

@@ -1143,26 +1143,21 @@ __device__ __forceinline__ void cut_body_cta(const OpArgs<T>& A, T* __restrict__
   // block-uniform outcome (the solve below shuffles across full warps)
   ok = __syncthreads_and(ok) != 0;
   if (ok) {
-    // delta = A_j^{-1} r: row e split over K lanes (columns k, k + K, ..),
-    // the K partial sums combined by shuffles in a fixed order
+    // delta = A_j^{-1} r, one lane per row e reading column e of the
+    // (exactly symmetric) inverse so that neighbouring lanes read neighbouring
+    // addresses.  The order of the sums depends on m only: a patch gets the
+    // same bits in every launch shape (solo, batched, served).
     const T* Ai = tma ? sinv : inv + M.io;
-    const int K = m <= 32 ? 4 : (m <= 64 ? 2 : 1);
-    for (int e0 = 0; e0 < m; e0 += kCutThreads / K) {
-      const int e = e0 + tid / K, k = tid - (tid / K) * K;
+    for (int e = tid; e < m; e += kCutThreads) {
+      const T* Ac = Ai + e;
       T a0 = T(0), a1 = T(0);
-      if (e < m) {
-        const T* Ar = Ai + (size_t)e * m;
-        int c = k;
-        for (; c + K < m; c += 2 * K) {
-          a0 += Ar[c] * S.r[c];
-          a1 += Ar[c + K] * S.r[c + K];
-        }
-        if (c < m) a0 += Ar[c] * S.r[c];
+      int c = 0;
+      for (; c + 1 < m; c += 2) {
+        a0 += Ac[(size_t)c * m] * S.r[c];
+        a1 += Ac[(size_t)(c + 1) * m] * S.r[c + 1];
       }
-      T a = a0 + a1;
-      if (K >= 4) a += __shfl_xor_sync(0xffffffffu, a, 2);
-      if (K >= 2) a += __shfl_xor_sync(0xffffffffu, a, 1);
-      if (e < m && k == 0) x[S.mn[e]] += a;
+      if (c < m) a0 += Ac[(size_t)c * m] * S.r[c];
+      x[S.mn[e]] += a0 + a1;
     }
   }
   __syncthreads();

@@ -83,3 +83,19 @@ def test_request_larger_than_budget_fails_cleanly():
     with pytest.raises(cm.CutmgError) as e:
         srv.result(rid)
     assert "budget" in str(e.value)
+
+
+def test_footprint_estimate_covers_the_device_allocation():
+    k = dict(dim=3, n_cells=32, n_levels=4, degree=2, center=[0.05, 0.03, 0.02], radius=0.7)
+    est = cm.Problem(**k, host_only=True).footprint()
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    pb = cm.Problem(**k)
+    b = torch.zeros(pb.n_dofs(), dtype=torch.float64, device=DEV)
+    x = torch.zeros_like(b)
+    pb.rhs(b)
+    pb.solve(b, x, rtol=1e-8)  # graphs and CG scratch allocated
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    used = free0 - free1 - 2 * b.numel() * 8
+    assert 0.5 * est <= used <= 1.25 * est + (64 << 20)

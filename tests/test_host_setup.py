@@ -107,3 +107,13 @@ def test_invalid_arguments_are_rejected():
         cm.Problem(2, 12, 4, 2, center=[0, 0], radius=0.5, host_only=True)  # 12 not divisible by 8
     with pytest.raises(cm.CutmgError):
         cm.Problem(2, 16, 2, 2, center=[0, 0], radius=-1.0, host_only=True)
+
+
+def test_footprint_estimate_grows_with_the_mesh():
+    small = cm.Problem(3, 16, 3, 2, center=[0.05, 0.03, 0.02], radius=0.7, host_only=True)
+    large = cm.Problem(3, 32, 4, 2, center=[0.05, 0.03, 0.02], radius=0.7, host_only=True)
+    fs, fl = small.footprint(), large.footprint()
+    # at least the FP64 + FP32 cut-patch inverses and the box vectors
+    inv = small.stats()["inverse_entries"]
+    assert fs >= 12 * inv
+    assert fl > 4 * fs
