@@ -283,6 +283,12 @@ cf_status cf_host_cell_matrix(const cf_problem* pb, int level, int64_t cell, dou
 cf_status cf_host_patch_counts(const cf_problem* pb, int level, int64_t* n_interior, int64_t* n_cut);
 /* Interior patch j: its vertex (lattice vertex index v_0 + (N+1) v_1 + ..). */
 cf_status cf_host_interior_patch(const cf_problem* pb, int level, int64_t j, int64_t* vertex);
+/* The exact local solve of an interior patch of a level (Sec. 2.3, every
+ * interior patch has the same local matrices) as one dense map:
+ * x_I <- A_I^{-1} b_I - A_I^{-1} A_{I,B} x_B.  h_W: (2p-1)^d x (2p+1)^d
+ * row-major; rows = interior nodes, columns = closure nodes, both first
+ * coordinate fastest; b enters at interior columns, x at boundary columns. */
+cf_status cf_host_interior_update(const cf_problem* pb, int level, double* h_W);
 /* Cut patch j: vertex, DoF count m, lattice indices of its m DoFs (h_nodes,
  * room for (2p+1)^d) and, if h_inv is not NULL, the m x m explicit inverse
  * of A[I_j, I_j] (row-major, in the order of h_nodes). */

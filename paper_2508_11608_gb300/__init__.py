@@ -184,6 +184,13 @@ class Problem:
         check(self._lib.cf_host_cell_matrix(self._h, level, cell, out.ctypes.data_as(ctypes.c_void_p)))
         return out
 
+    def host_interior_update(self, level):
+        """The level's dense interior-patch map W ((2p-1)^d x (2p+1)^d)."""
+        ni, nc = (2 * self.degree - 1) ** self.dim, (2 * self.degree + 1) ** self.dim
+        out = np.empty((ni, nc), dtype=np.float64)
+        check(self._lib.cf_host_interior_update(self._h, level, out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
     def host_patches(self, level, with_inverse=True):
         """(interior vertices, [(vertex, lattice nodes, inverse or None)] of cut patches)."""
         ni = ctypes.c_int64()

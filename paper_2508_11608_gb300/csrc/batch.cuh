@@ -39,6 +39,7 @@ struct LvlDesc {
   const int* cutmo;
   const int64_t* cutio;
   CutPatchArgs cp;
+  const float* dense_d;  // FP32 interior-patch map of the level
   const uint16_t* members;
   const int* mnode;
   const int* fofs;
@@ -103,6 +104,36 @@ __global__ void __launch_bounds__(32 * WARPS) kb_cart(const LvlDesc<DIM, P, T>* 
   }
 }
 
+// FP32 interior-patch step of the batched form: the dense map of
+// k_smooth_dense with each instance's transposed W read from its level
+// descriptor (the same products in the same order, so batched and solo
+// agree bitwise)
+template <int DIM, int P>
+__global__ void __launch_bounds__(256) kb_cart_dense(const LvlDesc<DIM, P, float>* __restrict__ D,
+                                                     const int* __restrict__ off, int K, int total, int colour) {
+  using G = DenseGeo<DIM, P>;
+  constexpr int C = G::C, NI = G::NI, NR4 = G::NR4;
+  for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < total; it += gridDim.x * blockDim.x) {
+    const int i = find_inst(off, K, it);
+    const LvlDesc<DIM, P, float>& L = D[i];
+    const int base = dense_base<DIM, P>(L.cart[L.cart_start[colour] + it - off[i]], L.N, L.n);
+    float acc[NI];
+#pragma unroll
+    for (int r = 0; r < NI; ++r) acc[r] = 0.f;
+    for (int row = 0; row < G::ROWS; ++row) {
+      bool inner;
+      const int ro = dense_row<DIM, P>(row, L.n, inner);
+#pragma unroll
+      for (int cx = 0; cx < C; ++cx) {
+        const float* src = (inner && cx >= 1 && cx <= C - 2) ? L.b : L.x;
+        dense_fma<NI, NR4>(L.dense_d + (row * C + cx) * NR4, src[base + ro + cx], acc);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < NI; ++r) L.x[base + dense_interior_offset<DIM, P>(r, L.n)] = acc[r];
+  }
+}
+
 template <int DIM, int P, typename T>
 __global__ void __launch_bounds__(128) kb_face_moments(const LvlDesc<DIM, P, T>* __restrict__ D,
                                                        const T* const* __restrict__ X,
@@ -159,7 +190,7 @@ __global__ void __launch_bounds__(kCutThreads) kb_cut_solve_cta(const LvlDesc<DI
     const CutMeta M = cut_meta(L.cp, j);
     // uncut cells read the level's element matrix from global memory
     // (instances differ in h)
-    cut_body_cta<DIM, P, T, false>(L.op, L.x, L.b, M, j, L.cp, L.members, L.mnode, L.fofs, L.fent, L.inv, S,
+    cut_body_cta<DIM, P, T, false, kCutThreads>(L.op, L.x, L.b, M, j, L.cp, L.members, L.mnode, L.fofs, L.fent, L.inv, S,
                                    sinv, nullptr, inv_cap, &bar, phase, L.op.Kref, err);
   }
 }
@@ -608,6 +639,7 @@ class BatchGroup final : public BatchGroupBase {
         L.cutmo = C.cutmo;
         L.cutio = C.cutio;
         L.cp = E::cut_args(C);
+        L.dense_d = e->template typed<float>()[l].dense_d;
         L.members = C.members;
         L.mnode = C.mnode;
         L.fofs = C.fofs;
@@ -808,9 +840,17 @@ class BatchGroup final : public BatchGroupBase {
   template <typename T>
   void launch_cart(const LvlDesc<DIM, P, T>* D, const Work& w, int colour, cudaStream_t s) {
     const int gridw = std::max(1, std::min((w.total + tile_w_ - 1) / tile_w_, sms_ * tile_b_));
-    if (tile_w_ == 2) kb_cart<DIM, P, T, 2><<<gridw, 64, 0, s>>>(D, w.off, K_, w.total, colour);
-    else if (tile_w_ == 8) kb_cart<DIM, P, T, 8><<<gridw, 256, 0, s>>>(D, w.off, K_, w.total, colour);
-    else kb_cart<DIM, P, T, 4><<<gridw, 128, 0, s>>>(D, w.off, K_, w.total, colour);
+    if constexpr (std::is_same<T, float>::value) {
+      const int bs = 32 * tile_w_;
+      const int gridd = std::max(1, std::min((w.total + bs - 1) / bs, sms_ * tile_b_));
+      kb_cart_dense<DIM, P><<<gridd, bs, 0, s>>>(D, w.off, K_, w.total, colour);
+    } else if (tile_w_ == 2) {
+      kb_cart<DIM, P, T, 2><<<gridw, 64, 0, s>>>(D, w.off, K_, w.total, colour);
+    } else if (tile_w_ == 8) {
+      kb_cart<DIM, P, T, 8><<<gridw, 256, 0, s>>>(D, w.off, K_, w.total, colour);
+    } else {
+      kb_cart<DIM, P, T, 4><<<gridw, 128, 0, s>>>(D, w.off, K_, w.total, colour);
+    }
     count("batched interior patches");
   }
   template <typename T>

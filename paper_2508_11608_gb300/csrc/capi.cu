@@ -504,6 +504,13 @@ cf_status cf_host_patch_counts(const cf_problem* pb, int level, int64_t* n_inter
   return CF_OK;
 }
 
+cf_status cf_host_interior_update(const cf_problem* pb, int level, double* h_W) {
+  if (bad_level(pb, level) || !h_W || level < 1) return fail(CF_EINVAL, "bad level or null output");
+  const auto& W = pb->H.levels[level].Wcart;
+  std::copy(W.begin(), W.end(), h_W);
+  return CF_OK;
+}
+
 cf_status cf_host_interior_patch(const cf_problem* pb, int level, int64_t j, int64_t* vertex) {
   if (bad_level(pb, level) || !vertex) return fail(CF_EINVAL, "bad argument");
   const HostLevel& L = pb->H.levels[level];

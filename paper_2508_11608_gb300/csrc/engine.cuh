@@ -126,6 +126,7 @@ class Engine final : public EngineBase {
     T* pro_w;
     T* res_w;
     T* coarse_inv;
+    float* dense_d;  // FP32 interior-patch map, transposed, rows padded to 4 (Wt[kc][r])
     T *x, *b, *r;          // box vectors
     T *t1, *t2, *t3, *t4;  // transfer intermediates (restriction: t1,t2; prolongation: t3,t4)
   };
@@ -150,13 +151,13 @@ class Engine final : public EngineBase {
     part_ = pool_.alloc<double>(kDotBlocks);
     sc_ = pool_.alloc<double>(16);
     err_ = pool_.alloc<int>(1);
-    CUTMG_CUDA(cudaFuncSetAttribute(k_cut_solve_cta<DIM, P, double, false>,
+    CUTMG_CUDA(cudaFuncSetAttribute(k_cut_solve_cta<DIM, P, double, false, kCutNT<double>>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, kInvSlotBytesMax));
-    CUTMG_CUDA(cudaFuncSetAttribute(k_cut_solve_cta<DIM, P, float, false>,
+    CUTMG_CUDA(cudaFuncSetAttribute(k_cut_solve_cta<DIM, P, float, false, kCutNT<float>>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, kInvSlotBytesMax));
-    CUTMG_CUDA(cudaFuncSetAttribute(k_cut_solve_cta<DIM, P, double, true>,
+    CUTMG_CUDA(cudaFuncSetAttribute(k_cut_solve_cta<DIM, P, double, true, kCutThreads>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, kInvSlotBytesMax));
-    CUTMG_CUDA(cudaFuncSetAttribute(k_cut_solve_cta<DIM, P, float, true>,
+    CUTMG_CUDA(cudaFuncSetAttribute(k_cut_solve_cta<DIM, P, float, true, kCutThreads>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, kInvSlotBytesMax));
     {
       int dev = 0;
@@ -481,6 +482,13 @@ class Engine final : public EngineBase {
   static constexpr int kInvSlotBytesStage = 48 * 1024;
   static constexpr int kInvSlotBytesMax = 96 * 1024;  // attribute bound of every variant
   static constexpr int kSmallGrid = 2 * 152;
+  // interior colours with at least this many patches take two per thread in
+  // the FP32 dense step (enough blocks to fill every SM either way)
+  static constexpr int kDensePairPatches = 150000;
+  // threads per patch of the unstaged cut kernel (64 was measured slower
+  // than 128 for FP32 at 224^3: 233 against 191 us per finest colour step)
+  template <typename T>
+  static constexpr int kCutNT = kCutThreads;
   // when no patch can exceed 64 DoFs, (2p+1)^d <= 64 (2D Q1-Q3, 3D Q1), one
   // warp solves a patch, one or two rows per lane; otherwise (3D Q2) each
   // patch takes a block.  The choice depends on (d, p) only, so a problem
@@ -504,7 +512,7 @@ class Engine final : public EngineBase {
         const int cap = std::min(c.cut_maxm2[colour], (slot - 16) / (int)sizeof(T));
         const int dyn = (int)inv_slot_bytes<T>(cap) + rows;
         int nb = 0;
-        CUTMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cut_solve_cta<DIM, P, T, true>,
+        CUTMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cut_solve_cta<DIM, P, T, true, kCutThreads>,
                                                                  kCutThreads, dyn));
         if (nb > 0 && cnt <= nb * sms_) {
           pl.staged = true;
@@ -648,6 +656,14 @@ class Engine final : public EngineBase {
       }
       for (int j = 0; j < M; ++j) D.fd.S[i][j] = (T)h.S[i * M + j];
       D.fd.lam[i] = (T)h.lam[i];
+    }
+    {
+      using G = DenseGeo<DIM, P>;
+      std::vector<float> wt((size_t)G::NC * G::NR4, 0.f);
+      if (l > 0)
+        for (int i = 0; i < G::NI; ++i)
+          for (int k = 0; k < G::NC; ++k) wt[(size_t)k * G::NR4 + i] = (float)h.Wcart[(size_t)i * G::NC + k];
+      D.dense_d = pool_.upload<float>(wt);
     }
     D.inv = pool_.upload<T>(h.inv);
     D.pro_w = l > 0 ? pool_.upload<T>(h.pro_w) : nullptr;
@@ -829,7 +845,14 @@ class Engine final : public EngineBase {
       const int a0 = c.cart_start[colour], cnt = c.cart_start[colour + 1] - a0;
       if (cnt <= 0) return;
       prof_mark(2, s);
-      if (cnt <= 4 * sms_)
+      if constexpr (std::is_same<T, float>::value)
+      {
+        if (cnt >= kDensePairPatches)
+          k_smooth_dense<DIM, P, 2><<<blocks_for(cnt, 256), 128, 0, s>>>(D.dense_d, c.N, c.n, x, b, c.cart + a0, cnt);
+        else
+          k_smooth_dense<DIM, P, 1><<<blocks_for(cnt, 128), 128, 0, s>>>(D.dense_d, c.N, c.n, x, b, c.cart + a0, cnt);
+      }
+      else if (cnt <= 4 * sms_)
         k_smooth_cart_cta<DIM, P, T><<<cnt, 128, 0, s>>>(D.fd, c.N, c.n, x, b, c.cart + a0, cnt);
       else
         k_smooth_cart<DIM, P, T, WARPS><<<blocks_for(cnt, WARPS), 32 * WARPS, 0, s>>>(
@@ -850,11 +873,11 @@ class Engine final : public EngineBase {
       } else {
         const CutPlan& pl = (sizeof(T) == 8 ? c.plan64 : c.plan32)[colour];
         if (pl.staged)
-          k_cut_solve_cta<DIM, P, T, true><<<pl.grid, kCutThreads, pl.dyn, s>>>(
+          k_cut_solve_cta<DIM, P, T, true, kCutThreads><<<pl.grid, kCutThreads, pl.dyn, s>>>(
               D.op, x, b, cut_args(c), c.members, c.mnode, c.fofs, c.fent, D.inv, a0, cnt, pl.cap,
               pl.row_off, err_);
         else
-          k_cut_solve_cta<DIM, P, T, false><<<pl.grid, kCutThreads, pl.dyn, s>>>(
+          k_cut_solve_cta<DIM, P, T, false, kCutNT<T>><<<pl.grid, kCutNT<T>, pl.dyn, s>>>(
               D.op, x, b, cut_args(c), c.members, c.mnode, c.fofs, c.fent, D.inv, a0, cnt, pl.cap,
               pl.row_off, err_);
       }

@@ -750,6 +750,115 @@ __global__ void __launch_bounds__(32 * WARPS) k_smooth_cart(FdArgs<T, P> F, int 
   cart_body<DIM, P, T>(F, N, n, x, b, verts[pidx], lane, sCS[w]);
 }
 
+// FP32 interior-patch step as one dense map per level (the mixed form):
+// every interior patch of a level has the same local matrices, so its exact
+// local solve is x_I <- W [b_I ; x_B] with the fixed (2p-1)^d x (2p+1)^d
+// matrix W = [A_I^{-1} | -A_I^{-1} A_{I,B}] over the closure (interior
+// columns read b, boundary columns read x): a dense contraction of W with
+// the gathered closures of all patches of a colour.  W is stored transposed
+// with rows padded to a multiple of 4 (Wt[kc][r]).  Patches of one colour
+// write interior nodes that no other patch of the colour reads.
+template <int DIM, int P>
+struct DenseGeo {
+  static constexpr int C = 2 * P + 1, M = 2 * P - 1;
+  static constexpr int NI = (DIM == 2) ? M * M : M * M * M;
+  static constexpr int NC = (DIM == 2) ? C * C : C * C * C;
+  static constexpr int NR4 = (NI + 3) / 4 * 4;
+  static constexpr int ROWS = NC / C;  // closure lines along x
+};
+
+template <int DIM, int P>
+__device__ __forceinline__ int dense_base(int vert, int N, int n) {
+  int base = 0, s = 1, q = vert;
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) {
+    base += P * (q % (N + 1) - 1) * s;
+    q /= N + 1;
+    s *= n;
+  }
+  return base;
+}
+
+template <int DIM, int P>
+__device__ __forceinline__ int dense_interior_offset(int r, int n) {
+  constexpr int M = 2 * P - 1;
+  const int ix = r % M + 1, iy = (r / M) % M + 1, iz = (DIM == 3) ? r / (M * M) + 1 : 0;
+  return (DIM == 2) ? ix + n * iy : ix + n * (iy + n * iz);
+}
+
+// closure line `row` (the (cy, cz) pair): its lattice offset and whether
+// its nodes with 1 <= cx <= C-2 are interior
+template <int DIM, int P>
+__device__ __forceinline__ int dense_row(int row, int n, bool& inner) {
+  constexpr int C = 2 * P + 1;
+  const int cy = row % C, cz = (DIM == 3) ? row / C : 0;
+  inner = cy >= 1 && cy <= C - 2 && (DIM == 2 || (cz >= 1 && cz <= C - 2));
+  return (DIM == 2) ? n * cy : n * (cy + n * cz);
+}
+
+// acc[r] += W[r][kc] g, rows in order, 4 rows of Wt per (broadcast) load
+template <int NI, int NR4>
+__device__ __forceinline__ void dense_fma(const float* __restrict__ wt, float g, float* acc) {
+#pragma unroll
+  for (int r4 = 0; r4 < NR4; r4 += 4) {
+    const float4 w = *reinterpret_cast<const float4*>(wt + r4);
+    if (r4 + 0 < NI) acc[r4 + 0] = fmaf(w.x, g, acc[r4 + 0]);
+    if (r4 + 1 < NI) acc[r4 + 1] = fmaf(w.y, g, acc[r4 + 1]);
+    if (r4 + 2 < NI) acc[r4 + 2] = fmaf(w.z, g, acc[r4 + 2]);
+    if (r4 + 3 < NI) acc[r4 + 3] = fmaf(w.w, g, acc[r4 + 3]);
+  }
+}
+
+// 128 threads and 128 * PPT patches per block: thread t takes patches t,
+// t + 128, ..; Wt staged in shared memory once per block.  PPT = 2 reuses each
+// W load for two patches (colours with enough patches to fill the GPU),
+// PPT = 1 puts twice the threads on smaller colours.
+template <int DIM, int P, int PPT>
+__global__ void __launch_bounds__(128, PPT == 2 ? 6 : 8) k_smooth_dense(const float* __restrict__ Wt, int N,
+                                                                        int n, float* __restrict__ x,
+                                                                        const float* __restrict__ b,
+                                                                        const int* __restrict__ verts, int nv) {
+  using G = DenseGeo<DIM, P>;
+  constexpr int C = G::C, NI = G::NI, NR4 = G::NR4;
+  __shared__ __align__(16) float Ws[G::NC * NR4];
+  for (int i = threadIdx.x; i < G::NC * NR4; i += blockDim.x) Ws[i] = Wt[i];
+  __syncthreads();
+  const int p0 = blockIdx.x * (128 * PPT) + threadIdx.x;
+  if (p0 >= nv) return;
+  int base[PPT];
+  bool has[PPT];
+#pragma unroll
+  for (int q = 0; q < PPT; ++q) {
+    has[q] = p0 + 128 * q < nv;
+    base[q] = has[q] ? dense_base<DIM, P>(verts[p0 + 128 * q], N, n) : base[0];
+  }
+  float acc[PPT][NI];
+#pragma unroll
+  for (int q = 0; q < PPT; ++q)
+#pragma unroll
+    for (int r = 0; r < NI; ++r) acc[q][r] = 0.f;
+  for (int row = 0; row < G::ROWS; ++row) {
+    bool inner;
+    const int ro = dense_row<DIM, P>(row, n, inner);
+#pragma unroll
+    for (int cx = 0; cx < C; ++cx) {
+      const float* src = (inner && cx >= 1 && cx <= C - 2) ? b : x;
+      float g[PPT];
+#pragma unroll
+      for (int q = 0; q < PPT; ++q) g[q] = src[base[q] + ro + cx];
+      const float* wt = Ws + (row * C + cx) * NR4;
+#pragma unroll
+      for (int q = 0; q < PPT; ++q) dense_fma<NI, NR4>(wt, g[q], acc[q]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < PPT; ++q) {
+    if (!has[q]) continue;
+#pragma unroll
+    for (int r = 0; r < NI; ++r) x[base[q] + dense_interior_offset<DIM, P>(r, n)] = acc[q][r];
+  }
+}
+
 // One 128-thread block per interior patch: for launches with few patches per
 // SM, where one warp's chain of dependent FP64 steps sets the launch time.
 template <int DIM, int P, typename T>
@@ -938,7 +1047,6 @@ struct CutScratch {
   T r[G::NCL];
   const T* rowbase[G::NCELL];
   T fc[kFeCap];  // contribution of each ghost-face entry to its row
-  int mn[G::NCL];  // lattice index of each patch DoF
   uint8_t item[G::NCELL * G::NB];
 };
 
@@ -948,7 +1056,7 @@ struct CutScratch {
 // round reads the element-matrix rows and the ghost-face moments (one entry
 // per thread), and the solve splits each of the m rows over up to 4 lanes.
 // Uncut cells read the level's element matrix through L1.
-template <int DIM, int P, typename T, bool STAGE>
+template <int DIM, int P, typename T, bool STAGE, int NT>
 __device__ __forceinline__ void cut_body_cta(const OpArgs<T>& A, T* __restrict__ x,
                                              const T* __restrict__ b, const CutMeta& M, int j,
                                              const CutPatchArgs& C, const uint16_t* __restrict__ members,
@@ -959,7 +1067,7 @@ __device__ __forceinline__ void cut_body_cta(const OpArgs<T>& A, T* __restrict__
                                              int* err) {
   using G = PatchGeo<DIM, P>;
   constexpr int CC = G::C, NB = G::NB, NCL = G::NCL, NCELL = G::NCELL, NTF = FaceGeo<DIM, P>::NT;
-  static_assert(NCL <= kCutThreads, "one patch DoF per thread");
+  constexpr int TPT = (NCL + NT - 1) / NT;  // patch DoFs per thread
   const int tid = threadIdx.x, m = M.m, n = A.n;
   const bool tma = m * m <= inv_cap;
   if (tma && tid == 0) {
@@ -977,8 +1085,8 @@ __device__ __forceinline__ void cut_body_cta(const OpArgs<T>& A, T* __restrict__
     }
   }
   // round 1: everything that depends on the metadata only
-  if (tid < NCL) {
-    int u = tid, c[3] = {0, 0, 0};
+  for (int e = tid; e < NCL; e += NT) {
+    int u = e, c[3] = {0, 0, 0};
     bool in = true;
 #pragma unroll
     for (int k = 0; k < DIM; ++k) {
@@ -986,43 +1094,48 @@ __device__ __forceinline__ void cut_body_cta(const OpArgs<T>& A, T* __restrict__
       u /= CC;
       if (c[k] < 0 || c[k] >= n) in = false;
     }
-    S.x[tid] = in ? x[lat_index<DIM>(c, n)] : T(0);
+    S.x[e] = in ? x[lat_index<DIM>(c, n)] : T(0);
   }
   if (tid < NCELL) {
     const int id = C.cell[(size_t)j * NCELL + tid];
     S.rowbase[tid] = id == -2 ? nullptr : (id == -1 ? sK : A.cutmat + (size_t)id * NB * NB);
   }
   const int nfe = M.f1 - M.f0, nit = M.i1 - M.i0;
-  constexpr int EPT = kFeCap / kCutThreads;
+  constexpr int EPT = kFeCap / NT;
   const bool fe_par = nfe <= kFeCap;
   int ent[EPT];
 #pragma unroll
   for (int u = 0; u < EPT; ++u) {
-    const int q = tid + u * kCutThreads;
+    const int q = tid + u * NT;
     ent[u] = (fe_par && q < nfe) ? fent[M.f0 + q] : -1;
   }
-  for (int q = tid; q < nit; q += kCutThreads) S.item[q] = C.items[M.i0 + q];
-  int tg = 0, fa = 0, fb = 0, mn = 0;
-  if (tid < m) {
-    tg = members[M.mo + tid];
-    fa = fofs[M.mo + tid] - M.f0;
-    fb = fofs[M.mo + tid + 1] - M.f0;
-    mn = mnode[M.mo + tid];
-    S.mn[tid] = mn;
+  for (int q = tid; q < nit; q += NT) S.item[q] = C.items[M.i0 + q];
+  int tg[TPT], fa[TPT], fb[TPT], mn[TPT];
+#pragma unroll
+  for (int w = 0; w < TPT; ++w) {
+    const int e = tid + w * NT;
+    tg[w] = fa[w] = fb[w] = mn[w] = 0;
+    if (e < m) {
+      tg[w] = members[M.mo + e];
+      fa[w] = fofs[M.mo + e] - M.f0;
+      fb[w] = fofs[M.mo + e + 1] - M.f0;
+      mn[w] = mnode[M.mo + e];
+    }
   }
   __syncthreads();
   // latency-bound launches (few patches per SM): bring the element-matrix
   // row of every item into shared memory with all copies in flight at once
   if (STAGE) {
-    for (int q = tid; q < nit; q += kCutThreads) {
+    for (int q = tid; q < nit; q += NT) {
       const int it = S.item[q], sc = it / NB, jj = it - sc * NB;
       const T* row = S.rowbase[sc] + jj * NB;
 #pragma unroll
       for (int e = 0; e < NB; ++e) cp_async_elem(srow + q * NB + e, row + e);
     }
   }
-  T bval = T(0);
-  if (tid < m) bval = b[mn];
+  T bval[TPT];
+#pragma unroll
+  for (int w = 0; w < TPT; ++w) bval[w] = (tid + w * NT < m) ? b[mn[w]] : T(0);
   // round 2: ghost-face entries, one per thread (dvec_m[i_k] G_m[t] summed
   // over m), and the element-matrix rows
 #pragma unroll
@@ -1036,15 +1149,18 @@ __device__ __forceinline__ void cut_body_cta(const OpArgs<T>& A, T* __restrict__
     T c = T(0);
 #pragma unroll
     for (int mm = 0; mm < P; ++mm) c += A.dvec[mm][il] * gv[mm];
-    S.fc[tid + u * kCutThreads] = c;
+    S.fc[tid + u * NT] = c;
   }
-  T facc = T(0);
-  if (tid < m && !fe_par) {
+  T facc[TPT];
+#pragma unroll
+  for (int w = 0; w < TPT; ++w) {
+    facc[w] = T(0);
+    if (tid + w * NT >= m || fe_par) continue;
     const int* fe = fent + M.f0;
-    for (int q0 = fa; q0 < fb; q0 += 8) {
+    for (int q0 = fa[w]; q0 < fb[w]; q0 += 8) {
       int en[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) en[u] = (q0 + u < fb) ? fe[q0 + u] : -1;
+      for (int u = 0; u < 8; ++u) en[u] = (q0 + u < fb[w]) ? fe[q0 + u] : -1;
       T gv[8][P];
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
@@ -1060,7 +1176,7 @@ __device__ __forceinline__ void cut_body_cta(const OpArgs<T>& A, T* __restrict__
         T c = T(0);
 #pragma unroll
         for (int mm = 0; mm < P; ++mm) c += A.dvec[mm][il] * gv[u][mm];
-        facc += c;
+        facc[w] += c;
       }
     }
   }
@@ -1070,7 +1186,7 @@ __device__ __forceinline__ void cut_body_cta(const OpArgs<T>& A, T* __restrict__
   }
   // rows (patch cell s, local node i) of the patch DoFs: row_i of the cell
   // matrix against the cell's closure values
-  for (int q = tid; q < nit; q += kCutThreads) {
+  for (int q = tid; q < nit; q += NT) {
     const int it = S.item[q], sc = it / NB, jj = it - sc * NB;
     int base = 0, ost = 1;
 #pragma unroll
@@ -1097,19 +1213,22 @@ __device__ __forceinline__ void cut_body_cta(const OpArgs<T>& A, T* __restrict__
     S.part[sc][jj] = acc;
   }
   __syncthreads();
-  // residual of the own row: cell parts in cell order, then the face terms
-  if (tid < m) {
+  // residual of the own rows: cell parts in cell order, then the face terms
+#pragma unroll
+  for (int w = 0; w < TPT; ++w) {
+    const int e = tid + w * NT;
+    if (e >= m) continue;
     if (fe_par) {
       T f4[4] = {T(0), T(0), T(0), T(0)};
-      int q = fa;
-      for (; q + 4 <= fb; q += 4) {
+      int q = fa[w];
+      for (; q + 4 <= fb[w]; q += 4) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) f4[u] += S.fc[q + u];
       }
-      for (; q < fb; ++q) f4[0] += S.fc[q];
-      facc = (f4[0] + f4[1]) + (f4[2] + f4[3]);
+      for (; q < fb[w]; ++q) f4[0] += S.fc[q];
+      facc[w] = (f4[0] + f4[1]) + (f4[2] + f4[3]);
     }
-    int o[3] = {0, 0, 0}, u = tg;
+    int o[3] = {0, 0, 0}, u = tg[w];
 #pragma unroll
     for (int k = 0; k < DIM; ++k) {
       o[k] = u % CC;
@@ -1129,7 +1248,7 @@ __device__ __forceinline__ void cut_body_cta(const OpArgs<T>& A, T* __restrict__
       }
       if (in) acc += S.part[sc][jj];
     }
-    S.r[tid] = bval - (acc + facc);
+    S.r[e] = bval[w] - (acc + facc[w]);
   }
   bool ok = true;
   if (tma) {
@@ -1147,8 +1266,13 @@ __device__ __forceinline__ void cut_body_cta(const OpArgs<T>& A, T* __restrict__
     // (exactly symmetric) inverse so that neighbouring lanes read neighbouring
     // addresses.  The order of the sums depends on m only: a patch gets the
     // same bits in every launch shape (solo, batched, served).
+    // The new value is written from the staged closure value: no other patch
+    // of the colour writes this DoF, so S.x still holds x there.
     const T* Ai = tma ? sinv : inv + M.io;
-    for (int e = tid; e < m; e += kCutThreads) {
+#pragma unroll
+    for (int w = 0; w < TPT; ++w) {
+      const int e = tid + w * NT;
+      if (e >= m) continue;
       const T* Ac = Ai + e;
       T a0 = T(0), a1 = T(0);
       int c = 0;
@@ -1157,7 +1281,7 @@ __device__ __forceinline__ void cut_body_cta(const OpArgs<T>& A, T* __restrict__
         a1 += Ac[(size_t)(c + 1) * m] * S.r[c + 1];
       }
       if (c < m) a0 += Ac[(size_t)c * m] * S.r[c];
-      x[S.mn[e]] += a0 + a1;
+      x[mn[w]] = S.x[tg[w]] + (a0 + a1);
     }
   }
   __syncthreads();
@@ -1165,9 +1289,11 @@ __device__ __forceinline__ void cut_body_cta(const OpArgs<T>& A, T* __restrict__
 
 // STAGE: launches of at most a couple of blocks per SM stage the element-
 // matrix rows in the dynamic shared memory after the inverse slot (at
-// row_off bytes); large grids read them through L1.
-template <int DIM, int P, typename T, bool STAGE>
-__global__ void __launch_bounds__(kCutThreads) k_cut_solve_cta(OpArgs<T> A, T* __restrict__ x,
+// row_off bytes); large grids read them through L1.  NT threads per patch.
+// Blocks of 128 threads resident per SM: seven for FP64 (at most 72
+// registers), nine for FP32 (at most 56).
+template <int DIM, int P, typename T, bool STAGE, int NT>
+__global__ void __launch_bounds__(NT, sizeof(T) == 8 ? 7 : 9) k_cut_solve_cta(OpArgs<T> A, T* __restrict__ x,
                                                                const T* __restrict__ b, CutPatchArgs C,
                                                                const uint16_t* __restrict__ members,
                                                                const int* __restrict__ mnode,
@@ -1189,8 +1315,8 @@ __global__ void __launch_bounds__(kCutThreads) k_cut_solve_cta(OpArgs<T> A, T* _
   for (; j < npatch; j += gridDim.x) {
     CutMeta nxt = cur;
     if (j + (int)gridDim.x < npatch) nxt = cut_meta(C, j0 + j + gridDim.x);
-    cut_body_cta<DIM, P, T, STAGE>(A, x, b, cur, j0 + j, C, members, mnode, fofs, fent, inv, S, sinv, srow,
-                                   inv_cap, &bar, phase, A.Kref, err);
+    cut_body_cta<DIM, P, T, STAGE, NT>(A, x, b, cur, j0 + j, C, members, mnode, fofs, fent, inv, S, sinv, srow,
+                                       inv_cap, &bar, phase, A.Kref, err);
     cur = nxt;
   }
 }

@@ -467,6 +467,62 @@ void build_level(const SetupParams& prm, const RefTables& R, int N, HostLevel& L
         L.S[i * M + j] = t;
       }
     L.lam = lam;
+    // The exact local solve of an interior patch as one dense map per level:
+    // x_I <- A_I^{-1} b_I - A_I^{-1} A_{I,B} x_B over the closure; columns in
+    // closure order (first coordinate fastest), b at interior columns and x
+    // at boundary columns; rows in interior order.
+    {
+      const int NI = ipow(M, d), NC = ipow(C, d);
+      std::vector<double> AIcl((size_t)NI * NC, 0.0);
+      for (int i = 0; i < NI; ++i) {
+        int ii[3] = {0, 0, 0}, t = i;
+        for (int k = 0; k < d; ++k) {
+          ii[k] = t % M;
+          t /= M;
+        }
+        for (int kc = 0; kc < NC; ++kc) {
+          int cc[3] = {0, 0, 0}, u = kc;
+          for (int k = 0; k < d; ++k) {
+            cc[k] = u % C;
+            u /= C;
+          }
+          double v = 0.0;
+          for (int a = 0; a < d; ++a) {  // stiffness along a, mass along the others
+            double f = 1.0;
+            for (int k = 0; k < d; ++k) f *= (k == a ? L.Kr[ii[k] * C + cc[k]] : L.Mr[ii[k] * C + cc[k]]);
+            v += f;
+          }
+          AIcl[(size_t)i * NC + kc] = v;
+        }
+      }
+      auto closure_of = [&](int i) {
+        int kc = 0, st = 1, t = i;
+        for (int k = 0; k < d; ++k) {
+          kc += (t % M + 1) * st;
+          t /= M;
+          st *= C;
+        }
+        return kc;
+      };
+      std::vector<double> AIi((size_t)NI * NI);
+      for (int i = 0; i < NI; ++i)
+        for (int j = 0; j < NI; ++j) AIi[(size_t)i * NI + j] = AIcl[(size_t)i * NC + closure_of(j)];
+      spd_inverse(NI, AIi.data());
+      std::vector<int> interior_index(NC, -1);
+      for (int j = 0; j < NI; ++j) interior_index[closure_of(j)] = j;
+      L.Wcart.assign((size_t)NI * NC, 0.0);
+      for (int i = 0; i < NI; ++i)
+        for (int kc = 0; kc < NC; ++kc) {
+          double w;
+          if (interior_index[kc] >= 0) {
+            w = AIi[(size_t)i * NI + interior_index[kc]];
+          } else {
+            w = 0.0;
+            for (int j = 0; j < NI; ++j) w -= AIi[(size_t)i * NI + j] * AIcl[(size_t)j * NC + kc];
+          }
+          L.Wcart[(size_t)i * NC + kc] = w;
+        }
+    }
   }
   // patches
   {

@@ -75,6 +75,7 @@ struct HostLevel {
   std::vector<double> Kref;       // NB x NB stiffness of an uncut cell
   std::vector<double> Mr, Kr;     // M x C rows of the two-cell 1D mass / stiffness
   std::vector<double> S, lam;     // fast-diagonalisation eigenvectors / values (M)
+  std::vector<double> Wcart;      // (2p-1)^d x (2p+1)^d dense interior-patch update
   double dvec[3][7] = {};         // ghost normal-derivative jump weights
   double coef[3] = {};            // gamma_m h^(2m-1)/(m!)^2 * h^(d-1)
   double Mhat[4][4] = {};         // reference 1D mass on [0, 1]

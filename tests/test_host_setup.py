@@ -117,3 +117,41 @@ def test_footprint_estimate_grows_with_the_mesh():
     inv = small.stats()["inverse_entries"]
     assert fs >= 12 * inv
     assert fl > 4 * fs
+
+
+def test_interior_patch_update_is_the_exact_local_solve(pair):
+    """x_I <- A_I^{-1} b_I - A_I^{-1} A_{I,B} x_B with A_I, A_{I,B} taken from
+    the oracle's assembled matrix at interior patches (Sec. 2.3), and the
+    rows of interior-patch DoFs reach no node outside the closure."""
+    pb, H, k = pair
+    d, p = k["dim"], k["p"]
+    C, M = 2 * p + 1, 2 * p - 1
+    for l in range(1, k["L"]):
+        P = H.levels[l].patches
+        lev = H.levels[l].lev
+        A = H.levels[l].A.tocsr()
+        W = pb.host_interior_update(l)
+        inter = [j for j in range(len(P.verts)) if not P.cut[j]]
+        for j in inter[:: max(1, len(inter) // 6)]:
+            v = P.verts[j]
+            cl = []
+            for kc in range(C ** d):
+                c, t = [], kc
+                for _ in range(d):
+                    c.append(t % C)
+                    t //= C
+                cl.append((sum((p * (int(v[q]) - 1) + c[q]) * lev.n ** q for q in range(d)),
+                           all(1 <= c[q] <= C - 2 for q in range(d))))
+            dofs = np.array([lev.node_to_dof[nd] for nd, _ in cl])
+            inner = np.array([i for i, (_, a) in enumerate(cl) if a])
+            outer = np.array([i for i, (_, a) in enumerate(cl) if not a])
+            assert (dofs >= 0).all() and inner.size == M ** d
+            AI = A[dofs[inner]][:, dofs[inner]].toarray()
+            AIB = A[dofs[inner]][:, dofs[outer]].toarray()
+            rows = A[dofs[inner]]
+            assert set(rows.indices.tolist()) <= set(dofs.tolist())
+            Wo = np.zeros_like(W)
+            AIinv = np.linalg.inv(AI)
+            Wo[:, inner] = AIinv
+            Wo[:, outer] = -AIinv @ AIB
+            assert np.abs(W - Wo).max() <= 1e-10 * np.abs(Wo).max()
