@@ -485,6 +485,8 @@ class Engine final : public EngineBase {
   // interior colours with at least this many patches take two per thread in
   // the FP32 dense step (enough blocks to fill every SM either way)
   static constexpr int kDensePairPatches = 150000;
+  // below this many patches a colour takes several threads per patch
+  static constexpr int kDenseThreadPatches = 20000;
   // threads per patch of the unstaged cut kernel (64 was measured slower
   // than 128 for FP32 at 224^3: 233 against 191 us per finest colour step)
   template <typename T>
@@ -850,10 +852,14 @@ class Engine final : public EngineBase {
       prof_mark(2, s);
       if constexpr (std::is_same<T, float>::value)
       {
+        constexpr int PPB = 128 / DenseGeo<DIM, P>::NPART;
         if (cnt >= kDensePairPatches)
           k_smooth_dense<DIM, P, 2><<<blocks_for(cnt, 256), 128, 0, s>>>(D.dense_d, c.N, c.n, x, b, c.cart + a0, cnt);
-        else
+        else if (cnt >= kDenseThreadPatches)
           k_smooth_dense<DIM, P, 1><<<blocks_for(cnt, 128), 128, 0, s>>>(D.dense_d, c.N, c.n, x, b, c.cart + a0, cnt);
+        else
+          k_smooth_dense_split<DIM, P><<<blocks_for(cnt, PPB), 128, 0, s>>>(D.dense_d, c.N, c.n, x, b,
+                                                                          c.cart + a0, cnt);
       }
       else if (cnt <= 4 * sms_)
         k_smooth_cart_cta<DIM, P, T><<<cnt, 128, 0, s>>>(D.fd, c.N, c.n, x, b, c.cart + a0, cnt);

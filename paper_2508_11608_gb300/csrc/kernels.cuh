@@ -763,8 +763,9 @@ struct DenseGeo {
   static constexpr int C = 2 * P + 1, M = 2 * P - 1;
   static constexpr int NI = (DIM == 2) ? M * M : M * M * M;
   static constexpr int NC = (DIM == 2) ? C * C : C * C * C;
-  static constexpr int NR4 = (NI + 3) / 4 * 4;
-  static constexpr int ROWS = NC / C;  // closure lines along x
+  static constexpr int NPART = (NI + 7) / 8;  // 8-row parts of W (split form)
+  static constexpr int NR4 = NPART * 8;        // padded row count of Wt
+  static constexpr int ROWS = NC / C;          // closure lines along x
 };
 
 template <int DIM, int P>
@@ -856,6 +857,61 @@ __global__ void __launch_bounds__(128, PPT == 2 ? 6 : 8) k_smooth_dense(const fl
     if (!has[q]) continue;
 #pragma unroll
     for (int r = 0; r < NI; ++r) x[base[q] + dense_interior_offset<DIM, P>(r, n)] = acc[q][r];
+  }
+}
+
+// Split form for colours too small to fill the GPU with one thread per patch:
+// the closures of the block's 128 / NPART patches are first gathered into
+// shared memory with every load in flight at once, then NPART threads per
+// patch each form 8 rows of W [b_I ; x_B] (the same products in the same
+// order as above, so the launch shape never changes a result).
+template <int DIM, int P>
+__global__ void __launch_bounds__(128) k_smooth_dense_split(const float* __restrict__ Wt, int N, int n,
+                                                           float* __restrict__ x, const float* __restrict__ b,
+                                                           const int* __restrict__ verts, int nv) {
+  using G = DenseGeo<DIM, P>;
+  constexpr int C = G::C, NC = G::NC, NI = G::NI, NR = G::NR4, NPART = G::NPART, PPB = 128 / NPART;
+  __shared__ __align__(16) float Ws[NC * NR];
+  __shared__ float Gs[PPB][NC + 1];
+  __shared__ int Bs[PPB];
+  for (int i = threadIdx.x; i < NC * NR; i += blockDim.x) Ws[i] = Wt[i];
+  const int p0 = blockIdx.x * PPB;
+  const int np = min(PPB, nv - p0);
+  if (threadIdx.x < np) Bs[threadIdx.x] = dense_base<DIM, P>(verts[p0 + threadIdx.x], N, n);
+  __syncthreads();
+  for (int i = threadIdx.x; i < np * NC; i += blockDim.x) {
+    const int q = i / NC, kc = i - q * NC;
+    const int row = kc / C, cx = kc - row * C;
+    bool inner;
+    const int ro = dense_row<DIM, P>(row, n, inner);
+    const float* src = (inner && cx >= 1 && cx <= C - 2) ? b : x;
+    Gs[q][kc] = src[Bs[q] + ro + cx];
+  }
+  __syncthreads();
+  const int part = threadIdx.x % NPART, slot = threadIdx.x / NPART;
+  if (slot >= np) return;
+  float acc[8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) acc[r] = 0.f;
+  for (int kc = 0; kc < NC; ++kc) {
+    const float g = Gs[slot][kc];
+    const float* wt = Ws + kc * NR + part * 8;
+    const float4 w0 = *reinterpret_cast<const float4*>(wt);
+    const float4 w1 = *reinterpret_cast<const float4*>(wt + 4);
+    acc[0] = fmaf(w0.x, g, acc[0]);
+    acc[1] = fmaf(w0.y, g, acc[1]);
+    acc[2] = fmaf(w0.z, g, acc[2]);
+    acc[3] = fmaf(w0.w, g, acc[3]);
+    acc[4] = fmaf(w1.x, g, acc[4]);
+    acc[5] = fmaf(w1.y, g, acc[5]);
+    acc[6] = fmaf(w1.z, g, acc[6]);
+    acc[7] = fmaf(w1.w, g, acc[7]);
+  }
+  const int base = Bs[slot];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int rr = part * 8 + r;
+    if (rr < NI) x[base + dense_interior_offset<DIM, P>(rr, n)] = acc[r];
   }
 }
 
