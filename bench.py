@@ -123,8 +123,8 @@ FP32_PEAK_TFLOPS = 78.5
 # + dram__bytes_write.sum summed over every k_cut_solve_cta launch of one FP64
 # solve of the 64^3 workload, divided by the launches (cold caches: ncu flushes
 # them before each launch).  Valid only for the kernel source it was taken on.
-CUT_TRAFFIC = {"bytes_per_launch": 18894886.6,
-               "kernels_sha256": "c5e665dbe17c2859e55369b32709d4e2443cbc8c19b02c9011e63c049d9879a7"}
+CUT_TRAFFIC = {"bytes_per_launch": 18894944.3,
+               "kernels_sha256": "b5cb2c79a80a173bcb4d7dd1f67b1e415fa1253708b3c05b52bc4a691be7d64b"}
 
 
 def _kernels_sha256():

@@ -147,6 +147,23 @@ cf_status cf_vcycle(cf_problem* pb, const double* d_r, double* d_z, void* stream
  * reached (x holds the last iterate). */
 cf_status cf_solve(cf_problem* pb, const double* d_b, double* d_x, double rtol,
                    int maxit, cf_info* info, void* stream);
+/* The V-cycle as the solver (Sec. 2.2, the direct V-cycle iteration):
+ * x_{k+1} = x_k + B (b - A x_k) from x_0 = 0, B one V-cycle in the precision
+ * set by cf_set_precision, until ||b - A x_k||_2 <= rtol ||b||_2 (the residual
+ * in FP64).  Vectors and info as for cf_solve; CF_ENOCONV when maxit is
+ * reached first (x then holds the last iterate). */
+cf_status cf_solve_vcycle(cf_problem* pb, const double* d_b, double* d_x, double rtol, int maxit,
+                          cf_info* info, void* stream);
+/* GMRES(restart) with one V-cycle as right preconditioner (Sec. 2.2; the
+ * paper's outer solver): minimises ||b - A x||_2 over x_0 + B K_k(A B, r_0),
+ * x_0 = 0, modified Gram-Schmidt Arnoldi in FP64, restarted from the true
+ * residual after `restart` steps; stops when the residual estimate falls to
+ * rtol ||b||_2.  info->iterations counts Arnoldi steps over all cycles.  The
+ * first call with a given restart allocates (2 restart + 2) finest-level
+ * vectors on the device.  CF_EINVAL for restart < 1; CF_ENOCONV when maxit
+ * is reached first (x holds the iterate after the last step). */
+cf_status cf_solve_gmres(cf_problem* pb, const double* d_b, double* d_x, double rtol, int restart, int maxit,
+                         cf_info* info, void* stream);
 
 /* ---- single steps of the hot path on one level (parity testing) ---------
  * All vectors are FP64 device arrays in the level's DoF order; `precision`

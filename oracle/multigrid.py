@@ -230,6 +230,77 @@ class Hierarchy:
         x = self.smooth(l, x, b, post=True)
         return x
 
+    def vcycle_solve(self, b, rtol=1e-9, maxit=500):
+        """The V-cycle as a solver (Sec. 2.2, the direct V-cycle iteration):
+        x_{k+1} = x_k + B (b - A x_k), x_0 = 0, until ||b - A x_k||_2 <=
+        rtol ||b||_2.  Returns (x, iterations, history of ||r||_2)."""
+        A = self.fine.A
+        x = np.zeros_like(b)
+        r = b.copy()
+        bn = np.linalg.norm(b)
+        hist = [np.linalg.norm(r)]
+        it = 0
+        while hist[-1] > rtol * bn and it < maxit:
+            x = x + self.vcycle(r)
+            r = b - A @ x
+            it += 1
+            hist.append(np.linalg.norm(r))
+        return x, it, hist
+
+    def gmres(self, b, rtol=1e-9, restart=30, maxit=500):
+        """GMRES(restart) with the V-cycle as right preconditioner (Sec. 2.2):
+        minimises ||b - A x||_2 over x_0 + B K_k(A B, r_0), x_0 = 0, Arnoldi
+        by modified Gram-Schmidt, least squares by Givens rotations; stops
+        when the residual norm falls to rtol ||b||_2.  Returns (x, total
+        iterations, history of the residual norms)."""
+        A = self.fine.A
+        n = b.size
+        x = np.zeros_like(b)
+        bn = np.linalg.norm(b)
+        r = b.copy()
+        beta = np.linalg.norm(r)
+        hist = [beta]
+        total = 0
+        while beta > rtol * bn and total < maxit:
+            m = restart
+            V = np.zeros((m + 1, n))
+            Z = np.zeros((m, n))
+            H = np.zeros((m + 1, m))
+            cs, sn = np.zeros(m), np.zeros(m)
+            g = np.zeros(m + 1)
+            g[0] = beta
+            V[0] = r / beta
+            k = 0
+            for j in range(m):
+                Z[j] = self.vcycle(V[j])
+                w = A @ Z[j]
+                for i in range(j + 1):
+                    H[i, j] = w @ V[i]
+                    w = w - H[i, j] * V[i]
+                H[j + 1, j] = np.linalg.norm(w)
+                if H[j + 1, j] > 0:
+                    V[j + 1] = w / H[j + 1, j]
+                for i in range(j):  # earlier rotations on the new column
+                    t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+                    H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
+                    H[i, j] = t
+                den = np.hypot(H[j, j], H[j + 1, j])
+                cs[j], sn[j] = H[j, j] / den, H[j + 1, j] / den
+                H[j, j] = den
+                H[j + 1, j] = 0.0
+                g[j + 1] = -sn[j] * g[j]
+                g[j] = cs[j] * g[j]
+                k = j + 1
+                total += 1
+                hist.append(abs(g[j + 1]))
+                if abs(g[j + 1]) <= rtol * bn or total >= maxit:
+                    break
+            y = np.linalg.solve(np.triu(H[:k, :k]), g[:k])
+            x = x + Z[:k].T @ y
+            r = b - A @ x
+            beta = np.linalg.norm(r)
+        return x, total, hist
+
     def pcg(self, b, rtol=1e-8, maxit=500):
         """CG on A_L x = b preconditioned by one V-cycle; x_0 = 0.
         Returns (x, iterations, history of ||r||_2)."""

@@ -128,6 +128,26 @@ class Problem:
         return {"iterations": info.iterations, "rel_residual": info.rel_residual,
                 "true_rel_residual": info.true_rel_residual, "solve_ms": info.solve_ms}
 
+    def solve_vcycle(self, b, x, rtol=1e-9, maxit=500, stream=None, allow_noconv=False):
+        """The V-cycle iteration as the solver (cf_solve_vcycle)."""
+        info = _lib.cf_info()
+        st = self._lib.cf_solve_vcycle(self._h, _ptr(b), _ptr(x), rtol, maxit, ctypes.byref(info),
+                                       _stream(stream))
+        if not (allow_noconv and st == _lib.CF_ENOCONV):
+            check(st)
+        return {"iterations": info.iterations, "rel_residual": info.rel_residual,
+                "true_rel_residual": info.true_rel_residual, "solve_ms": info.solve_ms}
+
+    def solve_gmres(self, b, x, rtol=1e-9, restart=30, maxit=500, stream=None, allow_noconv=False):
+        """GMRES(restart) preconditioned by the V-cycle (cf_solve_gmres)."""
+        info = _lib.cf_info()
+        st = self._lib.cf_solve_gmres(self._h, _ptr(b), _ptr(x), rtol, restart, maxit, ctypes.byref(info),
+                                      _stream(stream))
+        if not (allow_noconv and st == _lib.CF_ENOCONV):
+            check(st)
+        return {"iterations": info.iterations, "rel_residual": info.rel_residual,
+                "true_rel_residual": info.true_rel_residual, "solve_ms": info.solve_ms}
+
     # ---- single steps on one level ---------------------------------------------------
     def level_apply(self, level, x, y, precision=CF_FP64, stream=None):
         check(self._lib.cf_level_apply(self._h, level, precision, _ptr(x), _ptr(y), _stream(stream)))

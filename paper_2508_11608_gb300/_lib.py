@@ -18,7 +18,7 @@ CF_K_CUT_SOLVE, CF_K_INTERIOR, CF_K_APPLY_BULK, CF_K_APPLY_BND, CF_K_FACE_MOMENT
 EXPORTED = [
     "cf_setup", "cf_destroy", "cf_last_error", "cf_n_levels", "cf_n_dofs", "cf_level_n_dofs",
     "cf_dof_lattice", "cf_dof_coords", "cf_stats", "cf_work_model", "cf_footprint", "cf_set_precision", "cf_rhs", "cf_apply",
-    "cf_vcycle", "cf_solve", "cf_level_apply", "cf_level_colour_step", "cf_level_smooth",
+    "cf_vcycle", "cf_solve", "cf_solve_vcycle", "cf_solve_gmres", "cf_level_apply", "cf_level_colour_step", "cf_level_smooth",
     "cf_level_restrict", "cf_level_prolongate", "cf_coarse_solve", "cf_setup_host", "cf_host_rhs",
     "cf_host_cell_matrix", "cf_host_patch_counts", "cf_host_interior_update", "cf_host_interior_patch", "cf_host_cut_patch",
     "cf_launch_count", "cf_profile_start", "cf_profile_read", "cf_coarse_solve_noalloc",
@@ -88,6 +88,8 @@ def load():
     lib.cf_apply.argtypes = [P, P, P, V]
     lib.cf_vcycle.argtypes = [P, P, P, V]
     lib.cf_solve.argtypes = [P, P, P, D, I, ctypes.POINTER(cf_info), V]
+    lib.cf_solve_vcycle.argtypes = [P, P, P, D, I, ctypes.POINTER(cf_info), V]
+    lib.cf_solve_gmres.argtypes = [P, P, P, D, I, I, ctypes.POINTER(cf_info), V]
     lib.cf_level_apply.argtypes = [P, I, I, P, P, V]
     lib.cf_level_colour_step.argtypes = [P, I, I, I, I, P, P, V]
     lib.cf_level_smooth.argtypes = [P, I, I, I, P, P, V]

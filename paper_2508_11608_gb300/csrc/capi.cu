@@ -306,6 +306,48 @@ cf_status cf_solve(cf_problem* pb, const double* d_b, double* d_x, double rtol, 
   return CF_OK;
 }
 
+cf_status cf_solve_vcycle(cf_problem* pb, const double* d_b, double* d_x, double rtol, int maxit,
+                          cf_info* info, void* stream) {
+  if (no_device(pb) || !d_b || !d_x) return fail(CF_EINVAL, "null argument");
+  if (!(rtol > 0.0) || maxit < 1) return fail(CF_EINVAL, "rtol must be positive and maxit >= 1");
+  int it = 0;
+  double rel = 0, trel = 0;
+  float ms = 0;
+  cf_status st = guarded([&] {
+    it = pb->eng->solve_vcycle(pb->precision, d_b, d_x, rtol, maxit, &rel, &trel, &ms, S(stream));
+  });
+  if (st != CF_OK) return st;
+  if (info) {
+    info->iterations = it;
+    info->rel_residual = rel;
+    info->true_rel_residual = trel;
+    info->solve_ms = ms;
+  }
+  if (rel > rtol) return fail(CF_ENOCONV, "the V-cycle iteration reached maxit before the tolerance");
+  return CF_OK;
+}
+
+cf_status cf_solve_gmres(cf_problem* pb, const double* d_b, double* d_x, double rtol, int restart, int maxit,
+                         cf_info* info, void* stream) {
+  if (no_device(pb) || !d_b || !d_x) return fail(CF_EINVAL, "null argument");
+  if (!(rtol > 0.0) || maxit < 1 || restart < 1) return fail(CF_EINVAL, "rtol > 0, maxit >= 1, restart >= 1");
+  int it = 0;
+  double rel = 0, trel = 0;
+  float ms = 0;
+  cf_status st = guarded([&] {
+    it = pb->eng->solve_gmres(pb->precision, d_b, d_x, rtol, restart, maxit, &rel, &trel, &ms, S(stream));
+  });
+  if (st != CF_OK) return st;
+  if (info) {
+    info->iterations = it;
+    info->rel_residual = rel;
+    info->true_rel_residual = trel;
+    info->solve_ms = ms;
+  }
+  if (rel > rtol) return fail(CF_ENOCONV, "GMRES reached maxit before the tolerance");
+  return CF_OK;
+}
+
 cf_status cf_level_apply(cf_problem* pb, int level, int precision, const double* d_x, double* d_y,
                          void* stream) {
   if (bad_level(pb, level) || no_device(pb) || bad_prec(precision) || !d_x || !d_y) return fail(CF_EINVAL, "bad argument");

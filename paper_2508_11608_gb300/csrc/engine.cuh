@@ -35,6 +35,31 @@ inline void launch_check(const char* what) {
 }
 
 // owns every device allocation of a problem
+// FP64 vector updates of the Krylov solvers (finest level, box layout)
+// y += a x over a region; a = sign * (*as) when as is given, else a = sign
+static __global__ void __launch_bounds__(256) k_axpy(Region R, const double* __restrict__ as, double sign,
+                                                     const double* __restrict__ x, double* __restrict__ y) {
+  const double a = as ? sign * *as : sign;
+  const int64_t tot = R.size();
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = R.at(t);
+    y[o] += a * x[o];
+  }
+}
+
+// y = x / sqrt(*nn) over a region (normalisation by a squared norm on the device)
+static __global__ void __launch_bounds__(256) k_scale_rsqrt(Region R, const double* __restrict__ nn,
+                                                            const double* __restrict__ x, double* __restrict__ y) {
+  const double a = 1.0 / sqrt(*nn);
+  const int64_t tot = R.size();
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = R.at(t);
+    y[o] = a * x[o];
+  }
+}
+
 class DevPool {
  public:
   ~DevPool() {
@@ -404,6 +429,135 @@ class Engine final : public EngineBase {
     return it;
   }
 
+  // The V-cycle as the solver (Sec. 2.2): x_{k+1} = x_k + B (b - A x_k),
+  // x_0 = 0, until ||b - A x_k|| <= rtol ||b||; one host read per iteration.
+  int solve_vcycle(int prec, const double* b, double* x, double rtol, int maxit, double* rel, double* true_rel,
+                   float* ms, cudaStream_t s) override {
+    const int L = n_levels() - 1;
+    const auto& F = com_[L];
+    Timer tm(s);
+    to_box(L, b, bF_, s);
+    const size_t bytes = sizeof(double) * F.nbox;
+    CUTMG_CUDA(cudaMemsetAsync(xF_, 0, bytes, s));
+    CUTMG_CUDA(cudaMemcpyAsync(rF_, bF_, bytes, cudaMemcpyDeviceToDevice, s));
+    dot(F.region, bF_, bF_, sc_ + 4, s);
+    const double bn = std::sqrt(read_scalar(4, s));
+    double rn = bn;
+    int it = 0;
+    while (rn > rtol * bn && it < maxit) {
+      run_graph(GraphKey{300 + prec, rF_, zF_}, s, [&](cudaStream_t cs) { precondition(prec, rF_, zF_, cs); });
+      run_graph(GraphKey{400, zF_, rF_}, s, [&](cudaStream_t cs) {
+        k_axpy<<<kVecBlocks, 256, 0, cs>>>(F.region, nullptr, 1.0, zF_, xF_);
+        count_launch("axpy");
+        apply<double>(L, d64_[L], xF_, bF_, rF_, cs);
+        dot(F.region, rF_, rF_, sc_ + 3, cs);
+        CUTMG_CUDA(cudaMemcpyAsync(host_sc_ + 3, sc_ + 3, sizeof(double), cudaMemcpyDeviceToHost, cs));
+      });
+      CUTMG_CUDA(cudaStreamSynchronize(s));
+      rn = std::sqrt(host_sc_[3]);
+      ++it;
+    }
+    *ms = tm.stop();
+    check_err(s);
+    *true_rel = bn > 0 ? true_residual(s) / bn : 0.0;
+    *rel = bn > 0 ? rn / bn : 0.0;
+    from_box(L, xF_, x, s);
+    return it;
+  }
+
+  // GMRES(restart) right-preconditioned by one V-cycle (Sec. 2.2): minimises
+  // ||b - A x|| over x_0 + B K_k(A B, r_0), Arnoldi by modified Gram-Schmidt
+  // with the Hessenberg entries on the device, Givens rotations of each new
+  // column on the host; restarts from the true residual.
+  int solve_gmres(int prec, const double* b, double* x, double rtol, int restart, int maxit, double* rel,
+                  double* true_rel, float* ms, cudaStream_t s) override {
+    const int L = n_levels() - 1;
+    const auto& F = com_[L];
+    const int m = restart;
+    gmres_storage(m);
+    Timer tm(s);
+    to_box(L, b, bF_, s);
+    const size_t bytes = sizeof(double) * F.nbox;
+    CUTMG_CUDA(cudaMemsetAsync(xF_, 0, bytes, s));
+    CUTMG_CUDA(cudaMemcpyAsync(rF_, bF_, bytes, cudaMemcpyDeviceToDevice, s));
+    dot(F.region, bF_, bF_, sc_ + 4, s);
+    const double bn = std::sqrt(read_scalar(4, s));
+    dot(F.region, rF_, rF_, gsc_ + m + 1, s);
+    double beta = bn, rn = bn;
+    int total = 0;
+    std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), col(m + 2);
+    while (beta > rtol * bn && total < maxit) {
+      // v_0 = r / ||r||  (gsc_[m + 1] holds ||r||^2)
+      for (auto& h : H) h = 0.0;
+      std::fill(g.begin(), g.end(), 0.0);
+      g[0] = beta;
+      k_scale_rsqrt<<<kVecBlocks, 256, 0, s>>>(F.region, gsc_ + m + 1, rF_, gV_[0]);
+      count_launch("gmres normalise");
+      int k = 0;
+      bool done = false;
+      for (int j = 0; j < m; ++j) {
+        // z_j = B v_j, w = A z_j, MGS against v_0..v_j, h_{j+1,j} = ||w||
+        run_graph(GraphKey{300 + prec, gV_[j], gZ_[j]}, s,
+                  [&](cudaStream_t c2) { precondition(prec, gV_[j], gZ_[j], c2); });
+        apply<double>(L, d64_[L], gZ_[j], nullptr, gW_, s);
+        for (int i = 0; i <= j; ++i) {
+          dot(F.region, gW_, gV_[i], gsc_ + i, s);
+          k_axpy<<<kVecBlocks, 256, 0, s>>>(F.region, gsc_ + i, -1.0, gV_[i], gW_);
+          count_launch("gmres orthogonalise");
+        }
+        dot(F.region, gW_, gW_, gsc_ + j + 1, s);
+        k_scale_rsqrt<<<kVecBlocks, 256, 0, s>>>(F.region, gsc_ + j + 1, gW_, gV_[j + 1]);
+        count_launch("gmres normalise");
+        CUTMG_CUDA(cudaMemcpyAsync(col.data(), gsc_, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, s));
+        CUTMG_CUDA(cudaStreamSynchronize(s));
+        col[j + 1] = std::sqrt(col[j + 1]);
+        for (int i = 0; i <= j + 1; ++i) H[(size_t)i * m + j] = col[i];
+        for (int i = 0; i < j; ++i) {
+          const double t = cs[i] * H[(size_t)i * m + j] + sn[i] * H[(size_t)(i + 1) * m + j];
+          H[(size_t)(i + 1) * m + j] = -sn[i] * H[(size_t)i * m + j] + cs[i] * H[(size_t)(i + 1) * m + j];
+          H[(size_t)i * m + j] = t;
+        }
+        const double den = std::hypot(H[(size_t)j * m + j], H[(size_t)(j + 1) * m + j]);
+        cs[j] = H[(size_t)j * m + j] / den;
+        sn[j] = H[(size_t)(j + 1) * m + j] / den;
+        H[(size_t)j * m + j] = den;
+        H[(size_t)(j + 1) * m + j] = 0.0;
+        g[j + 1] = -sn[j] * g[j];
+        g[j] = cs[j] * g[j];
+        k = j + 1;
+        ++total;
+        rn = std::fabs(g[j + 1]);
+        if (rn <= rtol * bn || total >= maxit) {
+          done = true;
+          break;
+        }
+      }
+      // x += Z_k y with H_k y = g_k (upper triangular, on the host)
+      std::vector<double> y(k);
+      for (int i = k - 1; i >= 0; --i) {
+        double t = g[i];
+        for (int q = i + 1; q < k; ++q) t -= H[(size_t)i * m + q] * y[q];
+        y[i] = t / H[(size_t)i * m + i];
+      }
+      for (int i = 0; i < k; ++i) {
+        k_axpy<<<kVecBlocks, 256, 0, s>>>(F.region, nullptr, y[i], gZ_[i], xF_);
+        count_launch("gmres update");
+      }
+      apply<double>(L, d64_[L], xF_, bF_, rF_, s);
+      dot(F.region, rF_, rF_, gsc_ + m + 1, s);
+      CUTMG_CUDA(cudaMemcpyAsync(col.data(), gsc_ + m + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+      CUTMG_CUDA(cudaStreamSynchronize(s));
+      beta = std::sqrt(col[0]);
+      if (done) break;
+    }
+    *ms = tm.stop();
+    check_err(s);
+    *true_rel = bn > 0 ? true_residual(s) / bn : 0.0;
+    *rel = bn > 0 ? rn / bn : 0.0;
+    from_box(L, xF_, x, s);
+    return total;
+  }
+
   template <typename T>
   std::vector<Typed<T>>& typed();
 
@@ -548,6 +702,9 @@ class Engine final : public EngineBase {
  private:
   static constexpr int kVecBlocks = 1024;
   int sms_ = 152;
+  std::vector<double*> gV_, gZ_;  // GMRES basis (box vectors), allocated on first use
+  double* gW_ = nullptr;
+  double* gsc_ = nullptr;
 
   const Hierarchy& H_;
   DevPool pool_;
@@ -780,6 +937,46 @@ class Engine final : public EngineBase {
       CUTMG_CUDA(cudaMemsetAsync(err_, 0, sizeof(int), s));
       throw TimeoutError("a bounded wait on a TMA copy ran out in the cut-patch kernel");
     }
+  }
+
+  // CUDA-event timer on one stream
+  struct Timer {
+    cudaStream_t s;
+    cudaEvent_t e0, e1;
+    explicit Timer(cudaStream_t st) : s(st) {
+      CUTMG_CUDA(cudaEventCreate(&e0));
+      CUTMG_CUDA(cudaEventCreate(&e1));
+      CUTMG_CUDA(cudaEventRecord(e0, s));
+    }
+    float stop() {
+      float ms = 0.f;
+      CUTMG_CUDA(cudaEventRecord(e1, s));
+      CUTMG_CUDA(cudaEventSynchronize(e1));
+      CUTMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      return ms;
+    }
+    ~Timer() {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+    }
+  };
+
+  // ||b - A x|| of the finest-level iterate (FP64)
+  double true_residual(cudaStream_t s) {
+    const int L = n_levels() - 1;
+    apply<double>(L, d64_[L], xF_, bF_, tF_, s);
+    dot(com_[L].region, tF_, tF_, sc_ + 5, s);
+    return std::sqrt(read_scalar(5, s));
+  }
+
+  // Krylov basis of GMRES(m): v_0..v_m, z_0..z_{m-1}, w and m + 2 scalars
+  void gmres_storage(int m) {
+    if ((int)gZ_.size() >= m) return;
+    const int64_t nb = com_.back().nbox;
+    while ((int)gV_.size() < m + 1) gV_.push_back(pool_.alloc<double>(nb));  // zeroed
+    while ((int)gZ_.size() < m) gZ_.push_back(pool_.alloc<double>(nb));
+    if (!gW_) gW_ = pool_.alloc<double>(nb);
+    gsc_ = pool_.alloc<double>(m + 2);
   }
 
   double read_scalar(int i, cudaStream_t s) {

@@ -44,6 +44,12 @@ class EngineBase {
                     double* true_rel, float* ms, cudaStream_t s) = 0;
   // the parts of a CG solve around its iterations: x = 0, r = b, z = B r,
   // p = z (returns ||b||); at the end the true residual norm and x gathered
+  // The V-cycle as the solver: x += B (b - A x) from x = 0 (Sec. 2.2)
+  virtual int solve_vcycle(int prec, const double* b, double* x, double rtol, int maxit, double* rel,
+                           double* true_rel, float* ms, cudaStream_t s) = 0;
+  // GMRES(restart) with the V-cycle as right preconditioner (Sec. 2.2)
+  virtual int solve_gmres(int prec, const double* b, double* x, double rtol, int restart, int maxit, double* rel,
+                          double* true_rel, float* ms, cudaStream_t s) = 0;
   virtual double cg_begin(int prec, const double* b, cudaStream_t s) = 0;
   virtual double cg_end(double* x, cudaStream_t s) = 0;
   // kernel launches issued so far, and event timing of one kernel family

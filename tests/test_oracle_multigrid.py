@@ -133,3 +133,56 @@ def test_iteration_counts_bounded_under_refinement():
         its.append(it)
     assert max(its) <= 8
     assert its[-1] <= its[0] + 1
+
+
+def _tiny_b_and_B(H):
+    A = H.fine.A.toarray()
+    n = A.shape[0]
+    B = np.stack([H.vcycle(np.eye(n)[:, i]) for i in range(n)], axis=1)
+    b = H.rhs()
+    return A, B, b
+
+
+def test_vcycle_solver_residuals_are_powers_of_the_iteration_matrix(h2d):
+    """x_{k+1} = x_k + B (b - A x_k) from 0: r_k = (I - A B)^k b exactly."""
+    H = h2d
+    A, B, b = _tiny_b_and_B(H)
+    _, it, hist = H.vcycle_solve(b, rtol=1e-30, maxit=5)
+    r = b.copy()
+    for k in range(1, 6):
+        r = r - A @ (B @ r)
+        assert hist[k] == pytest.approx(np.linalg.norm(r), rel=1e-9)
+
+
+def test_gmres_is_the_minimal_residual_over_the_preconditioned_krylov_space(h2d):
+    """After k steps from x_0 = 0, GMRES with right preconditioner B returns
+    the x in B K_k(A B, b) of least ||b - A x||_2 (checked by least squares
+    over an explicit orthonormal Krylov basis), for k = 1..4."""
+    H = h2d
+    A, B, b = _tiny_b_and_B(H)
+    AB = A @ B
+    K = [b / np.linalg.norm(b)]
+    for k in range(1, 5):
+        Q, _ = np.linalg.qr(np.stack(K, axis=1))
+        Y = B @ Q                        # x = Y c
+        c, *_ = np.linalg.lstsq(A @ Y, b, rcond=None)
+        best = np.linalg.norm(b - A @ (Y @ c))
+        x, it, hist = H.gmres(b, rtol=1e-30, restart=30, maxit=k)
+        assert it == k
+        assert np.linalg.norm(b - A @ x) == pytest.approx(best, rel=1e-8)
+        assert hist[-1] == pytest.approx(best, rel=1e-8)
+        K.append(AB @ K[-1])
+        K[-1] = K[-1] / np.linalg.norm(K[-1])
+
+
+def test_solvers_converge_to_the_direct_solution(h2d):
+    H = h2d
+    import scipy.sparse.linalg as spla
+    b = H.rhs()
+    xd = spla.spsolve(H.fine.A.tocsc(), b)
+    for solve in (H.vcycle_solve, H.gmres):
+        x, it, hist = solve(b, rtol=1e-12)
+        assert np.linalg.norm(x - xd) <= 1e-8 * np.linalg.norm(xd)
+        assert all(hist[i + 1] <= hist[i] * (1 + 1e-12) for i in range(len(hist) - 1))
+    x3, _, _ = H.gmres(b, rtol=1e-12, restart=3)
+    assert np.linalg.norm(x3 - xd) <= 1e-8 * np.linalg.norm(xd)
