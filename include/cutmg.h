@@ -88,7 +88,17 @@ typedef struct {
   int n_c;               /* repetitions of the cut-patch sweep (eq. "smoother-split"); default 2 */
   int quad_q;            /* Gauss points per sub-interval of the cut-cell rules; default p + 2 */
   int precision;         /* cf_precision of cf_vcycle / cf_solve; default CF_FP64 */
+  int smoother;          /* cf_smoother: CF_SMOOTHER_MVS (default) or CF_SMOOTHER_CHEBYSHEV */
+  int smoother_degree;   /* degree of the Chebyshev smoother (Sec. 4 compares degree 5); default 5 */
 } cf_params;
+
+/* Smoother of the V-cycle.  MVS: the multiplicative vertex-patch smoother
+ * (Sec. 2.3, the method).  CHEBYSHEV: the baseline the paper compares it with
+ * (Sec. 4): point-Jacobi-scaled Chebyshev smoothing of the given degree on
+ * [lambda / 20, lambda], lambda = 1.2 x lambda_max(D^{-1} A_l) estimated by 30
+ * power iterations from the all-ones vector; the same polynomial pre and post
+ * (a symmetric V-cycle).  The batched form supports MVS only. */
+typedef enum { CF_SMOOTHER_MVS = 0, CF_SMOOTHER_CHEBYSHEV = 1 } cf_smoother;
 
 typedef struct {
   int iterations;          /* CG iterations taken */
@@ -306,6 +316,9 @@ cf_status cf_host_interior_patch(const cf_problem* pb, int level, int64_t j, int
  * row-major; rows = interior nodes, columns = closure nodes, both first
  * coordinate fastest; b enters at interior columns, x at boundary columns. */
 cf_status cf_host_interior_update(const cf_problem* pb, int level, double* h_W);
+/* Diagonal of A_level (host array of cf_level_n_dofs doubles, DoF order):
+ * the point-Jacobi scaling of the Chebyshev smoother.  Levels >= 1. */
+cf_status cf_host_diagonal(const cf_problem* pb, int level, double* h_d);
 /* Cut patch j: vertex, DoF count m, lattice indices of its m DoFs (h_nodes,
  * room for (2p+1)^d) and, if h_inv is not NULL, the m x m explicit inverse
  * of A[I_j, I_j] (row-major, in the order of h_nodes). */

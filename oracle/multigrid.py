@@ -159,8 +159,16 @@ class Hierarchy:
     """Levels l = 0..L (N_l = N_L / 2^(L-l)), assembled operators, transfers,
     patches; V-cycle and PCG."""
 
-    def __init__(self, ls, d, N, p, n_levels, gamma_D=None, gammas=None, q=None, n_c=2):
+    # Chebyshev smoother (the paper's comparison in Sec. 4): degree, power
+    # iterations of the lambda_max estimate, safety factor, smoothing range
+    CHEB_POWER_STEPS = 30
+    CHEB_SAFETY = 1.2
+    CHEB_RANGE = 20.0
+
+    def __init__(self, ls, d, N, p, n_levels, gamma_D=None, gammas=None, q=None, n_c=2,
+                 smoother="mvs", cheb_degree=5):
         self.d, self.p, self.n_c = d, p, n_c
+        self.smoother, self.cheb_degree = smoother, cheb_degree
         self.gamma_D = 20.0 * p * p if gamma_D is None else gamma_D
         self.gammas = [0.1] * p if gammas is None else list(gammas)
         self.q = p + 2 if q is None else q
@@ -174,6 +182,45 @@ class Hierarchy:
             self.levels[l].patches = Patches(self.levels[l].lev, self.levels[l].A)
         A0 = self.levels[0].A.toarray()
         self.coarse_chol = sla.cho_factor(A0)
+        if smoother == "chebyshev":
+            for l in range(1, n_levels):
+                L = self.levels[l]
+                L.dinv = 1.0 / L.A.diagonal()
+                L.lam_max = self.power_lambda_max(L)
+
+    def power_lambda_max(self, L):
+        """lambda_max of D^{-1} A by power iteration from the normalised
+        all-ones vector: v <- w / ||w|| with w = D^{-1} A v; returns the last
+        ||w|| (a fixed number of steps, so that every implementation gets the
+        same estimate up to rounding)."""
+        v = np.ones(L.A.shape[0])
+        v /= np.linalg.norm(v)
+        lam = 0.0
+        for _ in range(self.CHEB_POWER_STEPS):
+            w = L.dinv * (L.A @ v)
+            lam = np.linalg.norm(w)
+            v = w / lam
+        return lam
+
+    def chebyshev(self, l, x, b):
+        """Degree-k Chebyshev smoothing of A_l x = b with point-Jacobi scaling
+        on [lambda / range, lambda], lambda = safety * lambda_max(D^{-1} A)
+        (three-term recurrence): k operator applications."""
+        L = self.levels[l]
+        lmax = self.CHEB_SAFETY * L.lam_max
+        lmin = lmax / self.CHEB_RANGE
+        theta, delta = 0.5 * (lmax + lmin), 0.5 * (lmax - lmin)
+        sigma = theta / delta
+        rho = 1.0 / sigma
+        r = b - L.A @ x
+        xp = x
+        x = x + (1.0 / theta) * (L.dinv * r)
+        for _ in range(1, self.cheb_degree):
+            r = b - L.A @ x
+            rho_new = 1.0 / (2.0 * sigma - rho)
+            x, xp = x + rho_new * rho * (x - xp) + (2.0 * rho_new / delta) * (L.dinv * r), x
+            rho = rho_new
+        return x
 
     @property
     def fine(self):
@@ -208,6 +255,8 @@ class Hierarchy:
         return x
 
     def smooth(self, l, x, b, post=False):
+        if self.smoother == "chebyshev":
+            return self.chebyshev(l, x, b)
         seq = self.schedule()
         if post:
             seq = seq[::-1]

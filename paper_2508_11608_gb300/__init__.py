@@ -10,7 +10,7 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import CF_FP64, CF_MIXED, CutmgError, check  # noqa: F401
+from ._lib import CF_FP64, CF_MIXED, CF_SMOOTHER_CHEBYSHEV, CF_SMOOTHER_MVS, CutmgError, check  # noqa: F401
 
 
 def _ptr(t):
@@ -28,7 +28,7 @@ class Problem:
 
     def __init__(self, dim, n_cells, n_levels, degree, center=None, radius=None, plane=None,
                  levelset=None, lo=-1.0, hi=1.0, gamma_D=0.0, gamma_ghost=(0.0,) * 4, n_c=0,
-                 quad_q=0, precision=CF_FP64, host_only=False):
+                 quad_q=0, precision=CF_FP64, host_only=False, smoother=0, smoother_degree=0):
         lib = _lib.load()
         self._lib = lib
         mesh = _lib.cf_mesh(dim, n_cells, lo, hi, n_levels)
@@ -46,6 +46,8 @@ class Problem:
         prm.n_c = n_c
         prm.quad_q = quad_q
         prm.precision = precision
+        prm.smoother = smoother
+        prm.smoother_degree = smoother_degree
         h = ctypes.c_void_p()
         setup = lib.cf_setup_host if host_only else lib.cf_setup
         check(setup(ctypes.byref(mesh), ctypes.byref(ls), degree, ctypes.byref(prm), ctypes.byref(h)))
@@ -202,6 +204,12 @@ class Problem:
         nb = (self.degree + 1) ** self.dim
         out = np.empty((nb, nb), dtype=np.float64)
         check(self._lib.cf_host_cell_matrix(self._h, level, cell, out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def host_diagonal(self, level):
+        """Diagonal of A_level in DoF order (levels >= 1)."""
+        out = np.empty(self.n_dofs(level), dtype=np.float64)
+        check(self._lib.cf_host_diagonal(self._h, level, out.ctypes.data_as(ctypes.c_void_p)))
         return out
 
     def host_interior_update(self, level):

@@ -13,6 +13,7 @@ LIB_PATH = os.path.join(_HERE, "libcutmg.so")
 CF_OK, CF_EINVAL, CF_ENOMEM, CF_ECUDA, CF_ENOCONV, CF_ETIMEOUT, CF_EUNSUPPORTED = range(7)
 CF_LS_SPHERE, CF_LS_PLANE, CF_LS_ELLIPSOID, CF_LS_TORUS, CF_LS_FLOWER = 0, 1, 2, 3, 4
 CF_FP64, CF_MIXED = 0, 1
+CF_SMOOTHER_MVS, CF_SMOOTHER_CHEBYSHEV = 0, 1
 CF_K_CUT_SOLVE, CF_K_INTERIOR, CF_K_APPLY_BULK, CF_K_APPLY_BND, CF_K_FACE_MOMENTS = 1, 2, 3, 4, 5
 
 EXPORTED = [
@@ -20,7 +21,7 @@ EXPORTED = [
     "cf_dof_lattice", "cf_dof_coords", "cf_stats", "cf_work_model", "cf_footprint", "cf_set_precision", "cf_rhs", "cf_apply",
     "cf_vcycle", "cf_solve", "cf_solve_vcycle", "cf_solve_gmres", "cf_level_apply", "cf_level_colour_step", "cf_level_smooth",
     "cf_level_restrict", "cf_level_prolongate", "cf_coarse_solve", "cf_setup_host", "cf_host_rhs",
-    "cf_host_cell_matrix", "cf_host_patch_counts", "cf_host_interior_update", "cf_host_interior_patch", "cf_host_cut_patch",
+    "cf_host_cell_matrix", "cf_host_patch_counts", "cf_host_interior_update", "cf_host_diagonal", "cf_host_interior_patch", "cf_host_cut_patch",
     "cf_launch_count", "cf_profile_start", "cf_profile_read", "cf_coarse_solve_noalloc",
     "cf_batch_create", "cf_batch_solve", "cf_batch_launch_count", "cf_batch_destroy",
     "cf_server_create", "cf_server_submit", "cf_server_run", "cf_server_result", "cf_server_stats",
@@ -42,7 +43,8 @@ class cf_levelset(ctypes.Structure):
 
 class cf_params(ctypes.Structure):
     _fields_ = [("gamma_D", ctypes.c_double), ("gamma_ghost", ctypes.c_double * 4), ("n_c", ctypes.c_int),
-                ("quad_q", ctypes.c_int), ("precision", ctypes.c_int)]
+                ("quad_q", ctypes.c_int), ("precision", ctypes.c_int), ("smoother", ctypes.c_int),
+                ("smoother_degree", ctypes.c_int)]
 
 
 class cf_info(ctypes.Structure):
@@ -101,6 +103,7 @@ def load():
     lib.cf_host_cell_matrix.argtypes = [P, I, ctypes.c_int64, P]
     lib.cf_host_patch_counts.argtypes = [P, I, P, P]
     lib.cf_host_interior_update.argtypes = [P, I, P]
+    lib.cf_host_diagonal.argtypes = [P, I, P]
     lib.cf_host_interior_patch.argtypes = [P, I, ctypes.c_int64, P]
     lib.cf_host_cut_patch.argtypes = [P, I, ctypes.c_int64, P, P, P, P]
     lib.cf_coarse_solve_noalloc.argtypes = [P, P, P, V]

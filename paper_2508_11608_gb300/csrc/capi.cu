@@ -121,6 +121,11 @@ static cf_status setup_impl(const cf_mesh* mesh, const cf_levelset* ls, int degr
     if (params->quad_q > 0) prm.quad_q = params->quad_q;
     if (bad_prec(params->precision)) return fail(CF_EINVAL, "bad precision");
     precision = params->precision;
+    if (params->smoother != CF_SMOOTHER_MVS && params->smoother != CF_SMOOTHER_CHEBYSHEV)
+      return fail(CF_EINVAL, "bad smoother");
+    prm.smoother = params->smoother;
+    if (params->smoother_degree < 0 || params->smoother_degree > 32) return fail(CF_EINVAL, "bad smoother degree");
+    if (params->smoother_degree > 0) prm.cheb_degree = params->smoother_degree;
   }
   prm.ls.kind = ls->kind;
   prm.ls.d = mesh->dim;
@@ -420,6 +425,7 @@ cf_status cf_batch_create(cf_problem* const* problems, int count, cf_batch** out
           const auto& prm = problems[i]->H.prm;
           if (prm.dim != dim || prm.degree != deg) continue;
           if (n_c >= 0 && prm.n_c != n_c) throw std::invalid_argument("n_c differs within a batch group");
+          if (prm.smoother != 0) throw std::invalid_argument("the batched form runs the vertex-patch smoother only");
           n_c = prm.n_c;
           inst.push_back(problems[i]->eng.get());
           idx.push_back(i);
@@ -543,6 +549,13 @@ cf_status cf_host_patch_counts(const cf_problem* pb, int level, int64_t* n_inter
   if (bad_level(pb, level) || !n_interior || !n_cut) return fail(CF_EINVAL, "bad argument");
   *n_interior = (int64_t)pb->H.levels[level].cart_vert.size();
   *n_cut = (int64_t)pb->H.levels[level].cut_vert.size();
+  return CF_OK;
+}
+
+cf_status cf_host_diagonal(const cf_problem* pb, int level, double* h_d) {
+  if (bad_level(pb, level) || !h_d || level < 1) return fail(CF_EINVAL, "bad level or null output");
+  const auto& D = pb->H.levels[level].diag;
+  std::copy(D.begin(), D.end(), h_d);
   return CF_OK;
 }
 

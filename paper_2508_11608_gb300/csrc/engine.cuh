@@ -35,6 +35,34 @@ inline void launch_check(const char* what) {
 }
 
 // owns every device allocation of a problem
+// One step of the Chebyshev smoother over a level's active box:
+// x_new = x + c1 (x - xp) + c2 D^{-1} r, then xp <- x, x <- x_new
+template <typename T>
+__global__ void __launch_bounds__(256) k_chebyshev(Region R, T* __restrict__ x, T* __restrict__ xp,
+                                                   const T* __restrict__ r, const T* __restrict__ dinv, T c1,
+                                                   T c2) {
+  const int64_t tot = R.size();
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = R.at(t);
+    const T xo = x[o];
+    x[o] = xo + c1 * (xo - xp[o]) + c2 * (dinv[o] * r[o]);
+    xp[o] = xo;
+  }
+}
+
+// w = D^{-1} v over a region (the power iteration of the Chebyshev bound)
+template <typename T>
+__global__ void __launch_bounds__(256) k_scale_diag(Region R, const T* __restrict__ dinv, const T* __restrict__ v,
+                                                    T* __restrict__ w) {
+  const int64_t tot = R.size();
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = R.at(t);
+    w[o] = dinv[o] * v[o];
+  }
+}
+
 // FP64 vector updates of the Krylov solvers (finest level, box layout)
 // y += a x over a region; a = sign * (*as) when as is given, else a = sign
 static __global__ void __launch_bounds__(256) k_axpy(Region R, const double* __restrict__ as, double sign,
@@ -152,6 +180,8 @@ class Engine final : public EngineBase {
     T* res_w;
     T* coarse_inv;
     float* dense_d;  // FP32 interior-patch map, transposed, rows padded to 4 (Wt[kc][r])
+    T* dinv = nullptr;  // Chebyshev smoother: 1 / diag(A_l) on the box (0 off the DoFs)
+    T* xp = nullptr;    // Chebyshev smoother: previous iterate
     T *x, *b, *r;          // box vectors
     T *t1, *t2, *t3, *t4;  // transfer intermediates (restriction: t1,t2; prolongation: t3,t4)
   };
@@ -196,6 +226,10 @@ class Engine final : public EngineBase {
       }
     CUTMG_CUDA(cudaMallocHost(&host_sc_, 16 * sizeof(double)));
     CUTMG_CUDA(cudaStreamCreateWithFlags(&cap_, cudaStreamNonBlocking));
+    if (H.prm.smoother == 1) {
+      lam_.assign(L, 0.0);
+      for (int l = 1; l < L; ++l) lam_[l] = power_lambda_max(l);
+    }
     const char* g = std::getenv("CUTMG_GRAPHS");
     use_graphs_ = !(g && g[0] == '0');
   }
@@ -702,6 +736,7 @@ class Engine final : public EngineBase {
  private:
   static constexpr int kVecBlocks = 1024;
   int sms_ = 152;
+  std::vector<double> lam_;        // Chebyshev smoother: lambda_max(D^{-1} A_l) estimates
   std::vector<double*> gV_, gZ_;  // GMRES basis (box vectors), allocated on first use
   double* gW_ = nullptr;
   double* gsc_ = nullptr;
@@ -834,6 +869,12 @@ class Engine final : public EngineBase {
     D.x = pool_.alloc<T>(c.nbox);
     D.b = pool_.alloc<T>(c.nbox);
     D.r = pool_.alloc<T>(c.nbox);
+    if (H_.prm.smoother == 1 && l > 0) {
+      std::vector<T> dv((size_t)c.nbox, T(0));
+      for (size_t i = 0; i < h.dofs.size(); ++i) dv[(size_t)h.dofs[i]] = (T)(1.0 / h.diag[i]);
+      D.dinv = pool_.upload<T>(dv);
+      D.xp = pool_.alloc<T>(c.nbox);
+    }
     D.t1 = D.t2 = D.t3 = D.t4 = nullptr;
     if (l > 0) {
       const int64_t nf = h.n, nc = H_.levels[l - 1].n;
@@ -1094,10 +1135,60 @@ class Engine final : public EngineBase {
     }
   }
 
+  // Chebyshev smoothing of A_l x = b (the baseline smoother of Sec. 4):
+  // point-Jacobi scaling on [lambda / 20, lambda], lambda = 1.2 lambda_max,
+  // three-term recurrence, `cheb_degree` operator applications; the same
+  // polynomial before and after the coarse correction
+  template <typename T>
+  void chebyshev(int l, Typed<T>& D, T* x, const T* b, cudaStream_t s) {
+    const Common& c = com_[l];
+    const double lmax = 1.2 * lam_[l], lmin = lmax / 20.0;
+    const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
+    double rho = 1.0 / sigma;
+    for (int k = 0; k < H_.prm.cheb_degree; ++k) {
+      apply<T>(l, D, x, b, D.r, s);  // r = b - A x
+      double c1 = 0.0, c2 = 1.0 / theta;
+      if (k > 0) {
+        const double rho_new = 1.0 / (2.0 * sigma - rho);
+        c1 = rho_new * rho;
+        c2 = 2.0 * rho_new / delta;
+        rho = rho_new;
+      }
+      k_chebyshev<T><<<kVecBlocks, 256, 0, s>>>(c.region, x, D.xp, D.r, D.dinv, (T)c1, (T)c2);
+      count_launch("chebyshev step");
+    }
+  }
+
+  // lambda_max(D^{-1} A_l) by 30 power iterations from the normalised
+  // all-ones vector (FP64): v <- w / ||w||, w = D^{-1} A v; the last ||w||
+  double power_lambda_max(int l) {
+    Typed<double>& D = d64_[l];
+    const Common& c = com_[l];
+    cudaStream_t s = 0;
+    std::vector<double> ones((size_t)c.nbox, 0.0);
+    for (int64_t i = 0; i < c.ndof; ++i) ones[(size_t)H_.levels[l].dofs[i]] = 1.0 / std::sqrt((double)c.ndof);
+    CUTMG_CUDA(cudaMemcpy(D.x, ones.data(), sizeof(double) * c.nbox, cudaMemcpyHostToDevice));
+    for (int it = 0; it < 30; ++it) {
+      apply<double>(l, D, D.x, nullptr, D.r, s);
+      k_scale_diag<double><<<kVecBlocks, 256, 0, s>>>(c.region, D.dinv, D.r, D.r);
+      dot(c.region, D.r, D.r, sc_ + 6, s);
+      k_scale_rsqrt<<<kVecBlocks, 256, 0, s>>>(c.region, sc_ + 6, D.r, D.x);
+    }
+    const double lam = std::sqrt(read_scalar(6, s));
+    CUTMG_CUDA(cudaMemsetAsync(D.x, 0, sizeof(double) * c.nbox, s));
+    CUTMG_CUDA(cudaMemsetAsync(D.r, 0, sizeof(double) * c.nbox, s));
+    CUTMG_CUDA(cudaStreamSynchronize(s));
+    return lam;
+  }
+
   // eq. "smoother-split": interior colours, then n_c sweeps of the cut
   // colours; the post-smoother runs the same steps in reverse order
   template <typename T>
   void smooth(int l, Typed<T>& D, bool post, T* x, const T* b, cudaStream_t s) {
+    if (H_.prm.smoother == 1) {
+      chebyshev<T>(l, D, x, b, s);
+      return;
+    }
     const int ncol = 1 << DIM, nc = H_.prm.n_c;
     std::vector<std::pair<int, int>> seq;
     for (int c = 0; c < ncol; ++c) seq.push_back({0, c});

@@ -918,13 +918,15 @@ void build_transfer(const RefTables& R, int Nc, HostLevel& F) {
 }
 
 // dense A_0 over the coarsest DoFs, explicit inverse
-void build_coarse(const RefTables& R, HostLevel& L) {
+// Every contribution A_l[i][j] += v of a level (active cells' element
+// matrices, then the ghost faces of each cell), in a fixed order, with i, j
+// DoF indices: the coarse matrix and the Jacobi diagonal are built from it.
+template <class Add>
+void visit_level_entries(const RefTables& R, const HostLevel& L, Add&& add) {
   const int d = L.d, p = L.p, N = L.N, n = L.n, NB = R.NB;
   const int64_t nd = (int64_t)L.dofs.size();
   std::vector<int64_t> map((size_t)ipow(n, d), -1);
   for (int64_t i = 0; i < nd; ++i) map[L.dofs[i]] = i;
-  std::vector<double>& A = L.coarse_inv;
-  A.assign((size_t)nd * nd, 0.0);
   auto node_of = [&](const int* lat) -> int64_t {
     int64_t f = 0, st = 1;
     for (int k = 0; k < d; ++k) {
@@ -961,7 +963,7 @@ void build_coarse(const RefTables& R, HostLevel& L) {
       g[j] = node_of(lat);
     }
     for (int a = 0; a < NB; ++a)
-      for (int b = 0; b < NB; ++b) A[(size_t)g[a] * nd + g[b]] += K[a * NB + b];
+      for (int b = 0; b < NB; ++b) add(g[a], g[b], K[a * NB + b]);
     for (int k = 0; k < d; ++k) {
       int uc[3] = {ci[0], ci[1], ci[2]};
       uc[k] += 1;
@@ -992,11 +994,27 @@ void build_coarse(const RefTables& R, HostLevel& L) {
           for (int q = 0; q < d - 1; ++q) tm *= L.Mhat[tt[e1 * 2 + q]][tt[e2 * 2 + q]];
           double s = 0.0;
           for (int mm = 0; mm < p; ++mm) s += L.coef[mm] * L.dvec[mm][ii[e1]] * L.dvec[mm][ii[e2]];
-          A[(size_t)gi[e1] * nd + gi[e2]] += s * tm;
+          add(gi[e1], gi[e2], s * tm);
         }
     }
   }
+  (void)nd;
+}
+
+void build_coarse(const RefTables& R, HostLevel& L) {
+  const int64_t nd = (int64_t)L.dofs.size();
+  std::vector<double>& A = L.coarse_inv;
+  A.assign((size_t)nd * nd, 0.0);
+  visit_level_entries(R, L, [&](int64_t i, int64_t j, double v) { A[(size_t)i * nd + j] += v; });
   spd_inverse((int)nd, A.data());
+}
+
+// diagonal of A_l (point-Jacobi scaling of the Chebyshev smoother)
+void build_diag(const RefTables& R, HostLevel& L) {
+  L.diag.assign(L.dofs.size(), 0.0);
+  visit_level_entries(R, L, [&](int64_t i, int64_t j, double v) {
+    if (i == j) L.diag[i] += v;
+  });
 }
 
 // b_i = (f, phi_i)_Omega + (g, gamma_D/h phi_i - d_n phi_i)_Gamma for
@@ -1121,6 +1139,7 @@ void build_hierarchy(const SetupParams& prm, Hierarchy& H) {
     throw std::invalid_argument("the coarsest level has " + std::to_string(H.levels[0].dofs.size()) +
                                 " DoFs (dense exact solve); use more levels");
   build_coarse(R, H.levels[0]);
+  for (size_t l = 1; l < H.levels.size(); ++l) build_diag(R, H.levels[l]);
   build_rhs(prm, R, H.levels.back(), H.rhs);
 }
 

@@ -21,6 +21,8 @@ struct SetupParams {
   double gamma_ghost[4] = {0.1, 0.1, 0.1, 0.1};
   int n_c = 2;
   int quad_q = 4;
+  int smoother = 0;     // 0 vertex-patch smoother, 1 Chebyshev
+  int cheb_degree = 5;
   LevelSet ls;
 };
 
@@ -76,6 +78,7 @@ struct HostLevel {
   std::vector<double> Mr, Kr;     // M x C rows of the two-cell 1D mass / stiffness
   std::vector<double> S, lam;     // fast-diagonalisation eigenvectors / values (M)
   std::vector<double> Wcart;      // (2p-1)^d x (2p+1)^d dense interior-patch update
+  std::vector<double> diag;       // diagonal of A_l per DoF (levels >= 1)
   double dvec[3][7] = {};         // ghost normal-derivative jump weights
   double coef[3] = {};            // gamma_m h^(2m-1)/(m!)^2 * h^(d-1)
   double Mhat[4][4] = {};         // reference 1D mass on [0, 1]

@@ -12,7 +12,10 @@ fine-grained comparisons.
   python -m paper_2508_11608_gb300.iteration_study ghost [cells]
       GMRES for ghost-penalty factors: gamma_1 over [0.05, 0.15] for Q1;
       Q2 / Q3 vary gamma_2 / gamma_3 with the lower factors at the best
-      value found for the lower degree"""
+      value found for the lower degree
+  python -m paper_2508_11608_gb300.iteration_study smoother [max_cells]
+      GMRES with the vertex-patch smoother against the degree-5 Chebyshev
+      smoother under refinement"""
 
 import json
 import math
@@ -23,10 +26,10 @@ import torch
 import paper_2508_11608_gb300 as cm
 
 
-def _problem(p, n, n_c=2, gammas=(0.1, 0.1, 0.1, 0.0), prec=cm.CF_FP64):
+def _problem(p, n, n_c=2, gammas=(0.1, 0.1, 0.1, 0.0), prec=cm.CF_FP64, smoother=cm.CF_SMOOTHER_MVS):
     levels = int(math.log2(n // 4)) + 1
     pb = cm.Problem(2, n, levels, p, center=[0.0, 0.0], radius=1.0, lo=-1.21, hi=1.21, n_c=n_c,
-                    gamma_ghost=tuple(gammas))
+                    gamma_ghost=tuple(gammas), smoother=smoother)
     pb.set_precision(prec)
     b = torch.zeros(pb.n_dofs(), dtype=torch.float64, device="cuda")
     pb.rhs(b)
@@ -82,6 +85,19 @@ def ghost_sweep(n):
     print(json.dumps({"mode": "ghost", "best_gammas": best}), flush=True)
 
 
+def smoother_sweep(nmax):
+    for p in (1, 2, 3):
+        n = 8
+        while n <= nmax:
+            out = {"mode": "smoother", "degree": p, "cells": n}
+            for name, sm in (("mvs", cm.CF_SMOOTHER_MVS), ("chebyshev", cm.CF_SMOOTHER_CHEBYSHEV)):
+                pb, b, _ = _problem(p, n, smoother=sm)
+                out[name], out[name + "_nfrac"] = _run(pb.solve_gmres, b)
+                pb.close()
+            print(json.dumps(out), flush=True)
+            n *= 2
+
+
 def main(argv):
     mode = argv[1] if len(argv) > 1 else "refine"
     if mode == "refine":
@@ -92,8 +108,10 @@ def main(argv):
         n_c_sweep(int(argv[2]) if len(argv) > 2 else 128)
     elif mode == "ghost":
         ghost_sweep(int(argv[2]) if len(argv) > 2 else 128)
+    elif mode == "smoother":
+        smoother_sweep(int(argv[2]) if len(argv) > 2 else 256)
     else:
-        raise SystemExit("mode: refine | nc | ghost")
+        raise SystemExit("mode: refine | nc | ghost | smoother")
     return 0
 
 

@@ -155,3 +155,11 @@ def test_interior_patch_update_is_the_exact_local_solve(pair):
             Wo[:, inner] = AIinv
             Wo[:, outer] = -AIinv @ AIB
             assert np.abs(W - Wo).max() <= 1e-10 * np.abs(Wo).max()
+
+
+def test_diagonal_matches_the_assembled_matrix(pair):
+    pb, H, k = pair
+    for l in range(1, k["L"]):
+        d = pb.host_diagonal(l)
+        do = H.levels[l].A.diagonal()
+        assert np.abs(d - do).max() <= 1e-13 * np.abs(do).max()

@@ -186,3 +186,48 @@ def test_solvers_converge_to_the_direct_solution(h2d):
         assert all(hist[i + 1] <= hist[i] * (1 + 1e-12) for i in range(len(hist) - 1))
     x3, _, _ = H.gmres(b, rtol=1e-12, restart=3)
     assert np.linalg.norm(x3 - xd) <= 1e-8 * np.linalg.norm(xd)
+
+
+@pytest.fixture(scope="module")
+def h2d_cheb():
+    return Hierarchy(Sphere([0.031, 0.017], 0.7), 2, 16, 2, 2, smoother="chebyshev")
+
+
+def test_chebyshev_smoother_is_the_scaled_chebyshev_polynomial(h2d_cheb):
+    """With b = A x*, one smoothing maps the error e = x - x* to p(D^{-1} A) e,
+    p(t) = T_k((theta - t) / delta) / T_k(theta / delta) on [lmin, lmax]: the
+    recurrence against the closed form through the eigenvectors of the
+    symmetric D^{-1/2} A D^{-1/2}."""
+    H = h2d_cheb
+    l = 1
+    L = H.levels[l]
+    A = L.A.toarray()
+    dh = np.sqrt(L.dinv)
+    lam, Q = np.linalg.eigh(dh[:, None] * A * dh[None, :])
+    lmax = H.CHEB_SAFETY * L.lam_max
+    lmin = lmax / H.CHEB_RANGE
+    theta, delta = 0.5 * (lmax + lmin), 0.5 * (lmax - lmin)
+    k = H.cheb_degree
+    Tk = np.polynomial.chebyshev.chebval
+    coef = np.zeros(k + 1)
+    coef[k] = 1.0
+    p = Tk((theta - lam) / delta, coef) / Tk(theta / delta, coef)
+    rng = np.random.default_rng(5)
+    xs = rng.standard_normal(A.shape[0])
+    x0 = rng.standard_normal(A.shape[0])
+    x1 = H.chebyshev(l, x0, A @ xs)
+    # e1 = D^{-1/2} Q diag(p) Q^T D^{1/2} e0
+    e1 = (Q @ (p * (Q.T @ ((x0 - xs) / dh)))) * dh
+    assert np.abs((x1 - xs) - e1).max() <= 1e-10 * np.abs(x0 - xs).max()
+    # the estimate sits at the top of the spectrum of D^{-1} A
+    assert L.lam_max == pytest.approx(lam.max(), rel=0.05)
+
+
+def test_chebyshev_vcycle_is_symmetric_positive_definite(h2d_cheb):
+    H = h2d_cheb
+    A = H.fine.A.toarray()
+    n = A.shape[0]
+    B = np.stack([H.vcycle(np.eye(n)[:, i]) for i in range(n)], axis=1)
+    assert np.abs(B - B.T).max() <= 1e-12 * np.abs(B).max()
+    assert np.linalg.eigvalsh(0.5 * (B + B.T)).min() > 0
+    assert np.abs(np.linalg.eigvals(np.eye(n) - B @ A)).max() < 1.0
