@@ -1035,66 +1035,88 @@ void build_rhs(const SetupParams& prm, const RefTables& R, const HostLevel& L,
   const int nq = ipow(q, d);
   CutQuadrature Q(prm.ls, q);
   const int64_t ncell = ipow(N, d);
-  std::vector<double> v(NB), gr(NB * d);
-  for (int64_t c = 0; c < ncell; ++c) {
-    uint8_t f = L.cflag[c];
-    if (!(f & kFlagActive)) continue;
-    int ci[3] = {0, 0, 0};
-    double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
-    int64_t t = c;
-    for (int k = 0; k < d; ++k) {
-      ci[k] = (int)(t % N);
-      t /= N;
-      lo[k] = prm.lo + h * ci[k];
-      hi[k] = lo[k] + h;
-    }
-    std::vector<double> loc(NB, 0.0);
-    if (!(f & kFlagCut)) {
-      for (int iq = 0; iq < nq; ++iq) {
-        double xi[3] = {0, 0, 0}, x[3] = {0, 0, 0}, w = 1.0;
-        int u = iq;
-        for (int k = 0; k < d; ++k) {
-          int a = u % q;
-          u /= q;
-          xi[k] = g.x[a];
-          w *= g.w[a];
-          x[k] = lo[k] + h * xi[k];
-        }
-        R.eval(xi, h, v.data(), gr.data());
-        double fx = d * M_PI * M_PI * uex(x) * w * std::pow(h, d);
-        for (int j = 0; j < NB; ++j) loc[j] += v[j] * fx;
-      }
-    } else {
-      CutRule rule = Q.cell(lo, hi);
-      for (const auto& nd : rule.vol) {
-        double xi[3] = {0, 0, 0};
-        for (int k = 0; k < d; ++k) xi[k] = (nd.x[k] - lo[k]) / h;
-        R.eval(xi, h, v.data(), gr.data());
-        double fx = d * M_PI * M_PI * uex(nd.x) * nd.w;
-        for (int j = 0; j < NB; ++j) loc[j] += v[j] * fx;
-      }
-      for (size_t s = 0; s < rule.surf.size(); ++s) {
-        const auto& nd = rule.surf[s];
-        double xi[3] = {0, 0, 0};
-        for (int k = 0; k < d; ++k) xi[k] = (nd.x[k] - lo[k]) / h;
-        R.eval(xi, h, v.data(), gr.data());
-        double gx = uex(nd.x) * nd.w;
-        for (int j = 0; j < NB; ++j) {
-          double dn = 0.0;
-          for (int k = 0; k < d; ++k) dn += rule.normal[s][k] * gr[j * d + k];
-          loc[j] += gx * (prm.gamma_D / h * v[j] - dn);
-        }
-      }
-    }
-    for (int j = 0; j < NB; ++j) {
-      int a[3] = {0, 0, 0};
-      R.split(j, a);
-      int64_t node = 0, st = 1;
+  std::vector<int64_t> act;
+  for (int64_t c = 0; c < ncell; ++c)
+    if (L.cflag[c] & kFlagActive) act.push_back(c);
+  // cell contributions in parallel, summed into b in cell order (the result
+  // does not depend on the thread count)
+  const int64_t nact = (int64_t)act.size(), CH = 1 << 16;
+  std::vector<double> locs((size_t)std::min<int64_t>(CH, std::max<int64_t>(nact, 1)) * NB);
+  for (int64_t c0 = 0; c0 < nact; c0 += CH) {
+    const int64_t c1 = std::min(nact, c0 + CH);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t ic = c0; ic < c1; ++ic) {
+      const int64_t c = act[ic];
+      const uint8_t f = L.cflag[c];
+      int ci[3] = {0, 0, 0};
+      double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+      int64_t t = c;
       for (int k = 0; k < d; ++k) {
-        node += (int64_t)(p * ci[k] + a[k]) * st;
-        st *= n;
+        ci[k] = (int)(t % N);
+        t /= N;
+        lo[k] = prm.lo + h * ci[k];
+        hi[k] = lo[k] + h;
       }
-      b[map[node]] += loc[j];
+      std::vector<double> v(NB), gr(NB * d);
+      double* loc = &locs[(size_t)(ic - c0) * NB];
+      for (int j = 0; j < NB; ++j) loc[j] = 0.0;
+      if (!(f & kFlagCut)) {
+        for (int iq = 0; iq < nq; ++iq) {
+          double xi[3] = {0, 0, 0}, x[3] = {0, 0, 0}, w = 1.0;
+          int u = iq;
+          for (int k = 0; k < d; ++k) {
+            int a = u % q;
+            u /= q;
+            xi[k] = g.x[a];
+            w *= g.w[a];
+            x[k] = lo[k] + h * xi[k];
+          }
+          R.eval(xi, h, v.data(), gr.data());
+          double fx = d * M_PI * M_PI * uex(x) * w * std::pow(h, d);
+          for (int j = 0; j < NB; ++j) loc[j] += v[j] * fx;
+        }
+      } else {
+        CutRule rule = Q.cell(lo, hi);
+        for (const auto& nd : rule.vol) {
+          double xi[3] = {0, 0, 0};
+          for (int k = 0; k < d; ++k) xi[k] = (nd.x[k] - lo[k]) / h;
+          R.eval(xi, h, v.data(), gr.data());
+          double fx = d * M_PI * M_PI * uex(nd.x) * nd.w;
+          for (int j = 0; j < NB; ++j) loc[j] += v[j] * fx;
+        }
+        for (size_t s2 = 0; s2 < rule.surf.size(); ++s2) {
+          const auto& nd = rule.surf[s2];
+          double xi[3] = {0, 0, 0};
+          for (int k = 0; k < d; ++k) xi[k] = (nd.x[k] - lo[k]) / h;
+          R.eval(xi, h, v.data(), gr.data());
+          double gx = uex(nd.x) * nd.w;
+          for (int j = 0; j < NB; ++j) {
+            double dn = 0.0;
+            for (int k = 0; k < d; ++k) dn += rule.normal[s2][k] * gr[j * d + k];
+            loc[j] += gx * (prm.gamma_D / h * v[j] - dn);
+          }
+        }
+      }
+    }
+    for (int64_t ic = c0; ic < c1; ++ic) {
+      const int64_t c = act[ic];
+      int ci[3] = {0, 0, 0};
+      int64_t t = c;
+      for (int k = 0; k < d; ++k) {
+        ci[k] = (int)(t % N);
+        t /= N;
+      }
+      const double* loc = &locs[(size_t)(ic - c0) * NB];
+      for (int j = 0; j < NB; ++j) {
+        int a[3] = {0, 0, 0};
+        R.split(j, a);
+        int64_t node = 0, st = 1;
+        for (int k = 0; k < d; ++k) {
+          node += (int64_t)(p * ci[k] + a[k]) * st;
+          st *= n;
+        }
+        b[map[node]] += loc[j];
+      }
     }
   }
 }
@@ -1139,7 +1161,8 @@ void build_hierarchy(const SetupParams& prm, Hierarchy& H) {
     throw std::invalid_argument("the coarsest level has " + std::to_string(H.levels[0].dofs.size()) +
                                 " DoFs (dense exact solve); use more levels");
   build_coarse(R, H.levels[0]);
-  for (size_t l = 1; l < H.levels.size(); ++l) build_diag(R, H.levels[l]);
+  if (prm.smoother == 1)
+    for (size_t l = 1; l < H.levels.size(); ++l) build_diag(R, H.levels[l]);
   build_rhs(prm, R, H.levels.back(), H.rhs);
 }
 
