@@ -1,9 +1,11 @@
 // Served form: a stream of solve requests with arrival times, solved with
 // continuous batching on one GPU.
 //
-//  * A host worker thread builds each request's hierarchy (classification,
-//    cut quadrature, cell and patch matrices) once the request has arrived,
-//    at most kLookahead requests ahead of admission.
+//  * A pool of host workers builds the requests' hierarchies (classification,
+//    cut quadrature, cell and patch matrices), each once its request has
+//    arrived, in arrival order and at most kLookahead requests ahead of
+//    admission; the workers share the host cores (one setup alone scales
+//    sublinearly with threads, so concurrent setups raise the rate).
 //  * Admission (FIFO): a prepared request enters as soon as its device
 //    footprint (estimated from the host hierarchy) fits the HBM budget next to
 //    the resident problems and an active slot is free; its hierarchy is
@@ -18,6 +20,7 @@
 // alone or in the mix (the batched kernels reuse the single-problem device
 // code and reduction partitions).
 #include <cuda_runtime.h>
+#include <omp.h>
 
 #include <algorithm>
 #include <chrono>
@@ -36,6 +39,8 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 constexpr int kLookahead = 8;
+constexpr int kMaxSetupWorkers = 4;  // host setups built concurrently
+constexpr int kThreadsPerSetup = 4;
 
 struct Request {
   int64_t id = 0;
@@ -137,15 +142,23 @@ cf_status cf_server_run(cf_server* s, void* stream) {
   const auto t0 = Clock::now();
   auto now = [&] { return std::chrono::duration<double>(Clock::now() - t0).count(); };
 
-  // host worker: hierarchies in arrival order, at most kLookahead ahead
-  std::thread worker([&] {
-    for (int i = 0; i < n; ++i) {
-      Request& r = s->reqs[i];
+  // host workers: each claims the next request in arrival order, at most
+  // kLookahead ahead of admission, and builds its hierarchy after arrival
+  const int hw = std::max(1, (int)std::thread::hardware_concurrency());
+  const int nworkers = std::max(1, std::min(kMaxSetupWorkers, hw / kThreadsPerSetup));
+  const int threads_each = std::max(1, hw / nworkers);
+  int claimed = 0;
+  auto work = [&] {
+    omp_set_num_threads(threads_each);
+    for (;;) {
+      int i;
       {
         std::unique_lock<std::mutex> lk(mu);
-        cv.wait(lk, [&] { return stop || i - admitted < kLookahead; });
-        if (stop) return;
+        cv.wait(lk, [&] { return stop || claimed >= n || claimed - admitted < kLookahead; });
+        if (stop || claimed >= n) return;
+        i = claimed++;
       }
+      Request& r = s->reqs[i];
       const double wait = r.arrival - now();
       if (wait > 0) std::this_thread::sleep_for(std::chrono::duration<double>(wait));
       cf_problem* pb = nullptr;
@@ -161,7 +174,9 @@ cf_status cf_server_run(cf_server* s, void* stream) {
       }
       cv.notify_all();
     }
-  });
+  };
+  std::vector<std::thread> workers;
+  for (int w = 0; w < nworkers; ++w) workers.emplace_back(work);
 
   cf_status result = CF_OK;
   std::vector<int> active;
@@ -319,7 +334,7 @@ cf_status cf_server_run(cf_server* s, void* stream) {
     stop = true;
     cv.notify_all();
   }
-  worker.join();
+  for (auto& w : workers) w.join();
   s->run_s = now();
   return result;
 }
