@@ -138,6 +138,17 @@ cf_status cf_stats(const cf_problem* pb, int level, int64_t* h_out6);
  * (the coarsest, solved exactly) has no colour steps and reports zeros. */
 cf_status cf_work_model(const cf_problem* pb, int level, int kind, int colour, double* h_out3);
 
+/* Finest-level right-hand side for user data (Sec. 2.1 with Nitsche data,
+ * reading 7): b_i = (f, phi_i)_Omega + (g, gamma_D/h phi_i - d_n phi_i)_Gamma,
+ * integrated with the same cut-cell rules as the operator.  f(x, user) is the
+ * source, g(x, user) the Dirichlet data on Gamma; x has 3 components (unused
+ * ones 0); a NULL function counts as zero.  The callbacks run sequentially on
+ * the calling thread during the call (host assembly), then b is copied to d_b
+ * (cf_n_dofs doubles, DoF order) on `stream` and the call waits for it.
+ * CF_EINVAL on null problem or output. */
+cf_status cf_rhs_user(cf_problem* pb, double (*f)(const double* x, void* user),
+                      double (*g)(const double* x, void* user), void* user, double* d_b, void* stream);
+
 /* Select the precision of cf_vcycle and cf_solve (CF_FP64 or CF_MIXED). */
 cf_status cf_set_precision(cf_problem* pb, int precision);
 
@@ -301,6 +312,9 @@ cf_status cf_setup_host(const cf_mesh* mesh, const cf_levelset* ls, int degree,
 cf_status cf_footprint(const cf_problem* pb, size_t* bytes);
 /* Finest-level right-hand side (host array of cf_n_dofs doubles). */
 cf_status cf_host_rhs(const cf_problem* pb, double* h_b);
+/* cf_rhs_user into a host array (works on host-only handles). */
+cf_status cf_host_rhs_user(const cf_problem* pb, double (*f)(const double* x, void* user),
+                           double (*g)(const double* x, void* user), void* user, double* h_b);
 /* Element matrix of cell `cell` (flat index c_0 + N c_1 + N^2 c_2) of a level:
  * volume + Nitsche terms for a cut cell, the uncut stiffness for an uncut
  * active cell; (p+1)^d x (p+1)^d row-major, local nodes first coordinate

@@ -115,6 +115,25 @@ class Problem:
     def rhs(self, b, stream=None):
         check(self._lib.cf_rhs(self._h, _ptr(b), _stream(stream)))
 
+    @staticmethod
+    def _data_fn(fn, dim):
+        if fn is None:
+            return ctypes.cast(None, _lib.DATA_FN)
+        return _lib.DATA_FN(lambda xp, user: float(fn(tuple(xp[k] for k in range(dim)))))
+
+    def rhs_user(self, f, g, b=None, stream=None):
+        """Right-hand side for source f(x) and Dirichlet data g(x) (Python
+        callables of a coordinate tuple; None = zero).  With a device tensor b
+        it is filled in place (cf_rhs_user); without, the host array is
+        returned (cf_host_rhs_user)."""
+        cf, cg = self._data_fn(f, self.dim), self._data_fn(g, self.dim)
+        if b is None:
+            out = np.empty(self.n_dofs(), dtype=np.float64)
+            check(self._lib.cf_host_rhs_user(self._h, cf, cg, None, out.ctypes.data_as(ctypes.c_void_p)))
+            return out
+        check(self._lib.cf_rhs_user(self._h, cf, cg, None, _ptr(b), _stream(stream)))
+        return b
+
     def apply(self, x, y, stream=None):
         check(self._lib.cf_apply(self._h, _ptr(x), _ptr(y), _stream(stream)))
 

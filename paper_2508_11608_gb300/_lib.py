@@ -19,7 +19,7 @@ CF_K_CUT_SOLVE, CF_K_INTERIOR, CF_K_APPLY_BULK, CF_K_APPLY_BND, CF_K_FACE_MOMENT
 EXPORTED = [
     "cf_setup", "cf_destroy", "cf_last_error", "cf_n_levels", "cf_n_dofs", "cf_level_n_dofs",
     "cf_dof_lattice", "cf_dof_coords", "cf_stats", "cf_work_model", "cf_footprint", "cf_set_precision", "cf_rhs", "cf_apply",
-    "cf_vcycle", "cf_solve", "cf_solve_vcycle", "cf_solve_gmres", "cf_level_apply", "cf_level_colour_step", "cf_level_smooth",
+    "cf_vcycle", "cf_solve", "cf_solve_vcycle", "cf_solve_gmres", "cf_rhs_user", "cf_host_rhs_user", "cf_level_apply", "cf_level_colour_step", "cf_level_smooth",
     "cf_level_restrict", "cf_level_prolongate", "cf_coarse_solve", "cf_setup_host", "cf_host_rhs",
     "cf_host_cell_matrix", "cf_host_patch_counts", "cf_host_interior_update", "cf_host_diagonal", "cf_host_interior_patch", "cf_host_cut_patch",
     "cf_launch_count", "cf_profile_start", "cf_profile_read", "cf_coarse_solve_noalloc",
@@ -45,6 +45,10 @@ class cf_params(ctypes.Structure):
     _fields_ = [("gamma_D", ctypes.c_double), ("gamma_ghost", ctypes.c_double * 4), ("n_c", ctypes.c_int),
                 ("quad_q", ctypes.c_int), ("precision", ctypes.c_int), ("smoother", ctypes.c_int),
                 ("smoother_degree", ctypes.c_int)]
+
+
+# double f(const double* x, void* user)
+DATA_FN = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p)
 
 
 class cf_info(ctypes.Structure):
@@ -91,6 +95,8 @@ def load():
     lib.cf_vcycle.argtypes = [P, P, P, V]
     lib.cf_solve.argtypes = [P, P, P, D, I, ctypes.POINTER(cf_info), V]
     lib.cf_solve_vcycle.argtypes = [P, P, P, D, I, ctypes.POINTER(cf_info), V]
+    lib.cf_rhs_user.argtypes = [P, DATA_FN, DATA_FN, V, P, V]
+    lib.cf_host_rhs_user.argtypes = [P, DATA_FN, DATA_FN, V, P]
     lib.cf_solve_gmres.argtypes = [P, P, P, D, I, I, ctypes.POINTER(cf_info), V]
     lib.cf_level_apply.argtypes = [P, I, I, P, P, V]
     lib.cf_level_colour_step.argtypes = [P, I, I, I, I, P, P, V]

@@ -269,6 +269,28 @@ cf_status cf_work_model(const cf_problem* pb, int level, int kind, int colour, d
   return CF_OK;
 }
 
+cf_status cf_host_rhs_user(const cf_problem* pb, double (*f)(const double*, void*),
+                           double (*g)(const double*, void*), void* user, double* h_b) {
+  if (!pb || !h_b) return fail(CF_EINVAL, "null argument");
+  return guarded([&] {
+    std::vector<double> b;
+    build_rhs_user(pb->H, f, g, user, b);
+    std::copy(b.begin(), b.end(), h_b);
+  });
+}
+
+cf_status cf_rhs_user(cf_problem* pb, double (*f)(const double*, void*), double (*g)(const double*, void*),
+                      void* user, double* d_b, void* stream) {
+  if (no_device(pb) || !d_b) return fail(CF_EINVAL, "null argument");
+  return guarded([&] {
+    std::vector<double> b;
+    build_rhs_user(pb->H, f, g, user, b);
+    cudaStream_t st = S(stream);
+    CUTMG_CHECK(cudaMemcpyAsync(d_b, b.data(), sizeof(double) * b.size(), cudaMemcpyHostToDevice, st));
+    CUTMG_CHECK(cudaStreamSynchronize(st));
+  });
+}
+
 cf_status cf_set_precision(cf_problem* pb, int precision) {
   if (!pb || bad_prec(precision)) return fail(CF_EINVAL, "bad precision");
   pb->precision = precision;

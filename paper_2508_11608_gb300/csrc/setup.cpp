@@ -13,6 +13,8 @@
 // diagonalisation, all others an explicit FP64 inverse of A[I_j, I_j].
 #include "setup.hpp"
 
+#include <functional>
+
 #include <cmath>
 #include <cstring>
 #include <stdexcept>
@@ -1019,18 +1021,14 @@ void build_diag(const RefTables& R, HostLevel& L) {
 
 // b_i = (f, phi_i)_Omega + (g, gamma_D/h phi_i - d_n phi_i)_Gamma for
 // u = prod sin(pi x_k), f = d pi^2 u, g = u
-void build_rhs(const SetupParams& prm, const RefTables& R, const HostLevel& L,
-               std::vector<double>& b) {
+void build_rhs(const SetupParams& prm, const RefTables& R, const HostLevel& L, std::vector<double>& b,
+               const std::function<double(const double*)>& fsrc, const std::function<double(const double*)>& gdir,
+               bool parallel) {
   const int d = L.d, p = L.p, N = L.N, n = L.n, NB = R.NB, q = prm.quad_q;
   const double h = L.h;
   std::vector<int64_t> map((size_t)ipow(n, d), -1);
   for (size_t i = 0; i < L.dofs.size(); ++i) map[L.dofs[i]] = (int64_t)i;
   b.assign(L.dofs.size(), 0.0);
-  auto uex = [&](const double* x) {
-    double u = 1.0;
-    for (int k = 0; k < d; ++k) u *= std::sin(M_PI * x[k]);
-    return u;
-  };
   GaussRule g = gauss_legendre01(q);
   const int nq = ipow(q, d);
   CutQuadrature Q(prm.ls, q);
@@ -1044,7 +1042,7 @@ void build_rhs(const SetupParams& prm, const RefTables& R, const HostLevel& L,
   std::vector<double> locs((size_t)std::min<int64_t>(CH, std::max<int64_t>(nact, 1)) * NB);
   for (int64_t c0 = 0; c0 < nact; c0 += CH) {
     const int64_t c1 = std::min(nact, c0 + CH);
-#pragma omp parallel for schedule(dynamic, 64)
+#pragma omp parallel for schedule(dynamic, 64) if (parallel)
     for (int64_t ic = c0; ic < c1; ++ic) {
       const int64_t c = act[ic];
       const uint8_t f = L.cflag[c];
@@ -1072,7 +1070,7 @@ void build_rhs(const SetupParams& prm, const RefTables& R, const HostLevel& L,
             x[k] = lo[k] + h * xi[k];
           }
           R.eval(xi, h, v.data(), gr.data());
-          double fx = d * M_PI * M_PI * uex(x) * w * std::pow(h, d);
+          double fx = fsrc(x) * w * std::pow(h, d);
           for (int j = 0; j < NB; ++j) loc[j] += v[j] * fx;
         }
       } else {
@@ -1081,7 +1079,7 @@ void build_rhs(const SetupParams& prm, const RefTables& R, const HostLevel& L,
           double xi[3] = {0, 0, 0};
           for (int k = 0; k < d; ++k) xi[k] = (nd.x[k] - lo[k]) / h;
           R.eval(xi, h, v.data(), gr.data());
-          double fx = d * M_PI * M_PI * uex(nd.x) * nd.w;
+          double fx = fsrc(nd.x) * nd.w;
           for (int j = 0; j < NB; ++j) loc[j] += v[j] * fx;
         }
         for (size_t s2 = 0; s2 < rule.surf.size(); ++s2) {
@@ -1089,7 +1087,7 @@ void build_rhs(const SetupParams& prm, const RefTables& R, const HostLevel& L,
           double xi[3] = {0, 0, 0};
           for (int k = 0; k < d; ++k) xi[k] = (nd.x[k] - lo[k]) / h;
           R.eval(xi, h, v.data(), gr.data());
-          double gx = uex(nd.x) * nd.w;
+          double gx = gdir(nd.x) * nd.w;
           for (int j = 0; j < NB; ++j) {
             double dn = 0.0;
             for (int k = 0; k < d; ++k) dn += rule.normal[s2][k] * gr[j * d + k];
@@ -1163,7 +1161,29 @@ void build_hierarchy(const SetupParams& prm, Hierarchy& H) {
   build_coarse(R, H.levels[0]);
   if (prm.smoother == 1)
     for (size_t l = 1; l < H.levels.size(); ++l) build_diag(R, H.levels[l]);
-  build_rhs(prm, R, H.levels.back(), H.rhs);
+  // manufactured data of the workloads: u = prod sin(pi x_k), f = d pi^2 u, g = u
+  const int d = prm.dim;
+  auto uex = [d](const double* x) {
+    double u = 1.0;
+    for (int k = 0; k < d; ++k) u *= std::sin(M_PI * x[k]);
+    return u;
+  };
+  build_rhs(prm, R, H.levels.back(), H.rhs, [&](const double* x) { return d * M_PI * M_PI * uex(x); }, uex,
+            true);
+}
+
+void build_rhs_user(const Hierarchy& H, double (*f)(const double*, void*), double (*g)(const double*, void*),
+                    void* user, std::vector<double>& b) {
+  RefTables R(H.prm.degree, H.prm.dim);
+  const int d = H.prm.dim;
+  auto wrap = [d, user](double (*fn)(const double*, void*)) {
+    return [d, user, fn](const double* x) {
+      if (!fn) return 0.0;
+      double y[3] = {x[0], d > 1 ? x[1] : 0.0, d > 2 ? x[2] : 0.0};
+      return fn(y, user);
+    };
+  };
+  build_rhs(H.prm, R, H.levels.back(), b, wrap(f), wrap(g), false);
 }
 
 }  // namespace cutmg

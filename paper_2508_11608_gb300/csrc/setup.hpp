@@ -100,4 +100,10 @@ struct Hierarchy {
 // Builds the hierarchy.  Throws std::runtime_error with a message on error.
 void build_hierarchy(const SetupParams& prm, Hierarchy& H);
 
+// finest-level right-hand side b_i = (f, phi_i)_Omega + (g, gamma_D/h phi_i
+// - d_n phi_i)_Gamma for user data (f, g called sequentially on the calling
+// thread with a 3-component point; a null function is zero)
+void build_rhs_user(const Hierarchy& H, double (*f)(const double*, void*), double (*g)(const double*, void*),
+                    void* user, std::vector<double>& b);
+
 }  // namespace cutmg
