@@ -51,7 +51,8 @@ typedef enum {
   CF_LS_PLANE = 1,     /* phi = normal . x - offset (half space; used in tests)            */
   CF_LS_ELLIPSOID = 2, /* phi = sqrt(sum (y_i / axes_i)^2) - 1 (3D)                         */
   CF_LS_TORUS = 3,     /* phi = sqrt((sqrt(y_0^2 + y_1^2) - major)^2 + y_2^2) - radius (3D) */
-  CF_LS_FLOWER = 4     /* phi = |x - c| - (radius + amplitude cos(lobes (theta - phase))) (2D) */
+  CF_LS_FLOWER = 4,    /* phi = |x - c| - (radius + amplitude cos(lobes (theta - phase))) (2D) */
+  CF_LS_CALLBACK = 5   /* phi and its gradient from the user's callbacks (see cf_levelset)  */
 } cf_levelset_kind;
 
 typedef enum { CF_FP64 = 0, CF_MIXED = 1 } cf_precision;
@@ -79,6 +80,22 @@ typedef struct {
   int lobes;         /* flower: number of lobes */
   double amplitude;  /* flower: radius amplitude */
   double phase;      /* flower: rotation angle theta_0 */
+  /* CF_LS_CALLBACK: phi(x, user) and grad(x, g, user) = d phi / dx; x and g
+   * have 3 components (unused ones 0).  Known only at points, the level set
+   * is bounded on a cell or face from a 5-point-per-direction lattice of
+   * samples widened by the largest sampled |grad phi| times the distance to
+   * the nearest sample (an exact enclosure when that bounds |grad phi|, e.g.
+   * for signed distances); the quadrature's monotonicity test samples the
+   * gradient the same way.  Both must be pure functions of x, callable
+   * concurrently from several host threads (see cf_params.setup_threads).
+   * They are called during cf_setup / cf_setup_host, during cf_rhs_user /
+   * cf_host_rhs_user (which integrate the cut cells again), and during
+   * cf_server_run for a served request; they and `user` must stay valid
+   * until the handle is destroyed (the server: until cf_server_run returns).
+   * Ignored for the other kinds. */
+  double (*phi)(const double* x, void* user);
+  void (*grad)(const double* x, double* g, void* user);
+  void* user;
 } cf_levelset;
 
 /* Method parameters.  Zero / negative entries select the defaults given. */
@@ -90,6 +107,8 @@ typedef struct {
   int precision;         /* cf_precision of cf_vcycle / cf_solve; default CF_FP64 */
   int smoother;          /* cf_smoother: CF_SMOOTHER_MVS (default) or CF_SMOOTHER_CHEBYSHEV */
   int smoother_degree;   /* degree of the Chebyshev smoother (Sec. 4 compares degree 5); default 5 */
+  int setup_threads;     /* host threads of the setup (OpenMP); default: the OpenMP default.  One
+                            suits level-set callbacks that serialise (an interpreter's lock) */
 } cf_params;
 
 /* Smoother of the V-cycle.  MVS: the multiplicative vertex-patch smoother

@@ -13,6 +13,9 @@ Each level set provides
                          True when d phi / d x_k provably keeps one strict sign
                          on the box (monotonicity test of the cut quadrature)
 
+A user level set given by point callbacks (Callback) has sampled bounds
+instead; its docstring states them.
+
 Interval enclosures use plain floating point (no outward rounding); the
 library's setup evaluates the same expressions in the same order.
 """
@@ -398,9 +401,88 @@ class Flower:
         return bool(v[0] > 0.0 or v[1] < 0.0)
 
 
+SAMPLE_INTERVALS = 4
+
+
+class Callback:
+    """A user level set known only through point values phi(X) and gradients
+    grad(X) (vectorised callables over X of shape (..., d)).  The paper's
+    examples are closed forms; for these no enclosure exists, so both bounds
+    come from samples (a reading of the classification and the quadrature's
+    monotonicity test for point-only level sets):
+
+    * samples: the lattice of SAMPLE_INTERVALS + 1 points per free direction
+      of the box, x_k = lo_k + (hi_k - lo_k) i / SAMPLE_INTERVALS (one point
+      in a degenerate direction);
+    * delta = half the diagonal of one lattice cell: every box point lies
+      within delta of a sample;
+    * box_minmax = (min phi - L delta, max phi + L delta), L the largest
+      sampled |grad phi| (an exact enclosure when L bounds |grad phi| on the
+      box, e.g. for distance functions, where L = 1);
+    * grad_sign_const(k): every sampled d phi/d x_k has one strict sign and
+      its smallest magnitude exceeds C_k delta, C_k the largest difference
+      quotient of d phi/d x_k between neighbouring samples."""
+
+    kind = "callback"
+
+    def __init__(self, phi, grad, d):
+        self._phi = phi
+        self._grad = grad
+        self.d = int(d)
+
+    def phi(self, X):
+        return np.asarray(self._phi(np.asarray(X, dtype=np.float64)), dtype=np.float64)
+
+    def grad(self, X):
+        return np.asarray(self._grad(np.asarray(X, dtype=np.float64)), dtype=np.float64)
+
+    def _samples(self, lo, hi):
+        d = len(lo)
+        cnt = [SAMPLE_INTERVALS + 1 if hi[k] > lo[k] else 1 for k in range(d)]
+        axes = [np.array([lo[k] + (hi[k] - lo[k]) * i / SAMPLE_INTERVALS for i in range(cnt[k])])
+                for k in range(d)]
+        # lexicographic with the first direction fastest
+        grids = np.meshgrid(*axes, indexing="ij")
+        X = np.stack([g.transpose(tuple(range(d))[::-1]).ravel() for g in grids], axis=-1)
+        s = 0.0
+        for k in range(d):
+            t = (hi[k] - lo[k]) / SAMPLE_INTERVALS
+            s = t * t if k == 0 else s + t * t
+        delta = 0.5 * math.sqrt(s)
+        return X, cnt, delta
+
+    def box_minmax(self, lo, hi):
+        X, _, delta = self._samples(lo, hi)
+        v = self.phi(X)
+        G = self.grad(X)
+        nrm = G[:, 0] * G[:, 0]
+        for k in range(1, G.shape[1]):
+            nrm = nrm + G[:, k] * G[:, k]
+        lip = float(np.sqrt(nrm).max())
+        return float(v.min()) - lip * delta, float(v.max()) + lip * delta
+
+    def grad_sign_const(self, k, lo, hi):
+        X, cnt, delta = self._samples(lo, hi)
+        gk = self.grad(X)[:, k]
+        if not (np.all(gk > 0.0) or np.all(gk < 0.0)):
+            return False
+        d = len(lo)
+        A = gk.reshape(tuple(cnt[::-1]))  # axis d-1-j is direction j
+        curv = 0.0
+        for j in range(d):
+            if cnt[j] == 1:
+                continue
+            step = (hi[j] - lo[j]) / SAMPLE_INTERVALS
+            diff = np.abs(np.diff(A, axis=d - 1 - j)) / step
+            curv = max(curv, float(diff.max()))
+        return bool(float(np.abs(gk).min()) > curv * delta)
+
+
 def make_levelset(spec):
     """Build a level set from a plain dict (kind and its parameters)."""
     kind = spec["kind"]
+    if kind == "callback":
+        return Callback(spec["phi"], spec["grad"], spec["dim"])
     if kind == "sphere":
         return Sphere(spec["center"], spec["radius"])
     if kind == "plane":

@@ -28,7 +28,7 @@ class Problem:
 
     def __init__(self, dim, n_cells, n_levels, degree, center=None, radius=None, plane=None,
                  levelset=None, lo=-1.0, hi=1.0, gamma_D=0.0, gamma_ghost=(0.0,) * 4, n_c=0,
-                 quad_q=0, precision=CF_FP64, host_only=False, smoother=0, smoother_degree=0):
+                 quad_q=0, precision=CF_FP64, host_only=False, smoother=0, smoother_degree=0, setup_threads=None):
         lib = _lib.load()
         self._lib = lib
         mesh = _lib.cf_mesh(dim, n_cells, lo, hi, n_levels)
@@ -39,6 +39,7 @@ class Problem:
         else:
             spec = {"kind": "sphere", "center": center, "radius": radius}
         ls = _lib.make_levelset(spec)
+        self._ls = ls  # level-set callbacks are called again by rhs_user
         prm = _lib.cf_params()
         prm.gamma_D = gamma_D
         for k, v in enumerate(gamma_ghost):
@@ -48,6 +49,9 @@ class Problem:
         prm.precision = precision
         prm.smoother = smoother
         prm.smoother_degree = smoother_degree
+        if setup_threads is None:  # Python callbacks serialise on the interpreter lock
+            setup_threads = 1 if spec.get("kind") == "callback" else 0
+        prm.setup_threads = setup_threads
         h = ctypes.c_void_p()
         setup = lib.cf_setup_host if host_only else lib.cf_setup
         check(setup(ctypes.byref(mesh), ctypes.byref(ls), degree, ctypes.byref(prm), ctypes.byref(h)))
@@ -313,6 +317,7 @@ class Server:
         self._h = h
         self.keep = keep_solutions
         self.ndofs = []
+        self._levelsets = []
 
     def close(self):
         if getattr(self, "_h", None):
@@ -329,6 +334,7 @@ class Server:
                lo=-1.0, hi=1.0):
         mesh = _lib.cf_mesh(dim, n_cells, lo, hi, n_levels)
         ls = _lib.make_levelset(levelset)
+        self._levelsets.append(ls)  # callbacks run during run()
         prm = _lib.cf_params()
         rid = ctypes.c_int64()
         check(self._lib.cf_server_submit(self._h, ctypes.byref(mesh), ctypes.byref(ls), degree,

@@ -11,7 +11,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libcutmg.so")
 
 CF_OK, CF_EINVAL, CF_ENOMEM, CF_ECUDA, CF_ENOCONV, CF_ETIMEOUT, CF_EUNSUPPORTED = range(7)
-CF_LS_SPHERE, CF_LS_PLANE, CF_LS_ELLIPSOID, CF_LS_TORUS, CF_LS_FLOWER = 0, 1, 2, 3, 4
+CF_LS_SPHERE, CF_LS_PLANE, CF_LS_ELLIPSOID, CF_LS_TORUS, CF_LS_FLOWER, CF_LS_CALLBACK = 0, 1, 2, 3, 4, 5
 CF_FP64, CF_MIXED = 0, 1
 CF_SMOOTHER_MVS, CF_SMOOTHER_CHEBYSHEV = 0, 1
 CF_K_CUT_SOLVE, CF_K_INTERIOR, CF_K_APPLY_BULK, CF_K_APPLY_BND, CF_K_FACE_MOMENTS = 1, 2, 3, 4, 5
@@ -34,17 +34,23 @@ class cf_mesh(ctypes.Structure):
                 ("hi", ctypes.c_double), ("n_levels", ctypes.c_int)]
 
 
+# double phi(const double* x, void* user); void grad(const double* x, double* g, void* user)
+PHI_FN = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p)
+GRAD_FN = ctypes.CFUNCTYPE(None, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), ctypes.c_void_p)
+
+
 class cf_levelset(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("center", ctypes.c_double * 3), ("radius", ctypes.c_double),
                 ("normal", ctypes.c_double * 3), ("offset", ctypes.c_double),
                 ("axes", ctypes.c_double * 3), ("rot", ctypes.c_double * 9), ("major", ctypes.c_double),
-                ("lobes", ctypes.c_int), ("amplitude", ctypes.c_double), ("phase", ctypes.c_double)]
+                ("lobes", ctypes.c_int), ("amplitude", ctypes.c_double), ("phase", ctypes.c_double),
+                ("phi", PHI_FN), ("grad", GRAD_FN), ("user", ctypes.c_void_p)]
 
 
 class cf_params(ctypes.Structure):
     _fields_ = [("gamma_D", ctypes.c_double), ("gamma_ghost", ctypes.c_double * 4), ("n_c", ctypes.c_int),
                 ("quad_q", ctypes.c_int), ("precision", ctypes.c_int), ("smoother", ctypes.c_int),
-                ("smoother_degree", ctypes.c_int)]
+                ("smoother_degree", ctypes.c_int), ("setup_threads", ctypes.c_int)]
 
 
 # double f(const double* x, void* user)
@@ -146,11 +152,15 @@ def make_levelset(spec):
     """cf_levelset from a plain dict: {"kind": "sphere", "center", "radius"},
     {"kind": "plane", "normal", "offset"}, {"kind": "ellipsoid", "center",
     "axes", "rot"}, {"kind": "torus", "center", "rot", "major", "minor"},
-    {"kind": "flower", "center", "lobes", "phase", "base", "amplitude"}."""
+    {"kind": "flower", "center", "lobes", "phase", "base", "amplitude"},
+    {"kind": "callback", "dim", "phi", "grad"} with phi(X) -> values and
+    grad(X) -> gradients, vectorised over X of shape (..., dim) (the library
+    calls them one point at a time; the returned structure keeps the C
+    trampolines alive)."""
     ls = cf_levelset()
     kind = spec["kind"]
     kinds = {"sphere": CF_LS_SPHERE, "plane": CF_LS_PLANE, "ellipsoid": CF_LS_ELLIPSOID,
-             "torus": CF_LS_TORUS, "flower": CF_LS_FLOWER}
+             "torus": CF_LS_TORUS, "flower": CF_LS_FLOWER, "callback": CF_LS_CALLBACK}
     ls.kind = kinds[kind]
     for k, v in enumerate(spec.get("center", [])):
         ls.center[k] = v
@@ -175,4 +185,18 @@ def make_levelset(spec):
         ls.phase = spec["phase"]
         ls.radius = spec.get("base", 0.6)
         ls.amplitude = spec.get("amplitude", 0.1)
+    elif kind == "callback":
+        import numpy as np
+        d, fphi, fgrad = int(spec["dim"]), spec["phi"], spec["grad"]
+
+        def phi_c(x, user):
+            return float(fphi(np.array([x[k] for k in range(d)])))
+
+        def grad_c(x, g, user):
+            gv = fgrad(np.array([x[k] for k in range(d)]))
+            for k in range(d):
+                g[k] = float(gv[k])
+
+        ls.phi, ls.grad = PHI_FN(phi_c), GRAD_FN(grad_c)
+        ls._keep = (ls.phi, ls.grad)
     return ls

@@ -1,7 +1,9 @@
 // C ABI of the library (include/cutmg.h): argument checking, error
 // translation, dispatch to the (dim, degree)-specialised engines.
 #include <cuda_runtime.h>
+#include <omp.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <memory>
@@ -91,7 +93,9 @@ static cf_status setup_impl(const cf_mesh* mesh, const cf_levelset* ls, int degr
   if (degree < 1 || degree > 3) return fail(CF_EINVAL, "degree must be 1, 2 or 3");
   if (mesh->dim == 3 && degree > 2) return fail(CF_EUNSUPPORTED, "dim 3 supports degree 1 and 2");
   if (mesh->n_cells < 1 || mesh->n_levels < 1) return fail(CF_EINVAL, "n_cells and n_levels must be positive");
-  if (ls->kind < CF_LS_SPHERE || ls->kind > CF_LS_FLOWER) return fail(CF_EINVAL, "unknown level-set kind");
+  if (ls->kind < CF_LS_SPHERE || ls->kind > CF_LS_CALLBACK) return fail(CF_EINVAL, "unknown level-set kind");
+  if (ls->kind == CF_LS_CALLBACK && (!ls->phi || !ls->grad))
+    return fail(CF_EINVAL, "a callback level set needs phi and grad");
   if (ls->kind == CF_LS_SPHERE && !(ls->radius > 0.0)) return fail(CF_EINVAL, "radius must be positive");
   if ((ls->kind == CF_LS_ELLIPSOID || ls->kind == CF_LS_TORUS) && mesh->dim != 3)
     return fail(CF_EINVAL, "ellipsoid and torus level sets are three-dimensional");
@@ -126,7 +130,9 @@ static cf_status setup_impl(const cf_mesh* mesh, const cf_levelset* ls, int degr
     prm.smoother = params->smoother;
     if (params->smoother_degree < 0 || params->smoother_degree > 32) return fail(CF_EINVAL, "bad smoother degree");
     if (params->smoother_degree > 0) prm.cheb_degree = params->smoother_degree;
+    if (params->setup_threads < 0) return fail(CF_EINVAL, "bad setup thread count");
   }
+  const int threads = params ? params->setup_threads : 0;
   prm.ls.kind = ls->kind;
   prm.ls.d = mesh->dim;
   for (int k = 0; k < 3; ++k) {
@@ -142,8 +148,22 @@ static cf_status setup_impl(const cf_mesh* mesh, const cf_levelset* ls, int degr
   prm.ls.lobes = ls->lobes;
   prm.ls.amp = ls->amplitude;
   prm.ls.phase = ls->phase;
+  if (ls->kind == CF_LS_CALLBACK) {
+    prm.ls.uphi = ls->phi;
+    prm.ls.ugrad = ls->grad;
+    prm.ls.user = ls->user;
+    static std::atomic<uint64_t> epochs{0};
+    prm.ls.epoch = ++epochs;
+  }
   std::unique_ptr<cf_problem> pb;
   cf_status st = guarded([&] {
+    struct ThreadCount {  // the calling thread's OpenMP team size, restored on exit
+      int saved;
+      explicit ThreadCount(int n) : saved(omp_get_max_threads()) {
+        if (n > 0) omp_set_num_threads(n);
+      }
+      ~ThreadCount() { omp_set_num_threads(saved); }
+    } tc(threads);
     pb.reset(new cf_problem());
     build_hierarchy(prm, pb->H);
     if (device) {

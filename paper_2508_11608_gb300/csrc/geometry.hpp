@@ -164,8 +164,20 @@ inline Iv iv_sin(Iv a) { return iv_cos(Iv{a.lo - 0.5 * M_PI, a.hi - 0.5 * M_PI})
 // nested classifications).
 constexpr int kBoxDepth = 2;
 
+// A user level set is known only through point values and gradients, so its
+// bounds on a box come from samples: the lattice of kSampleIntervals + 1
+// points per free direction (one in a degenerate direction).  Every box point
+// lies within delta (half the diagonal of a lattice cell) of a sample, so
+//   [min phi - L delta, max phi + L delta], L = largest sampled |grad phi|,
+// encloses phi whenever L bounds |grad phi| on the box (distance functions:
+// L = 1).  d phi / d x_k counts as one-signed when every sample has the same
+// strict sign and the smallest |d phi / d x_k| exceeds C delta, C the largest
+// difference quotient of d phi / d x_k between neighbouring samples.
+constexpr int kSampleIntervals = 4;
+constexpr int kMaxSamples = (kSampleIntervals + 1) * (kSampleIntervals + 1) * (kSampleIntervals + 1);
+
 struct LevelSet {
-  enum Kind { kSphere = 0, kPlane = 1, kEllipsoid = 2, kTorus = 3, kFlower = 4 };
+  enum Kind { kSphere = 0, kPlane = 1, kEllipsoid = 2, kTorus = 3, kFlower = 4, kCallback = 5 };
   int kind = kSphere;
   int d = 3;
   double c[3] = {0, 0, 0};
@@ -177,6 +189,115 @@ struct LevelSet {
   double major = 0;             // torus major radius
   int lobes = 0;                // flower
   double amp = 0, phase = 0;    // flower
+  double (*uphi)(const double*, void*) = nullptr;          // user level set: value at a 3-component point
+  void (*ugrad)(const double*, double*, void*) = nullptr;  // user level set: gradient (3 components)
+  void* user = nullptr;
+  uint64_t epoch = 0;  // user level set: unique per setup, keys the per-thread sample cache
+
+  double user_phi(const double* x) const {
+    double p[3] = {x[0], d > 1 ? x[1] : 0.0, d > 2 ? x[2] : 0.0};
+    return uphi(p, user);
+  }
+  void user_grad(const double* x, double* g) const {
+    double p[3] = {x[0], d > 1 ? x[1] : 0.0, d > 2 ? x[2] : 0.0}, q[3] = {0.0, 0.0, 0.0};
+    ugrad(p, q, user);
+    for (int k = 0; k < d; ++k) g[k] = q[k];
+  }
+
+  struct Samples {
+    int cnt[3] = {1, 1, 1};
+    int n = 0;
+    double delta = 0.0;
+    double v[kMaxSamples];
+    double g[kMaxSamples][3];
+  };
+  // samples in lexicographic order, the first direction fastest
+  void sample_box(const double* lo, const double* hi, Samples& S) const {
+    for (int k = 0; k < d; ++k) S.cnt[k] = hi[k] > lo[k] ? kSampleIntervals + 1 : 1;
+    S.n = S.cnt[0] * S.cnt[1] * S.cnt[2];
+    for (int i = 0; i < S.n; ++i) {
+      int t = i, ik[3];
+      for (int k = 0; k < 3; ++k) {
+        ik[k] = t % S.cnt[k];
+        t /= S.cnt[k];
+      }
+      double x[3] = {0.0, 0.0, 0.0};
+      for (int k = 0; k < d; ++k) x[k] = lo[k] + (hi[k] - lo[k]) * ik[k] / kSampleIntervals;
+      S.v[i] = user_phi(x);
+      user_grad(x, S.g[i]);
+    }
+    double s = 0.0;
+    for (int k = 0; k < d; ++k) {
+      double t = (hi[k] - lo[k]) / kSampleIntervals;
+      s = (k == 0) ? t * t : s + t * t;
+    }
+    S.delta = 0.5 * std::sqrt(s);
+  }
+  // The quadrature bounds a box and then tests each direction on it: keep
+  // the last few boxes' samples per thread.
+  const Samples& samples(const double* lo, const double* hi) const {
+    constexpr int kSlots = 8;
+    struct Slot {
+      uint64_t epoch = 0;
+      double lo[3], hi[3];
+      Samples S;
+    };
+    thread_local Slot slot[kSlots];
+    thread_local int next = 0;
+    for (int i = 0; i < kSlots; ++i) {
+      Slot& e = slot[i];
+      bool same = e.epoch == epoch;
+      for (int k = 0; same && k < d; ++k) same = e.lo[k] == lo[k] && e.hi[k] == hi[k];
+      if (same) return e.S;
+    }
+    Slot& e = slot[next];
+    next = (next + 1) % kSlots;
+    e.epoch = 0;
+    sample_box(lo, hi, e.S);
+    for (int k = 0; k < d; ++k) {
+      e.lo[k] = lo[k];
+      e.hi[k] = hi[k];
+    }
+    e.epoch = epoch;
+    return e.S;
+  }
+  void sampled_minmax(const double* lo, const double* hi, double& mn, double& mx) const {
+    const Samples& S = samples(lo, hi);
+    double vmin = S.v[0], vmax = S.v[0], lip = 0.0;
+    for (int i = 0; i < S.n; ++i) {
+      vmin = std::min(vmin, S.v[i]);
+      vmax = std::max(vmax, S.v[i]);
+      double q = S.g[i][0] * S.g[i][0];
+      for (int k = 1; k < d; ++k) q = q + S.g[i][k] * S.g[i][k];
+      lip = std::max(lip, std::sqrt(q));
+    }
+    mn = vmin - lip * S.delta;
+    mx = vmax + lip * S.delta;
+  }
+  bool sampled_monotone(int k, const double* lo, const double* hi) const {
+    const Samples& S = samples(lo, hi);
+    bool pos = true, neg = true;
+    double gmin = 1e300;
+    for (int i = 0; i < S.n; ++i) {
+      const double gk = S.g[i][k];
+      if (!(gk > 0.0)) pos = false;
+      if (!(gk < 0.0)) neg = false;
+      gmin = std::min(gmin, std::fabs(gk));
+    }
+    if (!pos && !neg) return false;
+    double curv = 0.0;
+    int stride = 1;
+    for (int j = 0; j < d; ++j) {
+      if (S.cnt[j] > 1) {
+        const double step = (hi[j] - lo[j]) / kSampleIntervals;
+        for (int i = 0; i < S.n; ++i)
+          if ((i / stride) % S.cnt[j] < S.cnt[j] - 1)
+            curv = std::max(curv, std::fabs(S.g[i + stride][k] - S.g[i][k]) / step);
+      }
+      stride *= S.cnt[j];
+    }
+    return gmin > curv * S.delta;
+  }
 
   // body coordinates y = R (x - c)
   void body(const double* x, double* y) const {
@@ -186,6 +307,7 @@ struct LevelSet {
 
   double phi(const double* x) const {
     switch (kind) {
+      case kCallback: return user_phi(x);
       case kSphere: {
         double s = 0.0;
         for (int k = 0; k < d; ++k) {
@@ -226,6 +348,7 @@ struct LevelSet {
 
   void grad(const double* x, double* g) const {
     switch (kind) {
+      case kCallback: user_grad(x, g); return;
       case kSphere: {
         double s = 0.0;
         for (int k = 0; k < d; ++k) {
@@ -390,12 +513,17 @@ struct LevelSet {
       }
       return;
     }
+    if (kind == kCallback) {
+      sampled_minmax(lo, hi, mn, mx);
+      return;
+    }
     refined(lo, hi, 0, mn, mx);
   }
 
   // true when d phi / d x_k provably keeps one strict sign on the box
   bool monotone_in(int k, const double* lo, const double* hi) const {
     switch (kind) {
+      case kCallback: return sampled_monotone(k, lo, hi);
       case kSphere: return c[k] < lo[k] || c[k] > hi[k];
       case kPlane: return nrm[k] != 0.0;
       case kEllipsoid: {

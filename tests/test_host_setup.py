@@ -7,6 +7,8 @@ import pytest
 
 from oracle import Hierarchy
 from oracle.fem import assemble_rhs
+
+from callback_shapes import superellipse
 from oracle.levelset import make_levelset
 
 cm = pytest.importorskip("paper_2508_11608_gb300")
@@ -33,6 +35,9 @@ CASES = {
                                                    "axes": [0.7, 0.5, 0.45], "rot": _rot(0.3, 0.5)}),
     "torus_q2": dict(dim=3, N=16, L=2, p=2, ls={"kind": "torus", "center": [0.02, 0.01, -0.03],
                                                 "rot": _rot(0.4, 0.7), "major": 0.6, "minor": 0.2}),
+    # user level sets through point callbacks (sampled bounds on both sides)
+    "callback_q2": dict(dim=2, N=32, L=3, p=2, ls=superellipse([0.03, -0.02], [0.7, 0.55])),
+    "callback3d_q2": dict(dim=3, N=8, L=2, p=2, ls=superellipse([0.03, -0.02, 0.01], [0.7, 0.55, 0.6])),
 }
 
 
@@ -137,6 +142,18 @@ def test_patches_and_inverses_match(pair):
             invs = inv[np.ix_(po, po)]
             I = invs @ Aj
             assert np.abs(I - np.eye(len(nodes))).max() < 1e-9
+
+
+def test_callback_level_set_needs_both_functions():
+    spec = dict(superellipse([0.0, 0.0], [0.7, 0.6]))
+    ls = cm._lib.make_levelset(spec)
+    ls.grad = cm._lib.GRAD_FN()  # NULL
+    lib = cm._lib.load()
+    mesh = cm._lib.cf_mesh(2, 8, -1.0, 1.0, 1)
+    import ctypes
+    out = ctypes.c_void_p()
+    st = lib.cf_setup_host(ctypes.byref(mesh), ctypes.byref(ls), 2, None, ctypes.byref(out))
+    assert st == 1 and not out.value  # CF_EINVAL
 
 
 def test_invalid_arguments_are_rejected():
