@@ -57,7 +57,7 @@ def build(verbose=False, force=False):
     for f in CPP_SOURCES:
         o = os.path.join(BUILD, f + ".o")
         objs.append(o)
-        jobs.append(["g++", "-O2", "-std=c++17", "-fPIC", "-fopenmp", "-ffp-contract=off", *inc,
+        jobs.append(["g++", "-O3", "-std=c++17", "-fPIC", "-fopenmp", "-ffp-contract=off", *inc,
                      "-I", "/usr/local/cuda/include", "-c", os.path.join(CSRC, f), "-o", o])
     with ThreadPoolExecutor(max_workers=len(jobs)) as ex:
         outs = list(ex.map(_run, jobs))

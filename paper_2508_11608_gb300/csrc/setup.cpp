@@ -28,52 +28,98 @@ int ipow(int b, int e) {
   return r;
 }
 
-// SPD matrix (row-major, n x n) -> its inverse, through L L^T.  All inner
-// products run over contiguous rows; large matrices (the coarsest-level
-// operator) are split over threads, with the same summation order per entry.
+// SPD matrix (row-major, n x n) -> its inverse, in three passes of
+// contiguous row updates (axpy form, so the inner loops vectorise without
+// reassociating any sum):
+//   1. A = U^T U, U upper triangular, right-looking Cholesky in place; the
+//      trailing rows take the updates of a block of BS factor rows at once;
+//   2. W = U^{-1} by rows, row c from the forward solve U^T w_c = e_c, for a
+//      block of BS rows per pass over U;
+//   3. A^{-1} = W W^T, row i accumulated over k = i..n-1 as rank-one updates
+//      with column k of W, then mirrored.
+// Every entry's sum runs in ascending index order, whatever the thread
+// count; large matrices (the coarsest-level operator) are split over threads.
 void spd_inverse(int n, double* A) {
-  std::vector<double> L((size_t)n * n, 0.0), U((size_t)n * n, 0.0);
+  constexpr int BS = 16;
   const bool par = n > 256;
-  for (int j = 0; j < n; ++j) {
-    double s = A[(size_t)j * n + j];
-    for (int k = 0; k < j; ++k) s -= L[(size_t)j * n + k] * L[(size_t)j * n + k];
-    if (!(s > 0.0))
-      throw std::runtime_error("matrix is not positive definite (pivot " + std::to_string(j) + " of " +
-                               std::to_string(n) + ": " + std::to_string(s) + ")");
-    double ljj = std::sqrt(s);
-    L[(size_t)j * n + j] = ljj;
-    const double* Lj = &L[(size_t)j * n];
+  for (int jb = 0; jb < n; jb += BS) {
+    const int je = std::min(n, jb + BS);
+    for (int j = jb; j < je; ++j) {
+      double* Aj = A + (size_t)j * n;
+      for (int jj = jb; jj < j; ++jj) {
+        const double* Ujj = A + (size_t)jj * n;
+        const double a = Ujj[j];
+        for (int k = j; k < n; ++k) Aj[k] -= a * Ujj[k];
+      }
+      const double s = Aj[j];
+      if (!(s > 0.0))
+        throw std::runtime_error("matrix is not positive definite (pivot " + std::to_string(j) + " of " +
+                                 std::to_string(n) + ": " + std::to_string(s) + ")");
+      const double d = std::sqrt(s);
+      Aj[j] = d;
+      for (int k = j + 1; k < n; ++k) Aj[k] /= d;
+    }
+#pragma omp parallel for schedule(dynamic, 4) if (par)
+    for (int i = je; i < n; ++i) {
+      double* __restrict__ Ai = A + (size_t)i * n;
+      int j = jb;
+      // four factor rows per sweep, subtracted in row order
+      for (; j + 4 <= je; j += 4) {
+        const double* __restrict__ U0 = A + (size_t)j * n;
+        const double* __restrict__ U1 = U0 + n;
+        const double* __restrict__ U2 = U1 + n;
+        const double* __restrict__ U3 = U2 + n;
+        const double a0 = U0[i], a1 = U1[i], a2 = U2[i], a3 = U3[i];
+        for (int k = i; k < n; ++k) Ai[k] = (((Ai[k] - a0 * U0[k]) - a1 * U1[k]) - a2 * U2[k]) - a3 * U3[k];
+      }
+      for (; j < je; ++j) {
+        const double* Uj = A + (size_t)j * n;
+        const double a = Uj[i];
+        for (int k = i; k < n; ++k) Ai[k] -= a * Uj[k];
+      }
+    }
+  }
+  // W = U^{-1}: row c solves U^T w = e_c (w[k] = 0 for k < c); t carries the
+  // right-hand side minus the terms already known
+  std::vector<double> W((size_t)n * n, 0.0);
+  const int nblk = (n + BS - 1) / BS;
+#pragma omp parallel for schedule(dynamic, 1) if (par)
+  for (int bi = 0; bi < nblk; ++bi) {
+    const int c0 = bi * BS, c1 = std::min(n, c0 + BS);
+    for (int c = c0; c < c1; ++c) W[(size_t)c * n + c] = 1.0;
+    for (int k = c0; k < n; ++k) {
+      const double* Uk = A + (size_t)k * n;
+      const double dk = Uk[k];
+      for (int c = c0; c < c1 && c <= k; ++c) {
+        double* Wc = &W[(size_t)c * n];
+        const double wk = Wc[k] / dk;
+        Wc[k] = wk;
+        for (int q = k + 1; q < n; ++q) Wc[q] -= wk * Uk[q];
+      }
+    }
+  }
+  // Z = W^T (row k of Z = column k of W), then A^{-1}[i][0..i] = sum over
+  // k >= i of W[i][k] Z[k][0..i]
+  std::vector<double> Z((size_t)n * n, 0.0);
 #pragma omp parallel for schedule(static) if (par)
-    for (int i = j + 1; i < n; ++i) {
-      const double* Li = &L[(size_t)i * n];
-      double t = A[(size_t)i * n + j];
-      for (int k = 0; k < j; ++k) t -= Li[k] * Lj[k];
-      L[(size_t)i * n + j] = t / ljj;
+  for (int k = 0; k < n; ++k)
+    for (int i = 0; i <= k; ++i) Z[(size_t)k * n + i] = W[(size_t)i * n + k];
+#pragma omp parallel for schedule(dynamic, 1) if (par)
+  for (int bi = 0; bi < nblk; ++bi) {
+    const int i0 = bi * BS, i1 = std::min(n, i0 + BS);
+    for (int i = i0; i < i1; ++i)
+      for (int j = 0; j <= i; ++j) A[(size_t)i * n + j] = 0.0;
+    for (int k = i0; k < n; ++k) {
+      const double* Zk = &Z[(size_t)k * n];
+      for (int i = i0; i < i1 && i <= k; ++i) {
+        const double a = Zk[i];
+        double* Ai = A + (size_t)i * n;
+        for (int j = 0; j <= i; ++j) Ai[j] += a * Zk[j];
+      }
     }
   }
-  // U = L^{-T}: row c of U is column c of L^{-1} (forward substitution)
-#pragma omp parallel for schedule(dynamic, 8) if (par)
-  for (int c = 0; c < n; ++c) {
-    double* Uc = &U[(size_t)c * n];
-    for (int i = c; i < n; ++i) {
-      const double* Li = &L[(size_t)i * n];
-      double t = (i == c) ? 1.0 : 0.0;
-      for (int k = c; k < i; ++k) t -= Li[k] * Uc[k];
-      Uc[i] = t / Li[i];
-    }
-  }
-  // A^{-1} = L^{-T} L^{-1}: entry (i, j), j <= i, is row i of U dotted with row j
-#pragma omp parallel for schedule(dynamic, 8) if (par)
-  for (int i = 0; i < n; ++i) {
-    const double* Ui = &U[(size_t)i * n];
-    for (int j = 0; j <= i; ++j) {
-      const double* Uj = &U[(size_t)j * n];
-      double t = 0.0;
-      for (int k = i; k < n; ++k) t += Ui[k] * Uj[k];
-      A[(size_t)i * n + j] = t;
-      A[(size_t)j * n + i] = t;
-    }
-  }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < i; ++j) A[(size_t)j * n + i] = A[(size_t)i * n + j];
 }
 
 // Symmetric eigen-decomposition by cyclic Jacobi rotations: A = Q diag(lam) Q^T.
@@ -136,6 +182,19 @@ struct RefTables {
       j /= p + 1;
     }
   }
+  // tensor basis values at reference point xi
+  void values(const double* xi, double* v) const {
+    double l[3][4];
+    for (int k = 0; k < d; ++k)
+      for (int a = 0; a <= p; ++a) l[k][a] = b.eval(a, xi[k]);
+    for (int j = 0; j < NB; ++j) {
+      int a[3];
+      split(j, a);
+      double val = 1.0;
+      for (int k = 0; k < d; ++k) val *= l[k][a[k]];
+      v[j] = val;
+    }
+  }
   // tensor basis values and physical gradients at reference point xi
   void eval(const double* xi, double h, double* v, double* g /* NB x d */) const {
     double l[3][4], dl[3][4];
@@ -159,24 +218,33 @@ struct RefTables {
   }
 };
 
-// a_T(phi_j, phi_i) of a cut cell: volume + Nitsche terms
+// a_T(phi_j, phi_i) of a cut cell: volume + Nitsche terms.  Every term is
+// symmetric in (i, j), so each quadrature point adds rank-one updates to the
+// upper triangle (contiguous inner loops over j), mirrored at the end.
 void cut_cell_matrix(const RefTables& R, const CutRule& rule, const double* lo, double h,
                      double gamma_D, double* K) {
   const int NB = R.NB, d = R.d;
-  std::vector<double> v(NB), g(NB * d);
+  std::vector<double> v(NB), g(NB * d), gk((size_t)d * NB), dn(NB);
   std::fill(K, K + NB * NB, 0.0);
   double xi[3];
+  // volume: w grad(phi_i) . grad(phi_j), one update per direction k
   for (const auto& nd : rule.vol) {
     for (int k = 0; k < d; ++k) xi[k] = (nd.x[k] - lo[k]) / h;
     R.eval(xi, h, v.data(), g.data());
-    for (int i = 0; i < NB; ++i)
-      for (int j = 0; j < NB; ++j) {
-        double s = 0.0;
-        for (int k = 0; k < d; ++k) s += g[i * d + k] * g[j * d + k];
-        K[i * NB + j] += nd.w * s;
+    for (int k = 0; k < d; ++k)
+      for (int j = 0; j < NB; ++j) gk[(size_t)k * NB + j] = g[j * d + k];
+    for (int i = 0; i < NB; ++i) {
+      double* Ki = K + (size_t)i * NB;
+      for (int k = 0; k < d; ++k) {
+        const double* gj = &gk[(size_t)k * NB];
+        const double a = nd.w * gj[i];
+        for (int j = i; j < NB; ++j) Ki[j] += a * gj[j];
       }
+    }
   }
-  std::vector<double> dn(NB);
+  // Nitsche: w (-(dn_i v_j + v_i dn_j) + gamma_D / h v_i v_j)
+  //        = w (gamma_D / h v_i - dn_i) v_j - w v_i dn_j
+  const double pen = gamma_D / h;
   for (size_t q = 0; q < rule.surf.size(); ++q) {
     const auto& nd = rule.surf[q];
     for (int k = 0; k < d; ++k) xi[k] = (nd.x[k] - lo[k]) / h;
@@ -186,10 +254,14 @@ void cut_cell_matrix(const RefTables& R, const CutRule& rule, const double* lo, 
       for (int k = 0; k < d; ++k) s += rule.normal[q][k] * g[i * d + k];
       dn[i] = s;
     }
-    for (int i = 0; i < NB; ++i)
-      for (int j = 0; j < NB; ++j)
-        K[i * NB + j] += nd.w * (-(dn[i] * v[j] + v[i] * dn[j]) + gamma_D / h * v[i] * v[j]);
+    for (int i = 0; i < NB; ++i) {
+      double* Ki = K + (size_t)i * NB;
+      const double a = nd.w * (pen * v[i] - dn[i]), c = -nd.w * v[i];
+      for (int j = i; j < NB; ++j) Ki[j] += a * v[j] + c * dn[j];
+    }
   }
+  for (int i = 1; i < NB; ++i)
+    for (int j = 0; j < i; ++j) K[(size_t)i * NB + j] = K[(size_t)j * NB + i];
 }
 
 // cells containing lattice coordinate i along one direction
@@ -532,6 +604,9 @@ void build_level(const SetupParams& prm, const RefTables& R, int N, HostLevel& L
     const int NCL = ipow(C, d);
     const int64_t nvert = (int64_t)ipow(np, d);
     std::vector<std::vector<int>> cart(ncol), cutv(ncol);
+    // per vertex: -1 (no active cell around it), else colour + 8 if Cartesian
+    std::vector<int8_t> vkind(nvert);
+#pragma omp parallel for schedule(static)
     for (int64_t q = 0; q < nvert; ++q) {
       int v[3] = {0, 0, 0};
       int64_t t = q;
@@ -546,10 +621,14 @@ void build_level(const SetupParams& prm, const RefTables& R, int N, HostLevel& L
         if (cflag_at(c) & kFlagActive) any = true;
         if (!plain(c)) cartesian = false;
       }
-      if (!any) continue;
       int col = 0;
       for (int k = 0; k < d; ++k) col |= (v[k] & 1) << k;
-      (cartesian ? cart : cutv)[col].push_back((int)q);
+      vkind[q] = any ? (int8_t)(col + (cartesian ? 8 : 0)) : (int8_t)-1;
+    }
+    for (int64_t q = 0; q < nvert; ++q) {
+      if (vkind[q] < 0) continue;
+      const int col = vkind[q] & 7;
+      ((vkind[q] & 8) ? cart : cutv)[col].push_back((int)q);
     }
     L.cart_start.assign(ncol + 1, 0);
     L.cut_start.assign(ncol + 1, 0);
@@ -632,52 +711,70 @@ void build_level(const SetupParams& prm, const RefTables& R, int N, HostLevel& L
     }
     L.inv.assign(ioff, 0.0);
     // ghost-face entries of every cut-patch DoF (the faces whose two cells
-    // contain the node), and per colour the faces these rows need
+    // contain the node), and per colour the faces these rows need.  Entries
+    // are counted, then written at their offsets, member by member in
+    // parallel (the lists are the same for every thread count).
     {
       const int NTf = ipow(p + 1, d - 1);
-      L.fofs.assign(L.member_node.size() + 1, 0);
+      const int64_t nmem = (int64_t)L.member_node.size();
+      // entry = ((face id * NTf) + tangential node) * 8 + node along the normal
+      auto entries = [&](int64_t gm, auto&& emit) {
+        int64_t t = L.member_node[gm];
+        int idx[3] = {0, 0, 0};
+        for (int k = 0; k < d; ++k) {
+          idx[k] = (int)(t % n);
+          t /= n;
+        }
+        int cc[3][2], lcl[3][2], nopt[3] = {1, 1, 1};
+        for (int k = 0; k < d; ++k) nopt[k] = cells_of(idx[k], p, N, cc[k], lcl[k]);
+        for (int k = 0; k < d; ++k) {
+          const int a = idx[k] / p, r = idx[k] - a * p;
+          int Llo = (r == 0) ? a - 2 : a - 1, Lhi = a;
+          Llo = std::max(Llo, 0);
+          Lhi = std::min(Lhi, N - 2);
+          int td[2] = {0, 0}, q = 0;
+          for (int jj = 0; jj < d; ++jj)
+            if (jj != k) td[q++] = jj;
+          const int n0 = nopt[td[0]], n1 = (d == 3) ? nopt[td[1]] : 1;
+          for (int Lk = Llo; Lk <= Lhi; ++Lk)
+            for (int u0 = 0; u0 < n0; ++u0)
+              for (int u1 = 0; u1 < n1; ++u1) {
+                int c[3] = {0, 0, 0};
+                c[k] = Lk;
+                c[td[0]] = cc[td[0]][u0];
+                if (d == 3) c[td[1]] = cc[td[1]][u1];
+                int64_t cell = c[0] + (int64_t)N * (c[1] + (d == 3 ? (int64_t)N * c[2] : 0));
+                const int id = L.face_id[(size_t)cell * d + k];
+                if (id < 0) continue;
+                int tt = idx[td[0]] - p * c[td[0]];
+                if (d == 3) tt += (p + 1) * (idx[td[1]] - p * c[td[1]]);
+                emit(((id * NTf) + tt) * 8 + (idx[k] - p * Lk));
+              }
+        }
+      };
+      std::vector<int> cnt(nmem, 0);
+#pragma omp parallel for schedule(dynamic, 256)
+      for (int64_t gm = 0; gm < nmem; ++gm) {
+        int c = 0;
+        entries(gm, [&](int) { ++c; });
+        cnt[gm] = c;
+      }
+      L.fofs.assign(nmem + 1, 0);
+      for (int64_t gm = 0; gm < nmem; ++gm) L.fofs[gm + 1] = L.fofs[gm] + cnt[gm];
+      L.fent.assign((size_t)L.fofs[nmem], 0);
+#pragma omp parallel for schedule(dynamic, 256)
+      for (int64_t gm = 0; gm < nmem; ++gm) {
+        int o = L.fofs[gm];
+        entries(gm, [&](int v) { L.fent[o++] = v; });
+      }
       L.cf_start.assign(ncol + 1, 0);
       std::vector<uint8_t> need(L.ghost_faces.size(), 0);
-      size_t gm = 0;
+      int64_t gm = 0;
       for (int col = 0; col < ncol; ++col) {
         std::fill(need.begin(), need.end(), 0);
         for (int j = L.cut_start[col]; j < L.cut_start[col + 1]; ++j)
-          for (int e = 0; e < L.cut_n[j]; ++e, ++gm) {
-            int64_t t = L.member_node[gm];
-            int idx[3] = {0, 0, 0};
-            for (int k = 0; k < d; ++k) {
-              idx[k] = (int)(t % n);
-              t /= n;
-            }
-            int cc[3][2], lcl[3][2], nopt[3] = {1, 1, 1};
-            for (int k = 0; k < d; ++k) nopt[k] = cells_of(idx[k], p, N, cc[k], lcl[k]);
-            for (int k = 0; k < d; ++k) {
-              const int a = idx[k] / p, r = idx[k] - a * p;
-              int Llo = (r == 0) ? a - 2 : a - 1, Lhi = a;
-              Llo = std::max(Llo, 0);
-              Lhi = std::min(Lhi, N - 2);
-              int td[2] = {0, 0}, q = 0;
-              for (int jj = 0; jj < d; ++jj)
-                if (jj != k) td[q++] = jj;
-              const int n0 = nopt[td[0]], n1 = (d == 3) ? nopt[td[1]] : 1;
-              for (int Lk = Llo; Lk <= Lhi; ++Lk)
-                for (int u0 = 0; u0 < n0; ++u0)
-                  for (int u1 = 0; u1 < n1; ++u1) {
-                    int c[3] = {0, 0, 0};
-                    c[k] = Lk;
-                    c[td[0]] = cc[td[0]][u0];
-                    if (d == 3) c[td[1]] = cc[td[1]][u1];
-                    int64_t cell = c[0] + (int64_t)N * (c[1] + (d == 3 ? (int64_t)N * c[2] : 0));
-                    const int id = L.face_id[(size_t)cell * d + k];
-                    if (id < 0) continue;
-                    int tt = idx[td[0]] - p * c[td[0]];
-                    if (d == 3) tt += (p + 1) * (idx[td[1]] - p * c[td[1]]);
-                    L.fent.push_back(((id * NTf) + tt) * 8 + (idx[k] - p * Lk));
-                    need[id] = 1;
-                  }
-            }
-            L.fofs[gm + 1] = (int)L.fent.size();
-          }
+          for (int e = 0; e < L.cut_n[j]; ++e, ++gm)
+            for (int q = L.fofs[gm]; q < L.fofs[gm + 1]; ++q) need[(L.fent[q] >> 3) / NTf] = 1;
         for (size_t f = 0; f < need.size(); ++f)
           if (need[f]) L.cfaces.push_back((int)f);
         L.cf_start[col + 1] = (int)L.cfaces.size();
@@ -775,6 +872,28 @@ void build_level(const SetupParams& prm, const RefTables& R, int N, HostLevel& L
         L.work_cart[col] = {np_ * flc, np_ * scc, np_ * 4.0};
       }
     }
+    // ghost-face block of one face (block nodes e = i + (2p+1) u: i along the
+    // normal over both cells, u tangential): the same for every face and
+    // direction of the level
+    const int tn = ipow(p + 1, d - 1), nbk = (2 * p + 1) * tn;
+    std::vector<int> fb_i(nbk), fb_t((size_t)nbk * 2, 0);
+    for (int e = 0; e < nbk; ++e) {
+      int u = e / (2 * p + 1);
+      fb_i[e] = e % (2 * p + 1);
+      for (int q = 0; q < d - 1; ++q) {
+        fb_t[e * 2 + q] = u % (p + 1);
+        u /= p + 1;
+      }
+    }
+    std::vector<double> fblk((size_t)nbk * nbk);
+    for (int e1 = 0; e1 < nbk; ++e1)
+      for (int e2 = 0; e2 < nbk; ++e2) {
+        double tm = 1.0;
+        for (int q = 0; q < d - 1; ++q) tm *= L.Mhat[fb_t[e1 * 2 + q]][fb_t[e2 * 2 + q]];
+        double s = 0.0;
+        for (int mm = 0; mm < p; ++mm) s += L.coef[mm] * L.dvec[mm][fb_i[e1]] * L.dvec[mm][fb_i[e2]];
+        fblk[(size_t)e1 * nbk + e2] = s * tm;
+      }
     // A_j = A[I_j, I_j] from cell and ghost-face pieces, then inverted
     std::vector<int> err(ncp, 0);
     std::string first_err;
@@ -841,36 +960,19 @@ void build_level(const SetupParams& prm, const RefTables& R, int N, HostLevel& L
               uint8_t f1 = cflag_at(lc), f2 = cflag_at(uc);
               if (!((f1 & kFlagActive) && (f2 & kFlagActive) && ((f1 | f2) & kFlagCut))) continue;
               // block nodes: i in [0, 2p] along k, t in [0, p] tangential
-              const int tn = ipow(p + 1, d - 1);
-              const int nbk = (2 * p + 1) * tn;
-              std::vector<int> mi(nbk);
-              std::vector<int> ii(nbk), tt(nbk * 2);
+              int mi[7 * 16];
               for (int e = 0; e < nbk; ++e) {
-                int i = e % (2 * p + 1), u = e / (2 * p + 1);
                 int lat[3] = {0, 0, 0}, q = 0;
-                for (int kk = 0; kk < d; ++kk) {
-                  if (kk == k) {
-                    lat[kk] = p * lc[kk] + i;
-                  } else {
-                    int tv = u % (p + 1);
-                    u /= p + 1;
-                    lat[kk] = p * lc[kk] + tv;
-                    tt[e * 2 + q++] = tv;
-                  }
-                }
-                ii[e] = i;
+                for (int kk = 0; kk < d; ++kk)
+                  lat[kk] = p * lc[kk] + (kk == k ? fb_i[e] : fb_t[e * 2 + q++]);
                 mi[e] = closure_of(lat);
               }
               for (int e1 = 0; e1 < nbk; ++e1) {
                 if (mi[e1] < 0) continue;
-                for (int e2 = 0; e2 < nbk; ++e2) {
-                  if (mi[e2] < 0) continue;
-                  double tm = 1.0;
-                  for (int q = 0; q < d - 1; ++q) tm *= L.Mhat[tt[e1 * 2 + q]][tt[e2 * 2 + q]];
-                  double s = 0.0;
-                  for (int mm = 0; mm < p; ++mm) s += L.coef[mm] * L.dvec[mm][ii[e1]] * L.dvec[mm][ii[e2]];
-                  A[(size_t)mi[e1] * m + mi[e2]] += s * tm;
-                }
+                const double* fr = &fblk[(size_t)e1 * nbk];
+                double* Ar = A + (size_t)mi[e1] * m;
+                for (int e2 = 0; e2 < nbk; ++e2)
+                  if (mi[e2] >= 0) Ar[mi[e2]] += fr[e2];
               }
             }
       }
@@ -1021,6 +1123,31 @@ void build_diag(const RefTables& R, HostLevel& L) {
 
 // b_i = (f, phi_i)_Omega + (g, gamma_D/h phi_i - d_n phi_i)_Gamma for
 // u = prod sin(pi x_k), f = d pi^2 u, g = u
+// loc[j] = sum over the q^d tensor points of F[point] times basis j there
+// (Lt[a * q + i]: 1D basis a at Gauss point i), one 1D contraction per
+// direction; points and basis indices both run first coordinate fastest.
+// work holds 2 max(q, p + 1)^d values.
+void tensor_contract(int d, int p, int q, const double* Lt, const double* F, double* loc, double* work) {
+  const int half = ipow(std::max(q, p + 1), d);
+  int sz[3] = {q, q, q};
+  const double* cur = F;
+  for (int k = 0; k < d; ++k) {
+    double* out = (k == d - 1) ? loc : work + (k & 1) * half;
+    int inner = 1, outer = 1;
+    for (int kk = 0; kk < k; ++kk) inner *= sz[kk];
+    for (int kk = k + 1; kk < d; ++kk) outer *= sz[kk];
+    for (int o = 0; o < outer; ++o)
+      for (int a = 0; a <= p; ++a)
+        for (int i = 0; i < inner; ++i) {
+          double acc = 0.0;
+          for (int t = 0; t < q; ++t) acc += Lt[a * q + t] * cur[i + inner * (t + q * o)];
+          out[i + inner * (a + (p + 1) * o)] = acc;
+        }
+    sz[k] = p + 1;
+    cur = out;
+  }
+}
+
 void build_rhs(const SetupParams& prm, const RefTables& R, const HostLevel& L, std::vector<double>& b,
                const std::function<double(const double*)>& fsrc, const std::function<double(const double*)>& gdir,
                bool parallel) {
@@ -1031,6 +1158,10 @@ void build_rhs(const SetupParams& prm, const RefTables& R, const HostLevel& L, s
   b.assign(L.dofs.size(), 0.0);
   GaussRule g = gauss_legendre01(q);
   const int nq = ipow(q, d);
+  std::vector<double> Lt((size_t)(p + 1) * q);
+  for (int a = 0; a <= p; ++a)
+    for (int t = 0; t < q; ++t) Lt[a * q + t] = R.b.eval(a, g.x[t]);
+  const double hd = std::pow(h, d);
   CutQuadrature Q(prm.ls, q);
   const int64_t ncell = ipow(N, d);
   std::vector<int64_t> act;
@@ -1056,29 +1187,30 @@ void build_rhs(const SetupParams& prm, const RefTables& R, const HostLevel& L, s
         hi[k] = lo[k] + h;
       }
       std::vector<double> v(NB), gr(NB * d);
+      std::vector<double> Fw((size_t)nq + 2 * ipow(std::max(q, p + 1), d));
       double* loc = &locs[(size_t)(ic - c0) * NB];
       for (int j = 0; j < NB; ++j) loc[j] = 0.0;
       if (!(f & kFlagCut)) {
+        // tensor Gauss rule: f w at every point, then sum factorisation
+        double* F = Fw.data();
         for (int iq = 0; iq < nq; ++iq) {
-          double xi[3] = {0, 0, 0}, x[3] = {0, 0, 0}, w = 1.0;
+          double x[3] = {0, 0, 0}, w = 1.0;
           int u = iq;
           for (int k = 0; k < d; ++k) {
             int a = u % q;
             u /= q;
-            xi[k] = g.x[a];
             w *= g.w[a];
-            x[k] = lo[k] + h * xi[k];
+            x[k] = lo[k] + h * g.x[a];
           }
-          R.eval(xi, h, v.data(), gr.data());
-          double fx = fsrc(x) * w * std::pow(h, d);
-          for (int j = 0; j < NB; ++j) loc[j] += v[j] * fx;
+          F[iq] = fsrc(x) * w * hd;
         }
+        tensor_contract(d, p, q, Lt.data(), F, loc, F + nq);
       } else {
         CutRule rule = Q.cell(lo, hi);
         for (const auto& nd : rule.vol) {
           double xi[3] = {0, 0, 0};
           for (int k = 0; k < d; ++k) xi[k] = (nd.x[k] - lo[k]) / h;
-          R.eval(xi, h, v.data(), gr.data());
+          R.values(xi, v.data());
           double fx = fsrc(nd.x) * nd.w;
           for (int j = 0; j < NB; ++j) loc[j] += v[j] * fx;
         }
