@@ -163,7 +163,13 @@ struct RefTables {
   int p, d, NB;
   Poly1D b;
   std::vector<double> M1, K1;  // (p+1)^2 reference mass / stiffness on [0, 1]
-  explicit RefTables(int p_, int d_) : p(p_), d(d_), NB(ipow(p_ + 1, d_)), b(p_) {
+  std::vector<std::array<int, 3>> mi;  // multi-index of local basis function j
+  explicit RefTables(int p_, int d_) : p(p_), d(d_), NB(ipow(p_ + 1, d_)), b(p_), mi(NB) {
+    for (int j = 0; j < NB; ++j) {
+      int a[3] = {0, 0, 0};
+      split(j, a);
+      mi[j] = {a[0], a[1], a[2]};
+    }
     GaussRule g = gauss_legendre01(p + 1);
     M1.assign((p + 1) * (p + 1), 0.0);
     K1.assign((p + 1) * (p + 1), 0.0);
@@ -188,8 +194,7 @@ struct RefTables {
     for (int k = 0; k < d; ++k)
       for (int a = 0; a <= p; ++a) l[k][a] = b.eval(a, xi[k]);
     for (int j = 0; j < NB; ++j) {
-      int a[3];
-      split(j, a);
+      const int* a = mi[j].data();
       double val = 1.0;
       for (int k = 0; k < d; ++k) val *= l[k][a[k]];
       v[j] = val;
@@ -204,8 +209,7 @@ struct RefTables {
         dl[k][a] = b.eval(a, xi[k], 1) / h;
       }
     for (int j = 0; j < NB; ++j) {
-      int a[3];
-      split(j, a);
+      const int* a = mi[j].data();
       double val = 1.0;
       for (int k = 0; k < d; ++k) val *= l[k][a[k]];
       v[j] = val;
@@ -224,21 +228,51 @@ struct RefTables {
 void cut_cell_matrix(const RefTables& R, const CutRule& rule, const double* lo, double h,
                      double gamma_D, double* K) {
   const int NB = R.NB, d = R.d;
-  std::vector<double> v(NB), g(NB * d), gk((size_t)d * NB), dn(NB);
+  std::vector<double> v(NB), g(NB * d), dn(NB);
   std::fill(K, K + NB * NB, 0.0);
   double xi[3];
-  // volume: w grad(phi_i) . grad(phi_j), one update per direction k
-  for (const auto& nd : rule.vol) {
-    for (int k = 0; k < d; ++k) xi[k] = (nd.x[k] - lo[k]) / h;
-    R.eval(xi, h, v.data(), g.data());
-    for (int k = 0; k < d; ++k)
-      for (int j = 0; j < NB; ++j) gk[(size_t)k * NB + j] = g[j * d + k];
+  // volume: w grad(phi_i) . grad(phi_j), one update per (point, direction)
+  // row r, in point order; a batch of QB points is applied to each entry
+  // with the entry held in a register (four entries of a row at a time)
+  constexpr int QB = 8;
+  std::vector<double> Wg((size_t)QB * d * NB), Gg((size_t)QB * d * NB);  // w dphi_j/dx_k, dphi_j/dx_k
+  const size_t nv = rule.vol.size();
+  for (size_t q0 = 0; q0 < nv; q0 += QB) {
+    const int nb = (int)std::min<size_t>(QB, nv - q0);
+    for (int bq = 0; bq < nb; ++bq) {
+      const auto& nd = rule.vol[q0 + bq];
+      for (int k = 0; k < d; ++k) xi[k] = (nd.x[k] - lo[k]) / h;
+      R.eval(xi, h, v.data(), g.data());
+      for (int k = 0; k < d; ++k)
+        for (int j = 0; j < NB; ++j) {
+          const size_t r = (size_t)(bq * d + k) * NB + j;
+          Gg[r] = g[j * d + k];
+          Wg[r] = nd.w * g[j * d + k];
+        }
+    }
+    const int nr = nb * d;
     for (int i = 0; i < NB; ++i) {
       double* Ki = K + (size_t)i * NB;
-      for (int k = 0; k < d; ++k) {
-        const double* gj = &gk[(size_t)k * NB];
-        const double a = nd.w * gj[i];
-        for (int j = i; j < NB; ++j) Ki[j] += a * gj[j];
+      int j = i;
+      for (; j + 4 <= NB; j += 4) {
+        double a0 = Ki[j], a1 = Ki[j + 1], a2 = Ki[j + 2], a3 = Ki[j + 3];
+        for (int r = 0; r < nr; ++r) {
+          const double a = Wg[(size_t)r * NB + i];
+          const double* gr = &Gg[(size_t)r * NB + j];
+          a0 += a * gr[0];
+          a1 += a * gr[1];
+          a2 += a * gr[2];
+          a3 += a * gr[3];
+        }
+        Ki[j] = a0;
+        Ki[j + 1] = a1;
+        Ki[j + 2] = a2;
+        Ki[j + 3] = a3;
+      }
+      for (; j < NB; ++j) {
+        double a0 = Ki[j];
+        for (int r = 0; r < nr; ++r) a0 += Wg[(size_t)r * NB + i] * Gg[(size_t)r * NB + j];
+        Ki[j] = a0;
       }
     }
   }
