@@ -87,7 +87,45 @@ void spd_inverse(int n, double* A) {
   for (int bi = 0; bi < nblk; ++bi) {
     const int c0 = bi * BS, c1 = std::min(n, c0 + BS);
     for (int c = c0; c < c1; ++c) W[(size_t)c * n + c] = 1.0;
-    for (int k = c0; k < n; ++k) {
+    int k = c0;
+    for (; k < n && k < c1 - 1; ++k) {  // rows c > k of the block start later
+      const double* Uk = A + (size_t)k * n;
+      const double dk = Uk[k];
+      for (int c = c0; c < c1 && c <= k; ++c) {
+        double* Wc = &W[(size_t)c * n];
+        const double wk = Wc[k] / dk;
+        Wc[k] = wk;
+        for (int q = k + 1; q < n; ++q) Wc[q] -= wk * Uk[q];
+      }
+    }
+    // four steps k..k+3 per sweep once every row of the block has started:
+    // the four multipliers first (entries k+1..k+3 take the earlier steps'
+    // updates in order), then one fused pass over q >= k + 4
+    for (; k + 4 <= n; k += 4) {
+      const double* U0 = A + (size_t)k * n;
+      const double* U1 = U0 + n;
+      const double* U2 = U1 + n;
+      const double* U3 = U2 + n;
+      for (int c = c0; c < c1; ++c) {
+        double* __restrict__ Wc = &W[(size_t)c * n];
+        const double w0 = Wc[k] / U0[k];
+        Wc[k] = w0;
+        Wc[k + 1] -= w0 * U0[k + 1];
+        Wc[k + 2] -= w0 * U0[k + 2];
+        Wc[k + 3] -= w0 * U0[k + 3];
+        const double w1 = Wc[k + 1] / U1[k + 1];
+        Wc[k + 1] = w1;
+        Wc[k + 2] -= w1 * U1[k + 2];
+        Wc[k + 3] -= w1 * U1[k + 3];
+        const double w2 = Wc[k + 2] / U2[k + 2];
+        Wc[k + 2] = w2;
+        Wc[k + 3] -= w2 * U2[k + 3];
+        const double w3 = Wc[k + 3] / U3[k + 3];
+        Wc[k + 3] = w3;
+        for (int q = k + 4; q < n; ++q) Wc[q] = (((Wc[q] - w0 * U0[q]) - w1 * U1[q]) - w2 * U2[q]) - w3 * U3[q];
+      }
+    }
+    for (; k < n; ++k) {
       const double* Uk = A + (size_t)k * n;
       const double dk = Uk[k];
       for (int c = c0; c < c1 && c <= k; ++c) {
@@ -109,7 +147,28 @@ void spd_inverse(int n, double* A) {
     const int i0 = bi * BS, i1 = std::min(n, i0 + BS);
     for (int i = i0; i < i1; ++i)
       for (int j = 0; j <= i; ++j) A[(size_t)i * n + j] = 0.0;
-    for (int k = i0; k < n; ++k) {
+    int k = i0;
+    for (; k < n && k < i1 - 1; ++k) {
+      const double* Zk = &Z[(size_t)k * n];
+      for (int i = i0; i < i1 && i <= k; ++i) {
+        const double a = Zk[i];
+        double* Ai = A + (size_t)i * n;
+        for (int j = 0; j <= i; ++j) Ai[j] += a * Zk[j];
+      }
+    }
+    // every row of the block takes every k from here: four k per sweep
+    for (; k + 4 <= n; k += 4) {
+      const double* Z0 = &Z[(size_t)k * n];
+      const double* Z1 = Z0 + n;
+      const double* Z2 = Z1 + n;
+      const double* Z3 = Z2 + n;
+      for (int i = i0; i < i1; ++i) {
+        const double a0 = Z0[i], a1 = Z1[i], a2 = Z2[i], a3 = Z3[i];
+        double* __restrict__ Ai = A + (size_t)i * n;
+        for (int j = 0; j <= i; ++j) Ai[j] = (((Ai[j] + a0 * Z0[j]) + a1 * Z1[j]) + a2 * Z2[j]) + a3 * Z3[j];
+      }
+    }
+    for (; k < n; ++k) {
       const double* Zk = &Z[(size_t)k * n];
       for (int i = i0; i < i1 && i <= k; ++i) {
         const double a = Zk[i];
