@@ -5,7 +5,9 @@
 //    cut quadrature, cell and patch matrices), each once its request has
 //    arrived, in arrival order and at most kLookahead requests ahead of
 //    admission; the workers share the host cores (one setup alone scales
-//    sublinearly with threads, so concurrent setups raise the rate).
+//    sublinearly with threads, so concurrent setups raise the rate).  A
+//    setup takes the cores no other running setup holds, at least its share
+//    of them, so a request that arrives alone is built on every core.
 //  * Admission (FIFO): a prepared request enters as soon as its device
 //    footprint (estimated from the host hierarchy) fits the HBM budget next to
 //    the resident problems and an active slot is free; its hierarchy is
@@ -148,6 +150,7 @@ cf_status cf_server_run(cf_server* s, void* stream) {
   const int nworkers = std::max(1, std::min(kMaxSetupWorkers, hw / kThreadsPerSetup));
   const int threads_each = std::max(1, hw / nworkers);
   int claimed = 0;
+  int threads_busy = 0;  // OpenMP threads of the setups in progress
   auto work = [&] {
     omp_set_num_threads(threads_each);
     for (;;) {
@@ -161,9 +164,18 @@ cf_status cf_server_run(cf_server* s, void* stream) {
       Request& r = s->reqs[i];
       const double wait = r.arrival - now();
       if (wait > 0) std::this_thread::sleep_for(std::chrono::duration<double>(wait));
+      cf_params prm = r.params;
+      int mine = 0;
+      if (prm.setup_threads == 0) {  // the caller left the thread count open
+        std::lock_guard<std::mutex> lk(mu);
+        mine = std::max(threads_each, hw - threads_busy);
+        threads_busy += mine;
+        prm.setup_threads = mine;
+      }
       cf_problem* pb = nullptr;
-      cf_status rc = cutmg_build_host(&r.mesh, &r.ls, r.degree, &r.params, &pb);
+      cf_status rc = cutmg_build_host(&r.mesh, &r.ls, r.degree, &prm, &pb);
       std::lock_guard<std::mutex> lk(mu);
+      threads_busy -= mine;
       if (rc != CF_OK) {
         r.state = -1;
         r.error = cf_last_error();
