@@ -104,11 +104,16 @@ class DevPool {
     if (zero) CUTMG_CUDA(cudaMemset(p, 0, count * sizeof(T)));
     return static_cast<T*>(p);
   }
-  template <typename T, typename S>
-  T* upload(const std::vector<S>& v) {
-    std::vector<T> tmp(v.begin(), v.end());
-    T* p = alloc<T>(tmp.size(), false);
-    if (!tmp.empty()) CUTMG_CUDA(cudaMemcpy(p, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice));
+  template <typename T, typename S, typename A>
+  T* upload(const std::vector<S, A>& v) {
+    T* p = alloc<T>(v.size(), false);
+    if (v.empty()) return p;
+    if constexpr (std::is_same<T, S>::value) {
+      CUTMG_CUDA(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    } else {
+      std::vector<T> tmp(v.begin(), v.end());
+      CUTMG_CUDA(cudaMemcpy(p, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice));
+    }
     return p;
   }
   size_t bytes() const { return bytes_; }

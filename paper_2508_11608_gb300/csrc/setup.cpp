@@ -409,7 +409,7 @@ void build_level(const SetupParams& prm, const RefTables& R, int N, HostLevel& L
     }
   }
   L.n_cut = (int64_t)cut_cells.size();
-  L.cutmat.assign((size_t)L.n_cut * NB * NB, 0.0);
+  L.cutmat.resize((size_t)L.n_cut * NB * NB);  // every block written below
   CutQuadrature Q(prm.ls, prm.quad_q);
 #pragma omp parallel for schedule(dynamic, 8)
   for (int64_t i = 0; i < L.n_cut; ++i) {
@@ -802,7 +802,7 @@ void build_level(const SetupParams& prm, const RefTables& R, int N, HostLevel& L
         L.member_node.push_back((int)node);
       }
     }
-    L.inv.assign(ioff, 0.0);
+    L.inv.resize(ioff);  // every slot zeroed and filled by its patch below
     // ghost-face entries of every cut-patch DoF (the faces whose two cells
     // contain the node), and per colour the faces these rows need.  Entries
     // are counted, then written at their offsets, member by member in
@@ -841,7 +841,7 @@ void build_level(const SetupParams& prm, const RefTables& R, int N, HostLevel& L
                 if (id < 0) continue;
                 int tt = idx[td[0]] - p * c[td[0]];
                 if (d == 3) tt += (p + 1) * (idx[td[1]] - p * c[td[1]]);
-                emit(((id * NTf) + tt) * 8 + (idx[k] - p * Lk));
+                emit(((id * NTf) + tt) * 8 + (idx[k] - p * Lk), id);
               }
         }
       };
@@ -849,27 +849,35 @@ void build_level(const SetupParams& prm, const RefTables& R, int N, HostLevel& L
 #pragma omp parallel for schedule(dynamic, 256)
       for (int64_t gm = 0; gm < nmem; ++gm) {
         int c = 0;
-        entries(gm, [&](int) { ++c; });
+        entries(gm, [&](int, int) { ++c; });
         cnt[gm] = c;
       }
       L.fofs.assign(nmem + 1, 0);
       for (int64_t gm = 0; gm < nmem; ++gm) L.fofs[gm + 1] = L.fofs[gm] + cnt[gm];
       L.fent.assign((size_t)L.fofs[nmem], 0);
+      // colour of every member (the colour of its patch)
+      std::vector<uint8_t> mcol(nmem);
+      for (int col = 0; col < ncol; ++col)
+        for (int j = L.cut_start[col]; j < L.cut_start[col + 1]; ++j)
+          std::fill(mcol.begin() + L.cut_moff[j], mcol.begin() + L.cut_moff[j] + L.cut_n[j], (uint8_t)col);
+      // need[col][face]: a row of the colour reads the face's moments
+      const size_t nf = L.ghost_faces.size();
+      std::vector<uint8_t> need((size_t)ncol * nf, 0);
 #pragma omp parallel for schedule(dynamic, 256)
       for (int64_t gm = 0; gm < nmem; ++gm) {
         int o = L.fofs[gm];
-        entries(gm, [&](int v) { L.fent[o++] = v; });
+        uint8_t* nc = &need[(size_t)mcol[gm] * nf];
+        entries(gm, [&](int v, int id) {
+          L.fent[o++] = v;
+#pragma omp atomic write
+          nc[id] = 1;
+        });
       }
       L.cf_start.assign(ncol + 1, 0);
-      std::vector<uint8_t> need(L.ghost_faces.size(), 0);
-      int64_t gm = 0;
       for (int col = 0; col < ncol; ++col) {
-        std::fill(need.begin(), need.end(), 0);
-        for (int j = L.cut_start[col]; j < L.cut_start[col + 1]; ++j)
-          for (int e = 0; e < L.cut_n[j]; ++e, ++gm)
-            for (int q = L.fofs[gm]; q < L.fofs[gm + 1]; ++q) need[(L.fent[q] >> 3) / NTf] = 1;
-        for (size_t f = 0; f < need.size(); ++f)
-          if (need[f]) L.cfaces.push_back((int)f);
+        const uint8_t* nc = &need[(size_t)col * nf];
+        for (size_t f = 0; f < nf; ++f)
+          if (nc[f]) L.cfaces.push_back((int)f);
         L.cf_start[col + 1] = (int)L.cfaces.size();
       }
     }
@@ -882,9 +890,21 @@ void build_level(const SetupParams& prm, const RefTables& R, int N, HostLevel& L
       L.cut_cell.assign((size_t)ncp * NCELL, -2);
       L.cut_item_off.assign(ncp + 1, 0);
       L.cut_items.clear();
-      std::vector<char> is_mem(NCL);
-      for (int64_t j = 0; j < ncp; ++j) {
-        L.cut_fo[j] = L.fofs[L.cut_moff[j]];
+      // closure offset of local node jj of patch cell sc
+      std::vector<int> cell_node((size_t)NCELL * NB);
+      for (int sc = 0; sc < NCELL; ++sc)
+        for (int jj = 0; jj < NB; ++jj) {
+          int o = 0, ost = 1, u = jj;
+          for (int k = 0; k < d; ++k) {
+            o += (p * ((sc >> k) & 1) + u % (p + 1)) * ost;
+            u /= (p + 1);
+            ost *= C;
+          }
+          cell_node[(size_t)sc * NB + jj] = o;
+        }
+      // per patch (in parallel): its cells, then its items counted and written
+      // at their offsets
+      auto patch_items = [&](int64_t j, std::vector<char>& is_mem, auto&& emit) {
         int v[3] = {0, 0, 0};
         int64_t t = L.cut_vert[j];
         for (int k = 0; k < d; ++k) {
@@ -900,17 +920,31 @@ void build_level(const SetupParams& prm, const RefTables& R, int N, HostLevel& L
           if (!(f & kFlagActive)) continue;
           const int64_t cell = c[0] + (int64_t)N * (c[1] + (d == 3 ? (int64_t)N * c[2] : 0));
           L.cut_cell[(size_t)j * NCELL + sc] = (f & kFlagCut) ? L.cut_id[cell] : -1;
-          for (int jj = 0; jj < NB; ++jj) {
-            int o = 0, ost = 1, u = jj;
-            for (int k = 0; k < d; ++k) {
-              o += (p * ((sc >> k) & 1) + u % (p + 1)) * ost;
-              u /= (p + 1);
-              ost *= C;
-            }
-            if (is_mem[o]) L.cut_items.push_back((uint8_t)(sc * NB + jj));
-          }
+          for (int jj = 0; jj < NB; ++jj)
+            if (is_mem[cell_node[(size_t)sc * NB + jj]]) emit((uint8_t)(sc * NB + jj));
         }
-        L.cut_item_off[j + 1] = (int)L.cut_items.size();
+      };
+#pragma omp parallel
+      {
+        std::vector<char> is_mem(NCL);
+#pragma omp for schedule(dynamic, 64)
+        for (int64_t j = 0; j < ncp; ++j) {
+          L.cut_fo[j] = L.fofs[L.cut_moff[j]];
+          int c = 0;
+          patch_items(j, is_mem, [&](uint8_t) { ++c; });
+          L.cut_item_off[j + 1] = c;
+        }
+      }
+      for (int64_t j = 0; j < ncp; ++j) L.cut_item_off[j + 1] += L.cut_item_off[j];
+      L.cut_items.assign((size_t)L.cut_item_off[ncp], 0);
+#pragma omp parallel
+      {
+        std::vector<char> is_mem(NCL);
+#pragma omp for schedule(dynamic, 64)
+        for (int64_t j = 0; j < ncp; ++j) {
+          int o = L.cut_item_off[j];
+          patch_items(j, is_mem, [&](uint8_t it) { L.cut_items[o++] = it; });
+        }
       }
       L.cut_fo[ncp] = L.fofs[L.member_node.size()];
       L.cut_maxit.assign(ncol, 0);
@@ -1002,6 +1036,7 @@ void build_level(const SetupParams& prm, const RefTables& R, int N, HostLevel& L
       std::vector<int> pos(NCL, -1);
       for (int a = 0; a < m; ++a) pos[mem[j][a]] = a;
       double* A = &L.inv[L.cut_ioff[j]];
+      std::fill(A, L.inv.data() + (j + 1 < ncp ? L.cut_ioff[j + 1] : (int64_t)L.inv.size()), 0.0);
       auto closure_of = [&](const int* lat) -> int {  // lattice coords -> member or -1
         int o = 0, st = 1;
         for (int k = 0; k < d; ++k) {

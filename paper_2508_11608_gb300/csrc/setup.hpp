@@ -3,13 +3,40 @@
 #pragma once
 
 #include <cstdint>
+#include <memory>
+#include <new>
 #include <string>
 #include <array>
+#include <type_traits>
+#include <utility>
 #include <vector>
 
 #include "geometry.hpp"
 
 namespace cutmg {
+
+// Allocator for the large host arrays whose every element the setup writes
+// itself, block by block in parallel: resize leaves the new elements
+// uninitialised instead of zero-filling them on one thread.
+template <class T>
+struct DefaultInitAllocator : std::allocator<T> {
+  template <class U>
+  struct rebind {
+    using other = DefaultInitAllocator<U>;
+  };
+  DefaultInitAllocator() noexcept = default;
+  template <class U>
+  DefaultInitAllocator(const DefaultInitAllocator<U>&) noexcept {}
+  template <class U>
+  void construct(U* p) noexcept(std::is_nothrow_default_constructible<U>::value) {
+    ::new (static_cast<void*>(p)) U;
+  }
+  template <class U, class... Args>
+  void construct(U* p, Args&&... args) {
+    ::new (static_cast<void*>(p)) U(std::forward<Args>(args)...);
+  }
+};
+using HostBlocks = std::vector<double, DefaultInitAllocator<double>>;
 
 constexpr uint8_t kFlagActive = 1;
 constexpr uint8_t kFlagCut = 2;
@@ -34,7 +61,7 @@ struct HostLevel {
   // cells
   std::vector<uint8_t> cflag;   // N^d: kFlagActive | kFlagCut
   std::vector<int> cut_id;      // N^d: row block in cutmat or -1
-  std::vector<double> cutmat;   // [n_cut][NB][NB] volume + Nitsche terms
+  HostBlocks cutmat;            // [n_cut][NB][NB] volume + Nitsche terms
   int64_t n_cut = 0, n_active = 0, n_ghost = 0;
   // nodes
   std::vector<uint8_t> nact;    // n^d: node belongs to an active cell
@@ -68,7 +95,7 @@ struct HostLevel {
   // (patch cell s, local node i) that belong to a patch DoF
   std::vector<int> cut_fo, cut_cell, cut_item_off;
   std::vector<uint8_t> cut_items;
-  std::vector<double> inv;        // explicit FP64 inverses A_j^{-1}, row-major
+  HostBlocks inv;                 // explicit FP64 inverses A_j^{-1}, row-major
   // algorithmic work per launch, used to report achieved FLOP/s and bytes:
   // per colour of the cut-patch solve and of the interior-patch step
   // {flops, scalars moved, index bytes moved}
