@@ -352,6 +352,10 @@ cf_status cf_host_interior_update(const cf_problem* pb, int level, double* h_W);
 /* Diagonal of A_level (host array of cf_level_n_dofs doubles, DoF order):
  * the point-Jacobi scaling of the Chebyshev smoother.  Levels >= 1. */
 cf_status cf_host_diagonal(const cf_problem* pb, int level, double* h_d);
+/* The coarsest-level solve's explicit inverse A_0^{-1} (Sec. 2.2: exact
+ * solve on the coarsest mesh): cf_level_n_dofs(pb, 0)^2 doubles, row-major,
+ * rows and columns in the level's DoF order.  Caller-owned host array. */
+cf_status cf_host_coarse_inverse(const cf_problem* pb, double* h_inv);
 /* Cut patch j: vertex, DoF count m, lattice indices of its m DoFs (h_nodes,
  * room for (2p+1)^d) and, if h_inv is not NULL, the m x m explicit inverse
  * of A[I_j, I_j] (row-major, in the order of h_nodes). */

@@ -235,6 +235,13 @@ class Problem:
         check(self._lib.cf_host_diagonal(self._h, level, out.ctypes.data_as(ctypes.c_void_p)))
         return out
 
+    def host_coarse_inverse(self):
+        """A_0^{-1} of the coarsest level (n_0 x n_0, DoF order)."""
+        n0 = self.n_dofs(0)
+        out = np.empty((n0, n0), dtype=np.float64)
+        check(self._lib.cf_host_coarse_inverse(self._h, out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
     def host_interior_update(self, level):
         """The level's dense interior-patch map W ((2p-1)^d x (2p+1)^d)."""
         ni, nc = (2 * self.degree - 1) ** self.dim, (2 * self.degree + 1) ** self.dim

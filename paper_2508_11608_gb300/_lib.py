@@ -22,6 +22,7 @@ EXPORTED = [
     "cf_vcycle", "cf_solve", "cf_solve_vcycle", "cf_solve_gmres", "cf_rhs_user", "cf_host_rhs_user", "cf_level_apply", "cf_level_colour_step", "cf_level_smooth",
     "cf_level_restrict", "cf_level_prolongate", "cf_coarse_solve", "cf_setup_host", "cf_host_rhs",
     "cf_host_cell_matrix", "cf_host_patch_counts", "cf_host_interior_update", "cf_host_diagonal", "cf_host_interior_patch", "cf_host_cut_patch",
+    "cf_host_coarse_inverse",
     "cf_launch_count", "cf_profile_start", "cf_profile_read", "cf_coarse_solve_noalloc",
     "cf_batch_create", "cf_batch_solve", "cf_batch_launch_count", "cf_batch_destroy",
     "cf_server_create", "cf_server_submit", "cf_server_run", "cf_server_result", "cf_server_stats",
@@ -116,6 +117,7 @@ def load():
     lib.cf_host_patch_counts.argtypes = [P, I, P, P]
     lib.cf_host_interior_update.argtypes = [P, I, P]
     lib.cf_host_diagonal.argtypes = [P, I, P]
+    lib.cf_host_coarse_inverse.argtypes = [P, P]
     lib.cf_host_interior_patch.argtypes = [P, I, ctypes.c_int64, P]
     lib.cf_host_cut_patch.argtypes = [P, I, ctypes.c_int64, P, P, P, P]
     lib.cf_coarse_solve_noalloc.argtypes = [P, P, P, V]

@@ -601,6 +601,13 @@ cf_status cf_host_diagonal(const cf_problem* pb, int level, double* h_d) {
   return CF_OK;
 }
 
+cf_status cf_host_coarse_inverse(const cf_problem* pb, double* h_inv) {
+  if (!pb || !h_inv) return fail(CF_EINVAL, "null handle or output");
+  const auto& A = pb->H.levels[0].coarse_inv;
+  std::copy(A.begin(), A.end(), h_inv);
+  return CF_OK;
+}
+
 cf_status cf_host_interior_update(const cf_problem* pb, int level, double* h_W) {
   if (bad_level(pb, level) || !h_W || level < 1) return fail(CF_EINVAL, "bad level or null output");
   const auto& W = pb->H.levels[level].Wcart;

@@ -222,3 +222,18 @@ def test_diagonal_matches_the_assembled_matrix(pair):
         d = pb.host_diagonal(l)
         do = H.levels[l].A.diagonal()
         assert np.abs(d - do).max() <= 1e-13 * np.abs(do).max()
+
+
+def test_coarse_inverse_inverts_the_assembled_coarsest_matrix(pair):
+    """The coarsest solve's explicit inverse (exact solve on the coarsest mesh,
+    Sec. 2.2) against the oracle's assembled A_0: A_0 X = I and X equal to the
+    LAPACK inverse, both within rounding amplified by the condition number,
+    and X exactly symmetric (the library fills both triangles from one)."""
+    pb, H, _ = pair
+    X = pb.host_coarse_inverse()
+    A0 = H.levels[0].A.toarray()
+    ref = np.linalg.inv(A0)
+    tol = 1e-14 * np.linalg.cond(A0)
+    assert np.array_equal(X, X.T)
+    assert np.abs(A0 @ X - np.eye(len(A0))).max() <= tol
+    assert np.abs(X - ref).max() <= tol * np.abs(ref).max()
