@@ -37,7 +37,8 @@ int ipow(int b, int e) {
 //      block of BS rows per pass over U;
 //   3. A^{-1} = W W^T, row i accumulated over k = i..n-1 as rank-one updates
 //      with column k of W, then mirrored.
-// Every entry's sum runs in ascending index order, whatever the thread
+// Each pass applies four consecutive updates per sweep over a row where it
+// can.  Every entry's sum runs in ascending index order, whatever the thread
 // count; large matrices (the coarsest-level operator) are split over threads.
 void spd_inverse(int n, double* A) {
   constexpr int BS = 16;
