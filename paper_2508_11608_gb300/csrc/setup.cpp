@@ -358,6 +358,36 @@ void cut_cell_matrix(const RefTables& R, const CutRule& rule, const double* lo, 
     for (int j = 0; j < i; ++j) K[(size_t)i * NB + j] = K[(size_t)j * NB + i];
 }
 
+// right-hand side terms of one cut cell from its quadrature rule (volume:
+// f phi_j; Nitsche data: g (gamma_D / h phi_j - dphi_j/dn)), accumulated into
+// loc (zeroed here) point by point in rule order
+void cut_cell_rhs(const RefTables& R, const CutRule& rule, const double* lo, double h, double gamma_D,
+                  const std::function<double(const double*)>& fsrc,
+                  const std::function<double(const double*)>& gdir, double* loc) {
+  const int NB = R.NB, d = R.d;
+  std::vector<double> v(NB), gr(NB * d);
+  for (int j = 0; j < NB; ++j) loc[j] = 0.0;
+  for (const auto& nd : rule.vol) {
+    double xi[3] = {0, 0, 0};
+    for (int k = 0; k < d; ++k) xi[k] = (nd.x[k] - lo[k]) / h;
+    R.values(xi, v.data());
+    double fx = fsrc(nd.x) * nd.w;
+    for (int j = 0; j < NB; ++j) loc[j] += v[j] * fx;
+  }
+  for (size_t s2 = 0; s2 < rule.surf.size(); ++s2) {
+    const auto& nd = rule.surf[s2];
+    double xi[3] = {0, 0, 0};
+    for (int k = 0; k < d; ++k) xi[k] = (nd.x[k] - lo[k]) / h;
+    R.eval(xi, h, v.data(), gr.data());
+    double gx = gdir(nd.x) * nd.w;
+    for (int j = 0; j < NB; ++j) {
+      double dn = 0.0;
+      for (int k = 0; k < d; ++k) dn += rule.normal[s2][k] * gr[j * d + k];
+      loc[j] += gx * (gamma_D / h * v[j] - dn);
+    }
+  }
+}
+
 // cells containing lattice coordinate i along one direction
 int cells_of(int i, int p, int N, int* c, int* loc) {
   int a = i / p, r = i - a * p, m = 0;
@@ -370,7 +400,12 @@ int cells_of(int i, int p, int N, int* c, int* loc) {
   return m;
 }
 
-void build_level(const SetupParams& prm, const RefTables& R, int N, HostLevel& L) {
+// Optional: with cut_rhs, the cut cells' right-hand side terms for source
+// fsrc and Dirichlet data gdir are formed from the same quadrature rules
+// (n_cut x NB, in cut-cell order).
+using PointFn = std::function<double(const double*)>;
+void build_level(const SetupParams& prm, const RefTables& R, int N, HostLevel& L, const PointFn* fsrc = nullptr,
+                 const PointFn* gdir = nullptr, std::vector<double>* cut_rhs = nullptr) {
   const int d = prm.dim, p = prm.degree, NB = R.NB;
   L.d = d;
   L.p = p;
@@ -411,6 +446,7 @@ void build_level(const SetupParams& prm, const RefTables& R, int N, HostLevel& L
   }
   L.n_cut = (int64_t)cut_cells.size();
   L.cutmat.resize((size_t)L.n_cut * NB * NB);  // every block written below
+  if (cut_rhs) cut_rhs->assign((size_t)L.n_cut * NB, 0.0);
   CutQuadrature Q(prm.ls, prm.quad_q);
 #pragma omp parallel for schedule(dynamic, 8)
   for (int64_t i = 0; i < L.n_cut; ++i) {
@@ -423,6 +459,7 @@ void build_level(const SetupParams& prm, const RefTables& R, int N, HostLevel& L
     for (int k = 0; k < d; ++k) hi[k] = lo[k] + h;
     CutRule rule = Q.cell(lo, hi);
     cut_cell_matrix(R, rule, lo, h, prm.gamma_D, &L.cutmat[(size_t)i * NB * NB]);
+    if (cut_rhs) cut_cell_rhs(R, rule, lo, h, prm.gamma_D, *fsrc, *gdir, &(*cut_rhs)[(size_t)i * NB]);
   }
   // uncut stiffness, Kronecker form of 1D reference matrices
   L.Kref.assign(NB * NB, 0.0);
@@ -1279,7 +1316,7 @@ void tensor_contract(int d, int p, int q, const double* Lt, const double* F, dou
 
 void build_rhs(const SetupParams& prm, const RefTables& R, const HostLevel& L, std::vector<double>& b,
                const std::function<double(const double*)>& fsrc, const std::function<double(const double*)>& gdir,
-               bool parallel) {
+               bool parallel, const std::vector<double>* cut_rhs = nullptr) {
   const int d = L.d, p = L.p, N = L.N, n = L.n, NB = R.NB, q = prm.quad_q;
   const double h = L.h;
   std::vector<int64_t> map((size_t)ipow(n, d), -1);
@@ -1315,7 +1352,6 @@ void build_rhs(const SetupParams& prm, const RefTables& R, const HostLevel& L, s
         lo[k] = prm.lo + h * ci[k];
         hi[k] = lo[k] + h;
       }
-      std::vector<double> v(NB), gr(NB * d);
       std::vector<double> Fw((size_t)nq + 2 * ipow(std::max(q, p + 1), d));
       double* loc = &locs[(size_t)(ic - c0) * NB];
       for (int j = 0; j < NB; ++j) loc[j] = 0.0;
@@ -1334,27 +1370,11 @@ void build_rhs(const SetupParams& prm, const RefTables& R, const HostLevel& L, s
           F[iq] = fsrc(x) * w * hd;
         }
         tensor_contract(d, p, q, Lt.data(), F, loc, F + nq);
+      } else if (cut_rhs) {
+        const double* src = &(*cut_rhs)[(size_t)L.cut_id[c] * NB];
+        for (int j = 0; j < NB; ++j) loc[j] = src[j];
       } else {
-        CutRule rule = Q.cell(lo, hi);
-        for (const auto& nd : rule.vol) {
-          double xi[3] = {0, 0, 0};
-          for (int k = 0; k < d; ++k) xi[k] = (nd.x[k] - lo[k]) / h;
-          R.values(xi, v.data());
-          double fx = fsrc(nd.x) * nd.w;
-          for (int j = 0; j < NB; ++j) loc[j] += v[j] * fx;
-        }
-        for (size_t s2 = 0; s2 < rule.surf.size(); ++s2) {
-          const auto& nd = rule.surf[s2];
-          double xi[3] = {0, 0, 0};
-          for (int k = 0; k < d; ++k) xi[k] = (nd.x[k] - lo[k]) / h;
-          R.eval(xi, h, v.data(), gr.data());
-          double gx = gdir(nd.x) * nd.w;
-          for (int j = 0; j < NB; ++j) {
-            double dn = 0.0;
-            for (int k = 0; k < d; ++k) dn += rule.normal[s2][k] * gr[j * d + k];
-            loc[j] += gx * (prm.gamma_D / h * v[j] - dn);
-          }
-        }
+        cut_cell_rhs(R, Q.cell(lo, hi), lo, h, prm.gamma_D, fsrc, gdir, loc);
       }
     }
     for (int64_t ic = c0; ic < c1; ++ic) {
@@ -1393,9 +1413,21 @@ void build_hierarchy(const SetupParams& prm, Hierarchy& H) {
   H.prm = prm;
   H.levels.assign(prm.n_levels, HostLevel());
   RefTables R(prm.degree, prm.dim);
+  // manufactured data of the workloads: u = prod sin(pi x_k), f = d pi^2 u, g = u
+  const int d = prm.dim;
+  auto uex = [d](const double* x) {
+    double u = 1.0;
+    for (int k = 0; k < d; ++k) u *= std::sin(M_PI * x[k]);
+    return u;
+  };
+  const PointFn fman = [&](const double* x) { return d * M_PI * M_PI * uex(x); }, gman = uex;
+  std::vector<double> cut_rhs;  // finest level: cut cells' terms, formed with their matrices
   for (int l = 0; l < prm.n_levels; ++l) {
     int Nl = prm.n_cells >> (prm.n_levels - 1 - l);
-    build_level(prm, R, Nl, H.levels[l]);
+    if (l == prm.n_levels - 1)
+      build_level(prm, R, Nl, H.levels[l], &fman, &gman, &cut_rhs);
+    else
+      build_level(prm, R, Nl, H.levels[l]);
     if (H.levels[l].dofs.empty()) throw std::invalid_argument("level without active cells");
     if (l > 0) {
       build_transfer(R, H.levels[l - 1].N, H.levels[l]);
@@ -1422,15 +1454,7 @@ void build_hierarchy(const SetupParams& prm, Hierarchy& H) {
   build_coarse(R, H.levels[0]);
   if (prm.smoother == 1)
     for (size_t l = 1; l < H.levels.size(); ++l) build_diag(R, H.levels[l]);
-  // manufactured data of the workloads: u = prod sin(pi x_k), f = d pi^2 u, g = u
-  const int d = prm.dim;
-  auto uex = [d](const double* x) {
-    double u = 1.0;
-    for (int k = 0; k < d; ++k) u *= std::sin(M_PI * x[k]);
-    return u;
-  };
-  build_rhs(prm, R, H.levels.back(), H.rhs, [&](const double* x) { return d * M_PI * M_PI * uex(x); }, uex,
-            true);
+  build_rhs(prm, R, H.levels.back(), H.rhs, fman, gman, true, &cut_rhs);
 }
 
 void build_rhs_user(const Hierarchy& H, double (*f)(const double*, void*), double (*g)(const double*, void*),
