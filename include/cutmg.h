@@ -273,7 +273,11 @@ void cf_batch_destroy(cf_batch* bt);
 
 /* ---- served form -------------------------------------------------------------
  * A stream of solve requests with arrival times, solved with continuous
- * batching: a host thread builds each hierarchy after its arrival; a prepared
+ * batching: a host thread builds each hierarchy after its arrival (up to four
+ * at once; a request whose params leave setup_threads at 0 is built on the
+ * host cores no other running setup holds, at least a quarter of them, so a
+ * request that arrives alone uses them all; the result does not depend on
+ * the thread count); a prepared
  * request is admitted (FIFO) when its estimated device footprint fits the HBM
  * budget next to the resident problems and an active slot is free; every tick
  * runs one CG iteration of all active problems with the batched kernels;
