@@ -237,3 +237,27 @@ def test_coarse_inverse_inverts_the_assembled_coarsest_matrix(pair):
     assert np.array_equal(X, X.T)
     assert np.abs(A0 @ X - np.eye(len(A0))).max() <= tol
     assert np.abs(X - ref).max() <= tol * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("name", ["ball_q2", "torus_q2", "disk_q3"])
+def test_setup_is_the_same_on_any_number_of_threads(name):
+    """The served form builds a request on however many host cores are free;
+    every array of the setup must come out bit for bit the same."""
+    k = CASES[name]
+    a, b = (cm.Problem(k["dim"], k["N"], k["L"], k["p"], levelset=k["ls"], host_only=True, setup_threads=t)
+            for t in (1, 3))
+    assert np.array_equal(a.host_rhs(), b.host_rhs())
+    assert np.array_equal(a.host_coarse_inverse(), b.host_coarse_inverse())
+    for l in range(1, k["L"]):
+        ia, ca = a.host_patches(l)
+        ib, cb = b.host_patches(l)
+        assert ia == ib and len(ca) == len(cb)
+        for (va, na, Xa), (vb, nb, Xb) in zip(ca, cb):
+            assert va == vb and np.array_equal(na, nb) and np.array_equal(Xa, Xb)
+    L = k["L"] - 1
+    for c in range(k["N"] ** k["dim"]):
+        try:
+            Ka = a.host_cell_matrix(L, c)
+        except cm.CutmgError:  # inactive cell
+            continue
+        assert np.array_equal(Ka, b.host_cell_matrix(L, c))
