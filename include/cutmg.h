@@ -130,8 +130,10 @@ typedef struct cf_problem cf_problem;
 
 /* Build the hierarchy: classification, cut-cell quadrature, cell and patch
  * matrices (host, FP64), upload to the current device.  Blocking.
- * Errors: CF_EINVAL (bad sizes, degree, kind), CF_EUNSUPPORTED (dim 3 with
- * degree 3), CF_ENOMEM, CF_ECUDA. */
+ * Errors: CF_EINVAL (bad sizes, degree, kind; a domain that misses the mesh
+ * or whose boundary crosses no cell, which leaves no Dirichlet condition; a
+ * coarsest level above 12,000 DoFs), CF_EUNSUPPORTED (dim 3 with degree 3),
+ * CF_ENOMEM, CF_ECUDA. */
 cf_status cf_setup(const cf_mesh* mesh, const cf_levelset* ls, int degree,
                    const cf_params* params, cf_problem** out);
 void cf_destroy(cf_problem* pb);

@@ -1448,6 +1448,11 @@ void build_hierarchy(const SetupParams& prm, Hierarchy& H) {
       }
     }
   }
+  // without a cut cell there are no Nitsche terms: the operator is the pure
+  // Neumann stiffness on the active cells (constants in its kernel)
+  if (H.levels.back().n_cut == 0)
+    throw std::invalid_argument("no cut cell on the finest level: the domain's boundary does not cross the mesh, "
+                                "so the Nitsche-Dirichlet problem has no boundary condition");
   if (H.levels[0].dofs.size() > 12000)
     throw std::invalid_argument("the coarsest level has " + std::to_string(H.levels[0].dofs.size()) +
                                 " DoFs (dense exact solve); use more levels");

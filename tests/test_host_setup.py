@@ -35,6 +35,8 @@ CASES = {
                                                    "axes": [0.7, 0.5, 0.45], "rot": _rot(0.3, 0.5)}),
     "torus_q2": dict(dim=3, N=16, L=2, p=2, ls={"kind": "torus", "center": [0.02, 0.01, -0.03],
                                                 "rot": _rot(0.4, 0.7), "major": 0.6, "minor": 0.2}),
+    # degenerate: a disk smaller than a cell, every patch cut, no interior one
+    "tiny_q2": dict(dim=2, N=16, L=2, p=2, ls={"kind": "sphere", "center": [0.01, 0.02], "radius": 0.05}),
     # user level sets through point callbacks (sampled bounds on both sides)
     "callback_q2": dict(dim=2, N=32, L=3, p=2, ls=superellipse([0.03, -0.02], [0.7, 0.55])),
     "callback3d_q2": dict(dim=3, N=8, L=2, p=2, ls=superellipse([0.03, -0.02, 0.01], [0.7, 0.55, 0.6])),
@@ -163,6 +165,18 @@ def test_invalid_arguments_are_rejected():
         cm.Problem(2, 12, 4, 2, center=[0, 0], radius=0.5, host_only=True)  # 12 not divisible by 8
     with pytest.raises(cm.CutmgError):
         cm.Problem(2, 16, 2, 2, center=[0, 0], radius=-1.0, host_only=True)
+
+
+def test_degenerate_domains_are_rejected():
+    # no active cell: the domain misses the mesh
+    with pytest.raises(cm.CutmgError, match="without active cells"):
+        cm.Problem(2, 16, 2, 2, center=[5.0, 5.0], radius=0.5, host_only=True)
+    # no cut cell: no Nitsche terms, the operator would be singular
+    with pytest.raises(cm.CutmgError, match="no cut cell"):
+        cm.Problem(2, 16, 2, 2, center=[0.0, 0.0], radius=10.0, host_only=True)
+    # the coarsest level is solved densely: its size is bounded
+    with pytest.raises(cm.CutmgError, match="coarsest level has 62351 DoFs"):
+        cm.Problem(3, 32, 1, 2, center=[0.05, 0.03, 0.02], radius=0.7, host_only=True)
 
 
 def test_footprint_estimate_grows_with_the_mesh():
