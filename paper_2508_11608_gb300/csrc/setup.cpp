@@ -400,6 +400,618 @@ int cells_of(int i, int p, int N, int* c, int* loc) {
   return m;
 }
 
+// flag of cell c (cell coordinates) of a level; 0 outside the mesh
+uint8_t cell_flag(const HostLevel& L, const int* c) {
+  int64_t f = 0, st = 1;
+  for (int k = 0; k < L.d; ++k) {
+    if (c[k] < 0 || c[k] >= L.N) return 0;
+    f += (int64_t)c[k] * st;
+    st *= L.N;
+  }
+  return L.cflag[f];
+}
+
+// "plain" cell: active, uncut, no cut face-neighbour (no ghost face)
+bool plain_cell(const HostLevel& L, const int* c) {
+  uint8_t f = cell_flag(L, c);
+  if (!(f & kFlagActive) || (f & kFlagCut)) return false;
+  for (int k = 0; k < L.d; ++k)
+    for (int s = -1; s <= 1; s += 2) {
+      int cj[3] = {c[0], c[1], c[2]};
+      cj[k] += s;
+      if (cell_flag(L, cj) & kFlagCut) return false;
+    }
+  return true;
+}
+
+// Interior patches (every cell of the patch plain): the two-cell 1D mass and
+// stiffness rows, the fast-diagonalisation eigenpairs and the level's dense
+// interior-patch map.
+void interior_patch_tables(const RefTables& R, HostLevel& L) {
+  const int d = L.d, p = L.p;
+  const double h = L.h;
+  const int C = 2 * p + 1, M = 2 * p - 1;
+  std::vector<double> Mb(C * C, 0.0), Kb(C * C, 0.0);
+  for (int s = 0; s < 2; ++s)
+    for (int a = 0; a <= p; ++a)
+      for (int b = 0; b <= p; ++b) {
+        Mb[(s * p + a) * C + s * p + b] += R.M1[a * (p + 1) + b] * h;
+        Kb[(s * p + a) * C + s * p + b] += R.K1[a * (p + 1) + b] / h;
+      }
+  L.Mr.assign(M * C, 0.0);
+  L.Kr.assign(M * C, 0.0);
+  for (int i = 0; i < M; ++i)
+    for (int j = 0; j < C; ++j) {
+      L.Mr[i * C + j] = Mb[(i + 1) * C + j];
+      L.Kr[i * C + j] = Kb[(i + 1) * C + j];
+    }
+  // K_I s = lam M_I s with S^T M_I S = I: M_I = G G^T, Jacobi on G^-1 K_I G^-T
+  std::vector<double> MI(M * M), KI(M * M), G(M * M, 0.0), Gi(M * M, 0.0);
+  for (int i = 0; i < M; ++i)
+    for (int j = 0; j < M; ++j) {
+      MI[i * M + j] = L.Mr[i * C + j + 1];
+      KI[i * M + j] = L.Kr[i * C + j + 1];
+    }
+  for (int j = 0; j < M; ++j) {
+    double s = MI[j * M + j];
+    for (int k = 0; k < j; ++k) s -= G[j * M + k] * G[j * M + k];
+    G[j * M + j] = std::sqrt(s);
+    for (int i = j + 1; i < M; ++i) {
+      double t = MI[i * M + j];
+      for (int k = 0; k < j; ++k) t -= G[i * M + k] * G[j * M + k];
+      G[i * M + j] = t / G[j * M + j];
+    }
+  }
+  for (int c = 0; c < M; ++c)
+    for (int i = c; i < M; ++i) {
+      double t = (i == c) ? 1.0 : 0.0;
+      for (int k = c; k < i; ++k) t -= G[i * M + k] * Gi[k * M + c];
+      Gi[i * M + c] = t / G[i * M + i];
+    }
+  std::vector<double> Cm(M * M, 0.0), Qv, lam;
+  for (int i = 0; i < M; ++i)
+    for (int j = 0; j < M; ++j) {
+      double t = 0.0;
+      for (int a = 0; a < M; ++a)
+        for (int b = 0; b < M; ++b) t += Gi[i * M + a] * KI[a * M + b] * Gi[j * M + b];
+      Cm[i * M + j] = t;
+    }
+  jacobi_eigen(M, Cm, Qv, lam);
+  L.S.assign(M * M, 0.0);
+  for (int i = 0; i < M; ++i)
+    for (int j = 0; j < M; ++j) {
+      double t = 0.0;
+      for (int a = 0; a < M; ++a) t += Gi[a * M + i] * Qv[a * M + j];  // G^-T Q
+      L.S[i * M + j] = t;
+    }
+  L.lam = lam;
+  // The exact local solve of an interior patch as one dense map per level:
+  // x_I <- A_I^{-1} b_I - A_I^{-1} A_{I,B} x_B over the closure; columns in
+  // closure order (first coordinate fastest), b at interior columns and x
+  // at boundary columns; rows in interior order.
+  {
+    const int NI = ipow(M, d), NC = ipow(C, d);
+    std::vector<double> AIcl((size_t)NI * NC, 0.0);
+    for (int i = 0; i < NI; ++i) {
+      int ii[3] = {0, 0, 0}, t = i;
+      for (int k = 0; k < d; ++k) {
+        ii[k] = t % M;
+        t /= M;
+      }
+      for (int kc = 0; kc < NC; ++kc) {
+        int cc[3] = {0, 0, 0}, u = kc;
+        for (int k = 0; k < d; ++k) {
+          cc[k] = u % C;
+          u /= C;
+        }
+        double v = 0.0;
+        for (int a = 0; a < d; ++a) {  // stiffness along a, mass along the others
+          double f = 1.0;
+          for (int k = 0; k < d; ++k) f *= (k == a ? L.Kr[ii[k] * C + cc[k]] : L.Mr[ii[k] * C + cc[k]]);
+          v += f;
+        }
+        AIcl[(size_t)i * NC + kc] = v;
+      }
+    }
+    auto closure_of = [&](int i) {
+      int kc = 0, st = 1, t = i;
+      for (int k = 0; k < d; ++k) {
+        kc += (t % M + 1) * st;
+        t /= M;
+        st *= C;
+      }
+      return kc;
+    };
+    std::vector<double> AIi((size_t)NI * NI);
+    for (int i = 0; i < NI; ++i)
+      for (int j = 0; j < NI; ++j) AIi[(size_t)i * NI + j] = AIcl[(size_t)i * NC + closure_of(j)];
+    spd_inverse(NI, AIi.data());
+    std::vector<int> interior_index(NC, -1);
+    for (int j = 0; j < NI; ++j) interior_index[closure_of(j)] = j;
+    L.Wcart.assign((size_t)NI * NC, 0.0);
+    for (int i = 0; i < NI; ++i)
+      for (int kc = 0; kc < NC; ++kc) {
+        double w;
+        if (interior_index[kc] >= 0) {
+          w = AIi[(size_t)i * NI + interior_index[kc]];
+        } else {
+          w = 0.0;
+          for (int j = 0; j < NI; ++j) w -= AIi[(size_t)i * NI + j] * AIcl[(size_t)j * NC + kc];
+        }
+        L.Wcart[(size_t)i * NC + kc] = w;
+      }
+  }
+}
+
+// Patch vertices of a level by colour: Cartesian (every patch cell plain)
+// and cut patches, each list in vertex order.
+void patch_vertex_sets(HostLevel& L) {
+  const int d = L.d, N = L.N, np = N + 1, ncol = 1 << d;
+  auto cflag_at = [&](const int* c) { return cell_flag(L, c); };
+  auto plain = [&](const int* c) { return plain_cell(L, c); };
+  const int64_t nvert = (int64_t)ipow(np, d);
+  std::vector<std::vector<int>> cart(ncol), cutv(ncol);
+  // per vertex: -1 (no active cell around it), else colour + 8 if Cartesian
+  std::vector<int8_t> vkind(nvert);
+#pragma omp parallel for schedule(static)
+  for (int64_t q = 0; q < nvert; ++q) {
+    int v[3] = {0, 0, 0};
+    int64_t t = q;
+    for (int k = 0; k < d; ++k) {
+      v[k] = (int)(t % np);
+      t /= np;
+    }
+    bool any = false, cartesian = true;
+    for (int s = 0; s < (1 << d); ++s) {
+      int c[3] = {0, 0, 0};
+      for (int k = 0; k < d; ++k) c[k] = v[k] - 1 + ((s >> k) & 1);
+      if (cflag_at(c) & kFlagActive) any = true;
+      if (!plain(c)) cartesian = false;
+    }
+    int col = 0;
+    for (int k = 0; k < d; ++k) col |= (v[k] & 1) << k;
+    vkind[q] = any ? (int8_t)(col + (cartesian ? 8 : 0)) : (int8_t)-1;
+  }
+  for (int64_t q = 0; q < nvert; ++q) {
+    if (vkind[q] < 0) continue;
+    const int col = vkind[q] & 7;
+    ((vkind[q] & 8) ? cart : cutv)[col].push_back((int)q);
+  }
+  L.cart_start.assign(ncol + 1, 0);
+  L.cut_start.assign(ncol + 1, 0);
+  for (int c = 0; c < ncol; ++c) {
+    L.cart_vert.insert(L.cart_vert.end(), cart[c].begin(), cart[c].end());
+    L.cut_vert.insert(L.cut_vert.end(), cutv[c].begin(), cutv[c].end());
+    L.cart_start[c + 1] = (int)L.cart_vert.size();
+    L.cut_start[c + 1] = (int)L.cut_vert.size();
+  }
+}
+
+// Cut patches: their DoFs (closure nodes all of whose active cells are patch
+// cells), member and inverse offsets, and the inverse storage.
+void cut_patch_members(HostLevel& L) {
+  const int d = L.d, p = L.p, N = L.N, n = L.n;
+  const int np = N + 1, C = 2 * p + 1, ncol = 1 << d, NCL = ipow(C, d);
+  const int64_t ncp = (int64_t)L.cut_vert.size();
+  auto cflag_at = [&](const int* c) { return cell_flag(L, c); };
+  // members: closure nodes all of whose active cells are patch cells
+  std::vector<std::vector<uint16_t>> mem(ncp);
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t j = 0; j < ncp; ++j) {
+    int v[3] = {0, 0, 0};
+    int64_t t = L.cut_vert[j];
+    for (int k = 0; k < d; ++k) {
+      v[k] = (int)(t % np);
+      t /= np;
+    }
+    for (int o = 0; o < NCL; ++o) {
+      int oc[3] = {0, 0, 0}, li[3] = {0, 0, 0}, u = o;
+      bool valid = true;
+      for (int k = 0; k < d; ++k) {
+        oc[k] = u % C;
+        u /= C;
+        li[k] = p * (v[k] - 1) + oc[k];
+        if (li[k] < 0 || li[k] >= n) valid = false;
+      }
+      if (!valid) continue;
+      int cc[3][2], lc[3][2], nc[3] = {1, 1, 1};
+      for (int k = 0; k < d; ++k) nc[k] = cells_of(li[k], p, N, cc[k], lc[k]);
+      bool inside = false, outside = false;
+      int tot = nc[0] * nc[1] * nc[2];
+      for (int s = 0; s < tot; ++s) {
+        int c[3] = {0, 0, 0}, r = s;
+        bool in_patch = true;
+        for (int k = 0; k < d; ++k) {
+          c[k] = cc[k][r % nc[k]];
+          r /= nc[k];
+          if (c[k] != v[k] - 1 && c[k] != v[k]) in_patch = false;
+        }
+        if (cflag_at(c) & kFlagActive) (in_patch ? inside : outside) = true;
+      }
+      if (inside && !outside) mem[j].push_back((uint16_t)o);
+    }
+  }
+  L.cut_n.resize(ncp);
+  L.cut_moff.resize(ncp);
+  L.cut_ioff.resize(ncp);
+  int64_t moff = 0, ioff = 0;
+  L.cut_maxm2.assign(ncol, 0);
+  for (int64_t j = 0; j < ncp; ++j) {
+    int m = (int)mem[j].size();
+    L.cut_n[j] = m;
+    L.cut_moff[j] = (int)moff;
+    L.cut_ioff[j] = ioff;
+    moff += m;
+    // every inverse starts on a 16-byte boundary in FP64 and FP32 (TMA bulk copies)
+    ioff += ((int64_t)m * m + 3) / 4 * 4;
+    for (int col = 0; col < ncol; ++col)
+      if (j >= L.cut_start[col] && j < L.cut_start[col + 1]) L.cut_maxm2[col] = std::max(L.cut_maxm2[col], m * m);
+    L.members.insert(L.members.end(), mem[j].begin(), mem[j].end());
+    int v[3] = {0, 0, 0};
+    int64_t t = L.cut_vert[j];
+    for (int k = 0; k < d; ++k) {
+      v[k] = (int)(t % np);
+      t /= np;
+    }
+    for (int e = 0; e < m; ++e) {
+      int o = mem[j][e];
+      int64_t node = 0, st = 1;
+      for (int k = 0; k < d; ++k) {
+        node += (int64_t)(p * (v[k] - 1) + o % C) * st;
+        o /= C;
+        st *= n;
+      }
+      L.member_node.push_back((int)node);
+    }
+  }
+  L.inv.resize(ioff);  // every slot zeroed and filled by its patch below
+}
+
+// Ghost-face entries of every cut-patch DoF (the faces whose two cells
+// contain the node), and per colour the faces these rows need.  Entries
+// are counted, then written at their offsets, member by member in
+// parallel (the lists are the same for every thread count).
+void cut_patch_face_entries(HostLevel& L) {
+  const int d = L.d, p = L.p, N = L.N, n = L.n, ncol = 1 << d;
+  const int NTf = ipow(p + 1, d - 1);
+  const int64_t nmem = (int64_t)L.member_node.size();
+  // entry = ((face id * NTf) + tangential node) * 8 + node along the normal
+  auto entries = [&](int64_t gm, auto&& emit) {
+    int64_t t = L.member_node[gm];
+    int idx[3] = {0, 0, 0};
+    for (int k = 0; k < d; ++k) {
+      idx[k] = (int)(t % n);
+      t /= n;
+    }
+    int cc[3][2], lcl[3][2], nopt[3] = {1, 1, 1};
+    for (int k = 0; k < d; ++k) nopt[k] = cells_of(idx[k], p, N, cc[k], lcl[k]);
+    for (int k = 0; k < d; ++k) {
+      const int a = idx[k] / p, r = idx[k] - a * p;
+      int Llo = (r == 0) ? a - 2 : a - 1, Lhi = a;
+      Llo = std::max(Llo, 0);
+      Lhi = std::min(Lhi, N - 2);
+      int td[2] = {0, 0}, q = 0;
+      for (int jj = 0; jj < d; ++jj)
+        if (jj != k) td[q++] = jj;
+      const int n0 = nopt[td[0]], n1 = (d == 3) ? nopt[td[1]] : 1;
+      for (int Lk = Llo; Lk <= Lhi; ++Lk)
+        for (int u0 = 0; u0 < n0; ++u0)
+          for (int u1 = 0; u1 < n1; ++u1) {
+            int c[3] = {0, 0, 0};
+            c[k] = Lk;
+            c[td[0]] = cc[td[0]][u0];
+            if (d == 3) c[td[1]] = cc[td[1]][u1];
+            int64_t cell = c[0] + (int64_t)N * (c[1] + (d == 3 ? (int64_t)N * c[2] : 0));
+            const int id = L.face_id[(size_t)cell * d + k];
+            if (id < 0) continue;
+            int tt = idx[td[0]] - p * c[td[0]];
+            if (d == 3) tt += (p + 1) * (idx[td[1]] - p * c[td[1]]);
+            emit(((id * NTf) + tt) * 8 + (idx[k] - p * Lk), id);
+          }
+    }
+  };
+  std::vector<int> cnt(nmem, 0);
+#pragma omp parallel for schedule(dynamic, 256)
+  for (int64_t gm = 0; gm < nmem; ++gm) {
+    int c = 0;
+    entries(gm, [&](int, int) { ++c; });
+    cnt[gm] = c;
+  }
+  L.fofs.assign(nmem + 1, 0);
+  for (int64_t gm = 0; gm < nmem; ++gm) L.fofs[gm + 1] = L.fofs[gm] + cnt[gm];
+  L.fent.assign((size_t)L.fofs[nmem], 0);
+  // colour of every member (the colour of its patch)
+  std::vector<uint8_t> mcol(nmem);
+  for (int col = 0; col < ncol; ++col)
+    for (int j = L.cut_start[col]; j < L.cut_start[col + 1]; ++j)
+      std::fill(mcol.begin() + L.cut_moff[j], mcol.begin() + L.cut_moff[j] + L.cut_n[j], (uint8_t)col);
+  // need[col][face]: a row of the colour reads the face's moments
+  const size_t nf = L.ghost_faces.size();
+  std::vector<uint8_t> need((size_t)ncol * nf, 0);
+#pragma omp parallel for schedule(dynamic, 256)
+  for (int64_t gm = 0; gm < nmem; ++gm) {
+    int o = L.fofs[gm];
+    uint8_t* nc = &need[(size_t)mcol[gm] * nf];
+    entries(gm, [&](int v, int id) {
+      L.fent[o++] = v;
+#pragma omp atomic write
+      nc[id] = 1;
+    });
+  }
+  L.cf_start.assign(ncol + 1, 0);
+  for (int col = 0; col < ncol; ++col) {
+    const uint8_t* nc = &need[(size_t)col * nf];
+    for (size_t f = 0; f < nf; ++f)
+      if (nc[f]) L.cfaces.push_back((int)f);
+    L.cf_start[col + 1] = (int)L.cfaces.size();
+  }
+}
+
+// Per cut patch, what its block loads up front: the range of its
+// ghost-face entries, the element matrix of each patch cell and the
+// (cell, local node) pairs whose rows it forms (node a patch DoF)
+void cut_patch_rows(HostLevel& L) {
+  const int d = L.d, p = L.p, N = L.N, NB = ipow(p + 1, d);
+  const int np = N + 1, C = 2 * p + 1, ncol = 1 << d, NCL = ipow(C, d);
+  const int64_t ncp = (int64_t)L.cut_vert.size();
+  auto cflag_at = [&](const int* c) { return cell_flag(L, c); };
+  const int NCELL = 1 << d;
+  L.cut_fo.resize(ncp + 1);
+  L.cut_cell.assign((size_t)ncp * NCELL, -2);
+  L.cut_item_off.assign(ncp + 1, 0);
+  L.cut_items.clear();
+  // closure offset of local node jj of patch cell sc
+  std::vector<int> cell_node((size_t)NCELL * NB);
+  for (int sc = 0; sc < NCELL; ++sc)
+    for (int jj = 0; jj < NB; ++jj) {
+      int o = 0, ost = 1, u = jj;
+      for (int k = 0; k < d; ++k) {
+        o += (p * ((sc >> k) & 1) + u % (p + 1)) * ost;
+        u /= (p + 1);
+        ost *= C;
+      }
+      cell_node[(size_t)sc * NB + jj] = o;
+    }
+  // per patch (in parallel): its cells, then its items counted and written
+  // at their offsets
+  auto patch_items = [&](int64_t j, std::vector<char>& is_mem, auto&& emit) {
+    int v[3] = {0, 0, 0};
+    int64_t t = L.cut_vert[j];
+    for (int k = 0; k < d; ++k) {
+      v[k] = (int)(t % np);
+      t /= np;
+    }
+    std::fill(is_mem.begin(), is_mem.end(), 0);
+    for (int e = 0; e < L.cut_n[j]; ++e) is_mem[L.members[L.cut_moff[j] + e]] = 1;
+    for (int sc = 0; sc < NCELL; ++sc) {
+      int c[3] = {0, 0, 0};
+      for (int k = 0; k < d; ++k) c[k] = v[k] - 1 + ((sc >> k) & 1);
+      const uint8_t f = cflag_at(c);
+      if (!(f & kFlagActive)) continue;
+      const int64_t cell = c[0] + (int64_t)N * (c[1] + (d == 3 ? (int64_t)N * c[2] : 0));
+      L.cut_cell[(size_t)j * NCELL + sc] = (f & kFlagCut) ? L.cut_id[cell] : -1;
+      for (int jj = 0; jj < NB; ++jj)
+        if (is_mem[cell_node[(size_t)sc * NB + jj]]) emit((uint8_t)(sc * NB + jj));
+    }
+  };
+#pragma omp parallel
+  {
+    std::vector<char> is_mem(NCL);
+#pragma omp for schedule(dynamic, 64)
+    for (int64_t j = 0; j < ncp; ++j) {
+      L.cut_fo[j] = L.fofs[L.cut_moff[j]];
+      int c = 0;
+      patch_items(j, is_mem, [&](uint8_t) { ++c; });
+      L.cut_item_off[j + 1] = c;
+    }
+  }
+  for (int64_t j = 0; j < ncp; ++j) L.cut_item_off[j + 1] += L.cut_item_off[j];
+  L.cut_items.assign((size_t)L.cut_item_off[ncp], 0);
+#pragma omp parallel
+  {
+    std::vector<char> is_mem(NCL);
+#pragma omp for schedule(dynamic, 64)
+    for (int64_t j = 0; j < ncp; ++j) {
+      int o = L.cut_item_off[j];
+      patch_items(j, is_mem, [&](uint8_t it) { L.cut_items[o++] = it; });
+    }
+  }
+  L.cut_fo[ncp] = L.fofs[L.member_node.size()];
+  L.cut_maxit.assign(ncol, 0);
+  for (int col = 0; col < ncol; ++col)
+    for (int j = L.cut_start[col]; j < L.cut_start[col + 1]; ++j)
+      L.cut_maxit[col] = std::max(L.cut_maxit[col], L.cut_item_off[j + 1] - L.cut_item_off[j]);
+}
+
+// Work model of the cut-patch solve (what the kernel computes per patch):
+// 2 NB flops per (active patch cell, patch DoF in it) for the cell rows,
+// 2p per ghost-face entry of a patch row, 2 m^2 for the local inverse.
+// Moved scalars: the inverse, the rows of cut-cell matrices used, the
+// closure of x, b and delta of the DoFs, p moments per ghost-face entry;
+// index bytes: the DoF lists, metadata, cell ids, row items and entries.
+// Face moments (computed once per colour step for the faces its patches
+// need): per face 2 (2p+1) p NT for the jumps, 2 p (p+1) NT per face
+// direction for the face mass, p NT for the coefficients; x of the two
+// cells read, p NT moments written.
+void patch_work_model(HostLevel& L) {
+  const int d = L.d, p = L.p, NB = ipow(p + 1, d);
+  const int C = 2 * p + 1, ncol = 1 << d, NCL = ipow(C, d);
+  const int NT = ipow(p + 1, d - 1);
+  L.work_cut.assign(ncol, {0.0, 0.0, 0.0});
+  L.work_face.assign(ncol, {0.0, 0.0, 0.0});
+  for (int col = 0; col < ncol; ++col) {
+    for (int j = L.cut_start[col]; j < L.cut_start[col + 1]; ++j) {
+      const int m = L.cut_n[j];
+      const double nent = L.cut_fo[j + 1] - L.cut_fo[j];
+      const double nit = L.cut_item_off[j + 1] - L.cut_item_off[j];
+      double fl = 2.0 * m * m + 2.0 * NB * nit + 2.0 * p * nent;
+      double sc = (double)m * m + NCL + 2.0 * m + p * nent;
+      for (int q = L.cut_item_off[j]; q < L.cut_item_off[j + 1]; ++q)
+        if (L.cut_cell[(size_t)j * (1 << d) + L.cut_items[q] / NB] >= 0) sc += NB;
+      L.work_cut[col][0] += fl;
+      L.work_cut[col][1] += sc;
+      L.work_cut[col][2] += 10.0 * m + 72.0 + nit + 4.0 * nent;
+    }
+    const double nf = L.cf_start[col + 1] - L.cf_start[col];
+    const double flf = 2.0 * (2 * p + 1) * p * NT + 2.0 * p * (p + 1) * NT * (d - 1) + (double)p * NT;
+    L.work_face[col] = {nf * flf, nf * ((2.0 * p + 1) * NT + (double)p * NT), nf * 8.0};
+  }
+  // interior patches: sum factorisation and fast diagonalisation
+  const int M = 2 * p - 1;
+  double flc, scc;
+  if (d == 3) {
+    flc = 2.0 * (2.0 * M * C * C * C + 3.0 * M * M * C * C + 2.0 * M * M * M * C + 6.0 * M * M * M * M + M * M * M);
+    scc = (double)C * C * C + 2.0 * M * M * M;
+  } else {
+    flc = 2.0 * (2.0 * M * C * C + 2.0 * M * M * C + 4.0 * M * M * M + M * M);
+    scc = (double)C * C + 2.0 * M * M;
+  }
+  L.work_cart.assign(ncol, {0.0, 0.0, 0.0});
+  for (int col = 0; col < ncol; ++col) {
+    double np_ = L.cart_start[col + 1] - L.cart_start[col];
+    L.work_cart[col] = {np_ * flc, np_ * scc, np_ * 4.0};
+  }
+}
+
+// Cut-patch matrices A_j = A[I_j, I_j] from their cell and ghost-face pieces,
+// inverted in place (explicit FP64 inverse per patch).
+void cut_patch_inverses(const RefTables& R, HostLevel& L) {
+  const int d = L.d, p = L.p, N = L.N, NB = R.NB;
+  const int np = N + 1, C = 2 * p + 1, NCL = ipow(C, d);
+  const int64_t ncp = (int64_t)L.cut_vert.size();
+  auto cflag_at = [&](const int* c) { return cell_flag(L, c); };
+  // ghost-face block of one face (block nodes e = i + (2p+1) u: i along the
+  // normal over both cells, u tangential): the same for every face and
+  // direction of the level
+  const int tn = ipow(p + 1, d - 1), nbk = (2 * p + 1) * tn;
+  std::vector<int> fb_i(nbk), fb_t((size_t)nbk * 2, 0);
+  for (int e = 0; e < nbk; ++e) {
+    int u = e / (2 * p + 1);
+    fb_i[e] = e % (2 * p + 1);
+    for (int q = 0; q < d - 1; ++q) {
+      fb_t[e * 2 + q] = u % (p + 1);
+      u /= p + 1;
+    }
+  }
+  std::vector<double> fblk((size_t)nbk * nbk);
+  for (int e1 = 0; e1 < nbk; ++e1)
+    for (int e2 = 0; e2 < nbk; ++e2) {
+      double tm = 1.0;
+      for (int q = 0; q < d - 1; ++q) tm *= L.Mhat[fb_t[e1 * 2 + q]][fb_t[e2 * 2 + q]];
+      double s = 0.0;
+      for (int mm = 0; mm < p; ++mm) s += L.coef[mm] * L.dvec[mm][fb_i[e1]] * L.dvec[mm][fb_i[e2]];
+      fblk[(size_t)e1 * nbk + e2] = s * tm;
+    }
+  // A_j = A[I_j, I_j] from cell and ghost-face pieces, then inverted
+  std::vector<int> err(ncp, 0);
+  std::string first_err;
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t j = 0; j < ncp; ++j) {
+    int v[3] = {0, 0, 0};
+    int64_t t = L.cut_vert[j];
+    for (int k = 0; k < d; ++k) {
+      v[k] = (int)(t % np);
+      t /= np;
+    }
+    const int m = L.cut_n[j];
+    std::vector<int> pos(NCL, -1);
+    for (int a = 0; a < m; ++a) pos[L.members[L.cut_moff[j] + a]] = a;
+    double* A = &L.inv[L.cut_ioff[j]];
+    std::fill(A, L.inv.data() + (j + 1 < ncp ? L.cut_ioff[j + 1] : (int64_t)L.inv.size()), 0.0);
+    auto closure_of = [&](const int* lat) -> int {  // lattice coords -> member or -1
+      int o = 0, st = 1;
+      for (int k = 0; k < d; ++k) {
+        int ok = lat[k] - p * (v[k] - 1);
+        if (ok < 0 || ok >= C) return -1;
+        o += ok * st;
+        st *= C;
+      }
+      return pos[o];
+    };
+    // cells of the patch
+    for (int s = 0; s < (1 << d); ++s) {
+      int c[3] = {0, 0, 0};
+      for (int k = 0; k < d; ++k) c[k] = v[k] - 1 + ((s >> k) & 1);
+      uint8_t f = cflag_at(c);
+      if (!(f & kFlagActive)) continue;
+      int64_t cf = 0, st = 1;
+      for (int k = 0; k < d; ++k) {
+        cf += (int64_t)c[k] * st;
+        st *= N;
+      }
+      const double* K = (f & kFlagCut) ? &L.cutmat[(size_t)L.cut_id[cf] * NB * NB] : L.Kref.data();
+      int mi[64];
+      for (int jl = 0; jl < NB; ++jl) {
+        int a[3] = {0, 0, 0}, lat[3] = {0, 0, 0};
+        R.split(jl, a);
+        for (int k = 0; k < d; ++k) lat[k] = p * c[k] + a[k];
+        mi[jl] = closure_of(lat);
+      }
+      for (int a = 0; a < NB; ++a) {
+        if (mi[a] < 0) continue;
+        for (int b = 0; b < NB; ++b)
+          if (mi[b] >= 0) A[(size_t)mi[a] * m + mi[b]] += K[a * NB + b];
+      }
+    }
+    // ghost faces touching a patch cell: lower cell Lc, upper Lc + e_k
+    for (int k = 0; k < d; ++k) {
+      int rng_lo[3], rng_hi[3];
+      for (int kk = 0; kk < d; ++kk) {
+        rng_lo[kk] = v[kk] - 1;
+        rng_hi[kk] = v[kk];
+      }
+      rng_lo[k] = v[k] - 2;
+      for (int c2 = (d > 2 ? rng_lo[2] : 0); c2 <= (d > 2 ? rng_hi[2] : 0); ++c2)
+        for (int c1 = rng_lo[1]; c1 <= rng_hi[1]; ++c1)
+          for (int c0 = rng_lo[0]; c0 <= rng_hi[0]; ++c0) {
+            int lc[3] = {c0, c1, c2}, uc[3] = {c0, c1, c2};
+            uc[k] += 1;
+            uint8_t f1 = cflag_at(lc), f2 = cflag_at(uc);
+            if (!((f1 & kFlagActive) && (f2 & kFlagActive) && ((f1 | f2) & kFlagCut))) continue;
+            // block nodes: i in [0, 2p] along k, t in [0, p] tangential
+            int mi[7 * 16];
+            for (int e = 0; e < nbk; ++e) {
+              int lat[3] = {0, 0, 0}, q = 0;
+              for (int kk = 0; kk < d; ++kk)
+                lat[kk] = p * lc[kk] + (kk == k ? fb_i[e] : fb_t[e * 2 + q++]);
+              mi[e] = closure_of(lat);
+            }
+            for (int e1 = 0; e1 < nbk; ++e1) {
+              if (mi[e1] < 0) continue;
+              const double* fr = &fblk[(size_t)e1 * nbk];
+              double* Ar = A + (size_t)mi[e1] * m;
+              for (int e2 = 0; e2 < nbk; ++e2)
+                if (mi[e2] >= 0) Ar[mi[e2]] += fr[e2];
+            }
+          }
+    }
+    try {
+      spd_inverse(m, A);
+    } catch (const std::exception& e) {
+      err[j] = 1;
+#pragma omp critical
+      if (first_err.empty())
+        first_err = "cut patch at vertex (" + std::to_string(v[0]) + "," + std::to_string(v[1]) + "," +
+                    std::to_string(v[2]) + ") with " + std::to_string(m) + " DoFs on level N=" +
+                    std::to_string(N) + ": " + e.what();
+    }
+  }
+  for (int64_t j = 0; j < ncp; ++j)
+    if (err[j]) throw std::runtime_error(first_err);
+}
+
+// Patches (Sec. 2.3, Sec. 3) of a level: vertex sets by colour, and for the
+// cut patches their DoF lists, ghost-face entries, row items, work model and
+// explicit inverses.
+void build_patches(const RefTables& R, HostLevel& L) {
+  patch_vertex_sets(L);
+  cut_patch_members(L);
+  cut_patch_face_entries(L);
+  cut_patch_rows(L);
+  patch_work_model(L);
+  cut_patch_inverses(R, L);
+}
+
 // Optional: with cut_rhs, the cut cells' right-hand side terms for source
 // fsrc and Dirichlet data gdir are formed from the same quadrature rules
 // (n_cut x NB, in cut-cell order).
@@ -615,547 +1227,8 @@ void build_level(const SetupParams& prm, const RefTables& R, int N, HostLevel& L
       if (!bulk[q]) L.bnd_node.push_back((int)i);
     }
   }
-  // one-dimensional two-cell patch matrices and fast diagonalisation
-  {
-    const int C = 2 * p + 1, M = 2 * p - 1;
-    std::vector<double> Mb(C * C, 0.0), Kb(C * C, 0.0);
-    for (int s = 0; s < 2; ++s)
-      for (int a = 0; a <= p; ++a)
-        for (int b = 0; b <= p; ++b) {
-          Mb[(s * p + a) * C + s * p + b] += R.M1[a * (p + 1) + b] * h;
-          Kb[(s * p + a) * C + s * p + b] += R.K1[a * (p + 1) + b] / h;
-        }
-    L.Mr.assign(M * C, 0.0);
-    L.Kr.assign(M * C, 0.0);
-    for (int i = 0; i < M; ++i)
-      for (int j = 0; j < C; ++j) {
-        L.Mr[i * C + j] = Mb[(i + 1) * C + j];
-        L.Kr[i * C + j] = Kb[(i + 1) * C + j];
-      }
-    // K_I s = lam M_I s with S^T M_I S = I: M_I = G G^T, Jacobi on G^-1 K_I G^-T
-    std::vector<double> MI(M * M), KI(M * M), G(M * M, 0.0), Gi(M * M, 0.0);
-    for (int i = 0; i < M; ++i)
-      for (int j = 0; j < M; ++j) {
-        MI[i * M + j] = L.Mr[i * C + j + 1];
-        KI[i * M + j] = L.Kr[i * C + j + 1];
-      }
-    for (int j = 0; j < M; ++j) {
-      double s = MI[j * M + j];
-      for (int k = 0; k < j; ++k) s -= G[j * M + k] * G[j * M + k];
-      G[j * M + j] = std::sqrt(s);
-      for (int i = j + 1; i < M; ++i) {
-        double t = MI[i * M + j];
-        for (int k = 0; k < j; ++k) t -= G[i * M + k] * G[j * M + k];
-        G[i * M + j] = t / G[j * M + j];
-      }
-    }
-    for (int c = 0; c < M; ++c)
-      for (int i = c; i < M; ++i) {
-        double t = (i == c) ? 1.0 : 0.0;
-        for (int k = c; k < i; ++k) t -= G[i * M + k] * Gi[k * M + c];
-        Gi[i * M + c] = t / G[i * M + i];
-      }
-    std::vector<double> Cm(M * M, 0.0), Qv, lam;
-    for (int i = 0; i < M; ++i)
-      for (int j = 0; j < M; ++j) {
-        double t = 0.0;
-        for (int a = 0; a < M; ++a)
-          for (int b = 0; b < M; ++b) t += Gi[i * M + a] * KI[a * M + b] * Gi[j * M + b];
-        Cm[i * M + j] = t;
-      }
-    jacobi_eigen(M, Cm, Qv, lam);
-    L.S.assign(M * M, 0.0);
-    for (int i = 0; i < M; ++i)
-      for (int j = 0; j < M; ++j) {
-        double t = 0.0;
-        for (int a = 0; a < M; ++a) t += Gi[a * M + i] * Qv[a * M + j];  // G^-T Q
-        L.S[i * M + j] = t;
-      }
-    L.lam = lam;
-    // The exact local solve of an interior patch as one dense map per level:
-    // x_I <- A_I^{-1} b_I - A_I^{-1} A_{I,B} x_B over the closure; columns in
-    // closure order (first coordinate fastest), b at interior columns and x
-    // at boundary columns; rows in interior order.
-    {
-      const int NI = ipow(M, d), NC = ipow(C, d);
-      std::vector<double> AIcl((size_t)NI * NC, 0.0);
-      for (int i = 0; i < NI; ++i) {
-        int ii[3] = {0, 0, 0}, t = i;
-        for (int k = 0; k < d; ++k) {
-          ii[k] = t % M;
-          t /= M;
-        }
-        for (int kc = 0; kc < NC; ++kc) {
-          int cc[3] = {0, 0, 0}, u = kc;
-          for (int k = 0; k < d; ++k) {
-            cc[k] = u % C;
-            u /= C;
-          }
-          double v = 0.0;
-          for (int a = 0; a < d; ++a) {  // stiffness along a, mass along the others
-            double f = 1.0;
-            for (int k = 0; k < d; ++k) f *= (k == a ? L.Kr[ii[k] * C + cc[k]] : L.Mr[ii[k] * C + cc[k]]);
-            v += f;
-          }
-          AIcl[(size_t)i * NC + kc] = v;
-        }
-      }
-      auto closure_of = [&](int i) {
-        int kc = 0, st = 1, t = i;
-        for (int k = 0; k < d; ++k) {
-          kc += (t % M + 1) * st;
-          t /= M;
-          st *= C;
-        }
-        return kc;
-      };
-      std::vector<double> AIi((size_t)NI * NI);
-      for (int i = 0; i < NI; ++i)
-        for (int j = 0; j < NI; ++j) AIi[(size_t)i * NI + j] = AIcl[(size_t)i * NC + closure_of(j)];
-      spd_inverse(NI, AIi.data());
-      std::vector<int> interior_index(NC, -1);
-      for (int j = 0; j < NI; ++j) interior_index[closure_of(j)] = j;
-      L.Wcart.assign((size_t)NI * NC, 0.0);
-      for (int i = 0; i < NI; ++i)
-        for (int kc = 0; kc < NC; ++kc) {
-          double w;
-          if (interior_index[kc] >= 0) {
-            w = AIi[(size_t)i * NI + interior_index[kc]];
-          } else {
-            w = 0.0;
-            for (int j = 0; j < NI; ++j) w -= AIi[(size_t)i * NI + j] * AIcl[(size_t)j * NC + kc];
-          }
-          L.Wcart[(size_t)i * NC + kc] = w;
-        }
-    }
-  }
-  // patches
-  {
-    const int np = N + 1, C = 2 * p + 1, ncol = 1 << d;
-    const int NCL = ipow(C, d);
-    const int64_t nvert = (int64_t)ipow(np, d);
-    std::vector<std::vector<int>> cart(ncol), cutv(ncol);
-    // per vertex: -1 (no active cell around it), else colour + 8 if Cartesian
-    std::vector<int8_t> vkind(nvert);
-#pragma omp parallel for schedule(static)
-    for (int64_t q = 0; q < nvert; ++q) {
-      int v[3] = {0, 0, 0};
-      int64_t t = q;
-      for (int k = 0; k < d; ++k) {
-        v[k] = (int)(t % np);
-        t /= np;
-      }
-      bool any = false, cartesian = true;
-      for (int s = 0; s < (1 << d); ++s) {
-        int c[3] = {0, 0, 0};
-        for (int k = 0; k < d; ++k) c[k] = v[k] - 1 + ((s >> k) & 1);
-        if (cflag_at(c) & kFlagActive) any = true;
-        if (!plain(c)) cartesian = false;
-      }
-      int col = 0;
-      for (int k = 0; k < d; ++k) col |= (v[k] & 1) << k;
-      vkind[q] = any ? (int8_t)(col + (cartesian ? 8 : 0)) : (int8_t)-1;
-    }
-    for (int64_t q = 0; q < nvert; ++q) {
-      if (vkind[q] < 0) continue;
-      const int col = vkind[q] & 7;
-      ((vkind[q] & 8) ? cart : cutv)[col].push_back((int)q);
-    }
-    L.cart_start.assign(ncol + 1, 0);
-    L.cut_start.assign(ncol + 1, 0);
-    for (int c = 0; c < ncol; ++c) {
-      L.cart_vert.insert(L.cart_vert.end(), cart[c].begin(), cart[c].end());
-      L.cut_vert.insert(L.cut_vert.end(), cutv[c].begin(), cutv[c].end());
-      L.cart_start[c + 1] = (int)L.cart_vert.size();
-      L.cut_start[c + 1] = (int)L.cut_vert.size();
-    }
-    const int64_t ncp = (int64_t)L.cut_vert.size();
-    // members: closure nodes all of whose active cells are patch cells
-    std::vector<std::vector<uint16_t>> mem(ncp);
-#pragma omp parallel for schedule(dynamic, 64)
-    for (int64_t j = 0; j < ncp; ++j) {
-      int v[3] = {0, 0, 0};
-      int64_t t = L.cut_vert[j];
-      for (int k = 0; k < d; ++k) {
-        v[k] = (int)(t % np);
-        t /= np;
-      }
-      for (int o = 0; o < NCL; ++o) {
-        int oc[3] = {0, 0, 0}, li[3] = {0, 0, 0}, u = o;
-        bool valid = true;
-        for (int k = 0; k < d; ++k) {
-          oc[k] = u % C;
-          u /= C;
-          li[k] = p * (v[k] - 1) + oc[k];
-          if (li[k] < 0 || li[k] >= n) valid = false;
-        }
-        if (!valid) continue;
-        int cc[3][2], lc[3][2], nc[3] = {1, 1, 1};
-        for (int k = 0; k < d; ++k) nc[k] = cells_of(li[k], p, N, cc[k], lc[k]);
-        bool inside = false, outside = false;
-        int tot = nc[0] * nc[1] * nc[2];
-        for (int s = 0; s < tot; ++s) {
-          int c[3] = {0, 0, 0}, r = s;
-          bool in_patch = true;
-          for (int k = 0; k < d; ++k) {
-            c[k] = cc[k][r % nc[k]];
-            r /= nc[k];
-            if (c[k] != v[k] - 1 && c[k] != v[k]) in_patch = false;
-          }
-          if (cflag_at(c) & kFlagActive) (in_patch ? inside : outside) = true;
-        }
-        if (inside && !outside) mem[j].push_back((uint16_t)o);
-      }
-    }
-    L.cut_n.resize(ncp);
-    L.cut_moff.resize(ncp);
-    L.cut_ioff.resize(ncp);
-    int64_t moff = 0, ioff = 0;
-    L.cut_maxm2.assign(ncol, 0);
-    for (int64_t j = 0; j < ncp; ++j) {
-      int m = (int)mem[j].size();
-      L.cut_n[j] = m;
-      L.cut_moff[j] = (int)moff;
-      L.cut_ioff[j] = ioff;
-      moff += m;
-      // every inverse starts on a 16-byte boundary in FP64 and FP32 (TMA bulk copies)
-      ioff += ((int64_t)m * m + 3) / 4 * 4;
-      for (int col = 0; col < ncol; ++col)
-        if (j >= L.cut_start[col] && j < L.cut_start[col + 1]) L.cut_maxm2[col] = std::max(L.cut_maxm2[col], m * m);
-      L.members.insert(L.members.end(), mem[j].begin(), mem[j].end());
-      int v[3] = {0, 0, 0};
-      int64_t t = L.cut_vert[j];
-      for (int k = 0; k < d; ++k) {
-        v[k] = (int)(t % np);
-        t /= np;
-      }
-      for (int e = 0; e < m; ++e) {
-        int o = mem[j][e];
-        int64_t node = 0, st = 1;
-        for (int k = 0; k < d; ++k) {
-          node += (int64_t)(p * (v[k] - 1) + o % C) * st;
-          o /= C;
-          st *= n;
-        }
-        L.member_node.push_back((int)node);
-      }
-    }
-    L.inv.resize(ioff);  // every slot zeroed and filled by its patch below
-    // ghost-face entries of every cut-patch DoF (the faces whose two cells
-    // contain the node), and per colour the faces these rows need.  Entries
-    // are counted, then written at their offsets, member by member in
-    // parallel (the lists are the same for every thread count).
-    {
-      const int NTf = ipow(p + 1, d - 1);
-      const int64_t nmem = (int64_t)L.member_node.size();
-      // entry = ((face id * NTf) + tangential node) * 8 + node along the normal
-      auto entries = [&](int64_t gm, auto&& emit) {
-        int64_t t = L.member_node[gm];
-        int idx[3] = {0, 0, 0};
-        for (int k = 0; k < d; ++k) {
-          idx[k] = (int)(t % n);
-          t /= n;
-        }
-        int cc[3][2], lcl[3][2], nopt[3] = {1, 1, 1};
-        for (int k = 0; k < d; ++k) nopt[k] = cells_of(idx[k], p, N, cc[k], lcl[k]);
-        for (int k = 0; k < d; ++k) {
-          const int a = idx[k] / p, r = idx[k] - a * p;
-          int Llo = (r == 0) ? a - 2 : a - 1, Lhi = a;
-          Llo = std::max(Llo, 0);
-          Lhi = std::min(Lhi, N - 2);
-          int td[2] = {0, 0}, q = 0;
-          for (int jj = 0; jj < d; ++jj)
-            if (jj != k) td[q++] = jj;
-          const int n0 = nopt[td[0]], n1 = (d == 3) ? nopt[td[1]] : 1;
-          for (int Lk = Llo; Lk <= Lhi; ++Lk)
-            for (int u0 = 0; u0 < n0; ++u0)
-              for (int u1 = 0; u1 < n1; ++u1) {
-                int c[3] = {0, 0, 0};
-                c[k] = Lk;
-                c[td[0]] = cc[td[0]][u0];
-                if (d == 3) c[td[1]] = cc[td[1]][u1];
-                int64_t cell = c[0] + (int64_t)N * (c[1] + (d == 3 ? (int64_t)N * c[2] : 0));
-                const int id = L.face_id[(size_t)cell * d + k];
-                if (id < 0) continue;
-                int tt = idx[td[0]] - p * c[td[0]];
-                if (d == 3) tt += (p + 1) * (idx[td[1]] - p * c[td[1]]);
-                emit(((id * NTf) + tt) * 8 + (idx[k] - p * Lk), id);
-              }
-        }
-      };
-      std::vector<int> cnt(nmem, 0);
-#pragma omp parallel for schedule(dynamic, 256)
-      for (int64_t gm = 0; gm < nmem; ++gm) {
-        int c = 0;
-        entries(gm, [&](int, int) { ++c; });
-        cnt[gm] = c;
-      }
-      L.fofs.assign(nmem + 1, 0);
-      for (int64_t gm = 0; gm < nmem; ++gm) L.fofs[gm + 1] = L.fofs[gm] + cnt[gm];
-      L.fent.assign((size_t)L.fofs[nmem], 0);
-      // colour of every member (the colour of its patch)
-      std::vector<uint8_t> mcol(nmem);
-      for (int col = 0; col < ncol; ++col)
-        for (int j = L.cut_start[col]; j < L.cut_start[col + 1]; ++j)
-          std::fill(mcol.begin() + L.cut_moff[j], mcol.begin() + L.cut_moff[j] + L.cut_n[j], (uint8_t)col);
-      // need[col][face]: a row of the colour reads the face's moments
-      const size_t nf = L.ghost_faces.size();
-      std::vector<uint8_t> need((size_t)ncol * nf, 0);
-#pragma omp parallel for schedule(dynamic, 256)
-      for (int64_t gm = 0; gm < nmem; ++gm) {
-        int o = L.fofs[gm];
-        uint8_t* nc = &need[(size_t)mcol[gm] * nf];
-        entries(gm, [&](int v, int id) {
-          L.fent[o++] = v;
-#pragma omp atomic write
-          nc[id] = 1;
-        });
-      }
-      L.cf_start.assign(ncol + 1, 0);
-      for (int col = 0; col < ncol; ++col) {
-        const uint8_t* nc = &need[(size_t)col * nf];
-        for (size_t f = 0; f < nf; ++f)
-          if (nc[f]) L.cfaces.push_back((int)f);
-        L.cf_start[col + 1] = (int)L.cfaces.size();
-      }
-    }
-    // per cut patch, what its block loads up front: the range of its
-    // ghost-face entries, the element matrix of each patch cell and the
-    // (cell, local node) pairs whose rows it forms (node a patch DoF)
-    {
-      const int NCELL = 1 << d;
-      L.cut_fo.resize(ncp + 1);
-      L.cut_cell.assign((size_t)ncp * NCELL, -2);
-      L.cut_item_off.assign(ncp + 1, 0);
-      L.cut_items.clear();
-      // closure offset of local node jj of patch cell sc
-      std::vector<int> cell_node((size_t)NCELL * NB);
-      for (int sc = 0; sc < NCELL; ++sc)
-        for (int jj = 0; jj < NB; ++jj) {
-          int o = 0, ost = 1, u = jj;
-          for (int k = 0; k < d; ++k) {
-            o += (p * ((sc >> k) & 1) + u % (p + 1)) * ost;
-            u /= (p + 1);
-            ost *= C;
-          }
-          cell_node[(size_t)sc * NB + jj] = o;
-        }
-      // per patch (in parallel): its cells, then its items counted and written
-      // at their offsets
-      auto patch_items = [&](int64_t j, std::vector<char>& is_mem, auto&& emit) {
-        int v[3] = {0, 0, 0};
-        int64_t t = L.cut_vert[j];
-        for (int k = 0; k < d; ++k) {
-          v[k] = (int)(t % np);
-          t /= np;
-        }
-        std::fill(is_mem.begin(), is_mem.end(), 0);
-        for (int e = 0; e < L.cut_n[j]; ++e) is_mem[L.members[L.cut_moff[j] + e]] = 1;
-        for (int sc = 0; sc < NCELL; ++sc) {
-          int c[3] = {0, 0, 0};
-          for (int k = 0; k < d; ++k) c[k] = v[k] - 1 + ((sc >> k) & 1);
-          const uint8_t f = cflag_at(c);
-          if (!(f & kFlagActive)) continue;
-          const int64_t cell = c[0] + (int64_t)N * (c[1] + (d == 3 ? (int64_t)N * c[2] : 0));
-          L.cut_cell[(size_t)j * NCELL + sc] = (f & kFlagCut) ? L.cut_id[cell] : -1;
-          for (int jj = 0; jj < NB; ++jj)
-            if (is_mem[cell_node[(size_t)sc * NB + jj]]) emit((uint8_t)(sc * NB + jj));
-        }
-      };
-#pragma omp parallel
-      {
-        std::vector<char> is_mem(NCL);
-#pragma omp for schedule(dynamic, 64)
-        for (int64_t j = 0; j < ncp; ++j) {
-          L.cut_fo[j] = L.fofs[L.cut_moff[j]];
-          int c = 0;
-          patch_items(j, is_mem, [&](uint8_t) { ++c; });
-          L.cut_item_off[j + 1] = c;
-        }
-      }
-      for (int64_t j = 0; j < ncp; ++j) L.cut_item_off[j + 1] += L.cut_item_off[j];
-      L.cut_items.assign((size_t)L.cut_item_off[ncp], 0);
-#pragma omp parallel
-      {
-        std::vector<char> is_mem(NCL);
-#pragma omp for schedule(dynamic, 64)
-        for (int64_t j = 0; j < ncp; ++j) {
-          int o = L.cut_item_off[j];
-          patch_items(j, is_mem, [&](uint8_t it) { L.cut_items[o++] = it; });
-        }
-      }
-      L.cut_fo[ncp] = L.fofs[L.member_node.size()];
-      L.cut_maxit.assign(ncol, 0);
-      for (int col = 0; col < ncol; ++col)
-        for (int j = L.cut_start[col]; j < L.cut_start[col + 1]; ++j)
-          L.cut_maxit[col] = std::max(L.cut_maxit[col], L.cut_item_off[j + 1] - L.cut_item_off[j]);
-    }
-    // work model of the cut-patch solve (what the kernel computes per patch):
-    // 2 NB flops per (active patch cell, patch DoF in it) for the cell rows,
-    // 2p per ghost-face entry of a patch row, 2 m^2 for the local inverse.
-    // Moved scalars: the inverse, the rows of cut-cell matrices used, the
-    // closure of x, b and delta of the DoFs, p moments per ghost-face entry;
-    // index bytes: the DoF lists, metadata, cell ids, row items and entries.
-    // Face moments (computed once per colour step for the faces its patches
-    // need): per face 2 (2p+1) p NT for the jumps, 2 p (p+1) NT per face
-    // direction for the face mass, p NT for the coefficients; x of the two
-    // cells read, p NT moments written.
-    {
-      const int NT = ipow(p + 1, d - 1);
-      L.work_cut.assign(ncol, {0.0, 0.0, 0.0});
-      L.work_face.assign(ncol, {0.0, 0.0, 0.0});
-      for (int col = 0; col < ncol; ++col) {
-        for (int j = L.cut_start[col]; j < L.cut_start[col + 1]; ++j) {
-          const int m = L.cut_n[j];
-          const double nent = L.cut_fo[j + 1] - L.cut_fo[j];
-          const double nit = L.cut_item_off[j + 1] - L.cut_item_off[j];
-          double fl = 2.0 * m * m + 2.0 * NB * nit + 2.0 * p * nent;
-          double sc = (double)m * m + NCL + 2.0 * m + p * nent;
-          for (int q = L.cut_item_off[j]; q < L.cut_item_off[j + 1]; ++q)
-            if (L.cut_cell[(size_t)j * (1 << d) + L.cut_items[q] / NB] >= 0) sc += NB;
-          L.work_cut[col][0] += fl;
-          L.work_cut[col][1] += sc;
-          L.work_cut[col][2] += 10.0 * m + 72.0 + nit + 4.0 * nent;
-        }
-        const double nf = L.cf_start[col + 1] - L.cf_start[col];
-        const double flf = 2.0 * (2 * p + 1) * p * NT + 2.0 * p * (p + 1) * NT * (d - 1) + (double)p * NT;
-        L.work_face[col] = {nf * flf, nf * ((2.0 * p + 1) * NT + (double)p * NT), nf * 8.0};
-      }
-      // interior patches: sum factorisation and fast diagonalisation
-      const int M = 2 * p - 1;
-      double flc, scc;
-      if (d == 3) {
-        flc = 2.0 * (2.0 * M * C * C * C + 3.0 * M * M * C * C + 2.0 * M * M * M * C + 6.0 * M * M * M * M + M * M * M);
-        scc = (double)C * C * C + 2.0 * M * M * M;
-      } else {
-        flc = 2.0 * (2.0 * M * C * C + 2.0 * M * M * C + 4.0 * M * M * M + M * M);
-        scc = (double)C * C + 2.0 * M * M;
-      }
-      L.work_cart.assign(ncol, {0.0, 0.0, 0.0});
-      for (int col = 0; col < ncol; ++col) {
-        double np_ = L.cart_start[col + 1] - L.cart_start[col];
-        L.work_cart[col] = {np_ * flc, np_ * scc, np_ * 4.0};
-      }
-    }
-    // ghost-face block of one face (block nodes e = i + (2p+1) u: i along the
-    // normal over both cells, u tangential): the same for every face and
-    // direction of the level
-    const int tn = ipow(p + 1, d - 1), nbk = (2 * p + 1) * tn;
-    std::vector<int> fb_i(nbk), fb_t((size_t)nbk * 2, 0);
-    for (int e = 0; e < nbk; ++e) {
-      int u = e / (2 * p + 1);
-      fb_i[e] = e % (2 * p + 1);
-      for (int q = 0; q < d - 1; ++q) {
-        fb_t[e * 2 + q] = u % (p + 1);
-        u /= p + 1;
-      }
-    }
-    std::vector<double> fblk((size_t)nbk * nbk);
-    for (int e1 = 0; e1 < nbk; ++e1)
-      for (int e2 = 0; e2 < nbk; ++e2) {
-        double tm = 1.0;
-        for (int q = 0; q < d - 1; ++q) tm *= L.Mhat[fb_t[e1 * 2 + q]][fb_t[e2 * 2 + q]];
-        double s = 0.0;
-        for (int mm = 0; mm < p; ++mm) s += L.coef[mm] * L.dvec[mm][fb_i[e1]] * L.dvec[mm][fb_i[e2]];
-        fblk[(size_t)e1 * nbk + e2] = s * tm;
-      }
-    // A_j = A[I_j, I_j] from cell and ghost-face pieces, then inverted
-    std::vector<int> err(ncp, 0);
-    std::string first_err;
-#pragma omp parallel for schedule(dynamic, 16)
-    for (int64_t j = 0; j < ncp; ++j) {
-      int v[3] = {0, 0, 0};
-      int64_t t = L.cut_vert[j];
-      for (int k = 0; k < d; ++k) {
-        v[k] = (int)(t % np);
-        t /= np;
-      }
-      const int m = L.cut_n[j];
-      std::vector<int> pos(NCL, -1);
-      for (int a = 0; a < m; ++a) pos[mem[j][a]] = a;
-      double* A = &L.inv[L.cut_ioff[j]];
-      std::fill(A, L.inv.data() + (j + 1 < ncp ? L.cut_ioff[j + 1] : (int64_t)L.inv.size()), 0.0);
-      auto closure_of = [&](const int* lat) -> int {  // lattice coords -> member or -1
-        int o = 0, st = 1;
-        for (int k = 0; k < d; ++k) {
-          int ok = lat[k] - p * (v[k] - 1);
-          if (ok < 0 || ok >= C) return -1;
-          o += ok * st;
-          st *= C;
-        }
-        return pos[o];
-      };
-      // cells of the patch
-      for (int s = 0; s < (1 << d); ++s) {
-        int c[3] = {0, 0, 0};
-        for (int k = 0; k < d; ++k) c[k] = v[k] - 1 + ((s >> k) & 1);
-        uint8_t f = cflag_at(c);
-        if (!(f & kFlagActive)) continue;
-        int64_t cf = 0, st = 1;
-        for (int k = 0; k < d; ++k) {
-          cf += (int64_t)c[k] * st;
-          st *= N;
-        }
-        const double* K = (f & kFlagCut) ? &L.cutmat[(size_t)L.cut_id[cf] * NB * NB] : L.Kref.data();
-        int mi[64];
-        for (int jl = 0; jl < NB; ++jl) {
-          int a[3] = {0, 0, 0}, lat[3] = {0, 0, 0};
-          R.split(jl, a);
-          for (int k = 0; k < d; ++k) lat[k] = p * c[k] + a[k];
-          mi[jl] = closure_of(lat);
-        }
-        for (int a = 0; a < NB; ++a) {
-          if (mi[a] < 0) continue;
-          for (int b = 0; b < NB; ++b)
-            if (mi[b] >= 0) A[(size_t)mi[a] * m + mi[b]] += K[a * NB + b];
-        }
-      }
-      // ghost faces touching a patch cell: lower cell Lc, upper Lc + e_k
-      for (int k = 0; k < d; ++k) {
-        int rng_lo[3], rng_hi[3];
-        for (int kk = 0; kk < d; ++kk) {
-          rng_lo[kk] = v[kk] - 1;
-          rng_hi[kk] = v[kk];
-        }
-        rng_lo[k] = v[k] - 2;
-        for (int c2 = (d > 2 ? rng_lo[2] : 0); c2 <= (d > 2 ? rng_hi[2] : 0); ++c2)
-          for (int c1 = rng_lo[1]; c1 <= rng_hi[1]; ++c1)
-            for (int c0 = rng_lo[0]; c0 <= rng_hi[0]; ++c0) {
-              int lc[3] = {c0, c1, c2}, uc[3] = {c0, c1, c2};
-              uc[k] += 1;
-              uint8_t f1 = cflag_at(lc), f2 = cflag_at(uc);
-              if (!((f1 & kFlagActive) && (f2 & kFlagActive) && ((f1 | f2) & kFlagCut))) continue;
-              // block nodes: i in [0, 2p] along k, t in [0, p] tangential
-              int mi[7 * 16];
-              for (int e = 0; e < nbk; ++e) {
-                int lat[3] = {0, 0, 0}, q = 0;
-                for (int kk = 0; kk < d; ++kk)
-                  lat[kk] = p * lc[kk] + (kk == k ? fb_i[e] : fb_t[e * 2 + q++]);
-                mi[e] = closure_of(lat);
-              }
-              for (int e1 = 0; e1 < nbk; ++e1) {
-                if (mi[e1] < 0) continue;
-                const double* fr = &fblk[(size_t)e1 * nbk];
-                double* Ar = A + (size_t)mi[e1] * m;
-                for (int e2 = 0; e2 < nbk; ++e2)
-                  if (mi[e2] >= 0) Ar[mi[e2]] += fr[e2];
-              }
-            }
-      }
-      try {
-        spd_inverse(m, A);
-      } catch (const std::exception& e) {
-        err[j] = 1;
-#pragma omp critical
-        if (first_err.empty())
-          first_err = "cut patch at vertex (" + std::to_string(v[0]) + "," + std::to_string(v[1]) + "," +
-                      std::to_string(v[2]) + ") with " + std::to_string(m) + " DoFs on level N=" +
-                      std::to_string(N) + ": " + e.what();
-      }
-    }
-    for (int64_t j = 0; j < ncp; ++j)
-      if (err[j]) throw std::runtime_error(first_err);
-  }
+  interior_patch_tables(R, L);
+  build_patches(R, L);
 }
 
 // 1D transfer tables between a coarse level (Nc cells) and its refinement
