@@ -35,6 +35,10 @@ CASES = {
                                                    "axes": [0.7, 0.5, 0.45], "rot": _rot(0.3, 0.5)}),
     "torus_q2": dict(dim=3, N=16, L=2, p=2, ls={"kind": "torus", "center": [0.02, 0.01, -0.03],
                                                 "rot": _rot(0.4, 0.7), "major": 0.6, "minor": 0.2}),
+    "disk_q1": dict(dim=2, N=32, L=3, p=1, ls=SPH2),
+    # an oblique half-space: the cut runs to the edge of the box
+    "plane3d_q2": dict(dim=3, N=8, L=2, p=2, ls={"kind": "plane", "normal": [0.36, 0.48, 0.8], "offset": 0.13}),
+    "plane2d_q3": dict(dim=2, N=16, L=2, p=3, ls={"kind": "plane", "normal": [0.6, -0.8], "offset": -0.07}),
     # degenerate: a disk smaller than a cell, every patch cut, no interior one
     "tiny_q2": dict(dim=2, N=16, L=2, p=2, ls={"kind": "sphere", "center": [0.01, 0.02], "radius": 0.05}),
     # user level sets through point callbacks (sampled bounds on both sides)
