@@ -5,9 +5,13 @@ Transfer (Sec. 2.2): prolongation is the embedding V_{l-1} -> V_l, i.e.
 P[i, J] = phi^{l-1}_J(x_i) for every active fine node i and active coarse
 node J; restriction is P^T.
 
-Patches (Sec. 2.3): one per interior mesh vertex X with phi(X) < 0; the patch
-is the 2^d cells around X; I_j are the lattice nodes strictly inside it;
-A_j = A_l[I_j, I_j].
+Patches (Sec. 2.3, covering reading): one per vertex X of an active cell; the
+patch cells are the active cells around X; I_j are the patch's lattice nodes
+all of whose active cells are patch cells (for a vertex whose 2^d cells are
+active and uncut: the (2p-1)^d nodes strictly inside the patch), so that the
+patches cover Omega_l; A_j = A_l[I_j, I_j].  The printed vertex set (mesh
+vertices inside Omega, interior nodes only) leaves the DoFs near the boundary
+in no patch; a test pins that consequence.
 
 Smoother (eqs. "smoother", "smoother-split"), with these readings:
 * the printed update drops y^{(j-1)} and flips the sign; the update used is
