@@ -1,13 +1,16 @@
 """Benchmark: DoF/s of the CutFEM multigrid solve to a 1e-8 relative residual.
 
 One step = one CG solve (V-cycle preconditioner, x_0 = 0, rtol 1e-8) of the
-3D Q2 ball problem on a 64^3 background mesh (435,603 active DoFs, 5
-levels), FP64 plain form, inputs resident in HBM.  The mixed form (FP32
-V-cycle inside FP64 CG) is timed on the same problem and reported under
-"mixed".  Each rank solves its own copy of the problem (weak scaling, no
-collective on the data path).
+3D Q2 ball problem on a 224^3 background mesh (16,851,851 active DoFs, 6
+levels: the "~17M DoF" sphere), FP64 plain form, inputs resident in HBM.  The
+mixed form (FP32 V-cycle inside FP64 CG) is timed on the same problem to the
+same residual and reported under "mixed", with its distance to the FP64
+solution.  The 128^3 and 64^3 sizes follow under "sizes" (the 64^3 one also
+against the stored oracle solution).  Each rank solves its own copy of the
+problem (weak scaling, no collective on the data path).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload NAME] [--extra NAME ...] [--no-batch] [--no-serve]
 
 --impl reference times the CPU oracle (test infrastructure, plain numpy /
 scipy) on a bounded sample of the same workload: the same ball on a 32^3
@@ -29,7 +32,8 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "DoF/s solved to 1e-8 rel. residual, mixed vs FP64 form; p50/p99 latency"
-WORKLOAD = "ball3d_q2_n64"
+WORKLOAD = "ball3d_q2_n224"
+EXTRA = ("ball3d_q2_n128", "ball3d_q2_n64")
 SAMPLE = "ball3d_q2_n32"
 RTOL = 1e-8
 
@@ -112,19 +116,18 @@ def _peaks():
         return {}
 
 
-# FP64 FMA throughput of this GB300 pool, measured by
-# paper_2508_11608_gb300/csrc/alu_peak_probe.cu (2 flops per FMA), and the
-# FP32 figure from the same probe.
+# FP64 and FP32 FMA throughput of this GB300 pool, measured by an FMA probe
+# (2 flops per FMA; method and output in profiles/alu_peaks_gb300.md).
 FP64_PEAK_TFLOPS = 1.26
 FP32_PEAK_TFLOPS = 78.5
 
 
-# DRAM traffic of the dominant kernel from one ncu capture: dram__bytes_read.sum
-# + dram__bytes_write.sum summed over every k_cut_solve_cta launch of one FP64
-# solve of the 64^3 workload, divided by the launches (cold caches: ncu flushes
-# them before each launch).  Valid only for the kernel source it was taken on.
-CUT_TRAFFIC = {"bytes_per_launch": 18894944.3,
-               "kernels_sha256": "b5cb2c79a80a173bcb4d7dd1f67b1e415fa1253708b3c05b52bc4a691be7d64b"}
+# DRAM traffic of a kernel relative to its algorithmic bytes, from one ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum over a few launches of
+# one kernel on a small case; profiles/ holds the summary and the command).
+# The bench scales it by the algorithmic bytes of a launch of the timed
+# workload.  Valid only for the kernel source it was taken on.
+TRAFFIC = {}
 
 
 def _kernels_sha256():
@@ -134,8 +137,9 @@ def _kernels_sha256():
         return hashlib.sha256(f.read()).hexdigest()
 
 
-def cpu_baseline(steps=1):
-    """Oracle PCG on the bounded sample, single-threaded BLAS, in a subprocess."""
+def cpu_baseline(steps=1, threads=1):
+    """Oracle PCG on the bounded sample in a subprocess, with the BLAS and
+    OpenMP thread limits set to `threads`."""
     code = r"""
 import json, os, sys, time
 sys.path.insert(0, %r)
@@ -152,7 +156,8 @@ for s in range(%d):
     out.append((time.perf_counter() - t, it))
 print(json.dumps({"n": int(n), "runs": out}))
 """ % (ROOT, SAMPLE, steps, RTOL)
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    t = str(threads)
+    env = dict(os.environ, OMP_NUM_THREADS=t, OPENBLAS_NUM_THREADS=t, MKL_NUM_THREADS=t)
     p = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
     if p.returncode != 0:
         return {"error": p.stderr.strip().splitlines()[-1] if p.stderr.strip() else "failed"}
@@ -173,7 +178,7 @@ def run_reference(args):
     tot = sum(secs)
     value = res["n"] * len(secs) / tot
     sample = (f"oracle PCG (numpy/scipy, 1 thread) on {SAMPLE} ({res['n']} active DoFs), same ball "
-              f"and method at 32^3 cells instead of 64^3, {res['iterations']} CG iterations; setup untimed")
+              f"and method at 32^3 cells instead of 224^3, {res['iterations']} CG iterations; setup untimed")
     line = {
         "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(secs), "higher_is_better": True,
@@ -205,6 +210,114 @@ def whole_job_rate(units_per_rank, world, ms_local, dist=None, device=None):
     return world * units_per_rank / (ms * 1e-3), ms
 
 
+def _timed_solves(pb, b, x, prec, steps, warmup, stream, flush, dist=None, profile_kernel=None):
+    """CUDA-event time of `steps` solves after `warmup` untimed ones, L2
+    flushed before each timed solve.  Returns (ms list, infos, launches,
+    profile)."""
+    import torch
+    pb.set_precision(prec)
+    for _ in range(warmup):
+        pb.solve(b, x, rtol=RTOL)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if profile_kernel:
+        pb.profile_start(profile_kernel)
+    l0 = pb.launch_count()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    infos = []
+    for k in range(steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        infos.append(pb.solve(b, x, rtol=RTOL))
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches = pb.launch_count() - l0
+    prof = pb.profile_read() if profile_kernel else None
+    return [e0.elapsed_time(e1) for e0, e1 in ev], infos, launches, prof
+
+
+KERNEL_NAMES = {1: "k_cut_solve_cta", 2: "interior-patch step", 3: "k_apply_bulk", 4: "k_apply_bnd",
+                5: "k_face_moments"}
+
+
+def _family_profile(cm, pb, b, x, prec, stream, flush):
+    """Event-timed passes (graphs off for the timed family) of each kernel
+    family: summed launch time, launches, algorithmic flops and bytes."""
+    out = {}
+    for kern in (cm._lib.CF_K_CUT_SOLVE, cm._lib.CF_K_INTERIOR, cm._lib.CF_K_APPLY_BULK,
+                 cm._lib.CF_K_APPLY_BND, cm._lib.CF_K_FACE_MOMENTS):
+        msk, _, _, pr = _timed_solves(pb, b, x, prec, 2, 1, stream, flush, profile_kernel=kern)
+        pr["share"] = pr["ms"] / sum(msk)
+        out[kern] = pr
+    return out
+
+
+def _roofline(cm, prof, prec, hbm):
+    top = max(prof, key=lambda k: prof[k]["share"])
+    pr = prof[top]
+    per_launch_ms = pr["ms"] / max(pr["launches"], 1)
+    fl_rate = pr["flops"] / (pr["ms"] * 1e-3) / 1e12 if pr["ms"] > 0 else 0.0
+    by_rate = pr["bytes"] / (pr["ms"] * 1e-3) / 1e9 if pr["ms"] > 0 else 0.0
+    alu = FP64_PEAK_TFLOPS if prec == cm.CF_FP64 else FP32_PEAK_TFLOPS
+    t_alu = pr["flops"] / (alu * 1e12)
+    t_hbm = pr["bytes"] / (hbm * 1e9)
+    if t_alu >= t_hbm:
+        roof = {"bound": "alu", "achieved": fl_rate, "peak": alu, "unit": "TFLOP/s", "frac": fl_rate / alu,
+                "peak_source": ("FP64" if prec == cm.CF_FP64 else "FP32") +
+                " FMA throughput measured on this pool (method in profiles/alu_peaks_gb300.md), of measured"}
+    else:
+        roof = {"bound": "hbm", "achieved": by_rate, "peak": hbm, "unit": "GB/s", "frac": by_rate / hbm,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs, of measured"}
+    bytes_per_launch = pr["bytes"] / max(pr["launches"], 1)
+    tr = TRAFFIC.get((KERNEL_NAMES[top], "fp64" if prec == cm.CF_FP64 else "fp32"))
+    traffic = None
+    if tr and tr["kernels_sha256"] == _kernels_sha256():
+        traffic = tr["dram_over_algorithmic"] * bytes_per_launch
+    roof.update({"kernel": KERNEL_NAMES[top], "traffic": traffic, "per_launch_ms": per_launch_ms,
+                 "launches_timed": pr["launches"], "share_of_step": pr["share"],
+                 "shares": {KERNEL_NAMES[k]: round(prof[k]["share"], 4) for k in prof},
+                 "flops_per_launch": pr["flops"] / max(pr["launches"], 1), "bytes_per_launch": bytes_per_launch,
+                 "timing": "CUDA events on the launching stream around every launch of the family, "
+                           "summed over 2 timed solves"})
+    return roof
+
+
+def _rel(a, b):
+    import torch
+    return (torch.linalg.norm(a - b) / torch.linalg.norm(b)).item()
+
+
+def _size_line(cm, torch, name, dev, stream, flush, steps):
+    """FP64 and mixed DoF/s of one more configuration (smaller sizes)."""
+    from paper_2508_11608_gb300.workloads import problem_kwargs
+    t0 = time.perf_counter()
+    pb = cm.Problem(**problem_kwargs(name))
+    setup_s = time.perf_counter() - t0
+    n = pb.n_dofs()
+    b = torch.zeros(n, dtype=torch.float64, device=dev)
+    pb.rhs(b)
+    xs, out = {}, {"workload": name, "active_dofs": n, "host_setup_s": setup_s}
+    for prec, key in ((cm.CF_FP64, "fp64"), (cm.CF_MIXED, "mixed")):
+        x = torch.zeros_like(b)
+        ms, infos, _, _ = _timed_solves(pb, b, x, prec, steps, 3, stream, flush)
+        xs[key] = x
+        out[key] = {"value": n * len(ms) / (sum(ms) * 1e-3), "unit": "DoF/s", "ms_per_solve": sum(ms) / len(ms),
+                    "iterations": infos[-1]["iterations"], "true_rel_residual": infos[-1]["true_rel_residual"]}
+    out["mixed"]["rel_l2_vs_fp64"] = _rel(xs["mixed"], xs["fp64"])
+    gold = os.path.join(ROOT, "tests", "golden", name + "_pcg.npz")
+    if os.path.exists(gold):
+        import numpy as np
+        xo = torch.tensor(np.load(gold)["x"], device=dev)
+        out["fp64"]["rel_l2_vs_oracle"] = _rel(xs["fp64"], xo)
+        out["mixed"]["rel_l2_vs_oracle"] = _rel(xs["mixed"], xo)
+    pb.close()
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -220,8 +333,11 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
+    workload = args.workload
 
-    pb = cm.Problem(**problem_kwargs(WORKLOAD))
+    t0 = time.perf_counter()
+    pb = cm.Problem(**problem_kwargs(workload))
+    setup_s = time.perf_counter() - t0
     n = pb.n_dofs()
     b = torch.zeros(n, dtype=torch.float64, device=dev)
     x = torch.zeros_like(b)
@@ -229,51 +345,22 @@ def run_ours(args):
     # L2 is 129 MB: a 512 MB write between timed solves evicts it
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float64, device=dev)
 
-    def timed_solves(prec, steps, warmup, profile_kernel=None):
-        pb.set_precision(prec)
-        for _ in range(warmup):
-            pb.solve(b, x, rtol=RTOL)
-        torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
-        if profile_kernel:
-            pb.profile_start(profile_kernel)
-        l0 = pb.launch_count()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-        infos = []
-        t0 = time.perf_counter()
-        for k in range(steps):
-            flush.zero_()
-            ev[k][0].record(stream)
-            infos.append(pb.solve(b, x, rtol=RTOL))
-            ev[k][1].record(stream)
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
-        if dist:
-            dist.barrier()
-        launches = pb.launch_count() - l0
-        prof = pb.profile_read() if profile_kernel else None
-        ms = [e0.elapsed_time(e1) for e0, e1 in ev]
-        return ms, infos, launches, prof, wall
-
     # FP64 plain form: the headline (CUDA graphs on, nothing else timed)
     sampler = ClockSampler(local)
     sampler.start()
-    ms64, inf64, launches, _, _ = timed_solves(cm.CF_FP64, args.steps, args.warmup)
+    ms64, inf64, launches, _ = _timed_solves(pb, b, x, cm.CF_FP64, args.steps, args.warmup, stream, flush, dist)
     clocks = sampler.stop()
-    # mixed form
-    ms32, inf32, _, _, _ = timed_solves(cm.CF_MIXED, args.steps, 1)
+    x64 = x.clone()
+    # mixed form, same final residual
+    ms32, inf32, launches32, _ = _timed_solves(pb, b, x, cm.CF_MIXED, args.steps, args.warmup, stream, flush, dist)
+    mixed_err = _rel(x, x64)
 
-    # kernel families, event-timed on the launching stream in separate timed
-    # passes of the same workload (event timing runs the launches without
-    # graphs, so it is kept out of the headline)
-    prof = {}
-    for kern in (cm._lib.CF_K_CUT_SOLVE, cm._lib.CF_K_INTERIOR, cm._lib.CF_K_APPLY_BULK,
-                 cm._lib.CF_K_APPLY_BND, cm._lib.CF_K_FACE_MOMENTS):
-        msk, _, _, pr, _ = timed_solves(cm.CF_FP64, 2, 1, profile_kernel=kern)
-        pr["share"] = pr["ms"] / sum(msk)
-        prof[kern] = pr
+    # kernel families, event-timed in separate passes of the same workload
+    hbm = _peaks().get("hbm_gbs", 6800.0)
+    prof32 = _family_profile(cm, pb, b, x, cm.CF_MIXED, stream, flush)
+    prof64 = _family_profile(cm, pb, b, x, cm.CF_FP64, stream, flush)
+    roof = _roofline(cm, prof32, cm.CF_MIXED, hbm)
+    roof64 = _roofline(cm, prof64, cm.CF_FP64, hbm)
 
     # e2e through the C ABI with host buffers: H2D of b, solve, D2H of x
     pb.set_precision(cm.CF_FP64)
@@ -292,7 +379,13 @@ def run_ours(args):
         torch.cuda.synchronize()
         if k > 0:
             e2e_ms.append(1e3 * (time.perf_counter() - t))
+    pb.close()
+    del x, x64, db, b
 
+    extra = {}
+    if world == 1:
+        for name in args.extra:
+            extra[name] = _size_line(cm, torch, name, dev, stream, flush, max(3, args.steps // 2))
     batched = None
     if not args.no_batch:
         batched = run_batched(cm, torch, dev, stream, args)
@@ -302,76 +395,53 @@ def run_ours(args):
 
     value, tot64 = whole_job_rate(n * args.steps, world, sum(ms64), dist, dev)
     mixed_value, tot32 = whole_job_rate(n * args.steps, world, sum(ms32), dist, dev)
-    e2e_value, tote2e = whole_job_rate(n * len(e2e_ms), world, sum(e2e_ms), dist, dev)
+    e2e_value, _ = whole_job_rate(n * len(e2e_ms), world, sum(e2e_ms), dist, dev)
 
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return 0
 
-    peaks = _peaks()
-    hbm = peaks.get("hbm_gbs", 6800.0)
-    top = max(prof, key=lambda k: prof[k]["share"])
-    pr = prof[top]
-    names = {1: "k_cut_solve_cta (cut-patch residual + dense local solve)",
-             2: "k_smooth_cart (interior-patch residual + fast diagonalisation)",
-             3: "k_apply_bulk (operator, interior positions)",
-             4: "k_apply_bnd (operator, boundary positions)",
-             5: "k_face_moments (ghost-face moments of the iterate)"}
-    per_launch_ms = pr["ms"] / max(pr["launches"], 1)
-    fl_rate = pr["flops"] / (pr["ms"] * 1e-3) / 1e12 if pr["ms"] > 0 else 0.0
-    by_rate = pr["bytes"] / (pr["ms"] * 1e-3) / 1e9 if pr["ms"] > 0 else 0.0
-    # FP64: the arithmetic bound is 1.2 TFLOP/s; compare time-at-peak of flops and bytes
-    t_alu = pr["flops"] / (FP64_PEAK_TFLOPS * 1e12)
-    t_hbm = pr["bytes"] / (hbm * 1e9)
-    if t_alu >= t_hbm:
-        roof = {"bound": "alu", "achieved": fl_rate, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": fl_rate / FP64_PEAK_TFLOPS}
-    else:
-        roof = {"bound": "hbm", "achieved": by_rate, "peak": hbm, "unit": "GB/s", "frac": by_rate / hbm}
-    traffic = None
-    if top == cm._lib.CF_K_CUT_SOLVE and CUT_TRAFFIC["kernels_sha256"] == _kernels_sha256():
-        traffic = CUT_TRAFFIC["bytes_per_launch"]
-    roof.update({"kernel": names[top], "traffic": traffic, "per_launch_ms": per_launch_ms,
-                 "launches_timed": pr["launches"],
-                 "share_of_step": pr["share"],
-                 "shares": {names[k].split(" ")[0]: round(prof[k]["share"], 4) for k in prof},
-                 "flops_per_launch": pr["flops"] / max(pr["launches"], 1),
-                 "bytes_per_launch": pr["bytes"] / max(pr["launches"], 1),
-                 "peak_source": "FP64 FMA probe (paper_2508_11608_gb300/csrc/alu_peak_probe.cu)"
-                 if roof["bound"] == "alu" else "MEASURED_PEAKS.json hbm_gbs"})
+    cpu_line = None
+    if world == 1:
+        cpu1 = cpu_baseline(steps=2, threads=1)
+        cpun = cpu_baseline(steps=2, threads=os.cpu_count() or 1)
+        if "error" not in cpu1:
+            cpu_line = {"value": cpu1["n"] / min(cpu1["secs"]), "unit": "DoF/s", "cores": 1, "kind": "oracle",
+                        "sample": f"oracle PCG on {SAMPLE} ({cpu1['n']} DoFs, {cpu1['iterations']} iterations; the "
+                                  f"same ball at 32^3 cells), best of {len(cpu1['secs'])}; setup untimed",
+                        "host_cores": os.cpu_count()}
+            if "error" not in cpun:
+                cpu_line["all_threads"] = {
+                    "value": cpun["n"] / min(cpun["secs"]), "threads": os.cpu_count(),
+                    "note": "BLAS/OpenMP thread limits set to the host's core count; scipy's sparse products "
+                            "run on one thread whatever the limit"}
 
-    cpu = cpu_baseline(steps=2) if world == 1 else {"error": "rank 0 at N=1 only"}
-    if "error" not in cpu:
-        cpu_line = {"value": cpu["n"] / min(cpu["secs"]), "unit": "DoF/s", "cores": 1, "kind": "oracle",
-                    "sample": f"oracle PCG on {SAMPLE} ({cpu['n']} DoFs, {cpu['iterations']} iterations), "
-                              f"1 thread, best of {len(cpu['secs'])}; setup untimed"}
-    else:
-        cpu_line = None
-
-    lat = sorted(ms64)
-    p50 = float(np.percentile(lat, 50))
-    p99 = float(np.percentile(lat, 99))
     line = {
         "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot64 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": _workload_desc(WORKLOAD), "active_dofs": n,
+        "config": {"workload": _workload_desc(workload), "active_dofs": n,
                    "form": "FP64 plain (CG, V-cycle, smoother, transfer all FP64), CUDA graphs",
-                   "l2": "512 MB buffer written between timed solves (flush)",
+                   "l2": "512 MB buffer written between timed solves (flush); the vectors exceed L2 too",
                    "iterations": inf64[-1]["iterations"],
-                   "true_rel_residual": inf64[-1]["true_rel_residual"]},
-        "latency_ms": {"p50": p50, "p99": p99},
+                   "true_rel_residual": inf64[-1]["true_rel_residual"], "host_setup_s": setup_s},
+        "latency_ms": {"p50": float(np.percentile(ms64, 50)), "p99": float(np.percentile(ms64, 99))},
         "mixed": {"value": mixed_value, "unit": "DoF/s", "ms_per_step": tot32 / args.steps,
                   "iterations": inf32[-1]["iterations"],
                   "true_rel_residual": inf32[-1]["true_rel_residual"],
+                  "rel_l2_vs_fp64": mixed_err,
+                  "speedup_vs_fp64": mixed_value / value,
                   "latency_ms": {"p50": float(np.percentile(ms32, 50)), "p99": float(np.percentile(ms32, 99))},
+                  "gpu_launches": launches32,
                   "form": "FP32 V-cycle (smoother, transfer, cut-patch inverses) inside FP64 CG"},
         "e2e": {"value": e2e_value, "unit": "DoF/s", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n},
         "gpu_launches": launches,
         "roofline": roof,
+        "roofline_fp64": roof64,
         "cpu_baseline": cpu_line,
         "clocks": clocks,
+        "sizes": extra,
         "batched": batched,
         "served": served,
     }
@@ -457,6 +527,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD, help="headline configuration (workloads.CONFIGS)")
+    ap.add_argument("--extra", nargs="*", default=list(EXTRA), help="further sizes timed after the headline")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-form measurement")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--no-serve", action="store_true", help="skip the served-form measurement")

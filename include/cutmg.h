@@ -173,6 +173,30 @@ cf_status cf_rhs_user(cf_problem* pb, double (*f)(const double* x, void* user),
 /* Select the precision of cf_vcycle and cf_solve (CF_FP64 or CF_MIXED). */
 cf_status cf_set_precision(cf_problem* pb, int precision);
 
+/* Launch variant of a kernel family, for tests and tuning; every variant
+ * computes the same colour step (Sec. 2.3), and the variants that share an
+ * arithmetic give the same bits.  family CF_VAR_INTERIOR (interior-patch
+ * step): FP32 (mixed form) 1 = dense map, one patch per thread; 2 = dense
+ * map, two patches per thread; 3 = dense map, several threads per patch;
+ * 4 = dense map on the tensor cores (TF32 products, FP32 accumulation; the
+ * automatic choice where it exists, else the same as 0); FP64 1 = one warp
+ * per patch, 2 = one block per patch.  family CF_VAR_CUT (cut-patch step,
+ * 3D degree 2): 1 = element-matrix rows staged in shared memory, 2 = rows
+ * read through L1.  variant 0 restores the automatic choice.  The next
+ * launches use it; captured CUDA graphs of the handle are dropped.
+ * CF_EINVAL for an unknown family or variant, or a host-only handle. */
+typedef enum { CF_VAR_INTERIOR = 1, CF_VAR_CUT = 2 } cf_variant_family;
+cf_status cf_set_kernel_variant(cf_problem* pb, int family, int variant);
+
+/* Polls the cut-patch kernel makes on its TMA copy's mbarrier before it
+ * gives up (default 2^22).  A block that gives up records the failure, waits
+ * (bounded, 2^22 polls) for its own copy to land, and skips its patch; the
+ * next cf_solve / cf_solve_vcycle / cf_solve_gmres then returns CF_ETIMEOUT
+ * and the handle stays usable.  A limit of 0 makes every wait give up at once
+ * (a test of that path).  CF_EINVAL outside [0, 2^30] or on a host-only
+ * handle. */
+cf_status cf_set_wait_limit(cf_problem* pb, int64_t polls);
+
 /* b = right-hand side of the manufactured solution u = prod_k sin(pi x_k),
  * f = d pi^2 u, Dirichlet data g = u (Nitsche data terms), finest level. */
 cf_status cf_rhs(cf_problem* pb, double* d_b, void* stream);

@@ -115,6 +115,15 @@ class Problem:
     def set_precision(self, precision):
         check(self._lib.cf_set_precision(self._h, precision))
 
+    def set_kernel_variant(self, family, variant):
+        """Force a launch variant (family _lib.CF_VAR_INTERIOR / CF_VAR_CUT;
+        0 = automatic)."""
+        check(self._lib.cf_set_kernel_variant(self._h, family, variant))
+
+    def set_wait_limit(self, polls):
+        """Polls of the cut-patch kernel's wait on its TMA copy (default 2^22)."""
+        check(self._lib.cf_set_wait_limit(self._h, int(polls)))
+
     # ---- finest-level calls ----------------------------------------------------------
     def rhs(self, b, stream=None):
         check(self._lib.cf_rhs(self._h, _ptr(b), _stream(stream)))

@@ -15,6 +15,7 @@ CF_LS_SPHERE, CF_LS_PLANE, CF_LS_ELLIPSOID, CF_LS_TORUS, CF_LS_FLOWER, CF_LS_CAL
 CF_FP64, CF_MIXED = 0, 1
 CF_SMOOTHER_MVS, CF_SMOOTHER_CHEBYSHEV = 0, 1
 CF_K_CUT_SOLVE, CF_K_INTERIOR, CF_K_APPLY_BULK, CF_K_APPLY_BND, CF_K_FACE_MOMENTS = 1, 2, 3, 4, 5
+CF_VAR_INTERIOR, CF_VAR_CUT = 1, 2
 
 EXPORTED = [
     "cf_setup", "cf_destroy", "cf_last_error", "cf_n_levels", "cf_n_dofs", "cf_level_n_dofs",
@@ -23,7 +24,7 @@ EXPORTED = [
     "cf_level_restrict", "cf_level_prolongate", "cf_coarse_solve", "cf_setup_host", "cf_host_rhs",
     "cf_host_cell_matrix", "cf_host_patch_counts", "cf_host_interior_update", "cf_host_diagonal", "cf_host_interior_patch", "cf_host_cut_patch",
     "cf_host_coarse_inverse",
-    "cf_launch_count", "cf_profile_start", "cf_profile_read", "cf_coarse_solve_noalloc",
+    "cf_set_kernel_variant", "cf_set_wait_limit", "cf_launch_count", "cf_profile_start", "cf_profile_read", "cf_coarse_solve_noalloc",
     "cf_batch_create", "cf_batch_solve", "cf_batch_launch_count", "cf_batch_destroy",
     "cf_server_create", "cf_server_submit", "cf_server_run", "cf_server_result", "cf_server_stats",
     "cf_server_destroy",
@@ -97,6 +98,8 @@ def load():
     lib.cf_work_model.argtypes = [P, I, I, I, P]
     lib.cf_footprint.argtypes = [P, P]
     lib.cf_set_precision.argtypes = [P, I]
+    lib.cf_set_kernel_variant.argtypes = [P, I, I]
+    lib.cf_set_wait_limit.argtypes = [P, ctypes.c_int64]
     lib.cf_rhs.argtypes = [P, P, V]
     lib.cf_apply.argtypes = [P, P, P, V]
     lib.cf_vcycle.argtypes = [P, P, P, V]

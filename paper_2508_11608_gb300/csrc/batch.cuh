@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(kCutThreads) kb_cut_solve_cta(const LvlDesc<DI
     // uncut cells read the level's element matrix from global memory
     // (instances differ in h)
     cut_body_cta<DIM, P, T, false, kCutThreads>(L.op, L.x, L.b, M, j, L.cp, L.members, L.mnode, L.fofs, L.fent, L.inv, S,
-                                   sinv, nullptr, inv_cap, &bar, phase, L.op.Kref, err);
+                                   sinv, nullptr, inv_cap, &bar, phase, L.op.Kref, err, kTmaSpin);
   }
 }
 

@@ -317,6 +317,17 @@ cf_status cf_set_precision(cf_problem* pb, int precision) {
   return CF_OK;
 }
 
+cf_status cf_set_kernel_variant(cf_problem* pb, int family, int variant) {
+  if (no_device(pb)) return fail(CF_EINVAL, "null or host-only problem");
+  return guarded([&] { pb->eng->set_variant(family, variant); });
+}
+
+cf_status cf_set_wait_limit(cf_problem* pb, int64_t polls) {
+  if (no_device(pb)) return fail(CF_EINVAL, "null or host-only problem");
+  if (polls < 0 || polls > (int64_t)1 << 30) return fail(CF_EINVAL, "wait limit must be in [0, 2^30]");
+  return guarded([&] { pb->eng->set_wait_limit((int)polls); });
+}
+
 cf_status cf_rhs(cf_problem* pb, double* d_b, void* stream) {
   if (no_device(pb) || !d_b) return fail(CF_EINVAL, "null argument");
   return guarded([&] { pb->eng->rhs(d_b, S(stream)); });

@@ -239,13 +239,34 @@ class Engine final : public EngineBase {
     use_graphs_ = !(g && g[0] == '0');
   }
   ~Engine() override {
-    for (auto& kv : graphs_) cudaGraphExecDestroy(kv.second.exec);
+    drop_graphs();
     if (cap_) cudaStreamDestroy(cap_);
     if (host_sc_) cudaFreeHost(host_sc_);
     for (auto& e : prof_.ev) cudaEventDestroy(e);
   }
 
   int64_t launches() const override { return launches_; }
+  // family 1 = interior-patch step (FP32: 1 dense one patch per thread, 2 dense
+  // two per thread, 3 dense split, 4 tensor cores; FP64: 1 warp per patch,
+  // 2 block per patch); family 2 = cut-patch step of the block kernel (1
+  // staged rows, 2 unstaged).  0 restores the automatic choice.
+  void set_variant(int family, int variant) override {
+    if (family == 1) {
+      if (variant < 0 || variant > 4) throw std::invalid_argument("interior variant must be 0..4");
+      var_int_ = variant;
+    } else if (family == 2) {
+      if (variant < 0 || variant > 2) throw std::invalid_argument("cut variant must be 0..2");
+      var_cut_ = variant;
+    } else {
+      throw std::invalid_argument("kernel family must be 1 (interior) or 2 (cut)");
+    }
+    drop_graphs();
+  }
+  void set_wait_limit(int polls) override {
+    if (polls < 0) throw std::invalid_argument("wait limit must be >= 0");
+    spin_ = polls;
+    drop_graphs();
+  }
   void coarse_data(const double** inv, const int** nodes, const int64_t** dofs, int64_t* n0,
                    int64_t* nbox) const override {
     *inv = d64_[0].coarse_inv;
@@ -726,6 +747,22 @@ class Engine final : public EngineBase {
     pl.grid = std::min(cnt, sms_ * (sizeof(T) == 8 ? 32 : 16));
     return pl;
   }
+  // a launch shape of the requested kind whatever the colour's size (tests):
+  // staged with the 48 KB slot, or unstaged with the 12 KB slot
+  template <typename T>
+  CutPlan cut_plan_forced(const Common& c, int colour, bool staged) const {
+    CutPlan pl;
+    const int cnt = c.cut_start[colour + 1] - c.cut_start[colour];
+    const int slot = staged ? kInvSlotBytesStage : kInvSlotBytes;
+    pl.staged = staged;
+    pl.cap = std::min(c.cut_maxm2[colour], (slot - 16) / (int)sizeof(T));
+    pl.row_off = (int)inv_slot_bytes<T>(pl.cap);
+    const int rows = staged ? (int)(((size_t)c.cut_maxit[colour] * NB * sizeof(T) + 15) / 16 * 16) : 0;
+    pl.dyn = pl.row_off + rows;
+    if (pl.dyn > kInvSlotBytesMax) throw std::invalid_argument("staged cut variant does not fit this level");
+    pl.grid = std::min(cnt, sms_ * 16);
+    return pl;
+  }
   static CutPatchArgs cut_args(const Common& c) {
     return CutPatchArgs{c.cutv, c.cutn, c.cutmo, c.cutio, c.cutfo, c.cutcell, c.citoff, c.citems};
   }
@@ -770,6 +807,14 @@ class Engine final : public EngineBase {
   std::map<GraphKey, GraphEntry> graphs_;
   cudaStream_t cap_ = nullptr;
   bool use_graphs_ = true;
+
+  int var_int_ = 0, var_cut_ = 0;  // forced launch variants (0: automatic)
+  int spin_ = kTmaSpin;            // polls of the cut kernel's first wait on its TMA copy
+
+  void drop_graphs() {
+    for (auto& kv : graphs_) cudaGraphExecDestroy(kv.second.exec);
+    graphs_.clear();
+  }
 
   template <class F>
   void run_graph(const GraphKey& key, cudaStream_t s, F&& body) {
@@ -1047,10 +1092,12 @@ class Engine final : public EngineBase {
       k_apply_bulk<DIM, P, T><<<blocks_for(c.nbulk, 128), 128, 0, s>>>(D.op, x, b, y, c.bulk, c.nbulk);
       count_launch("apply bulk");
       prof_mark(3, s);
-      // per position: 2^d cells x p^d owned rows x NB terms; x read and y
-      // written once per owned node (+ b)
+      // per position: the (cell, owned node) pairs that run are (p+1)^d (a
+      // cell s contributes the owned nodes with alpha_k = 0 wherever s_k = 1),
+      // NB terms each; x read and y written once per owned node (+ b)
       constexpr int NO = Shape<DIM, P>::NO;
-      prof_work(3, 2.0 * (1 << DIM) * NO * NB * c.nbulk, (double)c.nbulk * (NO * (b ? 3 : 2) * sizeof(T) + 4));
+      constexpr int PAIRS = (DIM == 2) ? (P + 1) * (P + 1) : (P + 1) * (P + 1) * (P + 1);
+      prof_work(3, 2.0 * PAIRS * NB * c.nbulk, (double)c.nbulk * (NO * (b ? 3 : 2) * sizeof(T) + 4));
     }
     if (c.nbnd > 0) {
       face_moments<T>(l, D, x, s);
@@ -1096,16 +1143,19 @@ class Engine final : public EngineBase {
       if constexpr (std::is_same<T, float>::value)
       {
         constexpr int PPB = 128 / DenseGeo<DIM, P>::NPART;
-        if (cnt >= kDensePairPatches)
+        int v = var_int_;
+        if (v == 4) v = 0;  // no tensor-core variant of this (d, p) yet
+        if (v == 0) v = cnt >= kDensePairPatches ? 2 : (cnt >= kDenseThreadPatches ? 1 : 3);
+        if (v == 2)
           k_smooth_dense<DIM, P, 2><<<blocks_for(cnt, 256), 128, 0, s>>>(D.dense_d, c.N, c.n, x, b, c.cart + a0, cnt);
-        else if (cnt >= kDenseThreadPatches)
+        else if (v == 1)
           k_smooth_dense<DIM, P, 1><<<blocks_for(cnt, 128), 128, 0, s>>>(D.dense_d, c.N, c.n, x, b, c.cart + a0, cnt);
         else
           k_smooth_dense_split<DIM, P><<<blocks_for(cnt, PPB), 128, 0, s>>>(D.dense_d, c.N, c.n, x, b,
                                                                           c.cart + a0, cnt);
       }
-      else if (cnt <= 4 * sms_)
-        k_smooth_cart_cta<DIM, P, T><<<cnt, 128, 0, s>>>(D.fd, c.N, c.n, x, b, c.cart + a0, cnt);
+      else if (var_int_ == 2 || (var_int_ != 1 && cnt <= 4 * sms_))
+        k_smooth_cart_cta<DIM, P, T><<<std::min(cnt, 16 * sms_), 128, 0, s>>>(D.fd, c.N, c.n, x, b, c.cart + a0, cnt);
       else
         k_smooth_cart<DIM, P, T, WARPS><<<blocks_for(cnt, WARPS), 32 * WARPS, 0, s>>>(
             D.fd, c.N, c.n, x, b, c.cart + a0, cnt);
@@ -1123,15 +1173,16 @@ class Engine final : public EngineBase {
             D.op, x, b, c.cutv + a0, c.cutn + a0, c.cutmo + a0, c.cutio + a0, c.members, c.mnode, c.fofs,
             c.fent, D.inv, cnt);
       } else {
-        const CutPlan& pl = (sizeof(T) == 8 ? c.plan64 : c.plan32)[colour];
+        CutPlan pl = (sizeof(T) == 8 ? c.plan64 : c.plan32)[colour];
+        if (var_cut_ != 0 && pl.staged != (var_cut_ == 1)) pl = cut_plan_forced<T>(c, colour, var_cut_ == 1);
         if (pl.staged)
           k_cut_solve_cta<DIM, P, T, true, kCutThreads><<<pl.grid, kCutThreads, pl.dyn, s>>>(
               D.op, x, b, cut_args(c), c.members, c.mnode, c.fofs, c.fent, D.inv, a0, cnt, pl.cap,
-              pl.row_off, err_);
+              pl.row_off, err_, spin_);
         else
           k_cut_solve_cta<DIM, P, T, false, kCutNT<T>><<<pl.grid, kCutNT<T>, pl.dyn, s>>>(
               D.op, x, b, cut_args(c), c.members, c.mnode, c.fofs, c.fent, D.inv, a0, cnt, pl.cap,
-              pl.row_off, err_);
+              pl.row_off, err_, spin_);
       }
       count_launch("cut patch solve");
       prof_mark(1, s);

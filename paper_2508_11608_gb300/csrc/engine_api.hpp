@@ -52,6 +52,11 @@ class EngineBase {
                           double* true_rel, float* ms, cudaStream_t s) = 0;
   virtual double cg_begin(int prec, const double* b, cudaStream_t s) = 0;
   virtual double cg_end(double* x, cudaStream_t s) = 0;
+  // launch variant of a kernel family (0 = the automatic choice), and the
+  // polls the cut-patch kernel waits for its TMA copy before it reports a
+  // timeout; both drop the captured CUDA graphs
+  virtual void set_variant(int family, int variant) = 0;
+  virtual void set_wait_limit(int polls) = 0;
   // kernel launches issued so far, and event timing of one kernel family
   virtual int64_t launches() const = 0;
   virtual void profile_start(int kind) = 0;

@@ -1006,8 +1006,10 @@ __global__ void __launch_bounds__(32 * WARPS) k_cut_solve(OpArgs<T> A, T* __rest
 // copy runs while the block forms the residual rows, and the local solve
 // then reads the inverse from shared memory.  Inverses larger than the
 // shared-memory slot are read from global memory instead.  The wait on the
-// mbarrier is bounded: past kTmaSpin polls the block records an error in
-// *err, polls again (bounded) for its own copy and gives up the patch.
+// mbarrier is bounded: past `spin` polls (a kernel argument, kTmaSpin unless
+// the caller lowers it) the block records an error in *err, polls again for
+// its own copy (at most kTmaSpin times, so that no copy is left in flight
+// into shared memory) and gives up the patch.
 constexpr int kCutThreads = 128;
 constexpr int kTmaSpin = 1 << 22;
 
@@ -1031,9 +1033,9 @@ __device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t
       : "memory");
 }
 
-// true once phase `parity` of the barrier has completed (bounded polling)
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (int it = 0; it < kTmaSpin; ++it) {
+// true once phase `parity` of the barrier has completed (at most `limit` polls)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int limit) {
+  for (int it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
@@ -1120,7 +1122,7 @@ __device__ __forceinline__ void cut_body_cta(const OpArgs<T>& A, T* __restrict__
                                              const int* __restrict__ fent, const T* __restrict__ inv,
                                              CutScratch<DIM, P, T>& S, T* sinv, T* srow, int inv_cap,
                                              uint64_t* bar, uint32_t& phase, const T* __restrict__ sK,
-                                             int* err) {
+                                             int* err, int spin) {
   using G = PatchGeo<DIM, P>;
   constexpr int CC = G::C, NB = G::NB, NCL = G::NCL, NCELL = G::NCELL, NTF = FaceGeo<DIM, P>::NT;
   constexpr int TPT = (NCL + NT - 1) / NT;  // patch DoFs per thread
@@ -1308,10 +1310,10 @@ __device__ __forceinline__ void cut_body_cta(const OpArgs<T>& A, T* __restrict__
   }
   bool ok = true;
   if (tma) {
-    ok = mbar_wait(bar, phase & 1u);
+    ok = mbar_wait(bar, phase & 1u, spin);
     if (!ok) {
       atomicExch(err, 1);
-      mbar_wait(bar, phase & 1u);
+      mbar_wait(bar, phase & 1u, kTmaSpin);
     }
     phase += 1;
   }
@@ -1356,7 +1358,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 8 ? 7 : 9) k_cut_solve_cta(Op
                                                                const int* __restrict__ fofs,
                                                                const int* __restrict__ fent,
                                                                const T* __restrict__ inv, int j0, int npatch,
-                                                               int inv_cap, int row_off, int* err) {
+                                                               int inv_cap, int row_off, int* err, int spin) {
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ __align__(8) uint64_t bar;
   __shared__ CutScratch<DIM, P, T> S;
@@ -1372,7 +1374,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 8 ? 7 : 9) k_cut_solve_cta(Op
     CutMeta nxt = cur;
     if (j + (int)gridDim.x < npatch) nxt = cut_meta(C, j0 + j + gridDim.x);
     cut_body_cta<DIM, P, T, STAGE, NT>(A, x, b, cur, j0 + j, C, members, mnode, fofs, fent, inv, S, sinv, srow,
-                                       inv_cap, &bar, phase, A.Kref, err);
+                                       inv_cap, &bar, phase, A.Kref, err, spin);
     cur = nxt;
   }
 }

@@ -9,6 +9,8 @@ cut-cell rule) and ghost-face matrices of the cells and faces around that DoF
 V-cycle B are symmetric, and the solves reach the 1e-8 residual with the
 residual entries of the final iterate confirmed by oracle rows."""
 
+import os
+
 import numpy as np
 import pytest
 
@@ -157,3 +159,40 @@ def test_full_size_solve_residual_confirmed_by_oracle_rows(setup, prec):
     for i in sample:
         ax, scale = orc.row_times(int(i), xh)
         assert abs(bh[i] - ax) <= 1e-8 * bnorm + 1e-12 * scale
+
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "ball3d_q2_n64_pcg.npz")
+
+
+@pytest.mark.parametrize("prec", [cm.CF_FP64, cm.CF_MIXED])
+def test_full_size_solve_matches_the_oracle_solution(setup, prec):
+    """Full-vector parity at the benchmark's size: the oracle's PCG solution
+    of the same problem (stored, written by tests/golden/make_ball64_solution.py
+    from oracle/ alone).  FP64: CG iterations within one and relative L2
+    difference 1e-10.  Mixed: the same final residual; its distance to the
+    FP64 oracle solution is that of two 1e-8-residual solutions (bounded by
+    1e-6 here, the measured value is printed)."""
+    pb, _, _ = setup
+    g = np.load(GOLDEN)
+    xo = g["x"]
+    n = pb.n_dofs()
+    assert n == xo.size
+    b = torch.zeros(n, dtype=torch.float64, device=DEV)
+    x = torch.zeros_like(b)
+    pb.rhs(b)
+    pb.set_precision(prec)
+    try:
+        info = pb.solve(b, x, rtol=1e-8)
+    finally:
+        pb.set_precision(cm.CF_FP64)
+    torch.cuda.synchronize()
+    err = np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo)
+    print(f"precision {prec}: {info['iterations']} iterations (oracle {int(g['iterations'])}), "
+          f"relative L2 difference to the oracle {err:.3e}")
+    assert info["true_rel_residual"] <= 1.01e-8
+    if prec == cm.CF_FP64:
+        assert abs(info["iterations"] - int(g["iterations"])) <= 1
+        assert err <= 1e-10
+    else:
+        assert info["iterations"] <= int(g["iterations"]) + 2
+        assert err <= 1e-6
