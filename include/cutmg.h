@@ -128,14 +128,19 @@ typedef struct {
 
 typedef struct cf_problem cf_problem;
 
-/* Build the hierarchy: classification, cut-cell quadrature, cell and patch
- * matrices (host, FP64), upload to the current device.  Blocking.
- * Errors: CF_EINVAL (bad sizes, degree, kind; a domain that misses the mesh
- * or whose boundary crosses no cell, which leaves no Dirichlet condition; a
- * coarsest level above 12,000 DoFs), CF_EUNSUPPORTED (dim 3 with degree 3),
- * CF_ENOMEM, CF_ECUDA. */
+/* Build the hierarchy (Sec. 2.1 operators on every level, Sec. 2.2 transfer,
+ * Sec. 2.3 / Sec. 3 patches): classification, cut-cell quadrature, cell and
+ * patch matrices (host, FP64), then the upload to the current device, ordered
+ * on `stream` (a cudaStream_t, 0 = legacy default stream).  Blocking: the
+ * call synchronises `stream` before it returns, so the handle is ready for
+ * any stream.  *out receives the handle (NULL on failure); the caller owns
+ * it and releases it with cf_destroy.
+ * Errors: CF_EINVAL (null argument, bad sizes, degree, kind; a domain that
+ * misses the mesh or whose boundary crosses no cell, which leaves no
+ * Dirichlet condition; a coarsest level above 12,000 DoFs), CF_EUNSUPPORTED
+ * (dim 3 with degree 3), CF_ENOMEM, CF_ECUDA. */
 cf_status cf_setup(const cf_mesh* mesh, const cf_levelset* ls, int degree,
-                   const cf_params* params, cf_problem** out);
+                   const cf_params* params, void* stream, cf_problem** out);
 void cf_destroy(cf_problem* pb);
 const char* cf_last_error(void);
 
@@ -354,11 +359,20 @@ cf_status cf_profile_read(cf_problem* pb, double* ms, int64_t* launches, double*
  * every device call on it returns CF_EINVAL. */
 cf_status cf_setup_host(const cf_mesh* mesh, const cf_levelset* ls, int degree,
                         const cf_params* params, cf_problem** out);
-/* Device memory a device handle of this problem holds (hierarchy in both
- * precisions, CG vectors, graph scratch), estimated from the host setup: the
- * figure the served form admits requests by (Sec. 5's resident
- * hierarchies).  Works on host-only and device handles; CF_EINVAL on null. */
-cf_status cf_footprint(const cf_problem* pb, size_t* bytes);
+/* Device memory cf_setup of this problem would hold (hierarchy in both
+ * precisions, CG vectors, graph scratch), estimated BEFORE any setup: the
+ * call classifies the cells of every level and builds the index lists
+ * (DoFs, ghost faces, patches and their DoF sets), but no cut-cell
+ * quadrature, element matrix, inverse or right-hand side.  The served form
+ * admits requests by this figure (Sec. 5's resident hierarchies) and refuses
+ * one that can never fit before building it.  Equal to cf_problem_footprint
+ * of the built problem.  Arguments as for cf_setup; *bytes receives the
+ * estimate.  Errors as cf_setup's argument checks (CF_EINVAL,
+ * CF_EUNSUPPORTED). */
+cf_status cf_footprint(const cf_mesh* mesh, const cf_levelset* ls, int degree, const cf_params* params,
+                       size_t* bytes);
+/* The same estimate for a built handle (host-only or device). CF_EINVAL on null. */
+cf_status cf_problem_footprint(const cf_problem* pb, size_t* bytes);
 /* Finest-level right-hand side (host array of cf_n_dofs doubles). */
 cf_status cf_host_rhs(const cf_problem* pb, double* h_b);
 /* cf_rhs_user into a host array (works on host-only handles). */

@@ -23,12 +23,27 @@ def _stream(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
+def footprint(dim, n_cells, n_levels, degree, levelset, lo=-1.0, hi=1.0, n_c=0, setup_threads=0):
+    """Device bytes a cf_setup of this problem would hold, estimated before
+    any setup (cf_footprint: classification and index lists only)."""
+    lib = _lib.load()
+    mesh = _lib.cf_mesh(dim, n_cells, lo, hi, n_levels)
+    ls = _lib.make_levelset(levelset)
+    prm = _lib.cf_params()
+    prm.n_c = n_c
+    prm.setup_threads = setup_threads
+    out = ctypes.c_size_t()
+    check(lib.cf_footprint(ctypes.byref(mesh), ctypes.byref(ls), degree, ctypes.byref(prm), ctypes.byref(out)))
+    return out.value
+
+
 class Problem:
     """A resident multigrid hierarchy (cf_setup .. cf_destroy)."""
 
     def __init__(self, dim, n_cells, n_levels, degree, center=None, radius=None, plane=None,
                  levelset=None, lo=-1.0, hi=1.0, gamma_D=0.0, gamma_ghost=(0.0,) * 4, n_c=0,
-                 quad_q=0, precision=CF_FP64, host_only=False, smoother=0, smoother_degree=0, setup_threads=None):
+                 quad_q=0, precision=CF_FP64, host_only=False, smoother=0, smoother_degree=0, setup_threads=None,
+                 stream=None):
         lib = _lib.load()
         self._lib = lib
         mesh = _lib.cf_mesh(dim, n_cells, lo, hi, n_levels)
@@ -53,8 +68,12 @@ class Problem:
             setup_threads = 1 if spec.get("kind") == "callback" else 0
         prm.setup_threads = setup_threads
         h = ctypes.c_void_p()
-        setup = lib.cf_setup_host if host_only else lib.cf_setup
-        check(setup(ctypes.byref(mesh), ctypes.byref(ls), degree, ctypes.byref(prm), ctypes.byref(h)))
+        if host_only:
+            check(lib.cf_setup_host(ctypes.byref(mesh), ctypes.byref(ls), degree, ctypes.byref(prm),
+                                    ctypes.byref(h)))
+        else:
+            check(lib.cf_setup(ctypes.byref(mesh), ctypes.byref(ls), degree, ctypes.byref(prm),
+                               _stream(stream), ctypes.byref(h)))
         self._h = h
         self.dim = dim
         self.degree = degree
@@ -102,7 +121,7 @@ class Problem:
     def footprint(self):
         """Estimated device bytes of this problem's device handle."""
         out = ctypes.c_size_t()
-        check(self._lib.cf_footprint(self._h, ctypes.byref(out)))
+        check(self._lib.cf_problem_footprint(self._h, ctypes.byref(out)))
         return out.value
 
     def work_model(self, level, kind, colour):

@@ -19,7 +19,7 @@ CF_VAR_INTERIOR, CF_VAR_CUT = 1, 2
 
 EXPORTED = [
     "cf_setup", "cf_destroy", "cf_last_error", "cf_n_levels", "cf_n_dofs", "cf_level_n_dofs",
-    "cf_dof_lattice", "cf_dof_coords", "cf_stats", "cf_work_model", "cf_footprint", "cf_set_precision", "cf_rhs", "cf_apply",
+    "cf_dof_lattice", "cf_dof_coords", "cf_stats", "cf_work_model", "cf_footprint", "cf_problem_footprint", "cf_set_precision", "cf_rhs", "cf_apply",
     "cf_vcycle", "cf_solve", "cf_solve_vcycle", "cf_solve_gmres", "cf_rhs_user", "cf_host_rhs_user", "cf_level_apply", "cf_level_colour_step", "cf_level_smooth",
     "cf_level_restrict", "cf_level_prolongate", "cf_coarse_solve", "cf_setup_host", "cf_host_rhs",
     "cf_host_cell_matrix", "cf_host_patch_counts", "cf_host_interior_update", "cf_host_diagonal", "cf_host_interior_patch", "cf_host_cut_patch",
@@ -83,7 +83,9 @@ def load():
     lib = ctypes.CDLL(LIB_PATH)
     P, I, D, V = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_void_p
     lib.cf_setup.argtypes = [ctypes.POINTER(cf_mesh), ctypes.POINTER(cf_levelset), I,
-                             ctypes.POINTER(cf_params), ctypes.POINTER(P)]
+                             ctypes.POINTER(cf_params), V, ctypes.POINTER(P)]
+    lib.cf_setup_host.argtypes = [ctypes.POINTER(cf_mesh), ctypes.POINTER(cf_levelset), I,
+                                  ctypes.POINTER(cf_params), ctypes.POINTER(P)]
     lib.cf_destroy.argtypes = [P]
     lib.cf_destroy.restype = None
     lib.cf_last_error.restype = ctypes.c_char_p
@@ -96,7 +98,9 @@ def load():
     lib.cf_dof_coords.argtypes = [P, I, P]
     lib.cf_stats.argtypes = [P, I, P]
     lib.cf_work_model.argtypes = [P, I, I, I, P]
-    lib.cf_footprint.argtypes = [P, P]
+    lib.cf_footprint.argtypes = [ctypes.POINTER(cf_mesh), ctypes.POINTER(cf_levelset), I,
+                                 ctypes.POINTER(cf_params), P]
+    lib.cf_problem_footprint.argtypes = [P, P]
     lib.cf_set_precision.argtypes = [P, I]
     lib.cf_set_kernel_variant.argtypes = [P, I, I]
     lib.cf_set_wait_limit.argtypes = [P, ctypes.c_int64]
@@ -114,7 +118,6 @@ def load():
     lib.cf_level_restrict.argtypes = [P, I, I, P, P, V]
     lib.cf_level_prolongate.argtypes = [P, I, I, P, P, V]
     lib.cf_coarse_solve.argtypes = [P, I, P, P, V]
-    lib.cf_setup_host.argtypes = lib.cf_setup.argtypes
     lib.cf_host_rhs.argtypes = [P, P]
     lib.cf_host_cell_matrix.argtypes = [P, I, ctypes.c_int64, P]
     lib.cf_host_patch_counts.argtypes = [P, I, P, P]

@@ -85,10 +85,11 @@ cf_status cutmg_noalloc_engine(cf_problem* pb, EngineBase** eng, int* device) {
 
 const char* cf_last_error(void) { return g_err.c_str(); }
 
-static cf_status setup_impl(const cf_mesh* mesh, const cf_levelset* ls, int degree, const cf_params* params,
-                            cf_problem** out, bool device) {
-  if (!mesh || !ls || !out) return fail(CF_EINVAL, "null argument");
-  *out = nullptr;
+// cf_mesh / cf_levelset / cf_params -> SetupParams, with the argument checks
+// of cf_setup
+static cf_status translate(const cf_mesh* mesh, const cf_levelset* ls, int degree, const cf_params* params,
+                           SetupParams& prm, int& precision, int& threads) {
+  if (!mesh || !ls) return fail(CF_EINVAL, "null argument");
   if (mesh->dim != 2 && mesh->dim != 3) return fail(CF_EINVAL, "dim must be 2 or 3");
   if (degree < 1 || degree > 3) return fail(CF_EINVAL, "degree must be 1, 2 or 3");
   if (mesh->dim == 3 && degree > 2) return fail(CF_EUNSUPPORTED, "dim 3 supports degree 1 and 2");
@@ -106,7 +107,7 @@ static cf_status setup_impl(const cf_mesh* mesh, const cf_levelset* ls, int degr
     return fail(CF_EINVAL, "torus radii must satisfy major > minor > 0");
   if (ls->kind == CF_LS_FLOWER && !(ls->radius > ls->amplitude && ls->amplitude >= 0 && ls->lobes >= 1))
     return fail(CF_EINVAL, "flower needs radius > amplitude >= 0 and lobes >= 1");
-  SetupParams prm;
+  prm = SetupParams();
   prm.dim = mesh->dim;
   prm.degree = degree;
   prm.n_cells = mesh->n_cells;
@@ -116,7 +117,7 @@ static cf_status setup_impl(const cf_mesh* mesh, const cf_levelset* ls, int degr
   prm.gamma_D = 20.0 * degree * degree;
   prm.n_c = 2;
   prm.quad_q = degree + 2;
-  int precision = CF_FP64;
+  precision = CF_FP64;
   if (params) {
     if (params->gamma_D > 0) prm.gamma_D = params->gamma_D;
     for (int k = 0; k < 4; ++k)
@@ -132,7 +133,7 @@ static cf_status setup_impl(const cf_mesh* mesh, const cf_levelset* ls, int degr
     if (params->smoother_degree > 0) prm.cheb_degree = params->smoother_degree;
     if (params->setup_threads < 0) return fail(CF_EINVAL, "bad setup thread count");
   }
-  const int threads = params ? params->setup_threads : 0;
+  threads = params ? params->setup_threads : 0;
   prm.ls.kind = ls->kind;
   prm.ls.d = mesh->dim;
   for (int k = 0; k < 3; ++k) {
@@ -155,20 +156,34 @@ static cf_status setup_impl(const cf_mesh* mesh, const cf_levelset* ls, int degr
     static std::atomic<uint64_t> epochs{0};
     prm.ls.epoch = ++epochs;
   }
+  return CF_OK;
+}
+
+// the calling thread's OpenMP team size for the setup, restored on exit
+struct ThreadCount {
+  int saved;
+  explicit ThreadCount(int n) : saved(omp_get_max_threads()) {
+    if (n > 0) omp_set_num_threads(n);
+  }
+  ~ThreadCount() { omp_set_num_threads(saved); }
+};
+
+static cf_status setup_impl(const cf_mesh* mesh, const cf_levelset* ls, int degree, const cf_params* params,
+                            cf_problem** out, bool device, cudaStream_t stream) {
+  if (!out) return fail(CF_EINVAL, "null argument");
+  *out = nullptr;
+  SetupParams prm;
+  int precision = CF_FP64, threads = 0;
+  cf_status tr = translate(mesh, ls, degree, params, prm, precision, threads);
+  if (tr != CF_OK) return tr;
   std::unique_ptr<cf_problem> pb;
   cf_status st = guarded([&] {
-    struct ThreadCount {  // the calling thread's OpenMP team size, restored on exit
-      int saved;
-      explicit ThreadCount(int n) : saved(omp_get_max_threads()) {
-        if (n > 0) omp_set_num_threads(n);
-      }
-      ~ThreadCount() { omp_set_num_threads(saved); }
-    } tc(threads);
+    ThreadCount tc(threads);
     pb.reset(new cf_problem());
     build_hierarchy(prm, pb->H);
     if (device) {
       if (cudaGetDevice(&pb->device) != cudaSuccess) throw CudaError("no CUDA device");
-      pb->eng = mesh->dim == 2 ? make_engine_d2(degree, pb->H) : make_engine_d3(degree, pb->H);
+      pb->eng = mesh->dim == 2 ? make_engine_d2(degree, pb->H, stream) : make_engine_d3(degree, pb->H, stream);
     }
     pb->precision = precision;
   });
@@ -177,28 +192,29 @@ static cf_status setup_impl(const cf_mesh* mesh, const cf_levelset* ls, int degr
   return CF_OK;
 }
 
-cf_status cf_setup(const cf_mesh* mesh, const cf_levelset* ls, int degree, const cf_params* params,
+cf_status cf_setup(const cf_mesh* mesh, const cf_levelset* ls, int degree, const cf_params* params, void* stream,
                    cf_problem** out) {
-  return setup_impl(mesh, ls, degree, params, out, true);
+  return setup_impl(mesh, ls, degree, params, out, true, S(stream));
 }
 
 cf_status cutmg_build_host(const cf_mesh* mesh, const cf_levelset* ls, int degree, const cf_params* params,
                            cf_problem** out) {
-  return setup_impl(mesh, ls, degree, params, out, false);
+  return setup_impl(mesh, ls, degree, params, out, false, nullptr);
 }
 
-cf_status cutmg_attach_device(cf_problem* pb) {
+cf_status cutmg_attach_device(cf_problem* pb, cudaStream_t stream) {
   if (!pb) return fail(CF_EINVAL, "null problem");
   if (pb->eng) return CF_OK;
   return guarded([&] {
     if (cudaGetDevice(&pb->device) != cudaSuccess) throw CudaError("no CUDA device");
-    pb->eng = pb->H.prm.dim == 2 ? make_engine_d2(pb->H.prm.degree, pb->H) : make_engine_d3(pb->H.prm.degree, pb->H);
+    pb->eng = pb->H.prm.dim == 2 ? make_engine_d2(pb->H.prm.degree, pb->H, stream)
+                                 : make_engine_d3(pb->H.prm.degree, pb->H, stream);
   });
 }
 
-size_t cutmg_estimate_device_bytes(const cf_problem* pb) {
+// the device bytes of a hierarchy built with or without prm.dry (sizes only)
+size_t cutmg_estimate_hierarchy_bytes(const Hierarchy& H) {
   // mirrors the allocations of Engine (both precisions) and its CG vectors
-  const auto& H = pb->H;
   const int d = H.prm.dim, p = H.prm.degree;
   size_t nb = 1;
   for (int k = 0; k < d; ++k) nb *= (size_t)(p + 1);
@@ -212,26 +228,54 @@ size_t cutmg_estimate_device_bytes(const cf_problem* pb) {
             L.ghost_faces.size() + L.cfaces.size() + L.face_id.size() + L.cut_fo.size() + L.cut_cell.size() +
             L.cut_item_off.size()) * 4 + L.cut_vert.size() * 8 + L.members.size() * 2 + L.cut_items.size();
     tot += (L.pro_col.size() + L.res_col.size()) * 4;
-    size_t typed = L.cutmat.size() + L.Kref.size() + L.inv.size() + L.pro_w.size() + L.res_w.size() +
-                   L.coarse_inv.size() + 3 * nbox + L.members.size() + L.ghost_faces.size() * p * nt;
+    const size_t ncoarse = l == 0 ? L.dofs.size() * L.dofs.size() : 0;
+    size_t typed = (size_t)L.n_cut * nb * nb + nb * nb + (size_t)L.n_inv + L.pro_w.size() + L.res_w.size() +
+                   ncoarse + 3 * nbox + L.members.size() + L.ghost_faces.size() * p * nt;
+    if (l > 0) {  // interior-patch dense map: transposed copy and the tensor-core operand (FP32 only)
+      size_t nc = 1, ni = 1;
+      for (int k = 0; k < d; ++k) {
+        nc *= (size_t)(2 * p + 1);
+        ni *= (size_t)(2 * p - 1);
+      }
+      const size_t np_tc = ni <= 16 ? 16 : (ni + 15) / 16 * 16;
+      tot += 4 * (2 * nc * ((ni + 7) / 8 * 8) + np_tc * ((nc + 7) / 8 * 8));
+    }
     if (l > 0) {
       const size_t nf = L.n, nc = H.levels[l - 1].n;
       typed += d == 3 ? nc * nf * nf + nc * nc * nf + nf * nc * nc + nf * nf * nc : 2 * nc * nf;
     }
     tot += typed * 12;  // FP64 + FP32 copies
   }
-  tot += 9 * H.levels.back().nact.size() * 8 + H.rhs.size() * 8 + 64 * 1024;
+  tot += 9 * H.levels.back().nact.size() * 8 + H.levels.back().dofs.size() * 8 + 64 * 1024;
   return tot;
 }
 
+size_t cutmg_estimate_device_bytes(const cf_problem* pb) { return cutmg_estimate_hierarchy_bytes(pb->H); }
+
 cf_status cf_setup_host(const cf_mesh* mesh, const cf_levelset* ls, int degree, const cf_params* params,
                         cf_problem** out) {
-  return setup_impl(mesh, ls, degree, params, out, false);
+  return setup_impl(mesh, ls, degree, params, out, false, nullptr);
 }
 
 void cf_destroy(cf_problem* pb) { delete pb; }
 
-cf_status cf_footprint(const cf_problem* pb, size_t* bytes) {
+cf_status cf_footprint(const cf_mesh* mesh, const cf_levelset* ls, int degree, const cf_params* params,
+                       size_t* bytes) {
+  if (!bytes) return fail(CF_EINVAL, "null argument");
+  SetupParams prm;
+  int precision = CF_FP64, threads = 0;
+  cf_status tr = translate(mesh, ls, degree, params, prm, precision, threads);
+  if (tr != CF_OK) return tr;
+  prm.dry = true;
+  return guarded([&] {
+    ThreadCount tc(threads);
+    Hierarchy H;
+    build_hierarchy(prm, H);
+    *bytes = cutmg_estimate_hierarchy_bytes(H);
+  });
+}
+
+cf_status cf_problem_footprint(const cf_problem* pb, size_t* bytes) {
   if (!pb || !bytes) return fail(CF_EINVAL, "null argument");
   *bytes = cutmg_estimate_device_bytes(pb);
   return CF_OK;

@@ -34,7 +34,16 @@ inline void launch_check(const char* what) {
   if (e != cudaSuccess) throw CudaError(std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-// owns every device allocation of a problem
+// FP32 -> TF32 (10 explicit mantissa bits), round to nearest even
+inline float round_tf32(float v) {
+  uint32_t u;
+  std::memcpy(&u, &v, 4);
+  if ((u & 0x7f800000u) != 0x7f800000u) u += 0xfffu + ((u >> 13) & 1u);
+  u &= 0xffffe000u;
+  std::memcpy(&v, &u, 4);
+  return v;
+}
+
 // One step of the Chebyshev smoother over a level's active box:
 // x_new = x + c1 (x - xp) + c2 D^{-1} r, then xp <- x, x <- x_new
 template <typename T>
@@ -88,11 +97,15 @@ static __global__ void __launch_bounds__(256) k_scale_rsqrt(Region R, const doub
   }
 }
 
+// Owns every device allocation of a problem.  Zero fills and uploads are
+// ordered on the stream given at set-up (uploads from pageable host memory
+// return once the data has been staged).
 class DevPool {
  public:
   ~DevPool() {
     for (void* p : ptrs_) cudaFree(p);
   }
+  void set_stream(cudaStream_t s) { s_ = s; }
   template <typename T>
   T* alloc(size_t count, bool zero = true) {
     if (count == 0) count = 1;
@@ -101,7 +114,7 @@ class DevPool {
     if (e != cudaSuccess) throw OomError("cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed");
     ptrs_.push_back(p);
     bytes_ += count * sizeof(T);
-    if (zero) CUTMG_CUDA(cudaMemset(p, 0, count * sizeof(T)));
+    if (zero) CUTMG_CUDA(cudaMemsetAsync(p, 0, count * sizeof(T), s_));
     return static_cast<T*>(p);
   }
   template <typename T, typename S, typename A>
@@ -109,10 +122,11 @@ class DevPool {
     T* p = alloc<T>(v.size(), false);
     if (v.empty()) return p;
     if constexpr (std::is_same<T, S>::value) {
-      CUTMG_CUDA(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+      CUTMG_CUDA(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s_));
     } else {
       std::vector<T> tmp(v.begin(), v.end());
-      CUTMG_CUDA(cudaMemcpy(p, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice));
+      CUTMG_CUDA(cudaMemcpyAsync(p, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice, s_));
+      CUTMG_CUDA(cudaStreamSynchronize(s_));  // tmp is released on return
     }
     return p;
   }
@@ -121,6 +135,7 @@ class DevPool {
  private:
   std::vector<void*> ptrs_;
   size_t bytes_ = 0;
+  cudaStream_t s_ = nullptr;
 };
 
 inline int blocks_for(int64_t n, int bs) { return (int)((n + bs - 1) / bs); }
@@ -185,6 +200,7 @@ class Engine final : public EngineBase {
     T* res_w;
     T* coarse_inv;
     float* dense_d;  // FP32 interior-patch map, transposed, rows padded to 4 (Wt[kc][r])
+    float* tc_b = nullptr;  // the same map as the tensor-core B operand (TF32, core-matrix layout)
     T* dinv = nullptr;  // Chebyshev smoother: 1 / diag(A_l) on the box (0 off the DoFs)
     T* xp = nullptr;    // Chebyshev smoother: previous iterate
     T *x, *b, *r;          // box vectors
@@ -192,7 +208,8 @@ class Engine final : public EngineBase {
   };
 
  public:
-  explicit Engine(const Hierarchy& H) : H_(H) {
+  Engine(const Hierarchy& H, cudaStream_t stream) : H_(H), setup_stream_(stream) {
+    pool_.set_stream(stream);
     const int L = (int)H.levels.size();
     com_.resize(L);
     d64_.resize(L);
@@ -211,6 +228,8 @@ class Engine final : public EngineBase {
     part_ = pool_.alloc<double>(kDotBlocks);
     sc_ = pool_.alloc<double>(16);
     err_ = pool_.alloc<int>(1);
+    CUTMG_CUDA(cudaFuncSetAttribute(k_smooth_tc<DIM, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    TcGeo<DIM, P>::SMEM));
     CUTMG_CUDA(cudaFuncSetAttribute(k_cut_solve_cta<DIM, P, double, false, kCutNT<double>>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, kInvSlotBytesMax));
     CUTMG_CUDA(cudaFuncSetAttribute(k_cut_solve_cta<DIM, P, float, false, kCutNT<float>>,
@@ -237,6 +256,7 @@ class Engine final : public EngineBase {
     }
     const char* g = std::getenv("CUTMG_GRAPHS");
     use_graphs_ = !(g && g[0] == '0');
+    CUTMG_CUDA(cudaStreamSynchronize(stream));
   }
   ~Engine() override {
     drop_graphs();
@@ -784,6 +804,7 @@ class Engine final : public EngineBase {
   double* gsc_ = nullptr;
 
   const Hierarchy& H_;
+  cudaStream_t setup_stream_ = nullptr;  // the stream of cf_setup (uploads, power iteration)
   DevPool pool_;
   int64_t launches_ = 0;
   struct Prof {
@@ -911,6 +932,14 @@ class Engine final : public EngineBase {
         for (int i = 0; i < G::NI; ++i)
           for (int k = 0; k < G::NC; ++k) wt[(size_t)k * G::NR4 + i] = (float)h.Wcart[(size_t)i * G::NC + k];
       D.dense_d = pool_.upload<float>(wt);
+      if (std::is_same<T, float>::value && l > 0) {
+        using TG = TcGeo<DIM, P>;
+        std::vector<float> bo((size_t)TG::B_BYTES / 4, 0.f);
+        for (int i = 0; i < G::NI; ++i)
+          for (int k = 0; k < G::NC; ++k)
+            bo[(size_t)umma_off<TG::NP>(i, k) / 4] = round_tf32((float)h.Wcart[(size_t)i * G::NC + k]);
+        D.tc_b = pool_.upload<float>(bo);
+      }
     }
     D.inv = pool_.upload<T>(h.inv);
     D.pro_w = l > 0 ? pool_.upload<T>(h.pro_w) : nullptr;
@@ -1026,7 +1055,7 @@ class Engine final : public EngineBase {
     CUTMG_CUDA(cudaStreamSynchronize(s));
     if (h) {
       CUTMG_CUDA(cudaMemsetAsync(err_, 0, sizeof(int), s));
-      throw TimeoutError("a bounded wait on a TMA copy ran out in the cut-patch kernel");
+      throw TimeoutError("a bounded wait ran out in a kernel (TMA copy of a patch inverse or tensor-core MMA completion)");
     }
   }
 
@@ -1144,9 +1173,11 @@ class Engine final : public EngineBase {
       {
         constexpr int PPB = 128 / DenseGeo<DIM, P>::NPART;
         int v = var_int_;
-        if (v == 4) v = 0;  // no tensor-core variant of this (d, p) yet
         if (v == 0) v = cnt >= kDensePairPatches ? 2 : (cnt >= kDenseThreadPatches ? 1 : 3);
-        if (v == 2)
+        if (v == 4)
+          k_smooth_tc<DIM, P><<<std::min(blocks_for(cnt, 128), 2 * sms_), 256, TcGeo<DIM, P>::SMEM, s>>>(
+              D.tc_b, c.N, c.n, x, b, c.cart + a0, cnt, err_, spin_);
+        else if (v == 2)
           k_smooth_dense<DIM, P, 2><<<blocks_for(cnt, 256), 128, 0, s>>>(D.dense_d, c.N, c.n, x, b, c.cart + a0, cnt);
         else if (v == 1)
           k_smooth_dense<DIM, P, 1><<<blocks_for(cnt, 128), 128, 0, s>>>(D.dense_d, c.N, c.n, x, b, c.cart + a0, cnt);
@@ -1220,10 +1251,11 @@ class Engine final : public EngineBase {
   double power_lambda_max(int l) {
     Typed<double>& D = d64_[l];
     const Common& c = com_[l];
-    cudaStream_t s = 0;
+    cudaStream_t s = setup_stream_;
     std::vector<double> ones((size_t)c.nbox, 0.0);
     for (int64_t i = 0; i < c.ndof; ++i) ones[(size_t)H_.levels[l].dofs[i]] = 1.0 / std::sqrt((double)c.ndof);
-    CUTMG_CUDA(cudaMemcpy(D.x, ones.data(), sizeof(double) * c.nbox, cudaMemcpyHostToDevice));
+    CUTMG_CUDA(cudaMemcpyAsync(D.x, ones.data(), sizeof(double) * c.nbox, cudaMemcpyHostToDevice, s));
+    CUTMG_CUDA(cudaStreamSynchronize(s));
     for (int it = 0; it < 30; ++it) {
       apply<double>(l, D, D.x, nullptr, D.r, s);
       k_scale_diag<double><<<kVecBlocks, 256, 0, s>>>(c.region, D.dinv, D.r, D.r);

@@ -67,8 +67,10 @@ class EngineBase {
                            int64_t* nbox) const = 0;
 };
 
-std::unique_ptr<EngineBase> make_engine_d2(int degree, const Hierarchy& H);
-std::unique_ptr<EngineBase> make_engine_d3(int degree, const Hierarchy& H);
+// device engine of a built hierarchy; its uploads are ordered on `stream`,
+// which the constructor synchronises before it returns
+std::unique_ptr<EngineBase> make_engine_d2(int degree, const Hierarchy& H, cudaStream_t stream);
+std::unique_ptr<EngineBase> make_engine_d3(int degree, const Hierarchy& H, cudaStream_t stream);
 
 class BatchGroupBase;
 std::unique_ptr<BatchGroupBase> make_batch_group_d2(int degree, const std::vector<EngineBase*>& inst, int n_c);

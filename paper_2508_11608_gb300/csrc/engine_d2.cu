@@ -3,11 +3,11 @@
 
 namespace cutmg {
 
-std::unique_ptr<EngineBase> make_engine_d2(int degree, const Hierarchy& H) {
+std::unique_ptr<EngineBase> make_engine_d2(int degree, const Hierarchy& H, cudaStream_t stream) {
   switch (degree) {
-    case 1: return std::make_unique<Engine<2, 1>>(H);
-    case 2: return std::make_unique<Engine<2, 2>>(H);
-    case 3: return std::make_unique<Engine<2, 3>>(H);
+    case 1: return std::make_unique<Engine<2, 1>>(H, stream);
+    case 2: return std::make_unique<Engine<2, 2>>(H, stream);
+    case 3: return std::make_unique<Engine<2, 3>>(H, stream);
     default: throw std::invalid_argument("unsupported degree");
   }
 }

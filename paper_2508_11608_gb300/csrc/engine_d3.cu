@@ -3,10 +3,10 @@
 
 namespace cutmg {
 
-std::unique_ptr<EngineBase> make_engine_d3(int degree, const Hierarchy& H) {
+std::unique_ptr<EngineBase> make_engine_d3(int degree, const Hierarchy& H, cudaStream_t stream) {
   switch (degree) {
-    case 1: return std::make_unique<Engine<3, 1>>(H);
-    case 2: return std::make_unique<Engine<3, 2>>(H);
+    case 1: return std::make_unique<Engine<3, 1>>(H, stream);
+    case 2: return std::make_unique<Engine<3, 2>>(H, stream);
     default: throw std::invalid_argument("unsupported degree");
   }
 }

@@ -1380,6 +1380,221 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 8 ? 7 : 9) k_cut_solve_cta(Op
 }
 
 // ---------------------------------------------------------------------------
+// The same FP32 interior-patch step on the 5th-generation tensor cores: for a
+// tile of 128 patches of one colour, D[128 x NP] = G[128 x KP] W^T[KP x NP]
+// with G the gathered closures (rows = patches, K = closure nodes) and W the
+// level's dense map (rows = interior nodes), one tcgen05.mma kind::tf32 per 8
+// closure nodes (TF32 products, FP32 accumulation in tensor memory).  Both
+// operands sit in shared memory in the canonical K-major layout without
+// swizzle: 8-row x 16-byte core matrices, each 128 contiguous bytes, ordered
+// by 4-column K block, then by 8-row group.  One thread issues the MMAs and
+// commits them to an mbarrier; the block's warps then read D back with
+// tcgen05.ld (warp w: lanes 32 (w mod 4) .., half w / 4 of the columns) and
+// write the new interior values.  256 threads per block: thread t gathers
+// patch t mod 128, half t / 128 of its closure, with all its loads in flight
+// at once; two blocks per SM overlap one block's gather with the other's
+// MMA and write-back.  Persistent over the tiles of the colour.
+template <int DIM, int P>
+struct TcGeo {
+  static constexpr int NI = DenseGeo<DIM, P>::NI, NC = DenseGeo<DIM, P>::NC;
+  static constexpr int KP = (NC + 7) / 8 * 8;                       // K padded to the MMA's step
+  static constexpr int NP = NI <= 16 ? 16 : (NI + 15) / 16 * 16;    // N padded (M = 128: N % 16 == 0)
+  static constexpr int KH = KP / 2, NH = NP / 2;                    // per-thread halves
+  static constexpr int COLS = NP <= 32 ? 32 : (NP <= 64 ? 64 : 128);  // tensor-memory columns
+  static constexpr int A_BYTES = 128 * KP * 4, B_BYTES = NP * KP * 4;
+  // The MMAs read [start, start + 2 (R / 8) 128) of an R-row operand per
+  // K step.  The allocation also covers the reach the same descriptors would
+  // have with the two byte offsets exchanged ((R / 8 - 1) (R / 8) 128 + 256
+  // past the last step's start), so that no descriptor can address shared
+  // memory outside the block.
+  static constexpr int reach(int R, int start) { return start + (R / 8 - 1) * (R / 8) * 128 + 256; }
+  static constexpr int cmax(int a, int b) { return a > b ? a : b; }
+  static constexpr int SMEM =
+      (cmax(cmax(A_BYTES + B_BYTES, reach(128, (KP / 8 - 1) * 2 * 16 * 128)),
+            A_BYTES + reach(NP, (KP / 8 - 1) * 2 * (NP / 8) * 128)) + 127) / 128 * 128;
+  static_assert(KH % 4 == 0, "each gathering thread stores whole 16-byte core-matrix rows");
+};
+
+// byte offset of element (row r, column k) of an R-row operand in the
+// K-major, unswizzled core-matrix layout
+template <int R>
+__host__ __device__ constexpr int umma_off(int r, int k) {
+  return ((k >> 2) * (R >> 3) + (r >> 3)) * 128 + (r & 7) * 16 + (k & 3) * 4;
+}
+
+// shared-memory matrix descriptor: start address, leading-dimension byte
+// offset (between K-adjacent core matrices), stride-dimension byte offset
+// (between 8-row groups), descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// instruction descriptor of kind::tf32: D FP32, A and B TF32, both K-major,
+// M = 128, N = np
+__host__ __device__ constexpr uint32_t umma_idesc_tf32(int np) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(np >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// columns of tensor memory for this block (one warp, converged); the
+// address is written to *slot
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t cols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(cols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t cols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(cols) : "memory");
+}
+
+// 32 lanes x NH consecutive 32-bit columns of tensor memory, one lane per thread
+template <int NH>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, float* v);
+template <>
+__device__ __forceinline__ void tmem_ld<8>(uint32_t taddr, float* v) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr)
+               : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+template <>
+__device__ __forceinline__ void tmem_ld<16>(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ float to_tf32(float v) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+  return __uint_as_float(r);
+}
+
+// closure values [H KH, H KH + KH) of the patch at lattice offset `base`
+// (interior nodes read b, boundary nodes x), rounded to TF32, stored as
+// row `p` of the A operand
+template <int DIM, int P, int H>
+__device__ __forceinline__ void tc_gather(const float* __restrict__ x, const float* __restrict__ b, int base, int n,
+                                          bool has, int p, unsigned char* sA) {
+  using G = TcGeo<DIM, P>;
+  constexpr int C = 2 * P + 1;
+  float g[G::KH];
+#pragma unroll
+  for (int q = 0; q < G::KH; ++q) {
+    const int kc = H * G::KH + q;
+    g[q] = 0.f;
+    if (kc < G::NC && has) {
+      const int cx = kc % C, cy = (kc / C) % C, cz = (DIM == 3) ? kc / (C * C) : 0;
+      const bool inner = cx >= 1 && cx <= C - 2 && cy >= 1 && cy <= C - 2 && (DIM == 2 || (cz >= 1 && cz <= C - 2));
+      const int off = (DIM == 2) ? cx + n * cy : cx + n * (cy + n * cz);
+      g[q] = (inner ? b : x)[base + off];
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < G::KH; q += 4) {
+    const float4 v = make_float4(to_tf32(g[q]), to_tf32(g[q + 1]), to_tf32(g[q + 2]), to_tf32(g[q + 3]));
+    *reinterpret_cast<float4*>(sA + umma_off<128>(p, H * G::KH + q)) = v;
+  }
+}
+
+// Bop: the level's W as the B operand (NP x KP, TF32-rounded, in the core-
+// matrix layout above, zero padding).  A bounded wait on the MMAs' mbarrier
+// (`spin` polls) records a timeout in *err.
+template <int DIM, int P>
+__global__ void __launch_bounds__(256, 2) k_smooth_tc(const float* __restrict__ Bop, int N, int n,
+                                                      float* __restrict__ x, const float* __restrict__ b,
+                                                      const int* __restrict__ verts, int nv, int* err, int spin) {
+  using G = TcGeo<DIM, P>;
+  extern __shared__ __align__(128) unsigned char tsm[];
+  unsigned char* sA = tsm;
+  unsigned char* sB = tsm + G::A_BYTES;
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tmem_slot;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int i = tid; i < G::B_BYTES / 16; i += blockDim.x)
+    reinterpret_cast<float4*>(sB)[i] = reinterpret_cast<const float4*>(Bop)[i];
+  if (warp == 0) tmem_alloc(&tmem_slot, G::COLS);
+  if (tid == 0) mbar_init(&bar);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  const int ntiles = (nv + 127) / 128;
+  const int p = tid & 127, half = tid >> 7;
+  constexpr uint32_t idesc = umma_idesc_tf32(G::NP);
+  const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+  uint32_t phase = 0;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int j = tile * 128 + p;
+    const bool has = j < nv;
+    const int base = has ? dense_base<DIM, P>(verts[j], N, n) : 0;
+    if (half == 0)
+      tc_gather<DIM, P, 0>(x, b, base, n, has, p, sA);
+    else
+      tc_gather<DIM, P, 1>(x, b, base, n, has, p, sA);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int i = 0; i < G::KP / 8; ++i)
+        umma_tf32(tmem, umma_desc(a0 + i * 2 * 16 * 128, 16 * 128, 128),
+                  umma_desc(b0 + i * 2 * (G::NP / 8) * 128, (G::NP / 8) * 128, 128), idesc, i > 0 ? 1u : 0u);
+      umma_commit(&bar);
+    }
+    if (!mbar_wait(&bar, phase & 1u, spin)) {
+      atomicExch(err, 1);
+      mbar_wait(&bar, phase & 1u, kTmaSpin);
+    }
+    phase += 1;
+    tc_fence_after();
+    float d[G::NH];
+    tmem_ld<G::NH>(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(G::NH * half), d);
+    if (has) {
+#pragma unroll
+      for (int r = 0; r < G::NH; ++r) {
+        const int rr = G::NH * half + r;
+        if (rr < G::NI) x[base + dense_interior_offset<DIM, P>(rr, n)] = d[r];
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+  }
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, G::COLS);
+}
+
+// ---------------------------------------------------------------------------
 // Transfer: one direction of a tensor-product sparse 1D matrix with W entries
 // per output index, over a box region of the output.  MODE 0: out = sum;
 // MODE 1: out = mask ? sum : 0; MODE 2: out += mask ? sum : 0.

@@ -18,8 +18,10 @@ extern "C" {
 // host phase of cf_setup (hierarchy only), device phase (engine + upload)
 cf_status cutmg_build_host(const cf_mesh* mesh, const cf_levelset* ls, int degree, const cf_params* params,
                            cf_problem** out);
-cf_status cutmg_attach_device(cf_problem* pb);
+cf_status cutmg_attach_device(cf_problem* pb, cudaStream_t stream);
 // device bytes the engine of a host-built problem will allocate
 size_t cutmg_estimate_device_bytes(const cf_problem* pb);
+// the same from a hierarchy, also one built with SetupParams::dry (sizes only)
+size_t cutmg_estimate_hierarchy_bytes(const cutmg::Hierarchy& H);
 }
 cf_status cutmg_set_error(cf_status s, const char* msg);

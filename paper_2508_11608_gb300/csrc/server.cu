@@ -9,7 +9,7 @@
 //    setup takes the cores no other running setup holds, at least its share
 //    of them, so a request that arrives alone is built on every core.
 //  * Admission (FIFO): a prepared request enters as soon as its device
-//    footprint (estimated from the host hierarchy) fits the HBM budget next to
+//    footprint (estimated before its setup by cf_footprint) fits the HBM budget next to
 //    the resident problems and an active slot is free; its hierarchy is
 //    uploaded and its CG is started (x = 0, r = b, z = B r, p = z).
 //  * Every tick runs one CG iteration for all active problems together: each
@@ -172,16 +172,28 @@ cf_status cf_server_run(cf_server* s, void* stream) {
         threads_busy += mine;
         prm.setup_threads = mine;
       }
+      // admission estimate before the setup (cf_footprint: sizes only, no
+      // quadrature, matrices or inverses); a request that can never fit is
+      // refused without building it
+      size_t est = 0;
       cf_problem* pb = nullptr;
-      cf_status rc = cutmg_build_host(&r.mesh, &r.ls, r.degree, &prm, &pb);
+      cf_status rc = cf_footprint(&r.mesh, &r.ls, r.degree, &prm, &est);
+      std::string why;
+      if (rc == CF_OK && est > s->budget) {
+        rc = CF_ENOMEM;
+        why = "device footprint exceeds the server's HBM budget";
+      } else if (rc == CF_OK) {
+        rc = cutmg_build_host(&r.mesh, &r.ls, r.degree, &prm, &pb);
+      }
+      if (rc != CF_OK && why.empty()) why = cf_last_error();
       std::lock_guard<std::mutex> lk(mu);
       threads_busy -= mine;
       if (rc != CF_OK) {
         r.state = -1;
-        r.error = cf_last_error();
+        r.error = why;
       } else {
         r.pb = pb;
-        r.bytes = cutmg_estimate_device_bytes(pb);
+        r.bytes = est;
         r.state = 1;
       }
       cv.notify_all();
@@ -234,7 +246,7 @@ cf_status cf_server_run(cf_server* s, void* stream) {
           }
           break;
         }
-        cf_status rc = cutmg_attach_device(r.pb);
+        cf_status rc = cutmg_attach_device(r.pb, st);
         if (rc != CF_OK) throw cutmg::CudaError(cf_last_error());
         r.ndof = cf_n_dofs(r.pb);
         if (cudaMalloc(&r.d_b, sizeof(double) * std::max<int64_t>(1, r.ndof)) != cudaSuccess ||

@@ -589,7 +589,7 @@ void patch_vertex_sets(HostLevel& L) {
 
 // Cut patches: their DoFs (closure nodes all of whose active cells are patch
 // cells), member and inverse offsets, and the inverse storage.
-void cut_patch_members(HostLevel& L) {
+void cut_patch_members(HostLevel& L, bool dry) {
   const int d = L.d, p = L.p, N = L.N, n = L.n;
   const int np = N + 1, C = 2 * p + 1, ncol = 1 << d, NCL = ipow(C, d);
   const int64_t ncp = (int64_t)L.cut_vert.size();
@@ -664,7 +664,8 @@ void cut_patch_members(HostLevel& L) {
       L.member_node.push_back((int)node);
     }
   }
-  L.inv.resize(ioff);  // every slot zeroed and filled by its patch below
+  L.n_inv = ioff;
+  if (!dry) L.inv.resize(ioff);  // every slot zeroed and filled by its patch below
 }
 
 // Ghost-face entries of every cut-patch DoF (the faces whose two cells
@@ -1003,13 +1004,13 @@ void cut_patch_inverses(const RefTables& R, HostLevel& L) {
 // Patches (Sec. 2.3, Sec. 3) of a level: vertex sets by colour, and for the
 // cut patches their DoF lists, ghost-face entries, row items, work model and
 // explicit inverses.
-void build_patches(const RefTables& R, HostLevel& L) {
+void build_patches(const RefTables& R, HostLevel& L, bool dry) {
   patch_vertex_sets(L);
-  cut_patch_members(L);
+  cut_patch_members(L, dry);
   cut_patch_face_entries(L);
   cut_patch_rows(L);
   patch_work_model(L);
-  cut_patch_inverses(R, L);
+  if (!dry) cut_patch_inverses(R, L);
 }
 
 // Optional: with cut_rhs, the cut cells' right-hand side terms for source
@@ -1057,11 +1058,11 @@ void build_level(const SetupParams& prm, const RefTables& R, int N, HostLevel& L
     }
   }
   L.n_cut = (int64_t)cut_cells.size();
-  L.cutmat.resize((size_t)L.n_cut * NB * NB);  // every block written below
+  if (!prm.dry) L.cutmat.resize((size_t)L.n_cut * NB * NB);  // every block written below
   if (cut_rhs) cut_rhs->assign((size_t)L.n_cut * NB, 0.0);
   CutQuadrature Q(prm.ls, prm.quad_q);
 #pragma omp parallel for schedule(dynamic, 8)
-  for (int64_t i = 0; i < L.n_cut; ++i) {
+  for (int64_t i = 0; i < (prm.dry ? 0 : L.n_cut); ++i) {
     int64_t c = cut_cells[i], t = c;
     double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
     for (int k = 0; k < d; ++k) {
@@ -1228,7 +1229,7 @@ void build_level(const SetupParams& prm, const RefTables& R, int N, HostLevel& L
     }
   }
   interior_patch_tables(R, L);
-  build_patches(R, L);
+  build_patches(R, L, prm.dry);
 }
 
 // 1D transfer tables between a coarse level (Nc cells) and its refinement
@@ -1497,7 +1498,7 @@ void build_hierarchy(const SetupParams& prm, Hierarchy& H) {
   std::vector<double> cut_rhs;  // finest level: cut cells' terms, formed with their matrices
   for (int l = 0; l < prm.n_levels; ++l) {
     int Nl = prm.n_cells >> (prm.n_levels - 1 - l);
-    if (l == prm.n_levels - 1)
+    if (l == prm.n_levels - 1 && !prm.dry)
       build_level(prm, R, Nl, H.levels[l], &fman, &gman, &cut_rhs);
     else
       build_level(prm, R, Nl, H.levels[l]);
@@ -1529,6 +1530,7 @@ void build_hierarchy(const SetupParams& prm, Hierarchy& H) {
   if (H.levels[0].dofs.size() > 12000)
     throw std::invalid_argument("the coarsest level has " + std::to_string(H.levels[0].dofs.size()) +
                                 " DoFs (dense exact solve); use more levels");
+  if (prm.dry) return;
   build_coarse(R, H.levels[0]);
   if (prm.smoother == 1)
     for (size_t l = 1; l < H.levels.size(); ++l) build_diag(R, H.levels[l]);

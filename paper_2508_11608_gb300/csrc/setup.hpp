@@ -50,6 +50,10 @@ struct SetupParams {
   int quad_q = 4;
   int smoother = 0;     // 0 vertex-patch smoother, 1 Chebyshev
   int cheb_degree = 5;
+  // sizes only: classification, DoFs, faces and patch lists, but no cut-cell
+  // quadrature, no element matrices, no inverses and no right-hand side
+  // (what a device-footprint estimate needs before a full setup)
+  bool dry = false;
   LevelSet ls;
 };
 
@@ -63,6 +67,7 @@ struct HostLevel {
   std::vector<int> cut_id;      // N^d: row block in cutmat or -1
   HostBlocks cutmat;            // [n_cut][NB][NB] volume + Nitsche terms
   int64_t n_cut = 0, n_active = 0, n_ghost = 0;
+  int64_t n_inv = 0;            // entries of the cut-patch inverse storage (inv.size() unless dry)
   // nodes
   std::vector<uint8_t> nact;    // n^d: node belongs to an active cell
   std::vector<int64_t> dofs;    // lattice index of each DoF (ascending)

@@ -2,28 +2,47 @@
 for example: ncu --metrics gpu__time_duration.sum --clock-control none --csv
 python -m paper_2508_11608_gb300.profile_solve ball3d_q2_n64 fp64 1).
 
-Arguments: workload name (paper_2508_11608_gb300.workloads.CONFIGS),
-precision (fp64 | mixed | both), number of solves.  Prints the host setup
-time, the solve info and, over the solves after the first, the CUDA-event
-time per solve and DoF/s (inputs resident on the device)."""
+    python -m paper_2508_11608_gb300.profile_solve WORKLOAD [fp64|mixed|both] [SOLVES]
+        [--interior V] [--cut V] [--families]
 
+WORKLOAD names paper_2508_11608_gb300.workloads.CONFIGS.  Prints the host
+setup time, the solve info and, over the solves after the first, the
+CUDA-event time per solve and DoF/s (inputs resident on the device).
+--interior / --cut force a launch variant (cf_set_kernel_variant); with
+--families every kernel family is event-timed in one more pass of solves:
+summed launch time, launches, and the achieved rate of its algorithmic
+flops and bytes."""
+
+import argparse
 import sys
 import time
 
 import torch
 
 import paper_2508_11608_gb300 as cm
+from paper_2508_11608_gb300 import _lib
 from paper_2508_11608_gb300.workloads import problem_kwargs
+
+FAMILIES = {_lib.CF_K_CUT_SOLVE: "cut-patch step", _lib.CF_K_INTERIOR: "interior-patch step",
+            _lib.CF_K_APPLY_BULK: "operator, bulk", _lib.CF_K_APPLY_BND: "operator, boundary",
+            _lib.CF_K_FACE_MOMENTS: "ghost-face moments"}
 
 
 def main(argv):
-    name = argv[1] if len(argv) > 1 else "ball3d_q2_n64"
-    which = argv[2] if len(argv) > 2 else "fp64"
-    precs = {"fp64": [cm.CF_FP64], "mixed": [cm.CF_MIXED], "both": [cm.CF_FP64, cm.CF_MIXED]}[which]
-    solves = int(argv[3]) if len(argv) > 3 else 2
+    ap = argparse.ArgumentParser()
+    ap.add_argument("workload", nargs="?", default="ball3d_q2_n64")
+    ap.add_argument("precision", nargs="?", default="fp64", choices=["fp64", "mixed", "both"])
+    ap.add_argument("solves", nargs="?", type=int, default=2)
+    ap.add_argument("--interior", type=int, default=0)
+    ap.add_argument("--cut", type=int, default=0)
+    ap.add_argument("--families", action="store_true")
+    a = ap.parse_args(argv[1:])
+    precs = {"fp64": [cm.CF_FP64], "mixed": [cm.CF_MIXED], "both": [cm.CF_FP64, cm.CF_MIXED]}[a.precision]
     t0 = time.perf_counter()
-    pb = cm.Problem(**problem_kwargs(name))
+    pb = cm.Problem(**problem_kwargs(a.workload))
     setup_s = time.perf_counter() - t0
+    pb.set_kernel_variant(_lib.CF_VAR_INTERIOR, a.interior)
+    pb.set_kernel_variant(_lib.CF_VAR_CUT, a.cut)
     n = pb.n_dofs()
     b = torch.zeros(n, dtype=torch.float64, device="cuda")
     x = torch.zeros_like(b)
@@ -31,8 +50,9 @@ def main(argv):
     stream = torch.cuda.current_stream()
     for prec in precs:
         pb.set_precision(prec)
+        label = "mixed" if prec == cm.CF_MIXED else "fp64"
         ms = []
-        for k in range(solves):
+        for k in range(a.solves):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             info = pb.solve(b, x, rtol=1e-8)
@@ -40,11 +60,21 @@ def main(argv):
             torch.cuda.synchronize()
             if k > 0:
                 ms.append(e0.elapsed_time(e1))
-        label = "mixed" if prec == cm.CF_MIXED else "fp64"
-        print(name, "precision", label, "dofs", n, "setup_s", round(setup_s, 2), info, flush=True)
+        print(a.workload, "precision", label, "dofs", n, "setup_s", round(setup_s, 2), info, flush=True)
         if ms:
             avg = sum(ms) / len(ms)
             print(f"  ms_per_solve {avg:.3f} dof_per_s {n / (avg * 1e-3):.4e} over {len(ms)} solves", flush=True)
+        if a.families:
+            for fam, name in FAMILIES.items():
+                pb.profile_start(fam)
+                pb.solve(b, x, rtol=1e-8)
+                pr = pb.profile_read()
+                if pr["launches"] == 0:
+                    continue
+                per = pr["ms"] / pr["launches"]
+                print(f"  {label} {name:22s} {pr['ms']:9.3f} ms  {pr['launches']:5d} launches  "
+                      f"{per * 1e3:8.2f} us/launch  {pr['bytes'] / (pr['ms'] * 1e-3) / 1e9:8.1f} GB/s  "
+                      f"{pr['flops'] / (pr['ms'] * 1e-3) / 1e12:7.3f} TFLOP/s (algorithmic)", flush=True)
     return 0
 
 

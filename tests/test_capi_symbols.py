@@ -16,7 +16,7 @@ def declared_functions():
 
 def test_header_declares_the_boundary():
     names = declared_functions()
-    for must in ("cf_setup", "cf_solve", "cf_vcycle", "cf_apply", "cf_level_colour_step",
+    for must in ("cf_setup", "cf_footprint", "cf_solve", "cf_vcycle", "cf_apply", "cf_level_colour_step",
                  "cf_coarse_solve_noalloc", "cf_batch_solve", "cf_server_run"):
         assert must in names
 
@@ -51,7 +51,10 @@ def test_bad_arguments_return_einval_without_a_device():
         "cf_coarse_solve_noalloc": lambda: lib.cf_coarse_solve_noalloc(h, dummy, dummy, None),
         "cf_batch_create": lambda: lib.cf_batch_create(ctypes.byref(ctypes.c_void_p(h.value)), 1,
                                                        ctypes.byref(ctypes.c_void_p())),
-        "cf_footprint(null)": lambda: lib.cf_footprint(None, ctypes.byref(ctypes.c_size_t())),
+        "cf_footprint(null)": lambda: lib.cf_footprint(None, None, 2, None, ctypes.byref(ctypes.c_size_t())),
+        "cf_problem_footprint(null)": lambda: lib.cf_problem_footprint(None, ctypes.byref(ctypes.c_size_t())),
+        "cf_set_kernel_variant(host-only)": lambda: lib.cf_set_kernel_variant(h, 1, 1),
+        "cf_set_wait_limit(host-only)": lambda: lib.cf_set_wait_limit(h, 5),
         "cf_dof_coords(bad level)": lambda: lib.cf_dof_coords(h, pb.n_levels, dummy),
         "cf_host_cell_matrix(bad level)": lambda: lib.cf_host_cell_matrix(h, -1, 0, dummy),
         "cf_host_cell_matrix(inactive cell)": lambda: lib.cf_host_cell_matrix(h, 1, 0, dummy),
@@ -65,3 +68,16 @@ def test_bad_arguments_return_einval_without_a_device():
         assert lib.cf_last_error(), name
     # the handle still answers afterwards
     assert pb.n_dofs() > 0 and np.isfinite(pb.host_rhs()).all()
+
+
+def test_setup_and_footprint_signatures_follow_the_boundary():
+    """cf_setup takes (mesh, level set, degree, params, stream, out) and
+    cf_footprint (mesh, level set, degree, params, bytes): the estimate needs
+    no built problem."""
+    import re
+    src = open(os.path.join(ROOT, "include", "cutmg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    setup = re.search(r"cf_status cf_setup\(([^)]*)\)", src).group(1)
+    assert [a.split()[-1].lstrip("*") for a in setup.split(",")] == ["mesh", "ls", "degree", "params", "stream", "out"]
+    fp = re.search(r"cf_status cf_footprint\(([^)]*)\)", src).group(1)
+    assert [a.split()[-1].lstrip("*") for a in fp.split(",")] == ["mesh", "ls", "degree", "params", "bytes"]

@@ -193,6 +193,23 @@ def test_footprint_estimate_grows_with_the_mesh():
     assert fl > 4 * fs
 
 
+@pytest.mark.parametrize("dim,N,L,p,spec", [
+    (3, 16, 3, 2, {"kind": "sphere", "center": [0.05, 0.03, 0.02], "radius": 0.7}),
+    (2, 64, 4, 3, {"kind": "flower", "center": [0.01, -0.02], "lobes": 5, "phase": 0.3}),
+    (3, 16, 2, 1, {"kind": "torus", "center": [0.0, 0.0, 0.0], "major": 0.6, "minor": 0.2,
+                   "rot": [[1, 0, 0], [0, 1, 0], [0, 0, 1]]}),
+])
+def test_pre_setup_footprint_equals_the_built_problems(dim, N, L, p, spec):
+    """cf_footprint needs no built problem (sizes only, no quadrature, matrices
+    or inverses) and gives the same bytes as the estimate from the full host
+    setup."""
+    pre = cm.footprint(dim, N, L, p, spec)
+    built = cm.Problem(dim, N, L, p, levelset=spec, host_only=True).footprint()
+    assert pre == built
+    with pytest.raises(cm.CutmgError):
+        cm.footprint(3, 16, 3, 3, spec)  # 3D Q3 is refused as by cf_setup
+
+
 def test_interior_patch_update_is_the_exact_local_solve(pair):
     """x_I <- A_I^{-1} b_I - A_I^{-1} A_{I,B} x_B with A_I, A_{I,B} taken from
     the oracle's assembled matrix at interior patches (Sec. 2.3), and the
