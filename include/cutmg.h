@@ -156,9 +156,11 @@ cf_status cf_dof_coords(const cf_problem* pb, int level, double* h_xyz);
 cf_status cf_stats(const cf_problem* pb, int level, int64_t* h_out6);
 /* Algorithmic work of one colour step on a level, from the host setup
  * (Sec. 3's two patch kinds): kind 0 = interior patches (fast
- * diagonalisation, Sec. 2.3), 1 = cut patches (residual rows and the dense
- * local inverse), 2 = the ghost-face moments the cut-patch rows of the colour
- * read (face penalty of Sec. 2.1).  h_out3 = [flops, scalars moved, index
+ * diagonalisation, Sec. 2.3), 1 = cut patches (residual rows, the ghost-face
+ * moments of the patch rows where the cut kernel forms them itself (3D
+ * degree 2), and the dense local inverse), 2 = the ghost-face moments a
+ * separate launch computes for the cut-patch rows of the colour (face
+ * penalty of Sec. 2.1; zero where the cut kernel forms them).  h_out3 = [flops, scalars moved, index
  * bytes moved]; bytes = scalars x sizeof(precision) + index bytes.
  * CF_EINVAL for a bad level, kind or colour (0 <= colour < 2^dim); level 0
  * (the coarsest, solved exactly) has no colour steps and reports zeros. */
@@ -186,8 +188,10 @@ cf_status cf_set_precision(cf_problem* pb, int precision);
  * 4 = dense map on the tensor cores (TF32 products, FP32 accumulation; the
  * automatic choice where it exists, else the same as 0); FP64 1 = one warp
  * per patch, 2 = one block per patch.  family CF_VAR_CUT (cut-patch step,
- * 3D degree 2): 1 = element-matrix rows staged in shared memory, 2 = rows
- * read through L1.  variant 0 restores the automatic choice.  The next
+ * 3D degree 2): 1 = each patch's record (packed inverse and cut-cell rows)
+ * brought into shared memory by a TMA bulk copy (the automatic choice),
+ * 2 = records read from global memory.  variant 0 restores the automatic
+ * choice.  The next
  * launches use it; captured CUDA graphs of the handle are dropped.
  * CF_EINVAL for an unknown family or variant, or a host-only handle. */
 typedef enum { CF_VAR_INTERIOR = 1, CF_VAR_CUT = 2 } cf_variant_family;
@@ -351,6 +355,9 @@ typedef enum {
  * and bytes of those launches (a model computed at setup: see the design
  * notes), then stops recording.  Adds two event records per launch. */
 cf_status cf_profile_start(cf_problem* pb, int kernel);
+/* The same, restricted to the launches on one level (-1: all levels);
+ * CF_EINVAL for a level outside [-1, cf_n_levels). */
+cf_status cf_profile_start_level(cf_problem* pb, int kernel, int level);
 cf_status cf_profile_read(cf_problem* pb, double* ms, int64_t* launches, double* flops, double* bytes);
 
 /* ---- host-only handles (no device work; used to check the setup) ---------

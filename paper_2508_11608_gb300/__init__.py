@@ -233,8 +233,8 @@ class Problem:
     def launch_count(self):
         return self._lib.cf_launch_count(self._h)
 
-    def profile_start(self, kernel):
-        check(self._lib.cf_profile_start(self._h, kernel))
+    def profile_start(self, kernel, level=-1):
+        check(self._lib.cf_profile_start_level(self._h, kernel, level))
 
     def profile_read(self):
         ms = ctypes.c_double()

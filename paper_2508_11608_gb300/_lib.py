@@ -24,7 +24,7 @@ EXPORTED = [
     "cf_level_restrict", "cf_level_prolongate", "cf_coarse_solve", "cf_setup_host", "cf_host_rhs",
     "cf_host_cell_matrix", "cf_host_patch_counts", "cf_host_interior_update", "cf_host_diagonal", "cf_host_interior_patch", "cf_host_cut_patch",
     "cf_host_coarse_inverse",
-    "cf_set_kernel_variant", "cf_set_wait_limit", "cf_launch_count", "cf_profile_start", "cf_profile_read", "cf_coarse_solve_noalloc",
+    "cf_set_kernel_variant", "cf_set_wait_limit", "cf_launch_count", "cf_profile_start", "cf_profile_start_level", "cf_profile_read", "cf_coarse_solve_noalloc",
     "cf_batch_create", "cf_batch_solve", "cf_batch_launch_count", "cf_batch_destroy",
     "cf_server_create", "cf_server_submit", "cf_server_run", "cf_server_result", "cf_server_stats",
     "cf_server_destroy",
@@ -103,6 +103,7 @@ def load():
     lib.cf_problem_footprint.argtypes = [P, P]
     lib.cf_set_precision.argtypes = [P, I]
     lib.cf_set_kernel_variant.argtypes = [P, I, I]
+    lib.cf_profile_start_level.argtypes = [P, I, I]
     lib.cf_set_wait_limit.argtypes = [P, ctypes.c_int64]
     lib.cf_rhs.argtypes = [P, P, V]
     lib.cf_apply.argtypes = [P, P, P, V]

@@ -38,7 +38,6 @@ struct LvlDesc {
   const int* cutn;
   const int* cutmo;
   const int64_t* cutio;
-  CutPatchArgs cp;
   const float* dense_d;  // FP32 interior-patch map of the level
   const uint16_t* members;
   const int* mnode;
@@ -54,6 +53,8 @@ struct LvlDesc {
   const T* coarse_inv;
   const int* coarse_nodes;
   int n0;
+  PipeLevel<T> pl;  // the level for the pipelined cut kernel (closures of more than 64 nodes)
+  const float* tc_b;  // FP32 interior-patch map as the tensor-core B operand
 };
 
 struct PassDesc {  // one separable transfer pass of one instance
@@ -134,6 +135,34 @@ __global__ void __launch_bounds__(256) kb_cart_dense(const LvlDesc<DIM, P, float
   }
 }
 
+// FP32 interior-patch step of the batched form on the tensor cores: work
+// items are tiles of 128 patches of one instance; the B operand is reloaded
+// when the instance changes.  A patch gets the same products as in the solo
+// kernel (k_smooth_tc): rows of an MMA do not interact.
+template <int DIM, int P>
+__global__ void __launch_bounds__(256, 2) kb_smooth_tc(const LvlDesc<DIM, P, float>* __restrict__ D,
+                                                       const int* __restrict__ off, int K, int total, int colour,
+                                                       int* err) {
+  extern __shared__ __align__(128) unsigned char tsm[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tmem_slot;
+  TcBlock tb;
+  tc_begin<DIM, P>(tb, tsm, &bar, &tmem_slot);
+  int loaded = -1;
+  for (int it = blockIdx.x; it < total; it += gridDim.x) {
+    const int i = find_inst(off, K, it);
+    const LvlDesc<DIM, P, float>& L = D[i];
+    if (i != loaded) {  // the previous tile's MMAs have completed (tc_tile waited)
+      tc_load_b<DIM, P>(L.tc_b, tb.sB);
+      loaded = i;
+    }
+    const int t0 = (it - off[i]) * 128, a0 = L.cart_start[colour];
+    const int cnt = L.cart_start[colour + 1] - a0;
+    tc_tile<DIM, P>(tb, L.N, L.n, L.x, L.b, L.cart + a0 + t0, min(128, cnt - t0), err, kTmaSpin);
+  }
+  tc_end<DIM, P>(tb);
+}
+
 template <int DIM, int P, typename T>
 __global__ void __launch_bounds__(128) kb_face_moments(const LvlDesc<DIM, P, T>* __restrict__ D,
                                                        const T* const* __restrict__ X,
@@ -171,27 +200,53 @@ __global__ void __launch_bounds__(32 * WARPS) kb_cut_solve(const LvlDesc<DIM, P,
   }
 }
 
+// Pipelined cut-patch step over the (instance, patch) work list: the device
+// body of k_cut_pipe (same prefetch, same arithmetic), with the next item's
+// loads in flight while a block computes the current one.  Uncut cells read
+// their instance's element matrix from global memory (instances differ in h).
 template <int DIM, int P, typename T>
-__global__ void __launch_bounds__(kCutThreads) kb_cut_solve_cta(const LvlDesc<DIM, P, T>* __restrict__ D,
-                                                                const int* __restrict__ off, int K, int total,
-                                                                int colour, int inv_cap, int* err) {
-  extern __shared__ __align__(16) unsigned char dsm[];
-  __shared__ __align__(8) uint64_t bar;
-  __shared__ CutScratch<DIM, P, T> S;
-  T* sinv = reinterpret_cast<T*>(dsm);
+__global__ void __launch_bounds__(128) kb_cut_pipe(const LvlDesc<DIM, P, T>* __restrict__ D,
+                                                   const int* __restrict__ off, int K, int total, int colour,
+                                                   int slot_bytes, int* err) {
+  constexpr int NT = 128;
+  extern __shared__ __align__(16) unsigned char psm[];
+  __shared__ __align__(16) PipeStage<DIM, P, T> stage[2];
+  __shared__ PipeShared<DIM, P, T> sh;
+  __shared__ __align__(8) uint64_t bar[2];
   if ((int)blockIdx.x >= total) return;
-  if (threadIdx.x == 0) mbar_init(&bar);
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0]);
+    mbar_init(&bar[1]);
+  }
   __syncthreads();
-  uint32_t phase = 0;
-  for (int it = blockIdx.x; it < total; it += gridDim.x) {
-    const int i = find_inst(off, K, it);
-    const LvlDesc<DIM, P, T>& L = D[i];
-    const int j = L.cut_start[colour] + it - off[i];
-    const CutMeta M = cut_meta(L.cp, j);
-    // uncut cells read the level's element matrix from global memory
-    // (instances differ in h)
-    cut_body_cta<DIM, P, T, false, kCutThreads>(L.op, L.x, L.b, M, j, L.cp, L.members, L.mnode, L.fofs, L.fent, L.inv, S,
-                                   sinv, nullptr, inv_cap, &bar, phase, L.op.Kref, err, kTmaSpin);
+  uint32_t ph = 0;
+  int it = blockIdx.x, s = 0;
+  int i = find_inst(off, K, it);
+  int j = D[i].cut_start[colour] + it - off[i];
+  PipeMeta cur = pipe_meta(D[i].pl, j);
+  pipe_prefetch<DIM, P, T, NT>(D[i].pl, cur, j, stage[0], reinterpret_cast<T*>(psm), slot_bytes, &bar[0]);
+  for (; it < total; it += gridDim.x, s ^= 1) {
+    const int itn = it + (int)gridDim.x;
+    const bool more = itn < total;
+    int in_ = i, jn = j;
+    PipeMeta nxt = cur;
+    if (more) {
+      in_ = find_inst(off, K, itn);
+      jn = D[in_].cut_start[colour] + itn - off[in_];
+      nxt = pipe_meta(D[in_].pl, jn);
+      pipe_prefetch<DIM, P, T, NT>(D[in_].pl, nxt, jn, stage[s ^ 1], reinterpret_cast<T*>(psm + (s ^ 1) * slot_bytes),
+                                   slot_bytes, &bar[s ^ 1]);
+    }
+    const bool tma = pipe_tma<T>(cur, slot_bytes);
+    bool ok;
+    if (more)
+      ok = pipe_wait<true>(tma, &bar[s], ph, s, kTmaSpin, err);
+    else
+      ok = pipe_wait<false>(tma, &bar[s], ph, s, kTmaSpin, err);
+    if (__syncthreads_and(ok)) pipe_compute<DIM, P, T, NT>(D[i].pl, stage[s], sh, D[i].pl.op.Kref);
+    cur = nxt;
+    i = in_;
+    j = jn;
   }
 }
 
@@ -380,10 +435,14 @@ class BatchGroup final : public BatchGroupBase {
     part_ = pool_.alloc<double>((size_t)K_ * kBatchDotBlocks);
     scg_ = pool_.alloc<double>((size_t)K_ * 16);
     err_ = pool_.alloc<int>(1);
-    CUTMG_CUDA(cudaFuncSetAttribute(kb_cut_solve_cta<DIM, P, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    E::kInvSlotBytesMax));
-    CUTMG_CUDA(cudaFuncSetAttribute(kb_cut_solve_cta<DIM, P, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    E::kInvSlotBytesMax));
+    CUTMG_CUDA(cudaFuncSetAttribute(kb_smooth_tc<DIM, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    TcGeo<DIM, P>::SMEM));
+    if (!E::kWarpCut) {
+      CUTMG_CUDA(cudaFuncSetAttribute(kb_cut_pipe<DIM, P, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      2 * E::kRecSlotMax));
+      CUTMG_CUDA(cudaFuncSetAttribute(kb_cut_pipe<DIM, P, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      2 * E::kRecSlotMax));
+    }
     CUTMG_CUDA(cudaMallocHost(&host_sc_, sizeof(double) * K_ * 16));
     rebuild_lists();
   }
@@ -568,7 +627,7 @@ class BatchGroup final : public BatchGroupBase {
     int* off = nullptr;  // device, K + 1
     int total = 0;
   };
-  std::vector<std::vector<Work>> w_cart_, w_cut_, w_cf_;  // [depth][colour]
+  std::vector<std::vector<Work>> w_cart_, w_tile_, w_cut_, w_cf_;  // [depth][colour]
   std::vector<Work> w_bulk_, w_bnd_, w_faces_, w_coarse_, w_xzero_;
   std::vector<std::array<Work, 3>> w_rpass_, w_ppass_;
   Work w_vecF_;
@@ -638,7 +697,6 @@ class BatchGroup final : public BatchGroupBase {
         L.cutn = C.cutn;
         L.cutmo = C.cutmo;
         L.cutio = C.cutio;
-        L.cp = E::cut_args(C);
         L.dense_d = e->template typed<float>()[l].dense_d;
         L.members = C.members;
         L.mnode = C.mnode;
@@ -649,6 +707,8 @@ class BatchGroup final : public BatchGroupBase {
         L.bulk = C.bulk;
         L.bnd = C.bnd;
         L.inv = Ty.inv;
+        if (!E::kWarpCut) L.pl = e->template pipe_level<T>(C, Ty, Ty.x, Ty.b);
+        L.tc_b = e->template typed<float>()[l].tc_b;
         for (int c = 0; c <= NCOL; ++c) {
           L.cart_start[c] = C.cart_start[c];
           L.cut_start[c] = C.cut_start[c];
@@ -690,6 +750,7 @@ class BatchGroup final : public BatchGroupBase {
   void rebuild_lists() {
     // (device memory of old lists is kept in the pool; rebuilds are rare)
     w_cart_.assign(depth_, std::vector<Work>(NCOL));
+    w_tile_.assign(depth_, std::vector<Work>(NCOL));
     w_cut_.assign(depth_, std::vector<Work>(NCOL));
     w_cf_.assign(depth_, std::vector<Work>(NCOL));
     w_bulk_.assign(depth_, Work{});
@@ -712,6 +773,12 @@ class BatchGroup final : public BatchGroupBase {
           if (l < 1) return 0;
           auto& C = inst_[i]->com_[l];
           return C.cart_start[c + 1] - C.cart_start[c];
+        });
+        w_tile_[t][c] = fill([&](int i) {
+          const int l = lv[i];
+          if (l < 1) return 0;
+          auto& C = inst_[i]->com_[l];
+          return (C.cart_start[c + 1] - C.cart_start[c] + 127) / 128;
         });
         w_cut_[t][c] = fill([&](int i) {
           const int l = lv[i];
@@ -808,31 +875,40 @@ class BatchGroup final : public BatchGroupBase {
     if (!cut) {
       const Work& w = w_cart_[t][colour];
       if (w.total == 0) return;
+      if constexpr (std::is_same<T, float>::value) {
+        // the tensor-core form, as the solo engine's automatic choice
+        const Work& wt = w_tile_[t][colour];
+        kb_smooth_tc<DIM, P><<<std::max(1, std::min(wt.total, 2 * sms_)), 256, TcGeo<DIM, P>::SMEM, s>>>(
+            D, wt.off, K_, wt.total, colour, err_);
+        count("batched interior patches");
+        return;
+      }
       launch_cart<T>(D, w, colour, s);
     } else {
       const Work& w = w_cut_[t][colour];
       if (w.total == 0) return;
       const Work& wf = w_cf_[t][colour];
-      if (wf.total > 0) {
+      if (E::kWarpCut && wf.total > 0) {
         kb_face_moments<DIM, P, T><<<grid(wf.total, 4 * FaceGeo<DIM, P>::PER_WARP), 128, 0, s>>>(D, nullptr, wf.off, K_,
                                                                                              wf.total, colour);
         count("batched face moments");
       }
-      {
-        int maxm2 = 0;
+      if (E::kWarpCut) {
+        launch_cut<T>(D, w, colour, s);
+      } else {
+        // record slot of the longest record among the instances at this depth
+        int maxrec = 0;
         for (int i = 0; i < K_; ++i) {
           const int l = DV[t].level[i];
-          if (l >= 1 && act_[i]) maxm2 = std::max(maxm2, inst_[i]->com_[l].cut_maxm2[colour]);
+          if (l >= 1 && act_[i]) maxrec = std::max(maxrec, inst_[i]->com_[l].cut_maxrec[colour]);
         }
-        if (E::kWarpCut) {
-          launch_cut<T>(D, w, colour, s);
-        } else {
-          const int cap = E::template inv_cap_for<T>(maxm2, w.total);
-          const int gridc = std::max(1, std::min(w.total, sms_ * 16));
-          kb_cut_solve_cta<DIM, P, T><<<gridc, kCutThreads, E::template inv_slot_bytes<T>(cap), s>>>(
-              D, w.off, K_, w.total, colour, cap, err_);
-          count("batched cut patches");
-        }
+        const int cap = sizeof(T) == 8 ? E::kRecSlot64 : E::kRecSlot;
+        const int slot = std::min(cap, (int)((maxrec * sizeof(T) + 15) / 16 * 16));
+        int nb = 0;
+        CUTMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kb_cut_pipe<DIM, P, T>, 128, 2 * slot));
+        const int gridc = std::max(1, std::min(w.total, std::max(1, nb) * sms_));
+        kb_cut_pipe<DIM, P, T><<<gridc, 128, 2 * slot, s>>>(D, w.off, K_, w.total, colour, slot, err_);
+        count("batched cut patches");
       }
     }
   }

@@ -491,9 +491,12 @@ cf_status cf_coarse_solve(cf_problem* pb, int precision, const double* d_b0, dou
 
 int64_t cf_launch_count(const cf_problem* pb) { return no_device(pb) ? 0 : pb->eng->launches(); }
 
-cf_status cf_profile_start(cf_problem* pb, int kernel) {
-  if (no_device(pb) || kernel < 1 || kernel > 5) return fail(CF_EINVAL, "bad argument");
-  return guarded([&] { pb->eng->profile_start(kernel); });
+cf_status cf_profile_start(cf_problem* pb, int kernel) { return cf_profile_start_level(pb, kernel, -1); }
+
+cf_status cf_profile_start_level(cf_problem* pb, int kernel, int level) {
+  if (no_device(pb) || kernel < 1 || kernel > 5 || level < -1 || level >= (int)pb->H.levels.size())
+    return fail(CF_EINVAL, "bad argument");
+  return guarded([&] { pb->eng->profile_start(kernel, level); });
 }
 
 cf_status cf_profile_read(cf_problem* pb, double* ms, int64_t* launches, double* flops, double* bytes) {

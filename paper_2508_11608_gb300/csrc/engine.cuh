@@ -16,6 +16,7 @@
 #include <string>
 #include <vector>
 
+#include "cutpipe.cuh"
 #include "engine_api.hpp"
 #include "kernels.cuh"
 #include "setup.hpp"
@@ -183,8 +184,16 @@ class Engine final : public EngineBase {
     std::vector<int> cut_start;
     std::vector<int> cut_maxm2;
     std::vector<int> cut_maxit;
-    std::vector<CutPlan> plan64, plan32;  // launch shape of the block cut kernel per colour
     int64_t nmembers;
+    // pipelined cut kernel (closures of more than 64 nodes)
+    int* members32 = nullptr;
+    int* pioff = nullptr;
+    int* pnit = nullptr;
+    uint32_t* pitems = nullptr;
+    int* ppk = nullptr;
+    uint64_t* pgmask = nullptr;
+    int64_t* proff = nullptr;
+    std::vector<int> cut_maxrec;
     int* pro_col;
     int* res_col;
     int* coarse_nodes;
@@ -201,6 +210,7 @@ class Engine final : public EngineBase {
     T* coarse_inv;
     float* dense_d;  // FP32 interior-patch map, transposed, rows padded to 4 (Wt[kc][r])
     float* tc_b = nullptr;  // the same map as the tensor-core B operand (TF32, core-matrix layout)
+    T* rec = nullptr;       // cut-patch records of the pipelined kernel (packed inverse + cut rows)
     T* dinv = nullptr;  // Chebyshev smoother: 1 / diag(A_l) on the box (0 off the DoFs)
     T* xp = nullptr;    // Chebyshev smoother: previous iterate
     T *x, *b, *r;          // box vectors
@@ -230,24 +240,17 @@ class Engine final : public EngineBase {
     err_ = pool_.alloc<int>(1);
     CUTMG_CUDA(cudaFuncSetAttribute(k_smooth_tc<DIM, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     TcGeo<DIM, P>::SMEM));
-    CUTMG_CUDA(cudaFuncSetAttribute(k_cut_solve_cta<DIM, P, double, false, kCutNT<double>>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, kInvSlotBytesMax));
-    CUTMG_CUDA(cudaFuncSetAttribute(k_cut_solve_cta<DIM, P, float, false, kCutNT<float>>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, kInvSlotBytesMax));
-    CUTMG_CUDA(cudaFuncSetAttribute(k_cut_solve_cta<DIM, P, double, true, kCutThreads>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, kInvSlotBytesMax));
-    CUTMG_CUDA(cudaFuncSetAttribute(k_cut_solve_cta<DIM, P, float, true, kCutThreads>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, kInvSlotBytesMax));
+    if (!kWarpCut) {
+      CUTMG_CUDA(cudaFuncSetAttribute(k_cut_pipe<DIM, P, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      2 * kRecSlotMax));
+      CUTMG_CUDA(cudaFuncSetAttribute(k_cut_pipe<DIM, P, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      2 * kRecSlotMax));
+    }
     {
       int dev = 0;
       CUTMG_CUDA(cudaGetDevice(&dev));
       CUTMG_CUDA(cudaDeviceGetAttribute(&sms_, cudaDevAttrMultiProcessorCount, dev));
     }
-    for (int l = 1; l < L; ++l)
-      for (int col = 0; col < (1 << DIM); ++col) {
-        com_[l].plan64.push_back(cut_plan<double>(com_[l], col));
-        com_[l].plan32.push_back(cut_plan<float>(com_[l], col));
-      }
     CUTMG_CUDA(cudaMallocHost(&host_sc_, 16 * sizeof(double)));
     CUTMG_CUDA(cudaStreamCreateWithFlags(&cap_, cudaStreamNonBlocking));
     if (H.prm.smoother == 1) {
@@ -268,8 +271,9 @@ class Engine final : public EngineBase {
   int64_t launches() const override { return launches_; }
   // family 1 = interior-patch step (FP32: 1 dense one patch per thread, 2 dense
   // two per thread, 3 dense split, 4 tensor cores; FP64: 1 warp per patch,
-  // 2 block per patch); family 2 = cut-patch step of the block kernel (1
-  // staged rows, 2 unstaged).  0 restores the automatic choice.
+  // 2 block per patch); family 2 = cut-patch step of the pipelined kernel (1
+  // records through shared memory by TMA, 2 records read from global
+  // memory).  0 restores the automatic choice.
   void set_variant(int family, int variant) override {
     if (family == 1) {
       if (variant < 0 || variant > 4) throw std::invalid_argument("interior variant must be 0..4");
@@ -295,8 +299,9 @@ class Engine final : public EngineBase {
     *n0 = com_[0].ndof;
     *nbox = com_[0].nbox;
   }
-  void profile_start(int kind) override {
+  void profile_start(int kind, int level) override {
     prof_.kind = kind;
+    prof_.level = level;
     prof_.used = 0;
     prof_.flops = prof_.bytes = 0.0;
     prof_.n = 0;
@@ -706,94 +711,49 @@ class Engine final : public EngineBase {
  private:
   static constexpr int kDotBlocks = 512;
  public:
-  // shared-memory slot for one patch inverse in the cut-patch kernel.  Grids
-  // of many patches (several blocks per SM) use a 12 KB slot (FP64 m <= 39,
-  // FP32 m <= 55 through TMA, larger inverses read from global memory) so
-  // that more blocks fit on an SM.  Grids of at most kSmallGrid blocks, where
-  // one patch's latency is the launch time, take inverses up to 48 KB through
-  // TMA and stage the element-matrix rows of the patch in shared memory.
-  static constexpr int kInvSlotBytes = 12 * 1024;
-  static constexpr int kInvSlotBytesStage = 48 * 1024;
-  static constexpr int kInvSlotBytesMax = 96 * 1024;  // attribute bound of every variant
-  static constexpr int kSmallGrid = 2 * 152;
-  // interior colours with at least this many patches take two per thread in
-  // the FP32 dense step (enough blocks to fill every SM either way)
-  static constexpr int kDensePairPatches = 150000;
-  // below this many patches a colour takes several threads per patch
-  static constexpr int kDenseThreadPatches = 20000;
-  // threads per patch of the unstaged cut kernel (64 was measured slower
-  // than 128 for FP32 at 224^3: 233 against 191 us per finest colour step)
-  template <typename T>
-  static constexpr int kCutNT = kCutThreads;
   // when no patch can exceed 64 DoFs, (2p+1)^d <= 64 (2D Q1-Q3, 3D Q1), one
-  // warp solves a patch, one or two rows per lane; otherwise (3D Q2) each
-  // patch takes a block.  The choice depends on (d, p) only, so a problem
+  // warp solves a patch, one or two rows per lane; otherwise (3D Q2) the
+  // pipelined block kernel (k_cut_pipe) takes the patches.  The choice depends on (d, p) only, so a problem
   // solved alone and inside a batch runs the same arithmetic.
   static constexpr bool kWarpCut = (DIM == 2 ? (2 * P + 1) * (2 * P + 1) : (2 * P + 1) * (2 * P + 1) * (2 * P + 1)) <= 64;
-  // inverses with m^2 <= cap elements go through shared memory; the slot
-  // holds the 16-byte-rounded copy
-  // Launch shape of one cut colour step of the block kernel.  At most two
-  // patches per SM (latency-bound): staged rows and the largest inverse slot
-  // (48, 24, 12 KB) with which every patch of the colour is resident at once.
-  // Otherwise the unstaged kernel with a 12 KB slot, eight blocks per SM
-  // hiding each other's latency, over a grid of at most 16 blocks per SM.
+  // Pipelined cut kernel: record slots of the colour's longest record (16-byte
+  // multiple) up to kRecSlot (FP32) / kRecSlot64 bytes; longer records are
+  // read from global memory.  Variant 2 of the cut family reads every record
+  // from global memory (the same arithmetic).  The grid: every block the
+  // occupancy calculator lets reside, at most one per patch.
+  static constexpr int kRecSlot = 8 * 1024, kRecSlot64 = 12 * 1024, kRecSlotMax = 16 * 1024;
+  struct PipePlan {
+    int slot = 0, grid = 0;
+  };
   template <typename T>
-  CutPlan cut_plan(const Common& c, int colour) const {
-    CutPlan pl;
+  PipePlan pipe_plan(const Common& c, int colour) const {
+    PipePlan pl;
     const int cnt = c.cut_start[colour + 1] - c.cut_start[colour];
-    if (kWarpCut || cnt <= 0) return pl;
-    const int rows = (int)(((size_t)c.cut_maxit[colour] * NB * sizeof(T) + 15) / 16 * 16);
-    if (cnt <= 2 * sms_)
-      for (int slot : {kInvSlotBytesStage, kInvSlotBytesStage / 2, kInvSlotBytes}) {
-        const int cap = std::min(c.cut_maxm2[colour], (slot - 16) / (int)sizeof(T));
-        const int dyn = (int)inv_slot_bytes<T>(cap) + rows;
-        int nb = 0;
-        CUTMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cut_solve_cta<DIM, P, T, true, kCutThreads>,
-                                                                 kCutThreads, dyn));
-        if (nb > 0 && cnt <= nb * sms_) {
-          pl.staged = true;
-          pl.cap = cap;
-          pl.row_off = (int)inv_slot_bytes<T>(cap);
-          pl.dyn = dyn;
-          pl.grid = cnt;
-          return pl;
-        }
-      }
-    pl.cap = std::min(c.cut_maxm2[colour], (kInvSlotBytes - 16) / (int)sizeof(T));
-    pl.row_off = pl.dyn = (int)inv_slot_bytes<T>(pl.cap);
-    // FP64: more, shorter waves (the tail of a wave idles the FP64 pipes;
-    // 32 per SM measured faster than 16 at 128^3 and 224^3).  FP32 large
-    // grids stay unstaged: staging their rows measured slower at both sizes.
-    pl.grid = std::min(cnt, sms_ * (sizeof(T) == 8 ? 32 : 16));
+    const int cap = sizeof(T) == 8 ? kRecSlot64 : kRecSlot;
+    pl.slot = var_cut_ == 2 ? 0 : std::min(cap, (int)((c.cut_maxrec[colour] * sizeof(T) + 15) / 16 * 16));
+    int nb = 0;
+    CUTMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cut_pipe<DIM, P, T>, 128, 2 * pl.slot));
+    pl.grid = std::max(1, std::min(cnt, std::max(1, nb) * sms_));
     return pl;
   }
-  // a launch shape of the requested kind whatever the colour's size (tests):
-  // staged with the 48 KB slot, or unstaged with the 12 KB slot
   template <typename T>
-  CutPlan cut_plan_forced(const Common& c, int colour, bool staged) const {
-    CutPlan pl;
-    const int cnt = c.cut_start[colour + 1] - c.cut_start[colour];
-    const int slot = staged ? kInvSlotBytesStage : kInvSlotBytes;
-    pl.staged = staged;
-    pl.cap = std::min(c.cut_maxm2[colour], (slot - 16) / (int)sizeof(T));
-    pl.row_off = (int)inv_slot_bytes<T>(pl.cap);
-    const int rows = staged ? (int)(((size_t)c.cut_maxit[colour] * NB * sizeof(T) + 15) / 16 * 16) : 0;
-    pl.dyn = pl.row_off + rows;
-    if (pl.dyn > kInvSlotBytesMax) throw std::invalid_argument("staged cut variant does not fit this level");
-    pl.grid = std::min(cnt, sms_ * 16);
-    return pl;
-  }
-  static CutPatchArgs cut_args(const Common& c) {
-    return CutPatchArgs{c.cutv, c.cutn, c.cutmo, c.cutio, c.cutfo, c.cutcell, c.citoff, c.citems};
-  }
-  template <typename T>
-  static int inv_cap_for(int maxm2, int npatch) {
-    const int cap = ((npatch <= kSmallGrid ? kInvSlotBytesStage : kInvSlotBytes) - 16) / (int)sizeof(T);
-    return maxm2 < cap ? maxm2 : cap;
-  }
-  template <typename T>
-  static size_t inv_slot_bytes(int cap) {
-    return ((size_t)cap * sizeof(T) + 15) / 16 * 16;
+  PipeLevel<T> pipe_level(const Common& c, Typed<T>& D, T* x, const T* b) const {
+    PipeLevel<T> L;
+    L.op = D.op;
+    L.x = x;
+    L.b = b;
+    L.vert = c.cutv;
+    L.cnt = c.cutn;
+    L.moff = c.cutmo;
+    L.members = c.members32;
+    L.ioff = c.pioff;
+    L.nit = c.pnit;
+    L.items = c.pitems;
+    L.pk = c.ppk;
+    L.gmask = c.pgmask;
+    L.roff = c.proff;
+    L.rec = D.rec;
+    return L;
   }
  private:
   static constexpr int kVecBlocks = 1024;
@@ -810,6 +770,7 @@ class Engine final : public EngineBase {
   struct Prof {
     int kind = 0;  // 1 cut-patch solve, 2 interior-patch step, 3 apply (bulk), 4 apply (boundary),
                    // 5 ghost-face moments
+    int level = -1;  // only launches on this level (-1: all levels)
     std::vector<cudaEvent_t> ev;
     int used = 0;
     int64_t n = 0;
@@ -873,8 +834,8 @@ class Engine final : public EngineBase {
     ++launches_;
   }
   // event pair around a launch of the profiled family (on the launching stream)
-  void prof_mark(int kind, cudaStream_t s) {
-    if (prof_.kind != kind) return;
+  void prof_mark(int kind, int level, cudaStream_t s) {
+    if (prof_.kind != kind || (prof_.level >= 0 && prof_.level != level)) return;
     if (prof_.used == (int)prof_.ev.size()) {
       cudaEvent_t e;
       CUTMG_CUDA(cudaEventCreate(&e));
@@ -882,8 +843,8 @@ class Engine final : public EngineBase {
     }
     CUTMG_CUDA(cudaEventRecord(prof_.ev[prof_.used++], s));
   }
-  void prof_work(int kind, double flops, double bytes) {
-    if (prof_.kind != kind) return;
+  void prof_work(int kind, int level, double flops, double bytes) {
+    if (prof_.kind != kind || (prof_.level >= 0 && prof_.level != level)) return;
     prof_.n += 1;
     prof_.flops += flops;
     prof_.bytes += bytes;
@@ -941,7 +902,10 @@ class Engine final : public EngineBase {
         D.tc_b = pool_.upload<float>(bo);
       }
     }
-    D.inv = pool_.upload<T>(h.inv);
+    if (kWarpCut)
+      D.inv = pool_.upload<T>(h.inv);
+    else
+      D.rec = pool_.upload<T>(h.rec);
     D.pro_w = l > 0 ? pool_.upload<T>(h.pro_w) : nullptr;
     D.res_w = l > 0 ? pool_.upload<T>(h.res_w) : nullptr;
     D.coarse_inv = l == 0 ? pool_.upload<T>(h.coarse_inv) : nullptr;
@@ -1007,6 +971,31 @@ class Engine final : public EngineBase {
     c.cut_maxm2 = h.cut_maxm2;
     c.cut_maxit = h.cut_maxit;
     c.nmembers = (int64_t)h.members.size();
+    if (!kWarpCut) {
+      std::vector<int> m32(h.members.begin(), h.members.end());
+      c.members32 = pool_.upload<int>(m32);
+      // row items in 4-byte aligned runs per patch
+      const int64_t ncp = (int64_t)h.cut_vert.size();
+      std::vector<int> io(ncp), ni(ncp);
+      std::vector<uint32_t> words;
+      for (int64_t j = 0; j < ncp; ++j) {
+        const int i0 = h.cut_item_off[j], i1 = h.cut_item_off[j + 1];
+        io[j] = (int)words.size();
+        ni[j] = i1 - i0;
+        for (int q = i0; q < i1; q += 4) {
+          uint32_t w = 0;
+          for (int b = 0; b < 4 && q + b < i1; ++b) w |= (uint32_t)h.cut_items[q + b] << (8 * b);
+          words.push_back(w);
+        }
+      }
+      c.pioff = pool_.upload<int>(io);
+      c.pnit = pool_.upload<int>(ni);
+      c.pitems = pool_.upload<uint32_t>(words);
+      c.ppk = pool_.upload<int>(h.cut_pk);
+      c.pgmask = pool_.upload<uint64_t>(h.cut_gmask);
+      c.proff = pool_.upload<int64_t>(h.cut_roff);
+      c.cut_maxrec = h.cut_maxrec;
+    }
     c.pro_col = l > 0 ? pool_.upload<int>(h.pro_col) : nullptr;
     c.res_col = l > 0 ? pool_.upload<int>(h.res_col) : nullptr;
     if (l == 0) {
@@ -1117,24 +1106,24 @@ class Engine final : public EngineBase {
   void apply(int l, Typed<T>& D, const T* x, const T* b, T* y, cudaStream_t s) {
     const Common& c = com_[l];
     if (c.nbulk > 0) {
-      prof_mark(3, s);
+      prof_mark(3, l, s);
       k_apply_bulk<DIM, P, T><<<blocks_for(c.nbulk, 128), 128, 0, s>>>(D.op, x, b, y, c.bulk, c.nbulk);
       count_launch("apply bulk");
-      prof_mark(3, s);
+      prof_mark(3, l, s);
       // per position: the (cell, owned node) pairs that run are (p+1)^d (a
       // cell s contributes the owned nodes with alpha_k = 0 wherever s_k = 1),
       // NB terms each; x read and y written once per owned node (+ b)
       constexpr int NO = Shape<DIM, P>::NO;
       constexpr int PAIRS = (DIM == 2) ? (P + 1) * (P + 1) : (P + 1) * (P + 1) * (P + 1);
-      prof_work(3, 2.0 * PAIRS * NB * c.nbulk, (double)c.nbulk * (NO * (b ? 3 : 2) * sizeof(T) + 4));
+      prof_work(3, l, 2.0 * PAIRS * NB * c.nbulk, (double)c.nbulk * (NO * (b ? 3 : 2) * sizeof(T) + 4));
     }
     if (c.nbnd > 0) {
       face_moments<T>(l, D, x, s);
-      prof_mark(4, s);
+      prof_mark(4, l, s);
       k_apply_bnd<DIM, P, T><<<blocks_for(c.nbnd, 128), 128, 0, s>>>(D.op, x, b, y, c.bnd, c.nbnd);
       count_launch("apply boundary");
-      prof_mark(4, s);
-      prof_work(4, 0.0, 0.0);
+      prof_mark(4, l, s);
+      prof_work(4, l, 0.0, 0.0);
     }
   }
 
@@ -1151,14 +1140,14 @@ class Engine final : public EngineBase {
     }
     if (cnt <= 0) return;
     constexpr int PW = FaceGeo<DIM, P>::PER_WARP;
-    prof_mark(5, s);
+    prof_mark(5, l, s);
     k_face_moments<DIM, P, T><<<blocks_for(blocks_for(cnt, PW), 4), 128, 0, s>>>(D.op, x, c.faces, ids, cnt);
     count_launch("ghost face moments");
-    prof_mark(5, s);
+    prof_mark(5, l, s);
     {
       constexpr int NTF = FaceGeo<DIM, P>::NT;
       const double flf = 2.0 * (2 * P + 1) * P * NTF + 2.0 * P * (P + 1) * NTF * (DIM - 1) + (double)P * NTF;
-      prof_work(5, cnt * flf, cnt * (((2.0 * P + 1) * NTF + (double)P * NTF) * sizeof(T) + 8.0));
+      prof_work(5, l, cnt * flf, cnt * (((2.0 * P + 1) * NTF + (double)P * NTF) * sizeof(T) + 8.0));
     }
   }
 
@@ -1168,12 +1157,12 @@ class Engine final : public EngineBase {
     if (!cut) {
       const int a0 = c.cart_start[colour], cnt = c.cart_start[colour + 1] - a0;
       if (cnt <= 0) return;
-      prof_mark(2, s);
+      prof_mark(2, l, s);
       if constexpr (std::is_same<T, float>::value)
       {
         constexpr int PPB = 128 / DenseGeo<DIM, P>::NPART;
         int v = var_int_;
-        if (v == 0) v = cnt >= kDensePairPatches ? 2 : (cnt >= kDenseThreadPatches ? 1 : 3);
+        if (v == 0) v = 4;  // tensor cores (TF32 products, FP32 accumulation)
         if (v == 4)
           k_smooth_tc<DIM, P><<<std::min(blocks_for(cnt, 128), 2 * sms_), 256, TcGeo<DIM, P>::SMEM, s>>>(
               D.tc_b, c.N, c.n, x, b, c.cart + a0, cnt, err_, spin_);
@@ -1191,34 +1180,27 @@ class Engine final : public EngineBase {
         k_smooth_cart<DIM, P, T, WARPS><<<blocks_for(cnt, WARPS), 32 * WARPS, 0, s>>>(
             D.fd, c.N, c.n, x, b, c.cart + a0, cnt);
       count_launch("smooth interior patches");
-      prof_mark(2, s);
+      prof_mark(2, l, s);
       const auto& w = H_.levels[l].work_cart[colour];
-      prof_work(2, w[0], w[1] * sizeof(T) + w[2]);
+      prof_work(2, l, w[0], w[1] * sizeof(T) + w[2]);
     } else {
       const int a0 = c.cut_start[colour], cnt = c.cut_start[colour + 1] - a0;
       if (cnt <= 0) return;
-      face_moments<T>(l, D, x, s, colour);
-      prof_mark(1, s);
-      if (kWarpCut) {
+      if (kWarpCut) face_moments<T>(l, D, x, s, colour);
+      prof_mark(1, l, s);
+      if (!kWarpCut) {
+        const PipePlan pl = pipe_plan<T>(c, colour);
+        k_cut_pipe<DIM, P, T><<<pl.grid, 128, 2 * pl.slot, s>>>(pipe_level<T>(c, D, x, b), a0, cnt, pl.slot,
+                                                                    err_, spin_);
+      } else {
         k_cut_solve<DIM, P, T, WARPS><<<blocks_for(cnt, WARPS), 32 * WARPS, 0, s>>>(
             D.op, x, b, c.cutv + a0, c.cutn + a0, c.cutmo + a0, c.cutio + a0, c.members, c.mnode, c.fofs,
             c.fent, D.inv, cnt);
-      } else {
-        CutPlan pl = (sizeof(T) == 8 ? c.plan64 : c.plan32)[colour];
-        if (var_cut_ != 0 && pl.staged != (var_cut_ == 1)) pl = cut_plan_forced<T>(c, colour, var_cut_ == 1);
-        if (pl.staged)
-          k_cut_solve_cta<DIM, P, T, true, kCutThreads><<<pl.grid, kCutThreads, pl.dyn, s>>>(
-              D.op, x, b, cut_args(c), c.members, c.mnode, c.fofs, c.fent, D.inv, a0, cnt, pl.cap,
-              pl.row_off, err_, spin_);
-        else
-          k_cut_solve_cta<DIM, P, T, false, kCutNT<T>><<<pl.grid, kCutNT<T>, pl.dyn, s>>>(
-              D.op, x, b, cut_args(c), c.members, c.mnode, c.fofs, c.fent, D.inv, a0, cnt, pl.cap,
-              pl.row_off, err_, spin_);
       }
       count_launch("cut patch solve");
-      prof_mark(1, s);
+      prof_mark(1, l, s);
       const auto& w = H_.levels[l].work_cut[colour];
-      prof_work(1, w[0], w[1] * sizeof(T) + w[2]);
+      prof_work(1, l, w[0], w[1] * sizeof(T) + w[2]);
     }
   }
 

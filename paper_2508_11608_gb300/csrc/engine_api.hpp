@@ -59,7 +59,7 @@ class EngineBase {
   virtual void set_wait_limit(int polls) = 0;
   // kernel launches issued so far, and event timing of one kernel family
   virtual int64_t launches() const = 0;
-  virtual void profile_start(int kind) = 0;
+  virtual void profile_start(int kind, int level) = 0;
   virtual void profile_read(double* ms, int64_t* n, double* flops, double* bytes) = 0;
   // device data of the coarsest level: FP64 explicit inverse (n0 x n0),
   // lattice index of each coarse DoF (int and int64), lattice size

@@ -1000,17 +1000,11 @@ __global__ void __launch_bounds__(32 * WARPS) k_cut_solve(OpArgs<T> A, T* __rest
 }
 
 // ---------------------------------------------------------------------------
-// Cut-patch step with one 128-thread block per patch.  Thread 0 starts a TMA
-// bulk copy (cp.async.bulk, completion on an mbarrier) of the patch's
-// explicit inverse into shared memory as soon as the patch is known; the
-// copy runs while the block forms the residual rows, and the local solve
-// then reads the inverse from shared memory.  Inverses larger than the
-// shared-memory slot are read from global memory instead.  The wait on the
-// mbarrier is bounded: past `spin` polls (a kernel argument, kTmaSpin unless
-// the caller lowers it) the block records an error in *err, polls again for
-// its own copy (at most kTmaSpin times, so that no copy is left in flight
-// into shared memory) and gives up the patch.
-constexpr int kCutThreads = 128;
+// Asynchronous copies into shared memory: TMA bulk copies (cp.async.bulk)
+// completing on an mbarrier, and per-element cp.async.  Every wait on an
+// mbarrier is bounded: past `limit` polls the caller records an error and
+// drains its own copy (at most kTmaSpin polls) before it moves on, so that no
+// copy is left in flight into shared memory.
 constexpr int kTmaSpin = 1 << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -1057,326 +1051,6 @@ __device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;" ::: "memory");
   asm volatile("cp.async.wait_group 0;" ::: "memory");
-}
-
-// Per-patch arrays of the block kernel (absolute patch index j).
-struct CutPatchArgs {
-  const int* vert;       // packed patch vertex
-  const int* cnt;        // m, DoFs of the patch
-  const int* moff;       // first member of the patch
-  const int64_t* ioff;   // offset of the patch inverse
-  const int* fo;         // [npatch + 1] ghost-face entries fent[fo[j] .. fo[j+1])
-  const int* cell;       // [npatch][2^DIM] cut-cell matrix id, -1 uncut, -2 inactive
-  const int* item_off;   // [npatch + 1]
-  const uint8_t* items;  // s * NB + i: rows (patch cell s, local node i) to form
-};
-
-// Launch shape of the block cut kernel for one colour step.
-struct CutPlan {
-  bool staged = false;
-  int cap = 0, row_off = 0, dyn = 0, grid = 0;
-};
-
-struct CutMeta {
-  int vert, m, mo, f0, f1, i0, i1;
-  int64_t io;
-};
-
-__device__ __forceinline__ CutMeta cut_meta(const CutPatchArgs& C, int j) {
-  CutMeta t;
-  t.vert = C.vert[j];
-  t.m = C.cnt[j];
-  t.mo = C.moff[j];
-  t.io = C.ioff[j];
-  t.f0 = C.fo[j];
-  t.f1 = C.fo[j + 1];
-  t.i0 = C.item_off[j];
-  t.i1 = C.item_off[j + 1];
-  return t;
-}
-
-constexpr int kFeCap = 512;  // ghost-face entries of one patch handled in parallel (more: per row from global)
-
-template <int DIM, int P, typename T>
-struct CutScratch {
-  using G = PatchGeo<DIM, P>;
-  T x[G::NCL];
-  T part[G::NCELL][G::NB];
-  T r[G::NCL];
-  const T* rowbase[G::NCELL];
-  T fc[kFeCap];  // contribution of each ghost-face entry to its row
-  uint8_t item[G::NCELL * G::NB];
-};
-
-// One cut patch on one block.  Every load that depends only on the patch
-// metadata is issued in one round (closure of x, DoF lists, cell matrices,
-// ghost-face entries, row items, the TMA copy of the inverse); the second
-// round reads the element-matrix rows and the ghost-face moments (one entry
-// per thread), and the solve splits each of the m rows over up to 4 lanes.
-// Uncut cells read the level's element matrix through L1.
-template <int DIM, int P, typename T, bool STAGE, int NT>
-__device__ __forceinline__ void cut_body_cta(const OpArgs<T>& A, T* __restrict__ x,
-                                             const T* __restrict__ b, const CutMeta& M, int j,
-                                             const CutPatchArgs& C, const uint16_t* __restrict__ members,
-                                             const int* __restrict__ mnode, const int* __restrict__ fofs,
-                                             const int* __restrict__ fent, const T* __restrict__ inv,
-                                             CutScratch<DIM, P, T>& S, T* sinv, T* srow, int inv_cap,
-                                             uint64_t* bar, uint32_t& phase, const T* __restrict__ sK,
-                                             int* err, int spin) {
-  using G = PatchGeo<DIM, P>;
-  constexpr int CC = G::C, NB = G::NB, NCL = G::NCL, NCELL = G::NCELL, NTF = FaceGeo<DIM, P>::NT;
-  constexpr int TPT = (NCL + NT - 1) / NT;  // patch DoFs per thread
-  const int tid = threadIdx.x, m = M.m, n = A.n;
-  const bool tma = m * m <= inv_cap;
-  if (tma && tid == 0) {
-    const uint32_t bytes = (uint32_t)(((size_t)m * m * sizeof(T) + 15) / 16 * 16);
-    tma_load_1d(sinv, inv + M.io, bytes, bar);
-  }
-  const int np = A.N + 1;
-  int v[3] = {0, 0, 0};
-  {
-    int q = M.vert;
-#pragma unroll
-    for (int k = 0; k < DIM; ++k) {
-      v[k] = q % np;
-      q /= np;
-    }
-  }
-  // round 1: everything that depends on the metadata only
-  for (int e = tid; e < NCL; e += NT) {
-    int u = e, c[3] = {0, 0, 0};
-    bool in = true;
-#pragma unroll
-    for (int k = 0; k < DIM; ++k) {
-      c[k] = P * (v[k] - 1) + u % CC;
-      u /= CC;
-      if (c[k] < 0 || c[k] >= n) in = false;
-    }
-    S.x[e] = in ? x[lat_index<DIM>(c, n)] : T(0);
-  }
-  if (tid < NCELL) {
-    const int id = C.cell[(size_t)j * NCELL + tid];
-    S.rowbase[tid] = id == -2 ? nullptr : (id == -1 ? sK : A.cutmat + (size_t)id * NB * NB);
-  }
-  const int nfe = M.f1 - M.f0, nit = M.i1 - M.i0;
-  constexpr int EPT = kFeCap / NT;
-  const bool fe_par = nfe <= kFeCap;
-  int ent[EPT];
-#pragma unroll
-  for (int u = 0; u < EPT; ++u) {
-    const int q = tid + u * NT;
-    ent[u] = (fe_par && q < nfe) ? fent[M.f0 + q] : -1;
-  }
-  for (int q = tid; q < nit; q += NT) S.item[q] = C.items[M.i0 + q];
-  int tg[TPT], fa[TPT], fb[TPT], mn[TPT];
-#pragma unroll
-  for (int w = 0; w < TPT; ++w) {
-    const int e = tid + w * NT;
-    tg[w] = fa[w] = fb[w] = mn[w] = 0;
-    if (e < m) {
-      tg[w] = members[M.mo + e];
-      fa[w] = fofs[M.mo + e] - M.f0;
-      fb[w] = fofs[M.mo + e + 1] - M.f0;
-      mn[w] = mnode[M.mo + e];
-    }
-  }
-  __syncthreads();
-  // latency-bound launches (few patches per SM): bring the element-matrix
-  // row of every item into shared memory with all copies in flight at once
-  if (STAGE) {
-    for (int q = tid; q < nit; q += NT) {
-      const int it = S.item[q], sc = it / NB, jj = it - sc * NB;
-      const T* row = S.rowbase[sc] + jj * NB;
-#pragma unroll
-      for (int e = 0; e < NB; ++e) cp_async_elem(srow + q * NB + e, row + e);
-    }
-  }
-  T bval[TPT];
-#pragma unroll
-  for (int w = 0; w < TPT; ++w) bval[w] = (tid + w * NT < m) ? b[mn[w]] : T(0);
-  // round 2: ghost-face entries, one per thread (dvec_m[i_k] G_m[t] summed
-  // over m), and the element-matrix rows
-#pragma unroll
-  for (int u = 0; u < EPT; ++u) {
-    if (ent[u] < 0) continue;
-    const T* g = A.G + (size_t)(ent[u] >> 3) / NTF * (P * NTF) + (ent[u] >> 3) % NTF;
-    T gv[P];
-#pragma unroll
-    for (int mm = 0; mm < P; ++mm) gv[mm] = g[mm * NTF];
-    const int il = ent[u] & 7;
-    T c = T(0);
-#pragma unroll
-    for (int mm = 0; mm < P; ++mm) c += A.dvec[mm][il] * gv[mm];
-    S.fc[tid + u * NT] = c;
-  }
-  T facc[TPT];
-#pragma unroll
-  for (int w = 0; w < TPT; ++w) {
-    facc[w] = T(0);
-    if (tid + w * NT >= m || fe_par) continue;
-    const int* fe = fent + M.f0;
-    for (int q0 = fa[w]; q0 < fb[w]; q0 += 8) {
-      int en[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) en[u] = (q0 + u < fb[w]) ? fe[q0 + u] : -1;
-      T gv[8][P];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        if (en[u] < 0) continue;
-        const T* g = A.G + (size_t)(en[u] >> 3) / NTF * (P * NTF) + (en[u] >> 3) % NTF;
-#pragma unroll
-        for (int mm = 0; mm < P; ++mm) gv[u][mm] = g[mm * NTF];
-      }
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        if (en[u] < 0) continue;
-        const int il = en[u] & 7;
-        T c = T(0);
-#pragma unroll
-        for (int mm = 0; mm < P; ++mm) c += A.dvec[mm][il] * gv[u][mm];
-        facc[w] += c;
-      }
-    }
-  }
-  if (STAGE) {
-    cp_async_wait_all();
-    __syncthreads();
-  }
-  // rows (patch cell s, local node i) of the patch DoFs: row_i of the cell
-  // matrix against the cell's closure values
-  for (int q = tid; q < nit; q += NT) {
-    const int it = S.item[q], sc = it / NB, jj = it - sc * NB;
-    int base = 0, ost = 1;
-#pragma unroll
-    for (int k = 0; k < DIM; ++k) {
-      base += P * ((sc >> k) & 1) * ost;
-      ost *= CC;
-    }
-    const T* row = STAGE ? srow + q * NB : S.rowbase[sc] + jj * NB;
-    T acc = T(0);
-    if (DIM == 2) {
-#pragma unroll
-      for (int q1 = 0; q1 <= P; ++q1)
-#pragma unroll
-        for (int q0 = 0; q0 <= P; ++q0) acc += row[q0 + (P + 1) * q1] * S.x[base + q0 + CC * q1];
-    } else {
-#pragma unroll
-      for (int q2 = 0; q2 <= P; ++q2)
-#pragma unroll
-        for (int q1 = 0; q1 <= P; ++q1)
-#pragma unroll
-          for (int q0 = 0; q0 <= P; ++q0)
-            acc += row[q0 + (P + 1) * (q1 + (P + 1) * q2)] * S.x[base + q0 + CC * (q1 + CC * q2)];
-    }
-    S.part[sc][jj] = acc;
-  }
-  __syncthreads();
-  // residual of the own rows: cell parts in cell order, then the face terms
-#pragma unroll
-  for (int w = 0; w < TPT; ++w) {
-    const int e = tid + w * NT;
-    if (e >= m) continue;
-    if (fe_par) {
-      T f4[4] = {T(0), T(0), T(0), T(0)};
-      int q = fa[w];
-      for (; q + 4 <= fb[w]; q += 4) {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) f4[u] += S.fc[q + u];
-      }
-      for (; q < fb[w]; ++q) f4[0] += S.fc[q];
-      facc[w] = (f4[0] + f4[1]) + (f4[2] + f4[3]);
-    }
-    int o[3] = {0, 0, 0}, u = tg[w];
-#pragma unroll
-    for (int k = 0; k < DIM; ++k) {
-      o[k] = u % CC;
-      u /= CC;
-    }
-    T acc = T(0);
-#pragma unroll
-    for (int sc = 0; sc < NCELL; ++sc) {
-      int jj = 0, jst = 1;
-      bool in = S.rowbase[sc] != nullptr;
-#pragma unroll
-      for (int k = 0; k < DIM; ++k) {
-        const int a = o[k] - P * ((sc >> k) & 1);
-        if (a < 0 || a > P) in = false;
-        jj += a * jst;
-        jst *= (P + 1);
-      }
-      if (in) acc += S.part[sc][jj];
-    }
-    S.r[e] = bval[w] - (acc + facc[w]);
-  }
-  bool ok = true;
-  if (tma) {
-    ok = mbar_wait(bar, phase & 1u, spin);
-    if (!ok) {
-      atomicExch(err, 1);
-      mbar_wait(bar, phase & 1u, kTmaSpin);
-    }
-    phase += 1;
-  }
-  // block-uniform outcome (the solve below shuffles across full warps)
-  ok = __syncthreads_and(ok) != 0;
-  if (ok) {
-    // delta = A_j^{-1} r, one lane per row e reading column e of the
-    // (exactly symmetric) inverse so that neighbouring lanes read neighbouring
-    // addresses.  The order of the sums depends on m only: a patch gets the
-    // same bits in every launch shape (solo, batched, served).
-    // The new value is written from the staged closure value: no other patch
-    // of the colour writes this DoF, so S.x still holds x there.
-    const T* Ai = tma ? sinv : inv + M.io;
-#pragma unroll
-    for (int w = 0; w < TPT; ++w) {
-      const int e = tid + w * NT;
-      if (e >= m) continue;
-      const T* Ac = Ai + e;
-      T a0 = T(0), a1 = T(0);
-      int c = 0;
-      for (; c + 1 < m; c += 2) {
-        a0 += Ac[(size_t)c * m] * S.r[c];
-        a1 += Ac[(size_t)(c + 1) * m] * S.r[c + 1];
-      }
-      if (c < m) a0 += Ac[(size_t)c * m] * S.r[c];
-      x[mn[w]] = S.x[tg[w]] + (a0 + a1);
-    }
-  }
-  __syncthreads();
-}
-
-// STAGE: launches of at most a couple of blocks per SM stage the element-
-// matrix rows in the dynamic shared memory after the inverse slot (at
-// row_off bytes); large grids read them through L1.  NT threads per patch.
-// Blocks of 128 threads resident per SM: seven for FP64 (at most 72
-// registers), nine for FP32 (at most 56).
-template <int DIM, int P, typename T, bool STAGE, int NT>
-__global__ void __launch_bounds__(NT, sizeof(T) == 8 ? 7 : 9) k_cut_solve_cta(OpArgs<T> A, T* __restrict__ x,
-                                                               const T* __restrict__ b, CutPatchArgs C,
-                                                               const uint16_t* __restrict__ members,
-                                                               const int* __restrict__ mnode,
-                                                               const int* __restrict__ fofs,
-                                                               const int* __restrict__ fent,
-                                                               const T* __restrict__ inv, int j0, int npatch,
-                                                               int inv_cap, int row_off, int* err, int spin) {
-  extern __shared__ __align__(16) unsigned char dsm[];
-  __shared__ __align__(8) uint64_t bar;
-  __shared__ CutScratch<DIM, P, T> S;
-  T* sinv = reinterpret_cast<T*>(dsm);
-  T* srow = reinterpret_cast<T*>(dsm + row_off);
-  int j = blockIdx.x;
-  if (j >= npatch) return;
-  CutMeta cur = cut_meta(C, j0 + j);
-  if (threadIdx.x == 0) mbar_init(&bar);
-  __syncthreads();
-  uint32_t phase = 0;
-  for (; j < npatch; j += gridDim.x) {
-    CutMeta nxt = cur;
-    if (j + (int)gridDim.x < npatch) nxt = cut_meta(C, j0 + j + gridDim.x);
-    cut_body_cta<DIM, P, T, STAGE, NT>(A, x, b, cur, j0 + j, C, members, mnode, fofs, fent, inv, S, sinv, srow,
-                                       inv_cap, &bar, phase, A.Kref, err, spin);
-    cur = nxt;
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1526,72 +1200,111 @@ __device__ __forceinline__ void tc_gather(const float* __restrict__ x, const flo
   }
 }
 
-// Bop: the level's W as the B operand (NP x KP, TF32-rounded, in the core-
-// matrix layout above, zero padding).  A bounded wait on the MMAs' mbarrier
-// (`spin` polls) records a timeout in *err.
+// Shared state of a tensor-core block: the A tile and B operand in dynamic
+// shared memory (TcGeo::SMEM bytes), the MMA mbarrier, the tensor-memory
+// columns.  tc_begin: all threads; tc_end releases the columns.
+struct TcBlock {
+  unsigned char* sA;
+  unsigned char* sB;
+  uint64_t* bar;
+  uint32_t tmem;
+  uint32_t phase;
+};
+
+// B operand (NP x KP, TF32-rounded, core-matrix layout, zero padding) into
+// shared memory; every thread calls it, a barrier must follow before an MMA
+template <int DIM, int P>
+__device__ __forceinline__ void tc_load_b(const float* __restrict__ Bop, unsigned char* sB) {
+  using G = TcGeo<DIM, P>;
+  for (int i = threadIdx.x; i < G::B_BYTES / 16; i += blockDim.x)
+    reinterpret_cast<float4*>(sB)[i] = reinterpret_cast<const float4*>(Bop)[i];
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// One tile of up to 128 patches (verts[0 .. cnt)) of one level: gather,
+// MMAs, write-back.  The per-patch result does not depend on the tile's other
+// rows.  A bounded wait on the MMAs' mbarrier (`spin` polls) records a
+// timeout in *err.
+template <int DIM, int P>
+__device__ __forceinline__ void tc_tile(TcBlock& tb, int N, int n, float* __restrict__ x,
+                                        const float* __restrict__ b, const int* __restrict__ verts, int cnt,
+                                        int* err, int spin) {
+  using G = TcGeo<DIM, P>;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int p = tid & 127, half = tid >> 7;
+  constexpr uint32_t idesc = umma_idesc_tf32(G::NP);
+  const bool has = p < cnt;
+  const int base = has ? dense_base<DIM, P>(verts[p], N, n) : 0;
+  if (half == 0)
+    tc_gather<DIM, P, 0>(x, b, base, n, has, p, tb.sA);
+  else
+    tc_gather<DIM, P, 1>(x, b, base, n, has, p, tb.sA);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncthreads();
+  if (tid == 0) {
+    const uint32_t a0 = smem_u32(tb.sA), b0 = smem_u32(tb.sB);
+    tc_fence_after();
+#pragma unroll
+    for (int i = 0; i < G::KP / 8; ++i)
+      umma_tf32(tb.tmem, umma_desc(a0 + i * 2 * 16 * 128, 16 * 128, 128),
+                umma_desc(b0 + i * 2 * (G::NP / 8) * 128, (G::NP / 8) * 128, 128), idesc, i > 0 ? 1u : 0u);
+    umma_commit(tb.bar);
+  }
+  if (!mbar_wait(tb.bar, tb.phase & 1u, spin)) {
+    atomicExch(err, 1);
+    mbar_wait(tb.bar, tb.phase & 1u, kTmaSpin);
+  }
+  tb.phase += 1;
+  tc_fence_after();
+  float d[G::NH];
+  tmem_ld<G::NH>(tb.tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(G::NH * half), d);
+  if (has) {
+#pragma unroll
+    for (int r = 0; r < G::NH; ++r) {
+      const int rr = G::NH * half + r;
+      if (rr < G::NI) x[base + dense_interior_offset<DIM, P>(rr, n)] = d[r];
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+}
+
+template <int DIM, int P>
+__device__ __forceinline__ void tc_begin(TcBlock& tb, unsigned char* tsm, uint64_t* bar, uint32_t* tmem_slot) {
+  using G = TcGeo<DIM, P>;
+  tb.sA = tsm;
+  tb.sB = tsm + G::A_BYTES;
+  tb.bar = bar;
+  tb.phase = 0;
+  if ((threadIdx.x >> 5) == 0) tmem_alloc(tmem_slot, G::COLS);
+  if (threadIdx.x == 0) mbar_init(bar);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  tb.tmem = *tmem_slot;
+}
+
+template <int DIM, int P>
+__device__ __forceinline__ void tc_end(const TcBlock& tb) {
+  tc_fence_after();
+  if ((threadIdx.x >> 5) == 0) tmem_dealloc(tb.tmem, TcGeo<DIM, P>::COLS);
+}
+
+// Bop: the level's W as the B operand.  Persistent over the colour's tiles.
 template <int DIM, int P>
 __global__ void __launch_bounds__(256, 2) k_smooth_tc(const float* __restrict__ Bop, int N, int n,
                                                       float* __restrict__ x, const float* __restrict__ b,
                                                       const int* __restrict__ verts, int nv, int* err, int spin) {
-  using G = TcGeo<DIM, P>;
   extern __shared__ __align__(128) unsigned char tsm[];
-  unsigned char* sA = tsm;
-  unsigned char* sB = tsm + G::A_BYTES;
   __shared__ __align__(8) uint64_t bar;
   __shared__ uint32_t tmem_slot;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  for (int i = tid; i < G::B_BYTES / 16; i += blockDim.x)
-    reinterpret_cast<float4*>(sB)[i] = reinterpret_cast<const float4*>(Bop)[i];
-  if (warp == 0) tmem_alloc(&tmem_slot, G::COLS);
-  if (tid == 0) mbar_init(&bar);
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = tmem_slot;
+  TcBlock tb;
+  tc_load_b<DIM, P>(Bop, tsm + TcGeo<DIM, P>::A_BYTES);
+  tc_begin<DIM, P>(tb, tsm, &bar, &tmem_slot);
   const int ntiles = (nv + 127) / 128;
-  const int p = tid & 127, half = tid >> 7;
-  constexpr uint32_t idesc = umma_idesc_tf32(G::NP);
-  const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
-  uint32_t phase = 0;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int j = tile * 128 + p;
-    const bool has = j < nv;
-    const int base = has ? dense_base<DIM, P>(verts[j], N, n) : 0;
-    if (half == 0)
-      tc_gather<DIM, P, 0>(x, b, base, n, has, p, sA);
-    else
-      tc_gather<DIM, P, 1>(x, b, base, n, has, p, sA);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
-      tc_fence_after();
-#pragma unroll
-      for (int i = 0; i < G::KP / 8; ++i)
-        umma_tf32(tmem, umma_desc(a0 + i * 2 * 16 * 128, 16 * 128, 128),
-                  umma_desc(b0 + i * 2 * (G::NP / 8) * 128, (G::NP / 8) * 128, 128), idesc, i > 0 ? 1u : 0u);
-      umma_commit(&bar);
-    }
-    if (!mbar_wait(&bar, phase & 1u, spin)) {
-      atomicExch(err, 1);
-      mbar_wait(&bar, phase & 1u, kTmaSpin);
-    }
-    phase += 1;
-    tc_fence_after();
-    float d[G::NH];
-    tmem_ld<G::NH>(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(G::NH * half), d);
-    if (has) {
-#pragma unroll
-      for (int r = 0; r < G::NH; ++r) {
-        const int rr = G::NH * half + r;
-        if (rr < G::NI) x[base + dense_interior_offset<DIM, P>(rr, n)] = d[r];
-      }
-    }
-    tc_fence_before();
-    __syncthreads();
-  }
-  tc_fence_after();
-  if (warp == 0) tmem_dealloc(tmem, G::COLS);
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
+    tc_tile<DIM, P>(tb, N, n, x, b, verts + tile * 128, min(128, nv - tile * 128), err, spin);
+  tc_end<DIM, P>(tb);
 }
 
 // ---------------------------------------------------------------------------

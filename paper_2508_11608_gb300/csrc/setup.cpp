@@ -1001,6 +1001,128 @@ void cut_patch_inverses(const RefTables& R, HostLevel& L) {
     if (err[j]) throw std::runtime_error(first_err);
 }
 
+// Records of the block cut kernel: ghost-face masks, per-cell pack offsets,
+// and (unless dry) the packed inverses and cut-cell row packs.
+void cut_patch_records(HostLevel& L, bool dry) {
+  const int d = L.d, p = L.p, N = L.N, NB = ipow(p + 1, d), NCELL = 1 << d;
+  if (ipow(2 * p + 1, d) <= 64) return;  // one warp per patch: the entry-list kernel
+  const int64_t ncp = (int64_t)L.cut_vert.size();
+  const int np = N + 1, ncol = 1 << d, half = 1 << (d - 1);
+  auto cflag_at = [&](const int* c) { return cell_flag(L, c); };
+  L.cut_roff.assign(ncp + 1, 0);
+  L.cut_pk.assign((size_t)ncp * NCELL, -2);
+  L.cut_gmask.assign(ncp, 0);
+  std::vector<int> rows(ncp, 0);
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t j = 0; j < ncp; ++j) {
+    int v[3] = {0, 0, 0};
+    int64_t t = L.cut_vert[j];
+    for (int k = 0; k < d; ++k) {
+      v[k] = (int)(t % np);
+      t /= np;
+    }
+    // pack offsets: the items of one cell are consecutive (emitted cell by cell)
+    const int i0 = L.cut_item_off[j], i1 = L.cut_item_off[j + 1];
+    int r = 0;
+    for (int sc = 0; sc < NCELL; ++sc) {
+      const int id = L.cut_cell[(size_t)j * NCELL + sc];
+      int q0 = i1 - i0, cnt = 0;
+      for (int q = i0; q < i1; ++q)
+        if (L.cut_items[q] / NB == sc) {
+          if (cnt == 0) q0 = q - i0;
+          ++cnt;
+        }
+      if (id == -2) continue;
+      if (id == -1) {
+        L.cut_pk[(size_t)j * NCELL + sc] = -1;
+        continue;
+      }
+      L.cut_pk[(size_t)j * NCELL + sc] = (r << 8) | q0;
+      r += cnt;
+    }
+    rows[j] = r;
+    // ghost faces of the block: plane L of direction k between cell layers
+    // L - 1 and L (block layers 0, 1; -1 and 2 outside)
+    uint64_t mask = 0;
+    for (int k = 0; k < d; ++k)
+      for (int Lp = 0; Lp < 3; ++Lp)
+        for (int u = 0; u < half; ++u) {
+          int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0}, q = 0;
+          for (int kk = 0; kk < d; ++kk) {
+            if (kk == k) {
+              lo[kk] = v[kk] - 1 + Lp - 1;
+              hi[kk] = v[kk] - 1 + Lp;
+            } else {
+              lo[kk] = hi[kk] = v[kk] - 1 + ((u >> q) & 1);
+              ++q;
+            }
+          }
+          const uint8_t f1 = cflag_at(lo), f2 = cflag_at(hi);
+          if ((f1 & kFlagActive) && (f2 & kFlagActive) && ((f1 | f2) & kFlagCut))
+            mask |= 1ull << ((k * 3 + Lp) * half + u);
+        }
+    L.cut_gmask[j] = mask;
+  }
+  for (int64_t j = 0; j < ncp; ++j) {
+    const int64_t m = L.cut_n[j];
+    const int64_t len = (m * (m + 1) / 2 + 3) / 4 * 4 + ((int64_t)rows[j] * NB + 3) / 4 * 4;
+    L.cut_roff[j + 1] = L.cut_roff[j] + len;
+  }
+  L.n_rec = L.cut_roff[ncp];
+  // work model of the pipelined kernel (replaces the entry-list kernel's):
+  // flops 2 m^2 (packed solve) + 2 NB per row item + per ghost face of the
+  // block p NT (2 (2p+1) + 2 NT) for its moments + 2p per ghost entry of a
+  // row; scalars: the record (packed inverse + cut rows), the closures of x
+  // and b, the halo of the boundary ghost faces, x of the DoFs written;
+  // index bytes: DoF list, items, cell kinds, metadata.  The face moments of
+  // the colour step are part of this kernel (no separate launch).
+  {
+    const int NTf = ipow(p + 1, d - 1), NCL = ipow(2 * p + 1, d);
+    uint64_t bnd_mask = 0;
+    for (int k = 0; k < d; ++k)
+      for (int u = 0; u < half; ++u) bnd_mask |= (1ull << ((k * 3 + 0) * half + u)) | (1ull << ((k * 3 + 2) * half + u));
+    L.work_cut.assign(ncol, {0.0, 0.0, 0.0});
+    L.work_face.assign(ncol, {0.0, 0.0, 0.0});
+    for (int col = 0; col < ncol; ++col)
+      for (int j = L.cut_start[col]; j < L.cut_start[col + 1]; ++j) {
+        const double m = L.cut_n[j], nit = L.cut_item_off[j + 1] - L.cut_item_off[j];
+        const double nent = L.cut_fo[j + 1] - L.cut_fo[j];
+        const double nf = __builtin_popcountll(L.cut_gmask[j]);
+        const double nbf = __builtin_popcountll(L.cut_gmask[j] & bnd_mask);
+        L.work_cut[col][0] += 2.0 * m * m + 2.0 * NB * nit + nf * p * NTf * (2.0 * (2 * p + 1) + 2.0 * NTf) +
+                              2.0 * p * nent;
+        L.work_cut[col][1] += m * (m + 1) / 2 + (double)rows[j] * NB + 2.0 * NCL + nbf * p * NTf + m;
+        L.work_cut[col][2] += 4.0 * m + nit + 4.0 * NCELL + 44.0;
+      }
+  }
+  L.cut_maxrec.assign(ncol, 0);
+  for (int col = 0; col < ncol; ++col)
+    for (int j = L.cut_start[col]; j < L.cut_start[col + 1]; ++j)
+      L.cut_maxrec[col] = std::max(L.cut_maxrec[col], (int)(L.cut_roff[j + 1] - L.cut_roff[j]));
+  if (dry) return;
+  L.rec.resize((size_t)L.n_rec);
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t j = 0; j < ncp; ++j) {
+    double* out = &L.rec[(size_t)L.cut_roff[j]];
+    std::fill(out, L.rec.data() + L.cut_roff[j + 1], 0.0);
+    const int m = L.cut_n[j];
+    const double* A = &L.inv[(size_t)L.cut_ioff[j]];
+    for (int i = 0; i < m; ++i)
+      for (int c = 0; c <= i; ++c) out[(size_t)i * (i + 1) / 2 + c] = A[(size_t)i * m + c];
+    double* rp = out + ((int64_t)m * (m + 1) / 2 + 3) / 4 * 4;
+    const int i0 = L.cut_item_off[j], i1 = L.cut_item_off[j + 1];
+    int r = 0;
+    for (int q = i0; q < i1; ++q) {
+      const int sc = L.cut_items[q] / NB, jj = L.cut_items[q] % NB;
+      const int id = L.cut_cell[(size_t)j * NCELL + sc];
+      if (id < 0) continue;
+      const double* K = &L.cutmat[((size_t)id * NB + jj) * NB];
+      std::copy(K, K + NB, rp + (size_t)r * NB);
+      ++r;
+    }
+  }
+}
+
 // Patches (Sec. 2.3, Sec. 3) of a level: vertex sets by colour, and for the
 // cut patches their DoF lists, ghost-face entries, row items, work model and
 // explicit inverses.
@@ -1011,6 +1133,7 @@ void build_patches(const RefTables& R, HostLevel& L, bool dry) {
   cut_patch_rows(L);
   patch_work_model(L);
   if (!dry) cut_patch_inverses(R, L);
+  cut_patch_records(L, dry);
 }
 
 // Optional: with cut_rhs, the cut cells' right-hand side terms for source

@@ -101,6 +101,22 @@ struct HostLevel {
   std::vector<int> cut_fo, cut_cell, cut_item_off;
   std::vector<uint8_t> cut_items;
   HostBlocks inv;                 // explicit FP64 inverses A_j^{-1}, row-major
+  // Per cut patch record of the block kernel ((2p+1)^d > 64, i.e. 3D Q2):
+  // rec[cut_roff[j] ..] = the inverse packed by rows of its lower triangle
+  // (entry (i, c), c <= i, at i (i + 1) / 2 + c; padded to 4 entries), then
+  // the rows of the cut-cell matrices its items use, NB entries each, in item
+  // order (padded to 4 entries); cut_roff[j + 1] - cut_roff[j] = its length.
+  // cut_pk[j * 2^d + s] = -2 inactive cell, -1 uncut, else (r0 << 8) | q0:
+  // the first pack row r0 and first item q0 of cut patch cell s.
+  // cut_gmask[j] bit (k * 3 + L) * 2^(d-1) + u: the face normal to k on
+  // cell-layer plane L of the patch block (0 lower boundary, 1 middle, 2
+  // upper boundary) at tangential cell u is a ghost face.
+  std::vector<int64_t> cut_roff;
+  std::vector<int> cut_pk;
+  std::vector<uint64_t> cut_gmask;
+  std::vector<int> cut_maxrec;    // per colour: longest record
+  HostBlocks rec;
+  int64_t n_rec = 0;              // rec.size() unless dry
   // algorithmic work per launch, used to report achieved FLOP/s and bytes:
   // per colour of the cut-patch solve and of the interior-patch step
   // {flops, scalars moved, index bytes moved}

@@ -3,7 +3,7 @@ for example: ncu --metrics gpu__time_duration.sum --clock-control none --csv
 python -m paper_2508_11608_gb300.profile_solve ball3d_q2_n64 fp64 1).
 
     python -m paper_2508_11608_gb300.profile_solve WORKLOAD [fp64|mixed|both] [SOLVES]
-        [--interior V] [--cut V] [--families]
+        [--interior V] [--cut V] [--families [--levels]]
 
 WORKLOAD names paper_2508_11608_gb300.workloads.CONFIGS.  Prints the host
 setup time, the solve info and, over the solves after the first, the
@@ -36,6 +36,7 @@ def main(argv):
     ap.add_argument("--interior", type=int, default=0)
     ap.add_argument("--cut", type=int, default=0)
     ap.add_argument("--families", action="store_true")
+    ap.add_argument("--levels", action="store_true", help="with --families: one line per level")
     a = ap.parse_args(argv[1:])
     precs = {"fp64": [cm.CF_FP64], "mixed": [cm.CF_MIXED], "both": [cm.CF_FP64, cm.CF_MIXED]}[a.precision]
     t0 = time.perf_counter()
@@ -66,15 +67,18 @@ def main(argv):
             print(f"  ms_per_solve {avg:.3f} dof_per_s {n / (avg * 1e-3):.4e} over {len(ms)} solves", flush=True)
         if a.families:
             for fam, name in FAMILIES.items():
-                pb.profile_start(fam)
-                pb.solve(b, x, rtol=1e-8)
-                pr = pb.profile_read()
-                if pr["launches"] == 0:
-                    continue
-                per = pr["ms"] / pr["launches"]
-                print(f"  {label} {name:22s} {pr['ms']:9.3f} ms  {pr['launches']:5d} launches  "
-                      f"{per * 1e3:8.2f} us/launch  {pr['bytes'] / (pr['ms'] * 1e-3) / 1e9:8.1f} GB/s  "
-                      f"{pr['flops'] / (pr['ms'] * 1e-3) / 1e12:7.3f} TFLOP/s (algorithmic)", flush=True)
+                for lev in (range(pb.n_levels) if a.levels else [-1]):
+                    pb.profile_start(fam, lev)
+                    pb.solve(b, x, rtol=1e-8)
+                    pr = pb.profile_read()
+                    if pr["launches"] == 0:
+                        continue
+                    per = pr["ms"] / pr["launches"]
+                    where = f"L{lev}" if lev >= 0 else "all"
+                    print(f"  {label} {name:22s} {where:3s} {pr['ms']:9.3f} ms  {pr['launches']:5d} launches  "
+                          f"{per * 1e3:8.2f} us/launch  {pr['bytes'] / (pr['ms'] * 1e-3) / 1e9:8.1f} GB/s  "
+                          f"{pr['flops'] / (pr['ms'] * 1e-3) / 1e12:7.3f} TFLOP/s  "
+                          f"{pr['bytes'] / pr['launches'] / 1e6:8.2f} MB/launch (algorithmic)", flush=True)
     return 0
 
 

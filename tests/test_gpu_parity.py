@@ -3,7 +3,10 @@
 Tolerances: FP64 kernels 1e-12 relative per step (rounding of sums of a few
 hundred terms); the solve 1e-10 relative L2 and CG iterations within one;
 FP32 kernels (mixed form) 2e-5 relative per step (single rounding ~6e-8
-amplified by the conditioning of the local solves)."""
+amplified by the conditioning of the local solves), except the interior-patch
+step of the mixed form, whose dense map runs on the tensor cores with TF32
+operands (unit roundoff 2^-11 = 4.9e-4; 2e-2 of the update, as the variant
+tests)."""
 
 import numpy as np
 import pytest
@@ -59,6 +62,7 @@ def test_colour_steps(pair, prec, tol):
     for l in range(1, pb.n_levels):
         n = pb.n_dofs(l)
         for cut in (False, True):
+            tstep = 2e-2 if (prec == cm.CF_MIXED and not cut) else tol
             for col in range(1 << pb.dim):
                 x0 = random_vector(n, 7 + col)
                 b = random_vector(n, 300 + col)
@@ -68,7 +72,7 @@ def test_colour_steps(pair, prec, tol):
                 # the FP32 path also rounds the untouched entries of x to FP32
                 floor = np.abs(x0).max() * (1e-6 if prec == cm.CF_MIXED else 1e-15)
                 err = np.abs(_n(xg) - xo).max()
-                assert err <= tol * np.abs(xo - x0).max() + floor, (l, cut, col)
+                assert err <= tstep * np.abs(xo - x0).max() + floor, (l, cut, col)
 
 
 def test_smoothing_step(pair):
