@@ -54,6 +54,9 @@ struct LvlDesc {
   const int* coarse_nodes;
   int n0;
   PipeLevel<T> pl;  // the level for the pipelined cut kernel (closures of more than 64 nodes)
+  const int* bf_face;  // per colour: block-boundary ghost faces and their moment slots
+  const int* bf_dst;
+  int bf_start[9];
   const float* tc_b;  // FP32 interior-patch map as the tensor-core B operand
 };
 
@@ -163,6 +166,29 @@ __global__ void __launch_bounds__(256, 2) kb_smooth_tc(const LvlDesc<DIM, P, flo
   tc_end<DIM, P>(tb);
 }
 
+// block-boundary ghost-face moments of a colour's cut patches, over the
+// (instance, face) work list (the face list of k_face_moments_to)
+template <int DIM, int P, typename T>
+__global__ void __launch_bounds__(128) kb_face_moments_to(const LvlDesc<DIM, P, T>* __restrict__ D,
+                                                          const int* __restrict__ off, int K, int total,
+                                                          int colour) {
+  constexpr int NT = FaceGeo<DIM, P>::NT, PW = FaceGeo<DIM, P>::PER_WARP;
+  const int lane = threadIdx.x & 31;
+  const int warps = gridDim.x * (blockDim.x >> 5);
+  for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w * PW < total; w += warps) {
+    const int it = w * PW + lane / NT;
+    const bool ok = lane / NT < PW && it < total;
+    const int i = find_inst(off, K, ok ? it : w * PW);
+    const LvlDesc<DIM, P, T>& L = D[i];
+    const int e = L.bf_start[colour] + (ok ? it : w * PW) - off[i];
+    const int d0 = ok ? L.bf_dst[2 * e] : -1, d1 = ok ? L.bf_dst[2 * e + 1] : -1;
+    T* out = const_cast<T*>(L.pl.Gb);
+    face_moment_lanes<DIM, P, T>(L.op, L.x, ok ? L.faces[L.bf_face[e]] : -1, lane,
+                                 d0 >= 0 ? out + (size_t)d0 * P * NT : nullptr,
+                                 d1 >= 0 ? out + (size_t)d1 * P * NT : nullptr);
+  }
+}
+
 template <int DIM, int P, typename T>
 __global__ void __launch_bounds__(128) kb_face_moments(const LvlDesc<DIM, P, T>* __restrict__ D,
                                                        const T* const* __restrict__ X,
@@ -180,7 +206,8 @@ __global__ void __launch_bounds__(128) kb_face_moments(const LvlDesc<DIM, P, T>*
     const LvlDesc<DIM, P, T>& L = D[i];
     const int local = (ok ? it : w * PW) - off[i];
     const int f = colour >= 0 ? L.cfaces[L.cf_start[colour] + local] : local;
-    face_moment_lanes<DIM, P, T>(L.op, X ? X[i] : L.x, ok ? L.faces[f] : -1, f, lane);
+    face_moment_lanes<DIM, P, T>(L.op, X ? X[i] : L.x, ok ? L.faces[f] : -1, lane,
+                                 L.op.G + (size_t)f * P * FaceGeo<DIM, P>::NT, nullptr);
   }
 }
 
@@ -627,7 +654,7 @@ class BatchGroup final : public BatchGroupBase {
     int* off = nullptr;  // device, K + 1
     int total = 0;
   };
-  std::vector<std::vector<Work>> w_cart_, w_tile_, w_cut_, w_cf_;  // [depth][colour]
+  std::vector<std::vector<Work>> w_cart_, w_tile_, w_cut_, w_cf_, w_bf_;  // [depth][colour]
   std::vector<Work> w_bulk_, w_bnd_, w_faces_, w_coarse_, w_xzero_;
   std::vector<std::array<Work, 3>> w_rpass_, w_ppass_;
   Work w_vecF_;
@@ -707,7 +734,12 @@ class BatchGroup final : public BatchGroupBase {
         L.bulk = C.bulk;
         L.bnd = C.bnd;
         L.inv = Ty.inv;
-        if (!E::kWarpCut) L.pl = e->template pipe_level<T>(C, Ty, Ty.x, Ty.b);
+        if (!E::kWarpCut) {
+          L.pl = e->template pipe_level<T>(C, Ty, Ty.x, Ty.b);
+          L.bf_face = C.bf_face;
+          L.bf_dst = C.bf_dst;
+          for (int c = 0; c <= NCOL; ++c) L.bf_start[c] = C.bf_start[c];
+        }
         L.tc_b = e->template typed<float>()[l].tc_b;
         for (int c = 0; c <= NCOL; ++c) {
           L.cart_start[c] = C.cart_start[c];
@@ -751,6 +783,7 @@ class BatchGroup final : public BatchGroupBase {
     // (device memory of old lists is kept in the pool; rebuilds are rare)
     w_cart_.assign(depth_, std::vector<Work>(NCOL));
     w_tile_.assign(depth_, std::vector<Work>(NCOL));
+    w_bf_.assign(depth_, std::vector<Work>(NCOL));
     w_cut_.assign(depth_, std::vector<Work>(NCOL));
     w_cf_.assign(depth_, std::vector<Work>(NCOL));
     w_bulk_.assign(depth_, Work{});
@@ -779,6 +812,12 @@ class BatchGroup final : public BatchGroupBase {
           if (l < 1) return 0;
           auto& C = inst_[i]->com_[l];
           return (C.cart_start[c + 1] - C.cart_start[c] + 127) / 128;
+        });
+        w_bf_[t][c] = fill([&](int i) {
+          const int l = lv[i];
+          if (l < 1 || E::kWarpCut) return 0;
+          auto& C = inst_[i]->com_[l];
+          return C.bf_start[c + 1] - C.bf_start[c];
         });
         w_cut_[t][c] = fill([&](int i) {
           const int l = lv[i];
@@ -896,6 +935,12 @@ class BatchGroup final : public BatchGroupBase {
       if (E::kWarpCut) {
         launch_cut<T>(D, w, colour, s);
       } else {
+        const Work& wb = w_bf_[t][colour];
+        if (wb.total > 0) {
+          kb_face_moments_to<DIM, P, T><<<grid(wb.total, 4 * FaceGeo<DIM, P>::PER_WARP), 128, 0, s>>>(
+              D, wb.off, K_, wb.total, colour);
+          count("batched boundary face moments");
+        }
         // record slot of the longest record among the instances at this depth
         int maxrec = 0;
         for (int i = 0; i < K_; ++i) {

@@ -229,8 +229,20 @@ size_t cutmg_estimate_hierarchy_bytes(const Hierarchy& H) {
             L.cut_item_off.size()) * 4 + L.cut_vert.size() * 8 + L.members.size() * 2 + L.cut_items.size();
     tot += (L.pro_col.size() + L.res_col.size()) * 4;
     const size_t ncoarse = l == 0 ? L.dofs.size() * L.dofs.size() : 0;
-    size_t typed = (size_t)L.n_cut * nb * nb + nb * nb + (size_t)L.n_inv + L.pro_w.size() + L.res_w.size() +
+    // cut-patch storage: explicit inverses (warp kernel) or records and the
+    // boundary-face moment slots (pipelined kernel)
+    const bool pipe = !L.cut_roff.empty();
+    const size_t ncp = L.cut_vert.size();
+    const size_t cutstore = pipe ? (size_t)L.n_rec + (size_t)(L.cut_gboff.empty() ? 0 : L.cut_gboff.back()) * p * nt
+                                 : (size_t)L.n_inv;
+    size_t typed = (size_t)L.n_cut * nb * nb + nb * nb + cutstore + L.pro_w.size() + L.res_w.size() +
                    ncoarse + 3 * nbox + L.members.size() + L.ghost_faces.size() * p * nt;
+    if (pipe) {
+      size_t words = 0;
+      for (size_t j = 0; j < ncp; ++j) words += (size_t)(L.cut_item_off[j + 1] - L.cut_item_off[j] + 3) / 4;
+      tot += 4 * L.members.size() + 4 * words + 8 * ncp + 4 * L.cut_pk.size() + 8 * L.cut_gmask.size() +
+             8 * L.cut_roff.size() + 4 * L.cut_gboff.size() + 4 * L.bf_face.size() + 4 * L.bf_dst.size();
+    }
     if (l > 0) {  // interior-patch dense map: transposed copy and the tensor-core operand (FP32 only)
       size_t nc = 1, ni = 1;
       for (int k = 0; k < d; ++k) {

@@ -11,19 +11,20 @@
 //     and the rows of the cut-cell matrices its items use, one contiguous
 //     run brought into shared memory by one TMA bulk copy (cp.async.bulk,
 //     completion on an mbarrier),
-//   * for each ghost face on the boundary planes of the patch block, the x
-//     values of the p node planes beyond the closure (cp.async).
-// The ghost-face penalty terms of the patch rows (eq. "cutfem-ghost") are
-// formed inside the block from these values: every ghost face in the row of
-// a patch DoF is a face of an active cell that contains the DoF, hence of a
-// patch cell, so it lies on one of the 3 planes per direction of the
-// 2 x .. x 2 block; its moments G_m = coef_m (Mhat x Mhat) J_m with
-// J_m[t] = sum_i dvec_m[i] x(i, t) over the 2p + 1 nodes across the face need
-// the closure and, for the two boundary planes, the halo.  Moments are taken
-// from the x before the colour step, like the rest of the residual
-// (additive within a colour, Sec. 2.3): no DoF of one patch of the colour is
-// read by another patch of the colour (its active cells and their faces lie
-// in its own block).
+//   * the moments of the ghost faces on the boundary planes of its block
+//     (cp.async from its moment slots).
+// Every ghost face in the row of a patch DoF is a face of an active cell that
+// contains the DoF, hence of a patch cell, so it lies on one of the 3 planes
+// per direction of the 2 x .. x 2 block (eq. "cutfem-ghost").  The faces on
+// the middle plane are formed inside the block from the staged closure
+// (G_m = coef_m (Mhat x Mhat) J_m, J_m[t] = sum_i dvec_m[i] x(i, t) over the
+// 2p + 1 nodes across the face): all their nodes belong to active patch
+// cells, so no other patch of the colour writes them.  The faces on the two
+// boundary planes reach into the neighbouring block, whose cut patch of the
+// same colour may update those nodes in the same launch; their moments are
+// therefore computed before the colour step by a separate launch
+// (k_face_moments_to), like every moment of the additive-within-a-colour
+// step (Sec. 2.3): the patch sees the x from before the colour step only.
 #pragma once
 
 #include "kernels.cuh"
@@ -39,8 +40,9 @@ struct PipeGeo {
   static constexpr int NT = FaceGeo<DIM, P>::NT;  // nodes of a face, (p+1)^(d-1)
   static constexpr int HALF = 1 << (DIM - 1);     // cells per block plane
   static constexpr int NFACE = DIM * 3 * HALF;    // faces on the block's planes
+  static constexpr int NIF = DIM * HALF;          // faces on its middle planes
   static constexpr int NBF = DIM * 2 * HALF;      // faces on its boundary planes
-  static constexpr int HALO = NBF * P * NT;       // x beyond the closure for those
+  static constexpr int HALO = NBF * P * NT;       // the moments of those
   static constexpr int ITEMW = (NCELL * NB + 3) / 4;  // 32-bit words of the item list
 };
 
@@ -61,7 +63,19 @@ struct PipeLevel {
   const uint64_t* gmask;    // ghost faces of the block planes
   const int64_t* roff;      // record offsets (entries); roff[j + 1] - roff[j] = length
   const T* rec;             // records
+  const int* gboff;         // first boundary-face moment slot of each patch
+  const T* Gb;              // boundary-face moment slots, P (p+1)^(d-1) values each
 };
+
+// bits of the block-boundary planes (0 and 2) in a ghost-face mask
+template <int DIM, int P>
+__host__ __device__ constexpr uint64_t pipe_bnd_bits() {
+  constexpr int HALF = 1 << (DIM - 1);
+  uint64_t m = 0;
+  for (int k = 0; k < DIM; ++k)
+    for (int u = 0; u < HALF; ++u) m |= (1ull << ((k * 3 + 0) * HALF + u)) | (1ull << ((k * 3 + 2) * HALF + u));
+  return m;
+}
 
 template <int DIM, int P, typename T>
 struct PipeStage {
@@ -82,13 +96,13 @@ struct PipeShared {
   using G = PipeGeo<DIM, P>;
   T part[G::NCELL][G::NB];
   T r[G::NCL];
-  T J[G::NFACE][P][G::NT];
-  T Gm[G::NFACE][P][G::NT];
-  int flist[G::NFACE];
+  T J[G::NIF][P][G::NT];
+  T Gm[G::NIF][P][G::NT];
+  int flist[G::NIF];
 };
 
 struct PipeMeta {
-  int vert, m, mo, io, nit;
+  int vert, m, mo, io, nit, gb;
   int64_t r0, r1;
   uint64_t gmask;
 };
@@ -104,6 +118,7 @@ __device__ __forceinline__ PipeMeta pipe_meta(const PipeLevel<T>& L, int j) {
   t.r0 = L.roff[j];
   t.r1 = L.roff[j + 1];
   t.gmask = L.gmask[j];
+  t.gb = L.gboff[j];
   return t;
 }
 
@@ -162,47 +177,17 @@ __device__ __forceinline__ void pipe_prefetch(const PipeLevel<T>& L, const PipeM
   }
   for (int w = tid; w < (M.nit + 3) / 4; w += NT) cp_async_elem(&st.item[w], L.items + M.io + w);
   if (tid < G::NCELL) cp_async_elem(&st.pk[tid], L.pk + (size_t)j * G::NCELL + tid);
-  // halo of the ghost faces on the two boundary planes of each direction
-  const uint64_t gm = M.gmask;
-  for (int w = tid; w < G::HALO; w += NT) {
-    const int hs = w / (P * G::NT), rem = w - hs * (P * G::NT);
-    const int pl = rem / G::NT, t = rem - pl * G::NT;
-    const int u = hs % G::HALF, ks = hs / G::HALF, k = ks >> 1, side = ks & 1;
-    if (!((gm >> ((k * 3 + 2 * side) * G::HALF + u)) & 1ull)) continue;
-    int c[3] = {0, 0, 0}, q = 0, tt = t;
-    bool in = true;
-#pragma unroll
-    for (int kk = 0; kk < DIM; ++kk) {
-      int ck;
-      if (kk == k) {
-        ck = side == 0 ? pl - P : 2 * P + 1 + pl;
-      } else {
-        ck = P * ((u >> q) & 1) + tt % (P + 1);
-        tt /= P + 1;
-        ++q;
-      }
-      c[kk] = P * (v[kk] - 1) + ck;
-      if (c[kk] < 0 || c[kk] >= n) in = false;
-    }
-    if (in)
-      cp_async_elem(&st.halo[w], L.x + lat_index<DIM>(c, n));
-    else
-      st.halo[w] = T(0);
-  }
+  // moments of the block-boundary ghost faces (one slot per set bit)
+  const int nbv = __popcll(M.gmask & pipe_bnd_bits<DIM, P>()) * P * G::NT;
+  for (int w = tid; w < nbv; w += NT) cp_async_elem(&st.halo[w], L.Gb + (size_t)M.gb * P * G::NT + w);
   asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
-// x at closure coordinates ck (along k, may lie in the halo) and tangential
-// closure coordinates, for a face of plane Lp
+// x at closure coordinate ck along k and tangential cell u, node t, for a
+// face of the middle plane
 template <int DIM, int P, typename T>
-__device__ __forceinline__ T pipe_x(const PipeStage<DIM, P, T>& st, int k, int Lp, int u, int ck, int t) {
-  using G = PipeGeo<DIM, P>;
-  constexpr int C = G::C;
-  if (ck < 0 || ck > 2 * P) {
-    const int side = ck < 0 ? 0 : 1;
-    const int pl = side == 0 ? ck + P : ck - (2 * P + 1);
-    return st.halo[((k * 2 + side) * G::HALF + u) * (P * G::NT) + pl * G::NT + t];
-  }
+__device__ __forceinline__ T pipe_x(const PipeStage<DIM, P, T>& st, int k, int u, int ck, int t) {
+  constexpr int C = 2 * P + 1;
   int o = 0, st_ = 1, q = 0, tt = t;
 #pragma unroll
   for (int kk = 0; kk < DIM; ++kk) {
@@ -217,7 +202,6 @@ __device__ __forceinline__ T pipe_x(const PipeStage<DIM, P, T>& st, int k, int L
     o += c * st_;
     st_ *= C;
   }
-  (void)Lp;
   return st.x[o];
 }
 
@@ -229,17 +213,18 @@ __device__ __forceinline__ void pipe_compute(const PipeLevel<T>& L, const PipeSt
   using G = PipeGeo<DIM, P>;
   constexpr int C = G::C, NB = G::NB, NTF = G::NT;
   const int tid = threadIdx.x, m = st.m, n = L.op.n, np = L.op.N + 1;
-  const uint64_t gm = st.gmask;
-  const int nf = __popcll(gm);
-  if (tid < G::NFACE && ((gm >> tid) & 1ull)) sh.flist[__popcll(gm & ((1ull << tid) - 1ull))] = tid;
+  constexpr uint64_t bnd = pipe_bnd_bits<DIM, P>();
+  const uint64_t gm = st.gmask, gint = gm & ~bnd, gbnd = gm & bnd;
+  const int nf = __popcll(gint);
+  if (tid < G::NFACE && ((gint >> tid) & 1ull)) sh.flist[__popcll(gint & ((1ull << tid) - 1ull))] = tid;
   __syncthreads();
-  // J_m[t] of every ghost face, and the cell rows of the items
+  // J_m[t] of the ghost faces of the middle planes, and the cell rows of the items
   for (int w = tid; w < nf * P * NTF; w += NT) {
     const int fi = w / (P * NTF), rem = w - fi * (P * NTF), mm = rem / NTF, t = rem - mm * NTF;
-    const int f = sh.flist[fi], u = f % G::HALF, kl = f / G::HALF, k = kl / 3, Lp = kl % 3;
+    const int f = sh.flist[fi], u = f % G::HALF, k = f / G::HALF / 3;
     T acc = T(0);
 #pragma unroll
-    for (int i = 0; i <= 2 * P; ++i) acc += L.op.dvec[mm][i] * pipe_x<DIM, P, T>(st, k, Lp, u, P * (Lp - 1) + i, t);
+    for (int i = 0; i <= 2 * P; ++i) acc += L.op.dvec[mm][i] * pipe_x<DIM, P, T>(st, k, u, i, t);
     sh.J[fi][mm][t] = acc;
   }
   const T* rows = st.recp + ((m * (m + 1) / 2 + 3) / 4 * 4);
@@ -333,10 +318,12 @@ __device__ __forceinline__ void pipe_compute(const PipeLevel<T>& L, const PipeSt
             const int uu = u0 + 2 * u1;
             const int bit = (k * 3 + Lp) * G::HALF + uu;
             if (!((gm >> bit) & 1ull)) continue;
-            const int fi = __popcll(gm & ((1ull << bit) - 1ull));
+            const uint64_t below = (1ull << bit) - 1ull;
             const int t = (tj[0] - P * u0) + (DIM == 3 ? (P + 1) * (tj[1] - P * u1) : 0);
+            const T* g = Lp == 1 ? &sh.Gm[__popcll(gint & below)][0][0]
+                                 : &st.halo[__popcll(gbnd & below) * P * NTF];
 #pragma unroll
-            for (int mm = 0; mm < P; ++mm) fac += L.op.dvec[mm][i] * sh.Gm[fi][mm][t];
+            for (int mm = 0; mm < P; ++mm) fac += L.op.dvec[mm][i] * g[mm * NTF + t];
           }
       }
     }

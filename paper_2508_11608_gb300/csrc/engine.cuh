@@ -194,6 +194,10 @@ class Engine final : public EngineBase {
     uint64_t* pgmask = nullptr;
     int64_t* proff = nullptr;
     std::vector<int> cut_maxrec;
+    int* gboff = nullptr;     // boundary-face moment slots per patch
+    int* bf_face = nullptr;   // per colour: block-boundary ghost faces to compute
+    int* bf_dst = nullptr;    // and their two destination slots
+    std::vector<int> bf_start;
     int* pro_col;
     int* res_col;
     int* coarse_nodes;
@@ -211,6 +215,7 @@ class Engine final : public EngineBase {
     float* dense_d;  // FP32 interior-patch map, transposed, rows padded to 4 (Wt[kc][r])
     float* tc_b = nullptr;  // the same map as the tensor-core B operand (TF32, core-matrix layout)
     T* rec = nullptr;       // cut-patch records of the pipelined kernel (packed inverse + cut rows)
+    T* Gb = nullptr;        // moment slots of the block-boundary ghost faces
     T* dinv = nullptr;  // Chebyshev smoother: 1 / diag(A_l) on the box (0 off the DoFs)
     T* xp = nullptr;    // Chebyshev smoother: previous iterate
     T *x, *b, *r;          // box vectors
@@ -753,6 +758,8 @@ class Engine final : public EngineBase {
     L.gmask = c.pgmask;
     L.roff = c.proff;
     L.rec = D.rec;
+    L.gboff = c.gboff;
+    L.Gb = D.Gb;
     return L;
   }
  private:
@@ -902,10 +909,13 @@ class Engine final : public EngineBase {
         D.tc_b = pool_.upload<float>(bo);
       }
     }
-    if (kWarpCut)
+    if (kWarpCut) {
       D.inv = pool_.upload<T>(h.inv);
-    else
+    } else {
       D.rec = pool_.upload<T>(h.rec);
+      D.Gb = pool_.alloc<T>((size_t)std::max(1, h.cut_gboff.empty() ? 0 : h.cut_gboff.back()) * P *
+                            FaceGeo<DIM, P>::NT);
+    }
     D.pro_w = l > 0 ? pool_.upload<T>(h.pro_w) : nullptr;
     D.res_w = l > 0 ? pool_.upload<T>(h.res_w) : nullptr;
     D.coarse_inv = l == 0 ? pool_.upload<T>(h.coarse_inv) : nullptr;
@@ -995,6 +1005,10 @@ class Engine final : public EngineBase {
       c.pgmask = pool_.upload<uint64_t>(h.cut_gmask);
       c.proff = pool_.upload<int64_t>(h.cut_roff);
       c.cut_maxrec = h.cut_maxrec;
+      c.gboff = pool_.upload<int>(h.cut_gboff);
+      c.bf_face = pool_.upload<int>(h.bf_face);
+      c.bf_dst = pool_.upload<int>(h.bf_dst);
+      c.bf_start = h.bf_start;
     }
     c.pro_col = l > 0 ? pool_.upload<int>(h.pro_col) : nullptr;
     c.res_col = l > 0 ? pool_.upload<int>(h.res_col) : nullptr;
@@ -1151,6 +1165,23 @@ class Engine final : public EngineBase {
     }
   }
 
+  // moments of the block-boundary ghost faces of the cut patches of a colour,
+  // from x before the colour step, into the patches' moment slots
+  template <typename T>
+  void boundary_face_moments(int l, Typed<T>& D, const T* x, cudaStream_t s, int colour) {
+    const Common& c = com_[l];
+    const int f0 = c.bf_start[colour], cnt = c.bf_start[colour + 1] - f0;
+    if (cnt <= 0) return;
+    constexpr int PW = FaceGeo<DIM, P>::PER_WARP;
+    prof_mark(5, l, s);
+    k_face_moments_to<DIM, P, T><<<blocks_for(blocks_for(cnt, PW), 4), 128, 0, s>>>(
+        D.op, x, c.faces, c.bf_face + f0, c.bf_dst + 2 * f0, cnt, D.Gb);
+    count_launch("boundary ghost face moments");
+    prof_mark(5, l, s);
+    const auto& w = H_.levels[l].work_face[colour];
+    prof_work(5, l, w[0], w[1] * sizeof(T) + w[2]);
+  }
+
   template <typename T>
   void colour_step(int l, Typed<T>& D, int cut, int colour, T* x, const T* b, cudaStream_t s) {
     const Common& c = com_[l];
@@ -1187,6 +1218,7 @@ class Engine final : public EngineBase {
       const int a0 = c.cut_start[colour], cnt = c.cut_start[colour + 1] - a0;
       if (cnt <= 0) return;
       if (kWarpCut) face_moments<T>(l, D, x, s, colour);
+      else boundary_face_moments<T>(l, D, x, s, colour);
       prof_mark(1, l, s);
       if (!kWarpCut) {
         const PipePlan pl = pipe_plan<T>(c, colour);

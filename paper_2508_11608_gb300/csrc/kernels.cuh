@@ -56,8 +56,8 @@ struct FaceGeo {
 // across the group by shuffles, and lane t writes G_m[t].  All 32 lanes must
 // call this (packed < 0: padding lane).
 template <int DIM, int P, typename T>
-__device__ __forceinline__ void face_moment_lanes(const OpArgs<T>& A, const T* __restrict__ x, int packed, int f,
-                                                  int lane) {
+__device__ __forceinline__ void face_moment_lanes(const OpArgs<T>& A, const T* __restrict__ x, int packed, int lane,
+                                                  T* out0, T* out1) {
   constexpr int NT = FaceGeo<DIM, P>::NT;
   const int grp = lane / NT, t = lane - grp * NT;
   T J[P];
@@ -116,9 +116,12 @@ __device__ __forceinline__ void face_moment_lanes(const OpArgs<T>& A, const T* _
     }
   }
   if (packed >= 0) {
-    T* g = A.G + (size_t)f * P * NT;
 #pragma unroll
-    for (int m = 0; m < P; ++m) g[m * NT + t] = A.coef[m] * acc[m];
+    for (int m = 0; m < P; ++m) {
+      const T g = A.coef[m] * acc[m];
+      if (out0) out0[m * NT + t] = g;
+      if (out1) out1[m * NT + t] = g;
+    }
   }
 }
 
@@ -132,7 +135,25 @@ __global__ void __launch_bounds__(128) k_face_moments(OpArgs<T> A, const T* __re
   const int i = warp * PW + lane / NT;
   const bool ok = lane / NT < PW && i < nfaces;
   const int f = ok ? (ids ? ids[i] : i) : 0;
-  face_moment_lanes<DIM, P, T>(A, x, ok ? faces[f] : -1, f, lane);
+  face_moment_lanes<DIM, P, T>(A, x, ok ? faces[f] : -1, lane, A.G + (size_t)f * P * NT, nullptr);
+}
+
+// The moments of listed ghost faces written to one or two destinations
+// (offsets in units of P (p+1)^(d-1) values into `out`, -1: none): the
+// block-boundary faces of the cut patches of a colour, each copied into the
+// moment slots of the (at most two) patches whose rows read it.
+template <int DIM, int P, typename T>
+__global__ void __launch_bounds__(128) k_face_moments_to(OpArgs<T> A, const T* __restrict__ x,
+                                                         const int* __restrict__ faces, const int* __restrict__ ids,
+                                                         const int* __restrict__ dst, int nfaces, T* __restrict__ out) {
+  constexpr int NT = FaceGeo<DIM, P>::NT, PW = FaceGeo<DIM, P>::PER_WARP;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp * PW >= nfaces) return;  // whole warp
+  const int i = warp * PW + lane / NT;
+  const bool ok = lane / NT < PW && i < nfaces;
+  const int d0 = ok ? dst[2 * i] : -1, d1 = ok ? dst[2 * i + 1] : -1;
+  face_moment_lanes<DIM, P, T>(A, x, ok ? faces[ids[i]] : -1, lane, d0 >= 0 ? out + (size_t)d0 * P * NT : nullptr,
+                               d1 >= 0 ? out + (size_t)d1 * P * NT : nullptr);
 }
 
 // sum over the ghost faces whose two cells contain node idx of (G_F x)(node)

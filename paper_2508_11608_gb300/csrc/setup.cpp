@@ -13,6 +13,7 @@
 // diagonalisation, all others an explicit FP64 inverse of A[I_j, I_j].
 #include "setup.hpp"
 
+#include <algorithm>
 #include <functional>
 
 #include <cmath>
@@ -1069,6 +1070,55 @@ void cut_patch_records(HostLevel& L, bool dry) {
     L.cut_roff[j + 1] = L.cut_roff[j] + len;
   }
   L.n_rec = L.cut_roff[ncp];
+  // moment slots of the block-boundary ghost faces, and per colour the faces
+  // with their destination slots
+  uint64_t bnd_bits = 0;
+  for (int k = 0; k < d; ++k)
+    for (int u = 0; u < half; ++u) bnd_bits |= (1ull << ((k * 3 + 0) * half + u)) | (1ull << ((k * 3 + 2) * half + u));
+  L.cut_gboff.assign(ncp + 1, 0);
+  for (int64_t j = 0; j < ncp; ++j) L.cut_gboff[j + 1] = L.cut_gboff[j] + __builtin_popcountll(L.cut_gmask[j] & bnd_bits);
+  L.bf_start.assign(ncol + 1, 0);
+  L.bf_face.clear();
+  L.bf_dst.clear();
+  for (int col = 0; col < ncol; ++col) {
+    std::vector<std::pair<int, int>> fd;  // (face id, slot)
+    for (int j = L.cut_start[col]; j < L.cut_start[col + 1]; ++j) {
+      int v[3] = {0, 0, 0};
+      int64_t t = L.cut_vert[j];
+      for (int k = 0; k < d; ++k) {
+        v[k] = (int)(t % np);
+        t /= np;
+      }
+      int rank = 0;
+      for (int bit = 0; bit < 3 * d * half; ++bit) {
+        if (!((L.cut_gmask[j] >> bit) & 1ull) || !((bnd_bits >> bit) & 1ull)) continue;
+        const int u = bit % half, k = bit / half / 3, Lp = bit / half % 3;
+        int lo[3] = {0, 0, 0}, q = 0;
+        for (int kk = 0; kk < d; ++kk)
+          lo[kk] = (kk == k) ? v[kk] - 1 + Lp - 1 : v[kk] - 1 + ((u >> q++) & 1);
+        const int64_t cell = lo[0] + (int64_t)N * (lo[1] + (d == 3 ? (int64_t)N * lo[2] : 0));
+        const int fid = L.face_id[(size_t)cell * d + k];
+        if (fid < 0) throw std::logic_error("block-boundary ghost face without a face id");
+        fd.push_back({fid, L.cut_gboff[j] + rank});
+        ++rank;
+      }
+    }
+    std::sort(fd.begin(), fd.end());
+    for (size_t i = 0; i < fd.size();) {
+      L.bf_face.push_back(fd[i].first);
+      L.bf_dst.push_back(fd[i].second);
+      if (i + 1 < fd.size() && fd[i + 1].first == fd[i].first) {
+        if (i + 2 < fd.size() && fd[i + 2].first == fd[i].first)
+          throw std::logic_error("a ghost face read by three patches of one colour");
+        L.bf_dst.push_back(fd[i + 1].second);
+        i += 2;
+      } else {
+        L.bf_dst.push_back(-1);
+        i += 1;
+      }
+    }
+    L.bf_start[col + 1] = (int)L.bf_face.size();
+  }
   // work model of the pipelined kernel (replaces the entry-list kernel's):
   // flops 2 m^2 (packed solve) + 2 NB per row item + per ghost face of the
   // block p NT (2 (2p+1) + 2 NT) for its moments + 2p per ghost entry of a
@@ -1087,13 +1137,27 @@ void cut_patch_records(HostLevel& L, bool dry) {
       for (int j = L.cut_start[col]; j < L.cut_start[col + 1]; ++j) {
         const double m = L.cut_n[j], nit = L.cut_item_off[j + 1] - L.cut_item_off[j];
         const double nent = L.cut_fo[j + 1] - L.cut_fo[j];
-        const double nf = __builtin_popcountll(L.cut_gmask[j]);
         const double nbf = __builtin_popcountll(L.cut_gmask[j] & bnd_mask);
+        const double nf = __builtin_popcountll(L.cut_gmask[j]) - nbf;  // internal faces, formed in the block
         L.work_cut[col][0] += 2.0 * m * m + 2.0 * NB * nit + nf * p * NTf * (2.0 * (2 * p + 1) + 2.0 * NTf) +
                               2.0 * p * nent;
         L.work_cut[col][1] += m * (m + 1) / 2 + (double)rows[j] * NB + 2.0 * NCL + nbf * p * NTf + m;
-        L.work_cut[col][2] += 4.0 * m + nit + 4.0 * NCELL + 44.0;
+        L.work_cut[col][2] += 4.0 * m + nit + 4.0 * NCELL + 48.0;
       }
+    // the boundary-face moment launch of each colour: per face the jumps,
+    // the face mass and the coefficients; x of the two cells read, the
+    // moments written to each destination slot
+    for (int col = 0; col < ncol; ++col) {
+      const double flf = 2.0 * (2 * p + 1) * p * NTf + 2.0 * p * (p + 1) * NTf * (d - 1) + (double)p * NTf;
+      double fl = 0.0, sc = 0.0, ib = 0.0;
+      for (int i = L.bf_start[col]; i < L.bf_start[col + 1]; ++i) {
+        const int nd = (L.bf_dst[2 * i] >= 0) + (L.bf_dst[2 * i + 1] >= 0);
+        fl += flf;
+        sc += (2.0 * p + 1) * NTf + (double)p * NTf * nd;
+        ib += 16.0;
+      }
+      L.work_face[col] = {fl, sc, ib};
+    }
   }
   L.cut_maxrec.assign(ncol, 0);
   for (int col = 0; col < ncol; ++col)

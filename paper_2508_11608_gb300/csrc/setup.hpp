@@ -117,6 +117,14 @@ struct HostLevel {
   std::vector<int> cut_maxrec;    // per colour: longest record
   HostBlocks rec;
   int64_t n_rec = 0;              // rec.size() unless dry
+  // Moments of the ghost faces on the block's boundary planes (computed by a
+  // separate launch from the x before the colour step: the cell across such a
+  // face can hold DoFs of a same-colour patch): patch j reads them from
+  // slots cut_gboff[j] .. cut_gboff[j + 1] (one per set boundary bit of
+  // cut_gmask[j], in bit order; P (p+1)^(d-1) values each).  Per colour c the
+  // faces to compute are bf_face[bf_start[c] .. bf_start[c + 1]) (ghost-face
+  // ids) with their slots bf_dst[2 i], bf_dst[2 i + 1] (-1: none).
+  std::vector<int> cut_gboff, bf_start, bf_face, bf_dst;
   // algorithmic work per launch, used to report achieved FLOP/s and bytes:
   // per colour of the cut-patch solve and of the interior-patch step
   // {flops, scalars moved, index bytes moved}
