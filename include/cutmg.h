@@ -190,11 +190,13 @@ cf_status cf_set_precision(cf_problem* pb, int precision);
  * per patch, 2 = one block per patch.  family CF_VAR_CUT (cut-patch step,
  * 3D degree 2): 1 = each patch's record (packed inverse and cut-cell rows)
  * brought into shared memory by a TMA bulk copy (the automatic choice),
- * 2 = records read from global memory.  variant 0 restores the automatic
- * choice.  The next
+ * 2 = records read from global memory.  family CF_VAR_OPERATOR (operator
+ * rows of nodes whose cells are all uncut): 1 = element-matrix form, 2 =
+ * sum factorisation (the automatic choice in FP64).  variant 0 restores the
+ * automatic choice.  The next
  * launches use it; captured CUDA graphs of the handle are dropped.
  * CF_EINVAL for an unknown family or variant, or a host-only handle. */
-typedef enum { CF_VAR_INTERIOR = 1, CF_VAR_CUT = 2 } cf_variant_family;
+typedef enum { CF_VAR_INTERIOR = 1, CF_VAR_CUT = 2, CF_VAR_OPERATOR = 3 } cf_variant_family;
 cf_status cf_set_kernel_variant(cf_problem* pb, int family, int variant);
 
 /* Polls the cut-patch kernel makes on its TMA copy's mbarrier before it

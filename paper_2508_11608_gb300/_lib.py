@@ -15,7 +15,7 @@ CF_LS_SPHERE, CF_LS_PLANE, CF_LS_ELLIPSOID, CF_LS_TORUS, CF_LS_FLOWER, CF_LS_CAL
 CF_FP64, CF_MIXED = 0, 1
 CF_SMOOTHER_MVS, CF_SMOOTHER_CHEBYSHEV = 0, 1
 CF_K_CUT_SOLVE, CF_K_INTERIOR, CF_K_APPLY_BULK, CF_K_APPLY_BND, CF_K_FACE_MOMENTS = 1, 2, 3, 4, 5
-CF_VAR_INTERIOR, CF_VAR_CUT = 1, 2
+CF_VAR_INTERIOR, CF_VAR_CUT, CF_VAR_OPERATOR = 1, 2, 3
 
 EXPORTED = [
     "cf_setup", "cf_destroy", "cf_last_error", "cf_n_levels", "cf_n_dofs", "cf_level_n_dofs",

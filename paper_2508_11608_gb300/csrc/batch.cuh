@@ -241,40 +241,15 @@ __global__ void __launch_bounds__(128) kb_cut_pipe(const LvlDesc<DIM, P, T>* __r
   __shared__ PipeShared<DIM, P, T> sh;
   __shared__ __align__(8) uint64_t bar[2];
   if ((int)blockIdx.x >= total) return;
-  if (threadIdx.x == 0) {
-    mbar_init(&bar[0]);
-    mbar_init(&bar[1]);
-  }
-  __syncthreads();
-  uint32_t ph = 0;
-  int it = blockIdx.x, s = 0;
-  int i = find_inst(off, K, it);
-  int j = D[i].cut_start[colour] + it - off[i];
-  PipeMeta cur = pipe_meta(D[i].pl, j);
-  pipe_prefetch<DIM, P, T, NT>(D[i].pl, cur, j, stage[0], reinterpret_cast<T*>(psm), slot_bytes, &bar[0]);
-  for (; it < total; it += gridDim.x, s ^= 1) {
-    const int itn = it + (int)gridDim.x;
-    const bool more = itn < total;
-    int in_ = i, jn = j;
-    PipeMeta nxt = cur;
-    if (more) {
-      in_ = find_inst(off, K, itn);
-      jn = D[in_].cut_start[colour] + itn - off[in_];
-      nxt = pipe_meta(D[in_].pl, jn);
-      pipe_prefetch<DIM, P, T, NT>(D[in_].pl, nxt, jn, stage[s ^ 1], reinterpret_cast<T*>(psm + (s ^ 1) * slot_bytes),
-                                   slot_bytes, &bar[s ^ 1]);
-    }
-    const bool tma = pipe_tma<T>(cur, slot_bytes);
-    bool ok;
-    if (more)
-      ok = pipe_wait<true>(tma, &bar[s], ph, s, kTmaSpin, err);
-    else
-      ok = pipe_wait<false>(tma, &bar[s], ph, s, kTmaSpin, err);
-    if (__syncthreads_and(ok)) pipe_compute<DIM, P, T, NT>(D[i].pl, stage[s], sh, D[i].pl.op.Kref);
-    cur = nxt;
-    i = in_;
-    j = jn;
-  }
+  pipe_loop<DIM, P, T, NT>(
+      blockIdx.x, gridDim.x, total,
+      [&](int it, const PipeLevel<T>*& lv, int& j) {
+        const int i = find_inst(off, K, it);
+        lv = &D[i].pl;
+        j = D[i].cut_start[colour] + it - off[i];
+      },
+      [&](const PipeLevel<T>* lv) -> const T* { return lv->op.Kref; }, psm, slot_bytes, stage, sh, bar, kTmaSpin,
+      err);
 }
 
 // apply: items are bulk positions (mode 0) or boundary nodes (mode 1)
@@ -474,6 +449,8 @@ class BatchGroup final : public BatchGroupBase {
     rebuild_lists();
   }
   ~BatchGroup() override {
+    for (auto& g : graphs_) if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (cap_) cudaStreamDestroy(cap_);
     if (host_sc_) cudaFreeHost(host_sc_);
   }
 
@@ -491,6 +468,7 @@ class BatchGroup final : public BatchGroupBase {
   void set_tile(int w, int b) override {
     tile_w_ = (w == 2 || w == 8) ? w : 4;
     tile_b_ = b > 0 ? b : 4;
+    ++version_;
   }
 
   void autotune(cudaStream_t s) override {
@@ -524,6 +502,7 @@ class BatchGroup final : public BatchGroupBase {
       }
     tile_w_ = best_w_;
     tile_b_ = best_b_;
+    ++version_;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
   }
@@ -566,11 +545,13 @@ class BatchGroup final : public BatchGroupBase {
   }
 
   void half_a(cudaStream_t s) override {
-    apply_fine(s);
-    dot_all(3, 1, s);  // pq
-    kb_cg_xr<<<grid(tot_vec_, 256), 256, 0, s>>>(vec_cg_, sc_, off_vec_, K_, tot_vec_);
-    count("batched cg update x r");
-    dot_all(4, 3, s);  // rr
+    run_graph(0, s, [&](cudaStream_t cs) {
+      apply_fine(cs);
+      dot_all(3, 1, cs);  // pq
+      kb_cg_xr<<<grid(tot_vec_, 256), 256, 0, cs>>>(vec_cg_, sc_, off_vec_, K_, tot_vec_);
+      count("batched cg update x r");
+      dot_all(4, 3, cs);  // rr
+    });
   }
 
   void read_rr(double* host_rr, cudaStream_t s) override {
@@ -595,12 +576,14 @@ class BatchGroup final : public BatchGroupBase {
   }
 
   void half_b(int prec, cudaStream_t s) override {
-    precondition(prec, s);
-    dot_all(2, 2, s);  // rz_new
-    kb_cg_p<<<grid(tot_vec_, 256), 256, 0, s>>>(vec_cgz_, sc_, off_vec_, K_, tot_vec_);
-    count("batched cg update p");
-    kb_copy_scalar<<<(nact_ + 255) / 256, 256, 0, s>>>(sc_, act_list_d_, nact_, 0, 2);
-    count("batched cg scalar");
+    run_graph(1 + prec, s, [&](cudaStream_t cs) {
+      precondition(prec, cs);
+      dot_all(2, 2, cs);  // rz_new
+      kb_cg_p<<<grid(tot_vec_, 256), 256, 0, cs>>>(vec_cgz_, sc_, off_vec_, K_, tot_vec_);
+      count("batched cg update p");
+      kb_copy_scalar<<<(nact_ + 255) / 256, 256, 0, cs>>>(sc_, act_list_d_, nact_, 0, 2);
+      count("batched cg scalar");
+    });
   }
 
   void finish(double* const* x, BatchInfo* info, cudaStream_t s) override {
@@ -626,6 +609,48 @@ class BatchGroup final : public BatchGroupBase {
   int K_ = 0, depth_ = 0, n_c_ = 2, dev_ = 0, sms_ = 152;
   DevPool pool_;
   int64_t launches_ = 0;
+  // CUDA graphs of the two halves of a CG iteration (slot 0: q = A p .. (r, r);
+  // 1 + precision: z = B r .. p), captured for one version of the work lists
+  // (rebuild_lists starts a new version) and replayed while it holds
+  struct Graph {
+    cudaGraphExec_t exec = nullptr;
+    int version = -1;
+    int64_t launches = 0;
+  };
+  Graph graphs_[3];
+  int version_ = 0;
+  cudaStream_t cap_ = nullptr;
+  template <class F>
+  void run_graph(int slot, cudaStream_t s, F&& body) {
+    Graph& g = graphs_[slot];
+    if (!g.exec || g.version != version_) {
+      if (!cap_) CUTMG_CUDA(cudaStreamCreateWithFlags(&cap_, cudaStreamNonBlocking));
+      if (g.exec) {
+        cudaGraphExecDestroy(g.exec);
+        g.exec = nullptr;
+      }
+      const int64_t l0 = launches_;
+      cudaGraph_t gr = nullptr;
+      CUTMG_CUDA(cudaStreamBeginCapture(cap_, cudaStreamCaptureModeThreadLocal));
+      try {
+        body(cap_);
+      } catch (...) {
+        cudaStreamEndCapture(cap_, &gr);
+        if (gr) cudaGraphDestroy(gr);
+        launches_ = l0;
+        throw;
+      }
+      CUTMG_CUDA(cudaStreamEndCapture(cap_, &gr));
+      cudaError_t e = cudaGraphInstantiate(&g.exec, gr, 0);
+      cudaGraphDestroy(gr);
+      if (e != cudaSuccess) throw CudaError(std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+      g.version = version_;
+      g.launches = launches_ - l0;
+      launches_ = l0;
+    }
+    CUTMG_CUDA(cudaGraphLaunch(g.exec, s));
+    launches_ += g.launches;
+  }
   int tile_w_ = 4, tile_b_ = 4, best_w_ = 4, best_b_ = 4;
   std::vector<int> act_, its_;
   std::vector<double> bn_, rel_;
@@ -780,6 +805,7 @@ class BatchGroup final : public BatchGroupBase {
   }
 
   void rebuild_lists() {
+    ++version_;  // captured graphs refer to the old lists
     // (device memory of old lists is kept in the pool; rebuilds are rare)
     w_cart_.assign(depth_, std::vector<Work>(NCOL));
     w_tile_.assign(depth_, std::vector<Work>(NCOL));

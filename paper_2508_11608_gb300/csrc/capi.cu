@@ -241,7 +241,8 @@ size_t cutmg_estimate_hierarchy_bytes(const Hierarchy& H) {
       size_t words = 0;
       for (size_t j = 0; j < ncp; ++j) words += (size_t)(L.cut_item_off[j + 1] - L.cut_item_off[j] + 3) / 4;
       tot += 4 * L.members.size() + 4 * words + 8 * ncp + 4 * L.cut_pk.size() + 8 * L.cut_gmask.size() +
-             8 * L.cut_roff.size() + 4 * L.cut_gboff.size() + 4 * L.bf_face.size() + 4 * L.bf_dst.size();
+             8 * L.cut_roff.size() + 4 * L.cut_gboff.size() + 4 * L.bf_face.size() + 4 * L.bf_dst.size() +
+             4 * L.cut_geoff.size() + 2 * L.cut_gent.size();
     }
     if (l > 0) {  // interior-patch dense map: transposed copy and the tensor-core operand (FP32 only)
       size_t nc = 1, ni = 1;

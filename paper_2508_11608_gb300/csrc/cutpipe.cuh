@@ -9,8 +9,8 @@
 //   * the DoF list, the row items and the cell kinds (cp.async),
 //   * its record: the explicit inverse packed by rows of its lower triangle
 //     and the rows of the cut-cell matrices its items use, one contiguous
-//     run brought into shared memory by one TMA bulk copy (cp.async.bulk,
-//     completion on an mbarrier),
+//     run, and its ghost-entry list; both by TMA bulk copies (cp.async.bulk)
+//     completing on one mbarrier,
 //   * the moments of the ghost faces on the boundary planes of its block
 //     (cp.async from its moment slots).
 // Every ghost face in the row of a patch DoF is a face of an active cell that
@@ -25,6 +25,11 @@
 // therefore computed before the colour step by a separate launch
 // (k_face_moments_to), like every moment of the additive-within-a-colour
 // step (Sec. 2.3): the patch sees the x from before the colour step only.
+//
+// The ghost-entry list of a patch (built at setup) holds, for each DoF row,
+// the (face, node along the normal, tangential node) triples of the ghost
+// faces whose stencil contains the DoF; the rows and the local solve split
+// each DoF over 4 lanes, combined by shuffles in a fixed order.
 #pragma once
 
 #include "kernels.cuh"
@@ -44,7 +49,15 @@ struct PipeGeo {
   static constexpr int NBF = DIM * 2 * HALF;      // faces on its boundary planes
   static constexpr int HALO = NBF * P * NT;       // the moments of those
   static constexpr int ITEMW = (NCELL * NB + 3) / 4;  // 32-bit words of the item list
+  static constexpr int GCAP = 1024;               // ghost-entry list entries staged (longer: global)
+  static constexpr int LANES = 4;                 // threads per DoF row in rows and solve
 };
+
+// ghost entry: bit of the face in the block mask (6 bits), node along the
+// normal (3 bits), tangential node (7 bits)
+__host__ __device__ constexpr uint16_t ghost_entry(int bit, int i, int t) {
+  return (uint16_t)(bit | (i << 6) | (t << 9));
+}
 
 // device arrays of one level for the pipelined cut kernel
 template <typename T>
@@ -65,6 +78,8 @@ struct PipeLevel {
   const T* rec;             // records
   const int* gboff;         // first boundary-face moment slot of each patch
   const T* Gb;              // boundary-face moment slots, P (p+1)^(d-1) values each
+  const int* geoff;         // ghost-entry lists: [geoff[j], geoff[j + 1]) in gent (16-byte aligned)
+  const uint16_t* gent;     // per patch: m + 1 row offsets, then the entries
 };
 
 // bits of the block-boundary planes (0 and 2) in a ghost-face mask
@@ -86,9 +101,11 @@ struct PipeStage {
   int mem[G::NCL];
   uint32_t item[G::ITEMW];
   int pk[G::NCELL];
+  __align__(16) uint16_t gl[G::GCAP];
   uint64_t gmask;
-  const T* recp;  // the record: the stage's slot or global memory
-  int vert, m, nit, tma;
+  const T* recp;         // the record: the stage's slot or global memory
+  const uint16_t* glp;   // the ghost-entry list: gl or global memory
+  int vert, m, nit;
 };
 
 template <int DIM, int P, typename T>
@@ -102,7 +119,7 @@ struct PipeShared {
 };
 
 struct PipeMeta {
-  int vert, m, mo, io, nit, gb;
+  int vert, m, mo, io, nit, gb, g0, g1;
   int64_t r0, r1;
   uint64_t gmask;
 };
@@ -119,18 +136,42 @@ __device__ __forceinline__ PipeMeta pipe_meta(const PipeLevel<T>& L, int j) {
   t.r1 = L.roff[j + 1];
   t.gmask = L.gmask[j];
   t.gb = L.gboff[j];
+  t.g0 = L.geoff[j];
+  t.g1 = L.geoff[j + 1];
   return t;
 }
 
-// whether patch M's record goes through a shared-memory slot of slot_bytes
+// whether patch M's record goes through a shared-memory slot of slot_bytes,
+// and whether its ghost-entry list goes into the stage
 template <typename T>
 __device__ __forceinline__ bool pipe_tma(const PipeMeta& M, int slot_bytes) {
   const int64_t len = M.r1 - M.r0;
   return len > 0 && (size_t)len * sizeof(T) <= (size_t)slot_bytes;
 }
+template <int DIM, int P>
+__device__ __forceinline__ bool pipe_gl_tma(const PipeMeta& M) {
+  return M.g1 - M.g0 <= PipeGeo<DIM, P>::GCAP;
+}
+
+// one expected-bytes arrival on the mbarrier (always made, also for zero
+// bytes, so that every stage's phase completes once per prefetch), then the
+// bulk copies that complete it
+__device__ __forceinline__ void mbar_expect(uint64_t* bar, uint32_t bytes) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
 
 // Issue every load of patch j into stage `st` (cp.async, one group per call;
-// the record by TMA on `bar` when it fits `slot_bytes`).  All threads call it.
+// the record when it fits `slot_bytes` and the ghost-entry list when it
+// fits the stage, by TMA on `bar`).  All threads call it.
 template <int DIM, int P, typename T, int NT>
 __device__ __forceinline__ void pipe_prefetch(const PipeLevel<T>& L, const PipeMeta& M, int j,
                                               PipeStage<DIM, P, T>& st, T* slot, int slot_bytes, uint64_t* bar) {
@@ -146,15 +187,19 @@ __device__ __forceinline__ void pipe_prefetch(const PipeLevel<T>& L, const PipeM
       q /= np;
     }
   }
-  const bool tma = pipe_tma<T>(M, slot_bytes);
+  const bool tma = pipe_tma<T>(M, slot_bytes), gtma = pipe_gl_tma<DIM, P>(M);
   if (tid == 0) {
     st.vert = M.vert;
     st.m = M.m;
     st.nit = M.nit;
-    st.tma = tma;
     st.gmask = M.gmask;
     st.recp = tma ? slot : L.rec + M.r0;
-    if (tma) tma_load_1d(slot, L.rec + M.r0, (uint32_t)((M.r1 - M.r0) * sizeof(T)), bar);
+    st.glp = gtma ? st.gl : L.gent + M.g0;
+    const uint32_t rb = tma ? (uint32_t)((M.r1 - M.r0) * sizeof(T)) : 0u;
+    const uint32_t gb = gtma ? (uint32_t)((M.g1 - M.g0) * sizeof(uint16_t)) : 0u;
+    mbar_expect(bar, rb + gb);
+    if (rb) bulk_copy(slot, L.rec + M.r0, rb, bar);
+    if (gb) bulk_copy(st.gl, L.gent + M.g0, gb, bar);
   }
   for (int e = tid; e < G::NCL; e += NT) {
     int u = e, c[3] = {0, 0, 0};
@@ -205,13 +250,22 @@ __device__ __forceinline__ T pipe_x(const PipeStage<DIM, P, T>& st, int k, int u
   return st.x[o];
 }
 
+// sum over the 4 lanes of a DoF row (lanes 4k .. 4k+3 of a warp), the same
+// order on every lane
+template <typename T>
+__device__ __forceinline__ T lane4_sum(T v) {
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  v += __shfl_xor_sync(0xffffffffu, v, 2);
+  return v;
+}
+
 // One patch from a filled stage: ghost-face moments, residual rows, local
 // solve, x updated in place.  Kref: the level's uncut element matrix.
 template <int DIM, int P, typename T, int NT>
 __device__ __forceinline__ void pipe_compute(const PipeLevel<T>& L, const PipeStage<DIM, P, T>& st,
                                              PipeShared<DIM, P, T>& sh, const T* __restrict__ Kref) {
   using G = PipeGeo<DIM, P>;
-  constexpr int C = G::C, NB = G::NB, NTF = G::NT;
+  constexpr int C = G::C, NB = G::NB, NTF = G::NT, LN = G::LANES, ROWS = NT / LN;
   const int tid = threadIdx.x, m = st.m, n = L.op.n, np = L.op.N + 1;
   constexpr uint64_t bnd = pipe_bnd_bits<DIM, P>();
   const uint64_t gm = st.gmask, gint = gm & ~bnd, gbnd = gm & bnd;
@@ -270,68 +324,51 @@ __device__ __forceinline__ void pipe_compute(const PipeLevel<T>& L, const PipeSt
     sh.Gm[fi][mm][t] = L.op.coef[mm] * acc;
   }
   __syncthreads();
-  // residual of the own rows: cell parts in cell order, then the ghost faces
-  for (int e = tid; e < m; e += NT) {
-    int o[3] = {0, 0, 0}, u = st.mem[e];
-#pragma unroll
-    for (int k = 0; k < DIM; ++k) {
-      o[k] = u % C;
-      u /= C;
-    }
+  // residual of the own rows, LN lanes per DoF: lane 0 the cell parts in
+  // cell order, every lane a strided share of the row's ghost entries
+  const uint16_t* gl = st.glp;
+  const int lane = tid % LN;
+  for (int e0 = 0; e0 < m; e0 += ROWS) {
+    const int e = e0 + tid / LN;
     T acc = T(0);
+    if (e < m) {
+      if (lane == 0) {
+        int o[3] = {0, 0, 0}, u = st.mem[e];
 #pragma unroll
-    for (int sc = 0; sc < G::NCELL; ++sc) {
-      int jj = 0, jst = 1;
-      bool in = st.pk[sc] != -2;
-#pragma unroll
-      for (int k = 0; k < DIM; ++k) {
-        const int a = o[k] - P * ((sc >> k) & 1);
-        if (a < 0 || a > P) in = false;
-        jj += a * jst;
-        jst *= (P + 1);
-      }
-      if (in) acc += sh.part[sc][jj];
-    }
-    T fac = T(0);
-#pragma unroll
-    for (int k = 0; k < DIM; ++k) {
-      // planes of the faces of the node's cell layers along k
-      const int ok = o[k], lay = ok / P, onp = ok - lay * P == 0;
-      const int Llo = onp ? lay - 1 : lay, Lhi = lay + 1;
-      for (int Lp = Llo < 0 ? 0 : Llo; Lp <= (Lhi > 2 ? 2 : Lhi); ++Lp) {
-        const int i = ok - P * (Lp - 1);
-        // tangential cells of the block plane containing the node
-        int ulo[2] = {0, 0}, uhi[2] = {0, 0}, tj[2] = {0, 0}, q = 0;
-#pragma unroll
-        for (int kk = 0; kk < DIM; ++kk) {
-          if (kk == k) continue;
-          const int oj = o[kk], cj = oj / P, on = oj - cj * P == 0;
-          ulo[q] = on ? cj - 1 : cj;
-          uhi[q] = cj;
-          if (ulo[q] < 0) ulo[q] = 0;
-          if (uhi[q] > 1) uhi[q] = 1;
-          tj[q] = oj;
-          ++q;
+        for (int k = 0; k < DIM; ++k) {
+          o[k] = u % C;
+          u /= C;
         }
-        for (int u1 = (DIM == 3 ? ulo[1] : 0); u1 <= (DIM == 3 ? uhi[1] : 0); ++u1)
-          for (int u0 = ulo[0]; u0 <= uhi[0]; ++u0) {
-            const int uu = u0 + 2 * u1;
-            const int bit = (k * 3 + Lp) * G::HALF + uu;
-            if (!((gm >> bit) & 1ull)) continue;
-            const uint64_t below = (1ull << bit) - 1ull;
-            const int t = (tj[0] - P * u0) + (DIM == 3 ? (P + 1) * (tj[1] - P * u1) : 0);
-            const T* g = Lp == 1 ? &sh.Gm[__popcll(gint & below)][0][0]
-                                 : &st.halo[__popcll(gbnd & below) * P * NTF];
 #pragma unroll
-            for (int mm = 0; mm < P; ++mm) fac += L.op.dvec[mm][i] * g[mm * NTF + t];
+        for (int sc = 0; sc < G::NCELL; ++sc) {
+          int jj = 0, jst = 1;
+          bool in = st.pk[sc] != -2;
+#pragma unroll
+          for (int k = 0; k < DIM; ++k) {
+            const int a = o[k] - P * ((sc >> k) & 1);
+            if (a < 0 || a > P) in = false;
+            jj += a * jst;
+            jst *= (P + 1);
           }
+          if (in) acc += sh.part[sc][jj];
+        }
+      }
+      for (int q = gl[e] + lane; q < gl[e + 1]; q += LN) {
+        const int en = gl[m + 1 + q], bit = en & 63, i = (en >> 6) & 7, t = en >> 9;
+        const uint64_t below = (1ull << bit) - 1ull;
+        const T* g = ((bnd >> bit) & 1ull) ? &st.halo[__popcll(gbnd & below) * P * NTF]
+                                            : &sh.Gm[__popcll(gint & below)][0][0];
+#pragma unroll
+        for (int mm = 0; mm < P; ++mm) acc += L.op.dvec[mm][i] * g[mm * NTF + t];
       }
     }
-    sh.r[e] = st.b[st.mem[e]] - (acc + fac);
+    acc = lane4_sum(acc);
+    if (e < m && lane == 0) sh.r[e] = st.b[st.mem[e]] - acc;
   }
   __syncthreads();
-  // delta = A_j^{-1} r from the packed lower triangle; the new value from
-  // the staged closure value (no other patch of the colour writes this DoF)
+  // delta = A_j^{-1} r from the packed lower triangle, LN lanes per row; the
+  // new value from the staged closure value (no other patch of the colour
+  // writes this DoF)
   const T* Ai = st.recp;
   int v[3] = {0, 0, 0};
   {
@@ -342,52 +379,103 @@ __device__ __forceinline__ void pipe_compute(const PipeLevel<T>& L, const PipeSt
       q /= np;
     }
   }
-  for (int e = tid; e < m; e += NT) {
-    const T* Re = Ai + e * (e + 1) / 2;
-    T a0 = T(0), a1 = T(0);
-    int c = 0;
-    for (; c + 1 <= e; c += 2) {
-      a0 += Re[c] * sh.r[c];
-      a1 += Re[c + 1] * sh.r[c + 1];
+  for (int e0 = 0; e0 < m; e0 += ROWS) {
+    const int e = e0 + tid / LN;
+    T acc = T(0);
+    if (e < m) {
+      const T* Re = Ai + e * (e + 1) / 2;
+      int c = lane;
+      for (; c <= e; c += LN) acc += Re[c] * sh.r[c];
+      for (; c < m; c += LN) acc += Ai[c * (c + 1) / 2 + e] * sh.r[c];
     }
-    if (c <= e) {
-      a0 += Re[c] * sh.r[c];
-      ++c;
-    }
-    for (; c < m; ++c) a1 += Ai[c * (c + 1) / 2 + e] * sh.r[c];
-    int u = st.mem[e], lc[3] = {0, 0, 0};
+    acc = lane4_sum(acc);
+    if (e < m && lane == 0) {
+      int u = st.mem[e], lc[3] = {0, 0, 0};
 #pragma unroll
-    for (int k = 0; k < DIM; ++k) {
-      lc[k] = P * (v[k] - 1) + u % C;
-      u /= C;
+      for (int k = 0; k < DIM; ++k) {
+        lc[k] = P * (v[k] - 1) + u % C;
+        u /= C;
+      }
+      L.x[lat_index<DIM>(lc, n)] = st.x[st.mem[e]] + acc;
     }
-    L.x[lat_index<DIM>(lc, n)] = st.x[st.mem[e]] + (a0 + a1);
   }
   __syncthreads();
 }
 
-// waits for stage `st`'s loads (the newer group of cp.asyncs may stay in
-// flight) and, if its record came by TMA, for the mbarrier; false when the
-// bounded wait ran out (the copy is then drained within kTmaSpin polls)
-// (ph bit s: the parity of stage s's next mbarrier phase, flipped here)
+// waits for stage s's loads (the newer group of cp.asyncs may stay in flight)
+// and for its mbarrier (ph bit s: the parity of stage s's next phase, flipped
+// here); false when the bounded wait ran out (the copies are then drained
+// within kTmaSpin polls)
 template <bool NEWER_PENDING>
-__device__ __forceinline__ bool pipe_wait(bool tma, uint64_t* bar, uint32_t& ph, int s, int spin, int* err) {
+__device__ __forceinline__ bool pipe_wait(uint64_t* bar, uint32_t& ph, int s, int spin, int* err) {
   if (NEWER_PENDING)
     asm volatile("cp.async.wait_group 1;" ::: "memory");
   else
     asm volatile("cp.async.wait_group 0;" ::: "memory");
-  bool ok = true;
-  if (tma) {
-    const uint32_t parity = (ph >> s) & 1u;
-    ok = mbar_wait(bar, parity, spin);
-    if (!ok) {
-      atomicExch(err, 1);
-      mbar_wait(bar, parity, kTmaSpin);
-    }
-    ph ^= 1u << s;
+  const uint32_t parity = (ph >> s) & 1u;
+  bool ok = mbar_wait(bar, parity, spin);
+  if (!ok) {
+    atomicExch(err, 1);
+    mbar_wait(bar, parity, kTmaSpin);
   }
+  ph ^= 1u << s;
   __syncthreads();
   return ok;
+}
+
+// The pipelined loop of one block over the work items it, it + step, ..
+// below total.  locate(item, level, patch) gives an item's level descriptor
+// and patch; kref(level) its uncut element matrix.  Metadata run two items
+// ahead, data one item ahead.
+template <int DIM, int P, typename T, int NT, class Locate, class Kref>
+__device__ __forceinline__ void pipe_loop(int it, int step, int total, Locate&& locate, Kref&& kref,
+                                          unsigned char* psm, int slot_bytes, PipeStage<DIM, P, T>* stage,
+                                          PipeShared<DIM, P, T>& sh, uint64_t* bar, int spin, int* err) {
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0]);
+    mbar_init(&bar[1]);
+  }
+  __syncthreads();
+  uint32_t ph = 0;
+  int s = 0;
+  const PipeLevel<T>* Lc;
+  int jc;
+  locate(it, Lc, jc);
+  PipeMeta cur = pipe_meta(*Lc, jc);
+  const PipeLevel<T>* Ln = Lc;
+  int jn = jc;
+  PipeMeta nxt = cur;
+  if (it + step < total) {
+    locate(it + step, Ln, jn);
+    nxt = pipe_meta(*Ln, jn);
+  }
+  pipe_prefetch<DIM, P, T, NT>(*Lc, cur, jc, stage[0], reinterpret_cast<T*>(psm), slot_bytes, &bar[0]);
+  for (; it < total; it += step, s ^= 1) {
+    const bool more = it + step < total;
+    // metadata of the item after next
+    const PipeLevel<T>* L2 = Ln;
+    int j2 = jn;
+    PipeMeta nn = nxt;
+    if (it + 2 * step < total) {
+      locate(it + 2 * step, L2, j2);
+      nn = pipe_meta(*L2, j2);
+    }
+    if (more)
+      pipe_prefetch<DIM, P, T, NT>(*Ln, nxt, jn, stage[s ^ 1], reinterpret_cast<T*>(psm + (s ^ 1) * slot_bytes),
+                                   slot_bytes, &bar[s ^ 1]);
+    bool ok;
+    if (more)
+      ok = pipe_wait<true>(&bar[s], ph, s, spin, err);
+    else
+      ok = pipe_wait<false>(&bar[s], ph, s, spin, err);
+    if (__syncthreads_and(ok)) pipe_compute<DIM, P, T, NT>(*Lc, stage[s], sh, kref(Lc));
+    Lc = Ln;
+    jc = jn;
+    cur = nxt;
+    Ln = L2;
+    jn = j2;
+    nxt = nn;
+  }
 }
 
 // One colour step: patches j0 .. j0 + npatch - 1, block b takes b, b + grid,
@@ -402,34 +490,18 @@ __global__ void __launch_bounds__(128) k_cut_pipe(PipeLevel<T> L, int j0, int np
   __shared__ PipeShared<DIM, P, T> sh;
   __shared__ __align__(16) T sK[G::NB * G::NB];
   __shared__ __align__(8) uint64_t bar[2];
+  __shared__ PipeLevel<T> sL;
   if ((int)blockIdx.x >= npatch) return;
   for (int i = threadIdx.x; i < G::NB * G::NB; i += NT) sK[i] = L.op.Kref[i];
-  if (threadIdx.x == 0) {
-    mbar_init(&bar[0]);
-    mbar_init(&bar[1]);
-  }
-  __syncthreads();
-  uint32_t ph = 0;
-  int j = blockIdx.x, s = 0;
-  PipeMeta cur = pipe_meta(L, j0 + j);
-  pipe_prefetch<DIM, P, T, NT>(L, cur, j0 + j, stage[0], reinterpret_cast<T*>(psm), slot_bytes, &bar[0]);
-  for (; j < npatch; j += gridDim.x, s ^= 1) {
-    const int jn = j + (int)gridDim.x;
-    const bool more = jn < npatch;
-    if (more) {
-      const PipeMeta nxt = pipe_meta(L, j0 + jn);
-      pipe_prefetch<DIM, P, T, NT>(L, nxt, j0 + jn, stage[s ^ 1], reinterpret_cast<T*>(psm + (s ^ 1) * slot_bytes),
-                                   slot_bytes, &bar[s ^ 1]);
-    }
-    const bool tma = pipe_tma<T>(cur, slot_bytes);
-    bool ok;
-    if (more)
-      ok = pipe_wait<true>(tma, &bar[s], ph, s, spin, err);
-    else
-      ok = pipe_wait<false>(tma, &bar[s], ph, s, spin, err);
-    if (__syncthreads_and(ok)) pipe_compute<DIM, P, T, NT>(L, stage[s], sh, sK);
-    if (more) cur = pipe_meta(L, j0 + jn);
-  }
+  if (threadIdx.x == 0) sL = L;  // the level's arrays and tables, read by every thread
+  const PipeLevel<T>* Lp = &sL;
+  pipe_loop<DIM, P, T, NT>(
+      blockIdx.x, gridDim.x, npatch,
+      [&](int it, const PipeLevel<T>*& lv, int& j) {
+        lv = Lp;
+        j = j0 + it;
+      },
+      [&](const PipeLevel<T>*) -> const T* { return sK; }, psm, slot_bytes, stage, sh, bar, spin, err);
 }
 
 }  // namespace cutmg

@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <array>
 #include <map>
 #include <memory>
 #include <tuple>
@@ -18,6 +19,7 @@
 
 #include "cutpipe.cuh"
 #include "engine_api.hpp"
+#include "sumfact.cuh"
 #include "kernels.cuh"
 #include "setup.hpp"
 
@@ -162,6 +164,9 @@ class Engine final : public EngineBase {
     int nbulk;
     int* bnd;
     int nbnd;
+    int* sf_tiles = nullptr;     // sum-factorised operator: tiles of bulk positions
+    uint32_t* sf_masks = nullptr;
+    int nsf = 0;
     int* mnode;
     int* faces;
     int nfaces;
@@ -195,6 +200,8 @@ class Engine final : public EngineBase {
     int64_t* proff = nullptr;
     std::vector<int> cut_maxrec;
     int* gboff = nullptr;     // boundary-face moment slots per patch
+    int* geoff = nullptr;     // ghost-entry lists per patch
+    uint16_t* gent = nullptr;
     int* bf_face = nullptr;   // per colour: block-boundary ghost faces to compute
     int* bf_dst = nullptr;    // and their two destination slots
     std::vector<int> bf_start;
@@ -208,6 +215,7 @@ class Engine final : public EngineBase {
   struct Typed {  // per-precision level data and work vectors
     OpArgs<T> op;
     FdArgs<T, P> fd;
+    SfArgs<T> sf;
     T* inv;
     T* pro_w;
     T* res_w;
@@ -245,6 +253,10 @@ class Engine final : public EngineBase {
     err_ = pool_.alloc<int>(1);
     CUTMG_CUDA(cudaFuncSetAttribute(k_smooth_tc<DIM, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     TcGeo<DIM, P>::SMEM));
+    CUTMG_CUDA(cudaFuncSetAttribute(k_apply_sf<DIM, P, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    SfGeo<DIM, P>::ELEMS * (int)sizeof(double)));
+    CUTMG_CUDA(cudaFuncSetAttribute(k_apply_sf<DIM, P, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    SfGeo<DIM, P>::ELEMS * (int)sizeof(float)));
     if (!kWarpCut) {
       CUTMG_CUDA(cudaFuncSetAttribute(k_cut_pipe<DIM, P, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       2 * kRecSlotMax));
@@ -286,8 +298,11 @@ class Engine final : public EngineBase {
     } else if (family == 2) {
       if (variant < 0 || variant > 2) throw std::invalid_argument("cut variant must be 0..2");
       var_cut_ = variant;
+    } else if (family == 3) {
+      if (variant < 0 || variant > 2) throw std::invalid_argument("operator variant must be 0..2");
+      var_op_ = variant;
     } else {
-      throw std::invalid_argument("kernel family must be 1 (interior) or 2 (cut)");
+      throw std::invalid_argument("kernel family must be 1 (interior), 2 (cut) or 3 (operator)");
     }
     drop_graphs();
   }
@@ -760,6 +775,8 @@ class Engine final : public EngineBase {
     L.rec = D.rec;
     L.gboff = c.gboff;
     L.Gb = D.Gb;
+    L.geoff = c.geoff;
+    L.gent = c.gent;
     return L;
   }
  private:
@@ -797,7 +814,13 @@ class Engine final : public EngineBase {
   cudaStream_t cap_ = nullptr;
   bool use_graphs_ = true;
 
-  int var_int_ = 0, var_cut_ = 0;  // forced launch variants (0: automatic)
+  int var_int_ = 0, var_cut_ = 0, var_op_ = 0;  // forced launch variants (0: automatic)
+  // operator on bulk positions: 1 element-matrix form, 2 sum-factorised
+  // (automatic: sum-factorised in FP64, where the flop count sets the time)
+  template <typename T>
+  bool use_sumfact() const {
+    return var_op_ == 2 || (var_op_ == 0 && sizeof(T) == 8);
+  }
   int spin_ = kTmaSpin;            // polls of the cut kernel's first wait on its TMA copy
 
   void drop_graphs() {
@@ -893,6 +916,18 @@ class Engine final : public EngineBase {
       for (int j = 0; j < M; ++j) D.fd.S[i][j] = (T)h.S[i * M + j];
       D.fd.lam[i] = (T)h.lam[i];
     }
+    // assembled 1D rows by residue (column i - p + s at tap s) from the
+    // two-cell rows: residue 0 = the middle row, residue r = row r of cell 0
+    for (int r = 0; r < 3; ++r)
+      for (int t = 0; t < 7; ++t) D.sf.Mrow[r][t] = D.sf.Krow[r][t] = T(0);
+    for (int r = 0; r < P; ++r) {
+      const int row = r == 0 ? P - 1 : r - 1, sh = r == 0 ? 0 : P - r;
+      for (int t = 0; t <= 2 * P; ++t) {
+        if (t + sh > 2 * P) continue;
+        D.sf.Mrow[r][t + sh] = (T)h.Mr[row * C + t];
+        D.sf.Krow[r][t + sh] = (T)h.Kr[row * C + t];
+      }
+    }
     {
       using G = DenseGeo<DIM, P>;
       std::vector<float> wt((size_t)G::NC * G::NR4, 0.f);
@@ -958,6 +993,41 @@ class Engine final : public EngineBase {
     c.nbulk = (int)h.bulk_pos.size();
     c.bnd = pool_.upload<int>(h.bnd_node);
     c.nbnd = (int)h.bnd_node.size();
+    {
+      // tiles of the sum-factorised operator: the bulk positions grouped by
+      // the tile of SfGeo positions that contains them
+      using SG = SfGeo<DIM, P>;
+      const int np = h.N + 1;
+      std::map<int64_t, std::array<uint32_t, SG::MASKW>> tm;
+      for (int q : h.bulk_pos) {
+        int a[3] = {0, 0, 0}, t = q;
+        for (int k = 0; k < DIM; ++k) {
+          a[k] = t % np;
+          t /= np;
+        }
+        const int T3[3] = {SG::TX, SG::TY, SG::TZ};
+        int ti[3] = {0, 0, 0}, loc[3] = {0, 0, 0};
+        for (int k = 0; k < DIM; ++k) {
+          ti[k] = (a[k] - 1) / T3[k];
+          loc[k] = (a[k] - 1) - ti[k] * T3[k];
+        }
+        const int64_t key = (int64_t)(1 + ti[0] * SG::TX) +
+                            (int64_t)np * ((1 + ti[1] * SG::TY) + (int64_t)np * (DIM == 3 ? 1 + ti[2] * SG::TZ : 0));
+        const int bit = loc[0] + SG::TX * (loc[1] + SG::TY * loc[2]);
+        auto it = tm.find(key);
+        if (it == tm.end()) it = tm.emplace(key, std::array<uint32_t, SG::MASKW>{}).first;
+        it->second[bit / 32] |= 1u << (bit % 32);
+      }
+      std::vector<int> tiles;
+      std::vector<uint32_t> masks;
+      for (auto& kv : tm) {
+        tiles.push_back((int)kv.first);
+        masks.insert(masks.end(), kv.second.begin(), kv.second.end());
+      }
+      c.nsf = (int)tiles.size();
+      c.sf_tiles = pool_.upload<int>(tiles);
+      c.sf_masks = pool_.upload<uint32_t>(masks);
+    }
     c.faces = pool_.upload<int>(h.ghost_faces);
     c.nfaces = (int)h.ghost_faces.size();
     c.face_id = pool_.upload<int>(h.face_id);
@@ -1006,6 +1076,8 @@ class Engine final : public EngineBase {
       c.proff = pool_.upload<int64_t>(h.cut_roff);
       c.cut_maxrec = h.cut_maxrec;
       c.gboff = pool_.upload<int>(h.cut_gboff);
+      c.geoff = pool_.upload<int>(h.cut_geoff);
+      c.gent = pool_.upload<uint16_t>(h.cut_gent);
       c.bf_face = pool_.upload<int>(h.bf_face);
       c.bf_dst = pool_.upload<int>(h.bf_dst);
       c.bf_start = h.bf_start;
@@ -1121,15 +1193,26 @@ class Engine final : public EngineBase {
     const Common& c = com_[l];
     if (c.nbulk > 0) {
       prof_mark(3, l, s);
-      k_apply_bulk<DIM, P, T><<<blocks_for(c.nbulk, 128), 128, 0, s>>>(D.op, x, b, y, c.bulk, c.nbulk);
+      if (use_sumfact<T>()) {
+        using SG = SfGeo<DIM, P>;
+        k_apply_sf<DIM, P, T><<<std::min(c.nsf, 2 * sms_), 256, SG::ELEMS * sizeof(T), s>>>(
+            D.sf, c.N, c.n, x, b, y, c.sf_tiles, c.sf_masks, c.nsf);
+      } else {
+        k_apply_bulk<DIM, P, T><<<blocks_for(c.nbulk, 128), 128, 0, s>>>(D.op, x, b, y, c.bulk, c.nbulk);
+      }
       count_launch("apply bulk");
       prof_mark(3, l, s);
       // per position: the (cell, owned node) pairs that run are (p+1)^d (a
       // cell s contributes the owned nodes with alpha_k = 0 wherever s_k = 1),
       // NB terms each; x read and y written once per owned node (+ b)
       constexpr int NO = Shape<DIM, P>::NO;
+      // flops: the element-matrix form's (p+1)^d (cell, node) pairs of NB
+      // terms; the sum-factorised form per owned node 2 taps per product
+      // of each pass (3D: 2 + 3 + 2 products, 2D: 2 + 2) and the combination
       constexpr int PAIRS = (DIM == 2) ? (P + 1) * (P + 1) : (P + 1) * (P + 1) * (P + 1);
-      prof_work(3, l, 2.0 * PAIRS * NB * c.nbulk, (double)c.nbulk * (NO * (b ? 3 : 2) * sizeof(T) + 4));
+      constexpr double TAPS = (2.0 * P + 1 + (P - 1) * (P + 1.0)) / P;
+      const double fl = use_sumfact<T>() ? (double)NO * (2.0 * TAPS * (DIM == 3 ? 7 : 4) + 2.0) : 2.0 * PAIRS * NB;
+      prof_work(3, l, fl * c.nbulk, (double)c.nbulk * (NO * (b ? 3 : 2) * sizeof(T) + 4));
     }
     if (c.nbnd > 0) {
       face_moments<T>(l, D, x, s);

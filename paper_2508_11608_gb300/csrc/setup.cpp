@@ -1119,6 +1119,58 @@ void cut_patch_records(HostLevel& L, bool dry) {
     }
     L.bf_start[col + 1] = (int)L.bf_face.size();
   }
+  // ghost-entry lists (the faces on the block planes whose stencil contains
+  // each DoF: along every direction k the planes of the faces of the DoF's
+  // cell layers, and the tangential cells of the plane containing it)
+  {
+    const int C = 2 * p + 1, NTf = ipow(p + 1, d - 1);
+    (void)NTf;
+    std::vector<std::vector<uint16_t>> lists(ncp);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t j = 0; j < ncp; ++j) {
+      const int m = L.cut_n[j];
+      std::vector<uint16_t> offs(m + 1, 0), ent;
+      for (int e = 0; e < m; ++e) {
+        int o[3] = {0, 0, 0}, u = L.members[L.cut_moff[j] + e];
+        for (int k = 0; k < d; ++k) {
+          o[k] = u % C;
+          u /= C;
+        }
+        for (int k = 0; k < d; ++k) {
+          const int ok = o[k], lay = ok / p, onp = ok - lay * p == 0;
+          const int Llo = std::max(0, onp ? lay - 1 : lay), Lhi = std::min(2, lay + 1);
+          for (int Lp = Llo; Lp <= Lhi; ++Lp) {
+            const int i = ok - p * (Lp - 1);
+            int ulo[2] = {0, 0}, uhi[2] = {0, 0}, tj[2] = {0, 0}, q = 0;
+            for (int kk = 0; kk < d; ++kk) {
+              if (kk == k) continue;
+              const int oj = o[kk], cj = oj / p, on = oj - cj * p == 0;
+              ulo[q] = std::max(0, on ? cj - 1 : cj);
+              uhi[q] = std::min(1, cj);
+              tj[q] = oj;
+              ++q;
+            }
+            for (int u1 = (d == 3 ? ulo[1] : 0); u1 <= (d == 3 ? uhi[1] : 0); ++u1)
+              for (int u0 = ulo[0]; u0 <= uhi[0]; ++u0) {
+                const int bit = (k * 3 + Lp) * half + u0 + 2 * u1;
+                if (!((L.cut_gmask[j] >> bit) & 1ull)) continue;
+                const int t = (tj[0] - p * u0) + (d == 3 ? (p + 1) * (tj[1] - p * u1) : 0);
+                ent.push_back((uint16_t)(bit | (i << 6) | (t << 9)));
+              }
+          }
+        }
+        offs[e + 1] = (uint16_t)ent.size();
+      }
+      std::vector<uint16_t>& out = lists[j];
+      out = offs;
+      out.insert(out.end(), ent.begin(), ent.end());
+      out.resize((out.size() + 7) / 8 * 8, 0);
+    }
+    L.cut_geoff.assign(ncp + 1, 0);
+    for (int64_t j = 0; j < ncp; ++j) L.cut_geoff[j + 1] = L.cut_geoff[j] + (int)lists[j].size();
+    L.cut_gent.resize(L.cut_geoff[ncp]);
+    for (int64_t j = 0; j < ncp; ++j) std::copy(lists[j].begin(), lists[j].end(), L.cut_gent.begin() + L.cut_geoff[j]);
+  }
   // work model of the pipelined kernel (replaces the entry-list kernel's):
   // flops 2 m^2 (packed solve) + 2 NB per row item + per ghost face of the
   // block p NT (2 (2p+1) + 2 NT) for its moments + 2p per ghost entry of a
@@ -1136,13 +1188,13 @@ void cut_patch_records(HostLevel& L, bool dry) {
     for (int col = 0; col < ncol; ++col)
       for (int j = L.cut_start[col]; j < L.cut_start[col + 1]; ++j) {
         const double m = L.cut_n[j], nit = L.cut_item_off[j + 1] - L.cut_item_off[j];
-        const double nent = L.cut_fo[j + 1] - L.cut_fo[j];
+        const double nent = L.cut_gent[L.cut_geoff[j] + L.cut_n[j]];  // ghost entries of the patch rows
         const double nbf = __builtin_popcountll(L.cut_gmask[j] & bnd_mask);
         const double nf = __builtin_popcountll(L.cut_gmask[j]) - nbf;  // internal faces, formed in the block
         L.work_cut[col][0] += 2.0 * m * m + 2.0 * NB * nit + nf * p * NTf * (2.0 * (2 * p + 1) + 2.0 * NTf) +
                               2.0 * p * nent;
         L.work_cut[col][1] += m * (m + 1) / 2 + (double)rows[j] * NB + 2.0 * NCL + nbf * p * NTf + m;
-        L.work_cut[col][2] += 4.0 * m + nit + 4.0 * NCELL + 48.0;
+        L.work_cut[col][2] += 4.0 * m + nit + 4.0 * NCELL + 56.0 + 2.0 * (L.cut_geoff[j + 1] - L.cut_geoff[j]);
       }
     // the boundary-face moment launch of each colour: per face the jumps,
     // the face mass and the coefficients; x of the two cells read, the

@@ -125,6 +125,13 @@ struct HostLevel {
   // faces to compute are bf_face[bf_start[c] .. bf_start[c + 1]) (ghost-face
   // ids) with their slots bf_dst[2 i], bf_dst[2 i + 1] (-1: none).
   std::vector<int> cut_gboff, bf_start, bf_face, bf_dst;
+  // Ghost-entry lists of the cut patches: patch j's run cut_gent[cut_geoff[j]
+  // .. cut_geoff[j + 1]) (a multiple of 8 entries) holds m + 1 row offsets,
+  // then per DoF row (member order) the ghost faces whose stencil contains
+  // the DoF: bit | (i << 6) | (t << 9), with bit the face's bit in
+  // cut_gmask[j], i the node along its normal, t the tangential node.
+  std::vector<int> cut_geoff;
+  std::vector<uint16_t> cut_gent;
   // algorithmic work per launch, used to report achieved FLOP/s and bytes:
   // per colour of the cut-patch solve and of the interior-patch step
   // {flops, scalars moved, index bytes moved}

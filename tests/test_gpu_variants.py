@@ -8,8 +8,10 @@ each one on the same small problems:
   interior step, FP32 (mixed form): dense map with 1 or 2 patches per thread,
     the split form with several threads per patch, and the tensor-core form;
   interior step, FP64: one warp per patch, one block per patch;
-  cut-patch step (3D Q2): element-matrix rows staged in shared memory or read
-    through L1.
+  cut-patch step (3D Q2): each patch's record (packed inverse and cut-cell
+    rows) brought into shared memory by TMA, or read from global memory;
+  operator rows of nodes with only uncut cells: element matrices or sum
+    factorisation.
 Tolerances as in test_gpu_parity (FP64 1e-11 of the update, FP32 2e-4); the
 variants that share an arithmetic must agree bit for bit.  The tensor-core
 form rounds its operands to TF32 (10-bit mantissa, unit roundoff 4.9e-4),
@@ -50,6 +52,7 @@ def pair(request):
     yield pb, H, request.param
     pb.set_kernel_variant(_lib.CF_VAR_INTERIOR, 0)
     pb.set_kernel_variant(_lib.CF_VAR_CUT, 0)
+    pb.set_kernel_variant(_lib.CF_VAR_OPERATOR, 0)
 
 
 def _steps(pb, H, cut, prec, tol):
@@ -139,7 +142,8 @@ def test_solve_with_every_variant_takes_the_oracle_iterations(pair):
 
 def test_bad_variants_are_rejected(pair):
     pb, _, _ = pair
-    for fam, v in ((0, 1), (3, 1), (_lib.CF_VAR_INTERIOR, 5), (_lib.CF_VAR_CUT, 3), (_lib.CF_VAR_CUT, -1)):
+    for fam, v in ((0, 1), (4, 1), (_lib.CF_VAR_INTERIOR, 5), (_lib.CF_VAR_CUT, 3), (_lib.CF_VAR_CUT, -1),
+                   (_lib.CF_VAR_OPERATOR, 3)):
         with pytest.raises(cm.CutmgError) as e:
             pb.set_kernel_variant(fam, v)
         assert e.value.status == _lib.CF_EINVAL
@@ -169,3 +173,20 @@ def test_wait_limit_runs_out_and_the_handle_recovers():
     assert np.array_equal(_n(x2), xr)
     with pytest.raises(cm.CutmgError):
         pb.set_wait_limit(-1)
+
+
+@pytest.mark.parametrize("prec,tol", [(cm.CF_FP64, 1e-12), (cm.CF_MIXED, 2e-5)])
+def test_operator_variants_match_oracle(pair, prec, tol):
+    """The rows of nodes whose cells are all uncut: element-matrix form
+    (variant 1) and sum factorisation (variant 2), on every level, against
+    the oracle's assembled operator."""
+    pb, H, _ = pair
+    for v in (1, 2):
+        pb.set_kernel_variant(_lib.CF_VAR_OPERATOR, v)
+        for l in range(pb.n_levels):
+            x = random_vector(pb.n_dofs(l), 100 + l)
+            y = torch.zeros(pb.n_dofs(l), dtype=torch.float64, device=DEV)
+            pb.level_apply(l, _t(x), y, precision=prec)
+            yo = H.levels[l].A @ x
+            assert np.abs(_n(y) - yo).max() <= tol * np.abs(yo).max(), (v, l)
+    pb.set_kernel_variant(_lib.CF_VAR_OPERATOR, 0)
