@@ -58,6 +58,9 @@ struct LvlDesc {
   const int* bf_dst;
   int bf_start[9];
   const float* tc_b;  // FP32 interior-patch map as the tensor-core B operand
+  SfArgs<T> sf;       // sum-factorised operator: 1D rows, tiles of bulk positions
+  const int* sf_tiles;
+  const uint32_t* sf_masks;
 };
 
 struct PassDesc {  // one separable transfer pass of one instance
@@ -252,6 +255,23 @@ __global__ void __launch_bounds__(128) kb_cut_pipe(const LvlDesc<DIM, P, T>* __r
       err);
 }
 
+// sum-factorised operator over the (instance, tile) work list: the tile body
+// of k_apply_sf (the same arithmetic as the instance alone)
+template <int DIM, int P, typename T>
+__global__ void __launch_bounds__(256) kb_apply_sf(const LvlDesc<DIM, P, T>* __restrict__ D,
+                                                   const T* const* __restrict__ X, const T* const* __restrict__ B,
+                                                   T* const* __restrict__ Y, const int* __restrict__ off, int K,
+                                                   int total) {
+  extern __shared__ __align__(16) unsigned char sfm[];
+  for (int it = blockIdx.x; it < total; it += gridDim.x) {
+    const int i = find_inst(off, K, it);
+    const LvlDesc<DIM, P, T>& L = D[i];
+    const int local = it - off[i];
+    sf_tile<DIM, P, T>(L.sf, L.N, L.n, X[i], B ? B[i] : nullptr, Y[i], L.sf_tiles[local],
+                       L.sf_masks + (size_t)local * SfGeo<DIM, P>::MASKW, reinterpret_cast<T*>(sfm));
+  }
+}
+
 // apply: items are bulk positions (mode 0) or boundary nodes (mode 1)
 template <int DIM, int P, typename T, int MODE>
 __global__ void __launch_bounds__(128) kb_apply(const LvlDesc<DIM, P, T>* __restrict__ D,
@@ -439,6 +459,10 @@ class BatchGroup final : public BatchGroupBase {
     err_ = pool_.alloc<int>(1);
     CUTMG_CUDA(cudaFuncSetAttribute(kb_smooth_tc<DIM, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     TcGeo<DIM, P>::SMEM));
+    CUTMG_CUDA(cudaFuncSetAttribute(kb_apply_sf<DIM, P, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    SfGeo<DIM, P>::ELEMS * (int)sizeof(double)));
+    CUTMG_CUDA(cudaFuncSetAttribute(kb_apply_sf<DIM, P, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    SfGeo<DIM, P>::ELEMS * (int)sizeof(float)));
     if (!E::kWarpCut) {
       CUTMG_CUDA(cudaFuncSetAttribute(kb_cut_pipe<DIM, P, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       2 * E::kRecSlotMax));
@@ -680,7 +704,7 @@ class BatchGroup final : public BatchGroupBase {
     int total = 0;
   };
   std::vector<std::vector<Work>> w_cart_, w_tile_, w_cut_, w_cf_, w_bf_;  // [depth][colour]
-  std::vector<Work> w_bulk_, w_bnd_, w_faces_, w_coarse_, w_xzero_;
+  std::vector<Work> w_bulk_, w_sft_, w_bnd_, w_faces_, w_coarse_, w_xzero_;
   std::vector<std::array<Work, 3>> w_rpass_, w_ppass_;
   Work w_vecF_;
   int* off_vec_ = nullptr;
@@ -766,6 +790,9 @@ class BatchGroup final : public BatchGroupBase {
           for (int c = 0; c <= NCOL; ++c) L.bf_start[c] = C.bf_start[c];
         }
         L.tc_b = e->template typed<float>()[l].tc_b;
+        L.sf = Ty.sf;
+        L.sf_tiles = C.sf_tiles;
+        L.sf_masks = C.sf_masks;
         for (int c = 0; c <= NCOL; ++c) {
           L.cart_start[c] = C.cart_start[c];
           L.cut_start[c] = C.cut_start[c];
@@ -813,6 +840,7 @@ class BatchGroup final : public BatchGroupBase {
     w_cut_.assign(depth_, std::vector<Work>(NCOL));
     w_cf_.assign(depth_, std::vector<Work>(NCOL));
     w_bulk_.assign(depth_, Work{});
+    w_sft_.assign(depth_, Work{});
     w_bnd_.assign(depth_, Work{});
     w_faces_.assign(depth_, Work{});
     w_coarse_.assign(depth_, Work{});
@@ -859,6 +887,9 @@ class BatchGroup final : public BatchGroupBase {
         });
       }
       w_bulk_[t] = fill([&](int i) { return lv[i] >= 1 || t == 0 ? (lv[i] >= 0 ? inst_[i]->com_[lv[i]].nbulk : 0) : 0; });
+      w_sft_[t] = fill([&](int i) {
+        return lv[i] >= 1 || t == 0 ? (lv[i] >= 0 && inst_[i]->com_[lv[i]].nbulk > 0 ? inst_[i]->com_[lv[i]].nsf : 0) : 0;
+      });
       w_bnd_[t] = fill([&](int i) { return lv[i] >= 1 || t == 0 ? (lv[i] >= 0 ? inst_[i]->com_[lv[i]].nbnd : 0) : 0; });
       w_faces_[t] = fill([&](int i) { return lv[i] >= 1 || t == 0 ? (lv[i] >= 0 ? inst_[i]->com_[lv[i]].nfaces : 0) : 0; });
       w_coarse_[t] = fill([&](int i) { return lv[i] == 0 ? (int)inst_[i]->com_[0].ndof : 0; });
@@ -1034,8 +1065,13 @@ class BatchGroup final : public BatchGroupBase {
     // X = x, B = b, Y = r from the descriptors: pointer tables built here once
     auto& tabs = res_tabs<T>(t);
     if (w_bulk_[t].total > 0) {
-      kb_apply<DIM, P, T, 0><<<grid(w_bulk_[t].total, 128), 128, 0, s>>>(D, tabs.X, tabs.B, tabs.Y,
-                                                                         w_bulk_[t].off, K_, w_bulk_[t].total);
+      if (inst_[0]->template use_sumfact<T>())
+        kb_apply_sf<DIM, P, T><<<std::max(1, std::min(w_sft_[t].total, 2 * sms_)), 256,
+                                 SfGeo<DIM, P>::ELEMS * sizeof(T), s>>>(D, tabs.X, tabs.B, tabs.Y, w_sft_[t].off, K_,
+                                                                       w_sft_[t].total);
+      else
+        kb_apply<DIM, P, T, 0><<<grid(w_bulk_[t].total, 128), 128, 0, s>>>(D, tabs.X, tabs.B, tabs.Y,
+                                                                           w_bulk_[t].off, K_, w_bulk_[t].total);
       count("batched apply bulk");
     }
     if (w_bnd_[t].total > 0) {
@@ -1153,8 +1189,13 @@ class BatchGroup final : public BatchGroupBase {
       count("batched face moments");
     }
     if (w_bulk_[0].total > 0) {
-      kb_apply<DIM, P, double, 0><<<grid(w_bulk_[0].total, 128), 128, 0, s>>>(D, X, B, Y, w_bulk_[0].off, K_,
-                                                                              w_bulk_[0].total);
+      if (inst_[0]->template use_sumfact<double>())
+        kb_apply_sf<DIM, P, double><<<std::max(1, std::min(w_sft_[0].total, 2 * sms_)), 256,
+                                      SfGeo<DIM, P>::ELEMS * sizeof(double), s>>>(D, X, B, Y, w_sft_[0].off, K_,
+                                                                                  w_sft_[0].total);
+      else
+        kb_apply<DIM, P, double, 0><<<grid(w_bulk_[0].total, 128), 128, 0, s>>>(D, X, B, Y, w_bulk_[0].off, K_,
+                                                                                w_bulk_[0].total);
       count("batched apply bulk");
     }
     if (w_bnd_[0].total > 0) {

@@ -79,24 +79,23 @@ __device__ __forceinline__ void sf_residues(F&& f) {
 }
 
 // y = A x (b == nullptr) or y = b - A x at the owned nodes of the bulk
-// positions of each listed tile.  tiles[t]: the tile's first position
-// (packed a_0 + (N+1)(a_1 + (N+1) a_2)); masks[t * MASKW ..]: its bulk
-// positions, bit ax + TX (ay + TY az).
+// positions of one tile.  tile_pos: the tile's first position (packed
+// a_0 + (N+1)(a_1 + (N+1) a_2)); mask: its bulk positions, bit
+// ax + TX (ay + TY az).  smem: SfGeo::ELEMS elements.  All threads of the
+// block call it; it ends with a barrier.
 template <int DIM, int P, typename T>
-__global__ void __launch_bounds__(256) k_apply_sf(SfArgs<T> A, int N, int n, const T* __restrict__ x,
-                                                  const T* __restrict__ b, T* __restrict__ y,
-                                                  const int* __restrict__ tiles, const uint32_t* __restrict__ masks,
-                                                  int ntiles) {
+__device__ __forceinline__ void sf_tile(const SfArgs<T>& A, int N, int n, const T* __restrict__ x,
+                                        const T* __restrict__ b, T* __restrict__ y, int tile_pos,
+                                        const uint32_t* __restrict__ mask, T* smem) {
   using G = SfGeo<DIM, P>;
-  extern __shared__ __align__(16) unsigned char sfm[];
-  T* X = reinterpret_cast<T*>(sfm);
+  T* X = smem;
   T* U = X + G::XS;
   T* V = U + G::US;
   const int tid = threadIdx.x, NT = blockDim.x, np = N + 1;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  {
     int a0[3] = {0, 0, 0};
     {
-      int q = tiles[tile];
+      int q = tile_pos;
 #pragma unroll
       for (int k = 0; k < DIM; ++k) {
         a0[k] = q % np;
@@ -151,7 +150,7 @@ __global__ void __launch_bounds__(256) k_apply_sf(SfArgs<T> A, int N, int n, con
       for (int w = tid; w < (G::NX / P) * G::NY * G::NZ; w += NT) {
         const int q = w % (G::NX / P), r = w / (G::NX / P), yo = r % G::NY, zo = r / G::NY;
         const int pos = q + G::TX * (yo / P + G::TY * (zo / P));
-        if (!((masks[(size_t)tile * G::MASKW + pos / 32] >> (pos % 32)) & 1u)) continue;
+        if (!((mask[pos / 32] >> (pos % 32)) & 1u)) continue;
         sf_residues<P, T>([&](auto rc) {
           constexpr int R = decltype(rc)::value;
           const int xo = P * q + R;
@@ -183,7 +182,7 @@ __global__ void __launch_bounds__(256) k_apply_sf(SfArgs<T> A, int N, int n, con
       for (int w = tid; w < (G::NX / P) * G::NY; w += NT) {
         const int q = w % (G::NX / P), yo = w / (G::NX / P);
         const int pos = q + G::TX * (yo / P);
-        if (!((masks[(size_t)tile * G::MASKW + pos / 32] >> (pos % 32)) & 1u)) continue;
+        if (!((mask[pos / 32] >> (pos % 32)) & 1u)) continue;
         sf_residues<P, T>([&](auto rc) {
           constexpr int R = decltype(rc)::value;
           const int xo = P * q + R;
@@ -196,6 +195,18 @@ __global__ void __launch_bounds__(256) k_apply_sf(SfArgs<T> A, int N, int n, con
     }
     __syncthreads();
   }
+}
+
+// The tiles of one level, block-stride over the tile list
+template <int DIM, int P, typename T>
+__global__ void __launch_bounds__(256) k_apply_sf(SfArgs<T> A, int N, int n, const T* __restrict__ x,
+                                                  const T* __restrict__ b, T* __restrict__ y,
+                                                  const int* __restrict__ tiles, const uint32_t* __restrict__ masks,
+                                                  int ntiles) {
+  extern __shared__ __align__(16) unsigned char sfm[];
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
+    sf_tile<DIM, P, T>(A, N, n, x, b, y, tiles[tile], masks + (size_t)tile * SfGeo<DIM, P>::MASKW,
+                       reinterpret_cast<T*>(sfm));
 }
 
 }  // namespace cutmg
