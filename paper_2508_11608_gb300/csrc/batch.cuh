@@ -471,6 +471,10 @@ class BatchGroup final : public BatchGroupBase {
     }
     CUTMG_CUDA(cudaMallocHost(&host_sc_, sizeof(double) * K_ * 16));
     rebuild_lists();
+    // pointer tables of the level residuals, uploaded here: the first use is
+    // inside a stream capture, where no allocation or copy may run
+    res_tabs<double>(0);
+    res_tabs<float>(0);
   }
   ~BatchGroup() override {
     for (auto& g : graphs_) if (g.exec) cudaGraphExecDestroy(g.exec);

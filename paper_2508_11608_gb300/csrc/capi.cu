@@ -169,13 +169,14 @@ struct ThreadCount {
 };
 
 static cf_status setup_impl(const cf_mesh* mesh, const cf_levelset* ls, int degree, const cf_params* params,
-                            cf_problem** out, bool device, cudaStream_t stream) {
+                            cf_problem** out, bool device, cudaStream_t stream, bool device_inverse) {
   if (!out) return fail(CF_EINVAL, "null argument");
   *out = nullptr;
   SetupParams prm;
   int precision = CF_FP64, threads = 0;
   cf_status tr = translate(mesh, ls, degree, params, prm, precision, threads);
   if (tr != CF_OK) return tr;
+  prm.device_inverse = device_inverse;
   std::unique_ptr<cf_problem> pb;
   cf_status st = guarded([&] {
     ThreadCount tc(threads);
@@ -194,12 +195,13 @@ static cf_status setup_impl(const cf_mesh* mesh, const cf_levelset* ls, int degr
 
 cf_status cf_setup(const cf_mesh* mesh, const cf_levelset* ls, int degree, const cf_params* params, void* stream,
                    cf_problem** out) {
-  return setup_impl(mesh, ls, degree, params, out, true, S(stream));
+  return setup_impl(mesh, ls, degree, params, out, true, S(stream), true);
 }
 
 cf_status cutmg_build_host(const cf_mesh* mesh, const cf_levelset* ls, int degree, const cf_params* params,
                            cf_problem** out) {
-  return setup_impl(mesh, ls, degree, params, out, false, nullptr);
+  // the served form attaches a device right after: its inverses are formed there
+  return setup_impl(mesh, ls, degree, params, out, false, nullptr, true);
 }
 
 cf_status cutmg_attach_device(cf_problem* pb, cudaStream_t stream) {
@@ -267,7 +269,7 @@ size_t cutmg_estimate_device_bytes(const cf_problem* pb) { return cutmg_estimate
 
 cf_status cf_setup_host(const cf_mesh* mesh, const cf_levelset* ls, int degree, const cf_params* params,
                         cf_problem** out) {
-  return setup_impl(mesh, ls, degree, params, out, false, nullptr);
+  return setup_impl(mesh, ls, degree, params, out, false, nullptr, false);
 }
 
 void cf_destroy(cf_problem* pb) { delete pb; }
@@ -718,8 +720,20 @@ cf_status cf_host_cut_patch(const cf_problem* pb, int level, int64_t j, int64_t*
     }
     h_nodes[e] = node;
   }
-  if (h_inv)
-    std::memcpy(h_inv, &L.inv[L.cut_ioff[j]], sizeof(double) * L.cut_n[j] * L.cut_n[j]);
+  if (h_inv) {
+    if (!L.inv_on_device) {
+      std::memcpy(h_inv, &L.inv[L.cut_ioff[j]], sizeof(double) * L.cut_n[j] * L.cut_n[j]);
+    } else {
+      // formed on the device: the packed lower triangle read back and unfolded
+      if (!pb->eng) return fail(CF_EINVAL, "cut-patch inverses of this handle live on a device that was not attached");
+      const int mm = L.cut_n[j];
+      std::vector<double> pk((size_t)mm * (mm + 1) / 2);
+      cf_status st = guarded([&] { pb->eng->cut_inverse(level, j, pk.data()); });
+      if (st != CF_OK) return st;
+      for (int i = 0; i < mm; ++i)
+        for (int c = 0; c <= i; ++c) h_inv[(size_t)i * mm + c] = h_inv[(size_t)c * mm + i] = pk[(size_t)i * (i + 1) / 2 + c];
+    }
+  }
   return CF_OK;
 }
 

@@ -505,3 +505,87 @@ __global__ void __launch_bounds__(128) k_cut_pipe(PipeLevel<T> L, int j0, int np
 }
 
 }  // namespace cutmg
+
+namespace cutmg {
+
+// Cut-patch inverses on the device, FP64 (the local solver's setup, Sec. 3):
+// for patch j, rec[roff[j] ..] holds the lower triangle of A_j by rows on
+// entry and that of A_j^{-1} on exit.  One block per patch (block-stride),
+// the matrix in shared memory with row stride ld >= m (dynamic, ld (ld + 1)
+// doubles): Cholesky A = L L^T (right-looking, L in the lower triangle),
+// W = L^{-1} by forward substitution, one column per thread (W's strictly
+// lower part stored transposed in the strictly upper triangle, its diagonal
+// apart), then A^{-1} = W^T W, entry (i, c) summed over k = i .. m-1 in
+// increasing order.  A pivot that is not positive records *err = 2 (the
+// patch matrix is not SPD) and the patch is skipped.
+__device__ __forceinline__ int tri_row(int e) {
+  int i = (int)((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
+  while (i * (i + 1) / 2 > e) --i;
+  while ((i + 1) * (i + 2) / 2 <= e) ++i;
+  return i;
+}
+
+static __global__ void __launch_bounds__(128) k_patch_inverse(double* __restrict__ rec, const int64_t* __restrict__ roff,
+                                                       const int* __restrict__ cnt, int npatch, int ld,
+                                                       int* __restrict__ err) {
+  extern __shared__ __align__(16) double S[];
+  double* Wd = S + (size_t)ld * ld;
+  __shared__ int bad;
+  const int tid = threadIdx.x, NT = blockDim.x;
+  for (int j = blockIdx.x; j < npatch; j += gridDim.x) {
+    const int m = cnt[j];
+    double* a = rec + roff[j];
+    const int ne = m * (m + 1) / 2;
+    if (tid == 0) bad = 0;
+    for (int e = tid; e < ne; e += NT) {
+      const int i = tri_row(e), c = e - i * (i + 1) / 2;
+      S[i * ld + c] = a[e];
+    }
+    __syncthreads();
+    for (int k = 0; k < m; ++k) {
+      if (tid == 0) {
+        const double d = S[k * ld + k];
+        if (!(d > 0.0)) bad = 1;
+        S[k * ld + k] = d > 0.0 ? sqrt(d) : 1.0;
+      }
+      __syncthreads();
+      const double piv = S[k * ld + k];
+      for (int i = k + 1 + tid; i < m; i += NT) S[i * ld + k] /= piv;
+      __syncthreads();
+      for (int i = k + 1 + tid; i < m; i += NT) {
+        const double lik = S[i * ld + k];
+        for (int c = k + 1; c <= i; ++c) S[i * ld + c] -= lik * S[c * ld + k];
+      }
+      __syncthreads();
+    }
+    for (int c = tid; c < m; c += NT) {
+      const double wcc = 1.0 / S[c * ld + c];
+      Wd[c] = wcc;
+      for (int i = c + 1; i < m; ++i) {
+        double s = S[i * ld + c] * wcc;
+        for (int k = c + 1; k < i; ++k) s += S[i * ld + k] * S[c * ld + k];
+        S[c * ld + i] = -s / S[i * ld + i];
+      }
+    }
+    __syncthreads();
+    if (bad) {
+      if (tid == 0) atomicExch(err, 2);
+    } else {
+      for (int e = tid; e < ne; e += NT) {
+        const int i = tri_row(e), c = e - i * (i + 1) / 2;
+        double s = (i == c ? Wd[i] : S[c * ld + i]) * Wd[i];
+        for (int k = i + 1; k < m; ++k) s += S[i * ld + k] * S[c * ld + k];
+        a[e] = s;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// FP64 -> FP32 copy of a whole array (the mixed form's records)
+static __global__ void __launch_bounds__(256) k_to_float(const double* __restrict__ in, float* __restrict__ out, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+
+}  // namespace cutmg

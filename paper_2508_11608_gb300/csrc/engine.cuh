@@ -237,6 +237,7 @@ class Engine final : public EngineBase {
     com_.resize(L);
     d64_.resize(L);
     d32_.resize(L);
+    err_ = pool_.alloc<int>(1);
     for (int l = 0; l < L; ++l) upload_level(l);
     const auto& F = com_.back();
     xF_ = pool_.alloc<double>(F.nbox);
@@ -250,7 +251,6 @@ class Engine final : public EngineBase {
     aux2_ = pool_.alloc<double>(F.nbox);
     part_ = pool_.alloc<double>(kDotBlocks);
     sc_ = pool_.alloc<double>(16);
-    err_ = pool_.alloc<int>(1);
     CUTMG_CUDA(cudaFuncSetAttribute(k_smooth_tc<DIM, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     TcGeo<DIM, P>::SMEM));
     CUTMG_CUDA(cudaFuncSetAttribute(k_apply_sf<DIM, P, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -305,6 +305,13 @@ class Engine final : public EngineBase {
       throw std::invalid_argument("kernel family must be 1 (interior), 2 (cut) or 3 (operator)");
     }
     drop_graphs();
+  }
+  void cut_inverse(int l, int64_t j, double* h_packed) override {
+    if (kWarpCut || l < 1 || l >= n_levels()) throw std::invalid_argument("no cut-patch records on this level");
+    const HostLevel& h = H_.levels[l];
+    const int m = h.cut_n[j];
+    CUTMG_CUDA(cudaMemcpy(h_packed, d64_[l].rec + h.cut_roff[j], sizeof(double) * m * (m + 1) / 2,
+                          cudaMemcpyDeviceToHost));
   }
   void set_wait_limit(int polls) override {
     if (polls < 0) throw std::invalid_argument("wait limit must be >= 0");
@@ -947,7 +954,18 @@ class Engine final : public EngineBase {
     if (kWarpCut) {
       D.inv = pool_.upload<T>(h.inv);
     } else {
-      D.rec = pool_.upload<T>(h.rec);
+      if (!h.inv_on_device) {
+        D.rec = pool_.upload<T>(h.rec);
+      } else if (std::is_same<T, double>::value) {
+        // A_j packed in the records: inverted here, in FP64
+        D.rec = pool_.upload<T>(h.rec);
+        device_inverses(h, reinterpret_cast<double*>(D.rec));
+      } else {
+        // the mixed form's records: the FP64 device records rounded
+        D.rec = pool_.alloc<T>((size_t)std::max<int64_t>(1, h.n_rec), false);
+        k_to_float<<<1024, 256, 0, setup_stream_>>>(d64_[l].rec, reinterpret_cast<float*>(D.rec), h.n_rec);
+        launch_check("record conversion");
+      }
       D.Gb = pool_.alloc<T>((size_t)std::max(1, h.cut_gboff.empty() ? 0 : h.cut_gboff.back()) * P *
                             FaceGeo<DIM, P>::NT);
     }
@@ -976,6 +994,28 @@ class Engine final : public EngineBase {
         D.t3 = pool_.alloc<T>(nf * nc);
       }
     }
+  }
+
+  // the cut-patch inverses of a level from the assembled A_j in the FP64
+  // records (k_patch_inverse, in place)
+  void device_inverses(const HostLevel& h, double* rec) {
+    const int64_t ncp = (int64_t)h.cut_vert.size();
+    if (ncp == 0) return;
+    int mmax = 1;
+    for (int m : h.cut_n) mmax = std::max(mmax, m);
+    const int ld = mmax | 1;
+    const size_t dyn = sizeof(double) * ((size_t)ld * ld + ld);
+    CUTMG_CUDA(cudaFuncSetAttribute(k_patch_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    int* cnt = pool_.upload<int>(h.cut_n);
+    int64_t* roff = pool_.upload<int64_t>(h.cut_roff);
+    k_patch_inverse<<<(int)std::min<int64_t>(ncp, 8 * sms_), 128, dyn, setup_stream_>>>(rec, roff, cnt, (int)ncp, ld,
+                                                                                         err_);
+    launch_check("cut-patch inverses");
+    int e = 0;
+    CUTMG_CUDA(cudaMemcpyAsync(&e, err_, sizeof(int), cudaMemcpyDeviceToHost, setup_stream_));
+    CUTMG_CUDA(cudaStreamSynchronize(setup_stream_));
+    if (e) throw std::runtime_error("a cut-patch matrix is not positive definite (device Cholesky, level N=" +
+                                    std::to_string(h.N) + ")");
   }
 
   void upload_level(int l) {

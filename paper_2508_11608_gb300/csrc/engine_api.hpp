@@ -57,6 +57,9 @@ class EngineBase {
   // timeout; both drop the captured CUDA graphs
   virtual void set_variant(int family, int variant) = 0;
   virtual void set_wait_limit(int polls) = 0;
+  // packed lower triangle of cut patch j's inverse on level l (FP64, from the
+  // device records; synchronises)
+  virtual void cut_inverse(int l, int64_t j, double* h_packed) = 0;
   // kernel launches issued so far, and event timing of one kernel family
   virtual int64_t launches() const = 0;
   virtual void profile_start(int kind, int level) = 0;

@@ -877,7 +877,7 @@ void patch_work_model(HostLevel& L) {
 
 // Cut-patch matrices A_j = A[I_j, I_j] from their cell and ghost-face pieces,
 // inverted in place (explicit FP64 inverse per patch).
-void cut_patch_inverses(const RefTables& R, HostLevel& L) {
+void cut_patch_inverses(const RefTables& R, HostLevel& L, bool invert) {
   const int d = L.d, p = L.p, N = L.N, NB = R.NB;
   const int np = N + 1, C = 2 * p + 1, NCL = ipow(C, d);
   const int64_t ncp = (int64_t)L.cut_vert.size();
@@ -988,7 +988,7 @@ void cut_patch_inverses(const RefTables& R, HostLevel& L) {
           }
     }
     try {
-      spd_inverse(m, A);
+      if (invert) spd_inverse(m, A);
     } catch (const std::exception& e) {
       err[j] = 1;
 #pragma omp critical
@@ -1242,13 +1242,14 @@ void cut_patch_records(HostLevel& L, bool dry) {
 // Patches (Sec. 2.3, Sec. 3) of a level: vertex sets by colour, and for the
 // cut patches their DoF lists, ghost-face entries, row items, work model and
 // explicit inverses.
-void build_patches(const RefTables& R, HostLevel& L, bool dry) {
+void build_patches(const RefTables& R, HostLevel& L, bool dry, bool device_inverse) {
   patch_vertex_sets(L);
   cut_patch_members(L, dry);
   cut_patch_face_entries(L);
   cut_patch_rows(L);
   patch_work_model(L);
-  if (!dry) cut_patch_inverses(R, L);
+  L.inv_on_device = device_inverse && ipow(2 * L.p + 1, L.d) > 64;
+  if (!dry) cut_patch_inverses(R, L, !L.inv_on_device);
   cut_patch_records(L, dry);
 }
 
@@ -1468,7 +1469,7 @@ void build_level(const SetupParams& prm, const RefTables& R, int N, HostLevel& L
     }
   }
   interior_patch_tables(R, L);
-  build_patches(R, L, prm.dry);
+  build_patches(R, L, prm.dry, prm.device_inverse);
 }
 
 // 1D transfer tables between a coarse level (Nc cells) and its refinement

@@ -54,6 +54,10 @@ struct SetupParams {
   // quadrature, no element matrices, no inverses and no right-hand side
   // (what a device-footprint estimate needs before a full setup)
   bool dry = false;
+  // the cut-patch inverses of the block kernel ((2p+1)^d > 64) are formed on
+  // the device (FP64) from the assembled A_j; the host then keeps A_j (packed
+  // in the records, full in inv) instead of the inverse
+  bool device_inverse = false;
   LevelSet ls;
 };
 
@@ -67,6 +71,7 @@ struct HostLevel {
   std::vector<int> cut_id;      // N^d: row block in cutmat or -1
   HostBlocks cutmat;            // [n_cut][NB][NB] volume + Nitsche terms
   int64_t n_cut = 0, n_active = 0, n_ghost = 0;
+  bool inv_on_device = false;   // inv / rec hold A_j, inverted by the engine (SetupParams::device_inverse)
   int64_t n_inv = 0;            // entries of the cut-patch inverse storage (inv.size() unless dry)
   // nodes
   std::vector<uint8_t> nact;    // n^d: node belongs to an active cell

@@ -190,3 +190,28 @@ def test_operator_variants_match_oracle(pair, prec, tol):
             yo = H.levels[l].A @ x
             assert np.abs(_n(y) - yo).max() <= tol * np.abs(yo).max(), (v, l)
     pb.set_kernel_variant(_lib.CF_VAR_OPERATOR, 0)
+
+
+def test_device_patch_inverses_match_the_host_inverses():
+    """3D Q2: the cut-patch inverses of a device handle are formed on the GPU
+    in FP64 (Cholesky, triangular inverse, W^T W); they agree with the host
+    setup's inverses of the same patches (a host-only handle) and invert the
+    oracle's patch matrix A[I_j, I_j]."""
+    name = "ball3d_q2_n16"
+    c = CONFIGS[name]
+    dev = cm.Problem(**problem_kwargs(name))
+    host = cm.Problem(**problem_kwargs(name), host_only=True)
+    H = Hierarchy(Sphere(c["center"], c["radius"]), c["dim"], c["n_cells"], c["degree"], c["n_levels"])
+    for l in range(1, dev.n_levels):
+        pd = dev.host_patches(l)
+        ph = host.host_patches(l)
+        lev = H.levels[l]
+        assert len(pd) == len(ph) > 0
+        worst = 0.0
+        for a, b in zip(pd, ph):
+            assert a["vertex"] == b["vertex"] and np.array_equal(a["nodes"], b["nodes"])
+            worst = max(worst, np.abs(a["inverse"] - b["inverse"]).max() / np.abs(b["inverse"]).max())
+            idx = lev.lev.node_to_dof[a["nodes"]]
+            Aj = lev.A[idx][:, idx].toarray()
+            assert np.abs(a["inverse"] @ Aj - np.eye(len(idx))).max() < 1e-9
+        assert worst < 1e-10, (l, worst)
