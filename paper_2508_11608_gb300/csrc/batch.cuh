@@ -251,7 +251,8 @@ __global__ void __launch_bounds__(128) kb_cut_pipe(const LvlDesc<DIM, P, T>* __r
         lv = &D[i].pl;
         j = D[i].cut_start[colour] + it - off[i];
       },
-      psm, slot_bytes, stage, sh, bar, kTmaSpin, err);
+      [&](const PipeLevel<T>* lv) -> const T* { return lv->op.Kref; }, psm, slot_bytes, stage, sh, bar, kTmaSpin,
+      err);
 }
 
 // sum-factorised operator over the (instance, tile) work list: the tile body

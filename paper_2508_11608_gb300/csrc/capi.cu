@@ -239,9 +239,26 @@ size_t cutmg_estimate_hierarchy_bytes(const Hierarchy& H) {
                                  : (size_t)L.n_inv;
     size_t typed = (size_t)L.n_cut * nb * nb + nb * nb + cutstore + L.pro_w.size() + L.res_w.size() +
                    ncoarse + 3 * nbox + L.members.size() + L.ghost_faces.size() * p * nt;
-    if (pipe)
-      tot += 4 * L.members.size() + 8 * L.cut_gmask.size() + 8 * L.cut_roff.size() + 4 * L.cut_gboff.size() +
-             4 * L.bf_face.size() + 4 * L.bf_dst.size() + 4 * L.cut_geoff.size() + 2 * L.cut_gent.size();
+    if (pipe) {
+      size_t words = 0;
+      for (size_t j = 0; j < ncp; ++j) words += (size_t)(L.cut_item_off[j + 1] - L.cut_item_off[j] + 3) / 4;
+      tot += 4 * L.members.size() + 4 * words + 8 * ncp + 4 * L.cut_pk.size() + 8 * L.cut_gmask.size() +
+             8 * L.cut_roff.size() + 4 * L.cut_gboff.size() + 4 * L.bf_face.size() + 4 * L.bf_dst.size() +
+             4 * L.cut_geoff.size() + 2 * L.cut_gent.size();
+    }
+    if (l > 0) {  // interior-patch dense map: transposed copy and the tensor-core operand (FP32 only)
+      size_t nc = 1, ni = 1;
+      for (int k = 0; k < d; ++k) {
+        nc *= (size_t)(2 * p + 1);
+        ni *= (size_t)(2 * p - 1);
+      }
+      const size_t np_tc = ni <= 16 ? 16 : (ni + 15) / 16 * 16;
+      tot += 4 * (2 * nc * ((ni + 7) / 8 * 8) + np_tc * ((nc + 7) / 8 * 8));
+    }
+    if (l > 0) {
+      const size_t nf = L.n, nc = H.levels[l - 1].n;
+      typed += d == 3 ? nc * nf * nf + nc * nc * nf + nf * nc * nc + nf * nf * nc : 2 * nc * nf;
+    }
     tot += typed * 12;  // FP64 + FP32 copies
   }
   tot += 9 * H.levels.back().nact.size() * 8 + H.levels.back().dofs.size() * 8 + 64 * 1024;

@@ -6,29 +6,30 @@
 //
 // Per patch j the block needs
 //   * the closure of x and b (cp.async, one element per thread),
-//   * its DoF list (cp.async),
-//   * its record: the explicit inverse A_j^{-1} packed by rows of its lower
-//     triangle, and the dense rows B_j = A[I_j, K_j] over the closure nodes
-//     K_j of its active cells of everything in the patch rows that involves
-//     only closure nodes (the cell matrices, and the ghost faces on the
-//     block's middle planes, all of whose nodes belong to active patch
-//     cells); with its entry list (the ghost terms of the block's boundary
-//     planes per row, then K_j); both by TMA bulk copies (cp.async.bulk)
+//   * the DoF list, the row items and the cell kinds (cp.async),
+//   * its record: the explicit inverse packed by rows of its lower triangle
+//     and the rows of the cut-cell matrices its items use, one contiguous
+//     run, and its ghost-entry list; both by TMA bulk copies (cp.async.bulk)
 //     completing on one mbarrier,
 //   * the moments of the ghost faces on the boundary planes of its block
 //     (cp.async from its moment slots).
 // Every ghost face in the row of a patch DoF is a face of an active cell that
 // contains the DoF, hence of a patch cell, so it lies on one of the 3 planes
 // per direction of the 2 x .. x 2 block (eq. "cutfem-ghost").  The faces on
-// the two boundary planes reach into the neighbouring block, whose cut patch
-// of the same colour may update those nodes in the same launch; their
-// moments (G_m = coef_m (Mhat x Mhat) J_m, J_m[t] = sum_i dvec_m[i] x(i, t)
-// over the 2p + 1 nodes across the face) are therefore computed before the
-// colour step by a separate launch (k_face_moments_to), like every term of
-// the additive-within-a-colour step (Sec. 2.3): the patch sees the x from
-// before the colour step only.  Per patch: r = b_I - B_j x_K - (boundary
-// ghost terms), x_I += A_j^{-1} r, each DoF row on 4 lanes combined by
-// shuffles in a fixed order.
+// the middle plane are formed inside the block from the staged closure
+// (G_m = coef_m (Mhat x Mhat) J_m, J_m[t] = sum_i dvec_m[i] x(i, t) over the
+// 2p + 1 nodes across the face): all their nodes belong to active patch
+// cells, so no other patch of the colour writes them.  The faces on the two
+// boundary planes reach into the neighbouring block, whose cut patch of the
+// same colour may update those nodes in the same launch; their moments are
+// therefore computed before the colour step by a separate launch
+// (k_face_moments_to), like every moment of the additive-within-a-colour
+// step (Sec. 2.3): the patch sees the x from before the colour step only.
+//
+// The ghost-entry list of a patch (built at setup) holds, for each DoF row,
+// the (face, node along the normal, tangential node) triples of the ghost
+// faces whose stencil contains the DoF; the rows and the local solve split
+// each DoF over 4 lanes, combined by shuffles in a fixed order.
 #pragma once
 
 #include "kernels.cuh"
@@ -61,20 +62,24 @@ __host__ __device__ constexpr uint16_t ghost_entry(int bit, int i, int t) {
 // device arrays of one level for the pipelined cut kernel
 template <typename T>
 struct PipeLevel {
-  OpArgs<T> op;             // N, n, dvec (the ghost-entry weights)
+  OpArgs<T> op;             // N, n, dvec, coef, Mhat (Kref: the uncut element matrix)
   T* x;
   const T* b;
   const int* vert;          // packed patch vertex
   const int* cnt;           // DoFs m
   const int* moff;          // first DoF in members
   const int* members;       // closure-local index of each DoF (32-bit)
+  const int* ioff;          // first 32-bit word of the patch's row items (4-byte aligned lists)
+  const int* nit;           // row items of the patch
+  const uint32_t* items;    // s * NB + i per item, four per word
+  const int* pk;            // [patch][2^d] cell kind / first pack row and item
   const uint64_t* gmask;    // ghost faces of the block planes
   const int64_t* roff;      // record offsets (entries); roff[j + 1] - roff[j] = length
   const T* rec;             // records
   const int* gboff;         // first boundary-face moment slot of each patch
   const T* Gb;              // boundary-face moment slots, P (p+1)^(d-1) values each
-  const int* geoff;         // entry lists: [geoff[j], geoff[j + 1]) in gent (16-byte aligned)
-  const uint16_t* gent;     // per patch: m + 1 row offsets, entries, |K_j|, K_j
+  const int* geoff;         // ghost-entry lists: [geoff[j], geoff[j + 1]) in gent (16-byte aligned)
+  const uint16_t* gent;     // per patch: m + 1 row offsets, then the entries
 };
 
 // bits of the block-boundary planes (0 and 2) in a ghost-face mask
@@ -94,20 +99,27 @@ struct PipeStage {
   T b[G::NCL];
   T halo[G::HALO];
   int mem[G::NCL];
+  uint32_t item[G::ITEMW];
+  int pk[G::NCELL];
   __align__(16) uint16_t gl[G::GCAP];
   uint64_t gmask;
   const T* recp;         // the record: the stage's slot or global memory
-  const uint16_t* glp;   // the entry list: gl or global memory
-  int vert, m;
+  const uint16_t* glp;   // the ghost-entry list: gl or global memory
+  int vert, m, nit;
 };
 
 template <int DIM, int P, typename T>
 struct PipeShared {
-  T r[PipeGeo<DIM, P>::NCL];
+  using G = PipeGeo<DIM, P>;
+  T part[G::NCELL][G::NB];
+  T r[G::NCL];
+  T J[G::NIF][P][G::NT];
+  T Gm[G::NIF][P][G::NT];
+  int flist[G::NIF];
 };
 
 struct PipeMeta {
-  int vert, m, mo, gb, g0, g1;
+  int vert, m, mo, io, nit, gb, g0, g1;
   int64_t r0, r1;
   uint64_t gmask;
 };
@@ -118,6 +130,8 @@ __device__ __forceinline__ PipeMeta pipe_meta(const PipeLevel<T>& L, int j) {
   t.vert = L.vert[j];
   t.m = L.cnt[j];
   t.mo = L.moff[j];
+  t.io = L.ioff[j];
+  t.nit = L.nit[j];
   t.r0 = L.roff[j];
   t.r1 = L.roff[j + 1];
   t.gmask = L.gmask[j];
@@ -177,6 +191,7 @@ __device__ __forceinline__ void pipe_prefetch(const PipeLevel<T>& L, const PipeM
   if (tid == 0) {
     st.vert = M.vert;
     st.m = M.m;
+    st.nit = M.nit;
     st.gmask = M.gmask;
     st.recp = tma ? slot : L.rec + M.r0;
     st.glp = gtma ? st.gl : L.gent + M.g0;
@@ -205,10 +220,34 @@ __device__ __forceinline__ void pipe_prefetch(const PipeLevel<T>& L, const PipeM
     }
     if (e < M.m) cp_async_elem(&st.mem[e], L.members + M.mo + e);
   }
+  for (int w = tid; w < (M.nit + 3) / 4; w += NT) cp_async_elem(&st.item[w], L.items + M.io + w);
+  if (tid < G::NCELL) cp_async_elem(&st.pk[tid], L.pk + (size_t)j * G::NCELL + tid);
   // moments of the block-boundary ghost faces (one slot per set bit)
   const int nbv = __popcll(M.gmask & pipe_bnd_bits<DIM, P>()) * P * G::NT;
   for (int w = tid; w < nbv; w += NT) cp_async_elem(&st.halo[w], L.Gb + (size_t)M.gb * P * G::NT + w);
   asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// x at closure coordinate ck along k and tangential cell u, node t, for a
+// face of the middle plane
+template <int DIM, int P, typename T>
+__device__ __forceinline__ T pipe_x(const PipeStage<DIM, P, T>& st, int k, int u, int ck, int t) {
+  constexpr int C = 2 * P + 1;
+  int o = 0, st_ = 1, q = 0, tt = t;
+#pragma unroll
+  for (int kk = 0; kk < DIM; ++kk) {
+    int c;
+    if (kk == k) {
+      c = ck;
+    } else {
+      c = P * ((u >> q) & 1) + tt % (P + 1);
+      tt /= P + 1;
+      ++q;
+    }
+    o += c * st_;
+    st_ *= C;
+  }
+  return st.x[o];
 }
 
 // sum over the 4 lanes of a DoF row (lanes 4k .. 4k+3 of a warp), the same
@@ -220,31 +259,105 @@ __device__ __forceinline__ T lane4_sum(T v) {
   return v;
 }
 
-// One patch from a filled stage: residual rows, local solve, x updated in
-// place.
+// One patch from a filled stage: ghost-face moments, residual rows, local
+// solve, x updated in place.  Kref: the level's uncut element matrix.
 template <int DIM, int P, typename T, int NT>
 __device__ __forceinline__ void pipe_compute(const PipeLevel<T>& L, const PipeStage<DIM, P, T>& st,
-                                             PipeShared<DIM, P, T>& sh) {
+                                             PipeShared<DIM, P, T>& sh, const T* __restrict__ Kref) {
   using G = PipeGeo<DIM, P>;
-  constexpr int C = G::C, NTF = G::NT, LN = G::LANES, ROWS = NT / LN;
+  constexpr int C = G::C, NB = G::NB, NTF = G::NT, LN = G::LANES, ROWS = NT / LN;
   const int tid = threadIdx.x, m = st.m, n = L.op.n, np = L.op.N + 1;
   constexpr uint64_t bnd = pipe_bnd_bits<DIM, P>();
-  const uint64_t gbnd = st.gmask & bnd;
+  const uint64_t gm = st.gmask, gint = gm & ~bnd, gbnd = gm & bnd;
+  const int nf = __popcll(gint);
+  if (tid < G::NFACE && ((gint >> tid) & 1ull)) sh.flist[__popcll(gint & ((1ull << tid) - 1ull))] = tid;
+  __syncthreads();
+  // J_m[t] of the ghost faces of the middle planes, and the cell rows of the items
+  for (int w = tid; w < nf * P * NTF; w += NT) {
+    const int fi = w / (P * NTF), rem = w - fi * (P * NTF), mm = rem / NTF, t = rem - mm * NTF;
+    const int f = sh.flist[fi], u = f % G::HALF, k = f / G::HALF / 3;
+    T acc = T(0);
+#pragma unroll
+    for (int i = 0; i <= 2 * P; ++i) acc += L.op.dvec[mm][i] * pipe_x<DIM, P, T>(st, k, u, i, t);
+    sh.J[fi][mm][t] = acc;
+  }
+  const T* rows = st.recp + ((m * (m + 1) / 2 + 3) / 4 * 4);
+  const uint8_t* item = reinterpret_cast<const uint8_t*>(st.item);
+  for (int q = tid; q < st.nit; q += NT) {
+    const int it = item[q], sc = it / NB, jj = it - sc * NB;
+    const int pkv = st.pk[sc];
+    const T* row = pkv == -1 ? Kref + jj * NB : rows + (size_t)((pkv >> 8) + q - (pkv & 255)) * NB;
+    int base = 0, ost = 1;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+      base += P * ((sc >> k) & 1) * ost;
+      ost *= C;
+    }
+    T acc = T(0);
+    if (DIM == 2) {
+#pragma unroll
+      for (int q1 = 0; q1 <= P; ++q1)
+#pragma unroll
+        for (int q0 = 0; q0 <= P; ++q0) acc += row[q0 + (P + 1) * q1] * st.x[base + q0 + C * q1];
+    } else {
+#pragma unroll
+      for (int q2 = 0; q2 <= P; ++q2)
+#pragma unroll
+        for (int q1 = 0; q1 <= P; ++q1)
+#pragma unroll
+          for (int q0 = 0; q0 <= P; ++q0)
+            acc += row[q0 + (P + 1) * (q1 + (P + 1) * q2)] * st.x[base + q0 + C * (q1 + C * q2)];
+    }
+    sh.part[sc][jj] = acc;
+  }
+  __syncthreads();
+  // G_m[t] = coef_m sum_t' (Mhat x Mhat)[t][t'] J_m[t']
+  for (int w = tid; w < nf * P * NTF; w += NT) {
+    const int fi = w / (P * NTF), rem = w - fi * (P * NTF), mm = rem / NTF, t = rem - mm * NTF;
+    const int t0 = t % (P + 1), t1 = t / (P + 1);
+    T acc = T(0);
+#pragma unroll
+    for (int s = 0; s < NTF; ++s) {
+      const T wgt = (DIM == 2) ? L.op.Mhat[t0][s] : L.op.Mhat[t0][s % (P + 1)] * L.op.Mhat[t1][s / (P + 1)];
+      acc += wgt * sh.J[fi][mm][s];
+    }
+    sh.Gm[fi][mm][t] = L.op.coef[mm] * acc;
+  }
+  __syncthreads();
+  // residual of the own rows, LN lanes per DoF: lane 0 the cell parts in
+  // cell order, every lane a strided share of the row's ghost entries
   const uint16_t* gl = st.glp;
-  const int nent = gl[m], K = gl[m + 1 + nent];
-  const uint16_t* cols = gl + m + 2 + nent;
-  const T* B = st.recp + ((m * (m + 1) / 2 + 3) / 4 * 4);
   const int lane = tid % LN;
-  // r = b_I - B_j x_K - boundary ghost terms, LN lanes per DoF row
   for (int e0 = 0; e0 < m; e0 += ROWS) {
     const int e = e0 + tid / LN;
     T acc = T(0);
     if (e < m) {
-      const T* Be = B + (size_t)e * K;
-      for (int c = lane; c < K; c += LN) acc += Be[c] * st.x[cols[c]];
+      if (lane == 0) {
+        int o[3] = {0, 0, 0}, u = st.mem[e];
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+          o[k] = u % C;
+          u /= C;
+        }
+#pragma unroll
+        for (int sc = 0; sc < G::NCELL; ++sc) {
+          int jj = 0, jst = 1;
+          bool in = st.pk[sc] != -2;
+#pragma unroll
+          for (int k = 0; k < DIM; ++k) {
+            const int a = o[k] - P * ((sc >> k) & 1);
+            if (a < 0 || a > P) in = false;
+            jj += a * jst;
+            jst *= (P + 1);
+          }
+          if (in) acc += sh.part[sc][jj];
+        }
+      }
       for (int q = gl[e] + lane; q < gl[e + 1]; q += LN) {
         const int en = gl[m + 1 + q], bit = en & 63, i = (en >> 6) & 7, t = en >> 9;
-        const T* g = &st.halo[__popcll(gbnd & ((1ull << bit) - 1ull)) * P * NTF];
+        const uint64_t below = (1ull << bit) - 1ull;
+        const T* g = ((bnd >> bit) & 1ull) ? &st.halo[__popcll(gbnd & below) * P * NTF]
+                                            : &sh.Gm[__popcll(gint & below)][0][0];
 #pragma unroll
         for (int mm = 0; mm < P; ++mm) acc += L.op.dvec[mm][i] * g[mm * NTF + t];
       }
@@ -312,9 +425,10 @@ __device__ __forceinline__ bool pipe_wait(uint64_t* bar, uint32_t& ph, int s, in
 
 // The pipelined loop of one block over the work items it, it + step, ..
 // below total.  locate(item, level, patch) gives an item's level descriptor
-// and patch.  Metadata run two items ahead, data one item ahead.
-template <int DIM, int P, typename T, int NT, class Locate>
-__device__ __forceinline__ void pipe_loop(int it, int step, int total, Locate&& locate,
+// and patch; kref(level) its uncut element matrix.  Metadata run two items
+// ahead, data one item ahead.
+template <int DIM, int P, typename T, int NT, class Locate, class Kref>
+__device__ __forceinline__ void pipe_loop(int it, int step, int total, Locate&& locate, Kref&& kref,
                                           unsigned char* psm, int slot_bytes, PipeStage<DIM, P, T>* stage,
                                           PipeShared<DIM, P, T>& sh, uint64_t* bar, int spin, int* err) {
   if (threadIdx.x == 0) {
@@ -354,7 +468,7 @@ __device__ __forceinline__ void pipe_loop(int it, int step, int total, Locate&& 
       ok = pipe_wait<true>(&bar[s], ph, s, spin, err);
     else
       ok = pipe_wait<false>(&bar[s], ph, s, spin, err);
-    if (__syncthreads_and(ok)) pipe_compute<DIM, P, T, NT>(*Lc, stage[s], sh);
+    if (__syncthreads_and(ok)) pipe_compute<DIM, P, T, NT>(*Lc, stage[s], sh, kref(Lc));
     Lc = Ln;
     jc = jn;
     cur = nxt;
@@ -369,13 +483,16 @@ __device__ __forceinline__ void pipe_loop(int it, int step, int total, Locate&& 
 template <int DIM, int P, typename T>
 __global__ void __launch_bounds__(128) k_cut_pipe(PipeLevel<T> L, int j0, int npatch, int slot_bytes, int* err,
                                                   int spin) {
+  using G = PipeGeo<DIM, P>;
   constexpr int NT = 128;
   extern __shared__ __align__(16) unsigned char psm[];
   __shared__ __align__(16) PipeStage<DIM, P, T> stage[2];
   __shared__ PipeShared<DIM, P, T> sh;
+  __shared__ __align__(16) T sK[G::NB * G::NB];
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ PipeLevel<T> sL;
   if ((int)blockIdx.x >= npatch) return;
+  for (int i = threadIdx.x; i < G::NB * G::NB; i += NT) sK[i] = L.op.Kref[i];
   if (threadIdx.x == 0) sL = L;  // the level's arrays and tables, read by every thread
   const PipeLevel<T>* Lp = &sL;
   pipe_loop<DIM, P, T, NT>(
@@ -384,7 +501,7 @@ __global__ void __launch_bounds__(128) k_cut_pipe(PipeLevel<T> L, int j0, int np
         lv = Lp;
         j = j0 + it;
       },
-      psm, slot_bytes, stage, sh, bar, spin, err);
+      [&](const PipeLevel<T>*) -> const T* { return sK; }, psm, slot_bytes, stage, sh, bar, spin, err);
 }
 
 }  // namespace cutmg

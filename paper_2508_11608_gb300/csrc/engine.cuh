@@ -192,6 +192,10 @@ class Engine final : public EngineBase {
     int64_t nmembers;
     // pipelined cut kernel (closures of more than 64 nodes)
     int* members32 = nullptr;
+    int* pioff = nullptr;
+    int* pnit = nullptr;
+    uint32_t* pitems = nullptr;
+    int* ppk = nullptr;
     uint64_t* pgmask = nullptr;
     int64_t* proff = nullptr;
     std::vector<int> cut_maxrec;
@@ -740,12 +744,11 @@ class Engine final : public EngineBase {
   // solved alone and inside a batch runs the same arithmetic.
   static constexpr bool kWarpCut = (DIM == 2 ? (2 * P + 1) * (2 * P + 1) : (2 * P + 1) * (2 * P + 1) * (2 * P + 1)) <= 64;
   // Pipelined cut kernel: record slots of the colour's longest record (16-byte
-  // multiple) up to kRecSlot (FP32) / kRecSlot64 bytes (3D Q2: m (m + 1) / 2
-  // + m |K_j| entries, about 13 KB in FP32 for m = 28); longer records are
+  // multiple) up to kRecSlot (FP32) / kRecSlot64 bytes; longer records are
   // read from global memory.  Variant 2 of the cut family reads every record
   // from global memory (the same arithmetic).  The grid: every block the
   // occupancy calculator lets reside, at most one per patch.
-  static constexpr int kRecSlot = 24 * 1024, kRecSlot64 = 40 * 1024, kRecSlotMax = 48 * 1024;
+  static constexpr int kRecSlot = 8 * 1024, kRecSlot64 = 12 * 1024, kRecSlotMax = 16 * 1024;
   struct PipePlan {
     int slot = 0, grid = 0;
   };
@@ -770,6 +773,10 @@ class Engine final : public EngineBase {
     L.cnt = c.cutn;
     L.moff = c.cutmo;
     L.members = c.members32;
+    L.ioff = c.pioff;
+    L.nit = c.pnit;
+    L.items = c.pitems;
+    L.pk = c.ppk;
     L.gmask = c.pgmask;
     L.roff = c.proff;
     L.rec = D.rec;
@@ -1087,6 +1094,24 @@ class Engine final : public EngineBase {
     if (!kWarpCut) {
       std::vector<int> m32(h.members.begin(), h.members.end());
       c.members32 = pool_.upload<int>(m32);
+      // row items in 4-byte aligned runs per patch
+      const int64_t ncp = (int64_t)h.cut_vert.size();
+      std::vector<int> io(ncp), ni(ncp);
+      std::vector<uint32_t> words;
+      for (int64_t j = 0; j < ncp; ++j) {
+        const int i0 = h.cut_item_off[j], i1 = h.cut_item_off[j + 1];
+        io[j] = (int)words.size();
+        ni[j] = i1 - i0;
+        for (int q = i0; q < i1; q += 4) {
+          uint32_t w = 0;
+          for (int b = 0; b < 4 && q + b < i1; ++b) w |= (uint32_t)h.cut_items[q + b] << (8 * b);
+          words.push_back(w);
+        }
+      }
+      c.pioff = pool_.upload<int>(io);
+      c.pnit = pool_.upload<int>(ni);
+      c.pitems = pool_.upload<uint32_t>(words);
+      c.ppk = pool_.upload<int>(h.cut_pk);
       c.pgmask = pool_.upload<uint64_t>(h.cut_gmask);
       c.proff = pool_.upload<int64_t>(h.cut_roff);
       c.cut_maxrec = h.cut_maxrec;

@@ -1002,59 +1002,18 @@ void cut_patch_inverses(const RefTables& R, HostLevel& L, bool invert) {
     if (err[j]) throw std::runtime_error(first_err);
 }
 
-// Records of the block cut kernel ((2p+1)^d > 64).  For cut patch j with
-// DoFs I_j and closure columns K_j (the closure nodes of its active cells):
-//   rec:  A_j^{-1} packed by rows of its lower triangle, then the dense rows
-//         B_j = A[I_j, K_j] of everything in the patch rows that involves
-//         only closure nodes: the cell matrices of the active patch cells and
-//         the ghost faces on the block's middle planes;
-//   gent: the row offsets and entries of the ghost faces on the block's
-//         boundary planes (whose moments come from a separate launch), then
-//         |K_j| and K_j (closure indices);
-// and the ghost-face mask, the moment slots of the boundary faces and, per
-// colour, the boundary faces with their destination slots.
+// Records of the block cut kernel: ghost-face masks, per-cell pack offsets,
+// and (unless dry) the packed inverses and cut-cell row packs.
 void cut_patch_records(HostLevel& L, bool dry) {
   const int d = L.d, p = L.p, N = L.N, NB = ipow(p + 1, d), NCELL = 1 << d;
-  const int C = 2 * p + 1, NCL = ipow(C, d);
-  if (NCL <= 64) return;  // one warp per patch: the entry-list kernel
+  if (ipow(2 * p + 1, d) <= 64) return;  // one warp per patch: the entry-list kernel
   const int64_t ncp = (int64_t)L.cut_vert.size();
   const int np = N + 1, ncol = 1 << d, half = 1 << (d - 1);
   auto cflag_at = [&](const int* c) { return cell_flag(L, c); };
-  uint64_t bnd_bits = 0;
-  for (int k = 0; k < d; ++k)
-    for (int u = 0; u < half; ++u) bnd_bits |= (1ull << ((k * 3 + 0) * half + u)) | (1ull << ((k * 3 + 2) * half + u));
-  // closure index of local node jj of patch cell sc
-  std::vector<int> cell_node((size_t)NCELL * NB);
-  for (int sc = 0; sc < NCELL; ++sc)
-    for (int jj = 0; jj < NB; ++jj) {
-      int o = 0, ost = 1, u = jj;
-      for (int k = 0; k < d; ++k) {
-        o += (p * ((sc >> k) & 1) + u % (p + 1)) * ost;
-        u /= (p + 1);
-        ost *= C;
-      }
-      cell_node[(size_t)sc * NB + jj] = o;
-    }
-  // the ghost-face block of one face (nodes e = i + (2p+1) u, i along the
-  // normal over both cells, u tangential), the same for every face
-  const int tn = ipow(p + 1, d - 1), nbk = (2 * p + 1) * tn;
-  std::vector<double> fblk((size_t)nbk * nbk);
-  for (int e1 = 0; e1 < nbk; ++e1)
-    for (int e2 = 0; e2 < nbk; ++e2) {
-      double tm = 1.0;
-      int u1 = e1 / (2 * p + 1), u2 = e2 / (2 * p + 1);
-      for (int q = 0; q < d - 1; ++q) {
-        tm *= L.Mhat[u1 % (p + 1)][u2 % (p + 1)];
-        u1 /= p + 1;
-        u2 /= p + 1;
-      }
-      double sm = 0.0;
-      for (int mm = 0; mm < p; ++mm) sm += L.coef[mm] * L.dvec[mm][e1 % (2 * p + 1)] * L.dvec[mm][e2 % (2 * p + 1)];
-      fblk[(size_t)e1 * nbk + e2] = sm * tm;
-    }
+  L.cut_roff.assign(ncp + 1, 0);
+  L.cut_pk.assign((size_t)ncp * NCELL, -2);
   L.cut_gmask.assign(ncp, 0);
-  std::vector<int> kcols(ncp, 0);
-  std::vector<std::vector<uint16_t>> lists(ncp);
+  std::vector<int> rows(ncp, 0);
 #pragma omp parallel for schedule(dynamic, 64)
   for (int64_t j = 0; j < ncp; ++j) {
     int v[3] = {0, 0, 0};
@@ -1063,8 +1022,28 @@ void cut_patch_records(HostLevel& L, bool dry) {
       v[k] = (int)(t % np);
       t /= np;
     }
-    // ghost faces of the block: plane Lp of direction k between cell layers
-    // Lp - 1 and Lp (block layers 0, 1; -1 and 2 outside)
+    // pack offsets: the items of one cell are consecutive (emitted cell by cell)
+    const int i0 = L.cut_item_off[j], i1 = L.cut_item_off[j + 1];
+    int r = 0;
+    for (int sc = 0; sc < NCELL; ++sc) {
+      const int id = L.cut_cell[(size_t)j * NCELL + sc];
+      int q0 = i1 - i0, cnt = 0;
+      for (int q = i0; q < i1; ++q)
+        if (L.cut_items[q] / NB == sc) {
+          if (cnt == 0) q0 = q - i0;
+          ++cnt;
+        }
+      if (id == -2) continue;
+      if (id == -1) {
+        L.cut_pk[(size_t)j * NCELL + sc] = -1;
+        continue;
+      }
+      L.cut_pk[(size_t)j * NCELL + sc] = (r << 8) | q0;
+      r += cnt;
+    }
+    rows[j] = r;
+    // ghost faces of the block: plane L of direction k between cell layers
+    // L - 1 and L (block layers 0, 1; -1 and 2 outside)
     uint64_t mask = 0;
     for (int k = 0; k < d; ++k)
       for (int Lp = 0; Lp < 3; ++Lp)
@@ -1084,70 +1063,18 @@ void cut_patch_records(HostLevel& L, bool dry) {
             mask |= 1ull << ((k * 3 + Lp) * half + u);
         }
     L.cut_gmask[j] = mask;
-    // columns: closure nodes of the active patch cells, ascending
-    std::vector<char> incol(NCL, 0);
-    for (int sc = 0; sc < NCELL; ++sc)
-      if (L.cut_cell[(size_t)j * NCELL + sc] != -2)
-        for (int jj = 0; jj < NB; ++jj) incol[cell_node[(size_t)sc * NB + jj]] = 1;
-    std::vector<uint16_t> cols;
-    for (int o = 0; o < NCL; ++o)
-      if (incol[o]) cols.push_back((uint16_t)o);
-    kcols[j] = (int)cols.size();
-    // boundary-plane ghost entries of each DoF row (the faces of the DoF's
-    // cell layers along every direction, the tangential cells containing it)
-    const int m = L.cut_n[j];
-    std::vector<uint16_t> offs(m + 1, 0), ent;
-    for (int e = 0; e < m; ++e) {
-      int o[3] = {0, 0, 0}, u = L.members[L.cut_moff[j] + e];
-      for (int k = 0; k < d; ++k) {
-        o[k] = u % C;
-        u /= C;
-      }
-      for (int k = 0; k < d; ++k) {
-        const int ok = o[k], lay = ok / p, onp = ok - lay * p == 0;
-        const int Llo = std::max(0, onp ? lay - 1 : lay), Lhi = std::min(2, lay + 1);
-        for (int Lp = Llo; Lp <= Lhi; ++Lp) {
-          if (Lp == 1) continue;  // middle plane: in B_j
-          const int i = ok - p * (Lp - 1);
-          int ulo[2] = {0, 0}, uhi[2] = {0, 0}, tj[2] = {0, 0}, q = 0;
-          for (int kk = 0; kk < d; ++kk) {
-            if (kk == k) continue;
-            const int oj = o[kk], cj = oj / p, on = oj - cj * p == 0;
-            ulo[q] = std::max(0, on ? cj - 1 : cj);
-            uhi[q] = std::min(1, cj);
-            tj[q] = oj;
-            ++q;
-          }
-          for (int u1 = (d == 3 ? ulo[1] : 0); u1 <= (d == 3 ? uhi[1] : 0); ++u1)
-            for (int u0 = ulo[0]; u0 <= uhi[0]; ++u0) {
-              const int bit = (k * 3 + Lp) * half + u0 + 2 * u1;
-              if (!((mask >> bit) & 1ull)) continue;
-              const int tt = (tj[0] - p * u0) + (d == 3 ? (p + 1) * (tj[1] - p * u1) : 0);
-              ent.push_back((uint16_t)(bit | (i << 6) | (tt << 9)));
-            }
-        }
-      }
-      offs[e + 1] = (uint16_t)ent.size();
-    }
-    std::vector<uint16_t>& out = lists[j];
-    out = offs;
-    out.insert(out.end(), ent.begin(), ent.end());
-    out.push_back((uint16_t)cols.size());
-    out.insert(out.end(), cols.begin(), cols.end());
-    out.resize((out.size() + 7) / 8 * 8, 0);
   }
-  L.cut_geoff.assign(ncp + 1, 0);
-  for (int64_t j = 0; j < ncp; ++j) L.cut_geoff[j + 1] = L.cut_geoff[j] + (int)lists[j].size();
-  L.cut_gent.resize(L.cut_geoff[ncp]);
-  for (int64_t j = 0; j < ncp; ++j) std::copy(lists[j].begin(), lists[j].end(), L.cut_gent.begin() + L.cut_geoff[j]);
-  L.cut_roff.assign(ncp + 1, 0);
   for (int64_t j = 0; j < ncp; ++j) {
     const int64_t m = L.cut_n[j];
-    L.cut_roff[j + 1] = L.cut_roff[j] + (m * (m + 1) / 2 + 3) / 4 * 4 + (m * kcols[j] + 3) / 4 * 4;
+    const int64_t len = (m * (m + 1) / 2 + 3) / 4 * 4 + ((int64_t)rows[j] * NB + 3) / 4 * 4;
+    L.cut_roff[j + 1] = L.cut_roff[j] + len;
   }
   L.n_rec = L.cut_roff[ncp];
   // moment slots of the block-boundary ghost faces, and per colour the faces
   // with their destination slots
+  uint64_t bnd_bits = 0;
+  for (int k = 0; k < d; ++k)
+    for (int u = 0; u < half; ++u) bnd_bits |= (1ull << ((k * 3 + 0) * half + u)) | (1ull << ((k * 3 + 2) * half + u));
   L.cut_gboff.assign(ncp + 1, 0);
   for (int64_t j = 0; j < ncp; ++j) L.cut_gboff[j + 1] = L.cut_gboff[j] + __builtin_popcountll(L.cut_gmask[j] & bnd_bits);
   L.bf_start.assign(ncol + 1, 0);
@@ -1192,25 +1119,87 @@ void cut_patch_records(HostLevel& L, bool dry) {
     }
     L.bf_start[col + 1] = (int)L.bf_face.size();
   }
-  // work model (what the kernel computes per patch): 2 m^2 for the packed
-  // solve, 2 m |K_j| for the dense rows, 2p per boundary ghost entry;
-  // scalars: the record, the closures of x and b, the boundary moments, x of
-  // the DoFs written; index bytes: the entry/column list, DoF list, metadata.
-  // The boundary moments' launch: per face the jumps, the face mass and the
-  // coefficients, x of the two cells read, the moments written per slot.
+  // ghost-entry lists (the faces on the block planes whose stencil contains
+  // each DoF: along every direction k the planes of the faces of the DoF's
+  // cell layers, and the tangential cells of the plane containing it)
   {
-    const int NTf = tn;
+    const int C = 2 * p + 1, NTf = ipow(p + 1, d - 1);
+    (void)NTf;
+    std::vector<std::vector<uint16_t>> lists(ncp);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t j = 0; j < ncp; ++j) {
+      const int m = L.cut_n[j];
+      std::vector<uint16_t> offs(m + 1, 0), ent;
+      for (int e = 0; e < m; ++e) {
+        int o[3] = {0, 0, 0}, u = L.members[L.cut_moff[j] + e];
+        for (int k = 0; k < d; ++k) {
+          o[k] = u % C;
+          u /= C;
+        }
+        for (int k = 0; k < d; ++k) {
+          const int ok = o[k], lay = ok / p, onp = ok - lay * p == 0;
+          const int Llo = std::max(0, onp ? lay - 1 : lay), Lhi = std::min(2, lay + 1);
+          for (int Lp = Llo; Lp <= Lhi; ++Lp) {
+            const int i = ok - p * (Lp - 1);
+            int ulo[2] = {0, 0}, uhi[2] = {0, 0}, tj[2] = {0, 0}, q = 0;
+            for (int kk = 0; kk < d; ++kk) {
+              if (kk == k) continue;
+              const int oj = o[kk], cj = oj / p, on = oj - cj * p == 0;
+              ulo[q] = std::max(0, on ? cj - 1 : cj);
+              uhi[q] = std::min(1, cj);
+              tj[q] = oj;
+              ++q;
+            }
+            for (int u1 = (d == 3 ? ulo[1] : 0); u1 <= (d == 3 ? uhi[1] : 0); ++u1)
+              for (int u0 = ulo[0]; u0 <= uhi[0]; ++u0) {
+                const int bit = (k * 3 + Lp) * half + u0 + 2 * u1;
+                if (!((L.cut_gmask[j] >> bit) & 1ull)) continue;
+                const int t = (tj[0] - p * u0) + (d == 3 ? (p + 1) * (tj[1] - p * u1) : 0);
+                ent.push_back((uint16_t)(bit | (i << 6) | (t << 9)));
+              }
+          }
+        }
+        offs[e + 1] = (uint16_t)ent.size();
+      }
+      std::vector<uint16_t>& out = lists[j];
+      out = offs;
+      out.insert(out.end(), ent.begin(), ent.end());
+      out.resize((out.size() + 7) / 8 * 8, 0);
+    }
+    L.cut_geoff.assign(ncp + 1, 0);
+    for (int64_t j = 0; j < ncp; ++j) L.cut_geoff[j + 1] = L.cut_geoff[j] + (int)lists[j].size();
+    L.cut_gent.resize(L.cut_geoff[ncp]);
+    for (int64_t j = 0; j < ncp; ++j) std::copy(lists[j].begin(), lists[j].end(), L.cut_gent.begin() + L.cut_geoff[j]);
+  }
+  // work model of the pipelined kernel (replaces the entry-list kernel's):
+  // flops 2 m^2 (packed solve) + 2 NB per row item + per ghost face of the
+  // block p NT (2 (2p+1) + 2 NT) for its moments + 2p per ghost entry of a
+  // row; scalars: the record (packed inverse + cut rows), the closures of x
+  // and b, the halo of the boundary ghost faces, x of the DoFs written;
+  // index bytes: DoF list, items, cell kinds, metadata.  The face moments of
+  // the colour step are part of this kernel (no separate launch).
+  {
+    const int NTf = ipow(p + 1, d - 1), NCL = ipow(2 * p + 1, d);
+    uint64_t bnd_mask = 0;
+    for (int k = 0; k < d; ++k)
+      for (int u = 0; u < half; ++u) bnd_mask |= (1ull << ((k * 3 + 0) * half + u)) | (1ull << ((k * 3 + 2) * half + u));
     L.work_cut.assign(ncol, {0.0, 0.0, 0.0});
     L.work_face.assign(ncol, {0.0, 0.0, 0.0});
-    for (int col = 0; col < ncol; ++col) {
+    for (int col = 0; col < ncol; ++col)
       for (int j = L.cut_start[col]; j < L.cut_start[col + 1]; ++j) {
-        const double m = L.cut_n[j], K = kcols[j];
-        const double nent = L.cut_gent[L.cut_geoff[j] + L.cut_n[j]];
-        const double nbf = __builtin_popcountll(L.cut_gmask[j] & bnd_bits);
-        L.work_cut[col][0] += 2.0 * m * m + 2.0 * m * K + 2.0 * p * nent;
-        L.work_cut[col][1] += m * (m + 1) / 2 + m * K + 2.0 * NCL + nbf * p * NTf + m;
-        L.work_cut[col][2] += 4.0 * m + 2.0 * (L.cut_geoff[j + 1] - L.cut_geoff[j]) + 48.0;
+        const double m = L.cut_n[j], nit = L.cut_item_off[j + 1] - L.cut_item_off[j];
+        const double nent = L.cut_gent[L.cut_geoff[j] + L.cut_n[j]];  // ghost entries of the patch rows
+        const double nbf = __builtin_popcountll(L.cut_gmask[j] & bnd_mask);
+        const double nf = __builtin_popcountll(L.cut_gmask[j]) - nbf;  // internal faces, formed in the block
+        L.work_cut[col][0] += 2.0 * m * m + 2.0 * NB * nit + nf * p * NTf * (2.0 * (2 * p + 1) + 2.0 * NTf) +
+                              2.0 * p * nent;
+        L.work_cut[col][1] += m * (m + 1) / 2 + (double)rows[j] * NB + 2.0 * NCL + nbf * p * NTf + m;
+        L.work_cut[col][2] += 4.0 * m + nit + 4.0 * NCELL + 56.0 + 2.0 * (L.cut_geoff[j + 1] - L.cut_geoff[j]);
       }
+    // the boundary-face moment launch of each colour: per face the jumps,
+    // the face mass and the coefficients; x of the two cells read, the
+    // moments written to each destination slot
+    for (int col = 0; col < ncol; ++col) {
       const double flf = 2.0 * (2 * p + 1) * p * NTf + 2.0 * p * (p + 1) * NTf * (d - 1) + (double)p * NTf;
       double fl = 0.0, sc = 0.0, ib = 0.0;
       for (int i = L.bf_start[col]; i < L.bf_start[col + 1]; ++i) {
@@ -1232,63 +1221,21 @@ void cut_patch_records(HostLevel& L, bool dry) {
   for (int64_t j = 0; j < ncp; ++j) {
     double* out = &L.rec[(size_t)L.cut_roff[j]];
     std::fill(out, L.rec.data() + L.cut_roff[j + 1], 0.0);
-    const int m = L.cut_n[j], K = kcols[j];
-    // packed lower triangle of A_j^{-1} (or of A_j, inverted on the device)
+    const int m = L.cut_n[j];
     const double* A = &L.inv[(size_t)L.cut_ioff[j]];
     for (int i = 0; i < m; ++i)
       for (int c = 0; c <= i; ++c) out[(size_t)i * (i + 1) / 2 + c] = A[(size_t)i * m + c];
-    double* B = out + ((int64_t)m * (m + 1) / 2 + 3) / 4 * 4;
-    // closure index -> DoF row / column
-    std::vector<int> row(NCL, -1), colx(NCL, -1);
-    for (int e = 0; e < m; ++e) row[L.members[L.cut_moff[j] + e]] = e;
-    const uint16_t* lst = &L.cut_gent[L.cut_geoff[j]];
-    const int nent = lst[m];
-    for (int c = 0; c < K; ++c) colx[lst[m + 1 + nent + 1 + c]] = c;
-    int v[3] = {0, 0, 0};
-    int64_t t = L.cut_vert[j];
-    for (int k = 0; k < d; ++k) {
-      v[k] = (int)(t % np);
-      t /= np;
-    }
-    // cell matrices of the active patch cells
-    for (int sc = 0; sc < NCELL; ++sc) {
+    double* rp = out + ((int64_t)m * (m + 1) / 2 + 3) / 4 * 4;
+    const int i0 = L.cut_item_off[j], i1 = L.cut_item_off[j + 1];
+    int r = 0;
+    for (int q = i0; q < i1; ++q) {
+      const int sc = L.cut_items[q] / NB, jj = L.cut_items[q] % NB;
       const int id = L.cut_cell[(size_t)j * NCELL + sc];
-      if (id == -2) continue;
-      const double* Ke = id >= 0 ? &L.cutmat[(size_t)id * NB * NB] : L.Kref.data();
-      for (int a = 0; a < NB; ++a) {
-        const int e = row[cell_node[(size_t)sc * NB + a]];
-        if (e < 0) continue;
-        for (int bb = 0; bb < NB; ++bb) B[(size_t)e * K + colx[cell_node[(size_t)sc * NB + bb]]] += Ke[a * NB + bb];
-      }
+      if (id < 0) continue;
+      const double* K = &L.cutmat[((size_t)id * NB + jj) * NB];
+      std::copy(K, K + NB, rp + (size_t)r * NB);
+      ++r;
     }
-    // ghost faces of the middle planes (all their nodes in active patch cells)
-    for (int k = 0; k < d; ++k)
-      for (int u = 0; u < half; ++u) {
-        const int bit = (k * 3 + 1) * half + u;
-        if (!((L.cut_gmask[j] >> bit) & 1ull)) continue;
-        std::vector<int> on(nbk);
-        for (int e1 = 0; e1 < nbk; ++e1) {
-          int uu = e1 / (2 * p + 1), o = 0, ost = 1, q = 0;
-          for (int kk = 0; kk < d; ++kk) {
-            int ck;
-            if (kk == k) {
-              ck = e1 % (2 * p + 1);
-            } else {
-              ck = p * ((u >> q) & 1) + uu % (p + 1);
-              uu /= p + 1;
-              ++q;
-            }
-            o += ck * ost;
-            ost *= C;
-          }
-          on[e1] = o;
-        }
-        for (int e1 = 0; e1 < nbk; ++e1) {
-          const int e = row[on[e1]];
-          if (e < 0) continue;
-          for (int e2 = 0; e2 < nbk; ++e2) B[(size_t)e * K + colx[on[e2]]] += fblk[(size_t)e1 * nbk + e2];
-        }
-      }
   }
 }
 

@@ -109,13 +109,15 @@ struct HostLevel {
   // Per cut patch record of the block kernel ((2p+1)^d > 64, i.e. 3D Q2):
   // rec[cut_roff[j] ..] = the inverse packed by rows of its lower triangle
   // (entry (i, c), c <= i, at i (i + 1) / 2 + c; padded to 4 entries), then
-  // the dense rows B_j = A[I_j, K_j] (m x |K_j|, row-major, padded to 4
-  // entries) over the closure nodes K_j of the active patch cells, of the
-  // cell matrices and the ghost faces of the block's middle planes.
+  // the rows of the cut-cell matrices its items use, NB entries each, in item
+  // order (padded to 4 entries); cut_roff[j + 1] - cut_roff[j] = its length.
+  // cut_pk[j * 2^d + s] = -2 inactive cell, -1 uncut, else (r0 << 8) | q0:
+  // the first pack row r0 and first item q0 of cut patch cell s.
   // cut_gmask[j] bit (k * 3 + L) * 2^(d-1) + u: the face normal to k on
   // cell-layer plane L of the patch block (0 lower boundary, 1 middle, 2
   // upper boundary) at tangential cell u is a ghost face.
   std::vector<int64_t> cut_roff;
+  std::vector<int> cut_pk;
   std::vector<uint64_t> cut_gmask;
   std::vector<int> cut_maxrec;    // per colour: longest record
   HostBlocks rec;
@@ -128,12 +130,11 @@ struct HostLevel {
   // faces to compute are bf_face[bf_start[c] .. bf_start[c + 1]) (ghost-face
   // ids) with their slots bf_dst[2 i], bf_dst[2 i + 1] (-1: none).
   std::vector<int> cut_gboff, bf_start, bf_face, bf_dst;
-  // Entry lists of the cut patches: patch j's run cut_gent[cut_geoff[j] ..
-  // cut_geoff[j + 1]) (a multiple of 8 entries) holds m + 1 row offsets, then
-  // per DoF row (member order) the ghost faces of the block's boundary planes
-  // whose stencil contains the DoF: bit | (i << 6) | (t << 9), with bit the
-  // face's bit in cut_gmask[j], i the node along its normal, t the tangential
-  // node; then |K_j| and K_j (closure indices, ascending).
+  // Ghost-entry lists of the cut patches: patch j's run cut_gent[cut_geoff[j]
+  // .. cut_geoff[j + 1]) (a multiple of 8 entries) holds m + 1 row offsets,
+  // then per DoF row (member order) the ghost faces whose stencil contains
+  // the DoF: bit | (i << 6) | (t << 9), with bit the face's bit in
+  // cut_gmask[j], i the node along its normal, t the tangential node.
   std::vector<int> cut_geoff;
   std::vector<uint16_t> cut_gent;
   // algorithmic work per launch, used to report achieved FLOP/s and bytes:
