@@ -188,9 +188,10 @@ cf_status cf_set_precision(cf_problem* pb, int precision);
  * 4 = dense map on the tensor cores (TF32 products, FP32 accumulation; the
  * automatic choice where it exists, else the same as 0); FP64 1 = one warp
  * per patch, 2 = one block per patch.  family CF_VAR_CUT (cut-patch step,
- * 3D degree 2): 1 = each patch's record (packed inverse and cut-cell rows)
- * brought into shared memory by a TMA bulk copy (the automatic choice),
- * 2 = records read from global memory.  family CF_VAR_OPERATOR (operator
+ * 3D degree 2; one warp per patch, records read from global memory):
+ * 1 = each patch's record (inverse and cut-cell rows) prefetched into L2 by
+ * a bulk prefetch when its loads are issued (the automatic choice), 2 = no
+ * prefetch.  family CF_VAR_OPERATOR (operator
  * rows of nodes whose cells are all uncut): 1 = element-matrix form, 2 =
  * sum factorisation (the automatic choice in FP64).  variant 0 restores the
  * automatic choice.  The next
@@ -199,13 +200,13 @@ cf_status cf_set_precision(cf_problem* pb, int precision);
 typedef enum { CF_VAR_INTERIOR = 1, CF_VAR_CUT = 2, CF_VAR_OPERATOR = 3 } cf_variant_family;
 cf_status cf_set_kernel_variant(cf_problem* pb, int family, int variant);
 
-/* Polls the cut-patch kernel makes on its TMA copy's mbarrier before it
- * gives up (default 2^22).  A block that gives up records the failure, waits
- * (bounded, 2^22 polls) for its own copy to land, and skips its patch; the
- * next cf_solve / cf_solve_vcycle / cf_solve_gmres then returns CF_ETIMEOUT
- * and the handle stays usable.  A limit of 0 makes every wait give up at once
- * (a test of that path).  CF_EINVAL outside [0, 2^30] or on a host-only
- * handle. */
+/* Polls the tensor-core interior-patch kernel (mixed form, 3D) makes on the
+ * mbarrier of its tensor-core product before it gives up (default 2^22).  A
+ * block that gives up records the failure and waits (bounded, 2^22 polls)
+ * for its own product to complete before it reads it; the next cf_solve /
+ * cf_solve_vcycle / cf_solve_gmres then returns CF_ETIMEOUT and the handle
+ * stays usable.  A limit of 0 makes every wait give up at once (a test of
+ * that path).  CF_EINVAL outside [0, 2^30] or on a host-only handle. */
 cf_status cf_set_wait_limit(cf_problem* pb, int64_t polls);
 
 /* b = right-hand side of the manufactured solution u = prod_k sin(pi x_k),

@@ -140,7 +140,8 @@ class Problem:
         check(self._lib.cf_set_kernel_variant(self._h, family, variant))
 
     def set_wait_limit(self, polls):
-        """Polls of the cut-patch kernel's wait on its TMA copy (default 2^22)."""
+        """Polls of the tensor-core interior kernel's wait on its product
+        (default 2^22)."""
         check(self._lib.cf_set_wait_limit(self._h, int(polls)))
 
     # ---- finest-level calls ----------------------------------------------------------

@@ -230,29 +230,25 @@ __global__ void __launch_bounds__(32 * WARPS) kb_cut_solve(const LvlDesc<DIM, P,
   }
 }
 
-// Pipelined cut-patch step over the (instance, patch) work list: the device
-// body of k_cut_pipe (same prefetch, same arithmetic), with the next item's
-// loads in flight while a block computes the current one.  Uncut cells read
-// their instance's element matrix from global memory (instances differ in h).
-template <int DIM, int P, typename T>
-__global__ void __launch_bounds__(128) kb_cut_pipe(const LvlDesc<DIM, P, T>* __restrict__ D,
-                                                   const int* __restrict__ off, int K, int total, int colour,
-                                                   int slot_bytes, int* err) {
-  constexpr int NT = 128;
-  extern __shared__ __align__(16) unsigned char psm[];
-  __shared__ __align__(16) PipeStage<DIM, P, T> stage[2];
-  __shared__ PipeShared<DIM, P, T> sh;
-  __shared__ __align__(8) uint64_t bar[2];
-  if ((int)blockIdx.x >= total) return;
-  pipe_loop<DIM, P, T, NT>(
-      blockIdx.x, gridDim.x, total,
+// Cut-patch step over the (instance, patch) work list: the warp loop of
+// k_cut_warp (same loads, same arithmetic), one warp per item, records
+// prefetched into L2.
+template <int DIM, int P, typename T, int WPB>
+__global__ void __launch_bounds__(32 * WPB, cut_min_blocks<T>())
+    kb_cut_warp(const LvlDesc<DIM, P, T>* __restrict__ D, const int* __restrict__ off, int K, int total, int colour) {
+  extern __shared__ __align__(128) unsigned char wsm[];
+  __shared__ CutTables<DIM, P> tb;
+  cut_tables<DIM, P>(tb);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5;
+  warp_loop<DIM, P, T>(
+      blockIdx.x * WPB + warp, gridDim.x * WPB, total,
       [&](int it, const PipeLevel<T>*& lv, int& j) {
         const int i = find_inst(off, K, it);
         lv = &D[i].pl;
         j = D[i].cut_start[colour] + it - off[i];
       },
-      [&](const PipeLevel<T>* lv) -> const T* { return lv->op.Kref; }, psm, slot_bytes, stage, sh, bar, kTmaSpin,
-      err);
+      *reinterpret_cast<WarpStage<DIM, P, T>*>(wsm + (size_t)warp * warp_stage_bytes<DIM, P, T>()), tb, true);
 }
 
 // sum-factorised operator over the (instance, tile) work list: the tile body
@@ -464,10 +460,12 @@ class BatchGroup final : public BatchGroupBase {
     CUTMG_CUDA(cudaFuncSetAttribute(kb_apply_sf<DIM, P, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     SfGeo<DIM, P>::ELEMS * (int)sizeof(float)));
     if (!E::kWarpCut) {
-      CUTMG_CUDA(cudaFuncSetAttribute(kb_cut_pipe<DIM, P, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      2 * E::kRecSlotMax));
-      CUTMG_CUDA(cudaFuncSetAttribute(kb_cut_pipe<DIM, P, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      2 * E::kRecSlotMax));
+      CUTMG_CUDA(cudaFuncSetAttribute(kb_cut_warp<DIM, P, double, E::kCutWarps>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      E::kCutWarps * warp_stage_bytes<DIM, P, double>()));
+      CUTMG_CUDA(cudaFuncSetAttribute(kb_cut_warp<DIM, P, float, E::kCutWarps>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      E::kCutWarps * warp_stage_bytes<DIM, P, float>()));
     }
     CUTMG_CUDA(cudaMallocHost(&host_sc_, sizeof(double) * K_ * 16));
     rebuild_lists();
@@ -1002,18 +1000,12 @@ class BatchGroup final : public BatchGroupBase {
               D, wb.off, K_, wb.total, colour);
           count("batched boundary face moments");
         }
-        // record slot of the longest record among the instances at this depth
-        int maxrec = 0;
-        for (int i = 0; i < K_; ++i) {
-          const int l = DV[t].level[i];
-          if (l >= 1 && act_[i]) maxrec = std::max(maxrec, inst_[i]->com_[l].cut_maxrec[colour]);
-        }
-        const int cap = sizeof(T) == 8 ? E::kRecSlot64 : E::kRecSlot;
-        const int slot = std::min(cap, (int)((maxrec * sizeof(T) + 15) / 16 * 16));
+        constexpr int WPB = E::kCutWarps;
+        const int smem = WPB * warp_stage_bytes<DIM, P, T>();
         int nb = 0;
-        CUTMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kb_cut_pipe<DIM, P, T>, 128, 2 * slot));
-        const int gridc = std::max(1, std::min(w.total, std::max(1, nb) * sms_));
-        kb_cut_pipe<DIM, P, T><<<gridc, 128, 2 * slot, s>>>(D, w.off, K_, w.total, colour, slot, err_);
+        CUTMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kb_cut_warp<DIM, P, T, WPB>, 32 * WPB, smem));
+        const int gridc = std::max(1, std::min((w.total + WPB - 1) / WPB, std::max(1, nb) * sms_));
+        kb_cut_warp<DIM, P, T, WPB><<<gridc, 32 * WPB, smem, s>>>(D, w.off, K_, w.total, colour);
         count("batched cut patches");
       }
     }

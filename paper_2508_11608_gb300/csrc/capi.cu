@@ -724,14 +724,10 @@ cf_status cf_host_cut_patch(const cf_problem* pb, int level, int64_t j, int64_t*
     if (!L.inv_on_device) {
       std::memcpy(h_inv, &L.inv[L.cut_ioff[j]], sizeof(double) * L.cut_n[j] * L.cut_n[j]);
     } else {
-      // formed on the device: the packed lower triangle read back and unfolded
+      // formed on the device: read back from the FP64 record
       if (!pb->eng) return fail(CF_EINVAL, "cut-patch inverses of this handle live on a device that was not attached");
-      const int mm = L.cut_n[j];
-      std::vector<double> pk((size_t)mm * (mm + 1) / 2);
-      cf_status st = guarded([&] { pb->eng->cut_inverse(level, j, pk.data()); });
+      cf_status st = guarded([&] { pb->eng->cut_inverse(level, j, h_inv); });
       if (st != CF_OK) return st;
-      for (int i = 0; i < mm; ++i)
-        for (int c = 0; c <= i; ++c) h_inv[(size_t)i * mm + c] = h_inv[(size_t)c * mm + i] = pk[(size_t)i * (i + 1) / 2 + c];
     }
   }
   return CF_OK;

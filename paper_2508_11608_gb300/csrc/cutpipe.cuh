@@ -1,22 +1,23 @@
 // Cut-patch colour step (Sec. 3: dense local solver on cut patches) for
-// patch closures of more than 64 nodes (3D Q2), as one persistent kernel per
-// colour step with a two-stage pipeline per block: while a block computes
-// one patch, the data of its next patch are already in flight to the other
-// stage.
+// patch closures of more than 64 nodes (3D Q2): one warp per patch, several
+// independent warps per block, each with its own stage in shared memory, so
+// that no barrier of one patch holds back another and the loads of one
+// warp's patch overlap the arithmetic of the others.
 //
-// Per patch j the block needs
-//   * the closure of x and b (cp.async, one element per thread),
-//   * the DoF list, the row items and the cell kinds (cp.async),
-//   * its record: the explicit inverse packed by rows of its lower triangle
-//     and the rows of the cut-cell matrices its items use, one contiguous
-//     run, and its ghost-entry list; both by TMA bulk copies (cp.async.bulk)
-//     completing on one mbarrier,
+// Per patch j the warp stages (cp.async, one group)
+//   * the closure of x and b, one element per lane,
+//   * the DoF list, the row items, the cell kinds and its ghost-entry list,
 //   * the moments of the ghost faces on the boundary planes of its block
-//     (cp.async from its moment slots).
+//     (from its moment slots),
+// and reads its record from global memory: the explicit inverse (m x m)
+// and the rows of the cut-cell matrices its items use, stored by columns,
+// so that the lanes of a warp always read consecutive addresses.  The
+// record is prefetched into L2 by one bulk prefetch when the patch's loads
+// are issued.
 // Every ghost face in the row of a patch DoF is a face of an active cell that
 // contains the DoF, hence of a patch cell, so it lies on one of the 3 planes
 // per direction of the 2 x .. x 2 block (eq. "cutfem-ghost").  The faces on
-// the middle plane are formed inside the block from the staged closure
+// the middle plane are formed by the warp from the staged closure
 // (G_m = coef_m (Mhat x Mhat) J_m, J_m[t] = sum_i dvec_m[i] x(i, t) over the
 // 2p + 1 nodes across the face): all their nodes belong to active patch
 // cells, so no other patch of the colour writes them.  The faces on the two
@@ -28,8 +29,7 @@
 //
 // The ghost-entry list of a patch (built at setup) holds, for each DoF row,
 // the (face, node along the normal, tangential node) triples of the ghost
-// faces whose stencil contains the DoF; the rows and the local solve split
-// each DoF over 4 lanes, combined by shuffles in a fixed order.
+// faces whose stencil contains the DoF.
 #pragma once
 
 #include "kernels.cuh"
@@ -40,6 +40,7 @@ template <int DIM, int P>
 struct PipeGeo {
   static constexpr int C = 2 * P + 1;
   static constexpr int NB = Shape<DIM, P>::NB;
+  static constexpr int NBP = (NB + 3) / 4 * 4;  // padded row of a cell vector (16-byte rows)
   static constexpr int NCL = PatchGeo<DIM, P>::NCL;
   static constexpr int NCELL = 1 << DIM;
   static constexpr int NT = FaceGeo<DIM, P>::NT;  // nodes of a face, (p+1)^(d-1)
@@ -49,14 +50,14 @@ struct PipeGeo {
   static constexpr int NBF = DIM * 2 * HALF;      // faces on its boundary planes
   static constexpr int HALO = NBF * P * NT;       // the moments of those
   static constexpr int ITEMW = (NCELL * NB + 3) / 4;  // 32-bit words of the item list
-  static constexpr int GCAP = 1024;               // ghost-entry list entries staged (longer: global)
-  static constexpr int LANES = 4;                 // threads per DoF row in rows and solve
+  static constexpr int GCAP = 512;                // ghost-entry list entries staged (longer: global)
 };
 
-// ghost entry: bit of the face in the block mask (6 bits), node along the
-// normal (3 bits), tangential node (7 bits)
-__host__ __device__ constexpr uint16_t ghost_entry(int bit, int i, int t) {
-  return (uint16_t)(bit | (i << 6) | (t << 9));
+// ghost entry: moment slot of the face in the patch (6 bits: the boundary-
+// plane faces first, then the middle-plane faces, each in mask-bit order),
+// node along the normal (3 bits), tangential node (7 bits)
+__host__ __device__ constexpr uint16_t ghost_entry(int slot, int i, int t) {
+  return (uint16_t)(slot | (i << 6) | (t << 9));
 }
 
 // device arrays of one level for the pipelined cut kernel
@@ -76,6 +77,8 @@ struct PipeLevel {
   const uint64_t* gmask;    // ghost faces of the block planes
   const int64_t* roff;      // record offsets (entries); roff[j + 1] - roff[j] = length
   const T* rec;             // records
+  const T* kp;              // [NB][NBP] uncut element matrix for h = 1, rows padded to NBP
+  T ksc;                    // h^(d-2): the level's uncut element matrix is ksc kp
   const int* gboff;         // first boundary-face moment slot of each patch
   const T* Gb;              // boundary-face moment slots, P (p+1)^(d-1) values each
   const int* geoff;         // ghost-entry lists: [geoff[j], geoff[j + 1]) in gent (16-byte aligned)
@@ -92,31 +95,167 @@ __host__ __device__ constexpr uint64_t pipe_bnd_bits() {
   return m;
 }
 
+// One warp's stage: the patch's closure and lists, and the scratch of its
+// residual.  The record stays in global memory (read with coalesced loads).
 template <int DIM, int P, typename T>
-struct PipeStage {
+struct WarpStage {
   using G = PipeGeo<DIM, P>;
   T x[G::NCL];
   T b[G::NCL];
-  T halo[G::HALO];
+  __align__(16) T xc[G::NCELL][G::NBP];  // x on the nodes of each patch cell (cell order)
+  // face moments G_m[t]: the block-boundary faces first (the staged slots),
+  // then the middle-plane faces (formed here), each in mask-bit order
+  __align__(16) T U[G::NFACE][P][G::NT];
+  T part[G::NCELL][G::NB];               // cell row products of the items
+  __align__(16) T r[(G::NCL + 3) / 4 * 4];  // residual of the patch rows (zero-padded to 4)
+  T dv[P][2 * P + 1];                    // dvec of the level being worked on
   int mem[G::NCL];
   uint32_t item[G::ITEMW];
   int pk[G::NCELL];
+  int flist[G::NIF];
   __align__(16) uint16_t gl[G::GCAP];
-  uint64_t gmask;
-  const T* recp;         // the record: the stage's slot or global memory
-  const uint16_t* glp;   // the ghost-entry list: gl or global memory
-  int vert, m, nit;
 };
 
+// bytes of one warp's stage, a multiple of 128
 template <int DIM, int P, typename T>
-struct PipeShared {
-  using G = PipeGeo<DIM, P>;
-  T part[G::NCELL][G::NB];
-  T r[G::NCL];
-  T J[G::NIF][P][G::NT];
-  T Gm[G::NIF][P][G::NT];
-  int flist[G::NIF];
+__host__ __device__ constexpr int warp_stage_bytes() {
+  return (int)((sizeof(WarpStage<DIM, P, T>) + 127) / 128 * 128);
+}
+
+// Per-lane constants of the record kernel, per level (reloaded when a warp
+// moves to another level): the face-mass rows of the lane's tangential node,
+// the penalty coefficients, the scale of the uncut element matrix and the
+// lattice sizes.
+template <int DIM, int P, typename T>
+struct WarpLane {
+  T mh0[P + 1], mh1[P + 1];
+  T cf[P];
+  T ksc;           // h^(d-2), the scale of the uncut element matrix
+  int n, np;       // lattice nodes and vertices per direction
+  float rnp;       // 1 / np, for the vertex decode
+  bool fdiv;       // whether every packed vertex is below 2^24 (exact in FP32)
+  const void* lv;  // the level descriptor the constants came from
 };
+
+// Level-independent tables of a block, in shared memory: per closure node o
+// the cell-local index of o in each patch cell (byte sc; 0xff: not in that
+// cell) and its closure coordinates (4 bits per direction); per entry of
+// the cell vectors the closure index | (cell-vector index << 16).
+template <int DIM, int P>
+struct CutTables {
+  using G = PipeGeo<DIM, P>;
+  uint64_t cpt[G::NCL];
+  int uc[G::NCL];
+  int xcm[G::NCELL * G::NB];
+};
+
+// The closure's first lattice node c0 = p (v - 1) of the patch at packed
+// vertex q = v_0 + np (v_1 + np v_2), its lattice index, and whether the
+// closure lies inside the lattice.  The divisions by np go through a float
+// reciprocal when q < 2^24 (q exact in FP32, the quotient off by at most
+// one and corrected from the remainder).
+struct PatchPos {
+  int c0[3];
+  int base;
+  bool inside;
+};
+__device__ __forceinline__ int div_np(int q, int np, float rnp, bool fast) {
+  if (!fast) return q / np;
+  int t = (int)((float)q * rnp);
+  const int r = q - t * np;
+  if (r < 0) --t;
+  else if (r >= np) ++t;
+  return t;
+}
+template <int DIM, int P, typename T>
+__device__ __forceinline__ PatchPos patch_pos(int vert, const WarpLane<DIM, P, T>& wl) {
+  PatchPos pp;
+  pp.base = 0;
+  pp.inside = true;
+  pp.c0[0] = pp.c0[1] = pp.c0[2] = 0;
+  int q = vert, stn = 1;
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) {
+    const int qn = k + 1 < DIM ? div_np(q, wl.np, wl.rnp, wl.fdiv) : 0;
+    const int v = k + 1 < DIM ? q - qn * wl.np : q;
+    q = qn;
+    pp.c0[k] = P * (v - 1);
+    pp.base += pp.c0[k] * stn;
+    stn *= wl.n;
+    if (pp.c0[k] < 0 || pp.c0[k] + 2 * P >= wl.n) pp.inside = false;
+  }
+  return pp;
+}
+
+// the per-level constants of level op (all 32 lanes; ends with __syncwarp)
+template <int DIM, int P, typename T>
+__device__ __forceinline__ void warp_lane_level(WarpLane<DIM, P, T>& wl, WarpStage<DIM, P, T>& st,
+                                                const OpArgs<T>& op, T ksc, const void* lv, int lane) {
+  using G = PipeGeo<DIM, P>;
+#pragma unroll
+  for (int mm = 0; mm < P; ++mm) wl.cf[mm] = op.coef[mm];
+  const int t = lane % G::NT, t0 = t % (P + 1), t1 = t / (P + 1) % (P + 1);
+#pragma unroll
+  for (int s = 0; s <= P; ++s) {
+    wl.mh0[s] = op.Mhat[t0][s];
+    wl.mh1[s] = op.Mhat[t1][s];
+  }
+  if (lane < P * (2 * P + 1)) st.dv[lane / (2 * P + 1)][lane % (2 * P + 1)] = op.dvec[lane / (2 * P + 1)][lane % (2 * P + 1)];
+  wl.ksc = ksc;
+  wl.n = op.n;
+  wl.np = op.N + 1;
+  wl.rnp = 1.0f / (float)wl.np;
+  {
+    int64_t nv = 1;
+    for (int k = 0; k < DIM; ++k) nv *= wl.np;
+    wl.fdiv = nv <= (int64_t(1) << 24);
+  }
+  wl.lv = lv;
+  __syncwarp();
+}
+
+// the block's tables (all threads; the caller synchronises)
+template <int DIM, int P>
+__device__ __forceinline__ void cut_tables(CutTables<DIM, P>& tb) {
+  using G = PipeGeo<DIM, P>;
+  constexpr int C = G::C;
+  for (int o = threadIdx.x; o < G::NCL; o += blockDim.x) {
+    int oc[3] = {0, 0, 0}, u = o, code = 0;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+      oc[k] = u % C;
+      u /= C;
+      code |= oc[k] << (4 * k);
+    }
+    uint64_t tab = ~0ull;
+#pragma unroll
+    for (int sc = 0; sc < G::NCELL; ++sc) {
+      int jj = 0, jst = 1;
+      bool in = true;
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) {
+        const int a = oc[k] - P * ((sc >> k) & 1);
+        if (a < 0 || a > P) in = false;
+        jj += a * jst;
+        jst *= P + 1;
+      }
+      if (in) tab = (tab & ~(0xffull << (8 * sc))) | ((uint64_t)jj << (8 * sc));
+    }
+    tb.cpt[o] = tab;
+    tb.uc[o] = code;
+  }
+  for (int idx = threadIdx.x; idx < G::NCELL * G::NB; idx += blockDim.x) {
+    const int sc = idx / G::NB, q = idx - sc * G::NB;
+    int o = 0, st = 1, qq = q;
+#pragma unroll
+    for (int kk = 0; kk < DIM; ++kk) {
+      o += (P * ((sc >> kk) & 1) + qq % (P + 1)) * st;
+      qq /= P + 1;
+      st *= C;
+    }
+    tb.xcm[idx] = o | ((sc * G::NBP + q) << 16);
+  }
+}
 
 struct PipeMeta {
   int vert, m, mo, io, nit, gb, g0, g1;
@@ -141,77 +280,61 @@ __device__ __forceinline__ PipeMeta pipe_meta(const PipeLevel<T>& L, int j) {
   return t;
 }
 
-// whether patch M's record goes through a shared-memory slot of slot_bytes,
-// and whether its ghost-entry list goes into the stage
-template <typename T>
-__device__ __forceinline__ bool pipe_tma(const PipeMeta& M, int slot_bytes) {
-  const int64_t len = M.r1 - M.r0;
-  return len > 0 && (size_t)len * sizeof(T) <= (size_t)slot_bytes;
-}
+// whether patch M's ghost-entry list goes into the stage
 template <int DIM, int P>
-__device__ __forceinline__ bool pipe_gl_tma(const PipeMeta& M) {
+__device__ __forceinline__ bool pipe_gl_staged(const PipeMeta& M) {
   return M.g1 - M.g0 <= PipeGeo<DIM, P>::GCAP;
 }
 
-// one expected-bytes arrival on the mbarrier (always made, also for zero
-// bytes, so that every stage's phase completes once per prefetch), then the
-// bulk copies that complete it
-__device__ __forceinline__ void mbar_expect(uint64_t* bar, uint32_t bytes) {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
-__device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+// bulk prefetch of bytes (a multiple of 16) at a 16-byte aligned address into L2
+__device__ __forceinline__ void prefetch_l2(const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 
-// Issue every load of patch j into stage `st` (cp.async, one group per call;
-// the record when it fits `slot_bytes` and the ghost-entry list when it
-// fits the stage, by TMA on `bar`).  All threads call it.
-template <int DIM, int P, typename T, int NT>
-__device__ __forceinline__ void pipe_prefetch(const PipeLevel<T>& L, const PipeMeta& M, int j,
-                                              PipeStage<DIM, P, T>& st, T* slot, int slot_bytes, uint64_t* bar) {
+// Issue every load of patch j into the warp's stage by cp.async (one
+// group): the closure of x and b, the DoF list, items, cell kinds, the
+// boundary-face moments and (when it fits the stage) the ghost-entry list;
+// with `prefetch`, lane 0 also starts a bulk prefetch of the patch's record
+// into L2, read later by the row products and the solve.  All 32 lanes call
+// it, after the warp is done with the previous patch.
+template <int DIM, int P, typename T>
+__device__ __forceinline__ void warp_issue(const PipeLevel<T>& L, const PipeMeta& M, const PatchPos& pp, int j,
+                                           WarpStage<DIM, P, T>& st, const WarpLane<DIM, P, T>& wl,
+                                           const CutTables<DIM, P>& tb, bool prefetch, int lane) {
   using G = PipeGeo<DIM, P>;
-  constexpr int C = G::C;
-  const int tid = threadIdx.x, n = L.op.n, np = L.op.N + 1;
-  int v[3] = {0, 0, 0};
-  {
-    int q = M.vert;
-#pragma unroll
-    for (int k = 0; k < DIM; ++k) {
-      v[k] = q % np;
-      q /= np;
-    }
+  const int n = wl.n;
+  if (prefetch && lane == 0 && M.r1 > M.r0) prefetch_l2(L.rec + M.r0, (uint32_t)((M.r1 - M.r0) * sizeof(T)));
+  if (pipe_gl_staged<DIM, P>(M)) {
+    // lists are 16-byte aligned runs of a multiple of 8 entries
+    const int nch = (M.g1 - M.g0) / 8;
+    for (int w = lane; w < nch; w += 32) cp_async16(&st.gl[8 * w], L.gent + M.g0 + 8 * w);
   }
-  const bool tma = pipe_tma<T>(M, slot_bytes), gtma = pipe_gl_tma<DIM, P>(M);
-  if (tid == 0) {
-    st.vert = M.vert;
-    st.m = M.m;
-    st.nit = M.nit;
-    st.gmask = M.gmask;
-    st.recp = tma ? slot : L.rec + M.r0;
-    st.glp = gtma ? st.gl : L.gent + M.g0;
-    const uint32_t rb = tma ? (uint32_t)((M.r1 - M.r0) * sizeof(T)) : 0u;
-    const uint32_t gb = gtma ? (uint32_t)((M.g1 - M.g0) * sizeof(uint16_t)) : 0u;
-    mbar_expect(bar, rb + gb);
-    if (rb) bulk_copy(slot, L.rec + M.r0, rb, bar);
-    if (gb) bulk_copy(st.gl, L.gent + M.g0, gb, bar);
-  }
-  for (int e = tid; e < G::NCL; e += NT) {
-    int u = e, c[3] = {0, 0, 0};
+  // a closure inside the lattice needs no per-node test
+  const int* c0 = pp.c0;
+  const int base = pp.base;
+  const bool inside = pp.inside;
+  for (int e = lane; e < G::NCL; e += 32) {
+    const int code = tb.uc[e];
+    int rel = 0, stn = 1;
     bool in = true;
 #pragma unroll
-    for (int k = 0; k < DIM; ++k) {
-      c[k] = P * (v[k] - 1) + u % C;
-      u /= C;
-      if (c[k] < 0 || c[k] >= n) in = false;
+    for (int kk = 0; kk < DIM; ++kk) {
+      const int u = (code >> (4 * kk)) & 15;
+      rel += u * stn;
+      stn *= n;
+      if (!inside) {
+        const int c = c0[kk] + u;
+        if (c < 0 || c >= n) in = false;
+      }
     }
     if (in) {
-      const int o = lat_index<DIM>(c, n);
+      const int o = base + rel;
       cp_async_elem(&st.x[e], L.x + o);
       cp_async_elem(&st.b[e], L.b + o);
     } else {
@@ -220,288 +343,285 @@ __device__ __forceinline__ void pipe_prefetch(const PipeLevel<T>& L, const PipeM
     }
     if (e < M.m) cp_async_elem(&st.mem[e], L.members + M.mo + e);
   }
-  for (int w = tid; w < (M.nit + 3) / 4; w += NT) cp_async_elem(&st.item[w], L.items + M.io + w);
-  if (tid < G::NCELL) cp_async_elem(&st.pk[tid], L.pk + (size_t)j * G::NCELL + tid);
-  // moments of the block-boundary ghost faces (one slot per set bit)
+  for (int w = lane; w < (M.nit + 3) / 4; w += 32) cp_async_elem(&st.item[w], L.items + M.io + w);
+  if (lane < G::NCELL) cp_async_elem(&st.pk[lane], L.pk + (size_t)j * G::NCELL + lane);
+  // moments of the block-boundary ghost faces (one slot per set bit), in
+  // 8-byte pieces (a slot holds an even number of FP32 values)
   const int nbv = __popcll(M.gmask & pipe_bnd_bits<DIM, P>()) * P * G::NT;
-  for (int w = tid; w < nbv; w += NT) cp_async_elem(&st.halo[w], L.Gb + (size_t)M.gb * P * G::NT + w);
+  const int nch = nbv * (int)sizeof(T) / 8;
+  const char* src = reinterpret_cast<const char*>(L.Gb + (size_t)M.gb * P * G::NT);
+  char* dst = reinterpret_cast<char*>(&st.U[0][0][0]);
+  for (int w = lane; w < nch; w += 32) cp_async8(dst + 8 * w, src + 8 * (size_t)w);
   asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
-// x at closure coordinate ck along k and tangential cell u, node t, for a
-// face of the middle plane
+// four consecutive read-only values from a 16-byte aligned global address
+__device__ __forceinline__ void ldg4(const float* p, float (&v)[4]) {
+  const float4 t = __ldg(reinterpret_cast<const float4*>(p));
+  v[0] = t.x;
+  v[1] = t.y;
+  v[2] = t.z;
+  v[3] = t.w;
+}
+__device__ __forceinline__ void ldg4(const double* p, double (&v)[4]) {
+  const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+  const double2 b = __ldg(reinterpret_cast<const double2*>(p + 2));
+  v[0] = a.x;
+  v[1] = a.y;
+  v[2] = b.x;
+  v[3] = b.y;
+}
+
+// four consecutive values from a 16-byte aligned address (shared or global)
+__device__ __forceinline__ void ld4(const float* p, float (&v)[4]) {
+  const float4 t = *reinterpret_cast<const float4*>(p);
+  v[0] = t.x;
+  v[1] = t.y;
+  v[2] = t.z;
+  v[3] = t.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double (&v)[4]) {
+  const double2 a = *reinterpret_cast<const double2*>(p);
+  const double2 b = *reinterpret_cast<const double2*>(p + 2);
+  v[0] = a.x;
+  v[1] = a.y;
+  v[2] = b.x;
+  v[3] = b.y;
+}
+
+// One patch from a filled stage, by one warp:
+//   1. x on the nodes of each patch cell (cell vectors, padded to NBP);
+//   2. G_m of the middle-plane ghost faces, NT lanes per face: lane t forms
+//      J_m[t] = sum_i dvec_m[i] x(i, t) across the face, then the face mass
+//      Mhat x Mhat in 1D passes by shuffles inside the lane group, times
+//      coef_m;  and one lane per item: the cell row (record, or the uncut
+//      element matrix for h = 1 times h^(d-2); 16-byte loads through the
+//      read-only path) times the cell vector;
+//   3. residual of the patch rows, one lane per row: b - (cell parts in cell
+//      order, then the row's ghost entries in list order);
+//   4. delta = A_j^{-1} r, one lane per row, reading its row of the inverse
+//      and r four entries at a time; x updated in place.
+// kp: the uncut element matrix for h = 1 (rows padded, global); tb: the
+// block's tables; rec: the record (global); gl: the ghost-entry list.  Products and solve rows run in independent partial
+// sums (fixed split, fixed order).
 template <int DIM, int P, typename T>
-__device__ __forceinline__ T pipe_x(const PipeStage<DIM, P, T>& st, int k, int u, int ck, int t) {
-  constexpr int C = 2 * P + 1;
-  int o = 0, st_ = 1, q = 0, tt = t;
-#pragma unroll
-  for (int kk = 0; kk < DIM; ++kk) {
-    int c;
-    if (kk == k) {
-      c = ck;
-    } else {
-      c = P * ((u >> q) & 1) + tt % (P + 1);
-      tt /= P + 1;
-      ++q;
-    }
-    o += c * st_;
-    st_ *= C;
-  }
-  return st.x[o];
-}
-
-// sum over the 4 lanes of a DoF row (lanes 4k .. 4k+3 of a warp), the same
-// order on every lane
-template <typename T>
-__device__ __forceinline__ T lane4_sum(T v) {
-  v += __shfl_xor_sync(0xffffffffu, v, 1);
-  v += __shfl_xor_sync(0xffffffffu, v, 2);
-  return v;
-}
-
-// One patch from a filled stage: ghost-face moments, residual rows, local
-// solve, x updated in place.  Kref: the level's uncut element matrix.
-template <int DIM, int P, typename T, int NT>
-__device__ __forceinline__ void pipe_compute(const PipeLevel<T>& L, const PipeStage<DIM, P, T>& st,
-                                             PipeShared<DIM, P, T>& sh, const T* __restrict__ Kref) {
+__device__ __forceinline__ void warp_compute(const T* __restrict__ kp, T* __restrict__ xg, int base,
+                                             WarpStage<DIM, P, T>& st, const WarpLane<DIM, P, T>& wl,
+                                             const CutTables<DIM, P>& tb, const T* __restrict__ rec,
+                                             const uint16_t* gl, const PipeMeta& M, int lane) {
   using G = PipeGeo<DIM, P>;
-  constexpr int C = G::C, NB = G::NB, NTF = G::NT, LN = G::LANES, ROWS = NT / LN;
-  const int tid = threadIdx.x, m = st.m, n = L.op.n, np = L.op.N + 1;
+  constexpr int C = G::C, NB = G::NB, NBP = G::NBP, NTF = G::NT;
+  constexpr int KR = (G::NCL + 31) / 32;  // rows per lane
   constexpr uint64_t bnd = pipe_bnd_bits<DIM, P>();
-  const uint64_t gm = st.gmask, gint = gm & ~bnd, gbnd = gm & bnd;
-  const int nf = __popcll(gint);
-  if (tid < G::NFACE && ((gint >> tid) & 1ull)) sh.flist[__popcll(gint & ((1ull << tid) - 1ull))] = tid;
-  __syncthreads();
-  // J_m[t] of the ghost faces of the middle planes, and the cell rows of the items
-  for (int w = tid; w < nf * P * NTF; w += NT) {
-    const int fi = w / (P * NTF), rem = w - fi * (P * NTF), mm = rem / NTF, t = rem - mm * NTF;
-    const int f = sh.flist[fi], u = f % G::HALF, k = f / G::HALF / 3;
-    T acc = T(0);
-#pragma unroll
-    for (int i = 0; i <= 2 * P; ++i) acc += L.op.dvec[mm][i] * pipe_x<DIM, P, T>(st, k, u, i, t);
-    sh.J[fi][mm][t] = acc;
+  const uint64_t gint = M.gmask & ~bnd;
+  const int nbf = __popcll(M.gmask & bnd), nf = __popcll(gint);
+  for (int f = lane; f < G::NFACE; f += 32)
+    if ((gint >> f) & 1ull) st.flist[__popcll(gint & ((1ull << f) - 1ull))] = f;
+  const int pkl = lane < G::NCELL ? st.pk[lane] : -2;
+  const uint32_t amask = __ballot_sync(0xffffffffu, pkl != -2);  // active patch cells
+  T* xc = &st.xc[0][0];
+  for (int idx = lane; idx < G::NCELL * G::NB; idx += 32) {
+    const int v = tb.xcm[idx];
+    xc[v >> 16] = st.x[v & 0xffff];
   }
-  const T* rows = st.recp + ((m * (m + 1) / 2 + 3) / 4 * 4);
-  const uint8_t* item = reinterpret_cast<const uint8_t*>(st.item);
-  for (int q = tid; q < st.nit; q += NT) {
-    const int it = item[q], sc = it / NB, jj = it - sc * NB;
-    const int pkv = st.pk[sc];
-    const T* row = pkv == -1 ? Kref + jj * NB : rows + (size_t)((pkv >> 8) + q - (pkv & 255)) * NB;
-    int base = 0, ost = 1;
-#pragma unroll
-    for (int k = 0; k < DIM; ++k) {
-      base += P * ((sc >> k) & 1) * ost;
-      ost *= C;
-    }
-    T acc = T(0);
-    if (DIM == 2) {
-#pragma unroll
-      for (int q1 = 0; q1 <= P; ++q1)
-#pragma unroll
-        for (int q0 = 0; q0 <= P; ++q0) acc += row[q0 + (P + 1) * q1] * st.x[base + q0 + C * q1];
-    } else {
-#pragma unroll
-      for (int q2 = 0; q2 <= P; ++q2)
-#pragma unroll
-        for (int q1 = 0; q1 <= P; ++q1)
-#pragma unroll
-          for (int q0 = 0; q0 <= P; ++q0)
-            acc += row[q0 + (P + 1) * (q1 + (P + 1) * q2)] * st.x[base + q0 + C * (q1 + C * q2)];
-    }
-    sh.part[sc][jj] = acc;
-  }
-  __syncthreads();
-  // G_m[t] = coef_m sum_t' (Mhat x Mhat)[t][t'] J_m[t']
-  for (int w = tid; w < nf * P * NTF; w += NT) {
-    const int fi = w / (P * NTF), rem = w - fi * (P * NTF), mm = rem / NTF, t = rem - mm * NTF;
-    const int t0 = t % (P + 1), t1 = t / (P + 1);
-    T acc = T(0);
-#pragma unroll
-    for (int s = 0; s < NTF; ++s) {
-      const T wgt = (DIM == 2) ? L.op.Mhat[t0][s] : L.op.Mhat[t0][s % (P + 1)] * L.op.Mhat[t1][s / (P + 1)];
-      acc += wgt * sh.J[fi][mm][s];
-    }
-    sh.Gm[fi][mm][t] = L.op.coef[mm] * acc;
-  }
-  __syncthreads();
-  // residual of the own rows, LN lanes per DoF: lane 0 the cell parts in
-  // cell order, every lane a strided share of the row's ghost entries
-  const uint16_t* gl = st.glp;
-  const int lane = tid % LN;
-  for (int e0 = 0; e0 < m; e0 += ROWS) {
-    const int e = e0 + tid / LN;
-    T acc = T(0);
-    if (e < m) {
-      if (lane == 0) {
-        int o[3] = {0, 0, 0}, u = st.mem[e];
-#pragma unroll
-        for (int k = 0; k < DIM; ++k) {
-          o[k] = u % C;
-          u /= C;
-        }
-#pragma unroll
-        for (int sc = 0; sc < G::NCELL; ++sc) {
-          int jj = 0, jst = 1;
-          bool in = st.pk[sc] != -2;
-#pragma unroll
-          for (int k = 0; k < DIM; ++k) {
-            const int a = o[k] - P * ((sc >> k) & 1);
-            if (a < 0 || a > P) in = false;
-            jj += a * jst;
-            jst *= (P + 1);
-          }
-          if (in) acc += sh.part[sc][jj];
-        }
-      }
-      for (int q = gl[e] + lane; q < gl[e + 1]; q += LN) {
-        const int en = gl[m + 1 + q], bit = en & 63, i = (en >> 6) & 7, t = en >> 9;
-        const uint64_t below = (1ull << bit) - 1ull;
-        const T* g = ((bnd >> bit) & 1ull) ? &st.halo[__popcll(gbnd & below) * P * NTF]
-                                            : &sh.Gm[__popcll(gint & below)][0][0];
-#pragma unroll
-        for (int mm = 0; mm < P; ++mm) acc += L.op.dvec[mm][i] * g[mm * NTF + t];
-      }
-    }
-    acc = lane4_sum(acc);
-    if (e < m && lane == 0) sh.r[e] = st.b[st.mem[e]] - acc;
-  }
-  __syncthreads();
-  // delta = A_j^{-1} r from the packed lower triangle, LN lanes per row; the
-  // new value from the staged closure value (no other patch of the colour
-  // writes this DoF)
-  const T* Ai = st.recp;
-  int v[3] = {0, 0, 0};
+  __syncwarp();
+  // 2a. middle-plane face moments
   {
-    int q = st.vert;
+    constexpr int FPR = 32 / NTF;
+    const int grp = lane / NTF, t = lane - grp * NTF, t0 = t % (P + 1), t1 = t / (P + 1) % (P + 1);
+    const int g0 = grp * NTF;
+    for (int f0 = 0; f0 < nf; f0 += FPR) {
+      const int fi = f0 + grp;
+      const bool act = grp < FPR && fi < nf;
+      T J[P];
 #pragma unroll
-    for (int k = 0; k < DIM; ++k) {
-      v[k] = q % np;
-      q /= np;
-    }
-  }
-  for (int e0 = 0; e0 < m; e0 += ROWS) {
-    const int e = e0 + tid / LN;
-    T acc = T(0);
-    if (e < m) {
-      const T* Re = Ai + e * (e + 1) / 2;
-      int c = lane;
-      for (; c <= e; c += LN) acc += Re[c] * sh.r[c];
-      for (; c < m; c += LN) acc += Ai[c * (c + 1) / 2 + e] * sh.r[c];
-    }
-    acc = lane4_sum(acc);
-    if (e < m && lane == 0) {
-      int u = st.mem[e], lc[3] = {0, 0, 0};
+      for (int mm = 0; mm < P; ++mm) J[mm] = T(0);
+      if (act) {
+        const int f = st.flist[fi], u = f % G::HALF, k = f / G::HALF / 3;
+        int o = 0, stc = 1, q = 0, tt = t, sk = 1;
 #pragma unroll
-      for (int k = 0; k < DIM; ++k) {
-        lc[k] = P * (v[k] - 1) + u % C;
-        u /= C;
+        for (int kk = 0; kk < DIM; ++kk) {
+          if (kk == k) {
+            sk = stc;
+          } else {
+            o += (P * ((u >> q) & 1) + tt % (P + 1)) * stc;
+            tt /= P + 1;
+            ++q;
+          }
+          stc *= C;
+        }
+#pragma unroll
+        for (int i = 0; i <= 2 * P; ++i) {
+          const T xv = st.x[o + i * sk];
+#pragma unroll
+          for (int mm = 0; mm < P; ++mm) J[mm] += st.dv[mm][i] * xv;
+        }
       }
-      L.x[lat_index<DIM>(lc, n)] = st.x[st.mem[e]] + acc;
+#pragma unroll
+      for (int mm = 0; mm < P; ++mm) {
+        T a = T(0);
+#pragma unroll
+        for (int s0 = 0; s0 <= P; ++s0) a += wl.mh0[s0] * __shfl_sync(0xffffffffu, J[mm], g0 + s0 + (P + 1) * t1);
+        T g = a;
+        if (DIM == 3) {
+          g = T(0);
+#pragma unroll
+          for (int s1 = 0; s1 <= P; ++s1) g += wl.mh1[s1] * __shfl_sync(0xffffffffu, a, g0 + t0 + (P + 1) * s1);
+        }
+        if (act) st.U[nbf + fi][mm][t] = wl.cf[mm] * g;
+      }
     }
   }
-  __syncthreads();
+  // 2b. cell rows of the items
+  const int m = M.m, MP = (m + 3) / 4 * 4;
+  {
+    const T* rows = rec + (size_t)m * MP;
+    const uint8_t* item = reinterpret_cast<const uint8_t*>(st.item);
+    for (int q = lane; q < M.nit; q += 32) {
+      const int it = item[q], sc = it / NB, jj = it - sc * NB;
+      const int pkv = st.pk[sc];
+      const bool unc = pkv == -1;
+      const T* row = unc ? kp + jj * NBP : rows + (size_t)((pkv >> 8) + q - (pkv & 255)) * NBP;
+      const T* xv = &st.xc[sc][0];
+      T acc[2] = {T(0), T(0)};  // entries of 4-groups 0, 2, 4, .. and 1, 3, 5, ..
+#pragma unroll
+      for (int c0 = 0; c0 < NBP; c0 += 4) {
+        T a4[4], x4[4];
+        ldg4(row + c0, a4);
+        ld4(xv + c0, x4);
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          if (c0 + c < NB) acc[(c0 / 4) & 1] += a4[c] * x4[c];
+      }
+      const T sum = acc[0] + acc[1];
+      st.part[sc][jj] = unc ? wl.ksc * sum : sum;
+    }
+  }
+  __syncwarp();
+  // 3. residual of the patch rows (lane + 32 k)
+#pragma unroll
+  for (int k = 0; k < KR; ++k) {
+    const int e = lane + 32 * k;
+    if (e >= m) {
+      if (e < MP) st.r[e] = T(0);
+      continue;
+    }
+    const int o = st.mem[e];
+    const uint64_t tab = tb.cpt[o];
+    T acc = T(0);
+#pragma unroll
+    for (int sc = 0; sc < G::NCELL; ++sc) {
+      const int jj = (int)((tab >> (8 * sc)) & 0xffu);
+      if (jj != 0xff && ((amask >> sc) & 1u)) acc += st.part[sc][jj];
+    }
+    const int q1 = gl[e + 1];
+    for (int q = gl[e]; q < q1; ++q) {
+      const int en = gl[m + 1 + q], slot = en & 63, i = (en >> 6) & 7, t = en >> 9;
+      const T* g = &st.U[slot][0][t];
+#pragma unroll
+      for (int mm = 0; mm < P; ++mm) acc += st.dv[mm][i] * g[mm * NTF];
+    }
+    st.r[e] = st.b[o] - acc;
+  }
+  __syncwarp();
+  // 4. local solve: delta_e = sum_c A^{-1}[e][c] r_c from row e of the
+  //    inverse (4 entries per load; zeros in the padding), columns in 4
+  //    partial sums by c mod 4
+  const int n = wl.n;
+#pragma unroll
+  for (int k = 0; k < KR; ++k) {
+    const int e = lane + 32 * k;
+    if (e >= m) break;
+    const T* Ae = rec + (size_t)e * MP;
+    T a[4] = {T(0), T(0), T(0), T(0)};
+    for (int c0 = 0; c0 < MP; c0 += 4) {
+      T a4[4], r4[4];
+      ldg4(Ae + c0, a4);
+      ld4(&st.r[c0], r4);
+#pragma unroll
+      for (int qq = 0; qq < 4; ++qq) a[qq] += a4[qq] * r4[qq];
+    }
+    const T acc = (a[0] + a[1]) + (a[2] + a[3]);
+    const int o = st.mem[e];
+    int u = o, off = 0, stn = 1;
+#pragma unroll
+    for (int kk = 0; kk < DIM; ++kk) {
+      off += (u % C) * stn;
+      u /= C;
+      stn *= n;
+    }
+    xg[base + off] = st.x[o] + acc;
+  }
+  __syncwarp();
 }
 
-// waits for stage s's loads (the newer group of cp.asyncs may stay in flight)
-// and for its mbarrier (ph bit s: the parity of stage s's next phase, flipped
-// here); false when the bounded wait ran out (the copies are then drained
-// within kTmaSpin polls)
-template <bool NEWER_PENDING>
-__device__ __forceinline__ bool pipe_wait(uint64_t* bar, uint32_t& ph, int s, int spin, int* err) {
-  if (NEWER_PENDING)
-    asm volatile("cp.async.wait_group 1;" ::: "memory");
-  else
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-  const uint32_t parity = (ph >> s) & 1u;
-  bool ok = mbar_wait(bar, parity, spin);
-  if (!ok) {
-    atomicExch(err, 1);
-    mbar_wait(bar, parity, kTmaSpin);
-  }
-  ph ^= 1u << s;
-  __syncthreads();
-  return ok;
-}
-
-// The pipelined loop of one block over the work items it, it + step, ..
-// below total.  locate(item, level, patch) gives an item's level descriptor
-// and patch; kref(level) its uncut element matrix.  Metadata run two items
-// ahead, data one item ahead.
-template <int DIM, int P, typename T, int NT, class Locate, class Kref>
-__device__ __forceinline__ void pipe_loop(int it, int step, int total, Locate&& locate, Kref&& kref,
-                                          unsigned char* psm, int slot_bytes, PipeStage<DIM, P, T>* stage,
-                                          PipeShared<DIM, P, T>& sh, uint64_t* bar, int spin, int* err) {
-  if (threadIdx.x == 0) {
-    mbar_init(&bar[0]);
-    mbar_init(&bar[1]);
-  }
-  __syncthreads();
-  uint32_t ph = 0;
-  int s = 0;
+// The loop of one warp over the work items it, it + step, .. below total.
+// locate(item, level, patch) gives an item's level descriptor and patch.
+// st: the warp's stage; tb: the block's tables.  Per item: issue the
+// loads, read the next item's metadata while they fly, wait for the
+// cp.async group, compute.
+template <int DIM, int P, typename T, class Locate>
+__device__ __forceinline__ void warp_loop(int it, int step, int total, Locate&& locate, WarpStage<DIM, P, T>& st,
+                                          const CutTables<DIM, P>& tb, bool prefetch) {
+  if (it >= total) return;
+  const int lane = threadIdx.x & 31;
+  WarpLane<DIM, P, T> wl;
+  wl.lv = nullptr;
   const PipeLevel<T>* Lc;
   int jc;
   locate(it, Lc, jc);
   PipeMeta cur = pipe_meta(*Lc, jc);
-  const PipeLevel<T>* Ln = Lc;
-  int jn = jc;
-  PipeMeta nxt = cur;
-  if (it + step < total) {
-    locate(it + step, Ln, jn);
-    nxt = pipe_meta(*Ln, jn);
-  }
-  pipe_prefetch<DIM, P, T, NT>(*Lc, cur, jc, stage[0], reinterpret_cast<T*>(psm), slot_bytes, &bar[0]);
-  for (; it < total; it += step, s ^= 1) {
-    const bool more = it + step < total;
-    // metadata of the item after next
-    const PipeLevel<T>* L2 = Ln;
-    int j2 = jn;
-    PipeMeta nn = nxt;
-    if (it + 2 * step < total) {
-      locate(it + 2 * step, L2, j2);
-      nn = pipe_meta(*L2, j2);
+  for (; it < total; it += step) {
+    if (wl.lv != Lc) warp_lane_level<DIM, P, T>(wl, st, Lc->op, Lc->ksc, Lc, lane);
+    const PatchPos pp = patch_pos<DIM, P, T>(cur.vert, wl);
+    warp_issue<DIM, P, T>(*Lc, cur, pp, jc, st, wl, tb, prefetch, lane);
+    const PipeLevel<T>* Ln = Lc;
+    int jn = jc;
+    PipeMeta nxt = cur;
+    if (it + step < total) {
+      locate(it + step, Ln, jn);
+      nxt = pipe_meta(*Ln, jn);
     }
-    if (more)
-      pipe_prefetch<DIM, P, T, NT>(*Ln, nxt, jn, stage[s ^ 1], reinterpret_cast<T*>(psm + (s ^ 1) * slot_bytes),
-                                   slot_bytes, &bar[s ^ 1]);
-    bool ok;
-    if (more)
-      ok = pipe_wait<true>(&bar[s], ph, s, spin, err);
-    else
-      ok = pipe_wait<false>(&bar[s], ph, s, spin, err);
-    if (__syncthreads_and(ok)) pipe_compute<DIM, P, T, NT>(*Lc, stage[s], sh, kref(Lc));
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncwarp();
+    const uint16_t* gl = pipe_gl_staged<DIM, P>(cur) ? st.gl : Lc->gent + cur.g0;
+    warp_compute<DIM, P, T>(Lc->kp, Lc->x, pp.base, st, wl, tb, Lc->rec + cur.r0, gl, cur, lane);
+    __syncwarp();
     Lc = Ln;
     jc = jn;
     cur = nxt;
-    Ln = L2;
-    jn = j2;
-    nxt = nn;
   }
 }
 
-// One colour step: patches j0 .. j0 + npatch - 1, block b takes b, b + grid,
-// ..; records of up to slot_bytes go through shared memory.
-template <int DIM, int P, typename T>
-__global__ void __launch_bounds__(128) k_cut_pipe(PipeLevel<T> L, int j0, int npatch, int slot_bytes, int* err,
-                                                  int spin) {
-  using G = PipeGeo<DIM, P>;
-  constexpr int NT = 128;
-  extern __shared__ __align__(16) unsigned char psm[];
-  __shared__ __align__(16) PipeStage<DIM, P, T> stage[2];
-  __shared__ PipeShared<DIM, P, T> sh;
-  __shared__ __align__(16) T sK[G::NB * G::NB];
-  __shared__ __align__(8) uint64_t bar[2];
+// resident blocks per SM the kernel is compiled for (registers)
+template <typename T>
+constexpr int cut_min_blocks() {
+  return sizeof(T) == 4 ? 3 : 2;
+}
+
+// One colour step: patches j0 .. j0 + npatch - 1, warp w of the grid takes
+// w, w + (warps of the grid), ..; with `prefetch` each record is prefetched
+// into L2 when its patch's loads are issued.  The level descriptor is
+// copied to shared memory once.
+template <int DIM, int P, typename T, int WPB>
+__global__ void __launch_bounds__(32 * WPB, cut_min_blocks<T>())
+    k_cut_warp(PipeLevel<T> L, int j0, int npatch, int prefetch) {
+  extern __shared__ __align__(128) unsigned char wsm[];
   __shared__ PipeLevel<T> sL;
-  if ((int)blockIdx.x >= npatch) return;
-  for (int i = threadIdx.x; i < G::NB * G::NB; i += NT) sK[i] = L.op.Kref[i];
-  if (threadIdx.x == 0) sL = L;  // the level's arrays and tables, read by every thread
+  __shared__ CutTables<DIM, P> tb;
+  if (threadIdx.x == 0) sL = L;
+  cut_tables<DIM, P>(tb);
+  __syncthreads();
   const PipeLevel<T>* Lp = &sL;
-  pipe_loop<DIM, P, T, NT>(
-      blockIdx.x, gridDim.x, npatch,
+  const int warp = threadIdx.x >> 5;
+  warp_loop<DIM, P, T>(
+      blockIdx.x * WPB + warp, gridDim.x * WPB, npatch,
       [&](int it, const PipeLevel<T>*& lv, int& j) {
         lv = Lp;
         j = j0 + it;
       },
-      [&](const PipeLevel<T>*) -> const T* { return sK; }, psm, slot_bytes, stage, sh, bar, spin, err);
+      *reinterpret_cast<WarpStage<DIM, P, T>*>(wsm + (size_t)warp * warp_stage_bytes<DIM, P, T>()), tb,
+      prefetch != 0);
 }
 
 }  // namespace cutmg
@@ -509,8 +629,9 @@ __global__ void __launch_bounds__(128) k_cut_pipe(PipeLevel<T> L, int j0, int np
 namespace cutmg {
 
 // Cut-patch inverses on the device, FP64 (the local solver's setup, Sec. 3):
-// for patch j, rec[roff[j] ..] holds the lower triangle of A_j by rows on
-// entry and that of A_j^{-1} on exit.  One block per patch (block-stride),
+// for patch j, rec[roff[j] ..] holds A_j by rows with row stride
+// MP = 4 ceil(m / 4) (symmetric; its lower triangle is read) on entry and
+// A_j^{-1} (both triangles, the same layout) on exit.  One block per patch (block-stride),
 // the matrix in shared memory with row stride ld >= m (dynamic, ld (ld + 1)
 // doubles): Cholesky A = L L^T (right-looking, L in the lower triangle),
 // W = L^{-1} by forward substitution, one column per thread (W's strictly
@@ -533,13 +654,13 @@ static __global__ void __launch_bounds__(128) k_patch_inverse(double* __restrict
   __shared__ int bad;
   const int tid = threadIdx.x, NT = blockDim.x;
   for (int j = blockIdx.x; j < npatch; j += gridDim.x) {
-    const int m = cnt[j];
+    const int m = cnt[j], mp = (m + 3) / 4 * 4;
     double* a = rec + roff[j];
     const int ne = m * (m + 1) / 2;
     if (tid == 0) bad = 0;
     for (int e = tid; e < ne; e += NT) {
       const int i = tri_row(e), c = e - i * (i + 1) / 2;
-      S[i * ld + c] = a[e];
+      S[i * ld + c] = a[(size_t)i * mp + c];
     }
     __syncthreads();
     for (int k = 0; k < m; ++k) {
@@ -575,7 +696,8 @@ static __global__ void __launch_bounds__(128) k_patch_inverse(double* __restrict
         const int i = tri_row(e), c = e - i * (i + 1) / 2;
         double s = (i == c ? Wd[i] : S[c * ld + i]) * Wd[i];
         for (int k = i + 1; k < m; ++k) s += S[i * ld + k] * S[c * ld + k];
-        a[e] = s;
+        a[(size_t)i * mp + c] = s;
+        a[(size_t)c * mp + i] = s;
       }
     }
     __syncthreads();

@@ -224,6 +224,8 @@ class Engine final : public EngineBase {
     float* tc_b = nullptr;  // the same map as the tensor-core B operand (TF32, core-matrix layout)
     T* rec = nullptr;       // cut-patch records of the pipelined kernel (packed inverse + cut rows)
     T* Gb = nullptr;        // moment slots of the block-boundary ghost faces
+    T* kp = nullptr;        // uncut element matrix for h = 1, rows padded to NBP (record kernel)
+    T ksc = T(1);           // h^(d-2): the uncut element matrix is ksc kp
     T* dinv = nullptr;  // Chebyshev smoother: 1 / diag(A_l) on the box (0 off the DoFs)
     T* xp = nullptr;    // Chebyshev smoother: previous iterate
     T *x, *b, *r;          // box vectors
@@ -258,10 +260,12 @@ class Engine final : public EngineBase {
     CUTMG_CUDA(cudaFuncSetAttribute(k_apply_sf<DIM, P, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     SfGeo<DIM, P>::ELEMS * (int)sizeof(float)));
     if (!kWarpCut) {
-      CUTMG_CUDA(cudaFuncSetAttribute(k_cut_pipe<DIM, P, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      2 * kRecSlotMax));
-      CUTMG_CUDA(cudaFuncSetAttribute(k_cut_pipe<DIM, P, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      2 * kRecSlotMax));
+      CUTMG_CUDA(cudaFuncSetAttribute(k_cut_warp<DIM, P, float, kCutWarps>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      kCutWarps * warp_stage_bytes<DIM, P, float>()));
+      CUTMG_CUDA(cudaFuncSetAttribute(k_cut_warp<DIM, P, double, kCutWarps>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      kCutWarps * warp_stage_bytes<DIM, P, double>()));
     }
     {
       int dev = 0;
@@ -288,9 +292,10 @@ class Engine final : public EngineBase {
   int64_t launches() const override { return launches_; }
   // family 1 = interior-patch step (FP32: 1 dense one patch per thread, 2 dense
   // two per thread, 3 dense split, 4 tensor cores; FP64: 1 warp per patch,
-  // 2 block per patch); family 2 = cut-patch step of the pipelined kernel (1
-  // records through shared memory by TMA, 2 records read from global
-  // memory).  0 restores the automatic choice.
+  // 2 block per patch); family 2 = cut-patch step of the record kernel (1
+  // records prefetched into L2, 2 no prefetch); family 3 = operator rows of
+  // plain nodes (1 element matrices, 2 sum factorisation).  0 restores the
+  // automatic choice.
   void set_variant(int family, int variant) override {
     if (family == 1) {
       if (variant < 0 || variant > 4) throw std::invalid_argument("interior variant must be 0..4");
@@ -306,12 +311,14 @@ class Engine final : public EngineBase {
     }
     drop_graphs();
   }
-  void cut_inverse(int l, int64_t j, double* h_packed) override {
+  void cut_inverse(int l, int64_t j, double* h_inv) override {
     if (kWarpCut || l < 1 || l >= n_levels()) throw std::invalid_argument("no cut-patch records on this level");
     const HostLevel& h = H_.levels[l];
-    const int m = h.cut_n[j];
-    CUTMG_CUDA(cudaMemcpy(h_packed, d64_[l].rec + h.cut_roff[j], sizeof(double) * m * (m + 1) / 2,
-                          cudaMemcpyDeviceToHost));
+    const int m = h.cut_n[j], mp = (m + 3) / 4 * 4;
+    std::vector<double> a((size_t)m * mp);
+    CUTMG_CUDA(cudaMemcpy(a.data(), d64_[l].rec + h.cut_roff[j], sizeof(double) * a.size(), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < m; ++i)
+      for (int c = 0; c < m; ++c) h_inv[(size_t)i * m + c] = a[(size_t)i * mp + c];
   }
   void set_wait_limit(int polls) override {
     if (polls < 0) throw std::invalid_argument("wait limit must be >= 0");
@@ -739,28 +746,30 @@ class Engine final : public EngineBase {
   static constexpr int kDotBlocks = 512;
  public:
   // when no patch can exceed 64 DoFs, (2p+1)^d <= 64 (2D Q1-Q3, 3D Q1), one
-  // warp solves a patch, one or two rows per lane; otherwise (3D Q2) the
-  // pipelined block kernel (k_cut_pipe) takes the patches.  The choice depends on (d, p) only, so a problem
-  // solved alone and inside a batch runs the same arithmetic.
+  // warp solves a patch, one or two rows per lane, from entry lists;
+  // otherwise (3D Q2) the warp-per-patch record kernel (k_cut_warp) takes
+  // the patches.  The choice depends on (d, p) only, so a problem solved
+  // alone and inside a batch runs the same arithmetic.
   static constexpr bool kWarpCut = (DIM == 2 ? (2 * P + 1) * (2 * P + 1) : (2 * P + 1) * (2 * P + 1) * (2 * P + 1)) <= 64;
-  // Pipelined cut kernel: record slots of the colour's longest record (16-byte
-  // multiple) up to kRecSlot (FP32) / kRecSlot64 bytes; longer records are
-  // read from global memory.  Variant 2 of the cut family reads every record
-  // from global memory (the same arithmetic).  The grid: every block the
-  // occupancy calculator lets reside, at most one per patch.
-  static constexpr int kRecSlot = 8 * 1024, kRecSlot64 = 12 * 1024, kRecSlotMax = 16 * 1024;
+  // Record kernel: kCutWarps independent warps per block, each with its own
+  // stage; the records are read from global memory, prefetched into L2 per
+  // patch (variant 1 of the cut family, the automatic choice) or not
+  // (variant 2; the same arithmetic).  The grid: every block the occupancy
+  // calculator lets reside, at most one warp per patch.
+  static constexpr int kCutWarps = 8;
   struct PipePlan {
-    int slot = 0, grid = 0;
+    int grid = 0, smem = 0, prefetch = 1;
   };
   template <typename T>
   PipePlan pipe_plan(const Common& c, int colour) const {
     PipePlan pl;
     const int cnt = c.cut_start[colour + 1] - c.cut_start[colour];
-    const int cap = sizeof(T) == 8 ? kRecSlot64 : kRecSlot;
-    pl.slot = var_cut_ == 2 ? 0 : std::min(cap, (int)((c.cut_maxrec[colour] * sizeof(T) + 15) / 16 * 16));
+    pl.prefetch = var_cut_ == 2 ? 0 : 1;
+    pl.smem = kCutWarps * warp_stage_bytes<DIM, P, T>();
     int nb = 0;
-    CUTMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cut_pipe<DIM, P, T>, 128, 2 * pl.slot));
-    pl.grid = std::max(1, std::min(cnt, std::max(1, nb) * sms_));
+    CUTMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cut_warp<DIM, P, T, kCutWarps>, 32 * kCutWarps,
+                                                             pl.smem));
+    pl.grid = std::max(1, std::min((cnt + kCutWarps - 1) / kCutWarps, std::max(1, nb) * sms_));
     return pl;
   }
   template <typename T>
@@ -780,6 +789,8 @@ class Engine final : public EngineBase {
     L.gmask = c.pgmask;
     L.roff = c.proff;
     L.rec = D.rec;
+    L.kp = D.kp;
+    L.ksc = D.ksc;
     L.gboff = c.gboff;
     L.Gb = D.Gb;
     L.geoff = c.geoff;
@@ -828,7 +839,7 @@ class Engine final : public EngineBase {
   bool use_sumfact() const {
     return var_op_ == 2 || (var_op_ == 0 && sizeof(T) == 8);
   }
-  int spin_ = kTmaSpin;            // polls of the cut kernel's first wait on its TMA copy
+  int spin_ = kTmaSpin;            // polls of the tensor-core interior kernel's wait on its MMA
 
   void drop_graphs() {
     for (auto& kv : graphs_) cudaGraphExecDestroy(kv.second.exec);
@@ -909,6 +920,14 @@ class Engine final : public EngineBase {
     D.op.face_id = c.face_id;
     D.op.G = pool_.alloc<T>((size_t)std::max<int64_t>(1, (int64_t)h.ghost_faces.size()) * P * (DIM == 2 ? P + 1 : (P + 1) * (P + 1)));
     D.op.Kref = pool_.upload<T>(h.Kref);
+    if (!kWarpCut) {
+      constexpr int NB = Shape<DIM, P>::NB, NBP = PipeGeo<DIM, P>::NBP;
+      std::vector<T> kp((size_t)NB * NBP, T(0));
+      for (int i = 0; i < NB; ++i)
+        for (int j = 0; j < NB; ++j) kp[(size_t)i * NBP + j] = (T)h.Kunit[(size_t)i * NB + j];
+      D.kp = pool_.upload<T>(kp);
+      D.ksc = (T)h.kscale;
+    }
     for (int m = 0; m < 3; ++m) {
       for (int i = 0; i < 7; ++i) D.op.dvec[m][i] = (T)h.dvec[m][i];
       D.op.coef[m] = (T)h.coef[m];
@@ -957,7 +976,7 @@ class Engine final : public EngineBase {
       if (!h.inv_on_device) {
         D.rec = pool_.upload<T>(h.rec);
       } else if (std::is_same<T, double>::value) {
-        // A_j packed in the records: inverted here, in FP64
+        // A_j (rows padded to 4) in the records: inverted here, in FP64
         D.rec = pool_.upload<T>(h.rec);
         device_inverses(h, reinterpret_cast<double*>(D.rec));
       } else {
@@ -1345,8 +1364,8 @@ class Engine final : public EngineBase {
       prof_mark(1, l, s);
       if (!kWarpCut) {
         const PipePlan pl = pipe_plan<T>(c, colour);
-        k_cut_pipe<DIM, P, T><<<pl.grid, 128, 2 * pl.slot, s>>>(pipe_level<T>(c, D, x, b), a0, cnt, pl.slot,
-                                                                    err_, spin_);
+        k_cut_warp<DIM, P, T, kCutWarps><<<pl.grid, 32 * kCutWarps, pl.smem, s>>>(pipe_level<T>(c, D, x, b), a0, cnt,
+                                                                                 pl.prefetch);
       } else {
         k_cut_solve<DIM, P, T, WARPS><<<blocks_for(cnt, WARPS), 32 * WARPS, 0, s>>>(
             D.op, x, b, c.cutv + a0, c.cutn + a0, c.cutmo + a0, c.cutio + a0, c.members, c.mnode, c.fofs,

@@ -59,7 +59,7 @@ class EngineBase {
   virtual void set_wait_limit(int polls) = 0;
   // packed lower triangle of cut patch j's inverse on level l (FP64, from the
   // device records; synchronises)
-  virtual void cut_inverse(int l, int64_t j, double* h_packed) = 0;
+  virtual void cut_inverse(int l, int64_t j, double* h_inv) = 0;  // m x m, row-major
   // kernel launches issued so far, and event timing of one kernel family
   virtual int64_t launches() const = 0;
   virtual void profile_start(int kind, int level) = 0;

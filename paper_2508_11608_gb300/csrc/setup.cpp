@@ -1004,8 +1004,12 @@ void cut_patch_inverses(const RefTables& R, HostLevel& L, bool invert) {
 
 // Records of the block cut kernel: ghost-face masks, per-cell pack offsets,
 // and (unless dry) the packed inverses and cut-cell row packs.
+// row stride of a record's inverse: m rounded up to 4 (16-byte rows)
+static inline int cut_n_pad(int m) { return (m + 3) / 4 * 4; }
+
 void cut_patch_records(HostLevel& L, bool dry) {
   const int d = L.d, p = L.p, N = L.N, NB = ipow(p + 1, d), NCELL = 1 << d;
+  const int NBP = (NB + 3) / 4 * 4;  // row stride of the cut rows (16-byte rows)
   if (ipow(2 * p + 1, d) <= 64) return;  // one warp per patch: the entry-list kernel
   const int64_t ncp = (int64_t)L.cut_vert.size();
   const int np = N + 1, ncol = 1 << d, half = 1 << (d - 1);
@@ -1066,7 +1070,7 @@ void cut_patch_records(HostLevel& L, bool dry) {
   }
   for (int64_t j = 0; j < ncp; ++j) {
     const int64_t m = L.cut_n[j];
-    const int64_t len = (m * (m + 1) / 2 + 3) / 4 * 4 + ((int64_t)rows[j] * NB + 3) / 4 * 4;
+    const int64_t len = m * ((m + 3) / 4 * 4) + (int64_t)rows[j] * NBP;
     L.cut_roff[j + 1] = L.cut_roff[j] + len;
   }
   L.n_rec = L.cut_roff[ncp];
@@ -1153,9 +1157,15 @@ void cut_patch_records(HostLevel& L, bool dry) {
             for (int u1 = (d == 3 ? ulo[1] : 0); u1 <= (d == 3 ? uhi[1] : 0); ++u1)
               for (int u0 = ulo[0]; u0 <= uhi[0]; ++u0) {
                 const int bit = (k * 3 + Lp) * half + u0 + 2 * u1;
-                if (!((L.cut_gmask[j] >> bit) & 1ull)) continue;
+                const uint64_t gm = L.cut_gmask[j], below = (1ull << bit) - 1ull;
+                if (!((gm >> bit) & 1ull)) continue;
+                // moment slot of the face: the block-boundary faces first
+                // (bit order), then the middle-plane faces (bit order)
+                const int slot = ((bnd_bits >> bit) & 1ull)
+                                     ? __builtin_popcountll(gm & bnd_bits & below)
+                                     : __builtin_popcountll(gm & bnd_bits) + __builtin_popcountll(gm & ~bnd_bits & below);
                 const int t = (tj[0] - p * u0) + (d == 3 ? (p + 1) * (tj[1] - p * u1) : 0);
-                ent.push_back((uint16_t)(bit | (i << 6) | (t << 9)));
+                ent.push_back((uint16_t)(slot | (i << 6) | (t << 9)));
               }
           }
         }
@@ -1171,13 +1181,15 @@ void cut_patch_records(HostLevel& L, bool dry) {
     L.cut_gent.resize(L.cut_geoff[ncp]);
     for (int64_t j = 0; j < ncp; ++j) std::copy(lists[j].begin(), lists[j].end(), L.cut_gent.begin() + L.cut_geoff[j]);
   }
-  // work model of the pipelined kernel (replaces the entry-list kernel's):
-  // flops 2 m^2 (packed solve) + 2 NB per row item + per ghost face of the
-  // block p NT (2 (2p+1) + 2 NT) for its moments + 2p per ghost entry of a
-  // row; scalars: the record (packed inverse + cut rows), the closures of x
-  // and b, the halo of the boundary ghost faces, x of the DoFs written;
-  // index bytes: DoF list, items, cell kinds, metadata.  The face moments of
-  // the colour step are part of this kernel (no separate launch).
+  // work model of the record kernel (replaces the entry-list kernel's):
+  // flops 2 m^2 (solve) + 2 NB per row item + per middle-plane ghost face
+  // p NT (2 (2p+1) + 2 NT) for its moments + 2p per ghost entry of a row;
+  // scalars, the algorithmic minimum: the inverse's m (m + 1) / 2 distinct
+  // entries (the stored record holds all m^2, rows padded) and the cut rows'
+  // NB entries each, the closures of x and b, the halo of the boundary ghost
+  // faces, x of the DoFs written; index bytes: DoF list, items, cell kinds,
+  // ghost-entry list, metadata.  The boundary-plane face moments are a
+  // separate launch (work_face).
   {
     const int NTf = ipow(p + 1, d - 1), NCL = ipow(2 * p + 1, d);
     uint64_t bnd_mask = 0;
@@ -1223,9 +1235,9 @@ void cut_patch_records(HostLevel& L, bool dry) {
     std::fill(out, L.rec.data() + L.cut_roff[j + 1], 0.0);
     const int m = L.cut_n[j];
     const double* A = &L.inv[(size_t)L.cut_ioff[j]];
-    for (int i = 0; i < m; ++i)
-      for (int c = 0; c <= i; ++c) out[(size_t)i * (i + 1) / 2 + c] = A[(size_t)i * m + c];
-    double* rp = out + ((int64_t)m * (m + 1) / 2 + 3) / 4 * 4;
+    const int MP = cut_n_pad(m);
+    for (int i = 0; i < m; ++i) std::copy(A + (size_t)i * m, A + (size_t)(i + 1) * m, out + (size_t)i * MP);
+    double* rp = out + (size_t)m * MP;
     const int i0 = L.cut_item_off[j], i1 = L.cut_item_off[j + 1];
     int r = 0;
     for (int q = i0; q < i1; ++q) {
@@ -1233,7 +1245,7 @@ void cut_patch_records(HostLevel& L, bool dry) {
       const int id = L.cut_cell[(size_t)j * NCELL + sc];
       if (id < 0) continue;
       const double* K = &L.cutmat[((size_t)id * NB + jj) * NB];
-      std::copy(K, K + NB, rp + (size_t)r * NB);
+      std::copy(K, K + NB, rp + (size_t)r * NBP);
       ++r;
     }
   }
@@ -1316,6 +1328,8 @@ void build_level(const SetupParams& prm, const RefTables& R, int N, HostLevel& L
   }
   // uncut stiffness, Kronecker form of 1D reference matrices
   L.Kref.assign(NB * NB, 0.0);
+  L.Kunit.assign(NB * NB, 0.0);
+  L.kscale = std::pow(h, d - 2);
   for (int i = 0; i < NB; ++i)
     for (int j = 0; j < NB; ++j) {
       int a[3], b[3];
@@ -1328,6 +1342,7 @@ void build_level(const SetupParams& prm, const RefTables& R, int N, HostLevel& L
           t *= (kk == k ? R.K1 : R.M1)[a[kk] * (p + 1) + b[kk]];
         s += t;
       }
+      L.Kunit[i * NB + j] = s;
       L.Kref[i * NB + j] = s * std::pow(h, d - 2);
     }
   // ghost-face tables

@@ -106,11 +106,12 @@ struct HostLevel {
   std::vector<int> cut_fo, cut_cell, cut_item_off;
   std::vector<uint8_t> cut_items;
   HostBlocks inv;                 // explicit FP64 inverses A_j^{-1}, row-major
-  // Per cut patch record of the block kernel ((2p+1)^d > 64, i.e. 3D Q2):
-  // rec[cut_roff[j] ..] = the inverse packed by rows of its lower triangle
-  // (entry (i, c), c <= i, at i (i + 1) / 2 + c; padded to 4 entries), then
-  // the rows of the cut-cell matrices its items use, NB entries each, in item
-  // order (padded to 4 entries); cut_roff[j + 1] - cut_roff[j] = its length.
+  // Per cut patch record of the record kernel ((2p+1)^d > 64, i.e. 3D Q2):
+  // rec[cut_roff[j] ..] = the inverse by rows with row stride MP = 4 ceil(m /
+  // 4) (entry (i, c) at i MP + c; zeros in the padding), then the rows of the
+  // cut-cell matrices its items use, in item order, each NB entries padded
+  // with zeros to NBP = 4 ceil(NB / 4) (16-byte rows in FP32 and FP64);
+  // cut_roff[j + 1] - cut_roff[j] = its length = m MP + rows NBP.
   // cut_pk[j * 2^d + s] = -2 inactive cell, -1 uncut, else (r0 << 8) | q0:
   // the first pack row r0 and first item q0 of cut patch cell s.
   // cut_gmask[j] bit (k * 3 + L) * 2^(d-1) + u: the face normal to k on
@@ -133,8 +134,11 @@ struct HostLevel {
   // Ghost-entry lists of the cut patches: patch j's run cut_gent[cut_geoff[j]
   // .. cut_geoff[j + 1]) (a multiple of 8 entries) holds m + 1 row offsets,
   // then per DoF row (member order) the ghost faces whose stencil contains
-  // the DoF: bit | (i << 6) | (t << 9), with bit the face's bit in
-  // cut_gmask[j], i the node along its normal, t the tangential node.
+  // the DoF: slot | (i << 6) | (t << 9), with i the node along the face's
+  // normal, t the tangential node and slot the face's moment slot in the
+  // patch: the set block-boundary bits of cut_gmask[j] first (bit order, the
+  // order of its cut_gboff slots), then the set middle-plane bits (bit
+  // order).
   std::vector<int> cut_geoff;
   std::vector<uint16_t> cut_gent;
   // algorithmic work per launch, used to report achieved FLOP/s and bytes:
@@ -143,6 +147,8 @@ struct HostLevel {
   std::vector<std::array<double, 3>> work_cut, work_cart, work_face;
   // reference tables
   std::vector<double> Kref;       // NB x NB stiffness of an uncut cell
+  std::vector<double> Kunit;      // the same for h = 1: Kref = kscale Kunit, kscale = h^(d-2)
+  double kscale = 1.0;
   std::vector<double> Mr, Kr;     // M x C rows of the two-cell 1D mass / stiffness
   std::vector<double> S, lam;     // fast-diagonalisation eigenvectors / values (M)
   std::vector<double> Wcart;      // (2p-1)^d x (2p+1)^d dense interior-patch update

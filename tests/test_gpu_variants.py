@@ -8,8 +8,8 @@ each one on the same small problems:
   interior step, FP32 (mixed form): dense map with 1 or 2 patches per thread,
     the split form with several threads per patch, and the tensor-core form;
   interior step, FP64: one warp per patch, one block per patch;
-  cut-patch step (3D Q2): each patch's record (packed inverse and cut-cell
-    rows) brought into shared memory by TMA, or read from global memory;
+  cut-patch step (3D Q2): each patch's record (inverse and cut-cell rows)
+    prefetched into L2 by a bulk prefetch, or not;
   operator rows of nodes with only uncut cells: element matrices or sum
     factorisation.
 Tolerances as in test_gpu_parity (FP64 1e-11 of the update, FP32 2e-4); the
@@ -150,12 +150,13 @@ def test_bad_variants_are_rejected(pair):
 
 
 def test_wait_limit_runs_out_and_the_handle_recovers():
-    """The cut-patch kernel's bounded wait on its TMA copy: with a limit of
-    zero polls every wait gives up at once (no hang: each block then drains
-    its own copy within the default bound and skips its patch), the solve
-    reports CF_ETIMEOUT, and with the default limit restored the same handle
-    solves to the usual result."""
+    """The tensor-core interior kernel's bounded wait on its product (mixed
+    form): with a limit of zero polls every wait gives up at once (no hang:
+    each block then waits for its own product within the default bound), the
+    solve reports CF_ETIMEOUT, and with the default limit restored the same
+    handle solves to the usual result."""
     pb = cm.Problem(**problem_kwargs("ball3d_q2_n16"))
+    pb.set_precision(cm.CF_MIXED)
     n = pb.n_dofs()
     b = torch.zeros(n, dtype=torch.float64, device=DEV)
     pb.rhs(b)
