@@ -126,15 +126,18 @@ FP32_PEAK_TFLOPS = 78.5
 # capture (dram__bytes_read.sum + dram__bytes_write.sum over a few launches of
 # one kernel on a small case; profiles/ holds the summary and the command).
 # The bench scales it by the algorithmic bytes of a launch of the timed
-# workload.  Valid only for the kernel source it was taken on.
+# workload.  Valid only for the kernel sources it was taken on (sha256 over
+# kernels.cuh and cutpipe.cuh).
 TRAFFIC = {}
 
 
 def _kernels_sha256():
     import hashlib
-    path = os.path.join(ROOT, "paper_2508_11608_gb300", "csrc", "kernels.cuh")
-    with open(path, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()
+    h = hashlib.sha256()
+    for name in ("kernels.cuh", "cutpipe.cuh"):
+        with open(os.path.join(ROOT, "paper_2508_11608_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
 
 
 def cpu_baseline(steps=1, threads=1):
@@ -210,10 +213,11 @@ def whole_job_rate(units_per_rank, world, ms_local, dist=None, device=None):
     return world * units_per_rank / (ms * 1e-3), ms
 
 
-def _timed_solves(pb, b, x, prec, steps, warmup, stream, flush, dist=None, profile_kernel=None):
+def _timed_solves(pb, b, x, prec, steps, warmup, stream, flush, dist=None, profile_kernel=None, level=-1):
     """CUDA-event time of `steps` solves after `warmup` untimed ones, L2
     flushed before each timed solve.  Returns (ms list, infos, launches,
-    profile)."""
+    profile); with profile_kernel, that family's launches (on `level`, or
+    all levels) are event-timed one by one."""
     import torch
     pb.set_precision(prec)
     for _ in range(warmup):
@@ -223,7 +227,7 @@ def _timed_solves(pb, b, x, prec, steps, warmup, stream, flush, dist=None, profi
         dist.barrier()
     torch.cuda.synchronize()
     if profile_kernel:
-        pb.profile_start(profile_kernel)
+        pb.profile_start(profile_kernel, level)
     l0 = pb.launch_count()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     infos = []
@@ -240,8 +244,11 @@ def _timed_solves(pb, b, x, prec, steps, warmup, stream, flush, dist=None, profi
     return [e0.elapsed_time(e1) for e0, e1 in ev], infos, launches, prof
 
 
-KERNEL_NAMES = {1: "k_cut_solve_cta", 2: "interior-patch step", 3: "k_apply_bulk", 4: "k_apply_bnd",
-                5: "k_face_moments"}
+# the kernel of each profiled family in the 3D Q2 workloads (FP32 V-cycle
+# of the mixed form / FP64 form)
+KERNEL_NAMES = {1: ("k_cut_warp", "k_cut_warp"), 2: ("k_smooth_tc", "k_smooth_cart"),
+                3: ("k_apply_bulk (V-cycle) + k_apply_sf (outer CG)", "k_apply_sf"),
+                4: ("k_apply_bnd", "k_apply_bnd"), 5: ("k_face_moments_to + k_face_moments", "k_face_moments_to + k_face_moments")}
 
 
 def _family_profile(cm, pb, b, x, prec, stream, flush):
@@ -273,13 +280,14 @@ def _roofline(cm, prof, prec, hbm):
         roof = {"bound": "hbm", "achieved": by_rate, "peak": hbm, "unit": "GB/s", "frac": by_rate / hbm,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs, of measured"}
     bytes_per_launch = pr["bytes"] / max(pr["launches"], 1)
-    tr = TRAFFIC.get((KERNEL_NAMES[top], "fp64" if prec == cm.CF_FP64 else "fp32"))
+    idx = 1 if prec == cm.CF_FP64 else 0
+    tr = TRAFFIC.get((KERNEL_NAMES[top][idx], "fp64" if prec == cm.CF_FP64 else "fp32"))
     traffic = None
     if tr and tr["kernels_sha256"] == _kernels_sha256():
         traffic = tr["dram_over_algorithmic"] * bytes_per_launch
-    roof.update({"kernel": KERNEL_NAMES[top], "traffic": traffic, "per_launch_ms": per_launch_ms,
+    roof.update({"kernel": KERNEL_NAMES[top][idx], "family": top, "traffic": traffic, "per_launch_ms": per_launch_ms,
                  "launches_timed": pr["launches"], "share_of_step": pr["share"],
-                 "shares": {KERNEL_NAMES[k]: round(prof[k]["share"], 4) for k in prof},
+                 "shares": {KERNEL_NAMES[k][idx]: round(prof[k]["share"], 4) for k in prof},
                  "flops_per_launch": pr["flops"] / max(pr["launches"], 1), "bytes_per_launch": bytes_per_launch,
                  "timing": "CUDA events on the launching stream around every launch of the family, "
                            "summed over 2 timed solves"})
@@ -361,6 +369,22 @@ def run_ours(args):
     prof64 = _family_profile(cm, pb, b, x, cm.CF_FP64, stream, flush)
     roof = _roofline(cm, prof32, cm.CF_MIXED, hbm)
     roof64 = _roofline(cm, prof64, cm.CF_FP64, hbm)
+    # the dominant family's finest-level launches alone (the average above
+    # includes the coarse levels' latency-bound launches)
+    for rf, prec in ((roof, cm.CF_MIXED), (roof64, cm.CF_FP64)):
+        fam = rf["family"]
+        _, _, _, pf = _timed_solves(pb, b, x, prec, 2, 1, stream, flush, profile_kernel=fam,
+                                    level=pb.n_levels - 1)
+        if pf["launches"] > 0 and pf["ms"] > 0:
+            sec = pf["ms"] * 1e-3
+            fin = {"level": pb.n_levels - 1, "launches_timed": pf["launches"],
+                   "per_launch_ms": pf["ms"] / pf["launches"]}
+            if rf["unit"] == "GB/s":
+                fin["achieved"] = pf["bytes"] / sec / 1e9
+            else:
+                fin["achieved"] = pf["flops"] / sec / 1e12
+            fin["frac"] = fin["achieved"] / rf["peak"]
+            rf["finest_level"] = fin
 
     # e2e through the C ABI with host buffers: H2D of b, solve, D2H of x
     pb.set_precision(cm.CF_FP64)

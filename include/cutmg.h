@@ -190,8 +190,11 @@ cf_status cf_set_precision(cf_problem* pb, int precision);
  * per patch, 2 = one block per patch.  family CF_VAR_CUT (cut-patch step,
  * 3D degree 2; one warp per patch, records read from global memory):
  * 1 = each patch's record (inverse and cut-cell rows) prefetched into L2 by
- * a bulk prefetch when its loads are issued (the automatic choice), 2 = no
- * prefetch.  family CF_VAR_OPERATOR (operator
+ * a bulk prefetch when its loads are issued, 2 = no prefetch, 3 = the next
+ * patch's record prefetched while the current patch is worked on, 4 = eight
+ * warps per block at every colour size (the automatic choice runs one warp
+ * per block for colours of fewer than 8 patches per SM).  family
+ * CF_VAR_OPERATOR (operator
  * rows of nodes whose cells are all uncut): 1 = element-matrix form, 2 =
  * sum factorisation (the automatic choice in FP64).  variant 0 restores the
  * automatic choice.  The next
@@ -281,6 +284,9 @@ cf_status cf_coarse_solve(cf_problem* pb, int precision, const double* d_b0,
  *    problem's.
  *  - The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *    The address is kept for the life of the process: do not call this entry
+ *    point after a cudaDeviceReset of that device (the kept address would no
+ *    longer name the array).
  *  - Every call on a device shares the array: calls that overlap on the GPU
  *    (different streams or threads without ordering) race and give wrong
  *    results.  Calls ordered on one stream are safe.

@@ -248,7 +248,8 @@ __global__ void __launch_bounds__(32 * WPB, cut_min_blocks<T>())
         lv = &D[i].pl;
         j = D[i].cut_start[colour] + it - off[i];
       },
-      *reinterpret_cast<WarpStage<DIM, P, T>*>(wsm + (size_t)warp * warp_stage_bytes<DIM, P, T>()), tb, true);
+      *reinterpret_cast<WarpStage<DIM, P, T>*>(wsm + (size_t)warp * warp_stage_bytes<DIM, P, T>()), tb,
+      kCutPrefetch);
 }
 
 // sum-factorised operator over the (instance, tile) work list: the tile body
@@ -362,11 +363,7 @@ static __global__ void __launch_bounds__(256) kb_dot_partial(const VecDesc* __re
   const double* a = static_cast<const double*>(Q.a);
   const double* b = static_cast<const double*>(Q.b);
   double acc = 0.0;
-  const int64_t tot = Q.R.size();
-  for (int64_t t = (int64_t)bk * blockDim.x + threadIdx.x; t < tot; t += (int64_t)kBatchDotBlocks * blockDim.x) {
-    const int64_t o = Q.R.at(t);
-    acc += a[o] * b[o];
-  }
+  Q.R.for_each_node_of(bk, kBatchDotBlocks, [&](int64_t o) { acc += a[o] * b[o]; });
   s[threadIdx.x] = acc;
   __syncthreads();
   for (int h = 128; h > 0; h >>= 1) {

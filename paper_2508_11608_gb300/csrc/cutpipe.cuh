@@ -263,20 +263,44 @@ struct PipeMeta {
   uint64_t gmask;
 };
 
+// The metadata of a patch spread over the lanes of a warp: lane f < 11
+// loads field f (PipeMeta's fields in declaration order, r0 = roff[j],
+// r1 = roff[j + 1], g1 = geoff[j + 1]); pipe_meta_gather rebuilds PipeMeta
+// in every lane by shuffles.  A warp that reads the next patch's metadata
+// while it works on the current one holds one 64-bit register per lane.
+constexpr int kMetaFields = 11;
 template <typename T>
-__device__ __forceinline__ PipeMeta pipe_meta(const PipeLevel<T>& L, int j) {
+__device__ __forceinline__ uint64_t pipe_meta_field(const PipeLevel<T>& L, int j, int f) {
+  switch (f) {
+    case 0: return (uint32_t)L.vert[j];
+    case 1: return (uint32_t)L.cnt[j];
+    case 2: return (uint32_t)L.moff[j];
+    case 3: return (uint32_t)L.ioff[j];
+    case 4: return (uint32_t)L.nit[j];
+    case 5: return (uint32_t)L.gboff[j];
+    case 6: return (uint32_t)L.geoff[j];
+    case 7: return (uint32_t)L.geoff[j + 1];
+    case 8: return (uint64_t)L.roff[j];
+    case 9: return (uint64_t)L.roff[j + 1];
+    case 10: return L.gmask[j];
+    default: return 0;
+  }
+}
+__device__ __forceinline__ PipeMeta pipe_meta_gather(uint64_t v) {
   PipeMeta t;
-  t.vert = L.vert[j];
-  t.m = L.cnt[j];
-  t.mo = L.moff[j];
-  t.io = L.ioff[j];
-  t.nit = L.nit[j];
-  t.r0 = L.roff[j];
-  t.r1 = L.roff[j + 1];
-  t.gmask = L.gmask[j];
-  t.gb = L.gboff[j];
-  t.g0 = L.geoff[j];
-  t.g1 = L.geoff[j + 1];
+  const unsigned full = 0xffffffffu;
+  const uint32_t lo = (uint32_t)v, hi = (uint32_t)(v >> 32);
+  t.vert = (int)__shfl_sync(full, lo, 0);
+  t.m = (int)__shfl_sync(full, lo, 1);
+  t.mo = (int)__shfl_sync(full, lo, 2);
+  t.io = (int)__shfl_sync(full, lo, 3);
+  t.nit = (int)__shfl_sync(full, lo, 4);
+  t.gb = (int)__shfl_sync(full, lo, 5);
+  t.g0 = (int)__shfl_sync(full, lo, 6);
+  t.g1 = (int)__shfl_sync(full, lo, 7);
+  t.r0 = (int64_t)(((uint64_t)__shfl_sync(full, hi, 8) << 32) | __shfl_sync(full, lo, 8));
+  t.r1 = (int64_t)(((uint64_t)__shfl_sync(full, hi, 9) << 32) | __shfl_sync(full, lo, 9));
+  t.gmask = ((uint64_t)__shfl_sync(full, hi, 10) << 32) | __shfl_sync(full, lo, 10);
   return t;
 }
 
@@ -297,6 +321,12 @@ __device__ __forceinline__ void prefetch_l2(const void* src, uint32_t bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 
+// lane 0: bulk prefetch of patch M's record into L2
+template <typename T>
+__device__ __forceinline__ void prefetch_record(const PipeLevel<T>& L, const PipeMeta& M, int lane) {
+  if (lane == 0 && M.r1 > M.r0) prefetch_l2(L.rec + M.r0, (uint32_t)((M.r1 - M.r0) * sizeof(T)));
+}
+
 // Issue every load of patch j into the warp's stage by cp.async (one
 // group): the closure of x and b, the DoF list, items, cell kinds, the
 // boundary-face moments and (when it fits the stage) the ghost-entry list;
@@ -309,7 +339,7 @@ __device__ __forceinline__ void warp_issue(const PipeLevel<T>& L, const PipeMeta
                                            const CutTables<DIM, P>& tb, bool prefetch, int lane) {
   using G = PipeGeo<DIM, P>;
   const int n = wl.n;
-  if (prefetch && lane == 0 && M.r1 > M.r0) prefetch_l2(L.rec + M.r0, (uint32_t)((M.r1 - M.r0) * sizeof(T)));
+  if (prefetch) prefetch_record(L, M, lane);
   if (pipe_gl_staged<DIM, P>(M)) {
     // lists are 16-byte aligned runs of a multiple of 8 entries
     const int nch = (M.g1 - M.g0) / 8;
@@ -389,6 +419,21 @@ __device__ __forceinline__ void ld4(const double* p, double (&v)[4]) {
   v[3] = b.y;
 }
 
+// lattice offset of closure node o (first coordinate fastest) from the
+// closure's first node, on a lattice of n nodes per direction
+template <int DIM, int P>
+__device__ __forceinline__ int closure_offset(int o, int n) {
+  constexpr int C = 2 * P + 1;
+  int off = 0, stn = 1;
+#pragma unroll
+  for (int kk = 0; kk < DIM; ++kk) {
+    off += (o % C) * stn;
+    o /= C;
+    stn *= n;
+  }
+  return off;
+}
+
 // One patch from a filled stage, by one warp:
 //   1. x on the nodes of each patch cell (cell vectors, padded to NBP);
 //   2. G_m of the middle-plane ghost faces, NT lanes per face: lane t forms
@@ -402,8 +447,9 @@ __device__ __forceinline__ void ld4(const double* p, double (&v)[4]) {
 //   4. delta = A_j^{-1} r, one lane per row, reading its row of the inverse
 //      and r four entries at a time; x updated in place.
 // kp: the uncut element matrix for h = 1 (rows padded, global); tb: the
-// block's tables; rec: the record (global); gl: the ghost-entry list.  Products and solve rows run in independent partial
-// sums (fixed split, fixed order).
+// block's tables; rec: the record (global); gl: the ghost-entry list.
+// Products and solve rows run in independent partial sums (fixed split,
+// fixed order).
 template <int DIM, int P, typename T>
 __device__ __forceinline__ void warp_compute(const T* __restrict__ kp, T* __restrict__ xg, int base,
                                              WarpStage<DIM, P, T>& st, const WarpLane<DIM, P, T>& wl,
@@ -475,6 +521,7 @@ __device__ __forceinline__ void warp_compute(const T* __restrict__ kp, T* __rest
   // 2b. cell rows of the items
   const int m = M.m, MP = (m + 3) / 4 * 4;
   {
+    // one item per lane: its row (16-byte loads) times the cell vector
     const T* rows = rec + (size_t)m * MP;
     const uint8_t* item = reinterpret_cast<const uint8_t*>(st.item);
     for (int q = lane; q < M.nit; q += 32) {
@@ -499,7 +546,7 @@ __device__ __forceinline__ void warp_compute(const T* __restrict__ kp, T* __rest
   }
   __syncwarp();
   // 3. residual of the patch rows (lane + 32 k)
-#pragma unroll
+#pragma unroll 1
   for (int k = 0; k < KR; ++k) {
     const int e = lane + 32 * k;
     if (e >= m) {
@@ -524,33 +571,34 @@ __device__ __forceinline__ void warp_compute(const T* __restrict__ kp, T* __rest
     st.r[e] = st.b[o] - acc;
   }
   __syncwarp();
-  // 4. local solve: delta_e = sum_c A^{-1}[e][c] r_c from row e of the
-  //    inverse (4 entries per load; zeros in the padding), columns in 4
-  //    partial sums by c mod 4
+  // 4. local solve delta = A^{-1} r, x updated in place: one lane per row
+  //    e, reading row e of the inverse (4 entries per load; zeros in the
+  //    padding), columns in 4 partial sums by c mod 4, in increasing c; the
+  //    loads of 4 groups of 4 columns issued before their products
   const int n = wl.n;
-#pragma unroll
+#pragma unroll 1
   for (int k = 0; k < KR; ++k) {
     const int e = lane + 32 * k;
     if (e >= m) break;
     const T* Ae = rec + (size_t)e * MP;
     T a[4] = {T(0), T(0), T(0), T(0)};
-    for (int c0 = 0; c0 < MP; c0 += 4) {
-      T a4[4], r4[4];
-      ldg4(Ae + c0, a4);
-      ld4(&st.r[c0], r4);
+    for (int c0 = 0; c0 < MP; c0 += 16) {
+      T a4[4][4];
 #pragma unroll
-      for (int qq = 0; qq < 4; ++qq) a[qq] += a4[qq] * r4[qq];
+      for (int u = 0; u < 4; ++u)
+        if (c0 + 4 * u < MP) ldg4(Ae + c0 + 4 * u, a4[u]);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (c0 + 4 * u >= MP) break;
+        T r4[4];
+        ld4(&st.r[c0 + 4 * u], r4);
+#pragma unroll
+        for (int qq = 0; qq < 4; ++qq) a[qq] += a4[u][qq] * r4[qq];
+      }
     }
     const T acc = (a[0] + a[1]) + (a[2] + a[3]);
     const int o = st.mem[e];
-    int u = o, off = 0, stn = 1;
-#pragma unroll
-    for (int kk = 0; kk < DIM; ++kk) {
-      off += (u % C) * stn;
-      u /= C;
-      stn *= n;
-    }
-    xg[base + off] = st.x[o] + acc;
+    xg[base + closure_offset<DIM, P>(o, n)] = st.x[o] + acc;
   }
   __syncwarp();
 }
@@ -559,10 +607,13 @@ __device__ __forceinline__ void warp_compute(const T* __restrict__ kp, T* __rest
 // locate(item, level, patch) gives an item's level descriptor and patch.
 // st: the warp's stage; tb: the block's tables.  Per item: issue the
 // loads, read the next item's metadata while they fly, wait for the
-// cp.async group, compute.
+// cp.async group, compute.  prefetch: 0 no record prefetch; 1 each record
+// prefetched into L2 when its patch's loads are issued; 2 the next item's
+// record prefetched as soon as its metadata is read, one patch ahead of its
+// use (the first item's at its issue).
 template <int DIM, int P, typename T, class Locate>
 __device__ __forceinline__ void warp_loop(int it, int step, int total, Locate&& locate, WarpStage<DIM, P, T>& st,
-                                          const CutTables<DIM, P>& tb, bool prefetch) {
+                                          const CutTables<DIM, P>& tb, int prefetch) {
   if (it >= total) return;
   const int lane = threadIdx.x & 31;
   WarpLane<DIM, P, T> wl;
@@ -570,39 +621,51 @@ __device__ __forceinline__ void warp_loop(int it, int step, int total, Locate&& 
   const PipeLevel<T>* Lc;
   int jc;
   locate(it, Lc, jc);
-  PipeMeta cur = pipe_meta(*Lc, jc);
+  PipeMeta cur = pipe_meta_gather(lane < kMetaFields ? pipe_meta_field(*Lc, jc, lane) : 0);
+  bool first = true;
   for (; it < total; it += step) {
     if (wl.lv != Lc) warp_lane_level<DIM, P, T>(wl, st, Lc->op, Lc->ksc, Lc, lane);
     const PatchPos pp = patch_pos<DIM, P, T>(cur.vert, wl);
-    warp_issue<DIM, P, T>(*Lc, cur, pp, jc, st, wl, tb, prefetch, lane);
+    warp_issue<DIM, P, T>(*Lc, cur, pp, jc, st, wl, tb, prefetch == 1 || (prefetch == 2 && first), lane);
+    first = false;
     const PipeLevel<T>* Ln = Lc;
     int jn = jc;
-    PipeMeta nxt = cur;
-    if (it + step < total) {
+    const bool more = it + step < total;
+    uint64_t nv = 0;  // this lane's field of the next patch's metadata
+    if (more) {
       locate(it + step, Ln, jn);
-      nxt = pipe_meta(*Ln, jn);
+      if (lane < kMetaFields) nv = pipe_meta_field(*Ln, jn, lane);
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncwarp();
+    if (more && prefetch == 2) {
+      const uint64_t r1 = __shfl_sync(0xffffffffu, nv, 9);
+      if (lane == 8 && r1 > nv) prefetch_l2(Ln->rec + nv, (uint32_t)((r1 - nv) * sizeof(T)));
+    }
     const uint16_t* gl = pipe_gl_staged<DIM, P>(cur) ? st.gl : Lc->gent + cur.g0;
     warp_compute<DIM, P, T>(Lc->kp, Lc->x, pp.base, st, wl, tb, Lc->rec + cur.r0, gl, cur, lane);
     __syncwarp();
+    if (more) cur = pipe_meta_gather(nv);
     Lc = Ln;
     jc = jn;
-    cur = nxt;
   }
 }
 
-// resident blocks per SM the kernel is compiled for (registers)
+// record prefetch mode of the automatic launch choice (warp_loop)
+constexpr int kCutPrefetch = 1;
+
+// resident blocks per SM the kernel is compiled for (registers): two blocks
+// of eight warps leave 128 registers per thread, which this kernel uses
+// without spilling (with three blocks the FP32 form spills; measured no
+// faster)
 template <typename T>
 constexpr int cut_min_blocks() {
-  return sizeof(T) == 4 ? 3 : 2;
+  return 2;
 }
 
 // One colour step: patches j0 .. j0 + npatch - 1, warp w of the grid takes
-// w, w + (warps of the grid), ..; with `prefetch` each record is prefetched
-// into L2 when its patch's loads are issued.  The level descriptor is
-// copied to shared memory once.
+// w, w + (warps of the grid), ..; `prefetch` as in warp_loop.  The level
+// descriptor is copied to shared memory once.
 template <int DIM, int P, typename T, int WPB>
 __global__ void __launch_bounds__(32 * WPB, cut_min_blocks<T>())
     k_cut_warp(PipeLevel<T> L, int j0, int npatch, int prefetch) {
@@ -621,7 +684,7 @@ __global__ void __launch_bounds__(32 * WPB, cut_min_blocks<T>())
         j = j0 + it;
       },
       *reinterpret_cast<WarpStage<DIM, P, T>*>(wsm + (size_t)warp * warp_stage_bytes<DIM, P, T>()), tb,
-      prefetch != 0);
+      prefetch);
 }
 
 }  // namespace cutmg

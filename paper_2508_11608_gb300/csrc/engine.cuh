@@ -53,26 +53,18 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_chebyshev(Region R, T* __restrict__ x, T* __restrict__ xp,
                                                    const T* __restrict__ r, const T* __restrict__ dinv, T c1,
                                                    T c2) {
-  const int64_t tot = R.size();
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t o = R.at(t);
+  R.for_each_node([&](int64_t o) {
     const T xo = x[o];
     x[o] = xo + c1 * (xo - xp[o]) + c2 * (dinv[o] * r[o]);
     xp[o] = xo;
-  }
+  });
 }
 
 // w = D^{-1} v over a region (the power iteration of the Chebyshev bound)
 template <typename T>
 __global__ void __launch_bounds__(256) k_scale_diag(Region R, const T* __restrict__ dinv, const T* __restrict__ v,
                                                     T* __restrict__ w) {
-  const int64_t tot = R.size();
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t o = R.at(t);
-    w[o] = dinv[o] * v[o];
-  }
+  R.for_each_node([&](int64_t o) { w[o] = dinv[o] * v[o]; });
 }
 
 // FP64 vector updates of the Krylov solvers (finest level, box layout)
@@ -80,24 +72,14 @@ __global__ void __launch_bounds__(256) k_scale_diag(Region R, const T* __restric
 static __global__ void __launch_bounds__(256) k_axpy(Region R, const double* __restrict__ as, double sign,
                                                      const double* __restrict__ x, double* __restrict__ y) {
   const double a = as ? sign * *as : sign;
-  const int64_t tot = R.size();
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t o = R.at(t);
-    y[o] += a * x[o];
-  }
+  R.for_each_node([&](int64_t o) { y[o] += a * x[o]; });
 }
 
 // y = x / sqrt(*nn) over a region (normalisation by a squared norm on the device)
 static __global__ void __launch_bounds__(256) k_scale_rsqrt(Region R, const double* __restrict__ nn,
                                                             const double* __restrict__ x, double* __restrict__ y) {
   const double a = 1.0 / sqrt(*nn);
-  const int64_t tot = R.size();
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t o = R.at(t);
-    y[o] = a * x[o];
-  }
+  R.for_each_node([&](int64_t o) { y[o] = a * x[o]; });
 }
 
 // Owns every device allocation of a problem.  Zero fills and uploads are
@@ -266,6 +248,10 @@ class Engine final : public EngineBase {
       CUTMG_CUDA(cudaFuncSetAttribute(k_cut_warp<DIM, P, double, kCutWarps>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       kCutWarps * warp_stage_bytes<DIM, P, double>()));
+      CUTMG_CUDA(cudaFuncSetAttribute(k_cut_warp<DIM, P, float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      warp_stage_bytes<DIM, P, float>()));
+      CUTMG_CUDA(cudaFuncSetAttribute(k_cut_warp<DIM, P, double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      warp_stage_bytes<DIM, P, double>()));
     }
     {
       int dev = 0;
@@ -293,7 +279,8 @@ class Engine final : public EngineBase {
   // family 1 = interior-patch step (FP32: 1 dense one patch per thread, 2 dense
   // two per thread, 3 dense split, 4 tensor cores; FP64: 1 warp per patch,
   // 2 block per patch); family 2 = cut-patch step of the record kernel (1
-  // records prefetched into L2, 2 no prefetch); family 3 = operator rows of
+  // records prefetched into L2 at issue, 2 no prefetch, 3 one patch ahead,
+  // 4 eight warps per block at every size); family 3 = operator rows of
   // plain nodes (1 element matrices, 2 sum factorisation).  0 restores the
   // automatic choice.
   void set_variant(int family, int variant) override {
@@ -301,7 +288,7 @@ class Engine final : public EngineBase {
       if (variant < 0 || variant > 4) throw std::invalid_argument("interior variant must be 0..4");
       var_int_ = variant;
     } else if (family == 2) {
-      if (variant < 0 || variant > 2) throw std::invalid_argument("cut variant must be 0..2");
+      if (variant < 0 || variant > 4) throw std::invalid_argument("cut variant must be 0..4");
       var_cut_ = variant;
     } else if (family == 3) {
       if (variant < 0 || variant > 2) throw std::invalid_argument("operator variant must be 0..2");
@@ -753,23 +740,32 @@ class Engine final : public EngineBase {
   static constexpr bool kWarpCut = (DIM == 2 ? (2 * P + 1) * (2 * P + 1) : (2 * P + 1) * (2 * P + 1) * (2 * P + 1)) <= 64;
   // Record kernel: kCutWarps independent warps per block, each with its own
   // stage; the records are read from global memory, prefetched into L2 per
-  // patch (variant 1 of the cut family, the automatic choice) or not
-  // (variant 2; the same arithmetic).  The grid: every block the occupancy
-  // calculator lets reside, at most one warp per patch.
+  // patch when its loads are issued (variant 1 of the cut family), one patch
+  // ahead (variant 3), or not (variant 2); the same arithmetic.  The grid:
+  // every block the occupancy calculator lets reside, at most one warp per
+  // patch.  A colour of fewer than kCutWarps patches per SM runs one warp
+  // per block, so that its patches spread over as many SMs as possible
+  // (a coarse level's launch is one patch's chain of dependent steps, and
+  // warps of one SM share its FP64 pipe); variant 4 keeps kCutWarps warps
+  // per block at every size.
   static constexpr int kCutWarps = 8;
   struct PipePlan {
-    int grid = 0, smem = 0, prefetch = 1;
+    int grid = 0, smem = 0, prefetch = 1, wpb = kCutWarps;
   };
   template <typename T>
   PipePlan pipe_plan(const Common& c, int colour) const {
     PipePlan pl;
     const int cnt = c.cut_start[colour + 1] - c.cut_start[colour];
-    pl.prefetch = var_cut_ == 2 ? 0 : 1;
-    pl.smem = kCutWarps * warp_stage_bytes<DIM, P, T>();
+    pl.prefetch = var_cut_ == 1 ? 1 : var_cut_ == 2 ? 0 : var_cut_ == 3 ? 2 : kCutPrefetch;
+    pl.wpb = cnt < kCutWarps * sms_ && var_cut_ != 4 ? 1 : kCutWarps;
+    pl.smem = pl.wpb * warp_stage_bytes<DIM, P, T>();
     int nb = 0;
-    CUTMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cut_warp<DIM, P, T, kCutWarps>, 32 * kCutWarps,
-                                                             pl.smem));
-    pl.grid = std::max(1, std::min((cnt + kCutWarps - 1) / kCutWarps, std::max(1, nb) * sms_));
+    if (pl.wpb == 1)
+      CUTMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cut_warp<DIM, P, T, 1>, 32, pl.smem));
+    else
+      CUTMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cut_warp<DIM, P, T, kCutWarps>, 32 * kCutWarps,
+                                                               pl.smem));
+    pl.grid = std::max(1, std::min((cnt + pl.wpb - 1) / pl.wpb, std::max(1, nb) * sms_));
     return pl;
   }
   template <typename T>
@@ -1364,8 +1360,11 @@ class Engine final : public EngineBase {
       prof_mark(1, l, s);
       if (!kWarpCut) {
         const PipePlan pl = pipe_plan<T>(c, colour);
-        k_cut_warp<DIM, P, T, kCutWarps><<<pl.grid, 32 * kCutWarps, pl.smem, s>>>(pipe_level<T>(c, D, x, b), a0, cnt,
-                                                                                 pl.prefetch);
+        if (pl.wpb == 1)
+          k_cut_warp<DIM, P, T, 1><<<pl.grid, 32, pl.smem, s>>>(pipe_level<T>(c, D, x, b), a0, cnt, pl.prefetch);
+        else
+          k_cut_warp<DIM, P, T, kCutWarps><<<pl.grid, 32 * kCutWarps, pl.smem, s>>>(pipe_level<T>(c, D, x, b), a0,
+                                                                                   cnt, pl.prefetch);
       } else {
         k_cut_solve<DIM, P, T, WARPS><<<blocks_for(cnt, WARPS), 32 * WARPS, 0, s>>>(
             D.op, x, b, c.cutv + a0, c.cutn + a0, c.cutmo + a0, c.cutio + a0, c.members, c.mnode, c.fofs,
@@ -1449,7 +1448,9 @@ class Engine final : public EngineBase {
             const int* ext, const int* col, const T* wt, int W, const uint8_t* mask, cudaStream_t s) {
     const int64_t tot = (int64_t)ext[0] * ext[1] * ext[2];
     if (tot <= 0) return;
-    k_pass<T, MODE><<<blocks_for(tot, 256), 256, 0, s>>>(in, out, in0, in1, out0, out1, axis, lo[0], lo[1],
+    const int bs = ext[0] > 64 ? 128 : (ext[0] > 32 ? 64 : 32);
+    const dim3 grid((unsigned)((ext[0] + bs - 1) / bs), (unsigned)ext[1], (unsigned)ext[2]);
+    k_pass<T, MODE><<<grid, bs, 0, s>>>(in, out, in0, in1, out0, out1, axis, lo[0], lo[1],
                                                           lo[2], ext[0], ext[1], ext[2], col, wt, W, mask);
     count_launch("transfer pass");
   }

@@ -1339,12 +1339,10 @@ __global__ void __launch_bounds__(256) k_pass(const T* __restrict__ in, T* __res
                                               int ext2, const int* __restrict__ col,
                                               const T* __restrict__ wt, int W,
                                               const uint8_t* __restrict__ mask) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t total = (int64_t)ext0 * ext1 * ext2;
-  if (t >= total) return;
-  const int i0 = lo0 + (int)(t % ext0);
-  const int i1 = lo1 + (int)((t / ext0) % ext1);
-  const int i2 = lo2 + (int)(t / ((int64_t)ext0 * ext1));
+  // grid (ceil(ext0 / blockDim.x), ext1, ext2): one thread per output node
+  const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t0 >= ext0) return;
+  const int i0 = lo0 + t0, i1 = lo1 + (int)blockIdx.y, i2 = lo2 + (int)blockIdx.z;
   const int io = (axis == 0) ? i0 : (axis == 1 ? i1 : i2);
   T acc = T(0);
   for (int e = 0; e < W; ++e) {
@@ -1379,13 +1377,43 @@ struct Region {
   int n0, n1;             // lattice strides (nodes per direction)
   int lo0, lo1, lo2;      // region origin
   int e0, e1, e2;         // region extents
+  // lattice index of the t-th node of the region (first coordinate fastest);
+  // 32-bit divisions while the region has fewer than 2^32 nodes
   __device__ __forceinline__ int64_t at(int64_t t) const {
-    const int i0 = lo0 + (int)(t % e0);
-    const int i1 = lo1 + (int)((t / e0) % e1);
-    const int i2 = lo2 + (int)(t / ((int64_t)e0 * e1));
+    int i0, i1, i2;
+    if (t < (int64_t(1) << 32)) {
+      const uint32_t u = (uint32_t)t, q = u / (uint32_t)e0, q2 = q / (uint32_t)e1;
+      i0 = lo0 + (int)(u - q * (uint32_t)e0);
+      i1 = lo1 + (int)(q - q2 * (uint32_t)e1);
+      i2 = lo2 + (int)q2;
+    } else {
+      i0 = lo0 + (int)(t % e0);
+      i1 = lo1 + (int)((t / e0) % e1);
+      i2 = lo2 + (int)(t / ((int64_t)e0 * e1));
+    }
     return (int64_t)i0 + (int64_t)n0 * (i1 + (int64_t)n1 * i2);
   }
   __host__ __device__ int64_t size() const { return (int64_t)e0 * e1 * e2; }
+  // f(o) for every node o of the region: each warp of the grid takes whole
+  // rows (fixed i1, i2), row r = (i1 - lo1) + e1 (i2 - lo2) going to warp
+  // r mod (warps of the grid), its lanes the row's consecutive nodes
+  template <class F>
+  __device__ __forceinline__ void for_each_node(F&& f) const {
+    for_each_node_of(blockIdx.x, gridDim.x, f);
+  }
+  // the same partition with this block taking the place of block blk of
+  // nblk (the batched kernels reproduce the single-problem partition)
+  template <class F>
+  __device__ __forceinline__ void for_each_node_of(int blk, int nblk, F&& f) const {
+    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    const int rows = e1 * e2;
+    for (int r = blk * wpb + (threadIdx.x >> 5); r < rows; r += nblk * wpb) {
+      const int q = r / e1;
+      const int64_t base = (int64_t)lo0 + (int64_t)n0 * (lo1 + (r - q * e1) + (int64_t)n1 * (lo2 + q));
+#pragma unroll 4
+      for (int i = lane; i < e0; i += 32) f(base + i);
+    }
+  }
 };
 
 // partial sums of a.b, one per block, fixed assignment (deterministic)
@@ -1394,12 +1422,7 @@ static __global__ void __launch_bounds__(256) k_dot_partial(Region R, const doub
                                                      double* __restrict__ part) {
   __shared__ double s[256];
   double acc = 0.0;
-  const int64_t tot = R.size();
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t o = R.at(t);
-    acc += a[o] * b[o];
-  }
+  R.for_each_node([&](int64_t o) { acc += a[o] * b[o]; });
   s[threadIdx.x] = acc;
   __syncthreads();
   for (int h = 128; h > 0; h >>= 1) {
@@ -1430,37 +1453,24 @@ static __global__ void __launch_bounds__(256) k_cg_update_xr(Region R, const dou
                                                       const double* __restrict__ p,
                                                       const double* __restrict__ q) {
   const double alpha = sc[0] / sc[1];
-  const int64_t tot = R.size();
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t o = R.at(t);
+  R.for_each_node([&](int64_t o) {
     x[o] += alpha * p[o];
     r[o] -= alpha * q[o];
-  }
+  });
 }
 
 // p = z + beta p, beta = rz_new / rz; then rz = rz_new (single writer after the grid)
 static __global__ void __launch_bounds__(256) k_cg_update_p(Region R, const double* __restrict__ sc,
                                                      double* __restrict__ p, const double* __restrict__ z) {
   const double beta = sc[2] / sc[0];
-  const int64_t tot = R.size();
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t o = R.at(t);
-    p[o] = z[o] + beta * p[o];
-  }
+  R.for_each_node([&](int64_t o) { p[o] = z[o] + beta * p[o]; });
 }
 
 static __global__ void k_copy_scalar(double* __restrict__ sc, int dst, int src) { sc[dst] = sc[src]; }
 
 template <typename TO, typename TI>
 __global__ void __launch_bounds__(256) k_convert(Region R, const TI* __restrict__ in, TO* __restrict__ out) {
-  const int64_t tot = R.size();
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t o = R.at(t);
-    out[o] = (TO)in[o];
-  }
+  R.for_each_node([&](int64_t o) { out[o] = (TO)in[o]; });
 }
 
 // compact (DoF order) <-> box

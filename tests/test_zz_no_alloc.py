@@ -45,3 +45,20 @@ def test_noalloc_rejects_large_coarse_level():
         pb.coarse_solve_noalloc(b0, x0)
     assert e.value.status == cm._lib.CF_EINVAL
     assert "at most" in str(e.value)
+
+
+def test_noalloc_call_leaves_free_device_memory_unchanged():
+    # after one call (kernels loaded, the array's address looked up), further
+    # calls take no device memory: the device's free bytes stay the same
+    pb = cm.Problem(**problem_kwargs("ball3d_q2_n16"))
+    n0 = pb.n_dofs(0)
+    b0 = torch.tensor(random_vector(n0, 900), dtype=torch.float64, device=DEV)
+    x0 = torch.zeros(n0, dtype=torch.float64, device=DEV)
+    pb.coarse_solve_noalloc(b0, x0)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        pb.coarse_solve_noalloc(b0, x0)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
