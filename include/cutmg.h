@@ -192,8 +192,10 @@ cf_status cf_set_precision(cf_problem* pb, int precision);
  * 1 = each patch's record (inverse and cut-cell rows) prefetched into L2 by
  * a bulk prefetch when its loads are issued, 2 = no prefetch, 3 = the next
  * patch's record prefetched while the current patch is worked on, 4 = eight
- * warps per block at every colour size (the automatic choice runs one warp
- * per block for colours of fewer than 8 patches per SM).  family
+ * warps per block, one patch each, at every colour size, 5 = one warp per
+ * block for colours of fewer than 8 patches per SM (the automatic choice
+ * runs such colours one patch per block with four warps working on it).
+ * family
  * CF_VAR_OPERATOR (operator
  * rows of nodes whose cells are all uncut): 1 = element-matrix form, 2 =
  * sum factorisation (the automatic choice in FP64).  variant 0 restores the

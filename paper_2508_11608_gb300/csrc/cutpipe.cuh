@@ -187,10 +187,19 @@ __device__ __forceinline__ PatchPos patch_pos(int vert, const WarpLane<DIM, P, T
   return pp;
 }
 
-// the per-level constants of level op (all 32 lanes; ends with __syncwarp)
-template <int DIM, int P, typename T>
+// A patch is worked on by a team of GW warps: one warp (GW = 1, several
+// teams per block) or the whole block (GW = warps of the block).
+template <int GW>
+__device__ __forceinline__ void team_sync() {
+  if constexpr (GW == 1) __syncwarp();
+  else __syncthreads();
+}
+
+// the per-level constants of level op (all threads of the team; tid: index
+// in the team; ends with a team barrier)
+template <int DIM, int P, typename T, int GW = 1>
 __device__ __forceinline__ void warp_lane_level(WarpLane<DIM, P, T>& wl, WarpStage<DIM, P, T>& st,
-                                                const OpArgs<T>& op, T ksc, const void* lv, int lane) {
+                                                const OpArgs<T>& op, T ksc, const void* lv, int lane, int tid) {
   using G = PipeGeo<DIM, P>;
 #pragma unroll
   for (int mm = 0; mm < P; ++mm) wl.cf[mm] = op.coef[mm];
@@ -200,7 +209,7 @@ __device__ __forceinline__ void warp_lane_level(WarpLane<DIM, P, T>& wl, WarpSta
     wl.mh0[s] = op.Mhat[t0][s];
     wl.mh1[s] = op.Mhat[t1][s];
   }
-  if (lane < P * (2 * P + 1)) st.dv[lane / (2 * P + 1)][lane % (2 * P + 1)] = op.dvec[lane / (2 * P + 1)][lane % (2 * P + 1)];
+  if (tid < P * (2 * P + 1)) st.dv[tid / (2 * P + 1)][tid % (2 * P + 1)] = op.dvec[tid / (2 * P + 1)][tid % (2 * P + 1)];
   wl.ksc = ksc;
   wl.n = op.n;
   wl.np = op.N + 1;
@@ -211,7 +220,7 @@ __device__ __forceinline__ void warp_lane_level(WarpLane<DIM, P, T>& wl, WarpSta
     wl.fdiv = nv <= (int64_t(1) << 24);
   }
   wl.lv = lv;
-  __syncwarp();
+  team_sync<GW>();
 }
 
 // the block's tables (all threads; the caller synchronises)
@@ -323,33 +332,35 @@ __device__ __forceinline__ void prefetch_l2(const void* src, uint32_t bytes) {
 
 // lane 0: bulk prefetch of patch M's record into L2
 template <typename T>
-__device__ __forceinline__ void prefetch_record(const PipeLevel<T>& L, const PipeMeta& M, int lane) {
-  if (lane == 0 && M.r1 > M.r0) prefetch_l2(L.rec + M.r0, (uint32_t)((M.r1 - M.r0) * sizeof(T)));
+__device__ __forceinline__ void prefetch_record(const PipeLevel<T>& L, const PipeMeta& M, int tid) {
+  if (tid == 0 && M.r1 > M.r0) prefetch_l2(L.rec + M.r0, (uint32_t)((M.r1 - M.r0) * sizeof(T)));
 }
 
-// Issue every load of patch j into the warp's stage by cp.async (one
-// group): the closure of x and b, the DoF list, items, cell kinds, the
-// boundary-face moments and (when it fits the stage) the ghost-entry list;
-// with `prefetch`, lane 0 also starts a bulk prefetch of the patch's record
-// into L2, read later by the row products and the solve.  All 32 lanes call
-// it, after the warp is done with the previous patch.
-template <int DIM, int P, typename T>
+// Issue every load of patch j into the team's stage by cp.async (one
+// group per thread): the closure of x and b, the DoF list, items, cell
+// kinds, the boundary-face moments and (when it fits the stage) the
+// ghost-entry list; with `prefetch`, thread 0 also starts a bulk prefetch of
+// the patch's record into L2, read later by the row products and the solve.
+// All threads of the team call it (tid: index in the team), after the team
+// is done with the previous patch.
+template <int DIM, int P, typename T, int GW = 1>
 __device__ __forceinline__ void warp_issue(const PipeLevel<T>& L, const PipeMeta& M, const PatchPos& pp, int j,
                                            WarpStage<DIM, P, T>& st, const WarpLane<DIM, P, T>& wl,
-                                           const CutTables<DIM, P>& tb, bool prefetch, int lane) {
+                                           const CutTables<DIM, P>& tb, bool prefetch, int tid) {
   using G = PipeGeo<DIM, P>;
+  constexpr int TS = 32 * GW;
   const int n = wl.n;
-  if (prefetch) prefetch_record(L, M, lane);
+  if (prefetch) prefetch_record(L, M, tid);
   if (pipe_gl_staged<DIM, P>(M)) {
     // lists are 16-byte aligned runs of a multiple of 8 entries
     const int nch = (M.g1 - M.g0) / 8;
-    for (int w = lane; w < nch; w += 32) cp_async16(&st.gl[8 * w], L.gent + M.g0 + 8 * w);
+    for (int w = tid; w < nch; w += TS) cp_async16(&st.gl[8 * w], L.gent + M.g0 + 8 * w);
   }
   // a closure inside the lattice needs no per-node test
   const int* c0 = pp.c0;
   const int base = pp.base;
   const bool inside = pp.inside;
-  for (int e = lane; e < G::NCL; e += 32) {
+  for (int e = tid; e < G::NCL; e += TS) {
     const int code = tb.uc[e];
     int rel = 0, stn = 1;
     bool in = true;
@@ -373,15 +384,15 @@ __device__ __forceinline__ void warp_issue(const PipeLevel<T>& L, const PipeMeta
     }
     if (e < M.m) cp_async_elem(&st.mem[e], L.members + M.mo + e);
   }
-  for (int w = lane; w < (M.nit + 3) / 4; w += 32) cp_async_elem(&st.item[w], L.items + M.io + w);
-  if (lane < G::NCELL) cp_async_elem(&st.pk[lane], L.pk + (size_t)j * G::NCELL + lane);
+  for (int w = tid; w < (M.nit + 3) / 4; w += TS) cp_async_elem(&st.item[w], L.items + M.io + w);
+  if (tid < G::NCELL) cp_async_elem(&st.pk[tid], L.pk + (size_t)j * G::NCELL + tid);
   // moments of the block-boundary ghost faces (one slot per set bit), in
   // 8-byte pieces (a slot holds an even number of FP32 values)
   const int nbv = __popcll(M.gmask & pipe_bnd_bits<DIM, P>()) * P * G::NT;
   const int nch = nbv * (int)sizeof(T) / 8;
   const char* src = reinterpret_cast<const char*>(L.Gb + (size_t)M.gb * P * G::NT);
   char* dst = reinterpret_cast<char*>(&st.U[0][0][0]);
-  for (int w = lane; w < nch; w += 32) cp_async8(dst + 8 * w, src + 8 * (size_t)w);
+  for (int w = tid; w < nch; w += TS) cp_async8(dst + 8 * w, src + 8 * (size_t)w);
   asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
@@ -434,7 +445,8 @@ __device__ __forceinline__ int closure_offset(int o, int n) {
   return off;
 }
 
-// One patch from a filled stage, by one warp:
+// One patch from a filled stage, by one team of GW warps (tid: index in the
+// team; lane: index in the warp):
 //   1. x on the nodes of each patch cell (cell vectors, padded to NBP);
 //   2. G_m of the middle-plane ghost faces, NT lanes per face: lane t forms
 //      J_m[t] = sum_i dvec_m[i] x(i, t) across the face, then the face mass
@@ -442,41 +454,44 @@ __device__ __forceinline__ int closure_offset(int o, int n) {
 //      coef_m;  and one lane per item: the cell row (record, or the uncut
 //      element matrix for h = 1 times h^(d-2); 16-byte loads through the
 //      read-only path) times the cell vector;
-//   3. residual of the patch rows, one lane per row: b - (cell parts in cell
-//      order, then the row's ghost entries in list order);
-//   4. delta = A_j^{-1} r, one lane per row, reading its row of the inverse
-//      and r four entries at a time; x updated in place.
+//   3. residual of the patch rows, one thread per row: b - (cell parts in
+//      cell order, then the row's ghost entries in list order);
+//   4. delta = A_j^{-1} r, one thread per row, reading its row of the
+//      inverse and r four entries at a time; x updated in place.
+// Every row and every face is formed by one thread or one lane group with
+// the same operations whatever GW is, so the result does not depend on it.
 // kp: the uncut element matrix for h = 1 (rows padded, global); tb: the
 // block's tables; rec: the record (global); gl: the ghost-entry list.
 // Products and solve rows run in independent partial sums (fixed split,
 // fixed order).
-template <int DIM, int P, typename T>
+template <int DIM, int P, typename T, int GW = 1>
 __device__ __forceinline__ void warp_compute(const T* __restrict__ kp, T* __restrict__ xg, int base,
                                              WarpStage<DIM, P, T>& st, const WarpLane<DIM, P, T>& wl,
                                              const CutTables<DIM, P>& tb, const T* __restrict__ rec,
-                                             const uint16_t* gl, const PipeMeta& M, int lane) {
+                                             const uint16_t* gl, const PipeMeta& M, int lane, int tid) {
   using G = PipeGeo<DIM, P>;
   constexpr int C = G::C, NB = G::NB, NBP = G::NBP, NTF = G::NT;
-  constexpr int KR = (G::NCL + 31) / 32;  // rows per lane
+  constexpr int TS = 32 * GW;
+  constexpr int KR = (G::NCL + TS - 1) / TS;  // rows per thread
   constexpr uint64_t bnd = pipe_bnd_bits<DIM, P>();
   const uint64_t gint = M.gmask & ~bnd;
   const int nbf = __popcll(M.gmask & bnd), nf = __popcll(gint);
-  for (int f = lane; f < G::NFACE; f += 32)
+  for (int f = tid; f < G::NFACE; f += TS)
     if ((gint >> f) & 1ull) st.flist[__popcll(gint & ((1ull << f) - 1ull))] = f;
   const int pkl = lane < G::NCELL ? st.pk[lane] : -2;
   const uint32_t amask = __ballot_sync(0xffffffffu, pkl != -2);  // active patch cells
   T* xc = &st.xc[0][0];
-  for (int idx = lane; idx < G::NCELL * G::NB; idx += 32) {
+  for (int idx = tid; idx < G::NCELL * G::NB; idx += TS) {
     const int v = tb.xcm[idx];
     xc[v >> 16] = st.x[v & 0xffff];
   }
-  __syncwarp();
+  team_sync<GW>();
   // 2a. middle-plane face moments
   {
     constexpr int FPR = 32 / NTF;
     const int grp = lane / NTF, t = lane - grp * NTF, t0 = t % (P + 1), t1 = t / (P + 1) % (P + 1);
     const int g0 = grp * NTF;
-    for (int f0 = 0; f0 < nf; f0 += FPR) {
+    for (int f0 = (tid >> 5) * FPR; f0 < nf; f0 += FPR * GW) {
       const int fi = f0 + grp;
       const bool act = grp < FPR && fi < nf;
       T J[P];
@@ -524,7 +539,7 @@ __device__ __forceinline__ void warp_compute(const T* __restrict__ kp, T* __rest
     // one item per lane: its row (16-byte loads) times the cell vector
     const T* rows = rec + (size_t)m * MP;
     const uint8_t* item = reinterpret_cast<const uint8_t*>(st.item);
-    for (int q = lane; q < M.nit; q += 32) {
+    for (int q = tid; q < M.nit; q += TS) {
       const int it = item[q], sc = it / NB, jj = it - sc * NB;
       const int pkv = st.pk[sc];
       const bool unc = pkv == -1;
@@ -544,11 +559,11 @@ __device__ __forceinline__ void warp_compute(const T* __restrict__ kp, T* __rest
       st.part[sc][jj] = unc ? wl.ksc * sum : sum;
     }
   }
-  __syncwarp();
-  // 3. residual of the patch rows (lane + 32 k)
+  team_sync<GW>();
+  // 3. residual of the patch rows (tid + TS k)
 #pragma unroll 1
   for (int k = 0; k < KR; ++k) {
-    const int e = lane + 32 * k;
+    const int e = tid + TS * k;
     if (e >= m) {
       if (e < MP) st.r[e] = T(0);
       continue;
@@ -570,7 +585,7 @@ __device__ __forceinline__ void warp_compute(const T* __restrict__ kp, T* __rest
     }
     st.r[e] = st.b[o] - acc;
   }
-  __syncwarp();
+  team_sync<GW>();
   // 4. local solve delta = A^{-1} r, x updated in place: one lane per row
   //    e, reading row e of the inverse (4 entries per load; zeros in the
   //    padding), columns in 4 partial sums by c mod 4, in increasing c; the
@@ -578,7 +593,7 @@ __device__ __forceinline__ void warp_compute(const T* __restrict__ kp, T* __rest
   const int n = wl.n;
 #pragma unroll 1
   for (int k = 0; k < KR; ++k) {
-    const int e = lane + 32 * k;
+    const int e = tid + TS * k;
     if (e >= m) break;
     const T* Ae = rec + (size_t)e * MP;
     T a[4] = {T(0), T(0), T(0), T(0)};
@@ -600,10 +615,12 @@ __device__ __forceinline__ void warp_compute(const T* __restrict__ kp, T* __rest
     const int o = st.mem[e];
     xg[base + closure_offset<DIM, P>(o, n)] = st.x[o] + acc;
   }
-  __syncwarp();
+  team_sync<GW>();
 }
 
-// The loop of one warp over the work items it, it + step, .. below total.
+// The loop of one team (GW warps: one warp, or the whole block) over the
+// work items it, it + step, .. below total; every warp of the team reads the
+// metadata itself.
 // locate(item, level, patch) gives an item's level descriptor and patch.
 // st: the warp's stage; tb: the block's tables.  Per item: issue the
 // loads, read the next item's metadata while they fly, wait for the
@@ -611,11 +628,11 @@ __device__ __forceinline__ void warp_compute(const T* __restrict__ kp, T* __rest
 // prefetched into L2 when its patch's loads are issued; 2 the next item's
 // record prefetched as soon as its metadata is read, one patch ahead of its
 // use (the first item's at its issue).
-template <int DIM, int P, typename T, class Locate>
+template <int DIM, int P, typename T, int GW = 1, class Locate>
 __device__ __forceinline__ void warp_loop(int it, int step, int total, Locate&& locate, WarpStage<DIM, P, T>& st,
                                           const CutTables<DIM, P>& tb, int prefetch) {
   if (it >= total) return;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, tid = threadIdx.x % (32 * GW);
   WarpLane<DIM, P, T> wl;
   wl.lv = nullptr;
   const PipeLevel<T>* Lc;
@@ -624,9 +641,9 @@ __device__ __forceinline__ void warp_loop(int it, int step, int total, Locate&& 
   PipeMeta cur = pipe_meta_gather(lane < kMetaFields ? pipe_meta_field(*Lc, jc, lane) : 0);
   bool first = true;
   for (; it < total; it += step) {
-    if (wl.lv != Lc) warp_lane_level<DIM, P, T>(wl, st, Lc->op, Lc->ksc, Lc, lane);
+    if (wl.lv != Lc) warp_lane_level<DIM, P, T, GW>(wl, st, Lc->op, Lc->ksc, Lc, lane, tid);
     const PatchPos pp = patch_pos<DIM, P, T>(cur.vert, wl);
-    warp_issue<DIM, P, T>(*Lc, cur, pp, jc, st, wl, tb, prefetch == 1 || (prefetch == 2 && first), lane);
+    warp_issue<DIM, P, T, GW>(*Lc, cur, pp, jc, st, wl, tb, prefetch == 1 || (prefetch == 2 && first), tid);
     first = false;
     const PipeLevel<T>* Ln = Lc;
     int jn = jc;
@@ -637,14 +654,14 @@ __device__ __forceinline__ void warp_loop(int it, int step, int total, Locate&& 
       if (lane < kMetaFields) nv = pipe_meta_field(*Ln, jn, lane);
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
-    __syncwarp();
+    team_sync<GW>();
     if (more && prefetch == 2) {
       const uint64_t r1 = __shfl_sync(0xffffffffu, nv, 9);
-      if (lane == 8 && r1 > nv) prefetch_l2(Ln->rec + nv, (uint32_t)((r1 - nv) * sizeof(T)));
+      if (tid == 8 && r1 > nv) prefetch_l2(Ln->rec + nv, (uint32_t)((r1 - nv) * sizeof(T)));
     }
     const uint16_t* gl = pipe_gl_staged<DIM, P>(cur) ? st.gl : Lc->gent + cur.g0;
-    warp_compute<DIM, P, T>(Lc->kp, Lc->x, pp.base, st, wl, tb, Lc->rec + cur.r0, gl, cur, lane);
-    __syncwarp();
+    warp_compute<DIM, P, T, GW>(Lc->kp, Lc->x, pp.base, st, wl, tb, Lc->rec + cur.r0, gl, cur, lane, tid);
+    team_sync<GW>();
     if (more) cur = pipe_meta_gather(nv);
     Lc = Ln;
     jc = jn;
@@ -685,6 +702,27 @@ __global__ void __launch_bounds__(32 * WPB, cut_min_blocks<T>())
       },
       *reinterpret_cast<WarpStage<DIM, P, T>*>(wsm + (size_t)warp * warp_stage_bytes<DIM, P, T>()), tb,
       prefetch);
+}
+
+// The same colour step with one patch per block at a time, worked on by the
+// block's GW warps together (colours of few patches: shorter chains of
+// dependent steps per patch, the same arithmetic per row and face).
+template <int DIM, int P, typename T, int GW>
+__global__ void __launch_bounds__(32 * GW) k_cut_team(PipeLevel<T> L, int j0, int npatch, int prefetch) {
+  extern __shared__ __align__(128) unsigned char wsm[];
+  __shared__ PipeLevel<T> sL;
+  __shared__ CutTables<DIM, P> tb;
+  if (threadIdx.x == 0) sL = L;
+  cut_tables<DIM, P>(tb);
+  __syncthreads();
+  const PipeLevel<T>* Lp = &sL;
+  warp_loop<DIM, P, T, GW>(
+      blockIdx.x, gridDim.x, npatch,
+      [&](int it, const PipeLevel<T>*& lv, int& j) {
+        lv = Lp;
+        j = j0 + it;
+      },
+      *reinterpret_cast<WarpStage<DIM, P, T>*>(wsm), tb, prefetch);
 }
 
 }  // namespace cutmg

@@ -252,6 +252,10 @@ class Engine final : public EngineBase {
                                       warp_stage_bytes<DIM, P, float>()));
       CUTMG_CUDA(cudaFuncSetAttribute(k_cut_warp<DIM, P, double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       warp_stage_bytes<DIM, P, double>()));
+      CUTMG_CUDA(cudaFuncSetAttribute(k_cut_team<DIM, P, float, kCutTeam>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, warp_stage_bytes<DIM, P, float>()));
+      CUTMG_CUDA(cudaFuncSetAttribute(k_cut_team<DIM, P, double, kCutTeam>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, warp_stage_bytes<DIM, P, double>()));
     }
     {
       int dev = 0;
@@ -280,7 +284,8 @@ class Engine final : public EngineBase {
   // two per thread, 3 dense split, 4 tensor cores; FP64: 1 warp per patch,
   // 2 block per patch); family 2 = cut-patch step of the record kernel (1
   // records prefetched into L2 at issue, 2 no prefetch, 3 one patch ahead,
-  // 4 eight warps per block at every size); family 3 = operator rows of
+  // 4 eight warps per block at every size, 5 one warp per block for small
+  // colours); family 3 = operator rows of
   // plain nodes (1 element matrices, 2 sum factorisation).  0 restores the
   // automatic choice.
   void set_variant(int family, int variant) override {
@@ -288,7 +293,7 @@ class Engine final : public EngineBase {
       if (variant < 0 || variant > 4) throw std::invalid_argument("interior variant must be 0..4");
       var_int_ = variant;
     } else if (family == 2) {
-      if (variant < 0 || variant > 4) throw std::invalid_argument("cut variant must be 0..4");
+      if (variant < 0 || variant > 5) throw std::invalid_argument("cut variant must be 0..5");
       var_cut_ = variant;
     } else if (family == 3) {
       if (variant < 0 || variant > 2) throw std::invalid_argument("operator variant must be 0..2");
@@ -743,29 +748,39 @@ class Engine final : public EngineBase {
   // patch when its loads are issued (variant 1 of the cut family), one patch
   // ahead (variant 3), or not (variant 2); the same arithmetic.  The grid:
   // every block the occupancy calculator lets reside, at most one warp per
-  // patch.  A colour of fewer than kCutWarps patches per SM runs one warp
-  // per block, so that its patches spread over as many SMs as possible
-  // (a coarse level's launch is one patch's chain of dependent steps, and
-  // warps of one SM share its FP64 pipe); variant 4 keeps kCutWarps warps
-  // per block at every size.
+  // patch.  A colour of fewer than kCutWarps patches per SM (the coarse
+  // levels, where a launch lasts about one patch's chain of dependent steps)
+  // runs one patch per block at a time with the block's kCutTeam warps
+  // working on it together (k_cut_team), which shortens that chain and
+  // spreads the patches over the SMs (whose warps share one FP64 pipe);
+  // variant 4 keeps kCutWarps warps per block, one patch each, at every
+  // size, variant 5 runs such colours one warp per block.
   static constexpr int kCutWarps = 8;
+  static constexpr int kCutTeam = 4;
   struct PipePlan {
     int grid = 0, smem = 0, prefetch = 1, wpb = kCutWarps;
+    bool team = false;
   };
   template <typename T>
   PipePlan pipe_plan(const Common& c, int colour) const {
     PipePlan pl;
     const int cnt = c.cut_start[colour + 1] - c.cut_start[colour];
     pl.prefetch = var_cut_ == 1 ? 1 : var_cut_ == 2 ? 0 : var_cut_ == 3 ? 2 : kCutPrefetch;
-    pl.wpb = cnt < kCutWarps * sms_ && var_cut_ != 4 ? 1 : kCutWarps;
-    pl.smem = pl.wpb * warp_stage_bytes<DIM, P, T>();
+    const bool small = cnt < kCutWarps * sms_ && var_cut_ != 4;
+    pl.team = small && var_cut_ != 5;
+    pl.wpb = small ? (pl.team ? kCutTeam : 1) : kCutWarps;
+    pl.smem = (pl.team ? 1 : pl.wpb) * warp_stage_bytes<DIM, P, T>();
     int nb = 0;
-    if (pl.wpb == 1)
+    if (pl.team)
+      CUTMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cut_team<DIM, P, T, kCutTeam>, 32 * kCutTeam,
+                                                               pl.smem));
+    else if (pl.wpb == 1)
       CUTMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cut_warp<DIM, P, T, 1>, 32, pl.smem));
     else
       CUTMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cut_warp<DIM, P, T, kCutWarps>, 32 * kCutWarps,
                                                                pl.smem));
-    pl.grid = std::max(1, std::min((cnt + pl.wpb - 1) / pl.wpb, std::max(1, nb) * sms_));
+    const int per_block = pl.team ? 1 : pl.wpb;
+    pl.grid = std::max(1, std::min((cnt + per_block - 1) / per_block, std::max(1, nb) * sms_));
     return pl;
   }
   template <typename T>
@@ -1360,7 +1375,10 @@ class Engine final : public EngineBase {
       prof_mark(1, l, s);
       if (!kWarpCut) {
         const PipePlan pl = pipe_plan<T>(c, colour);
-        if (pl.wpb == 1)
+        if (pl.team)
+          k_cut_team<DIM, P, T, kCutTeam><<<pl.grid, 32 * kCutTeam, pl.smem, s>>>(pipe_level<T>(c, D, x, b), a0, cnt,
+                                                                                  pl.prefetch);
+        else if (pl.wpb == 1)
           k_cut_warp<DIM, P, T, 1><<<pl.grid, 32, pl.smem, s>>>(pipe_level<T>(c, D, x, b), a0, cnt, pl.prefetch);
         else
           k_cut_warp<DIM, P, T, kCutWarps><<<pl.grid, 32 * kCutWarps, pl.smem, s>>>(pipe_level<T>(c, D, x, b), a0,

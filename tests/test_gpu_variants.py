@@ -10,8 +10,9 @@ each one on the same small problems:
   interior step, FP64: one warp per patch, one block per patch;
   cut-patch step (3D Q2): each patch's record (inverse and cut-cell rows)
     prefetched into L2 by a bulk prefetch when its loads are issued, one
-    patch ahead, or not; and eight warps per block where the automatic
-    choice runs one warp per block (colours of few patches);
+    patch ahead, or not; and, where the automatic choice runs colours of few
+    patches one patch per block with its warps working together, eight
+    warps per block with one patch each, or one warp per block;
   operator rows of nodes with only uncut cells: element matrices or sum
     factorisation.
 Tolerances as in test_gpu_parity (FP64 1e-11 of the update, FP32 2e-4); the
@@ -109,7 +110,7 @@ def test_cut_variants_match_oracle_and_each_other(pair, prec, tol):
     if name != "ball3d_q2_n16":
         pytest.skip("one cut kernel form for (d, p) with at most 64 closure nodes")
     ref = None
-    for v in (1, 2, 3, 4):
+    for v in (1, 2, 3, 4, 5):
         pb.set_kernel_variant(_lib.CF_VAR_CUT, v)
         outs = _steps(pb, H, True, prec, tol)
         if ref is None:
@@ -144,7 +145,7 @@ def test_solve_with_every_variant_takes_the_oracle_iterations(pair):
 
 def test_bad_variants_are_rejected(pair):
     pb, _, _ = pair
-    for fam, v in ((0, 1), (4, 1), (_lib.CF_VAR_INTERIOR, 5), (_lib.CF_VAR_CUT, 5), (_lib.CF_VAR_CUT, -1),
+    for fam, v in ((0, 1), (4, 1), (_lib.CF_VAR_INTERIOR, 5), (_lib.CF_VAR_CUT, 6), (_lib.CF_VAR_CUT, -1),
                    (_lib.CF_VAR_OPERATOR, 3)):
         with pytest.raises(cm.CutmgError) as e:
             pb.set_kernel_variant(fam, v)
