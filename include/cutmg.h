@@ -22,7 +22,8 @@
  *    message (thread-local).  A problem handle stays valid after CF_ENOCONV.
  *  - The problem handle owns every hierarchy buffer on the device it was
  *    created on (the current device at cf_setup).
- *  - Supported: dim 2 with degree 1..3, dim 3 with degree 1..2.
+ *  - Supported: dim 2 with degree 1..4 (degree 4 goes beyond the paper,
+ *    whose experiments stop at Q3), dim 3 with degree 1..2.
  */
 #ifndef CUTMG_H
 #define CUTMG_H
@@ -138,7 +139,7 @@ typedef struct cf_problem cf_problem;
  * Errors: CF_EINVAL (null argument, bad sizes, degree, kind; a domain that
  * misses the mesh or whose boundary crosses no cell, which leaves no
  * Dirichlet condition; a coarsest level above 12,000 DoFs), CF_EUNSUPPORTED
- * (dim 3 with degree 3), CF_ENOMEM, CF_ECUDA. */
+ * (dim 3 with degree 3 or 4), CF_ENOMEM, CF_ECUDA. */
 cf_status cf_setup(const cf_mesh* mesh, const cf_levelset* ls, int degree,
                    const cf_params* params, void* stream, cf_problem** out);
 void cf_destroy(cf_problem* pb);

@@ -8,8 +8,9 @@ from numpy.polynomial import Polynomial
 
 
 def gll_nodes(p):
-    """Gauss-Lobatto points on [0, 1] for degree p = 1, 2, 3 (closed forms:
-    the end points plus the roots of P_p')."""
+    """Gauss-Lobatto points on [0, 1] for degree p = 1, 2, 3, 4 (closed forms:
+    the end points plus the roots of P_p', mapped from [-1, 1]: 0 for p = 2,
+    +-1/sqrt(5) for p = 3, 0 and +-sqrt(3/7) for p = 4)."""
     if p == 1:
         return np.array([0.0, 1.0])
     if p == 2:
@@ -17,7 +18,10 @@ def gll_nodes(p):
     if p == 3:
         s = 1.0 / math.sqrt(5.0)
         return np.array([0.0, 0.5 * (1.0 - s), 0.5 * (1.0 + s), 1.0])
-    raise ValueError("degree must be 1, 2 or 3")
+    if p == 4:
+        s = math.sqrt(3.0 / 7.0)
+        return np.array([0.0, 0.5 * (1.0 - s), 0.5, 0.5 * (1.0 + s), 1.0])
+    raise ValueError("degree must be 1, 2, 3 or 4")
 
 
 class Basis1D:

@@ -91,7 +91,7 @@ static cf_status translate(const cf_mesh* mesh, const cf_levelset* ls, int degre
                            SetupParams& prm, int& precision, int& threads) {
   if (!mesh || !ls) return fail(CF_EINVAL, "null argument");
   if (mesh->dim != 2 && mesh->dim != 3) return fail(CF_EINVAL, "dim must be 2 or 3");
-  if (degree < 1 || degree > 3) return fail(CF_EINVAL, "degree must be 1, 2 or 3");
+  if (degree < 1 || degree > 4) return fail(CF_EINVAL, "degree must be 1, 2, 3 or 4");
   if (mesh->dim == 3 && degree > 2) return fail(CF_EUNSUPPORTED, "dim 3 supports degree 1 and 2");
   if (mesh->n_cells < 1 || mesh->n_levels < 1) return fail(CF_EINVAL, "n_cells and n_levels must be positive");
   if (ls->kind < CF_LS_SPHERE || ls->kind > CF_LS_CALLBACK) return fail(CF_EINVAL, "unknown level-set kind");
@@ -531,8 +531,9 @@ cf_status cf_batch_create(cf_problem* const* problems, int count, cf_batch** out
   std::unique_ptr<cf_batch> bt(new cf_batch());
   bt->count = count;
   cf_status st = guarded([&] {
+    int grouped = 0;
     for (int dim = 2; dim <= 3; ++dim)
-      for (int deg = 1; deg <= 3; ++deg) {
+      for (int deg = 1; deg <= 4; ++deg) {
         std::vector<EngineBase*> inst;
         std::vector<int> idx;
         int n_c = -1;
@@ -548,7 +549,9 @@ cf_status cf_batch_create(cf_problem* const* problems, int count, cf_batch** out
         if (inst.empty()) continue;
         bt->groups.push_back(dim == 2 ? make_batch_group_d2(deg, inst, n_c) : make_batch_group_d3(deg, inst, n_c));
         bt->members.push_back(idx);
+        grouped += (int)idx.size();
       }
+    if (grouped != count) throw std::invalid_argument("a problem of the batch fits no (dim, degree) group");
     cudaStream_t s;
     CUTMG_CHECK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
     for (auto& g : bt->groups) g->autotune(s);

@@ -55,9 +55,10 @@ struct PipeGeo {
 
 // ghost entry: moment slot of the face in the patch (6 bits: the boundary-
 // plane faces first, then the middle-plane faces, each in mask-bit order),
-// node along the normal (3 bits), tangential node (7 bits)
+// node along the normal (4 bits, 0 .. 2p), tangential node (6 bits); the
+// host setup writes the same packing
 __host__ __device__ constexpr uint16_t ghost_entry(int slot, int i, int t) {
-  return (uint16_t)(slot | (i << 6) | (t << 9));
+  return (uint16_t)(slot | (i << 6) | (t << 10));
 }
 
 // device arrays of one level for the pipelined cut kernel
@@ -209,7 +210,7 @@ __device__ __forceinline__ void warp_lane_level(WarpLane<DIM, P, T>& wl, WarpSta
     wl.mh0[s] = op.Mhat[t0][s];
     wl.mh1[s] = op.Mhat[t1][s];
   }
-  if (tid < P * (2 * P + 1)) st.dv[tid / (2 * P + 1)][tid % (2 * P + 1)] = op.dvec[tid / (2 * P + 1)][tid % (2 * P + 1)];
+  for (int e = tid; e < P * (2 * P + 1); e += 32 * GW) st.dv[e / (2 * P + 1)][e % (2 * P + 1)] = op.dvec[e / (2 * P + 1)][e % (2 * P + 1)];
   wl.ksc = ksc;
   wl.n = op.n;
   wl.np = op.N + 1;
@@ -578,7 +579,7 @@ __device__ __forceinline__ void warp_compute(const T* __restrict__ kp, T* __rest
     }
     const int q1 = gl[e + 1];
     for (int q = gl[e]; q < q1; ++q) {
-      const int en = gl[m + 1 + q], slot = en & 63, i = (en >> 6) & 7, t = en >> 9;
+      const int en = gl[m + 1 + q], slot = en & 63, i = (en >> 6) & 15, t = en >> 10;
       const T* g = &st.U[slot][0][t];
 #pragma unroll
       for (int mm = 0; mm < P; ++mm) acc += st.dv[mm][i] * g[mm * NTF];

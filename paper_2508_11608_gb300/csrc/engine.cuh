@@ -939,12 +939,12 @@ class Engine final : public EngineBase {
       D.kp = pool_.upload<T>(kp);
       D.ksc = (T)h.kscale;
     }
-    for (int m = 0; m < 3; ++m) {
-      for (int i = 0; i < 7; ++i) D.op.dvec[m][i] = (T)h.dvec[m][i];
+    for (int m = 0; m < 4; ++m) {
+      for (int i = 0; i < 9; ++i) D.op.dvec[m][i] = (T)h.dvec[m][i];
       D.op.coef[m] = (T)h.coef[m];
     }
-    for (int a = 0; a < 4; ++a)
-      for (int b2 = 0; b2 < 4; ++b2) D.op.Mhat[a][b2] = (T)h.Mhat[a][b2];
+    for (int a = 0; a < 5; ++a)
+      for (int b2 = 0; b2 < 5; ++b2) D.op.Mhat[a][b2] = (T)h.Mhat[a][b2];
     for (int i = 0; i < M; ++i) {
       for (int j = 0; j < C; ++j) {
         D.fd.Mr[i][j] = (T)h.Mr[i * C + j];
@@ -955,8 +955,8 @@ class Engine final : public EngineBase {
     }
     // assembled 1D rows by residue (column i - p + s at tap s) from the
     // two-cell rows: residue 0 = the middle row, residue r = row r of cell 0
-    for (int r = 0; r < 3; ++r)
-      for (int t = 0; t < 7; ++t) D.sf.Mrow[r][t] = D.sf.Krow[r][t] = T(0);
+    for (int r = 0; r < 4; ++r)
+      for (int t = 0; t < 9; ++t) D.sf.Mrow[r][t] = D.sf.Krow[r][t] = T(0);
     for (int r = 0; r < P; ++r) {
       const int row = r == 0 ? P - 1 : r - 1, sh = r == 0 ? 0 : P - r;
       for (int t = 0; t <= 2 * P; ++t) {

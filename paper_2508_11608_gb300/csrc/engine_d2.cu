@@ -1,4 +1,4 @@
-// Engines for two-dimensional problems, degrees 1..3.
+// Engines for two-dimensional problems, degrees 1..4.
 #include "batch.cuh"
 
 namespace cutmg {
@@ -8,6 +8,7 @@ std::unique_ptr<EngineBase> make_engine_d2(int degree, const Hierarchy& H, cudaS
     case 1: return std::make_unique<Engine<2, 1>>(H, stream);
     case 2: return std::make_unique<Engine<2, 2>>(H, stream);
     case 3: return std::make_unique<Engine<2, 3>>(H, stream);
+    case 4: return std::make_unique<Engine<2, 4>>(H, stream);
     default: throw std::invalid_argument("unsupported degree");
   }
 }
@@ -29,6 +30,11 @@ std::unique_ptr<BatchGroupBase> make_batch_group_d2(int degree, const std::vecto
       std::vector<Engine<2, 3>*> v;
       for (EngineBase* e : inst) v.push_back(static_cast<Engine<2, 3>*>(e));
       return std::make_unique<BatchGroup<2, 3>>(v, n_c);
+    }
+    case 4: {
+      std::vector<Engine<2, 4>*> v;
+      for (EngineBase* e : inst) v.push_back(static_cast<Engine<2, 4>*>(e));
+      return std::make_unique<BatchGroup<2, 4>>(v, n_c);
     }
     default: throw std::invalid_argument("unsupported degree");
   }

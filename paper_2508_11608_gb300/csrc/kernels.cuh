@@ -31,9 +31,9 @@ struct OpArgs {
   const int* cut_id;      // N^DIM index of the cut-cell matrix, -1 if none
   const T* cutmat;        // [n_cut][NB][NB] volume + Nitsche terms of cut cells
   const T* Kref;          // [NB][NB] stiffness of an uncut cell
-  T dvec[3][7];           // jump weights of the m-th normal derivative across a face
-  T coef[3];              // gamma_m h^(2m-1)/(m!)^2 h^(DIM-1)
-  T Mhat[4][4];           // 1D reference mass matrix
+  T dvec[4][9];           // jump weights of the m-th normal derivative across a face (m <= p <= 4)
+  T coef[4];              // gamma_m h^(2m-1)/(m!)^2 h^(DIM-1)
+  T Mhat[5][5];           // 1D reference mass matrix
   const int* face_id;     // [N^DIM][DIM] index of the ghost face (c, c + e_k), -1 if none
   T* G;                   // [n_ghost][P][(P+1)^(DIM-1)] face moments of the current x
 };
@@ -412,14 +412,14 @@ __device__ __forceinline__ void patch_rows(const OpArgs<T>& A, const T* __restri
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         if (ent[u] < 0) continue;
-        const T* g = A.G + (size_t)(ent[u] >> 3) / NTF * (P * NTF) + (ent[u] >> 3) % NTF;
+        const T* g = A.G + (size_t)(ent[u] >> 4) / NTF * (P * NTF) + (ent[u] >> 4) % NTF;
 #pragma unroll
         for (int mm = 0; mm < P; ++mm) gv[u][mm] = g[mm * NTF];
       }
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         if (ent[u] < 0) continue;
-        const int il = ent[u] & 7;
+        const int il = ent[u] & 15;
 #pragma unroll
         for (int mm = 0; mm < P; ++mm) acc += A.dvec[mm][il] * gv[u][mm];
       }
@@ -1186,6 +1186,12 @@ __device__ __forceinline__ void tmem_ld<16>(uint32_t taddr, float* v) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <>
+__device__ __forceinline__ void tmem_ld<32>(uint32_t taddr, float* v) {
+  tmem_ld<16>(taddr, v);
+  tmem_ld<16>(taddr + 16u, v + 16);
 }
 
 __device__ __forceinline__ float to_tf32(float v) {

@@ -279,7 +279,7 @@ cf_status cf_server_run(cf_server* s, void* stream) {
         groups.clear();
         gmem.clear();
         for (int dim = 2; dim <= 3; ++dim)
-          for (int deg = 1; deg <= 3; ++deg) {
+          for (int deg = 1; deg <= 4; ++deg) {
             std::vector<cutmg::EngineBase*> inst;
             std::vector<int> mem;
             int n_c = -1;

@@ -251,7 +251,7 @@ struct RefTables {
   }
   // tensor basis values at reference point xi
   void values(const double* xi, double* v) const {
-    double l[3][4];
+    double l[3][5];
     for (int k = 0; k < d; ++k)
       for (int a = 0; a <= p; ++a) l[k][a] = b.eval(a, xi[k]);
     for (int j = 0; j < NB; ++j) {
@@ -263,7 +263,7 @@ struct RefTables {
   }
   // tensor basis values and physical gradients at reference point xi
   void eval(const double* xi, double h, double* v, double* g /* NB x d */) const {
-    double l[3][4], dl[3][4];
+    double l[3][5], dl[3][5];
     for (int k = 0; k < d; ++k)
       for (int a = 0; a <= p; ++a) {
         l[k][a] = b.eval(a, xi[k]);
@@ -677,7 +677,7 @@ void cut_patch_face_entries(HostLevel& L) {
   const int d = L.d, p = L.p, N = L.N, n = L.n, ncol = 1 << d;
   const int NTf = ipow(p + 1, d - 1);
   const int64_t nmem = (int64_t)L.member_node.size();
-  // entry = ((face id * NTf) + tangential node) * 8 + node along the normal
+  // entry = ((face id * NTf) + tangential node) * 16 + node along the normal (0 .. 2p)
   auto entries = [&](int64_t gm, auto&& emit) {
     int64_t t = L.member_node[gm];
     int idx[3] = {0, 0, 0};
@@ -708,7 +708,7 @@ void cut_patch_face_entries(HostLevel& L) {
             if (id < 0) continue;
             int tt = idx[td[0]] - p * c[td[0]];
             if (d == 3) tt += (p + 1) * (idx[td[1]] - p * c[td[1]]);
-            emit(((id * NTf) + tt) * 8 + (idx[k] - p * Lk), id);
+            emit(((id * NTf) + tt) * 16 + (idx[k] - p * Lk), id);
           }
     }
   };
@@ -1165,7 +1165,7 @@ void cut_patch_records(HostLevel& L, bool dry) {
                                      ? __builtin_popcountll(gm & bnd_bits & below)
                                      : __builtin_popcountll(gm & bnd_bits) + __builtin_popcountll(gm & ~bnd_bits & below);
                 const int t = (tj[0] - p * u0) + (d == 3 ? (p + 1) * (tj[1] - p * u1) : 0);
-                ent.push_back((uint16_t)(slot | (i << 6) | (t << 9)));
+                ent.push_back((uint16_t)(slot | (i << 6) | (t << 10)));
               }
           }
         }
@@ -1733,7 +1733,8 @@ void build_rhs(const SetupParams& prm, const RefTables& R, const HostLevel& L, s
 
 void build_hierarchy(const SetupParams& prm, Hierarchy& H) {
   if (prm.dim != 2 && prm.dim != 3) throw std::invalid_argument("dim must be 2 or 3");
-  if (prm.degree < 1 || prm.degree > 3) throw std::invalid_argument("degree must be 1, 2 or 3");
+  if (prm.degree < 1 || prm.degree > 4) throw std::invalid_argument("degree must be 1, 2, 3 or 4");
+  if (prm.dim == 3 && prm.degree > 2) throw std::invalid_argument("dim 3 supports degree 1 and 2");
   if (prm.n_levels < 1 || prm.n_levels > 12) throw std::invalid_argument("n_levels out of range");
   if (prm.n_cells % (1 << (prm.n_levels - 1)) != 0)
     throw std::invalid_argument("n_cells must be divisible by 2^(n_levels-1)");

@@ -153,9 +153,9 @@ struct HostLevel {
   std::vector<double> S, lam;     // fast-diagonalisation eigenvectors / values (M)
   std::vector<double> Wcart;      // (2p-1)^d x (2p+1)^d dense interior-patch update
   std::vector<double> diag;       // diagonal of A_l per DoF (levels >= 1)
-  double dvec[3][7] = {};         // ghost normal-derivative jump weights
-  double coef[3] = {};            // gamma_m h^(2m-1)/(m!)^2 * h^(d-1)
-  double Mhat[4][4] = {};         // reference 1D mass on [0, 1]
+  double dvec[4][9] = {};         // ghost normal-derivative jump weights (m = 1..p, 2p + 1 nodes)
+  double coef[4] = {};            // gamma_m h^(2m-1)/(m!)^2 * h^(d-1)
+  double Mhat[5][5] = {};         // reference 1D mass on [0, 1]
   // transfer from the next coarser level (l >= 1)
   std::vector<int> pro_col;       // n x (p+1): coarse 1D column per fine 1D index
   std::vector<double> pro_w;

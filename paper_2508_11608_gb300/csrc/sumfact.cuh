@@ -38,7 +38,7 @@ struct SfGeo {
 // column i - p + s at tap s (zero outside the row's support)
 template <typename T>
 struct SfArgs {
-  T Mrow[3][7], Krow[3][7];
+  T Mrow[4][9], Krow[4][9];  // p <= 4
 };
 
 // taps [s0, s1] of residue r: vertex rows span both cells, others one cell
@@ -63,7 +63,7 @@ __device__ __forceinline__ void sf_pair(const SfArgs<T>& A, const T* __restrict_
 }
 
 template <int P, int R, typename T>
-__device__ __forceinline__ T sf_one(const T (&w)[3][7], const T* __restrict__ in, int stride) {
+__device__ __forceinline__ T sf_one(const T (&w)[4][9], const T* __restrict__ in, int stride) {
   T a = T(0);
 #pragma unroll
   for (int s = SfTaps<P, R>::S0; s <= SfTaps<P, R>::S1; ++s) a += w[R][s] * in[s * stride];
@@ -76,6 +76,8 @@ __device__ __forceinline__ void sf_residues(F&& f) {
   if constexpr (P >= 1) f(std::integral_constant<int, 0>());
   if constexpr (P >= 2) f(std::integral_constant<int, 1>());
   if constexpr (P >= 3) f(std::integral_constant<int, 2>());
+  if constexpr (P >= 4) f(std::integral_constant<int, 3>());
+  static_assert(P <= 4, "residues of degrees up to 4");
 }
 
 // y = A x (b == nullptr) or y = b - A x at the owned nodes of the bulk

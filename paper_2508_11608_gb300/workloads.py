@@ -22,6 +22,8 @@ CONFIGS = {
     "ball3d_q2_n32": dict(dim=3, n_cells=32, n_levels=4, degree=2, center=[0.05, 0.03, 0.02], radius=0.7),
     "ball3d_q1_n16": dict(dim=3, n_cells=16, n_levels=3, degree=1, center=[0.05, 0.03, 0.02], radius=0.7),
     "disk2d_q3_n32": dict(dim=2, n_cells=32, n_levels=3, degree=3, center=[0.031, 0.017], radius=0.7),
+    # degree 4 (beyond the paper's Q3)
+    "disk2d_q4_n32": dict(dim=2, n_cells=32, n_levels=3, degree=4, center=[0.031, 0.017], radius=0.7),
     "disk2d_q1_n64": dict(dim=2, n_cells=64, n_levels=4, degree=1, center=[0.031, 0.017], radius=0.7),
 }
 

@@ -21,7 +21,7 @@ import scipy.sparse as sp
 from oracle.fem import Level, assemble_level, ghost_face_matrix
 from oracle.levelset import Plane, Sphere
 
-GAMMAS = [0.1, 0.23, 0.37]
+GAMMAS = [0.1, 0.23, 0.37, 0.51]
 
 
 def _face_values(lev, k, xF, j):
@@ -36,7 +36,7 @@ def _face_values(lev, k, xF, j):
     return np.array(vals)
 
 
-@pytest.mark.parametrize("d,p", [(2, 1), (2, 2), (2, 3), (3, 1), (3, 2)])
+@pytest.mark.parametrize("d,p", [(2, 1), (2, 2), (2, 3), (2, 4), (3, 1), (3, 2)])
 def test_face_matrix_on_kinks_is_gamma_h_power_face_measure(d, p):
     lev = Level(Sphere([0.0] * d, 0.55), d, 8, p)
     h = lev.h
@@ -46,7 +46,10 @@ def test_face_matrix_on_kinks_is_gamma_h_power_face_measure(d, p):
         for j in range(1, p + 1):
             u = _face_values(lev, k, xF, j)
             expect = GAMMAS[j - 1] * h ** (2 * j - 1) * h ** (d - 1)
-            assert u @ G @ u == pytest.approx(expect, rel=1e-13, abs=0), (k, j)
+            # the Q4 face matrix (fourth derivatives) has entries up to 1e3
+            # against values of 6e-3 for j = 1: the sum cancels about 1e5
+            # and its rounding reaches a few 1e-12 relative
+            assert u @ G @ u == pytest.approx(expect, rel=1e-13 if p < 4 else 1e-11, abs=0), (k, j)
 
 
 @pytest.mark.parametrize("d,p", [(2, 1), (2, 2), (2, 3), (3, 2)])
