@@ -187,8 +187,8 @@ cf_status cf_set_precision(cf_problem* pb, int precision);
  * step): FP32 (mixed form) 1 = dense map, one patch per thread; 2 = dense
  * map, two patches per thread; 3 = dense map, several threads per patch;
  * 4 = dense map on the tensor cores (TF32 products, FP32 accumulation; the
- * automatic choice where it exists, else the same as 0); FP64 1 = one warp
- * per patch, 2 = one block per patch.  family CF_VAR_CUT (cut-patch step,
+ * automatic choice where it exists, else the same as 0); FP64 1 = two
+ * patches per warp (one per half-warp), 2 = one block per patch.  family CF_VAR_CUT (cut-patch step,
  * 3D degree 2; one warp per patch, records read from global memory):
  * 1 = each patch's record (inverse and cut-cell rows) prefetched into L2 by
  * a bulk prefetch when its loads are issued, 2 = no prefetch, 3 = the next

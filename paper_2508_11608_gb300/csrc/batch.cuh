@@ -1059,7 +1059,7 @@ class BatchGroup final : public BatchGroupBase {
     auto& tabs = res_tabs<T>(t);
     if (w_bulk_[t].total > 0) {
       if (inst_[0]->template use_sumfact<T>())
-        kb_apply_sf<DIM, P, T><<<std::max(1, std::min(w_sft_[t].total, 2 * sms_)), 256,
+        kb_apply_sf<DIM, P, T><<<std::max(1, std::min(w_sft_[t].total, 3 * sms_)), 256,
                                  SfGeo<DIM, P>::ELEMS * sizeof(T), s>>>(D, tabs.X, tabs.B, tabs.Y, w_sft_[t].off, K_,
                                                                        w_sft_[t].total);
       else
@@ -1183,7 +1183,7 @@ class BatchGroup final : public BatchGroupBase {
     }
     if (w_bulk_[0].total > 0) {
       if (inst_[0]->template use_sumfact<double>())
-        kb_apply_sf<DIM, P, double><<<std::max(1, std::min(w_sft_[0].total, 2 * sms_)), 256,
+        kb_apply_sf<DIM, P, double><<<std::max(1, std::min(w_sft_[0].total, 3 * sms_)), 256,
                                       SfGeo<DIM, P>::ELEMS * sizeof(double), s>>>(D, X, B, Y, w_sft_[0].off, K_,
                                                                                   w_sft_[0].total);
       else

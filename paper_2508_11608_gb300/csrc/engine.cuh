@@ -281,8 +281,8 @@ class Engine final : public EngineBase {
 
   int64_t launches() const override { return launches_; }
   // family 1 = interior-patch step (FP32: 1 dense one patch per thread, 2 dense
-  // two per thread, 3 dense split, 4 tensor cores; FP64: 1 warp per patch,
-  // 2 block per patch); family 2 = cut-patch step of the record kernel (1
+  // two per thread, 3 dense split, 4 tensor cores; FP64: 1 two patches per
+  // warp, 2 block per patch); family 2 = cut-patch step of the record kernel (1
   // records prefetched into L2 at issue, 2 no prefetch, 3 one patch ahead,
   // 4 eight warps per block at every size, 5 one warp per block for small
   // colours); family 3 = operator rows of
@@ -1265,7 +1265,10 @@ class Engine final : public EngineBase {
       prof_mark(3, l, s);
       if (use_sumfact<T>()) {
         using SG = SfGeo<DIM, P>;
-        k_apply_sf<DIM, P, T><<<std::min(c.nsf, 2 * sms_), 256, SG::ELEMS * sizeof(T), s>>>(
+        int nb = 0;  // resident blocks per SM (shared memory bound)
+        CUTMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_apply_sf<DIM, P, T>, 256,
+                                                                 SG::ELEMS * sizeof(T)));
+        k_apply_sf<DIM, P, T><<<std::min(c.nsf, std::max(1, nb) * sms_), 256, SG::ELEMS * sizeof(T), s>>>(
             D.sf, c.N, c.n, x, b, y, c.sf_tiles, c.sf_masks, c.nsf);
       } else {
         k_apply_bulk<DIM, P, T><<<blocks_for(c.nbulk, 128), 128, 0, s>>>(D.op, x, b, y, c.bulk, c.nbulk);
@@ -1361,7 +1364,7 @@ class Engine final : public EngineBase {
       else if (var_int_ == 2 || (var_int_ != 1 && cnt <= 4 * sms_))
         k_smooth_cart_cta<DIM, P, T><<<std::min(cnt, 16 * sms_), 128, 0, s>>>(D.fd, c.N, c.n, x, b, c.cart + a0, cnt);
       else
-        k_smooth_cart<DIM, P, T, WARPS><<<blocks_for(cnt, WARPS), 32 * WARPS, 0, s>>>(
+        k_smooth_cart<DIM, P, T, WARPS><<<blocks_for(cnt, 2 * WARPS), 32 * WARPS, 0, s>>>(
             D.fd, c.N, c.n, x, b, c.cart + a0, cnt);
       count_launch("smooth interior patches");
       prof_mark(2, l, s);

@@ -297,7 +297,7 @@ __device__ __forceinline__ int lat_index(const int* c, int n) {
 // synchronisation of the threads that work on one patch
 template <int NT>
 __device__ __forceinline__ void psync() {
-  if (NT == 32)
+  if (NT <= 32)
     __syncwarp();
   else
     __syncthreads();
@@ -586,11 +586,13 @@ struct CartScratch {
   T t[G::NI];
 };
 
-// NT threads (a warp, or a block for latency-bound launches) per patch
+// NT threads (a half-warp, a warp, or a block for latency-bound launches)
+// per patch; with live == false the patch is worked on but x is not written
+// (the idle half of a warp keeps its synchronisations)
 template <int DIM, int P, typename T, int NT = 32>
 __device__ __forceinline__ void cart_body(const FdArgs<T, P>& F, int N, int n, T* __restrict__ x,
                                           const T* __restrict__ b, int vert, int lane,
-                                          CartScratch<DIM, P, T>& CS) {
+                                          CartScratch<DIM, P, T>& CS, bool live = true) {
   constexpr int C = 2 * P + 1, M = 2 * P - 1;
   constexpr int NC = CartGeo<DIM, P>::NC;
   constexpr int NI = CartGeo<DIM, P>::NI;
@@ -756,19 +758,38 @@ __device__ __forceinline__ void cart_body(const FdArgs<T, P>& F, int N, int n, T
     int yi = rest % M, zi = rest / M;
     int node = (DIM == 2) ? base + (xi + 1) + n * (yi + 1)
                           : base + (xi + 1) + n * ((yi + 1) + n * (zi + 1));
-    x[node] += acc;
+    if (live) x[node] += acc;
   }
 }
 
+// the 1D tables of the interior step copied from the kernel parameters into
+// shared memory (all threads; a barrier follows): the lanes of a warp index
+// them with different rows, which the parameter space serves one address at
+// a time
+template <typename T, int P>
+__device__ __forceinline__ void stage_fd(const FdArgs<T, P>& F, FdArgs<T, P>& sF) {
+  constexpr int NV = (int)(sizeof(FdArgs<T, P>) / sizeof(T));
+  static_assert(sizeof(FdArgs<T, P>) % sizeof(T) == 0, "FdArgs holds T only");
+  for (int i = threadIdx.x; i < NV; i += blockDim.x) reinterpret_cast<T*>(&sF)[i] = reinterpret_cast<const T*>(&F)[i];
+}
+
+// Two patches per warp, one per half-warp: the element loops of a patch
+// (75, 45 and 27 entries for 3D Q2) fill 16 lanes better than 32, which the
+// FP64 pipe, busy with every issued warp instruction, rewards; each entry
+// is formed by one thread with the same operations as with a warp per patch.
 template <int DIM, int P, typename T, int WARPS>
 __global__ void __launch_bounds__(32 * WARPS) k_smooth_cart(FdArgs<T, P> F, int N, int n,
                                                             T* __restrict__ x, const T* __restrict__ b,
                                                             const int* __restrict__ verts, int nv) {
-  __shared__ CartScratch<DIM, P, T> sCS[WARPS];
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int pidx = blockIdx.x * WARPS + w;
-  if (pidx >= nv) return;
-  cart_body<DIM, P, T>(F, N, n, x, b, verts[pidx], lane, sCS[w]);
+  __shared__ CartScratch<DIM, P, T> sCS[2 * WARPS];
+  __shared__ FdArgs<T, P> sF;
+  stage_fd<T, P>(F, sF);
+  __syncthreads();
+  const int w = threadIdx.x >> 5, half = (threadIdx.x >> 4) & 1, hl = threadIdx.x & 15;
+  const int p0 = 2 * (blockIdx.x * WARPS + w);
+  if (p0 >= nv) return;  // whole warp
+  const bool live = p0 + half < nv;  // the idle half repeats the first patch without writing
+  cart_body<DIM, P, T, 16>(sF, N, n, x, b, verts[live ? p0 + half : p0], hl, sCS[2 * w + half], live);
 }
 
 // FP32 interior-patch step as one dense map per level (the mixed form):
@@ -943,8 +964,11 @@ __global__ void __launch_bounds__(128) k_smooth_cart_cta(FdArgs<T, P> F, int N, 
                                                           const T* __restrict__ b,
                                                           const int* __restrict__ verts, int nv) {
   __shared__ CartScratch<DIM, P, T> CS;
+  __shared__ FdArgs<T, P> sF;
+  stage_fd<T, P>(F, sF);
+  __syncthreads();
   for (int pidx = blockIdx.x; pidx < nv; pidx += gridDim.x) {
-    cart_body<DIM, P, T, 128>(F, N, n, x, b, verts[pidx], threadIdx.x, CS);
+    cart_body<DIM, P, T, 128>(sF, N, n, x, b, verts[pidx], threadIdx.x, CS);
     __syncthreads();
   }
 }

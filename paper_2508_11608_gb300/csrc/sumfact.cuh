@@ -31,7 +31,10 @@ struct SfGeo {
   static constexpr int XS = EX * EY * EZ;
   static constexpr int US = DIM == 3 ? 2 * EX * EY * NZ : 2 * EX * NY;
   static constexpr int VS = DIM == 3 ? 3 * EX * NY * NZ : 0;
-  static constexpr int ELEMS = XS + US + VS;
+  // V (3D) reuses X's space: X is read only by the first pass, V written by
+  // the second
+  static constexpr int XV = XS > VS ? XS : VS;
+  static constexpr int ELEMS = XV + US;
 };
 
 // rows of the assembled 1D physical mass / stiffness by residue r = i mod p,
@@ -91,8 +94,8 @@ __device__ __forceinline__ void sf_tile(const SfArgs<T>& A, int N, int n, const 
                                         const uint32_t* __restrict__ mask, T* smem) {
   using G = SfGeo<DIM, P>;
   T* X = smem;
-  T* U = X + G::XS;
-  T* V = U + G::US;
+  T* U = X + G::XV;
+  T* V = smem;  // over X (3D): written after the z pass, which is X's only reader
   const int tid = threadIdx.x, NT = blockDim.x, np = N + 1;
   {
     int a0[3] = {0, 0, 0};

@@ -81,7 +81,7 @@ def _steps(pb, H, cut):
 def test_interior_colour_steps(pair):
     pb, H = pair
     ref = None
-    for v in (1, 2):  # one warp / one block per patch: the same arithmetic
+    for v in (1, 2):  # half-warp / block per patch: the same arithmetic
         pb.set_kernel_variant(_lib.CF_VAR_INTERIOR, v)
         outs = _steps(pb, H, False)
         if ref is None:

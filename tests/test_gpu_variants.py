@@ -7,7 +7,7 @@ the variants the large benchmark sizes use.  cf_set_kernel_variant forces
 each one on the same small problems:
   interior step, FP32 (mixed form): dense map with 1 or 2 patches per thread,
     the split form with several threads per patch, and the tensor-core form;
-  interior step, FP64: one warp per patch, one block per patch;
+  interior step, FP64: two patches per warp (a half-warp each), one block per patch;
   cut-patch step (3D Q2): each patch's record (inverse and cut-cell rows)
     prefetched into L2 by a bulk prefetch when its loads are issued, one
     patch ahead, or not; and, where the automatic choice runs colours of few
