@@ -128,7 +128,13 @@ FP32_PEAK_TFLOPS = 78.5
 # The bench scales it by the algorithmic bytes of a launch of the timed
 # workload.  Valid only for the kernel sources it was taken on (sha256 over
 # kernels.cuh and cutpipe.cuh).
-TRAFFIC = {}
+TRAFFIC = {
+    # ncu, one finest-level launch of the 128^3 mixed solve (colour 2 of the
+    # first cut sweep): DRAM 117.74 + 4.30 MB against 89.32 MB algorithmic
+    # (profiles/k_cut_warp_ball3d_q2_n128_mixed.md)
+    ("k_cut_warp", "fp32"): {"dram_over_algorithmic": 122.04 / 89.32,
+                             "kernels_sha256": "29ba229c65e5860776d4ec851f02d22c3bc411c152ef2d925a941cffba35c220"},
+}
 
 
 def _kernels_sha256():
