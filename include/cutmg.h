@@ -195,7 +195,8 @@ cf_status cf_set_precision(cf_problem* pb, int precision);
  * patch's record prefetched while the current patch is worked on, 4 = eight
  * warps per block, one patch each, at every colour size, 5 = one warp per
  * block for colours of fewer than 8 patches per SM (the automatic choice
- * runs such colours one patch per block with four warps working on it).
+ * runs such colours one patch per block with four warps working on it),
+ * 6 = one patch per block with four warps at every colour size.
  * family
  * CF_VAR_OPERATOR (operator
  * rows of nodes whose cells are all uncut): 1 = element-matrix form, 2 =

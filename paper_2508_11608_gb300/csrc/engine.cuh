@@ -285,7 +285,7 @@ class Engine final : public EngineBase {
   // warp, 2 block per patch); family 2 = cut-patch step of the record kernel (1
   // records prefetched into L2 at issue, 2 no prefetch, 3 one patch ahead,
   // 4 eight warps per block at every size, 5 one warp per block for small
-  // colours); family 3 = operator rows of
+  // colours, 6 one patch per block at every size); family 3 = operator rows of
   // plain nodes (1 element matrices, 2 sum factorisation).  0 restores the
   // automatic choice.
   void set_variant(int family, int variant) override {
@@ -293,7 +293,7 @@ class Engine final : public EngineBase {
       if (variant < 0 || variant > 4) throw std::invalid_argument("interior variant must be 0..4");
       var_int_ = variant;
     } else if (family == 2) {
-      if (variant < 0 || variant > 5) throw std::invalid_argument("cut variant must be 0..5");
+      if (variant < 0 || variant > 6) throw std::invalid_argument("cut variant must be 0..6");
       var_cut_ = variant;
     } else if (family == 3) {
       if (variant < 0 || variant > 2) throw std::invalid_argument("operator variant must be 0..2");
@@ -766,7 +766,7 @@ class Engine final : public EngineBase {
     PipePlan pl;
     const int cnt = c.cut_start[colour + 1] - c.cut_start[colour];
     pl.prefetch = var_cut_ == 1 ? 1 : var_cut_ == 2 ? 0 : var_cut_ == 3 ? 2 : kCutPrefetch;
-    const bool small = cnt < kCutWarps * sms_ && var_cut_ != 4;
+    const bool small = (cnt < kCutWarps * sms_ && var_cut_ != 4) || var_cut_ == 6;
     pl.team = small && var_cut_ != 5;
     pl.wpb = small ? (pl.team ? kCutTeam : 1) : kCutWarps;
     pl.smem = (pl.team ? 1 : pl.wpb) * warp_stage_bytes<DIM, P, T>();
@@ -953,6 +953,13 @@ class Engine final : public EngineBase {
       for (int j = 0; j < M; ++j) D.fd.S[i][j] = (T)h.S[i * M + j];
       D.fd.lam[i] = (T)h.lam[i];
     }
+    // the eigenvalue sums of the fast-diagonalised solve, inverted once
+    for (int c = 0; c < (DIM == 3 ? M : 1); ++c)
+      for (int b2 = 0; b2 < M; ++b2)
+        for (int a = 0; a < M; ++a) {
+          const double den = h.lam[a] + h.lam[b2] + (DIM == 3 ? h.lam[c] : 0.0);
+          D.fd.dinv[a + M * (b2 + M * c)] = (T)(1.0 / den);
+        }
     // assembled 1D rows by residue (column i - p + s at tap s) from the
     // two-cell rows: residue 0 = the middle row, residue r = row r of cell 0
     for (int r = 0; r < 4; ++r)

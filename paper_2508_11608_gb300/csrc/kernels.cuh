@@ -565,6 +565,7 @@ struct FdArgs {
   T Mr[M][C], Kr[M][C];  // interior rows of the two-cell 1D mass / stiffness
   T S[M][M];             // K_I S = M_I S diag(lam), S^T M_I S = I
   T lam[M];
+  T dinv[M * M * M];     // 1 / (lam_a + lam_b (+ lam_c)), index a + M (b + M c), formed in FP64
 };
 
 template <int DIM, int P>
@@ -722,7 +723,7 @@ __device__ __forceinline__ void cart_body(const FdArgs<T, P>& F, int N, int n, T
 #pragma unroll
       for (int i = 0; i < M; ++i) acc += F.S[i][cz] * R[i * M * M + yx];
       int a = e % M, bb = (e / M) % M;
-      Tt[e] = acc / (F.lam[a] + F.lam[bb] + F.lam[cz]);
+      Tt[e] = acc * F.dinv[e];
     }
     psync<NT>();
     // S along z
@@ -736,7 +737,7 @@ __device__ __forceinline__ void cart_body(const FdArgs<T, P>& F, int N, int n, T
   } else {
     for (int e = lane; e < NI; e += NT) {
       int a = e % M, bb = e / M;
-      R[e] = R[e] / (F.lam[a] + F.lam[bb]);
+      R[e] = R[e] * F.dinv[e];
     }
   }
   psync<NT>();

@@ -95,7 +95,7 @@ def test_interior_colour_steps(pair):
 def test_cut_colour_steps_every_variant(pair):
     pb, H = pair
     ref = None
-    for v in (0, 1, 2, 3, 4, 5):
+    for v in (0, 1, 2, 3, 4, 5, 6):
         pb.set_kernel_variant(_lib.CF_VAR_CUT, v)
         outs = _steps(pb, H, True)
         if ref is None:

@@ -110,7 +110,7 @@ def test_cut_variants_match_oracle_and_each_other(pair, prec, tol):
     if name != "ball3d_q2_n16":
         pytest.skip("one cut kernel form for (d, p) with at most 64 closure nodes")
     ref = None
-    for v in (1, 2, 3, 4, 5):
+    for v in (1, 2, 3, 4, 5, 6):
         pb.set_kernel_variant(_lib.CF_VAR_CUT, v)
         outs = _steps(pb, H, True, prec, tol)
         if ref is None:
@@ -145,7 +145,7 @@ def test_solve_with_every_variant_takes_the_oracle_iterations(pair):
 
 def test_bad_variants_are_rejected(pair):
     pb, _, _ = pair
-    for fam, v in ((0, 1), (4, 1), (_lib.CF_VAR_INTERIOR, 5), (_lib.CF_VAR_CUT, 6), (_lib.CF_VAR_CUT, -1),
+    for fam, v in ((0, 1), (4, 1), (_lib.CF_VAR_INTERIOR, 5), (_lib.CF_VAR_CUT, 7), (_lib.CF_VAR_CUT, -1),
                    (_lib.CF_VAR_OPERATOR, 3)):
         with pytest.raises(cm.CutmgError) as e:
             pb.set_kernel_variant(fam, v)
