@@ -130,10 +130,14 @@ FP32_PEAK_TFLOPS = 78.5
 # kernels.cuh and cutpipe.cuh).
 TRAFFIC = {
     # ncu, one finest-level launch of the 128^3 mixed solve (colour 2 of the
-    # first cut sweep): DRAM 117.74 + 4.30 MB against 89.32 MB algorithmic
+    # first cut sweep): DRAM 117.74 + 3.99 MB against 89.32 MB algorithmic
     # (profiles/k_cut_warp_ball3d_q2_n128_mixed.md)
-    ("k_cut_warp", "fp32"): {"dram_over_algorithmic": 122.04 / 89.32,
-                             "kernels_sha256": "29ba229c65e5860776d4ec851f02d22c3bc411c152ef2d925a941cffba35c220"},
+    ("k_cut_warp", "fp32"): {"dram_over_algorithmic": 121.73 / 89.32,
+                             "kernels_sha256": "bdf2fa516d56fd94f76f6dabdb35aee623d8d9638b9252c4d75d029b7e533075"},
+    # the same launch of the FP64 solve: DRAM 223.33 + 4.98 MB against
+    # 171.20 MB algorithmic (profiles/k_cut_warp_ball3d_q2_n128_mixed.md)
+    ("k_cut_warp", "fp64"): {"dram_over_algorithmic": 228.31 / 171.20,
+                             "kernels_sha256": "bdf2fa516d56fd94f76f6dabdb35aee623d8d9638b9252c4d75d029b7e533075"},
 }
 
 
