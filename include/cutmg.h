@@ -207,7 +207,7 @@ cf_status cf_set_precision(cf_problem* pb, int precision);
 typedef enum { CF_VAR_INTERIOR = 1, CF_VAR_CUT = 2, CF_VAR_OPERATOR = 3 } cf_variant_family;
 cf_status cf_set_kernel_variant(cf_problem* pb, int family, int variant);
 
-/* Polls the tensor-core interior-patch kernel (mixed form, 3D) makes on the
+/* Polls the tensor-core interior-patch kernel (mixed form, 2D and 3D) makes on the
  * mbarrier of its tensor-core product before it gives up (default 2^22).  A
  * block that gives up records the failure and waits (bounded, 2^22 polls)
  * for its own product to complete before it reads it; the next cf_solve /

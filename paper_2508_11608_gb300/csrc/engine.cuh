@@ -146,6 +146,7 @@ class Engine final : public EngineBase {
     int nbulk;
     int* bnd;
     int nbnd;
+    double bnd_work[3] = {0.0, 0.0, 0.0};  // boundary-row launch: flops, scalars, index bytes
     int* sf_tiles = nullptr;     // sum-factorised operator: tiles of bulk positions
     uint32_t* sf_masks = nullptr;
     int nsf = 0;
@@ -1071,6 +1072,70 @@ class Engine final : public EngineBase {
     c.bnd = pool_.upload<int>(h.bnd_node);
     c.nbnd = (int)h.bnd_node.size();
     {
+      // work model of one boundary-row launch (k_apply_bnd): per node its
+      // active cells' rows (2 NB flops; NB values of x, plus the NB entries
+      // of a cut cell's row) and its ghost faces (2 p flops, p moments);
+      // b read and y written
+      double fl = 0.0, sc = 0.0;
+      const int N = h.N, n = h.n;
+      for (int node : h.bnd_node) {
+        int idx[3] = {0, 0, 0}, u = node;
+        for (int k = 0; k < DIM; ++k) {
+          idx[k] = u % n;
+          u /= n;
+        }
+        int cc[3][2], nopt[3];
+        for (int k = 0; k < DIM; ++k) {
+          const int a = idx[k] / P, r = idx[k] - a * P;
+          int m = 0;
+          if (r == 0) {
+            if (a - 1 >= 0) cc[k][m++] = a - 1;
+            if (a < N) cc[k][m++] = a;
+          } else {
+            cc[k][m++] = a;
+          }
+          nopt[k] = m;
+        }
+        const int tot = DIM == 2 ? nopt[0] * nopt[1] : nopt[0] * nopt[1] * nopt[2];
+        for (int t = 0; t < tot; ++t) {
+          int q = t, cell = 0, st = 1;
+          for (int k = 0; k < DIM; ++k) {
+            cell += cc[k][q % nopt[k]] * st;
+            q /= nopt[k];
+            st *= N;
+          }
+          const uint8_t f = h.cflag[cell];
+          if (!(f & kFlagActive)) continue;
+          fl += 2.0 * NB;
+          sc += NB + ((f & kFlagCut) ? NB : 0);
+        }
+        for (int k = 0; k < DIM; ++k) {
+          const int a = idx[k] / P, r = idx[k] - a * P;
+          const int Llo = std::max(0, r == 0 ? a - 2 : a - 1), Lhi = std::min(a, N - 2);
+          int td[2] = {0, 0}, q2 = 0;
+          for (int j = 0; j < DIM; ++j)
+            if (j != k) td[q2++] = j;
+          const int n0 = nopt[td[0]], n1 = DIM == 3 ? nopt[td[1]] : 1;
+          for (int Lk = Llo; Lk <= Lhi; ++Lk)
+            for (int u0 = 0; u0 < n0; ++u0)
+              for (int u1 = 0; u1 < n1; ++u1) {
+                int c[3] = {0, 0, 0};
+                c[k] = Lk;
+                c[td[0]] = cc[td[0]][u0];
+                if (DIM == 3) c[td[1]] = cc[td[1]][u1];
+                const int64_t cell = c[0] + (int64_t)N * (c[1] + (DIM == 3 ? (int64_t)N * c[2] : 0));
+                if (h.face_id[(size_t)cell * DIM + k] < 0) continue;
+                fl += 2.0 * P;
+                sc += P;
+              }
+        }
+        sc += 2.0;
+      }
+      c.bnd_work[0] = fl;
+      c.bnd_work[1] = sc;
+      c.bnd_work[2] = 4.0 * (double)h.bnd_node.size();
+    }
+    {
       // tiles of the sum-factorised operator: the bulk positions grouped by
       // the tile of SfGeo positions that contains them
       using SG = SfGeo<DIM, P>;
@@ -1300,7 +1365,7 @@ class Engine final : public EngineBase {
       k_apply_bnd<DIM, P, T><<<blocks_for(c.nbnd, 128), 128, 0, s>>>(D.op, x, b, y, c.bnd, c.nbnd);
       count_launch("apply boundary");
       prof_mark(4, l, s);
-      prof_work(4, l, 0.0, 0.0);
+      prof_work(4, l, c.bnd_work[0], c.bnd_work[1] * sizeof(T) + c.bnd_work[2]);
     }
   }
 
