@@ -5,6 +5,7 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -1069,8 +1070,25 @@ class Engine final : public EngineBase {
     c.dofs = pool_.upload<int64_t>(h.dofs);
     c.bulk = pool_.upload<int>(h.bulk_pos);
     c.nbulk = (int)h.bulk_pos.size();
-    c.bnd = pool_.upload<int>(h.bnd_node);
-    c.nbnd = (int)h.bnd_node.size();
+    {
+      // boundary nodes grouped by the number of directions in which they lie
+      // on a cell boundary (8, 4, 2 or 1 cells in 3D), lattice order within
+      // a group: a warp's rows then loop over the same number of cells and
+      // faces (each node's row is formed alone, so the order changes no
+      // result)
+      std::vector<int> bnd = h.bnd_node;
+      auto on_planes = [&](int node) {
+        int c = 0, u = node;
+        for (int k = 0; k < DIM; ++k) {
+          c += (u % h.n) % P == 0;
+          u /= h.n;
+        }
+        return c;
+      };
+      std::stable_sort(bnd.begin(), bnd.end(), [&](int a, int b) { return on_planes(a) > on_planes(b); });
+      c.bnd = pool_.upload<int>(bnd);
+      c.nbnd = (int)bnd.size();
+    }
     {
       // work model of one boundary-row launch (k_apply_bnd): per node its
       // active cells' rows (2 NB flops; NB values of x, plus the NB entries
