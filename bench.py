@@ -519,6 +519,8 @@ def run_batched(cm, torch, dev, stream, args):
             "iterations_min_max": [min(its), max(its)],
             "worst_true_rel_residual": max(i["true_rel_residual"] for i in infos),
             "launches_per_batch_solve": launches, "host_setup_s": setup_s,
+            "launch_mode": "each CG iteration's two halves (q = A p .. (r, r) and z = B r .. p) replayed as "
+                           "CUDA graphs captured per version of the work lists",
             "workload": "2D flowers r = 0.6 + 0.1 cos(m (theta - theta0)), m in 3..7, offset <= 0.05, "
                         "N in {32, 64, 128, 256}, Q2/Q3, coarsest 8^2, seed 20260101"}
 
