@@ -1,8 +1,9 @@
 """cf_coarse_solve_noalloc: the coarse solve for callers that cannot let a
 library call allocate device memory (graph capture, caller-owned memory
 arenas, allocation-free hot loops).  Its result must equal the allocating
-cf_coarse_solve's on two calls in a row, and it must refuse coarse levels
-larger than its fixed staging array.  Kept in its own file, collected last."""
+cf_coarse_solve's on two calls in a row, it must refuse coarse levels larger
+than its fixed staging array, leave the device's free memory unchanged and
+run inside a CUDA graph capture.  Kept in its own file, collected last."""
 
 import numpy as np
 import pytest
@@ -62,3 +63,27 @@ def test_noalloc_call_leaves_free_device_memory_unchanged():
     torch.cuda.synchronize()
     free1, _ = torch.cuda.mem_get_info()
     assert free1 == free0
+
+
+def test_noalloc_coarse_solve_runs_inside_cuda_graph_capture():
+    # captured in the global capture mode, where any device allocation during
+    # the capture (by this thread or another) fails it; the graph then
+    # replays the solve on new contents of the same input buffer
+    pb = cm.Problem(**problem_kwargs("ball3d_q2_n16"))
+    n0 = pb.n_dofs(0)
+    b0 = torch.tensor(random_vector(n0, 910), dtype=torch.float64, device=DEV)
+    x0 = torch.zeros(n0, dtype=torch.float64, device=DEV)
+    pb.coarse_solve_noalloc(b0, x0)  # first call outside the capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, capture_error_mode="global"):
+        pb.coarse_solve_noalloc(b0, x0)
+    for seed in (911, 912):
+        b0.copy_(torch.tensor(random_vector(n0, seed), dtype=torch.float64, device=DEV))
+        x0.fill_(np.nan)
+        g.replay()
+        ref = torch.zeros(n0, dtype=torch.float64, device=DEV)
+        pb.coarse_solve(b0, ref, precision=cm.CF_FP64)
+        torch.cuda.synchronize()
+        r, x = ref.cpu().numpy(), x0.cpu().numpy()
+        assert np.abs(x - r).max() <= 1e-12 * np.abs(r).max(), seed
