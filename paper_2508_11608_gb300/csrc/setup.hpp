@@ -95,7 +95,7 @@ struct HostLevel {
   std::vector<uint16_t> members;  // closure-local node index per cut-patch DoF
   std::vector<int> member_node;   // lattice index per cut-patch DoF
   // ghost-face terms of each cut-patch DoF's row: entries fent[fofs[i] ..
-  // fofs[i+1]) = (face id * (p+1)^(d-1) + t) * 8 + i_k, and per colour the
+  // fofs[i+1]) = (face id * (p+1)^(d-1) + t) * 16 + i_k, and per colour the
   // ghost faces those rows need (colour c: cfaces[cf_start[c] .. cf_start[c+1]))
   std::vector<int> fofs, fent;
   std::vector<int> cfaces, cf_start;
@@ -134,7 +134,7 @@ struct HostLevel {
   // Ghost-entry lists of the cut patches: patch j's run cut_gent[cut_geoff[j]
   // .. cut_geoff[j + 1]) (a multiple of 8 entries) holds m + 1 row offsets,
   // then per DoF row (member order) the ghost faces whose stencil contains
-  // the DoF: slot | (i << 6) | (t << 9), with i the node along the face's
+  // the DoF: slot | (i << 6) | (t << 10), with i the node along the face's
   // normal, t the tangential node and slot the face's moment slot in the
   // patch: the set block-boundary bits of cut_gmask[j] first (bit order, the
   // order of its cut_gboff slots), then the set middle-plane bits (bit
