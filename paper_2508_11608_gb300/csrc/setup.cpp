@@ -16,9 +16,12 @@
 #include <algorithm>
 #include <functional>
 
+#include <omp.h>
+
 #include <cmath>
 #include <cstring>
 #include <stdexcept>
+#include <string>
 
 namespace cutmg {
 namespace {
@@ -412,6 +415,22 @@ uint8_t cell_flag(const HostLevel& L, const int* c) {
   return L.cflag[f];
 }
 
+// Runs f(i, out) for i in [0, n) over contiguous blocks of i shared out to
+// the threads, and appends what the calls pushed to `out` in increasing i:
+// the result is the serial loop's, whatever the thread count.
+template <class T, class Alloc, class F>
+void ordered_collect(int64_t n, std::vector<T, Alloc>& out, F&& f) {
+  const int64_t nblk = std::max<int64_t>(1, std::min<int64_t>(n, 16 * std::max(1, omp_get_max_threads())));
+  std::vector<std::vector<T>> part(nblk);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t b = 0; b < nblk; ++b)
+    for (int64_t i = n * b / nblk; i < n * (b + 1) / nblk; ++i) f(i, part[b]);
+  size_t tot = out.size();
+  for (const auto& q : part) tot += q.size();
+  out.reserve(tot);
+  for (const auto& q : part) out.insert(out.end(), q.begin(), q.end());
+}
+
 // "plain" cell: active, uncut, no cut face-neighbour (no ghost face)
 bool plain_cell(const HostLevel& L, const int* c) {
   uint8_t f = cell_flag(L, c);
@@ -423,6 +442,24 @@ bool plain_cell(const HostLevel& L, const int* c) {
       if (cell_flag(L, cj) & kFlagCut) return false;
     }
   return true;
+}
+
+// plain_cell of every cell of the level (cell order)
+std::vector<uint8_t> plain_flags(const HostLevel& L) {
+  const int d = L.d, N = L.N;
+  const int64_t ncell = ipow(N, d);
+  std::vector<uint8_t> pl(ncell);
+#pragma omp parallel for schedule(static)
+  for (int64_t c = 0; c < ncell; ++c) {
+    int ci[3] = {0, 0, 0};
+    int64_t t = c;
+    for (int k = 0; k < d; ++k) {
+      ci[k] = (int)(t % N);
+      t /= N;
+    }
+    pl[c] = plain_cell(L, ci) ? 1 : 0;
+  }
+  return pl;
 }
 
 // Interior patches (every cell of the patch plain): the two-cell 1D mass and
@@ -549,11 +586,11 @@ void interior_patch_tables(const RefTables& R, HostLevel& L) {
 void patch_vertex_sets(HostLevel& L) {
   const int d = L.d, N = L.N, np = N + 1, ncol = 1 << d;
   auto cflag_at = [&](const int* c) { return cell_flag(L, c); };
-  auto plain = [&](const int* c) { return plain_cell(L, c); };
   const int64_t nvert = (int64_t)ipow(np, d);
   std::vector<std::vector<int>> cart(ncol), cutv(ncol);
   // per vertex: -1 (no active cell around it), else colour + 8 if Cartesian
   std::vector<int8_t> vkind(nvert);
+  const std::vector<uint8_t> pl = plain_flags(L);
 #pragma omp parallel for schedule(static)
   for (int64_t q = 0; q < nvert; ++q) {
     int v[3] = {0, 0, 0};
@@ -565,18 +602,28 @@ void patch_vertex_sets(HostLevel& L) {
     bool any = false, cartesian = true;
     for (int s = 0; s < (1 << d); ++s) {
       int c[3] = {0, 0, 0};
-      for (int k = 0; k < d; ++k) c[k] = v[k] - 1 + ((s >> k) & 1);
+      bool in = true;
+      int64_t ci = 0, st = 1;
+      for (int k = 0; k < d; ++k) {
+        c[k] = v[k] - 1 + ((s >> k) & 1);
+        in = in && c[k] >= 0 && c[k] < N;
+        ci += (int64_t)c[k] * st;
+        st *= N;
+      }
       if (cflag_at(c) & kFlagActive) any = true;
-      if (!plain(c)) cartesian = false;
+      if (!in || !pl[ci]) cartesian = false;  // plain_cell is false outside the mesh
     }
     int col = 0;
     for (int k = 0; k < d; ++k) col |= (v[k] & 1) << k;
     vkind[q] = any ? (int8_t)(col + (cartesian ? 8 : 0)) : (int8_t)-1;
   }
-  for (int64_t q = 0; q < nvert; ++q) {
-    if (vkind[q] < 0) continue;
-    const int col = vkind[q] & 7;
-    ((vkind[q] & 8) ? cart : cutv)[col].push_back((int)q);
+  for (int col = 0; col < ncol; ++col) {
+    ordered_collect(nvert, cart[col], [&](int64_t q, std::vector<int>& o) {
+      if (vkind[q] == col + 8) o.push_back((int)q);
+    });
+    ordered_collect(nvert, cutv[col], [&](int64_t q, std::vector<int>& o) {
+      if (vkind[q] == col) o.push_back((int)q);
+    });
   }
   L.cart_start.assign(ncol + 1, 0);
   L.cut_start.assign(ncol + 1, 0);
@@ -645,9 +692,16 @@ void cut_patch_members(HostLevel& L, bool dry) {
     moff += m;
     // every inverse starts on a 16-byte boundary in FP64 and FP32 (TMA bulk copies)
     ioff += ((int64_t)m * m + 3) / 4 * 4;
-    for (int col = 0; col < ncol; ++col)
-      if (j >= L.cut_start[col] && j < L.cut_start[col + 1]) L.cut_maxm2[col] = std::max(L.cut_maxm2[col], m * m);
-    L.members.insert(L.members.end(), mem[j].begin(), mem[j].end());
+  }
+  for (int col = 0; col < ncol; ++col)
+    for (int j = L.cut_start[col]; j < L.cut_start[col + 1]; ++j)
+      L.cut_maxm2[col] = std::max(L.cut_maxm2[col], L.cut_n[j] * L.cut_n[j]);
+  L.members.resize((size_t)moff);
+  L.member_node.resize((size_t)moff);
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t j = 0; j < ncp; ++j) {
+    const int m = L.cut_n[j];
+    std::copy(mem[j].begin(), mem[j].end(), L.members.begin() + L.cut_moff[j]);
     int v[3] = {0, 0, 0};
     int64_t t = L.cut_vert[j];
     for (int k = 0; k < d; ++k) {
@@ -662,7 +716,7 @@ void cut_patch_members(HostLevel& L, bool dry) {
         o /= C;
         st *= n;
       }
-      L.member_node.push_back((int)node);
+      L.member_node[(size_t)L.cut_moff[j] + e] = (int)node;
     }
   }
   L.n_inv = ioff;
@@ -1084,7 +1138,11 @@ void cut_patch_records(HostLevel& L, bool dry) {
   L.bf_start.assign(ncol + 1, 0);
   L.bf_face.clear();
   L.bf_dst.clear();
-  for (int col = 0; col < ncol; ++col) {
+  // the colours side by side, each into its own lists, joined in colour order
+  std::vector<std::vector<int>> bff(ncol), bfd(ncol);
+  std::vector<std::string> bf_err(ncol);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int col = 0; col < ncol; ++col) try {
     std::vector<std::pair<int, int>> fd;  // (face id, slot)
     for (int j = L.cut_start[col]; j < L.cut_start[col + 1]; ++j) {
       int v[3] = {0, 0, 0};
@@ -1108,19 +1166,27 @@ void cut_patch_records(HostLevel& L, bool dry) {
       }
     }
     std::sort(fd.begin(), fd.end());
+    std::vector<int>&face = bff[col], &dst = bfd[col];
     for (size_t i = 0; i < fd.size();) {
-      L.bf_face.push_back(fd[i].first);
-      L.bf_dst.push_back(fd[i].second);
+      face.push_back(fd[i].first);
+      dst.push_back(fd[i].second);
       if (i + 1 < fd.size() && fd[i + 1].first == fd[i].first) {
         if (i + 2 < fd.size() && fd[i + 2].first == fd[i].first)
           throw std::logic_error("a ghost face read by three patches of one colour");
-        L.bf_dst.push_back(fd[i + 1].second);
+        dst.push_back(fd[i + 1].second);
         i += 2;
       } else {
-        L.bf_dst.push_back(-1);
+        dst.push_back(-1);
         i += 1;
       }
     }
+  } catch (const std::exception& e) {
+    bf_err[col] = e.what();
+  }
+  for (int col = 0; col < ncol; ++col) {
+    if (!bf_err[col].empty()) throw std::logic_error(bf_err[col]);
+    L.bf_face.insert(L.bf_face.end(), bff[col].begin(), bff[col].end());
+    L.bf_dst.insert(L.bf_dst.end(), bfd[col].begin(), bfd[col].end());
     L.bf_start[col + 1] = (int)L.bf_face.size();
   }
   // ghost-entry lists (the faces on the block planes whose stencil contains
@@ -1179,6 +1245,7 @@ void cut_patch_records(HostLevel& L, bool dry) {
     L.cut_geoff.assign(ncp + 1, 0);
     for (int64_t j = 0; j < ncp; ++j) L.cut_geoff[j + 1] = L.cut_geoff[j] + (int)lists[j].size();
     L.cut_gent.resize(L.cut_geoff[ncp]);
+#pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < ncp; ++j) std::copy(lists[j].begin(), lists[j].end(), L.cut_gent.begin() + L.cut_geoff[j]);
   }
   // work model of the record kernel (replaces the entry-list kernel's):
@@ -1231,23 +1298,29 @@ void cut_patch_records(HostLevel& L, bool dry) {
   L.rec.resize((size_t)L.n_rec);
 #pragma omp parallel for schedule(dynamic, 64)
   for (int64_t j = 0; j < ncp; ++j) {
+    // every entry written once: rows, their zero padding, and zeros after
+    // the last row
     double* out = &L.rec[(size_t)L.cut_roff[j]];
-    std::fill(out, L.rec.data() + L.cut_roff[j + 1], 0.0);
+    double* const end = L.rec.data() + L.cut_roff[j + 1];
     const int m = L.cut_n[j];
     const double* A = &L.inv[(size_t)L.cut_ioff[j]];
     const int MP = cut_n_pad(m);
-    for (int i = 0; i < m; ++i) std::copy(A + (size_t)i * m, A + (size_t)(i + 1) * m, out + (size_t)i * MP);
+    for (int i = 0; i < m; ++i) {
+      std::copy(A + (size_t)i * m, A + (size_t)(i + 1) * m, out + (size_t)i * MP);
+      std::fill(out + (size_t)i * MP + m, out + (size_t)(i + 1) * MP, 0.0);
+    }
     double* rp = out + (size_t)m * MP;
     const int i0 = L.cut_item_off[j], i1 = L.cut_item_off[j + 1];
-    int r = 0;
     for (int q = i0; q < i1; ++q) {
       const int sc = L.cut_items[q] / NB, jj = L.cut_items[q] % NB;
       const int id = L.cut_cell[(size_t)j * NCELL + sc];
       if (id < 0) continue;
       const double* K = &L.cutmat[((size_t)id * NB + jj) * NB];
-      std::copy(K, K + NB, rp + (size_t)r * NBP);
-      ++r;
+      std::copy(K, K + NB, rp);
+      std::fill(rp + NB, rp + NBP, 0.0);
+      rp += NBP;
     }
+    std::fill(rp, end, 0.0);
   }
 }
 
@@ -1283,16 +1356,19 @@ void build_level(const SetupParams& prm, const RefTables& R, int N, HostLevel& L
   const int64_t ncell = (int64_t)ipow(N, d), nnode = (int64_t)ipow(n, d);
   L.cflag.assign(ncell, 0);
   L.cut_id.assign(ncell, -1);
-  // classification (Sec. 2.1: active = meets Omega, cut = meets Gamma)
-#pragma omp parallel for schedule(static)
+  // classification (Sec. 2.1: active = meets Omega, cut = meets Gamma), and
+  // the range of the active cells' coordinates
+  int cmin[3] = {N, N, N}, cmax[3] = {-1, -1, -1};
+#pragma omp parallel for schedule(static) reduction(min : cmin[:3]) reduction(max : cmax[:3])
   for (int64_t c = 0; c < ncell; ++c) {
     double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    int ci[3] = {0, 0, 0};
     int64_t t = c;
     for (int k = 0; k < d; ++k) {
-      int ck = (int)(t % N);
+      ci[k] = (int)(t % N);
       t /= N;
-      lo[k] = prm.lo + h * ck;
-      hi[k] = prm.lo + h * (ck + 1);
+      lo[k] = prm.lo + h * ci[k];
+      hi[k] = prm.lo + h * (ci[k] + 1);
     }
     double mn, mx;
     prm.ls.box_minmax(lo, hi, mn, mx);
@@ -1300,16 +1376,23 @@ void build_level(const SetupParams& prm, const RefTables& R, int N, HostLevel& L
     if (mn < 0.0) f |= kFlagActive;
     if (mn < 0.0 && mx > 0.0) f |= kFlagCut;
     L.cflag[c] = f;
+    if (f & kFlagActive)
+      for (int k = 0; k < d; ++k) {
+        cmin[k] = std::min(cmin[k], ci[k]);
+        cmax[k] = std::max(cmax[k], ci[k]);
+      }
   }
   std::vector<int64_t> cut_cells;
-  for (int64_t c = 0; c < ncell; ++c) {
-    if (L.cflag[c] & kFlagActive) L.n_active++;
-    if (L.cflag[c] & kFlagCut) {
-      L.cut_id[c] = (int)cut_cells.size();
-      cut_cells.push_back(c);
-    }
-  }
+  ordered_collect(ncell, cut_cells, [&](int64_t c, std::vector<int64_t>& o) {
+    if (L.cflag[c] & kFlagCut) o.push_back(c);
+  });
   L.n_cut = (int64_t)cut_cells.size();
+  int64_t n_active = 0;
+#pragma omp parallel for schedule(static) reduction(+ : n_active)
+  for (int64_t c = 0; c < ncell; ++c) n_active += (L.cflag[c] & kFlagActive) ? 1 : 0;
+  L.n_active = n_active;
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < L.n_cut; ++i) L.cut_id[cut_cells[i]] = (int)i;
   if (!prm.dry) L.cutmat.resize((size_t)L.n_cut * NB * NB);  // every block written below
   if (cut_rhs) cut_rhs->assign((size_t)L.n_cut * NB, 0.0);
   CutQuadrature Q(prm.ls, prm.quad_q);
@@ -1360,40 +1443,40 @@ void build_level(const SetupParams& prm, const RefTables& R, int N, HostLevel& L
   for (int a = 0; a <= p; ++a)
     for (int b = 0; b <= p; ++b) L.Mhat[a][b] = R.M1[a * (p + 1) + b];
   // nodes
+  // the nodes of the active cells, cell layers (outermost coordinate) in two
+  // passes, even then odd: the layers of one pass share no node
   L.nact.assign(nnode, 0);
-  for (int64_t c = 0; c < ncell; ++c) {
-    if (!(L.cflag[c] & kFlagActive)) continue;
-    int ci[3] = {0, 0, 0};
-    int64_t t = c;
-    for (int k = 0; k < d; ++k) {
-      ci[k] = (int)(t % N);
-      t /= N;
-    }
-    for (int j = 0; j < NB; ++j) {
-      int a[3] = {0, 0, 0};
-      R.split(j, a);
-      int64_t node = 0, st = 1;
-      for (int k = 0; k < d; ++k) {
-        node += (int64_t)(p * ci[k] + a[k]) * st;
-        st *= n;
+  const int64_t layer = ncell / N;
+  for (int par = 0; par < 2; ++par) {
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int cl = par; cl < N; cl += 2)
+      for (int64_t c = cl * layer; c < (cl + 1) * layer; ++c) {
+        if (!(L.cflag[c] & kFlagActive)) continue;
+        int ci[3] = {0, 0, 0};
+        int64_t t = c;
+        for (int k = 0; k < d; ++k) {
+          ci[k] = (int)(t % N);
+          t /= N;
+        }
+        for (int j = 0; j < NB; ++j) {
+          int a[3] = {0, 0, 0};
+          R.split(j, a);
+          int64_t node = 0, st = 1;
+          for (int k = 0; k < d; ++k) {
+            node += (int64_t)(p * ci[k] + a[k]) * st;
+            st *= n;
+          }
+          L.nact[node] = 1;
+        }
       }
-      L.nact[node] = 1;
-    }
   }
+  ordered_collect(nnode, L.dofs, [&](int64_t i, std::vector<int64_t>& o) {
+    if (L.nact[i]) o.push_back(i);
+  });
+  // the active nodes span p cmin_k .. p (cmax_k + 1) along every direction
   for (int k = 0; k < 3; ++k) {
-    L.bb_lo[k] = (k < d) ? n : 0;
-    L.bb_hi[k] = (k < d) ? -1 : 0;
-  }
-  for (int64_t i = 0; i < nnode; ++i) {
-    if (!L.nact[i]) continue;
-    L.dofs.push_back(i);
-    int64_t t = i;
-    for (int k = 0; k < d; ++k) {
-      int ik = (int)(t % n);
-      t /= n;
-      L.bb_lo[k] = std::min(L.bb_lo[k], ik);
-      L.bb_hi[k] = std::max(L.bb_hi[k], ik);
-    }
+    L.bb_lo[k] = (k < d) ? (cmax[k] < 0 ? n : p * cmin[k]) : 0;
+    L.bb_hi[k] = (k < d) ? (cmax[k] < 0 ? -1 : p * (cmax[k] + 1)) : 0;
   }
   auto cflag_at = [&](const int* c) -> uint8_t {
     int64_t f = 0, st = 1;
@@ -1406,7 +1489,9 @@ void build_level(const SetupParams& prm, const RefTables& R, int N, HostLevel& L
   };
   // ghost faces: list and per-cell ids
   L.face_id.assign((size_t)ncell * d, -1);
-  for (int64_t c = 0; c < ncell; ++c) {
+  ordered_collect(ncell, L.ghost_faces, [&](int64_t c, std::vector<int>& o) {
+    const uint8_t f1 = L.cflag[c];
+    if (!(f1 & kFlagActive)) return;
     int ci[3] = {0, 0, 0};
     int64_t t = c;
     for (int k = 0; k < d; ++k) {
@@ -1416,72 +1501,50 @@ void build_level(const SetupParams& prm, const RefTables& R, int N, HostLevel& L
     for (int k = 0; k < d; ++k) {
       int cj[3] = {ci[0], ci[1], ci[2]};
       cj[k] += 1;
-      uint8_t f1 = L.cflag[c], f2 = cflag_at(cj);
-      if ((f1 & kFlagActive) && (f2 & kFlagActive) && ((f1 | f2) & kFlagCut)) {
-        L.face_id[(size_t)c * d + k] = (int)L.ghost_faces.size();
-        L.ghost_faces.push_back((int)(c * d + k));
-        L.n_ghost++;
-      }
+      const uint8_t f2 = cflag_at(cj);
+      if ((f2 & kFlagActive) && ((f1 | f2) & kFlagCut)) o.push_back((int)(c * d + k));
     }
-  }
-  // "plain" cell: active, uncut, no cut face-neighbour (no ghost face)
-  auto plain = [&](const int* c) -> bool {
-    uint8_t f = cflag_at(c);
-    if (!(f & kFlagActive) || (f & kFlagCut)) return false;
-    for (int k = 0; k < d; ++k)
-      for (int s = -1; s <= 1; s += 2) {
-        int cj[3] = {c[0], c[1], c[2]};
-        cj[k] += s;
-        if (cflag_at(cj) & kFlagCut) return false;
-      }
-    return true;
-  };
-  // apply: bulk positions and boundary nodes
+  });
+  L.n_ghost = (int64_t)L.ghost_faces.size();
+#pragma omp parallel for schedule(static)
+  for (int64_t g = 0; g < L.n_ghost; ++g) L.face_id[L.ghost_faces[g]] = (int)g;
+  // apply: bulk positions (2^d plain cells around them) and boundary nodes
   {
     const int np = N + 1;
     const int64_t npos = (int64_t)ipow(np, d);
+    const std::vector<uint8_t> pl = plain_flags(L);
     std::vector<uint8_t> bulk(npos, 0);
-    for (int64_t q = 0; q < npos; ++q) {
+    ordered_collect(npos, L.bulk_pos, [&](int64_t q, std::vector<int>& o) {
       int a[3] = {0, 0, 0};
       int64_t t = q;
-      bool ok = true;
       for (int k = 0; k < d; ++k) {
         a[k] = (int)(t % np);
         t /= np;
-        if (a[k] < 1 || a[k] > N - 1) ok = false;
+        if (a[k] < 1 || a[k] > N - 1) return;
       }
-      if (!ok) continue;
-      for (int s = 0; s < (1 << d) && ok; ++s) {
-        int c[3] = {0, 0, 0};
-        for (int k = 0; k < d; ++k) c[k] = a[k] - ((s >> k) & 1);
-        if (!plain(c)) ok = false;
+      for (int s = 0; s < (1 << d); ++s) {
+        int64_t c = 0, st = 1;
+        for (int k = 0; k < d; ++k) {
+          c += (int64_t)(a[k] - ((s >> k) & 1)) * st;
+          st *= N;
+        }
+        if (!pl[c]) return;
       }
-      if (ok) {
-        bulk[q] = 1;
-        L.bulk_pos.push_back((int)q);
-      }
-    }
-    std::vector<uint8_t> owns(npos, 0);
-    for (int64_t i : L.dofs) {
+      bulk[q] = 1;
+      o.push_back((int)q);
+    });
+    // the owner position of node i is (i_k / p)_k
+    ordered_collect((int64_t)L.dofs.size(), L.bnd_node, [&](int64_t e, std::vector<int>& o) {
+      const int64_t i = L.dofs[e];
       int64_t t = i, q = 0, st = 1;
       for (int k = 0; k < d; ++k) {
-        int ik = (int)(t % n);
+        const int ik = (int)(t % n);
         t /= n;
         q += (int64_t)(ik / p) * st;
         st *= np;
       }
-      owns[q] = 1;
-    }
-    for (int64_t i : L.dofs) {
-      int64_t t = i, q = 0, st = 1;
-      for (int k = 0; k < d; ++k) {
-        int ik = (int)(t % n);
-        t /= n;
-        q += (int64_t)(ik / p) * st;
-        st *= np;
-      }
-      if (!bulk[q]) L.bnd_node.push_back((int)i);
-    }
+      if (!bulk[q]) o.push_back((int)i);
+    });
   }
   interior_patch_tables(R, L);
   build_patches(R, L, prm.dry, prm.device_inverse);
@@ -1648,8 +1711,12 @@ void build_rhs(const SetupParams& prm, const RefTables& R, const HostLevel& L, s
                bool parallel, const std::vector<double>* cut_rhs = nullptr) {
   const int d = L.d, p = L.p, N = L.N, n = L.n, NB = R.NB, q = prm.quad_q;
   const double h = L.h;
-  std::vector<int64_t> map((size_t)ipow(n, d), -1);
-  for (size_t i = 0; i < L.dofs.size(); ++i) map[L.dofs[i]] = (int64_t)i;
+  const int64_t nnode = ipow(n, d), ndof = (int64_t)L.dofs.size();
+  std::vector<int64_t, DefaultInitAllocator<int64_t>> map((size_t)nnode);
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < nnode; ++i) map[i] = -1;
+#pragma omp parallel for schedule(static)
+  for (int64_t e = 0; e < ndof; ++e) map[L.dofs[e]] = e;
   b.assign(L.dofs.size(), 0.0);
   GaussRule g = gauss_legendre01(q);
   const int nq = ipow(q, d);
@@ -1706,24 +1773,48 @@ void build_rhs(const SetupParams& prm, const RefTables& R, const HostLevel& L, s
         cut_cell_rhs(R, Q.cell(lo, hi), lo, h, prm.gamma_D, fsrc, gdir, loc);
       }
     }
-    for (int64_t ic = c0; ic < c1; ++ic) {
-      const int64_t c = act[ic];
-      int ci[3] = {0, 0, 0};
-      int64_t t = c;
+    // the sums: node rows (all coordinates but the first, row = node / n)
+    // split between the threads, each adding the terms of its rows cell by
+    // cell in order, so that every entry takes its terms in cell order
+    auto rows_of = [&](int64_t c, int* ci, int64_t& rlo, int64_t& rhi) {
+      int64_t t = c, st = 1;
+      rlo = rhi = 0;
       for (int k = 0; k < d; ++k) {
         ci[k] = (int)(t % N);
         t /= N;
-      }
-      const double* loc = &locs[(size_t)(ic - c0) * NB];
-      for (int j = 0; j < NB; ++j) {
-        int a[3] = {0, 0, 0};
-        R.split(j, a);
-        int64_t node = 0, st = 1;
-        for (int k = 0; k < d; ++k) {
-          node += (int64_t)(p * ci[k] + a[k]) * st;
+        if (k > 0) {
+          rlo += (int64_t)(p * ci[k]) * st;
+          rhi += (int64_t)(p * ci[k] + p) * st;
           st *= n;
         }
-        b[map[node]] += loc[j];
+      }
+    };
+    int cf[3], cl[3];
+    int64_t R0, R1, dummy;
+    rows_of(act[c0], cf, R0, dummy);
+    rows_of(act[c1 - 1], cl, dummy, R1);
+#pragma omp parallel if (parallel)
+    {
+      const int tid = omp_get_thread_num(), tn = omp_get_num_threads();
+      const int64_t span = R1 - R0 + 1;
+      const int64_t r0 = R0 + span * tid / tn, r1 = R0 + span * (tid + 1) / tn;
+      for (int64_t ic = c0; ic < c1; ++ic) {
+        int ci[3] = {0, 0, 0};
+        int64_t rlo, rhi;
+        rows_of(act[ic], ci, rlo, rhi);
+        if (rhi < r0 || rlo >= r1) continue;
+        const double* loc = &locs[(size_t)(ic - c0) * NB];
+        for (int j = 0; j < NB; ++j) {
+          int a[3] = {0, 0, 0};
+          R.split(j, a);
+          int64_t node = 0, st = 1;
+          for (int k = 0; k < d; ++k) {
+            node += (int64_t)(p * ci[k] + a[k]) * st;
+            st *= n;
+          }
+          const int64_t row = node / n;
+          if (row >= r0 && row < r1) b[map[node]] += loc[j];
+        }
       }
     }
   }
