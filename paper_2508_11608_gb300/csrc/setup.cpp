@@ -64,9 +64,13 @@ void spd_inverse(int n, double* A) {
       Aj[j] = d;
       for (int k = j + 1; k < n; ++k) Aj[k] /= d;
     }
-#pragma omp parallel for schedule(dynamic, 4) if (par)
-    for (int i = je; i < n; ++i) {
+    // rows i and i + 1 together (one load of each factor entry for both);
+    // entry k = i belongs to row i only
+#pragma omp parallel for schedule(dynamic, 2) if (par)
+    for (int i = je; i < n; i += 2) {
       double* __restrict__ Ai = A + (size_t)i * n;
+      double* __restrict__ Bi = Ai + n;
+      const bool two = i + 1 < n;
       int j = jb;
       // four factor rows per sweep, subtracted in row order
       for (; j + 4 <= je; j += 4) {
@@ -75,12 +79,31 @@ void spd_inverse(int n, double* A) {
         const double* __restrict__ U2 = U1 + n;
         const double* __restrict__ U3 = U2 + n;
         const double a0 = U0[i], a1 = U1[i], a2 = U2[i], a3 = U3[i];
-        for (int k = i; k < n; ++k) Ai[k] = (((Ai[k] - a0 * U0[k]) - a1 * U1[k]) - a2 * U2[k]) - a3 * U3[k];
+        Ai[i] = (((Ai[i] - a0 * U0[i]) - a1 * U1[i]) - a2 * U2[i]) - a3 * U3[i];
+        if (two) {
+          const double b0 = U0[i + 1], b1 = U1[i + 1], b2 = U2[i + 1], b3 = U3[i + 1];
+          for (int k = i + 1; k < n; ++k) {
+            const double u0 = U0[k], u1 = U1[k], u2 = U2[k], u3 = U3[k];
+            Ai[k] = (((Ai[k] - a0 * u0) - a1 * u1) - a2 * u2) - a3 * u3;
+            Bi[k] = (((Bi[k] - b0 * u0) - b1 * u1) - b2 * u2) - b3 * u3;
+          }
+        } else {
+          for (int k = i + 1; k < n; ++k) Ai[k] = (((Ai[k] - a0 * U0[k]) - a1 * U1[k]) - a2 * U2[k]) - a3 * U3[k];
+        }
       }
       for (; j < je; ++j) {
         const double* Uj = A + (size_t)j * n;
         const double a = Uj[i];
-        for (int k = i; k < n; ++k) Ai[k] -= a * Uj[k];
+        Ai[i] -= a * Uj[i];
+        if (two) {
+          const double bb = Uj[i + 1];
+          for (int k = i + 1; k < n; ++k) {
+            Ai[k] -= a * Uj[k];
+            Bi[k] -= bb * Uj[k];
+          }
+        } else {
+          for (int k = i + 1; k < n; ++k) Ai[k] -= a * Uj[k];
+        }
       }
     }
   }
@@ -111,23 +134,42 @@ void spd_inverse(int n, double* A) {
       const double* U1 = U0 + n;
       const double* U2 = U1 + n;
       const double* U3 = U2 + n;
-      for (int c = c0; c < c1; ++c) {
+      // the four multipliers of a row (entries k+1..k+3 take the earlier
+      // steps' updates in order)
+      auto mult = [&](double* Wc, double* w) {
+        w[0] = Wc[k] / U0[k];
+        Wc[k] = w[0];
+        Wc[k + 1] -= w[0] * U0[k + 1];
+        Wc[k + 2] -= w[0] * U0[k + 2];
+        Wc[k + 3] -= w[0] * U0[k + 3];
+        w[1] = Wc[k + 1] / U1[k + 1];
+        Wc[k + 1] = w[1];
+        Wc[k + 2] -= w[1] * U1[k + 2];
+        Wc[k + 3] -= w[1] * U1[k + 3];
+        w[2] = Wc[k + 2] / U2[k + 2];
+        Wc[k + 2] = w[2];
+        Wc[k + 3] -= w[2] * U2[k + 3];
+        w[3] = Wc[k + 3] / U3[k + 3];
+        Wc[k + 3] = w[3];
+      };
+      int c = c0;
+      for (; c + 2 <= c1; c += 2) {  // two rows per pass over q
         double* __restrict__ Wc = &W[(size_t)c * n];
-        const double w0 = Wc[k] / U0[k];
-        Wc[k] = w0;
-        Wc[k + 1] -= w0 * U0[k + 1];
-        Wc[k + 2] -= w0 * U0[k + 2];
-        Wc[k + 3] -= w0 * U0[k + 3];
-        const double w1 = Wc[k + 1] / U1[k + 1];
-        Wc[k + 1] = w1;
-        Wc[k + 2] -= w1 * U1[k + 2];
-        Wc[k + 3] -= w1 * U1[k + 3];
-        const double w2 = Wc[k + 2] / U2[k + 2];
-        Wc[k + 2] = w2;
-        Wc[k + 3] -= w2 * U2[k + 3];
-        const double w3 = Wc[k + 3] / U3[k + 3];
-        Wc[k + 3] = w3;
-        for (int q = k + 4; q < n; ++q) Wc[q] = (((Wc[q] - w0 * U0[q]) - w1 * U1[q]) - w2 * U2[q]) - w3 * U3[q];
+        double* __restrict__ Vc = Wc + n;
+        double w[4], v[4];
+        mult(Wc, w);
+        mult(Vc, v);
+        for (int q = k + 4; q < n; ++q) {
+          const double u0 = U0[q], u1 = U1[q], u2 = U2[q], u3 = U3[q];
+          Wc[q] = (((Wc[q] - w[0] * u0) - w[1] * u1) - w[2] * u2) - w[3] * u3;
+          Vc[q] = (((Vc[q] - v[0] * u0) - v[1] * u1) - v[2] * u2) - v[3] * u3;
+        }
+      }
+      for (; c < c1; ++c) {
+        double* __restrict__ Wc = &W[(size_t)c * n];
+        double w[4];
+        mult(Wc, w);
+        for (int q = k + 4; q < n; ++q) Wc[q] = (((Wc[q] - w[0] * U0[q]) - w[1] * U1[q]) - w[2] * U2[q]) - w[3] * U3[q];
       }
     }
     for (; k < n; ++k) {
@@ -167,7 +209,20 @@ void spd_inverse(int n, double* A) {
       const double* Z1 = Z0 + n;
       const double* Z2 = Z1 + n;
       const double* Z3 = Z2 + n;
-      for (int i = i0; i < i1; ++i) {
+      int i = i0;
+      for (; i + 2 <= i1; i += 2) {  // rows i, i + 1; entry j = i + 1 is row i + 1's only
+        const double a0 = Z0[i], a1 = Z1[i], a2 = Z2[i], a3 = Z3[i];
+        const double b0 = Z0[i + 1], b1 = Z1[i + 1], b2 = Z2[i + 1], b3 = Z3[i + 1];
+        double* __restrict__ Ai = A + (size_t)i * n;
+        double* __restrict__ Bi = Ai + n;
+        for (int j = 0; j <= i; ++j) {
+          const double z0 = Z0[j], z1 = Z1[j], z2 = Z2[j], z3 = Z3[j];
+          Ai[j] = (((Ai[j] + a0 * z0) + a1 * z1) + a2 * z2) + a3 * z3;
+          Bi[j] = (((Bi[j] + b0 * z0) + b1 * z1) + b2 * z2) + b3 * z3;
+        }
+        Bi[i + 1] = (((Bi[i + 1] + b0 * Z0[i + 1]) + b1 * Z1[i + 1]) + b2 * Z2[i + 1]) + b3 * Z3[i + 1];
+      }
+      for (; i < i1; ++i) {
         const double a0 = Z0[i], a1 = Z1[i], a2 = Z2[i], a3 = Z3[i];
         double* __restrict__ Ai = A + (size_t)i * n;
         for (int j = 0; j <= i; ++j) Ai[j] = (((Ai[j] + a0 * Z0[j]) + a1 * Z1[j]) + a2 * Z2[j]) + a3 * Z3[j];
