@@ -1051,17 +1051,20 @@ void cut_patch_inverses(const RefTables& R, HostLevel& L, bool invert) {
         st *= N;
       }
       const double* K = (f & kFlagCut) ? &L.cutmat[(size_t)L.cut_id[cf] * NB * NB] : L.Kref.data();
-      int mi[64];
+      // the cell's nodes that are patch DoFs (va, in node order) and their rows
+      int mi[64], va[64], nv = 0;
       for (int jl = 0; jl < NB; ++jl) {
         int a[3] = {0, 0, 0}, lat[3] = {0, 0, 0};
         R.split(jl, a);
         for (int k = 0; k < d; ++k) lat[k] = p * c[k] + a[k];
         mi[jl] = closure_of(lat);
+        if (mi[jl] >= 0) va[nv++] = jl;
       }
-      for (int a = 0; a < NB; ++a) {
-        if (mi[a] < 0) continue;
-        for (int b = 0; b < NB; ++b)
-          if (mi[b] >= 0) A[(size_t)mi[a] * m + mi[b]] += K[a * NB + b];
+      for (int x = 0; x < nv; ++x) {
+        const int a = va[x];
+        double* Ar = A + (size_t)mi[a] * m;
+        const double* Ka = K + a * NB;
+        for (int y = 0; y < nv; ++y) Ar[mi[va[y]]] += Ka[va[y]];
       }
     }
     // ghost faces touching a patch cell: lower cell Lc, upper Lc + e_k
@@ -1080,19 +1083,19 @@ void cut_patch_inverses(const RefTables& R, HostLevel& L, bool invert) {
             uint8_t f1 = cflag_at(lc), f2 = cflag_at(uc);
             if (!((f1 & kFlagActive) && (f2 & kFlagActive) && ((f1 | f2) & kFlagCut))) continue;
             // block nodes: i in [0, 2p] along k, t in [0, p] tangential
-            int mi[7 * 16];
+            int mi[7 * 16], ve[7 * 16], nv = 0;
             for (int e = 0; e < nbk; ++e) {
               int lat[3] = {0, 0, 0}, q = 0;
               for (int kk = 0; kk < d; ++kk)
                 lat[kk] = p * lc[kk] + (kk == k ? fb_i[e] : fb_t[e * 2 + q++]);
               mi[e] = closure_of(lat);
+              if (mi[e] >= 0) ve[nv++] = e;
             }
-            for (int e1 = 0; e1 < nbk; ++e1) {
-              if (mi[e1] < 0) continue;
+            for (int x = 0; x < nv; ++x) {
+              const int e1 = ve[x];
               const double* fr = &fblk[(size_t)e1 * nbk];
               double* Ar = A + (size_t)mi[e1] * m;
-              for (int e2 = 0; e2 < nbk; ++e2)
-                if (mi[e2] >= 0) Ar[mi[e2]] += fr[e2];
+              for (int y = 0; y < nv; ++y) Ar[mi[ve[y]]] += fr[ve[y]];
             }
           }
     }
