@@ -698,6 +698,30 @@ void cut_patch_members(HostLevel& L, bool dry) {
   const int64_t ncp = (int64_t)L.cut_vert.size();
   auto cflag_at = [&](const int* c) { return cell_flag(L, c); };
   // members: closure nodes all of whose active cells are patch cells
+  // closure node o: its coordinates in the (2p+1)^d closure and, along each
+  // direction, the cells containing it as offsets from the patch's first
+  // cell v - 1 (two where the node lies on a cell boundary)
+  struct ClosureNode {
+    int oc[3], rc[3][2], nrc[3];
+  };
+  std::vector<ClosureNode> cnode(NCL);
+  for (int o = 0; o < NCL; ++o) {
+    ClosureNode& q = cnode[o];
+    int u = o;
+    for (int k = 0; k < 3; ++k) {
+      q.oc[k] = 0;
+      q.rc[k][0] = q.rc[k][1] = 0;
+      q.nrc[k] = 1;
+    }
+    for (int k = 0; k < d; ++k) {
+      const int ok = u % C;
+      u /= C;
+      q.oc[k] = ok;
+      q.rc[k][0] = (ok % p == 0) ? ok / p - 1 : ok / p;
+      q.rc[k][1] = ok / p;
+      q.nrc[k] = (ok % p == 0) ? 2 : 1;
+    }
+  }
   std::vector<std::vector<uint16_t>> mem(ncp);
 #pragma omp parallel for schedule(dynamic, 64)
   for (int64_t j = 0; j < ncp; ++j) {
@@ -708,29 +732,27 @@ void cut_patch_members(HostLevel& L, bool dry) {
       t /= np;
     }
     for (int o = 0; o < NCL; ++o) {
-      int oc[3] = {0, 0, 0}, li[3] = {0, 0, 0}, u = o;
+      const ClosureNode& q = cnode[o];
       bool valid = true;
       for (int k = 0; k < d; ++k) {
-        oc[k] = u % C;
-        u /= C;
-        li[k] = p * (v[k] - 1) + oc[k];
-        if (li[k] < 0 || li[k] >= n) valid = false;
+        const int li = p * (v[k] - 1) + q.oc[k];
+        if (li < 0 || li >= n) valid = false;
       }
       if (!valid) continue;
-      int cc[3][2], lc[3][2], nc[3] = {1, 1, 1};
-      for (int k = 0; k < d; ++k) nc[k] = cells_of(li[k], p, N, cc[k], lc[k]);
       bool inside = false, outside = false;
-      int tot = nc[0] * nc[1] * nc[2];
-      for (int s = 0; s < tot; ++s) {
-        int c[3] = {0, 0, 0}, r = s;
-        bool in_patch = true;
-        for (int k = 0; k < d; ++k) {
-          c[k] = cc[k][r % nc[k]];
-          r /= nc[k];
-          if (c[k] != v[k] - 1 && c[k] != v[k]) in_patch = false;
-        }
-        if (cflag_at(c) & kFlagActive) (in_patch ? inside : outside) = true;
-      }
+      for (int s2 = 0; s2 < q.nrc[2]; ++s2)
+        for (int s1 = 0; s1 < q.nrc[1]; ++s1)
+          for (int s0 = 0; s0 < q.nrc[0]; ++s0) {
+            const int r[3] = {q.rc[0][s0], q.rc[1][s1], q.rc[2][s2]};
+            int c[3] = {0, 0, 0};
+            bool in_mesh = true, in_patch = true;
+            for (int k = 0; k < d; ++k) {
+              c[k] = v[k] - 1 + r[k];
+              if (c[k] < 0 || c[k] >= N) in_mesh = false;
+              if (r[k] != 0 && r[k] != 1) in_patch = false;
+            }
+            if (in_mesh && (cflag_at(c) & kFlagActive)) (in_patch ? inside : outside) = true;
+          }
       if (inside && !outside) mem[j].push_back((uint16_t)o);
     }
   }
