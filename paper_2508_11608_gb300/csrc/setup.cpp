@@ -14,6 +14,7 @@
 #include "setup.hpp"
 
 #include <algorithm>
+#include <array>
 #include <functional>
 
 #include <omp.h>
@@ -1276,25 +1277,48 @@ void cut_patch_records(HostLevel& L, bool dry) {
     const int C = 2 * p + 1, NTf = ipow(p + 1, d - 1);
     (void)NTf;
     std::vector<std::vector<uint16_t>> lists(ncp);
+    // closure-local digits of every closure node, and per digit its cell
+    // layer and whether it lies on a layer boundary
+    const int NCLc = ipow(C, d), nbits = 3 * d * half;
+    std::vector<std::array<int, 3>> digits(NCLc);
+    for (int o = 0; o < NCLc; ++o) {
+      int u = o;
+      digits[o] = {0, 0, 0};
+      for (int k = 0; k < d; ++k) {
+        digits[o][k] = u % C;
+        u /= C;
+      }
+    }
+    int lay_of[16], on_of[16];
+    for (int ok = 0; ok < C; ++ok) {
+      lay_of[ok] = ok / p;
+      on_of[ok] = ok % p == 0;
+    }
 #pragma omp parallel for schedule(dynamic, 64)
     for (int64_t j = 0; j < ncp; ++j) {
       const int m = L.cut_n[j];
+      const uint64_t gm = L.cut_gmask[j];
+      // moment slot of every set face bit: the block-boundary faces first
+      // (bit order), then the middle-plane faces (bit order)
+      int slot_of[64];
+      for (int bit = 0; bit < nbits; ++bit) {
+        const uint64_t below = (1ull << bit) - 1ull;
+        slot_of[bit] = ((bnd_bits >> bit) & 1ull)
+                           ? __builtin_popcountll(gm & bnd_bits & below)
+                           : __builtin_popcountll(gm & bnd_bits) + __builtin_popcountll(gm & ~bnd_bits & below);
+      }
       std::vector<uint16_t> offs(m + 1, 0), ent;
       for (int e = 0; e < m; ++e) {
-        int o[3] = {0, 0, 0}, u = L.members[L.cut_moff[j] + e];
+        const std::array<int, 3>& o = digits[L.members[L.cut_moff[j] + e]];
         for (int k = 0; k < d; ++k) {
-          o[k] = u % C;
-          u /= C;
-        }
-        for (int k = 0; k < d; ++k) {
-          const int ok = o[k], lay = ok / p, onp = ok - lay * p == 0;
+          const int ok = o[k], lay = lay_of[ok], onp = on_of[ok];
           const int Llo = std::max(0, onp ? lay - 1 : lay), Lhi = std::min(2, lay + 1);
           for (int Lp = Llo; Lp <= Lhi; ++Lp) {
             const int i = ok - p * (Lp - 1);
             int ulo[2] = {0, 0}, uhi[2] = {0, 0}, tj[2] = {0, 0}, q = 0;
             for (int kk = 0; kk < d; ++kk) {
               if (kk == k) continue;
-              const int oj = o[kk], cj = oj / p, on = oj - cj * p == 0;
+              const int oj = o[kk], cj = lay_of[oj], on = on_of[oj];
               ulo[q] = std::max(0, on ? cj - 1 : cj);
               uhi[q] = std::min(1, cj);
               tj[q] = oj;
@@ -1303,15 +1327,9 @@ void cut_patch_records(HostLevel& L, bool dry) {
             for (int u1 = (d == 3 ? ulo[1] : 0); u1 <= (d == 3 ? uhi[1] : 0); ++u1)
               for (int u0 = ulo[0]; u0 <= uhi[0]; ++u0) {
                 const int bit = (k * 3 + Lp) * half + u0 + 2 * u1;
-                const uint64_t gm = L.cut_gmask[j], below = (1ull << bit) - 1ull;
                 if (!((gm >> bit) & 1ull)) continue;
-                // moment slot of the face: the block-boundary faces first
-                // (bit order), then the middle-plane faces (bit order)
-                const int slot = ((bnd_bits >> bit) & 1ull)
-                                     ? __builtin_popcountll(gm & bnd_bits & below)
-                                     : __builtin_popcountll(gm & bnd_bits) + __builtin_popcountll(gm & ~bnd_bits & below);
                 const int t = (tj[0] - p * u0) + (d == 3 ? (p + 1) * (tj[1] - p * u1) : 0);
-                ent.push_back((uint16_t)(slot | (i << 6) | (t << 10)));
+                ent.push_back((uint16_t)(slot_of[bit] | (i << 6) | (t << 10)));
               }
           }
         }
