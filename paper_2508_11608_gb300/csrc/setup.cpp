@@ -1806,7 +1806,7 @@ void tensor_contract(int d, int p, int q, const double* Lt, const double* F, dou
 
 void build_rhs(const SetupParams& prm, const RefTables& R, const HostLevel& L, std::vector<double>& b,
                const std::function<double(const double*)>& fsrc, const std::function<double(const double*)>& gdir,
-               bool parallel, const std::vector<double>* cut_rhs = nullptr) {
+               bool parallel, const std::vector<double>* cut_rhs = nullptr, bool manufactured = false) {
   const int d = L.d, p = L.p, N = L.N, n = L.n, NB = R.NB, q = prm.quad_q;
   const double h = L.h;
   const int64_t nnode = ipow(n, d), ndof = (int64_t)L.dofs.size();
@@ -1852,16 +1852,36 @@ void build_rhs(const SetupParams& prm, const RefTables& R, const HostLevel& L, s
       if (!(f & kFlagCut)) {
         // tensor Gauss rule: f w at every point, then sum factorisation
         double* F = Fw.data();
-        for (int iq = 0; iq < nq; ++iq) {
-          double x[3] = {0, 0, 0}, w = 1.0;
-          int u = iq;
-          for (int k = 0; k < d; ++k) {
-            int a = u % q;
-            u /= q;
-            w *= g.w[a];
-            x[k] = lo[k] + h * g.x[a];
+        if (manufactured && q <= 16) {
+          // fsrc is the manufactured source d pi^2 prod_k sin(pi x_k): each
+          // direction's q sines once per cell, multiplied as fsrc does
+          double sn[3][16];
+          for (int k = 0; k < d; ++k)
+            for (int a = 0; a < q; ++a) sn[k][a] = std::sin(M_PI * (lo[k] + h * g.x[a]));
+          for (int iq = 0; iq < nq; ++iq) {
+            double w = 1.0, uv = 1.0;
+            int u = iq;
+            for (int k = 0; k < d; ++k) {
+              int a = u % q;
+              u /= q;
+              w *= g.w[a];
+              uv *= sn[k][a];
+            }
+            const double fv = d * M_PI * M_PI * uv;
+            F[iq] = fv * w * hd;
           }
-          F[iq] = fsrc(x) * w * hd;
+        } else {
+          for (int iq = 0; iq < nq; ++iq) {
+            double x[3] = {0, 0, 0}, w = 1.0;
+            int u = iq;
+            for (int k = 0; k < d; ++k) {
+              int a = u % q;
+              u /= q;
+              w *= g.w[a];
+              x[k] = lo[k] + h * g.x[a];
+            }
+            F[iq] = fsrc(x) * w * hd;
+          }
         }
         tensor_contract(d, p, q, Lt.data(), F, loc, F + nq);
       } else if (cut_rhs) {
@@ -1979,7 +1999,7 @@ void build_hierarchy(const SetupParams& prm, Hierarchy& H) {
   build_coarse(R, H.levels[0]);
   if (prm.smoother == 1)
     for (size_t l = 1; l < H.levels.size(); ++l) build_diag(R, H.levels[l]);
-  build_rhs(prm, R, H.levels.back(), H.rhs, fman, gman, true, &cut_rhs);
+  build_rhs(prm, R, H.levels.back(), H.rhs, fman, gman, true, &cut_rhs, true);
 }
 
 void build_rhs_user(const Hierarchy& H, double (*f)(const double*, void*), double (*g)(const double*, void*),
